@@ -1,0 +1,349 @@
+#!/usr/bin/env python
+"""Benchmark of one backward-Euler Oseen time step of the P2/P1 Navier-Stokes
+discretisation (assembly + preconditioned FGMRES solve) through the C ABI.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fs|reference]
+
+A "step" is one full pass of the hot path: per-step convection assembly,
+right-hand side and boundary rows, then the Krylov solve to a relative FP64
+residual of 1e-14.  The default workload is the 2D channel 512x96
+(98,304 triangles, 445,411 DOF, nu = 1e-3, dt = 1e-3).  Prints one JSON line.
+Under torchrun each rank runs an independent replica (the single-mesh path
+does not shard); the whole-job value is the steps of all ranks divided by the
+slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "NS steps/s & DOF/s vs plain FP64 GPU path; % HBM roofline; p50/p99 latency"
+L2_FLUSH_BYTES = 256 << 20  # > 135 MB of L2
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=40)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="fs", choices=["fs", "reference"])
+    p.add_argument("--workload", default="channel", choices=["channel", "unit_square", "cube"])
+    p.add_argument("--precision", default="fp32_refine", choices=["fp32_refine", "fp64"])
+    p.add_argument("--fp64-steps", type=int, default=20,
+                   help="steps of the plain FP64 path timed for the comparison")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--roofline-kernel", default="cheb", choices=["cheb", "spmv", "assemble"])
+    return p.parse_args()
+
+
+def workload(name):
+    import fs_workloads as W
+    return {"channel": W.C2, "unit_square": W.C1, "cube": W.C3}[name]
+
+
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled every 200 ms (reads only)."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.index)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        rows = []
+        for line in out.strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(parts[1]), smax=float(parts[2]),
+                                 hw=parts[5], hwt=parts[6], swt=parts[7], pcap=parts[8]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        reasons = set()
+        for r in rows:
+            for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"),
+                              ("swt", "sw_thermal_slowdown"), ("pcap", "sw_power_cap")):
+                if r[key].lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r["sm"] for r in rows),
+                "sm_max_mhz": max(r["smax"] for r in rows), "reasons": sorted(reasons),
+                "samples": len(rows)}
+
+
+def measured_peak_hbm():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def traffic_from_profiles(kernel, wl_name):
+    """DRAM bytes per launch from the committed ncu summary, or None."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    try:
+        for line in open(path):
+            parts = line.split()
+            if len(parts) >= 3 and not line.startswith("#") and parts[0] == kernel \
+                    and parts[1] == wl_name:
+                return float(parts[2])
+    except OSError:
+        pass
+    return None
+
+
+# ---------------------------------------------------------------------------
+def oracle_sample():
+    """One oracle step of the 128x24 channel (28,411 DOF); returns (seconds,
+    sample DOF).  Single-threaded plain C."""
+    import fs_workloads as W
+    from oracle import oracle as O
+    wl = W.channel(128, 24)
+    P = O.Problem(dim=wl.dim, n=wl.n, lo=wl.lo, hi=wl.hi, problem=wl.problem, nu=wl.nu,
+                  dt=wl.dt, jitter=wl.jitter, seed=wl.seed, side_mask=wl.side_mask,
+                  pin_p0=wl.pin_p0, init=wl.init)
+    t0 = time.perf_counter()
+    P.step(rtol=1e-14)
+    return time.perf_counter() - t0, P.ndof
+
+
+def reference_arm(args, rank):
+    if rank != 0:
+        return 0
+    wl = workload(args.workload)
+    from oracle import oracle as O
+    O.build()
+    for _ in range(max(args.warmup, 0)):
+        oracle_sample()
+    secs, dofs = [], 0
+    for _ in range(args.steps):
+        s, dofs = oracle_sample()
+        secs.append(s)
+    total = sum(secs)
+    dof_s = dofs * len(secs) / total
+    value = dof_s / wl.ndof
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * wl.ndof / dof_s, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl.name, "ndof": wl.ndof, "l2": "sample far below L2 reuse"},
+        "cpu_baseline": {"value": value, "unit": "steps/s", "cores": 1, "kind": "oracle",
+                         "sample": f"each step = one oracle backward-Euler Oseen step of the "
+                                   f"128x24 channel ({dofs} DOF; COO assembly + ILU(0)-GMRES "
+                                   f"to 1e-14), scaled to {wl.ndof} DOF by DOF/s"},
+        "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+def time_steps(torch, fs, S, stream, steps, flush):
+    """Per-step CUDA-event times (ms) of fs_step on the problem's stream;
+    L2 flushed (256 MB write) before each step, outside the timed window."""
+    out = []
+    stats = []
+    for _ in range(steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        stream.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = fs.fs_step(S.prob, 1)[0]
+        e1.record(stream)
+        e1.synchronize()
+        out.append(e0.elapsed_time(e1))
+        stats.append(st)
+    return out, stats
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return reference_arm(args, rank)
+
+    import numpy as np
+    import torch
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device (the CUDA path has no CPU fallback)")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import __graft_entry__ as G
+    G.build()
+    import fs_workloads as W
+    from paper_2605_25403_gb300 import fs
+
+    wl = workload(args.workload)
+    prec = fs.FS_PREC_FP32_REFINE if args.precision == "fp32_refine" else fs.FS_PREC_FP64
+    stream = torch.cuda.Stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    # ---- plain FP64 GPU path (the in-repo baseline) ----------------------
+    fp64 = None
+    k64 = args.fp64_steps
+    if prec != fs.FS_PREC_FP64 and k64 > 0:
+        S64 = fs.Stepper.from_workload(wl, precision=fs.FS_PREC_FP64, stream=stream.cuda_stream)
+        for _ in range(args.warmup):
+            fs.fs_step(S64.prob, 1)
+        t64, st64 = time_steps(torch, fs, S64, stream, k64, flush)
+        fp64 = {"steps_per_s": 1e3 * len(t64) / sum(t64),
+                "ms_per_step": sum(t64) / len(t64),
+                "iters_per_step": float(np.mean([s["iters"] for s in st64])),
+                "rel_res_max": max(s["rel_res"] for s in st64)}
+        S64.close()
+
+    # ---- the timed path ----------------------------------------------------
+    S = fs.Stepper.from_workload(wl, precision=prec, stream=stream.cuda_stream)
+    for _ in range(args.warmup):
+        fs.fs_step(S.prob, 1)
+    sampler = ClockSampler(local)
+    sampler.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = fs.fs_launch_count()
+    times, stats = time_steps(torch, fs, S, stream, args.steps, flush)
+    launches = fs.fs_launch_count() - l0
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    total_s = sum(times) / 1e3
+    if dist:
+        t = torch.tensor([total_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = world * args.steps / total_s
+    ms_per_step = 1e3 * total_s / args.steps
+
+    # ---- end to end through the C ABI with host buffers --------------------
+    ndof = S.info["n_dof"]
+    xh = torch.empty(ndof, dtype=torch.float64).pin_memory()
+    xn = xh.numpy()
+    x0, t0 = fs.fs_get_state(S.prob)
+    xn[:] = x0
+    tcur = t0
+    e2e_ms = []
+    for k in range(max(2, args.steps // 2) + 1):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fs.fs_set_state(S.prob, xn, tcur)                 # H2D of the step's input
+        fs.fs_step(S.prob, 1)
+        x_new, tcur = fs.fs_get_state(S.prob)            # D2H of the step's result
+        e1.record(stream)
+        e1.synchronize()
+        xn[:] = x_new
+        if k > 0:
+            e2e_ms.append(e0.elapsed_time(e1))
+    e2e_val = world * len(e2e_ms) / (sum(e2e_ms) / 1e3)
+
+    # ---- roofline of the dominant kernel ----------------------------------
+    kid = {"cheb": fs.FS_KERNEL_CHEB, "spmv": fs.FS_KERNEL_SPMV,
+           "assemble": fs.FS_KERNEL_ASSEMBLE_CONV}[args.roofline_kernel]
+    kernels = {}
+    for name, k in (("cheb", fs.FS_KERNEL_CHEB), ("spmv", fs.FS_KERNEL_SPMV),
+                    ("spmv_fp64", fs.FS_KERNEL_SPMV_FP64),
+                    ("assemble", fs.FS_KERNEL_ASSEMBLE_CONV)):
+        ms, by = fs.fs_profile_kernel(S.prob, k, reps=20)
+        kernels[name] = {"ms": ms, "alg_bytes": by, "gbs": by / ms / 1e6}
+    peak, peak_kind = measured_peak_hbm()
+    kname = args.roofline_kernel
+    achieved = kernels[kname]["gbs"]
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_kind,
+                "kernel": {"cheb": "k_cheb (fused Chebyshev step, finest P2 level)",
+                           "spmv": "k_spmv_full", "assemble": "k_assemble_conv"}[kname],
+                "traffic": traffic_from_profiles(kname, wl.name)}
+
+    # ---- CPU baseline: the oracle on a bounded sample ---------------------
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        secs, dofs = oracle_sample()
+        cpu = {"value": dofs / secs / wl.ndof, "unit": "steps/s", "cores": 1, "kind": "oracle",
+               "sample": f"one oracle step of the 128x24 channel ({dofs} DOF, COO assembly + "
+                         f"ILU(0)-GMRES to 1e-14) in {secs:.2f} s, scaled to {wl.ndof} DOF by "
+                         f"DOF/s"}
+
+    S.close()
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+    iters = [s["iters"] for s in stats]
+    line = {
+        "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "fp32+fp64" if prec == fs.FS_PREC_FP32_REFINE else "f64",
+        "data": "synthetic",
+        "config": {"workload": wl.name, "ndof": ndof, "cells": wl.ncell, "nu": wl.nu,
+                   "dt": wl.dt, "precision": args.precision, "rtol": 1e-14,
+                   "l2": "flushed before every timed step (256 MB write)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "dof_per_s": value * ndof,
+        "step_ms_p50": statistics.median(times),
+        "step_ms_p99": float(np.percentile(times, 99)),
+        "iters_per_step": float(np.mean(iters)),
+        "refinements_per_step": float(np.mean([s["refinements"] for s in stats])),
+        "rel_res_max": max(s["rel_res"] for s in stats),
+        "fp64_path": fp64,
+        "vs_fp64_path": (value / world) / fp64["steps_per_s"] if fp64 else None,
+        "clocks": clocks,
+        "e2e": {"value": e2e_val, "unit": "steps/s", "h2d_bytes_per_step": 8 * ndof,
+                "d2h_bytes_per_step": 8 * ndof},
+        "gpu_launches": launches,
+        "roofline": roofline,
+        "kernels": kernels,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,238 @@
+/*
+ * fs.h -- C ABI of the GB300-native Taylor-Hood P2/P1 Navier-Stokes stepper.
+ *
+ * One time step is the backward-Euler Oseen linearisation of the unsteady
+ * incompressible Navier-Stokes equations (paper, Sec. 2.1 Eq. (3) and
+ * Sec. 2.2.1, the Oseen equation with the convecting velocity lagged to
+ * u_h^n): find u in V_h = [P2]^d, p in Q_h = P1 with
+ *     ((u - u^n)/dt, v) + ((u^n . grad) u, v) + nu (grad u, grad v)
+ *       - (p, div v) = (f^{n+1}, v),        (div u, q) = 0.
+ * The library assembles this system on the GPU into a fixed sparsity
+ * pattern and solves it with a right-preconditioned flexible GMRES(m)
+ * (the paper's linear solver module, Sec. 3.2: GMRES).
+ *
+ * Conventions for every call:
+ *  - Ownership: the library owns every handle and every device buffer it
+ *    allocates; pointers passed in are borrowed for the duration of the call
+ *    and are never freed by the library.
+ *  - Device pointers are CUDA global-memory pointers on the current device;
+ *    host pointers are plain malloc/numpy memory.  Each argument says which.
+ *  - Streams: a problem runs every launch on the cudaStream_t given at
+ *    creation (NULL = the legacy default stream).  Calls return when the
+ *    work is enqueued unless they say they synchronise.
+ *  - Errors: every call returns an fs_status; FS_OK is 0.  A message with
+ *    details is available from fs_last_error() (thread-local, valid until
+ *    the next call on the same thread).  Device-side failures (iteration
+ *    caps, NaN/Inf, bounded waits that ran out) come back as status codes;
+ *    no kernel traps.
+ *  - Layouts: unknown vectors are component-blocked
+ *    [u_x (n_p2) | u_y (n_p2) | u_z (n_p2, 3D only) | p (n_vert)], FP64.
+ *    P2 node ids: vertices first (0..n_vert-1), then edge midpoints in the
+ *    lexicographic order of their (min,max) vertex pairs.
+ */
+#ifndef FS_H
+#define FS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FS_OK = 0,
+  FS_ERR_INVALID_ARG = 1,
+  FS_ERR_INVALID_MESH = 2,
+  FS_ERR_OOM = 3,
+  FS_ERR_CUDA = 4,
+  FS_ERR_NOT_CONVERGED = 5,
+  FS_ERR_NUMERIC = 6,
+  FS_ERR_TIMEOUT = 7,
+  FS_ERR_BUSY = 8,
+  FS_ERR_UNSUPPORTED = 9
+} fs_status;
+
+/* Built-in manufactured problems (the paper's problem library, Sec. 3.1
+ * "MathModel"; solutions of Sec. 3.3 and Sec. 4.1). */
+typedef enum {
+  FS_PROBLEM_UNSTEADY_BENCH = 0, /* 2D, Sec. 4.1: u1 = 2 pi sin t sin^2(pi x)
+                                    sin(pi y) cos(pi y), u2 = -2 pi sin t
+                                    sin(pi x) cos(pi x) sin^2(pi y),
+                                    p = 20 sin t (x^2 y - 1/6)            */
+  FS_PROBLEM_STEADY_POLY = 1,    /* 2D, Sec. 3.3 polynomial solution (no
+                                    time derivative in f)                 */
+  FS_PROBLEM_CHANNEL = 2,        /* 2D channel [0,2.2]x[0,0.41]: Poiseuille
+                                    inflow U_max = 1.5, f = 0             */
+  FS_PROBLEM_CUBE = 3,           /* 3D: u = sin t curl(Phi (1,1,1)),
+                                    Phi = sin^2(pi x) sin^2(pi y) sin^2(pi z),
+                                    p = sin t (x^2 y z - 1/12)            */
+  FS_PROBLEM_POLY_OSEEN = 4      /* u in P2 (div-free), p in P1, constant
+                                    convecting field wconst (exactness)   */
+} fs_problem_kind;
+
+typedef enum {
+  FS_PREC_FP64 = 0,        /* everything in FP64 (the plain FP64 path)     */
+  FS_PREC_FP32_REFINE = 1  /* FP32 inner FGMRES + preconditioner, FP64
+                              iterative refinement on r = b - A x          */
+} fs_precision;
+
+/* Dirichlet side bits: 1 x=lo, 2 x=hi, 4 y=lo, 8 y=hi, 16 z=lo, 32 z=hi. */
+typedef struct {
+  int dim;             /* 2 (triangles) or 3 (tetrahedra)                   */
+  int n[3];            /* cells per axis (n[2] ignored in 2D), each >= 1    */
+  double lo[3], hi[3]; /* box corners                                       */
+  double jitter;       /* interior vertices move by jitter*h*(2U-1) per axis,
+                          U from SplitMix64(seed ^ (3 v + axis)); < 0.25   */
+  uint64_t seed;
+  int dirichlet_sides; /* bit mask of sides carrying Dirichlet velocity      */
+} fs_mesh_desc;
+
+typedef struct fs_mesh fs_mesh;
+typedef struct fs_problem fs_problem;
+
+/* Builds a structured simplicial mesh (Sec. 2.2.1: a conforming mesh T_h;
+ * Sec. 3.3: init_mesh['uniform_tri']): 2 triangles per square split along
+ * v00-v11, or the 6 Kuhn tetrahedra per cube, the P2/P1 DOF map and the
+ * block CSR patterns with their per-element slot tables.  Host memory only
+ * until a problem is created on it.  Fails with FS_ERR_INVALID_MESH when a
+ * simplex is degenerate (|det J| <= 1e-12 h^d).  *out receives the handle. */
+int fs_mesh_create(const fs_mesh_desc* desc, fs_mesh** out);
+int fs_mesh_destroy(fs_mesh* mesh);
+
+/* Sizes of the Taylor-Hood P2/P1 discretisation (Sec. 2.2.1, V_h and Q_h
+ * with k = 2).  nnz counts the monolithic saddle-point CSR
+ *   [A 0 -Bx^T; 0 A -By^T; Bx By D] (3D analogous) with an explicit
+ * pressure diagonal D; nnz_a, nnz_b count the scalar P2-P2 block and one
+ * P1-P2 divergence block. */
+typedef struct {
+  int dim, nloc;
+  int64_t n_vert, n_edge, n_p2, n_cell, n_dof, nnz, nnz_a, nnz_b;
+} fs_dofmap_info;
+
+/* DOF map export (Sec. 3.1 "DOF management").  Every output pointer is a
+ * host pointer and may be NULL to skip it:
+ *   coords   n_vert x dim   FP64 vertex coordinates
+ *   cell2dof n_cell x nloc  P2 node ids per cell: vertices, then edges
+ *                           (triangle (1,2),(2,0),(0,1); tetrahedron
+ *                           (0,1),(0,2),(0,3),(1,2),(1,3),(2,3))
+ *   rowptr   n_dof + 1      int64 monolithic CSR row pointers
+ *   col      nnz            int32 columns, strictly ascending per row
+ *   dirichlet n_p2          1 for Dirichlet P2 nodes
+ * info (required) receives the sizes. */
+int fs_dof_map(const fs_mesh* mesh, fs_dofmap_info* info, double* coords,
+               int32_t* cell2dof, int64_t* rowptr, int32_t* col,
+               uint8_t* dirichlet);
+
+typedef struct {
+  int problem;       /* fs_problem_kind                                     */
+  double nu;         /* kinematic viscosity                                 */
+  double dt;         /* time step (> 0)                                     */
+  double t0;         /* initial time                                        */
+  int precision;     /* fs_precision                                        */
+  int pin_pressure;  /* 1: pressure row of vertex 0 -> identity holding
+                        p_exact(x_0, t) (all-Dirichlet boundaries)          */
+  int init;          /* 0: u^0 = I_h u(., t0); 1: zero inside, exact on
+                        Dirichlet nodes                                     */
+  double wconst[3];  /* constant convecting field (FS_PROBLEM_POLY_OSEEN)   */
+} fs_problem_desc;
+
+/* Creates a device-resident problem on `mesh` (which must outlive it):
+ * uploads the mesh tables, assembles the step-invariant parts (P2 mass,
+ * viscous and divergence blocks, the P1 pressure Laplacian and lumped mass)
+ * and builds the multigrid hierarchies of the preconditioner.  `stream` is
+ * a cudaStream_t (NULL = default stream).  Synchronises. */
+int fs_problem_create(fs_mesh* mesh, const fs_problem_desc* desc,
+                      void* stream, fs_problem** out);
+int fs_problem_destroy(fs_problem* prob);
+
+/* Assembles the Oseen system of the step t -> t_next (paper Sec. 2.2.1,
+ * Oseen equation; BForm/LForm of Sec. 3.1) with the convecting velocity
+ * w = u^n taken from the current state (or wconst), into the problem's
+ * fixed block-CSR values, and the right-hand side
+ *   b_u = M (u^n/dt + I_h f(t_next)),  b_p = 0,
+ * with Dirichlet rows replaced by identity rows holding u_exact(t_next) and
+ * the pinned pressure row holding p_exact(x_0, t_next).
+ * val_out (device, FP64, monolithic nnz, may be NULL) receives the values in
+ * the monolithic CSR order of fs_dof_map; b_out (device, FP64, n_dof, may be
+ * NULL) the right-hand side. */
+int fs_assemble_step(fs_problem* prob, double t_next, double* val_out,
+                     double* b_out);
+
+typedef struct {
+  int restart;        /* GMRES(m) restart length m (<= 64)                  */
+  int max_iter;       /* cap on (inner) Krylov iterations per solve         */
+  double rtol;        /* stop at ||b - A x||_2 <= rtol ||b||_2, FP64 true
+                         residual; a residual that stops decreasing (a
+                         restart cycle or refinement step that no longer
+                         contracts) is accepted within 100 rtol, the
+                         rounding floor of the system                      */
+  double inner_rtol;  /* FP32 inner solve tolerance (precision mode)        */
+  int max_refine;     /* cap on FP64 refinement steps (precision mode)      */
+  int use_graph;      /* 1: replay restart cycles as captured CUDA graphs   */
+} fs_solve_opts;
+
+typedef struct {
+  int iters;          /* Krylov iterations (inner ones in precision mode)   */
+  int refinements;    /* FP64 refinement steps (0 in FP64 mode)             */
+  int status;         /* fs_status of the solve                             */
+  int cycles;         /* GMRES restart cycles                               */
+  double rel_res;     /* final FP64 ||b - A x|| / ||b||                     */
+} fs_solve_stats;
+
+/* Fills opts with the defaults: m = 30, max_iter 2000, rtol 1e-14, inner_rtol
+ * 1e-5, max_refine 30, use_graph 1. */
+void fs_default_solve_opts(fs_solve_opts* opts);
+
+/* Solves the system last assembled by fs_assemble_step (paper Sec. 3.2,
+ * GMRES) with right-preconditioned flexible GMRES(m); the preconditioner is
+ * block upper-triangular: Cahouet-Chabard Schur approximation
+ * nu Mp^-1 + dt^-1 Kp^-1 and a multigrid V-cycle on the velocity block.
+ * x (device, FP64, n_dof) holds the initial guess and receives the solution;
+ * NULL means the problem's state vector.  Synchronises.  stats may be NULL.
+ * Returns FS_ERR_NOT_CONVERGED (with the best iterate kept) when max_iter or
+ * max_refine is reached first, FS_ERR_NUMERIC on NaN/Inf. */
+int fs_solve(fs_problem* prob, const fs_solve_opts* opts, double* x,
+             fs_solve_stats* stats);
+
+/* nsteps backward-Euler Oseen steps: assemble (w = u^n), solve, t += dt.
+ * per_step (host, nsteps entries, may be NULL) receives each solve's stats.
+ * Synchronises. */
+int fs_step(fs_problem* prob, int nsteps, const fs_solve_opts* opts,
+            fs_solve_stats* per_step);
+
+/* y = A x with the assembled FP64 saddle-point operator (device FP64
+ * vectors of n_dof entries). */
+int fs_apply_operator(fs_problem* prob, const double* x, double* y);
+
+/* State access: x (n_dof FP64) and the current time.  x_out/x_in are host
+ * pointers when `host` is 1, device pointers otherwise.  Synchronises. */
+int fs_get_state(fs_problem* prob, double* x_out, int host, double* t_out);
+int fs_set_state(fs_problem* prob, const double* x_in, int host, double t);
+
+/* Sizes of the problem's device footprint in bytes (HBM admission). */
+int64_t fs_problem_device_bytes(const fs_problem* prob);
+
+/* Instrumentation (no counterpart in the paper).
+ * fs_launch_count: kernels launched by this library since load, counting
+ * every node of each replayed CUDA graph (host-side counter).
+ * fs_profile_kernel: times `reps` back-to-back launches of one hot kernel on
+ * the problem's own data and stream with CUDA events (after 3 warm-up
+ * launches) and returns the mean duration and the kernel's algorithmic bytes
+ * per launch (each array it must touch counted once).  Kernel ids below.
+ * Leaves the problem's state and assembled system unchanged.  Synchronises. */
+enum {
+  FS_KERNEL_SPMV = 0,           /* saddle-point SpMV, solver arithmetic      */
+  FS_KERNEL_SPMV_FP64 = 1,      /* saddle-point SpMV, FP64                   */
+  FS_KERNEL_CHEB = 2,           /* fused Chebyshev step, finest P2 level     */
+  FS_KERNEL_ASSEMBLE_CONV = 3   /* per-step convection assembly (FP64)       */
+};
+int64_t fs_launch_count(void);
+int fs_profile_kernel(fs_problem* prob, int kernel, int reps, double* avg_ms,
+                      double* alg_bytes);
+
+const char* fs_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FS_H */

@@ -490,3 +490,49 @@ def steady_picard(prob: Problem, tol=1e-12, maxit=50):
 if __name__ == "__main__":  # pragma: no cover
     build(force="--force" in sys.argv)
     print(_LIB)
+
+
+def assemble_rows(prob: Problem, nodes, w=None, mass_coef=None, t_next=None):
+    """Rows of the monolithic system (after boundary conditions) for a sample
+    of P2 nodes, from the elements that contain them: returns a dict
+    {global row: {global col: value}} and the matching right-hand side.
+    Used to check full-size systems one row at a time."""
+    d, n2 = prob.dim, prob.n2
+    mc = 1.0 / prob.dt if mass_coef is None else mass_coef
+    t1 = prob.t + prob.dt if t_next is None else t_next
+    if w is None:
+        w = (np.repeat(np.asarray(prob.wconst, np.float64), n2)
+             if prob.wconst is not None else prob.u)
+    nodes = np.asarray(nodes)
+    want = set(int(i) for i in nodes)
+    cells = np.where(np.isin(prob.c2d, nodes).any(1))[0]
+    rows, rhs = {}, {}
+    nb = d + 1
+    for c in cells:
+        g = prob.c2d[c]
+        xv = prob.p2xyz[g[:nb]]
+        wl = np.stack([w[a * n2 + g] for a in range(d)], 1)
+        E = element(d, xv, wl, mc, prob.nu)
+        _, _, fj = exact(prob.problem, d, t1, prob.nu, prob.p2xyz[g], prob.wconst)
+        for i, gi in enumerate(g):
+            if int(gi) not in want:
+                continue
+            for a in range(d):
+                r = a * n2 + int(gi)
+                row = rows.setdefault(r, {})
+                for j, gj in enumerate(g):
+                    row[a * n2 + int(gj)] = row.get(a * n2 + int(gj), 0.0) + E["A"][i, j]
+                for q in range(nb):
+                    cp = d * n2 + int(g[q])
+                    row[cp] = row.get(cp, 0.0) - E["B"][a, q, i]
+                gl = mc * prob.u[a * n2 + g] + fj[:, a]
+                rhs[r] = rhs.get(r, 0.0) + float(E["M"][i] @ gl)
+    # boundary rows
+    for gi in want:
+        if prob.mask[gi]:
+            u, _, _ = exact(prob.problem, d, t1, prob.nu, prob.p2xyz[gi:gi + 1], prob.wconst)
+            for a in range(d):
+                r = a * n2 + gi
+                rows[r] = {cc: (1.0 if cc == r else 0.0) for cc in rows[r]}
+                rhs[r] = u[0, a]
+    return rows, rhs

@@ -1,0 +1,604 @@
+// Per-element assembly of the Oseen system on sm_103a, the right-hand side
+// and the boundary rows.
+//
+// Paper Sec. 2.2.1 (Oseen equation): the bilinear form
+//   (u/dt, v) + ((w.grad) u, v) + nu (grad u, grad v) - (p, div v) + (div u, q)
+// on P2/P1 Taylor-Hood elements, and the load (f^{n+1}, v) + (u^n/dt, v).
+// Sec. 3.1 names these BForm / LForm; here they are element kernels that
+// scatter into the fixed block-CSR pattern through per-element slot tables
+// (row offset + uint8 position), so no sort and no COO step runs per step.
+//
+// Element integrals: with grad(lambda_r) the (constant) barycentric
+// gradients and D = |det J|, each block is D times a contraction of a
+// reference-simplex integral with geometric coefficients:
+//   M_ij = D mass_ij,   K_ij = D sum_rs (grad l_r . grad l_s) stiff_ijrs,
+//   N_ij = D sum_k sum_(j,r) (w_k . grad l_r) conv_ik(j,r),
+//   B^c_qj = D sum_r (d l_r/d x_c) div_qjr.
+// The reference integrals come from a degree-5 Grundmann-Moeller rule
+// (exact for these polynomial integrands) evaluated once on the host.
+#include <cuda_runtime.h>
+
+#include <cstdio>
+
+#include "fs_device.h"
+
+namespace fs {
+
+struct CRef {
+  double mass[kMaxLoc][kMaxLoc];
+  double stiff[kMaxLoc][kMaxLoc][4][4];
+  double conv[kMaxLoc][kMaxLoc][16];
+  double div[4][kMaxLoc][4];
+};
+__constant__ CRef c_ref[2];
+
+void upload_ref_tensors(const RefTensors& R2, const RefTensors& R3) {
+  CRef h[2];
+  const RefTensors* src[2] = {&R2, &R3};
+  for (int d = 0; d < 2; ++d) {
+    memcpy(h[d].mass, src[d]->mass, sizeof(h[d].mass));
+    memcpy(h[d].stiff, src[d]->stiff, sizeof(h[d].stiff));
+    memcpy(h[d].conv, src[d]->conv, sizeof(h[d].conv));
+    memcpy(h[d].div, src[d]->div, sizeof(h[d].div));
+  }
+  cudaMemcpyToSymbol(c_ref, h, sizeof(h));
+}
+
+namespace {
+
+// Nonzero (j, r) pairs of d phi_j / d lambda_r in the local node order
+// (vertices, then edges (1,2),(2,0),(0,1) / (0,1),(0,2),(0,3),(1,2),(1,3),
+// (2,3)); the host reference tensors use the same order.
+template <int DIM> struct Pairs;
+template <> struct Pairs<2> {
+  static constexpr int n = 9;
+  __device__ static constexpr int j(int p) {
+    constexpr int t[9] = {0, 1, 2, 3, 3, 4, 4, 5, 5};
+    return t[p];
+  }
+  __device__ static constexpr int r(int p) {
+    constexpr int t[9] = {0, 1, 2, 1, 2, 2, 0, 0, 1};
+    return t[p];
+  }
+};
+template <> struct Pairs<3> {
+  static constexpr int n = 16;
+  __device__ static constexpr int j(int p) {
+    constexpr int t[16] = {0, 1, 2, 3, 4, 4, 5, 5, 6, 6, 7, 7, 8, 8, 9, 9};
+    return t[p];
+  }
+  __device__ static constexpr int r(int p) {
+    constexpr int t[16] = {0, 1, 2, 3, 0, 1, 0, 2, 0, 3, 1, 2, 1, 3, 2, 3};
+    return t[p];
+  }
+};
+
+template <int DIM> struct Loc { static constexpr int nb = DIM + 1, nl = DIM == 2 ? 6 : 10; };
+
+// Barycentric gradients of one affine simplex: with edge vectors e_r =
+// x_{r+1} - x_0, the gradients of lambda_1..d form the dual basis of
+// (e_1..e_d); grad lambda_0 = -(sum of the others).  Returns |det J|.
+template <int DIM>
+__device__ __forceinline__ double bary_grads(const double (&xv)[DIM + 1][DIM],
+                                             double (&gl)[DIM + 1][DIM]) {
+  double e[DIM][DIM];
+#pragma unroll
+  for (int r = 0; r < DIM; ++r)
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) e[r][a] = xv[r + 1][a] - xv[0][a];
+  double det;
+  if constexpr (DIM == 2) {
+    det = e[0][0] * e[1][1] - e[0][1] * e[1][0];
+    double id = 1.0 / det;
+    // dual basis: g1 . e1 = 1, g1 . e2 = 0, ...
+    gl[1][0] = e[1][1] * id;  gl[1][1] = -e[1][0] * id;
+    gl[2][0] = -e[0][1] * id; gl[2][1] = e[0][0] * id;
+  } else {
+    double c12[3] = {e[1][1] * e[2][2] - e[1][2] * e[2][1],
+                     e[1][2] * e[2][0] - e[1][0] * e[2][2],
+                     e[1][0] * e[2][1] - e[1][1] * e[2][0]};
+    double c20[3] = {e[2][1] * e[0][2] - e[2][2] * e[0][1],
+                     e[2][2] * e[0][0] - e[2][0] * e[0][2],
+                     e[2][0] * e[0][1] - e[2][1] * e[0][0]};
+    double c01[3] = {e[0][1] * e[1][2] - e[0][2] * e[1][1],
+                     e[0][2] * e[1][0] - e[0][0] * e[1][2],
+                     e[0][0] * e[1][1] - e[0][1] * e[1][0]};
+    det = e[0][0] * c12[0] + e[0][1] * c12[1] + e[0][2] * c12[2];
+    double id = 1.0 / det;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      gl[1][a] = c12[a] * id;
+      gl[2][a] = c20[a] * id;
+      gl[3][a] = c01[a] * id;
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) {
+    double s = 0;
+#pragma unroll
+    for (int r = 1; r <= DIM; ++r) s += gl[r][a];
+    gl[0][a] = -s;
+  }
+  return fabs(det);
+}
+
+template <int DIM>
+__device__ __forceinline__ void load_cell(const DMesh& m, int64_t e,
+                                          int32_t (&g)[Loc<DIM>::nl],
+                                          double (&xv)[DIM + 1][DIM]) {
+  constexpr int NL = Loc<DIM>::nl;
+#pragma unroll
+  for (int a = 0; a < NL; ++a) g[a] = __ldg(m.c2d + e * NL + a);
+#pragma unroll
+  for (int v = 0; v <= DIM; ++v)
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) xv[v][a] = __ldg(m.p2xyz + (int64_t)g[v] * DIM + a);
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(128) k_assemble_base(
+    DMesh m, double mass_coef, double nu, double* __restrict__ base,
+    double* __restrict__ Mv, double* __restrict__ B, double* __restrict__ BT,
+    double* __restrict__ Kp, double* __restrict__ mpl) {
+  constexpr int NB = DIM + 1, NL = Loc<DIM>::nl;
+  const CRef& R = c_ref[DIM - 2];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m.ncell;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int32_t g[NL];
+    double xv[NB][DIM], gl[NB][DIM];
+    load_cell<DIM>(m, e, g, xv);
+    double D = bary_grads<DIM>(xv, gl);
+    double G[NB][NB];
+#pragma unroll
+    for (int r = 0; r < NB; ++r)
+#pragma unroll
+      for (int s = 0; s < NB; ++s) {
+        double t = 0;
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) t += gl[r][a] * gl[s][a];
+        G[r][s] = t;
+      }
+    for (int i = 0; i < NL; ++i) {
+      int32_t rowbase = __ldg(m.rpA + g[i]);
+      const uint8_t* pos = m.posA + (e * NL + i) * NL;
+#pragma unroll
+      for (int j = 0; j < NL; ++j) {
+        double mm = D * R.mass[i][j];
+        double kk = 0;
+#pragma unroll
+        for (int r = 0; r < NB; ++r)
+#pragma unroll
+          for (int s = 0; s < NB; ++s) kk += G[r][s] * R.stiff[i][j][r][s];
+        kk *= D;
+        int32_t slot = rowbase + pos[j];
+        atomicAdd(base + slot, mass_coef * mm + nu * kk);
+        atomicAdd(Mv + slot, mm);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < NB; ++q)
+      for (int j = 0; j < NL; ++j) {
+        double bv[DIM];
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) {
+          double s = 0;
+#pragma unroll
+          for (int r = 0; r < NB; ++r) s += gl[r][c] * R.div[q][j][r];
+          bv[c] = D * s;
+        }
+        int64_t sB = __ldg(m.rpB + g[q]) + m.posB[(e * NB + q) * NL + j];
+        int64_t sBT = __ldg(m.rpBT + g[j]) + m.posBT[(e * NL + j) * NB + q];
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) {
+          atomicAdd(B + sB * DIM + c, bv[c]);
+          atomicAdd(BT + sBT * DIM + c, bv[c]);
+        }
+      }
+    const double vol = D / (DIM == 2 ? 2.0 : 6.0);
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+      int32_t rb = __ldg(m.rpK + g[q]);
+#pragma unroll
+      for (int s = 0; s < NB; ++s) atomicAdd(Kp + rb + m.posK[(e * NB + q) * NB + s], vol * G[q][s]);
+      atomicAdd(mpl + g[q], vol / NB);
+    }
+  }
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(128) k_assemble_conv(DMesh m,
+                                                       const double* __restrict__ w,
+                                                       int64_t ldw, double wc0,
+                                                       double wc1, double wc2,
+                                                       double* __restrict__ valA) {
+  constexpr int NB = DIM + 1, NL = Loc<DIM>::nl;
+  const CRef& R = c_ref[DIM - 2];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m.ncell;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int32_t g[NL];
+    double xv[NB][DIM], gl[NB][DIM];
+    load_cell<DIM>(m, e, g, xv);
+    double D = bary_grads<DIM>(xv, gl);
+    // cw[k][r] = D (w_k . grad lambda_r)
+    double cw[NL][NB];
+#pragma unroll
+    for (int k = 0; k < NL; ++k) {
+      double wk[DIM];
+      if (w) {
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) wk[c] = __ldg(w + c * ldw + g[k]);
+      } else {
+        wk[0] = wc0;
+        wk[1] = wc1;
+        if constexpr (DIM == 3) wk[2] = wc2;
+      }
+#pragma unroll
+      for (int r = 0; r < NB; ++r) {
+        double t = 0;
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) t += wk[c] * gl[r][c];
+        cw[k][r] = D * t;
+      }
+    }
+    for (int i = 0; i < NL; ++i) {
+      if (__ldg(m.dirichlet + g[i])) continue;
+      double acc[NL];
+#pragma unroll
+      for (int j = 0; j < NL; ++j) acc[j] = 0.0;
+#pragma unroll
+      for (int k = 0; k < NL; ++k)
+#pragma unroll
+        for (int p = 0; p < Pairs<DIM>::n; ++p)
+          acc[Pairs<DIM>::j(p)] += cw[k][Pairs<DIM>::r(p)] * R.conv[i][k][p];
+      int32_t rowbase = __ldg(m.rpA + g[i]);
+      const uint8_t* pos = m.posA + (e * NL + i) * NL;
+#pragma unroll
+      for (int j = 0; j < NL; ++j) atomicAdd(valA + rowbase + pos[j], acc[j]);
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_bc_rows(DMesh m, T* __restrict__ valA) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < m.ndir;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int32_t i = m.dlist[t];
+    for (int32_t k = m.rpA[i]; k < m.rpA[i + 1]; ++k) valA[k] = (m.ciA[k] == i) ? T(1) : T(0);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Manufactured solutions (the problem library): velocity, pressure and the
+// load f = u_t - nu Lap u + (w . grad) u + grad p, w = u except for the
+// polynomial Oseen problem (w = wconst).
+// ---------------------------------------------------------------------------
+constexpr double kPi = 3.141592653589793238462643383279502884;
+
+struct Fields {
+  double u[3], p, f[3];
+};
+
+// g(s) = sin^2(pi s) and derivatives 0..3
+__device__ __forceinline__ void g_ders(double s, double (&g)[4]) {
+  double sn = sin(kPi * s), s2 = sin(2.0 * kPi * s), c2 = cos(2.0 * kPi * s);
+  g[0] = sn * sn;
+  g[1] = kPi * s2;
+  g[2] = 2.0 * kPi * kPi * c2;
+  g[3] = -4.0 * kPi * kPi * kPi * s2;
+}
+
+template <int DIM>
+__device__ Fields eval_fields(const DPhys& ph, const double* x, double t, bool want_f) {
+  Fields F{};
+  const double nu = ph.nu;
+  double X = x[0], Y = x[1];
+  switch (ph.kind) {
+    case FS_PROBLEM_UNSTEADY_BENCH: {
+      double S = sin(t), C = cos(t);
+      double sx = sin(kPi * X), cx = cos(kPi * X), sy = sin(kPi * Y), cy = cos(kPi * Y);
+      double u1 = 2 * kPi * S * sx * sx * sy * cy;
+      double u2 = -2 * kPi * S * sx * cx * sy * sy;
+      F.u[0] = u1;
+      F.u[1] = u2;
+      F.p = 20 * S * (X * X * Y - 1.0 / 6.0);
+      if (want_f) {
+        double pi2 = kPi * kPi, pi3 = pi2 * kPi;
+        double u1t = 2 * kPi * C * sx * sx * sy * cy, u2t = -2 * kPi * C * sx * cx * sy * sy;
+        double u1x = 4 * pi2 * S * sx * cx * sy * cy;
+        double u1y = 2 * pi2 * S * sx * sx * (cy * cy - sy * sy);
+        double u2x = -2 * pi2 * S * (cx * cx - sx * sx) * sy * sy;
+        double u2y = -4 * pi2 * S * sx * cx * sy * cy;
+        double lap1 = 4 * pi3 * S * (cx * cx - sx * sx) * sy * cy - 8 * pi3 * S * sx * sx * sy * cy;
+        double lap2 = 8 * pi3 * S * sx * cx * sy * sy - 4 * pi3 * S * sx * cx * (cy * cy - sy * sy);
+        F.f[0] = u1t - nu * lap1 + u1 * u1x + u2 * u1y + 40 * S * X * Y;
+        F.f[1] = u2t - nu * lap2 + u1 * u2x + u2 * u2y + 20 * S * X * X;
+      }
+      break;
+    }
+    case FS_PROBLEM_STEADY_POLY: {
+      // u = 10 a(x) b(y), v = -10 b(x) a(y), a(s) = s^2 (s-1)^2,
+      // b(s) = s (s-1)(2s-1)
+      auto a0 = [](double s) { return s * s * (s - 1) * (s - 1); };
+      auto a1 = [](double s) { return 4 * s * s * s - 6 * s * s + 2 * s; };
+      auto a2 = [](double s) { return 12 * s * s - 12 * s + 2; };
+      auto b0 = [](double s) { return s * (s - 1) * (2 * s - 1); };
+      auto b1 = [](double s) { return 6 * s * s - 6 * s + 1; };
+      auto b2 = [](double s) { return 12 * s - 6; };
+      double u1 = 10 * a0(X) * b0(Y), u2 = -10 * b0(X) * a0(Y);
+      F.u[0] = u1;
+      F.u[1] = u2;
+      F.p = 10 * (2 * X - 1) * (2 * Y - 1);
+      if (want_f) {
+        double u1x = 10 * a1(X) * b0(Y), u1y = 10 * a0(X) * b1(Y);
+        double u2x = -10 * b1(X) * a0(Y), u2y = -10 * b0(X) * a1(Y);
+        double lap1 = 10 * (a2(X) * b0(Y) + a0(X) * b2(Y));
+        double lap2 = -10 * (b2(X) * a0(Y) + b0(X) * a2(Y));
+        F.f[0] = -nu * lap1 + u1 * u1x + u2 * u1y + 20 * (2 * Y - 1);
+        F.f[1] = -nu * lap2 + u1 * u2x + u2 * u2y + 20 * (2 * X - 1);
+      }
+      break;
+    }
+    case FS_PROBLEM_CHANNEL: {
+      const double H = 0.41, L = 2.2, U = 1.5;
+      F.u[0] = 4 * U * Y * (H - Y) / (H * H);
+      F.u[1] = 0;
+      F.p = 8 * nu * U * (L - X) / (H * H);
+      F.f[0] = F.f[1] = 0;  // Poiseuille solves the steady equations with f = 0
+      break;
+    }
+    case FS_PROBLEM_CUBE: {
+      if constexpr (DIM == 3) {
+        double S = sin(t), C = cos(t);
+        double gx[4], gy[4], gz[4];
+        g_ders(X, gx);
+        g_ders(Y, gy);
+        g_ders(x[2], gz);
+        // D(a,b,c) Phi = g^(a)(x) g^(b)(y) g^(c)(z)
+        auto Dp = [&](int a, int b, int c) { return gx[a] * gy[b] * gz[c]; };
+        // u_i = S (d_{i+1} Phi - d_{i+2} Phi), indices mod 3
+        int e[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+        double du[3][3], lap[3], uu[3];
+        for (int i = 0; i < 3; ++i) {
+          const int* ep = e[(i + 1) % 3];
+          const int* em = e[(i + 2) % 3];
+          uu[i] = Dp(ep[0], ep[1], ep[2]) - Dp(em[0], em[1], em[2]);
+          lap[i] = 0;
+          for (int j = 0; j < 3; ++j) {
+            int a[3] = {ep[0] + e[j][0], ep[1] + e[j][1], ep[2] + e[j][2]};
+            int b[3] = {em[0] + e[j][0], em[1] + e[j][1], em[2] + e[j][2]};
+            du[i][j] = S * (Dp(a[0], a[1], a[2]) - Dp(b[0], b[1], b[2]));
+            lap[i] += Dp(a[0] + e[j][0], a[1] + e[j][1], a[2] + e[j][2]) -
+                      Dp(b[0] + e[j][0], b[1] + e[j][1], b[2] + e[j][2]);
+          }
+          F.u[i] = S * uu[i];
+        }
+        double Z = x[2];
+        F.p = S * (X * X * Y * Z - 1.0 / 12.0);
+        if (want_f) {
+          double gp[3] = {2 * X * Y * Z, X * X * Z, X * X * Y};
+          for (int i = 0; i < 3; ++i) {
+            double conv = F.u[0] * du[i][0] + F.u[1] * du[i][1] + F.u[2] * du[i][2];
+            F.f[i] = C * uu[i] - nu * S * lap[i] + conv + S * gp[i];
+          }
+        }
+      }
+      break;
+    }
+    case FS_PROBLEM_POLY_OSEEN: {
+      double w1 = ph.wconst[0], w2 = ph.wconst[1];
+      F.u[0] = X * X;
+      F.u[1] = -2 * X * Y;
+      F.p = X + Y - 1;
+      F.f[0] = -2 * nu + 2 * X * w1 + 1;
+      F.f[1] = -2 * Y * w1 - 2 * X * w2 + 1;
+      if constexpr (DIM == 3) {
+        F.u[2] = X * Y;
+        F.p = X + Y + x[2] - 1;
+        F.f[2] = Y * w1 + X * w2 + 1;
+      }
+      break;
+    }
+    default:
+      break;
+  }
+  return F;
+}
+
+template <int DIM>
+__global__ void k_eval_load(DMesh m, DPhys ph, double t, double mass_coef,
+                            const double* __restrict__ u, double* __restrict__ F) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m.n2;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    double x[DIM];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) x[a] = m.p2xyz[j * DIM + a];
+    Fields f = eval_fields<DIM>(ph, x, t, true);
+#pragma unroll
+    for (int c = 0; c < DIM; ++c)
+      F[c * m.n2 + j] = (u ? mass_coef * u[c * m.n2 + j] : 0.0) + f.f[c];
+  }
+}
+
+// b_c[i] = sum_k Mv[k] F_c[col k]; L lanes per row.
+template <int DIM, int L>
+__global__ void k_rhs_vel(DMesh m, DPhys ph, double t, const double* __restrict__ Mv,
+                          const double* __restrict__ F, double* __restrict__ b) {
+  int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t i = gt / L;
+  int lane = (int)(gt % L);
+  bool live = i < m.n2;
+  double acc[DIM];
+#pragma unroll
+  for (int c = 0; c < DIM; ++c) acc[c] = 0;
+  bool dir = live && m.dirichlet[i];
+  if (live && !dir) {
+    for (int32_t k = m.rpA[i] + lane; k < m.rpA[i + 1]; k += L) {
+      double a = Mv[k];
+      int32_t col = m.ciA[k];
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) acc[c] += a * F[c * m.n2 + col];
+    }
+  }
+#pragma unroll
+  for (int off = L / 2; off > 0; off >>= 1)
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], off);
+  if (live && lane == 0) {
+    if (dir) {
+      double x[DIM];
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) x[a] = m.p2xyz[i * DIM + a];
+      Fields f = eval_fields<DIM>(ph, x, t, false);
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) b[c * m.n2 + i] = f.u[c];
+    } else {
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) b[c * m.n2 + i] = acc[c];
+    }
+  }
+}
+
+template <int DIM>
+__global__ void k_rhs_p(DMesh m, DPhys ph, double t, int pin, double* __restrict__ b) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < m.nv;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    double v = 0.0;
+    if (pin && q == 0) {
+      double x[DIM];
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) x[a] = m.p2xyz[a];
+      v = eval_fields<DIM>(ph, x, t, false).p;
+    }
+    b[DIM * m.n2 + q] = v;
+  }
+}
+
+template <int DIM>
+__global__ void k_exact_state(DMesh m, DPhys ph, double t, int zero_interior,
+                              double* __restrict__ x) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m.n2;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    double xx[DIM];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) xx[a] = m.p2xyz[j * DIM + a];
+    Fields f = eval_fields<DIM>(ph, xx, t, false);
+    bool keep = !zero_interior || m.dirichlet[j];
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) x[c * m.n2 + j] = keep ? f.u[c] : 0.0;
+    if (j < m.nv) x[DIM * m.n2 + j] = f.p;
+  }
+}
+
+__global__ void k_expand_monolithic(DMesh m, const double* __restrict__ valA,
+                                    const double* __restrict__ B,
+                                    const double* __restrict__ BT,
+                                    const double* __restrict__ diagp,
+                                    const int64_t* __restrict__ mrp,
+                                    double* __restrict__ out) {
+  const int dim = m.dim;
+  const int64_t nrow = dim * m.n2 + m.nv;
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nrow;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    int64_t o = mrp[r];
+    if (r < dim * m.n2) {
+      int c = (int)(r / m.n2);
+      int64_t i = r % m.n2;
+      for (int32_t k = m.rpA[i]; k < m.rpA[i + 1]; ++k) out[o++] = valA[k];
+      for (int32_t k = m.rpBT[i]; k < m.rpBT[i + 1]; ++k) out[o++] = -BT[(int64_t)k * dim + c];
+    } else {
+      int64_t q = r - dim * m.n2;
+      for (int c = 0; c < dim; ++c)
+        for (int32_t k = m.rpB[q]; k < m.rpB[q + 1]; ++k) out[o++] = B[(int64_t)k * dim + c];
+      out[o++] = diagp[q];
+    }
+  }
+}
+
+inline unsigned grid_for(int64_t n, int block) {
+  int64_t g = (n + block - 1) / block;
+  if (g < 1) g = 1;
+  if (g > 152 * 64) g = 152 * 64;
+  return (unsigned)g;
+}
+
+}  // namespace
+
+void launch_assemble_base(const DMesh& m, double mass_coef, double nu,
+                          double* base, double* Mv, double* B, double* BT,
+                          double* Kp, double* mpl, cudaStream_t s) {
+  unsigned g = grid_for(m.ncell, 128);
+  if (m.dim == 2)
+    k_assemble_base<2><<<g, 128, 0, s>>>(m, mass_coef, nu, base, Mv, B, BT, Kp, mpl);
+  else
+    k_assemble_base<3><<<g, 128, 0, s>>>(m, mass_coef, nu, base, Mv, B, BT, Kp, mpl);
+    count_launches(1);
+}
+
+void launch_assemble_conv(const DMesh& m, const double* w, int64_t ldw,
+                          const double* wc, double* valA, cudaStream_t s) {
+  unsigned g = grid_for(m.ncell, 128);
+  double w0 = wc ? wc[0] : 0, w1 = wc ? wc[1] : 0, w2 = wc ? wc[2] : 0;
+  if (m.dim == 2)
+    k_assemble_conv<2><<<g, 128, 0, s>>>(m, w, ldw, w0, w1, w2, valA);
+  else
+    k_assemble_conv<3><<<g, 128, 0, s>>>(m, w, ldw, w0, w1, w2, valA);
+    count_launches(1);
+}
+
+template <typename T>
+void launch_bc_rows(const DMesh& m, T* valA, cudaStream_t s) {
+  if (m.ndir == 0) return;
+  k_bc_rows<T><<<grid_for(m.ndir, 256), 256, 0, s>>>(m, valA);
+  count_launches(1);
+}
+template void launch_bc_rows<double>(const DMesh&, double*, cudaStream_t);
+template void launch_bc_rows<float>(const DMesh&, float*, cudaStream_t);
+
+void launch_eval_load(const DMesh& m, const DPhys& ph, double t,
+                      double mass_coef, const double* u, double* F,
+                      cudaStream_t s) {
+  unsigned g = grid_for(m.n2, 256);
+  if (m.dim == 2)
+    k_eval_load<2><<<g, 256, 0, s>>>(m, ph, t, mass_coef, u, F);
+  else
+    k_eval_load<3><<<g, 256, 0, s>>>(m, ph, t, mass_coef, u, F);
+    count_launches(1);
+}
+
+void launch_rhs(const DMesh& m, const DPhys& ph, double t, const double* Mv,
+                const double* F, int pin, double* b, cudaStream_t s) {
+  constexpr int L = 4;
+  unsigned g = (unsigned)((m.n2 * L + 255) / 256);
+  if (m.dim == 2) {
+    k_rhs_vel<2, L><<<g, 256, 0, s>>>(m, ph, t, Mv, F, b);
+    count_launches(1);
+    k_rhs_p<2><<<grid_for(m.nv, 256), 256, 0, s>>>(m, ph, t, pin, b);
+    count_launches(1);
+  } else {
+    k_rhs_vel<3, L><<<g, 256, 0, s>>>(m, ph, t, Mv, F, b);
+    count_launches(1);
+    k_rhs_p<3><<<grid_for(m.nv, 256), 256, 0, s>>>(m, ph, t, pin, b);
+    count_launches(1);
+  }
+}
+
+void launch_exact_state(const DMesh& m, const DPhys& ph, double t,
+                        int zero_interior, double* x, cudaStream_t s) {
+  unsigned g = grid_for(m.n2, 256);
+  if (m.dim == 2)
+    k_exact_state<2><<<g, 256, 0, s>>>(m, ph, t, zero_interior, x);
+  else
+    k_exact_state<3><<<g, 256, 0, s>>>(m, ph, t, zero_interior, x);
+    count_launches(1);
+}
+
+void launch_expand_monolithic(const DMesh& m, const double* valA,
+                              const double* B, const double* BT,
+                              const double* diagp, const int64_t* mrp,
+                              double* out, cudaStream_t s) {
+  int64_t nrow = m.dim * m.n2 + m.nv;
+  k_expand_monolithic<<<grid_for(nrow, 256), 256, 0, s>>>(m, valA, B, BT, diagp, mrp, out);
+  count_launches(1);
+}
+
+}  // namespace fs

@@ -1,0 +1,280 @@
+// Host-side construction of the multigrid hierarchies used by the block
+// preconditioner (not in the paper, which names no preconditioner; see the
+// Cahouet-Chabard reading in the design notes).  Prolongations are linear
+// interpolation in the index space of the structured simplicial meshes:
+// P1 on mesh n_{l+1} -> P1 on mesh n_l (nested when n_l is even), and, for
+// the velocity block, P1 -> P2 on the finest mesh.  Coarse operators are
+// Galerkin products R A P with R = P^T.  The coarsest operator is inverted
+// densely.  Built once per problem; the values are FP64.
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+#include <random>
+
+#include "fs_internal.h"
+
+namespace fs {
+
+namespace {
+
+HostCsr transpose(const HostCsr& P) {
+  HostCsr R;
+  R.nrow = P.ncol;
+  R.ncol = P.nrow;
+  R.rowptr.assign(R.nrow + 1, 0);
+  for (int32_t c : P.col) R.rowptr[c + 1]++;
+  for (int64_t r = 0; r < R.nrow; ++r) R.rowptr[r + 1] += R.rowptr[r];
+  R.col.resize(P.nnz());
+  R.val.resize(P.nnz());
+  std::vector<int32_t> f(R.rowptr.begin(), R.rowptr.end() - 1);
+  for (int64_t r = 0; r < P.nrow; ++r)
+    for (int32_t k = P.rowptr[r]; k < P.rowptr[r + 1]; ++k) {
+      int32_t dst = f[P.col[k]]++;
+      R.col[dst] = (int32_t)r;
+      R.val[dst] = P.val[k];
+    }
+  return R;
+}
+
+// C = A B (Gustavson, dense accumulator), columns sorted per row.
+HostCsr spgemm(const HostCsr& A, const HostCsr& B) {
+  HostCsr C;
+  C.nrow = A.nrow;
+  C.ncol = B.ncol;
+  C.rowptr.assign(C.nrow + 1, 0);
+  std::vector<double> acc(B.ncol, 0.0);
+  std::vector<int32_t> mark(B.ncol, -1), cols;
+  for (int64_t i = 0; i < A.nrow; ++i) {
+    cols.clear();
+    for (int32_t ka = A.rowptr[i]; ka < A.rowptr[i + 1]; ++ka) {
+      int32_t k = A.col[ka];
+      double a = A.val[ka];
+      for (int32_t kb = B.rowptr[k]; kb < B.rowptr[k + 1]; ++kb) {
+        int32_t j = B.col[kb];
+        if (mark[j] != (int32_t)i) {
+          mark[j] = (int32_t)i;
+          acc[j] = 0.0;
+          cols.push_back(j);
+        }
+        acc[j] += a * B.val[kb];
+      }
+    }
+    std::sort(cols.begin(), cols.end());
+    for (int32_t j : cols) {
+      C.col.push_back(j);
+      C.val.push_back(acc[j]);
+    }
+    C.rowptr[i + 1] = (int32_t)C.col.size();
+  }
+  return C;
+}
+
+// Linear interpolation from the structured simplicial mesh nc to nf (cells
+// per axis) in index space: fine vertex i sits at i nc / nf on the coarse
+// grid; its weights are the barycentric coordinates in the coarse Kuhn
+// simplex (triangle) that contains it.
+HostCsr p1_interp(int dim, const int* nf, const int* nc) {
+  int64_t sf[3] = {nf[0] + 1, nf[1] + 1, dim == 3 ? nf[2] + 1 : 1};
+  int64_t scn[3] = {nc[0] + 1, nc[1] + 1, dim == 3 ? nc[2] + 1 : 1};
+  HostCsr P;
+  P.nrow = sf[0] * sf[1] * sf[2];
+  P.ncol = scn[0] * scn[1] * scn[2];
+  P.rowptr.assign(P.nrow + 1, 0);
+  for (int64_t v = 0; v < P.nrow; ++v) {
+    int64_t fi[3] = {v % sf[0], (v / sf[0]) % sf[1], v / (sf[0] * sf[1])};
+    int64_t I[3] = {0, 0, 0};
+    double s[3] = {0, 0, 0};
+    for (int a = 0; a < dim; ++a) {
+      // exact rational position fi * nc / nf
+      int64_t num = fi[a] * nc[a];
+      I[a] = std::min<int64_t>(num / nf[a], nc[a] - 1);
+      s[a] = (double)(num - I[a] * nf[a]) / (double)nf[a];
+    }
+    int ord[3] = {0, 1, 2};
+    std::stable_sort(ord, ord + dim, [&](int x, int y) { return s[x] > s[y]; });
+    std::vector<std::pair<int32_t, double>> ent;
+    int64_t cur[3] = {I[0], I[1], I[2]};
+    auto cid = [&](const int64_t* c) {
+      return (int32_t)(c[0] + scn[0] * (c[1] + scn[1] * c[2]));
+    };
+    double w0 = 1.0 - s[ord[0]];
+    if (w0 > 1e-14) ent.push_back({cid(cur), w0});
+    for (int k = 0; k < dim; ++k) {
+      cur[ord[k]] += 1;
+      double w = s[ord[k]] - (k + 1 < dim ? s[ord[k + 1]] : 0.0);
+      if (w > 1e-14) ent.push_back({cid(cur), w});
+    }
+    std::sort(ent.begin(), ent.end());
+    for (auto& e : ent) {
+      P.col.push_back(e.first);
+      P.val.push_back(e.second);
+    }
+    P.rowptr[v + 1] = (int32_t)P.col.size();
+  }
+  return P;
+}
+
+// P1 -> P2 on the same mesh: vertices copy, edge midpoints average.
+HostCsr p2_from_p1(const Mesh& m) {
+  HostCsr P;
+  P.nrow = m.n2;
+  P.ncol = m.nv;
+  P.rowptr.assign(P.nrow + 1, 0);
+  for (int64_t v = 0; v < m.nv; ++v) {
+    P.col.push_back((int32_t)v);
+    P.val.push_back(1.0);
+    P.rowptr[v + 1] = (int32_t)P.col.size();
+  }
+  for (int64_t e = 0; e < m.ne; ++e) {
+    int32_t a = m.edges[2 * e], b = m.edges[2 * e + 1];
+    P.col.push_back(std::min(a, b));
+    P.val.push_back(0.5);
+    P.col.push_back(std::max(a, b));
+    P.val.push_back(0.5);
+    P.rowptr[m.nv + e + 1] = (int32_t)P.col.size();
+  }
+  return P;
+}
+
+void finish_level(HostLevel& L) {
+  const HostCsr& A = L.A;
+  L.dinv.assign(A.nrow, 1.0);
+  for (int64_t i = 0; i < A.nrow; ++i)
+    for (int32_t k = A.rowptr[i]; k < A.rowptr[i + 1]; ++k)
+      if (A.col[k] == i && A.val[k] != 0.0) L.dinv[i] = 1.0 / A.val[k];
+  // largest eigenvalue of D^-1 A by power iteration (30 steps)
+  std::vector<double> v(A.nrow), w(A.nrow);
+  std::mt19937_64 g(12345);
+  std::uniform_real_distribution<double> U(-1.0, 1.0);
+  for (auto& x : v) x = U(g);
+  double lam = 0;
+  for (int it = 0; it < 30; ++it) {
+    double nw = 0, nv = 0;
+    for (int64_t i = 0; i < A.nrow; ++i) {
+      double s = 0;
+      for (int32_t k = A.rowptr[i]; k < A.rowptr[i + 1]; ++k) s += A.val[k] * v[A.col[k]];
+      w[i] = L.dinv[i] * s;
+      nw += w[i] * w[i];
+      nv += v[i] * v[i];
+    }
+    lam = std::sqrt(nw / nv);
+    double inv = 1.0 / std::sqrt(nw);
+    for (int64_t i = 0; i < A.nrow; ++i) v[i] = w[i] * inv;
+  }
+  L.lmax = lam;
+}
+
+// Gauss-Jordan inverse with partial pivoting (n small).
+bool dense_inverse(const HostCsr& A, std::vector<double>& inv) {
+  int64_t n = A.nrow;
+  std::vector<double> M(n * n, 0.0);
+  inv.assign(n * n, 0.0);
+  for (int64_t i = 0; i < n; ++i) {
+    for (int32_t k = A.rowptr[i]; k < A.rowptr[i + 1]; ++k) M[i * n + A.col[k]] += A.val[k];
+    inv[i * n + i] = 1.0;
+  }
+  for (int64_t c = 0; c < n; ++c) {
+    int64_t p = c;
+    for (int64_t r = c + 1; r < n; ++r)
+      if (std::fabs(M[r * n + c]) > std::fabs(M[p * n + c])) p = r;
+    if (M[p * n + c] == 0.0) return false;
+    if (p != c)
+      for (int64_t j = 0; j < n; ++j) {
+        std::swap(M[p * n + j], M[c * n + j]);
+        std::swap(inv[p * n + j], inv[c * n + j]);
+      }
+    double d = 1.0 / M[c * n + c];
+    for (int64_t j = 0; j < n; ++j) {
+      M[c * n + j] *= d;
+      inv[c * n + j] *= d;
+    }
+    for (int64_t r = 0; r < n; ++r) {
+      if (r == c) continue;
+      double f = M[r * n + c];
+      if (f == 0.0) continue;
+      for (int64_t j = 0; j < n; ++j) {
+        M[r * n + j] -= f * M[c * n + j];
+        inv[r * n + j] -= f * inv[c * n + j];
+      }
+    }
+  }
+  return true;
+}
+
+}  // namespace
+
+void build_hierarchy(const Mesh& m, const HostCsr& A0, bool p2_fine,
+                     const std::vector<int32_t>& fixed_rows,
+                     int64_t coarse_max, HostHierarchy& H) {
+  H.levels.clear();
+  H.levels.emplace_back();
+  H.levels[0].A = A0;
+  int dim = m.dim;
+  int ncur[3] = {m.desc.n[0], m.desc.n[1], dim == 3 ? m.desc.n[2] : 1};
+  bool first = true;
+  while (H.levels.back().A.nrow > coarse_max) {
+    HostLevel& fine = H.levels.back();
+    HostCsr P;
+    if (first && p2_fine) {
+      P = p2_from_p1(m);  // coarse = P1 on the same mesh
+    } else {
+      int nn[3] = {ncur[0], ncur[1], ncur[2]};
+      bool changed = false;
+      for (int a = 0; a < dim; ++a) {
+        nn[a] = std::max(1, (ncur[a] + 1) / 2);
+        changed = changed || nn[a] != ncur[a];
+      }
+      if (!changed) break;
+      P = p1_interp(dim, ncur, nn);
+      for (int a = 0; a < dim; ++a) ncur[a] = nn[a];
+    }
+    if (first)
+      for (int32_t r : fixed_rows)
+        for (int32_t k = P.rowptr[r]; k < P.rowptr[r + 1]; ++k) P.val[k] = 0.0;
+    first = false;
+    HostCsr R = transpose(P);
+    HostCsr Ac = spgemm(R, spgemm(fine.A, P));
+    for (int64_t i = 0; i < Ac.nrow; ++i) {
+      bool has = false;
+      for (int32_t k = Ac.rowptr[i]; k < Ac.rowptr[i + 1]; ++k)
+        if (Ac.col[k] == i && Ac.val[k] != 0.0) has = true;
+      if (!has) {  // an unreachable coarse node: make its row the identity
+        for (int32_t k = Ac.rowptr[i]; k < Ac.rowptr[i + 1]; ++k) Ac.val[k] = 0.0;
+        bool found = false;
+        for (int32_t k = Ac.rowptr[i]; k < Ac.rowptr[i + 1]; ++k)
+          if (Ac.col[k] == i) { Ac.val[k] = 1.0; found = true; }
+        if (!found) {  // insert a diagonal entry
+          HostCsr B2 = Ac;
+          B2.col.insert(B2.col.begin() + Ac.rowptr[i], (int32_t)i);
+          B2.val.insert(B2.val.begin() + Ac.rowptr[i], 1.0);
+          for (int64_t r = i + 1; r <= Ac.nrow; ++r) B2.rowptr[r]++;
+          // keep the row sorted
+          auto b = B2.col.begin() + B2.rowptr[i], e = B2.col.begin() + B2.rowptr[i + 1];
+          std::vector<std::pair<int32_t, double>> row;
+          for (auto it = b; it != e; ++it)
+            row.push_back({*it, B2.val[it - B2.col.begin()]});
+          std::sort(row.begin(), row.end());
+          for (size_t k = 0; k < row.size(); ++k) {
+            B2.col[B2.rowptr[i] + k] = row[k].first;
+            B2.val[B2.rowptr[i] + k] = row[k].second;
+          }
+          Ac = B2;
+        }
+      }
+    }
+    fine.P = P;
+    fine.R = R;
+    H.levels.emplace_back();
+    H.levels.back().A = Ac;
+  }
+  for (auto& L : H.levels) finish_level(L);
+  H.ncoarse = H.levels.back().A.nrow;
+  if (!dense_inverse(H.levels.back().A, H.coarse_inv)) {
+    // singular coarsest operator: fall back to its Jacobi inverse
+    H.coarse_inv.assign(H.ncoarse * H.ncoarse, 0.0);
+    for (int64_t i = 0; i < H.ncoarse; ++i)
+      H.coarse_inv[i * H.ncoarse + i] = H.levels.back().dinv[i];
+  }
+}
+
+}  // namespace fs

@@ -1,0 +1,75 @@
+"""CPU tests of the C-ABI library: it loads, exports every symbol that
+include/fs.h declares, and its host-side mesh / DOF map / CSR pattern are
+bit-exact against the oracle (no GPU needed: these calls touch no device)."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import fs_workloads as W
+from oracle import oracle as O
+from tests.gpu_helpers import oracle_problem
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def fs():
+    from paper_2605_25403_gb300 import build
+    build.build()
+    from paper_2605_25403_gb300 import fs as mod
+    return mod
+
+
+def test_library_exports_every_declared_symbol(fs):
+    hdrs = [os.path.join(ROOT, "include", h) for h in os.listdir(os.path.join(ROOT, "include"))
+            if h.endswith(".h")]
+    declared = set()
+    for h in hdrs:
+        txt = open(h).read()
+        declared |= set(re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*(fs_[a-z_0-9]+)\s*\(",
+                                   txt, re.M))
+    assert declared, "no declarations found"
+    import ctypes
+    lib = ctypes.CDLL(fs.LIB_PATH)
+    for name in sorted(declared):
+        assert hasattr(lib, name), f"{name} declared in include/ but not exported"
+    assert set(fs.EXPORTED) <= declared
+
+
+@pytest.mark.parametrize("wl", [W.C1, W.cube(3), W.channel(16, 6), W.cube(2, jitter=0.2, seed=5),
+                                W.unit_square(7, jitter=0.0)], ids=lambda w: w.name)
+def test_dofmap_and_pattern_bitexact(fs, wl):
+    mesh = fs.fs_mesh_create(wl.dim, wl.n, wl.lo, wl.hi, wl.jitter, wl.seed, wl.side_mask)
+    try:
+        d = fs.fs_dof_map(mesh)
+    finally:
+        fs.fs_mesh_destroy(mesh)
+    P = oracle_problem(wl)
+    rp, col, _ = O.assemble(wl.dim, P.nv, P.n2, P.c2d, P.p2xyz, None, 1.0, 1.0)
+    assert d["n_dof"] == P.ndof == wl.ndof
+    assert np.array_equal(d["coords"], P.coords)      # bit-exact FP64 coordinates
+    assert np.array_equal(d["cell2dof"], P.c2d)
+    assert np.array_equal(d["rowptr"], rp)
+    assert np.array_equal(d["col"], col)
+    assert np.array_equal(d["dirichlet"], P.mask)
+    assert d["nnz"] == rp[-1]
+
+
+def test_config_sizes(fs):
+    """The documented sizes of the benchmark configurations."""
+    for wl, ndof, nnz in ((W.C1, 659, 11415), (W.C2, 445411, 8329191)):
+        mesh = fs.fs_mesh_create(wl.dim, wl.n, wl.lo, wl.hi, wl.jitter, wl.seed, wl.side_mask)
+        d = fs.fs_dof_map(mesh, arrays=False)
+        fs.fs_mesh_destroy(mesh)
+        assert (d["n_dof"], d["nnz"]) == (ndof, nnz)
+
+
+def test_invalid_arguments(fs):
+    with pytest.raises(fs.FsError, match="INVALID_ARG"):
+        fs.fs_mesh_create(4, (2, 2, 2), (0, 0, 0), (1, 1, 1))
+    with pytest.raises(fs.FsError, match="INVALID_ARG"):
+        fs.fs_mesh_create(2, (0, 2), (0, 0), (1, 1))
+    with pytest.raises(fs.FsError, match="INVALID_ARG"):
+        fs.fs_mesh_create(2, (2, 2), (0, 0), (1, 1), jitter=0.3)

@@ -1,0 +1,158 @@
+"""Parity of the CUDA path (through the C ABI) against the oracle.
+
+Bars ("Tolerances"):
+  * DOF map / CSR structure: bit-exact (tests/test_abi.py);
+  * assembled matrix and right-hand side: every entry within 1e-12 of the
+    largest entry of its row (both sides integrate exactly; they differ only
+    in rounding: quadrature vs monomial formulas, summation order);
+  * solutions: relative L2 <= 1e-9 per step against the oracle's direct solve.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import fs_workloads as W
+from oracle import oracle as O
+from tests.gpu_helpers import oracle_problem, poly_oseen, rel_l2
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+SMALL = [W.C1, W.unit_square(11, jitter=0.1, seed=3), W.channel(24, 8), W.cube(3),
+         W.cube(4, jitter=0.1, seed=2), poly_oseen(2, (5, 4)), poly_oseen(3, (2, 3, 2))]
+
+
+@pytest.fixture(scope="module")
+def fs():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2605_25403_gb300 import build
+    build.build()
+    from paper_2605_25403_gb300 import fs as mod
+    return mod
+
+
+def _gpu_system(fs, S, t_next):
+    info = S.info
+    val = torch.zeros(info["nnz"], dtype=torch.float64, device="cuda")
+    b = torch.zeros(info["n_dof"], dtype=torch.float64, device="cuda")
+    fs.fs_assemble_step(S.prob, t_next, val, b)
+    torch.cuda.synchronize()
+    return val.cpu().numpy(), b.cpu().numpy()
+
+
+def _row_scaled_err(rp, a, b):
+    err = 0.0
+    for r in range(rp.shape[0] - 1):
+        s = slice(rp[r], rp[r + 1])
+        scale = max(np.abs(b[s]).max(), 1e-300)
+        err = max(err, np.abs(a[s] - b[s]).max() / scale)
+    return err
+
+
+@pytest.mark.parametrize("wl", SMALL, ids=lambda w: w.name)
+def test_assembly_matches_oracle(fs, wl):
+    S = fs.Stepper.from_workload(wl)
+    try:
+        P = oracle_problem(wl)
+        rp, col, val, b = P.system(P.t + P.dt)
+        gval, gb = _gpu_system(fs, S, P.t + P.dt)
+        assert gval.shape == val.shape
+        assert _row_scaled_err(rp, gval, val) <= 1e-12
+        bscale = np.abs(b).max()
+        assert np.abs(gb - b).max() <= 1e-12 * bscale
+    finally:
+        S.close()
+
+
+@pytest.mark.parametrize("wl", SMALL[:4], ids=lambda w: w.name)
+def test_operator_apply_matches_oracle(fs, wl):
+    S = fs.Stepper.from_workload(wl)
+    try:
+        P = oracle_problem(wl)
+        rp, col, val, b = P.system(P.t + P.dt)
+        _gpu_system(fs, S, P.t + P.dt)
+        x = np.random.default_rng(1).standard_normal(P.ndof)
+        y = torch.zeros(P.ndof, dtype=torch.float64, device="cuda")
+        fs.fs_apply_operator(S.prob, torch.from_numpy(x).cuda(), y)
+        ref = O.spmv(rp, col, val, x)
+        assert np.abs(y.cpu().numpy() - ref).max() <= 1e-12 * np.abs(ref).max()
+    finally:
+        S.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "fp32_refine"])
+@pytest.mark.parametrize("wl", [W.C1, W.channel(24, 8).with_(steps=5), W.cube(4, jitter=0.05)
+                                .with_(steps=3)], ids=lambda w: w.name)
+def test_steps_match_oracle(fs, wl, prec):
+    """Free-running time steps: relative L2 <= 1e-9 at every step."""
+    S = fs.Stepper.from_workload(wl, precision=prec)
+    try:
+        P = oracle_problem(wl)
+        x0, t0 = S.state()
+        assert rel_l2(x0, P.x) <= 1e-14
+        for k in range(wl.steps):
+            st = fs.fs_step(S.prob, 1)[0]
+            assert st["status"] == 0 and st["rel_res"] <= 1e-12
+            P.step()
+            x, t = S.state()
+            assert abs(t - P.t) < 1e-15
+            assert rel_l2(x, P.x) <= 1e-9, (k, rel_l2(x, P.x), st)
+    finally:
+        S.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("dim,n", [(2, (5, 4)), (3, (2, 3, 2))])
+def test_polynomial_exactness_on_gpu(fs, dim, n, prec):
+    wl = poly_oseen(dim, n)
+    S = fs.Stepper.from_workload(wl, precision=prec)
+    try:
+        x0, _ = S.state()
+        fs.fs_step(S.prob, 2)
+        x, _ = S.state()
+        assert np.abs(x - x0).max() <= 1e-10 * max(1.0, np.abs(x0).max())
+    finally:
+        S.close()
+
+
+def test_poiseuille_preserved_on_gpu(fs):
+    wl = W.channel(32, 8, init="exact")
+    S = fs.Stepper.from_workload(wl)
+    try:
+        x0, _ = S.state()
+        fs.fs_step(S.prob, 3)
+        x, _ = S.state()
+        assert np.abs(x - x0).max() <= 1e-10
+    finally:
+        S.close()
+
+
+def test_solver_stats_and_limits(fs):
+    """max_iter = 1 cannot converge: the call reports NOT_CONVERGED and keeps
+    a finite iterate (a host-side limit, no device fault)."""
+    S = fs.Stepper.from_workload(W.C1)
+    try:
+        fs.fs_assemble_step(S.prob, W.C1.dt)
+        o = fs.fs_default_solve_opts(max_iter=1)
+        st = fs.fs_solve(S.prob, o, raise_on_error=False)
+        assert st["status"] == 5
+        x, _ = S.state()
+        assert np.all(np.isfinite(x))
+        st = fs.fs_solve(S.prob)
+        assert st["status"] == 0 and st["rel_res"] <= 1e-12
+    finally:
+        S.close()
+
+
+def test_graph_and_direct_launch_agree(fs):
+    xs = []
+    for g in (0, 1):
+        S = fs.Stepper.from_workload(W.C1)
+        try:
+            fs.fs_step(S.prob, 3, fs.fs_default_solve_opts(use_graph=g))
+            xs.append(S.state()[0])
+        finally:
+            S.close()
+    assert rel_l2(xs[0], xs[1]) <= 1e-12
