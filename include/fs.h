@@ -159,7 +159,7 @@ int fs_assemble_step(fs_problem* prob, double t_next, double* val_out,
                      double* b_out);
 
 typedef struct {
-  int restart;        /* GMRES(m) restart length m (<= 64)                  */
+  int restart;        /* GMRES(m) restart length m (this build: 30)         */
   int max_iter;       /* cap on (inner) Krylov iterations per solve         */
   double rtol;        /* stop at ||b - A x||_2 <= rtol ||b||_2, FP64 true
                          residual; a residual that stops decreasing (a
@@ -211,6 +211,20 @@ int fs_set_state(fs_problem* prob, const double* x_in, int host, double t);
 
 /* Sizes of the problem's device footprint in bytes (HBM admission). */
 int64_t fs_problem_device_bytes(const fs_problem* prob);
+
+/* FP64 residual check of a monolithic CSR system (the format fs_dof_map and
+ * fs_assemble_step export; paper Sec. 3.1, the error step after the linear
+ * solver): out2[0] = ||b - A x||_2, out2[1] = ||b||_2.
+ *   n       rows (>= 1); rowptr (n + 1, int64), col (int32), val (FP64),
+ *           x, b (n, FP64): device pointers, borrowed;
+ *   out2    host pointer to 2 doubles;
+ *   stream  cudaStream_t (NULL = default stream).
+ * Per-block partial sums go to stream-ordered scratch (cudaMallocAsync,
+ * freed before return).  Synchronises the stream.  FS_ERR_INVALID_ARG on a
+ * null pointer or n < 1, FS_ERR_OOM / FS_ERR_CUDA on runtime failures. */
+int fs_csr_residual_norm(int64_t n, const int64_t* rowptr, const int32_t* col,
+                         const double* val, const double* x, const double* b,
+                         double* out2, void* stream);
 
 /* Instrumentation (no counterpart in the paper).
  * fs_launch_count: kernels launched by this library since load, counting

@@ -240,7 +240,9 @@ int alloc_krylov(fs_problem* P, Krylov<V>& K, int m) {
   FS_TRY(P->alloc(&K.work_u, (int64_t)P->dim * P->n2));
   FS_TRY(P->alloc(&K.rhs, K.n));
   FS_TRY(P->alloc(&K.sol, K.n));
-  int64_t nblk = (K.n + 4095) / 4096 + 1;
+  // partial sums: (restart + 1) vectors x at most 4 x 152 blocks (CGS2
+  // passes) or one block per 4096 entries (norms)
+  int64_t nblk = std::max<int64_t>((K.n + 4095) / 4096 + 1, 4 * 152);
   FS_TRY(P->alloc(&K.partial, (int64_t)(kMaxRestart + 1) * nblk));
   FS_TRY(P->alloc(&K.st, 1));
   FS_CUDA(cudaMemset(K.st, 0, sizeof(GmresState)));
@@ -735,8 +737,8 @@ int fs_problem_create(fs_mesh* mesh, const fs_problem_desc* desc, void* stream,
         if (fixed[q] || fixed[Kp.col[k]]) Kp.val[k] = (Kp.col[k] == q) ? 1.0 : 0.0;
   }
   HostHierarchy HA, HK;
-  build_hierarchy(me, A0, true, me.dlist, 400, HA);
-  build_hierarchy(me, Kp, false, kfix, 400, HK);
+  build_hierarchy(me, A0, true, me.dlist, 800, HA);
+  build_hierarchy(me, Kp, false, kfix, 800, HK);
 
   // vectors
   FS_TRY(P->alloc(&P->x, P->ndof));

@@ -11,7 +11,7 @@
 namespace fs {
 
 constexpr int kMaxLoc = 10;  // P2 nodes per tetrahedron
-constexpr int kMaxRestart = 64;
+constexpr int kMaxRestart = 32;
 
 // Thread-local error message behind fs_last_error().
 void set_error(const std::string& msg);

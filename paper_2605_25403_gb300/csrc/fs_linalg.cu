@@ -416,17 +416,25 @@ __global__ void k_scale(V* __restrict__ x, int64_t n, const double* num, const d
 }
 
 // Classical Gram-Schmidt with one reorthogonalisation (CGS2) of
-// w = V[j+1] against V[0..j]; passes:
-//   1: h = V^T w                    -> H[:, j] = h
-//   2: w -= V h ; h2 = V^T w        -> H[:, j] += h2, st->h2 = h2
-//   3: w -= V h2 ; ||w||            -> H[j+1, j] = st->hn = ||w||
+// w = V[j+1] against V[0..j]; three grid-stride passes over the basis:
+//   1: h = V^T w                            -> H[:, j] = h
+//   2: w -= V h, then h2 = V^T w            -> H[:, j] += h2, st->h2 = h2
+//      (per element: the update needs only that element, so the re-dot
+//      reuses the basis values just read, from L1)
+//   3: w -= V h2 ; ||w||                    -> H[j+1, j] = st->hn = ||w||
+// Per-thread accumulators live in registers (restart length <= 32); block
+// sums go to partial[v][block]; the last block reduces them in FP64.
+constexpr int kCgsBlocks = 4 * 152;
+
 template <typename V, int PASS>
 __global__ void __launch_bounds__(kRB) k_cgs(V* __restrict__ Vb, int64_t n, int j,
                                              GmresState* st, double* partial,
                                              const int* skip) {
   if (st->done) return;
-  __shared__ double sm[32];
-  __shared__ double coef[kMaxRestart + 1];
+  constexpr int NV = kMaxRestart + 1;
+  constexpr int NW = kRB / 32;
+  __shared__ double coef[NV];
+  __shared__ double wsum[NV * NW];
   const int nvec = j + 1;
   const int m = st->m;
   V* __restrict__ w = Vb + (int64_t)(j + 1) * n;
@@ -435,64 +443,49 @@ __global__ void __launch_bounds__(kRB) k_cgs(V* __restrict__ Vb, int64_t n, int 
       coef[i] = PASS == 2 ? st->H[i * m + j] : st->h2[i];
     __syncthreads();
   }
-  const int64_t base = (int64_t)blockIdx.x * kTile + threadIdx.x;
-  double wl[kEPT];
+  // accumulators in the vector precision (a thread sums few elements), the
+  // block and grid reductions in FP64
+  V acc[NV];
 #pragma unroll
-  for (int e = 0; e < kEPT; ++e) {
-    const int64_t i = base + (int64_t)e * kRB;
-    wl[e] = i < n ? (double)w[i] : 0.0;
-  }
-  if (PASS >= 2) {
-    for (int v = 0; v < nvec; ++v) {
-      const V* __restrict__ vv = Vb + (int64_t)v * n;
-      const double c = coef[v];
+  for (int v = 0; v < NV; ++v) acc[v] = V(0);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+    V wi = w[i];
+    if (PASS >= 2) {
+      V u = V(0);
 #pragma unroll
-      for (int e = 0; e < kEPT; ++e) {
-        const int64_t i = base + (int64_t)e * kRB;
-        if (i < n) wl[e] -= c * (double)vv[i];
-      }
+      for (int v = 0; v < NV; ++v)
+        if (v < nvec) u += (V)coef[v] * Vb[(int64_t)v * n + i];
+      wi -= u;
+      w[i] = wi;
     }
+    if (PASS <= 2) {
 #pragma unroll
-    for (int e = 0; e < kEPT; ++e) {
-      const int64_t i = base + (int64_t)e * kRB;
-      if (i < n) {
-        w[i] = (V)wl[e];
-        wl[e] = (double)(V)wl[e];  // dot against the stored (rounded) vector
-      }
+      for (int v = 0; v < NV; ++v)
+        if (v < nvec) acc[v] += Vb[(int64_t)v * n + i] * wi;
+    } else {
+      acc[0] += wi * wi;
     }
   }
-  if (PASS <= 2) {
-    // per-warp sums of every dot product, then one barrier
-    __shared__ double wsum[(kMaxRestart + 1) * (kRB / 32)];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int v = 0; v < nvec; ++v) {
-      const V* __restrict__ vv = Vb + (int64_t)v * n;
-      double acc = 0;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nout = PASS <= 2 ? nvec : 1;
 #pragma unroll
-      for (int e = 0; e < kEPT; ++e) {
-        const int64_t i = base + (int64_t)e * kRB;
-        if (i < n) acc += wl[e] * (double)vv[i];
-      }
-      acc = warp_sum(acc);
-      if (lane == 0) wsum[v * (kRB / 32) + warp] = acc;
+  for (int v = 0; v < NV; ++v) {
+    if (v < nout) {
+      double t = warp_sum((double)acc[v]);
+      if (lane == 0) wsum[v * NW + warp] = t;
     }
-    __syncthreads();
-    for (int v = threadIdx.x; v < nvec; v += blockDim.x) {
-      double t = 0;
+  }
+  __syncthreads();
+  for (int v = threadIdx.x; v < nout; v += blockDim.x) {
+    double t = 0;
 #pragma unroll
-      for (int w2 = 0; w2 < kRB / 32; ++w2) t += wsum[v * (kRB / 32) + w2];
-      partial[(int64_t)v * gridDim.x + blockIdx.x] = t;
-    }
-  } else {
-    double acc = 0;
-#pragma unroll
-    for (int e = 0; e < kEPT; ++e) acc += wl[e] * wl[e];
-    double t = block_sum(acc, sm);
-    if (threadIdx.x == 0) partial[blockIdx.x] = t;
+    for (int w2 = 0; w2 < NW; ++w2) t += wsum[v * NW + w2];
+    partial[(int64_t)v * gridDim.x + blockIdx.x] = t;
   }
   if (!last_block(&st->counter[PASS])) return;
-  __shared__ double res[kMaxRestart + 1];
-  reduce_partials(partial, PASS <= 2 ? nvec : 1, gridDim.x, res);
+  __shared__ double res[NV];
+  reduce_partials(partial, nout, gridDim.x, res);
   if (threadIdx.x == 0) {
     if (PASS == 1) {
       for (int i = 0; i < nvec; ++i) st->H[i * m + j] = res[i];
@@ -726,8 +719,8 @@ template void launch_scale<float>(float*, int64_t, const double*, const double*,
 template <typename V>
 void launch_cgs2(V* Vb, int64_t n, int j, GmresState* st, double* partial, const int* skip,
                  cudaStream_t s) {
-  unsigned g = (unsigned)((n + kTile - 1) / kTile);
-  if (g < 1) g = 1;
+  int64_t gg = (n + kRB - 1) / kRB;
+  unsigned g = (unsigned)(gg < 1 ? 1 : (gg > kCgsBlocks ? kCgsBlocks : gg));
   k_cgs<V, 1><<<g, kRB, 0, s>>>(Vb, n, j, st, partial, skip);
   count_launches(1);
   k_cgs<V, 2><<<g, kRB, 0, s>>>(Vb, n, j, st, partial, skip);

@@ -89,6 +89,8 @@ _lib.fs_get_state.argtypes = [_vp, _vp, _int, _P(_d)]
 _lib.fs_set_state.argtypes = [_vp, _vp, _int, _d]
 _lib.fs_problem_device_bytes.restype = _i64
 _lib.fs_problem_device_bytes.argtypes = [_vp]
+_lib.fs_csr_residual_norm.restype = _int
+_lib.fs_csr_residual_norm.argtypes = [_i64, _vp, _vp, _vp, _vp, _vp, _P(_d), _vp]
 _lib.fs_launch_count.restype = _i64
 _lib.fs_launch_count.argtypes = []
 _lib.fs_profile_kernel.restype = _int
@@ -102,7 +104,7 @@ EXPORTED = ["fs_mesh_create", "fs_mesh_destroy", "fs_dof_map", "fs_problem_creat
             "fs_problem_destroy", "fs_assemble_step", "fs_solve", "fs_step",
             "fs_apply_operator", "fs_get_state", "fs_set_state", "fs_problem_device_bytes",
             "fs_default_solve_opts", "fs_last_error", "fs_launch_count",
-            "fs_profile_kernel"]
+            "fs_profile_kernel", "fs_csr_residual_norm"]
 FS_KERNEL_SPMV, FS_KERNEL_SPMV_FP64, FS_KERNEL_CHEB, FS_KERNEL_ASSEMBLE_CONV = range(4)
 
 
@@ -237,6 +239,16 @@ _state_sizes = {}
 
 def _state_len(prob):
     return _state_sizes[prob.value]
+
+
+def fs_csr_residual_norm(rowptr, col, val, x, b, stream=None):
+    """(||b - A x||_2, ||b||_2) of a monolithic CSR system held in CUDA
+    tensors (rowptr int64, col int32, val/x/b float64)."""
+    out = (_d * 2)()
+    s = None if stream is None else ctypes.c_void_p(int(stream))
+    _check(_lib.fs_csr_residual_norm(rowptr.numel() - 1, _dptr(rowptr), _dptr(col), _dptr(val),
+                                     _dptr(x), _dptr(b), out, s), "fs_csr_residual_norm")
+    return out[0], out[1]
 
 
 def fs_launch_count():

@@ -156,3 +156,21 @@ def test_graph_and_direct_launch_agree(fs):
         finally:
             S.close()
     assert rel_l2(xs[0], xs[1]) <= 1e-12
+
+
+@pytest.mark.parametrize("wl", [W.C1, W.cube(3)], ids=lambda w: w.name)
+def test_csr_residual_norm_matches_host(fs, wl):
+    """The device residual check of an exported monolithic system agrees with
+    the same norms computed on the host from the same arrays."""
+    S = fs.Stepper.from_workload(wl, dofmap_arrays=True)
+    try:
+        gval, gb = _gpu_system(fs, S, wl.dt)
+        rp, col = S.info["rowptr"], S.info["col"]
+        x = np.random.default_rng(3).standard_normal(S.info["n_dof"])
+        t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+        r, bn = fs.fs_csr_residual_norm(t(rp), t(col), t(gval), t(x), t(gb))
+        ref = gb - O.spmv(rp, col, gval, x)
+        assert abs(r - np.linalg.norm(ref)) <= 1e-12 * np.linalg.norm(ref)
+        assert abs(bn - np.linalg.norm(gb)) <= 1e-13 * np.linalg.norm(gb)
+    finally:
+        S.close()
