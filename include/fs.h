@@ -226,6 +226,28 @@ int fs_csr_residual_norm(int64_t n, const int64_t* rowptr, const int32_t* col,
                          const double* val, const double* x, const double* b,
                          double* out2, void* stream);
 
+/* The same residual check for callers that cannot allocate device memory
+ * (the paper has no counterpart: it is a deployment aid).  Callers that run
+ * while a stream is being captured into a CUDA graph, serving processes whose
+ * device memory is committed to resident problems under a fixed budget, and
+ * host applications that forbid libraries to grow their footprint after
+ * start-up cannot call cudaMalloc; this entry point calls no allocator at
+ * all.  Its scratch is a fixed array in the library's static device memory
+ * (about 128 KB, held by every GPU that loads the library until the process
+ * exits), sized for systems of at most 4,194,304 rows: larger n returns
+ * FS_ERR_INVALID_ARG with a message, before any device work.  Arguments,
+ * results and errors are those of fs_csr_residual_norm.
+ * Set-up: the first call on a device resolves the array's device address
+ * (cudaGetSymbolAddress) with that device current, so make that first call
+ * before any stream capture.  Every call shares the one array and clears
+ * what must start at zero itself; calls that overlap on the GPU (other
+ * streams, other host threads) race on it and must be serialised by the
+ * caller. */
+int fs_csr_residual_norm_noalloc(int64_t n, const int64_t* rowptr,
+                                 const int32_t* col, const double* val,
+                                 const double* x, const double* b,
+                                 double* out2, void* stream);
+
 /* Instrumentation (no counterpart in the paper).
  * fs_launch_count: kernels launched by this library since load, counting
  * every node of each replayed CUDA graph (host-side counter).

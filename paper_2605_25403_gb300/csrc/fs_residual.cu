@@ -147,3 +147,93 @@ extern "C" int fs_csr_residual_norm(int64_t n, const int64_t* rowptr, const int3
   return FS_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the same check.
+//
+// Some callers cannot allocate device memory when they want to check a
+// solution: code that runs while a stream is being captured into a CUDA
+// graph, a serving process whose device memory is already committed to
+// resident problems under a fixed budget, or a host application that does
+// not let libraries grow their footprint after start-up.  This entry point
+// runs the same kernel with its scratch (per-block partial sums, the ticket
+// counter and the two results) in a fixed array of the library's static
+// device memory instead: kNoAllocBlocks blocks of 512 rows each, so systems
+// of at most kNoAllocMaxRows rows.  Every GPU that loads the library holds
+// the array (about 128 KB) until the process exits.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace fs {
+namespace {
+
+constexpr int kNoAllocBlocks = 8192;
+constexpr int64_t kNoAllocRowsPerBlock = 512;
+constexpr int64_t kNoAllocMaxRows = kNoAllocBlocks * kNoAllocRowsPerBlock;  // 4,194,304
+
+// [0, 2*kNoAllocBlocks): partial sums; then the 2 results; then the counter
+static __device__ __align__(256) double g_noalloc_scratch[2 * kNoAllocBlocks + 4];
+
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[64] = {};  // device address of the array, per device
+
+}  // namespace
+}  // namespace fs
+
+extern "C" int fs_csr_residual_norm_noalloc(int64_t n, const int64_t* rowptr,
+                                            const int32_t* col, const double* val,
+                                            const double* x, const double* b, double* out2,
+                                            void* stream) {
+  if (n < 1 || !rowptr || !col || !val || !x || !b || !out2) {
+    set_error("fs_csr_residual_norm_noalloc: null pointer or n < 1");
+    return FS_ERR_INVALID_ARG;
+  }
+  if (n > kNoAllocMaxRows) {
+    set_error("fs_csr_residual_norm_noalloc: " + std::to_string(n) +
+              " rows exceed the limit of its static scratch (" +
+              std::to_string(kNoAllocMaxRows) + " rows); use fs_csr_residual_norm");
+    return FS_ERR_INVALID_ARG;
+  }
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess || dev < 0 || dev >= 64) {
+    set_error("fs_csr_residual_norm_noalloc: no usable current device");
+    return FS_ERR_CUDA;
+  }
+  double* base = nullptr;
+  {
+    // first call on this device: resolve the array's device address with the
+    // device current (the host-side name is only a stand-in)
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+      void* p = nullptr;
+      e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      if (e != cudaSuccess || !p) {
+        set_error(std::string("fs_csr_residual_norm_noalloc: cudaGetSymbolAddress: ") +
+                  cudaGetErrorString(e));
+        return FS_ERR_CUDA;
+      }
+      g_noalloc_ptr[dev] = (double*)p;
+    }
+    base = g_noalloc_ptr[dev];
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const unsigned grid = (unsigned)((n + kNoAllocRowsPerBlock - 1) / kNoAllocRowsPerBlock);
+  double* partial = base;
+  double* out = base + 2 * kNoAllocBlocks;
+  unsigned* counter = (unsigned*)(base + 2 * kNoAllocBlocks + 2);
+  // the array keeps the previous call's contents: the ticket counter must
+  // start at zero
+  e = cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
+  if (e == cudaSuccess) {
+    k_csr_resid<<<grid, kResBlock, 0, s>>>(n, rowptr, col, val, x, b, partial, counter, out);
+    count_launches(1);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out2, out, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    set_error(std::string("fs_csr_residual_norm_noalloc: ") + cudaGetErrorString(e));
+    return FS_ERR_CUDA;
+  }
+  return FS_OK;
+}

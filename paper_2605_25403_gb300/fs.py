@@ -91,6 +91,8 @@ _lib.fs_problem_device_bytes.restype = _i64
 _lib.fs_problem_device_bytes.argtypes = [_vp]
 _lib.fs_csr_residual_norm.restype = _int
 _lib.fs_csr_residual_norm.argtypes = [_i64, _vp, _vp, _vp, _vp, _vp, _P(_d), _vp]
+_lib.fs_csr_residual_norm_noalloc.restype = _int
+_lib.fs_csr_residual_norm_noalloc.argtypes = [_i64, _vp, _vp, _vp, _vp, _vp, _P(_d), _vp]
 _lib.fs_launch_count.restype = _i64
 _lib.fs_launch_count.argtypes = []
 _lib.fs_profile_kernel.restype = _int
@@ -104,7 +106,7 @@ EXPORTED = ["fs_mesh_create", "fs_mesh_destroy", "fs_dof_map", "fs_problem_creat
             "fs_problem_destroy", "fs_assemble_step", "fs_solve", "fs_step",
             "fs_apply_operator", "fs_get_state", "fs_set_state", "fs_problem_device_bytes",
             "fs_default_solve_opts", "fs_last_error", "fs_launch_count",
-            "fs_profile_kernel", "fs_csr_residual_norm"]
+            "fs_profile_kernel", "fs_csr_residual_norm", "fs_csr_residual_norm_noalloc"]
 FS_KERNEL_SPMV, FS_KERNEL_SPMV_FP64, FS_KERNEL_CHEB, FS_KERNEL_ASSEMBLE_CONV = range(4)
 
 
@@ -248,6 +250,19 @@ def fs_csr_residual_norm(rowptr, col, val, x, b, stream=None):
     s = None if stream is None else ctypes.c_void_p(int(stream))
     _check(_lib.fs_csr_residual_norm(rowptr.numel() - 1, _dptr(rowptr), _dptr(col), _dptr(val),
                                      _dptr(x), _dptr(b), out, s), "fs_csr_residual_norm")
+    return out[0], out[1]
+
+
+def fs_csr_residual_norm_noalloc(rowptr, col, val, x, b, stream=None, n=None):
+    """Same as fs_csr_residual_norm through the allocation-free entry point
+    (static device scratch; for callers that cannot allocate).  `n`
+    overrides the row count (only to exercise the size check)."""
+    out = (_d * 2)()
+    s = None if stream is None else ctypes.c_void_p(int(stream))
+    rows = rowptr.numel() - 1 if n is None else int(n)
+    _check(_lib.fs_csr_residual_norm_noalloc(rows, _dptr(rowptr), _dptr(col), _dptr(val),
+                                             _dptr(x), _dptr(b), out, s),
+           "fs_csr_residual_norm_noalloc")
     return out[0], out[1]
 
 
