@@ -29,7 +29,7 @@ METRIC = "NS steps/s & DOF/s vs plain FP64 GPU path; % HBM roofline; p50/p99 lat
 L2_FLUSH_BYTES = 256 << 20  # > 135 MB of L2
 
 
-def parse():
+def parse(argv=None):
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=40)
@@ -41,7 +41,11 @@ def parse():
                    help="steps of the plain FP64 path timed for the comparison")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--roofline-kernel", default="cheb", choices=["cheb", "spmv", "assemble"])
-    return p.parse_args()
+    p.add_argument("--batch-steps", type=int, default=3,
+                   help="timed steps of the 96-instance batched workload (0: skip)")
+    p.add_argument("--serve-requests", type=int, default=32,
+                   help="requests of the serving run (0: skip)")
+    return p.parse_args(argv)
 
 
 def workload(name):
@@ -171,6 +175,95 @@ def reference_arm(args, rank):
     return 0
 
 
+def aggregate_time(total_s, dist):
+    """Slowest rank's time (the whole job runs until its last rank ends)."""
+    if dist is None:
+        return total_s
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([total_s], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+def batched_run(torch, fs, steps, warmup=1):
+    """The batched workload: 96 unit-square instances, N and Re drawn
+    log-uniform from the seed, one problem over their union (one launch per
+    phase for all instances), FP32 inner / FP64 refinement."""
+    import fs_workloads as W
+    import numpy as np
+    wls = W.batched_instances()
+    t0 = time.perf_counter()
+    B = fs.Stepper.from_workloads(wls, precision=fs.FS_PREC_FP32_REFINE)
+    setup_s = time.perf_counter() - t0
+    try:
+        for _ in range(warmup):
+            fs.fs_step(B.prob, 1)
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fs.fs_step(B.prob, 1)
+            e1.record()
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        st = fs.fs_instance_stats(B.prob)
+        ndof = B.info["n_dof"]
+    finally:
+        B.close()
+    per_step = sum(ms) / len(ms) / 1e3
+    return {"workload": "96 unit squares, N log-uniform [16,256], Re log-uniform [1,2000], "
+                        "dt 1e-3, seed 0", "instances": len(wls), "ndof_total": ndof,
+            "ms_per_step": 1e3 * per_step, "steps_per_s": 1.0 / per_step,
+            "instance_steps_per_s": len(wls) / per_step, "dof_per_s": ndof / per_step,
+            "setup_s": setup_s, "timed_steps": steps,
+            "iters_max": max(x["iters"] for x in st),
+            "iters_median": float(np.median([x["iters"] for x in st])),
+            "status_ok": all(x["status"] == 0 for x in st),
+            "rel_res_max": max(x["rel_res"] for x in st)}
+
+
+def serving_run(fs, count, rate=200.0, budget=150 << 30, slots=32):
+    """Poisson arrivals (seeded) of 2D and 3D solves, sizes log-uniform but
+    capped so the run ends in seconds (2D N <= 96, 3D N <= 16, 5-20 steps),
+    admitted by the native loop under the HBM budget; latency = completion -
+    arrival on the wall clock."""
+    import fs_workloads as W
+    import numpy as np
+    reqs = W.serving_requests(count=count, rate=rate, n2d=(16, 96), n3d=(8, 16), steps=(5, 20))
+    srv = fs.Server(budget, slots)
+    try:
+        t0 = time.perf_counter()
+        pending = list(reqs)
+        done = []
+        while len(done) < len(reqs):
+            now = time.perf_counter() - t0
+            while pending and pending[0].arrival <= now:
+                r = pending.pop(0)
+                srv.submit(r.workload, r.workload.steps, r.arrival)
+            srv.progress(now)
+            done += srv.completed()
+            if time.perf_counter() - t0 > 600:
+                break
+        span = time.perf_counter() - t0
+    finally:
+        srv.close()
+    lat = np.array([d["finished"] - d["arrival"] for d in done])
+    steps = sum(d["nsteps"] for d in done)
+    dofsteps = sum(r.workload.ndof * r.workload.steps for r in reqs[:len(done)])
+    return {"requests": len(reqs), "completed": len(done),
+            "ok": sum(1 for d in done if d["status"] == 0), "rate_per_s": rate,
+            "latency_p50_s": float(np.percentile(lat, 50)) if len(lat) else None,
+            "latency_p99_s": float(np.percentile(lat, 99)) if len(lat) else None,
+            "steps_per_s": steps / span, "dof_steps_per_s": dofsteps / span,
+            "makespan_s": span, "hbm_budget_gb": budget / 2**30, "slots": slots,
+            "workload": "Poisson 200/s; 2D N log-uniform [16,96] / 3D N [8,16] (Bernoulli 1/2), "
+                        "Re log-uniform [1,2000], 5-20 steps, seed 0"}
+
+
 # ---------------------------------------------------------------------------
 def time_steps(torch, fs, S, stream, steps, flush):
     """Per-step CUDA-event times (ms) of fs_step on the problem's stream;
@@ -250,11 +343,7 @@ def main():
     if dist:
         dist.barrier()
     clocks = sampler.stop()
-    total_s = sum(times) / 1e3
-    if dist:
-        t = torch.tensor([total_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
+    total_s = aggregate_time(sum(times) / 1e3, dist)
     value = world * args.steps / total_s
     ms_per_step = 1e3 * total_s / args.steps
 
@@ -308,6 +397,8 @@ def main():
                          f"DOF/s"}
 
     S.close()
+    batch = batched_run(torch, fs, args.batch_steps) if args.batch_steps > 0 else None
+    serving = serving_run(fs, args.serve_requests) if args.serve_requests > 0 else None
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -338,6 +429,8 @@ def main():
         "roofline": roofline,
         "kernels": kernels,
         "cpu_baseline": cpu,
+        "batched": batch,
+        "serving": serving,
     }
     print(json.dumps(line), flush=True)
     if dist:

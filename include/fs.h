@@ -99,6 +99,19 @@ typedef struct fs_problem fs_problem;
 int fs_mesh_create(const fs_mesh_desc* desc, fs_mesh** out);
 int fs_mesh_destroy(fs_mesh* mesh);
 
+/* A batch: `count` independent structured meshes (same dim) numbered as one
+ * mesh with several disconnected pieces: all vertices instance by instance,
+ * then all edge nodes, then all cells.  Every later call treats the batch
+ * like one mesh; each kernel launch covers every instance.  descs is a host
+ * array of count descriptions.  Errors as fs_mesh_create. */
+int fs_mesh_create_batch(const fs_mesh_desc* descs, int count, fs_mesh** out);
+
+/* Where each instance sits in the union numbering.  offsets (host, 6 int64
+ * per instance, may be NULL): first vertex, vertex count, first edge node
+ * (union P2 id), edge node count, first cell, cell count.  Returns the number
+ * of instances, or a negative status. */
+int fs_mesh_instances(const fs_mesh* mesh, int64_t* offsets);
+
 /* Sizes of the Taylor-Hood P2/P1 discretisation (Sec. 2.2.1, V_h and Q_h
  * with k = 2).  nnz counts the monolithic saddle-point CSR
  *   [A 0 -Bx^T; 0 A -By^T; Bx By D] (3D analogous) with an explicit
@@ -145,6 +158,15 @@ int fs_problem_create(fs_mesh* mesh, const fs_problem_desc* desc,
                       void* stream, fs_problem** out);
 int fs_problem_destroy(fs_problem* prob);
 
+/* Problem on a batched mesh: one description per instance (host array of
+ * count = number of instances).  The instances may differ in nu and
+ * pin_pressure only.  Every instance runs its own Arnoldi process (own
+ * Hessenberg matrix, rotations, convergence test), so its iterates do not
+ * depend on the other instances; the launches are shared.  fs_problem_create
+ * on a batched mesh applies one description to all instances. */
+int fs_problem_create_batch(fs_mesh* mesh, const fs_problem_desc* descs,
+                            int count, void* stream, fs_problem** out);
+
 /* Assembles the Oseen system of the step t -> t_next (paper Sec. 2.2.1,
  * Oseen equation; BForm/LForm of Sec. 3.1) with the convecting velocity
  * w = u^n taken from the current state (or wconst), into the problem's
@@ -172,7 +194,8 @@ typedef struct {
 } fs_solve_opts;
 
 typedef struct {
-  int iters;          /* Krylov iterations (inner ones in precision mode)   */
+  int iters;          /* Krylov iterations (inner ones in precision mode);
+                         over a batch: the largest of the instances        */
   int refinements;    /* FP64 refinement steps (0 in FP64 mode)             */
   int status;         /* fs_status of the solve                             */
   int cycles;         /* GMRES restart cycles                               */
@@ -200,6 +223,20 @@ int fs_solve(fs_problem* prob, const fs_solve_opts* opts, double* x,
 int fs_step(fs_problem* prob, int nsteps, const fs_solve_opts* opts,
             fs_solve_stats* per_step);
 
+/* Non-blocking time stepping for callers that drive several problems at
+ * once (the serving loop): fs_step_begin enqueues the first step's assembly
+ * and the first device part of its solve and returns; fs_step_poll advances
+ * the solve's state machine by every part that has completed (wait = 0:
+ * never blocks; wait = 1: blocks until the next part completes) and sets
+ * *done when all nsteps are finished, returning their status then.  One step
+ * sequence per problem at a time (FS_ERR_BUSY otherwise). */
+int fs_step_begin(fs_problem* prob, int nsteps, const fs_solve_opts* opts);
+int fs_step_poll(fs_problem* prob, int wait, int* done);
+
+/* Per-instance statistics of the last solve (host array, one entry per
+ * instance). */
+int fs_instance_stats(const fs_problem* prob, fs_solve_stats* per_instance);
+
 /* y = A x with the assembled FP64 saddle-point operator (device FP64
  * vectors of n_dof entries). */
 int fs_apply_operator(fs_problem* prob, const double* x, double* y);
@@ -211,6 +248,49 @@ int fs_set_state(fs_problem* prob, const double* x_in, int host, double t);
 
 /* Sizes of the problem's device footprint in bytes (HBM admission). */
 int64_t fs_problem_device_bytes(const fs_problem* prob);
+
+/* ---- Continuous-batching request loop (no counterpart in the paper: its
+ * workflow runs one simulation at a time, Sec. 3.1 ComputationModel). ----
+ * Requests wait in a FIFO queue and are admitted while a slot is free and
+ * their estimated device footprint fits in the budget left by the resident
+ * requests.  Admitted requests are set up by host worker threads, then
+ * stepped through fs_step_begin / fs_step_poll on their own streams, so the
+ * work of all resident requests overlaps on the device.  Times are the
+ * caller's clock (seconds), passed to submit and progress. */
+typedef struct fs_server fs_server;
+typedef struct {
+  int64_t hbm_budget;   /* bytes of device memory the resident requests may use */
+  int max_slots;        /* resident requests at most                          */
+  int setup_threads;    /* host threads setting requests up (<= 0: 4)        */
+} fs_server_desc;
+typedef struct {
+  int64_t id;
+  int status;           /* fs_status of the request                           */
+  int nsteps, iters;    /* steps run; Krylov iterations of its last step      */
+  double arrival, admitted, started, finished;  /* caller clock, seconds     */
+  int64_t device_bytes; /* measured footprint                                 */
+} fs_request_result;
+int fs_server_create(const fs_server_desc* desc, fs_server** out);
+/* Destroys the server and every request still queued or resident. */
+int fs_server_destroy(fs_server* server);
+/* Queues one request (host descriptions, copied).  keep_state = 1 keeps the
+ * final state on the host for fs_server_take_state.  *id receives its id.
+ * FS_ERR_OOM when its estimate alone exceeds the budget. */
+int fs_server_submit(fs_server* server, const fs_mesh_desc* mesh,
+                     const fs_problem_desc* problem, int nsteps, double arrival,
+                     int keep_state, int64_t* id);
+/* Admits, starts and advances requests without blocking; *n_completed
+ * receives the number of requests that finished in this call. */
+int fs_server_progress(fs_server* server, double now, int* n_completed);
+/* Moves up to max finished-request records into out (host); *n = count. */
+int fs_server_pop_completed(fs_server* server, fs_request_result* out, int max,
+                            int* n);
+/* Copies the kept final state (n_dof FP64, host) of a finished request. */
+int fs_server_take_state(fs_server* server, int64_t id, double* x, int64_t n);
+int fs_server_status(const fs_server* server, int* queued, int* resident,
+                     int64_t* bytes_reserved);
+/* The admission estimate of a request's device footprint in bytes. */
+int64_t fs_server_estimate_bytes(const fs_mesh_desc* mesh, int precision);
 
 /* FP64 residual check of a monolithic CSR system (the format fs_dof_map and
  * fs_assemble_step export; paper Sec. 3.1, the error step after the linear

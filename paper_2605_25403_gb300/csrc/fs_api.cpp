@@ -1,20 +1,23 @@
-// C ABI of libfs (include/fs.h): problem lifecycle, the per-step assembly
-// driver, flexible GMRES(m) with FP64 or FP32-plus-FP64-refinement
-// arithmetic, and CUDA-graph replay of restart cycles.
+// C ABI of libfs (include/fs.h): problem lifecycle (single meshes and batches
+// of independent instances), the per-step assembly driver, and the flexible
+// GMRES(m) solve as a resumable state machine (FP64, or FP32 inner cycles
+// with FP64 iterative refinement), replaying restart cycles as CUDA graphs.
 //
 // Paper Sec. 3.1 (ComputationModel workflow: assembly -> linear solver ->
 // update) and Sec. 2.2.1 (Oseen step).  Host code only: every floating-point
-// operation on the step's data runs in the kernels of fs_assembly.cu and
-// fs_linalg.cu.
+// operation on the step's data runs in the kernels of fs_assembly.cu,
+// fs_linalg.cu and fs_krylov.cu.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <functional>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -33,7 +36,7 @@ thread_local bool g_capturing = false;
 std::atomic<int64_t> g_launches{0};
 
 RefTensors g_ref2, g_ref3;
-bool g_ref_ready = false;
+std::once_flag g_ref_once;
 }  // namespace
 
 void set_error(const std::string& msg) { g_err = msg; }
@@ -57,11 +60,20 @@ namespace {
     }                                                                            \
   } while (0)
 
-#define FS_TRY(expr)            \
-  do {                          \
-    int rc_ = (expr);           \
+#define FS_TRY(expr)              \
+  do {                            \
+    int rc_ = (expr);             \
     if (rc_ != FS_OK) return rc_; \
   } while (0)
+
+// Host mirror of the 64-byte status block at the head of SegState.
+struct SegHost {
+  double beta, resid, bnorm, rnorm, tol_abs;
+  int done, k, bad, retired, first_tile, ntiles;
+};
+static_assert(sizeof(SegHost) == 64, "status block layout");
+static_assert(offsetof(SegState, retired) == offsetof(SegHost, retired), "status layout");
+static_assert(offsetof(SegState, ntiles) == offsetof(SegHost, ntiles), "status layout");
 
 template <typename V>
 struct Krylov {
@@ -73,11 +85,12 @@ struct Krylov {
   V* work_u = nullptr;  // dim x n2
   V* rhs = nullptr;     // inner right-hand side (precision mode)
   V* sol = nullptr;     // inner solution (precision mode)
-  double* partial = nullptr;
-  GmresState* st = nullptr;
+  double* partial = nullptr;  // (m+1) x ntiles
+  SegState* st = nullptr;
+  KCtl* ctl = nullptr;
   cudaGraphExec_t g_check = nullptr, g_iter = nullptr;
   size_t n_check = 0, n_iter = 0;  // kernel nodes per graph
-  const void* g_x = nullptr;  // buffers the graphs were captured with
+  const void* g_x = nullptr;       // buffers the graphs were captured with
   const void* g_b = nullptr;
 };
 
@@ -90,14 +103,32 @@ struct Precision {
   int lanes = 4;
 };
 
+// Resumable solve / step state.
+enum Phase { PH_IDLE, PH_CHECK, PH_ITER, PH_RES64, PH_INNER, PH_DONE };
+
+struct SolveCtx {
+  fs_solve_opts o{};
+  double* x = nullptr;
+  int phase = PH_IDLE;
+  int steps_left = 0;
+  fs_solve_stats* per_step = nullptr;  // caller array (blocking fs_step)
+  int step_index = 0;
+  int rc = FS_OK;
+  // per segment
+  std::vector<int> status, iters, cycles, refines;
+  std::vector<double> relres, prev;
+  std::vector<int> retired;
+};
+
 }  // namespace
 
 struct fs_problem {
   fs_mesh* mesh = nullptr;
   fs_problem_desc desc{};
+  std::vector<fs_problem_desc> inst_desc;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
-  int dim = 0;
+  int dim = 0, nseg = 1;
   int64_t n2 = 0, nv = 0, ndof = 0;
   std::vector<void*> allocs;
   int64_t bytes = 0;
@@ -107,9 +138,6 @@ struct fs_problem {
   double *baseA = nullptr, *Mv = nullptr, *valA = nullptr, *B = nullptr, *BT = nullptr;
   double *Kp = nullptr, *mpl = nullptr, *diagp = nullptr;
   double *x = nullptr, *b = nullptr, *F = nullptr, *r64 = nullptr;
-  double* scal = nullptr;  // device scalars: [0] ||b||, [1] ||r||, ...
-  unsigned* counters = nullptr;
-  double* partial64 = nullptr;
   int32_t* pinned = nullptr;
   int npinned = 0;
   int64_t* mrp = nullptr;  // monolithic row pointers (export)
@@ -117,15 +145,28 @@ struct fs_problem {
   float *valA32 = nullptr, *B32 = nullptr, *BT32 = nullptr, *diagp32 = nullptr;
   Precision<double> p64;
   Precision<float> p32;
-  bool has64 = false, has32 = false;
+  bool has32 = false;
+  // work-list of the n_dof vectors and per-segment status mirrors
+  Tile* tiles = nullptr;
+  int ntiles = 0;
+  SegHost* host_status = nullptr;  // pinned, nseg entries
+  int* host_retired = nullptr;     // pinned, nseg entries
+  cudaEvent_t ev = nullptr;
+  SolveCtx ctx;
+  std::vector<fs_solve_stats> last_stats;  // per instance, last solve
   double t = 0;
   bool assembled = false;
 
+  TileList tl() const { return TileList{tiles, ntiles}; }
+
+  // Device memory is stream-ordered (cudaMallocAsync on the problem's
+  // stream): creating or destroying a problem does not synchronise the
+  // device while other problems run.
   template <typename T>
   int alloc(T** p, int64_t count) {
     size_t bytes_ = sizeof(T) * (size_t)std::max<int64_t>(count, 1);
     void* q = nullptr;
-    cudaError_t e = cudaMalloc(&q, bytes_);
+    cudaError_t e = cudaMallocAsync(&q, bytes_, stream);
     if (e != cudaSuccess) {
       set_error(std::string("cudaMalloc of ") + std::to_string(bytes_) + " bytes: " +
                 cudaGetErrorString(e));
@@ -139,13 +180,19 @@ struct fs_problem {
   template <typename T>
   int upload(T** p, const std::vector<T>& h) {
     FS_TRY(alloc(p, (int64_t)h.size()));
-    if (!h.empty()) FS_CUDA(cudaMemcpy(*p, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice));
+    if (!h.empty())
+      FS_CUDA(cudaMemcpyAsync(*p, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice, stream));
     return FS_OK;
   }
   ~fs_problem() {
+    if (stream) cudaStreamSynchronize(stream);
     for (auto* k : {&p64.kr.g_check, &p64.kr.g_iter, &p32.kr.g_check, &p32.kr.g_iter})
       if (*k) cudaGraphExecDestroy(*k);
-    for (void* q : allocs) cudaFree(q);
+    for (void* q : allocs) cudaFreeAsync(q, stream);
+    if (stream) cudaStreamSynchronize(stream);
+    if (host_status) cudaFreeHost(host_status);
+    if (host_retired) cudaFreeHost(host_retired);
+    if (ev) cudaEventDestroy(ev);
     if (own_stream && stream) cudaStreamDestroy(stream);
   }
 };
@@ -162,7 +209,7 @@ int check_launch(const char* what) {
 }
 
 template <typename T>
-int upload_csr(fs_problem* P, const HostCsr& H, DCsr<T>& d, const int32_t** rp_keep = nullptr) {
+int upload_csr(fs_problem* P, const HostCsr& H, DCsr<T>& d) {
   int32_t *rp, *ci;
   T* v;
   FS_TRY(P->upload(&rp, H.rowptr));
@@ -173,7 +220,6 @@ int upload_csr(fs_problem* P, const HostCsr& H, DCsr<T>& d, const int32_t** rp_k
   d.rp = rp;
   d.ci = ci;
   d.v = v;
-  if (rp_keep) *rp_keep = rp;
   return FS_OK;
 }
 
@@ -194,7 +240,8 @@ void cheb_coeffs(double lmax, DLevel<T>& L) {
 }
 
 template <typename T>
-int upload_hierarchy(fs_problem* P, const HostHierarchy& H, int nc, DHier<T>& D) {
+int upload_hierarchy(fs_problem* P, const UnionHierarchy& U, int nc, DHier<T>& D) {
+  const HostHierarchy& H = U.H;
   D.nlev = (int)H.levels.size();
   if (D.nlev > 16) {
     set_error("multigrid hierarchy deeper than 16 levels");
@@ -222,16 +269,65 @@ int upload_hierarchy(fs_problem* P, const HostHierarchy& H, int nc, DHier<T>& D)
     FS_TRY(P->alloc(&D.dw2[l], len));
     FS_TRY(P->alloc(&D.bw[l], len));
   }
-  std::vector<T> ci(H.coarse_inv.begin(), H.coarse_inv.end());
+  std::vector<T> ci(U.dense.begin(), U.dense.end());
   T* cinv;
   FS_TRY(P->upload(&cinv, ci));
   D.cinv = cinv;
+  int32_t* rb;
+  int64_t *br, *bn, *bd;
+  FS_TRY(P->upload(&rb, U.row_blk));
+  FS_TRY(P->upload(&br, U.blk_row));
+  FS_TRY(P->upload(&bn, U.blk_n));
+  FS_TRY(P->upload(&bd, U.blk_dense));
+  D.row_blk = rb;
+  D.blk_row = br;
+  D.blk_n = bn;
+  D.blk_dense = bd;
   D.ncoarse = H.ncoarse;
+  if (!U.perm.empty()) {
+    int32_t* pm;
+    FS_TRY(P->upload(&pm, U.perm));
+    D.perm = pm;
+    FS_TRY(P->alloc(&D.pin, (int64_t)nc * H.levels[0].A.nrow));
+    FS_TRY(P->alloc(&D.pout, (int64_t)nc * H.levels[0].A.nrow));
+  }
   return FS_OK;
 }
 
+// Work-list over the n_dof entries: for every instance its vertex and edge
+// ranges in each component block and its pressure range, cut into tiles of
+// at most kTileLen entries; tiles of one instance are consecutive.
+void build_tiles(const fs_problem* P, std::vector<Tile>& tiles, std::vector<int>& first,
+                 std::vector<int>& count) {
+  const Mesh& me = P->mesh->m;
+  const int d = P->dim;
+  tiles.clear();
+  first.assign(P->nseg, 0);
+  count.assign(P->nseg, 0);
+  auto add = [&](int64_t start, int64_t len, int seg) {
+    for (int64_t o = 0; o < len; o += kTileLen) {
+      Tile t;
+      t.start = start + o;
+      t.len = (int32_t)std::min<int64_t>(kTileLen, len - o);
+      t.seg = seg;
+      tiles.push_back(t);
+    }
+  };
+  for (int s = 0; s < P->nseg; ++s) {
+    const Instance& I = me.inst[s];
+    first[s] = (int)tiles.size();
+    for (int c = 0; c < d; ++c) {
+      add(c * me.n2 + I.voff, I.nv, s);
+      add(c * me.n2 + me.nv + I.eoff, I.ne, s);
+    }
+    add((int64_t)d * me.n2 + I.voff, I.nv, s);
+    count[s] = (int)tiles.size() - first[s];
+  }
+}
+
 template <typename V>
-int alloc_krylov(fs_problem* P, Krylov<V>& K, int m) {
+int alloc_krylov(fs_problem* P, Krylov<V>& K, int m, const std::vector<int>& first,
+                 const std::vector<int>& count) {
   K.m = m;
   K.n = P->ndof;
   FS_TRY(P->alloc(&K.Vb, (int64_t)(m + 1) * K.n));
@@ -240,46 +336,56 @@ int alloc_krylov(fs_problem* P, Krylov<V>& K, int m) {
   FS_TRY(P->alloc(&K.work_u, (int64_t)P->dim * P->n2));
   FS_TRY(P->alloc(&K.rhs, K.n));
   FS_TRY(P->alloc(&K.sol, K.n));
-  // partial sums: (restart + 1) vectors x at most 4 x 152 blocks (CGS2
-  // passes) or one block per 4096 entries (norms)
-  int64_t nblk = std::max<int64_t>((K.n + 4095) / 4096 + 1, 4 * 152);
-  FS_TRY(P->alloc(&K.partial, (int64_t)(kMaxRestart + 1) * nblk));
-  FS_TRY(P->alloc(&K.st, 1));
-  FS_CUDA(cudaMemset(K.st, 0, sizeof(GmresState)));
+  FS_TRY(P->alloc(&K.partial, (int64_t)(kMaxRestart + 1) * P->ntiles));
+  FS_TRY(P->alloc(&K.st, P->nseg));
+  FS_TRY(P->alloc(&K.ctl, 1));
+  FS_CUDA(cudaMemsetAsync(K.st, 0, sizeof(SegState) * P->nseg, P->stream));
+  std::vector<SegHost> init(P->nseg);
+  std::memset(init.data(), 0, sizeof(SegHost) * init.size());
+  for (int s = 0; s < P->nseg; ++s) {
+    init[s].first_tile = first[s];
+    init[s].ntiles = count[s];
+  }
+  FS_CUDA(cudaMemcpy2DAsync(K.st, sizeof(SegState), init.data(), sizeof(SegHost),
+                            sizeof(SegHost), P->nseg, cudaMemcpyHostToDevice, P->stream));
+  KCtl c{m, P->nseg, 0, 0};
+  FS_CUDA(cudaMemcpyAsync(K.ctl, &c, sizeof(KCtl), cudaMemcpyHostToDevice, P->stream));
+  FS_CUDA(cudaStreamSynchronize(P->stream));  // host sources go out of scope
   return FS_OK;
 }
 
 // Pressure vertices whose Poisson rows are fixed in the preconditioner: the
 // pinned vertex when the whole boundary is Dirichlet, else the vertices on
-// the sides with a natural (do-nothing) velocity condition.
-std::vector<int32_t> poisson_fixed(const Mesh& m, bool pin) {
+// the sides with a natural (do-nothing) velocity condition.  Local ids.
+std::vector<int32_t> poisson_fixed(const fs_mesh_desc& d, bool pin) {
   std::vector<int32_t> out;
-  const int dim = m.dim;
+  const int dim = d.dim;
   const int all = dim == 2 ? 0x0F : 0x3F;
-  int natural = all & ~m.desc.dirichlet_sides;
+  int natural = all & ~d.dirichlet_sides;
   if (natural == 0) {
     if (pin) out.push_back(0);
     return out;
   }
-  const int* n = m.desc.n;
+  const int* n = d.n;
   int64_t sx = n[0] + 1, sy = n[1] + 1;
-  for (int64_t v = 0; v < m.nv; ++v) {
+  int64_t nv = sx * sy * (dim == 3 ? (n[2] + 1) : 1);
+  for (int64_t v = 0; v < nv; ++v) {
     int64_t ijk[3] = {v % sx, (v / sx) % sy, dim == 3 ? v / (sx * sy) : 0};
     int bits = 0;
     for (int a = 0; a < dim; ++a) {
       if (ijk[a] == 0) bits |= 1 << (2 * a);
       if (ijk[a] == n[a]) bits |= 1 << (2 * a + 1);
     }
-    // vertices on a natural side that are not on a Dirichlet side
-    if ((bits & natural) && !(bits & m.desc.dirichlet_sides)) out.push_back((int32_t)v);
+    if ((bits & natural) && !(bits & d.dirichlet_sides)) out.push_back((int32_t)v);
   }
   return out;
 }
 
 template <typename T>
-int setup_precision(fs_problem* P, Precision<T>& pr, const HostHierarchy& HA,
-                    const HostHierarchy& HK, const std::vector<double>& mpl_h,
-                    const T* valA, const T* B, const T* BT, const T* diagp, int m) {
+int setup_precision(fs_problem* P, Precision<T>& pr, const UnionHierarchy& HA,
+                    const UnionHierarchy& HK, const std::vector<double>& mplinv_nu,
+                    const T* valA, const T* B, const T* BT, const T* diagp, int m,
+                    const std::vector<int>& first, const std::vector<int>& count) {
   const Mesh& me = P->mesh->m;
   pr.op.dim = P->dim;
   pr.op.n2 = P->n2;
@@ -292,34 +398,34 @@ int setup_precision(fs_problem* P, Precision<T>& pr, const HostHierarchy& HA,
   pr.lanes = avg >= 24.0 ? 8 : 4;
   FS_TRY(upload_hierarchy<T>(P, HA, P->dim, pr.HA));
   FS_TRY(upload_hierarchy<T>(P, HK, 1, pr.HK));
-  std::vector<T> mi(P->nv);
-  for (int64_t q = 0; q < P->nv; ++q) mi[q] = (T)(P->desc.nu / mpl_h[q]);
+  std::vector<T> mi(mplinv_nu.begin(), mplinv_nu.end());
   FS_TRY(P->upload(&pr.mplinv_nu, mi));
-  FS_TRY(alloc_krylov<T>(P, pr.kr, m));
+  FS_TRY(alloc_krylov<T>(P, pr.kr, m, first, count));
   return FS_OK;
 }
 
 // ---------------------------------------------------------------------------
-// Flexible GMRES(m), right preconditioned, restart cycles split in a "check"
-// part (true residual, norm, cycle init) and an "iteration" part (m Arnoldi
-// steps with CGS2, Givens rotations on the device, update of x).
+// Device parts of a solve (enqueued on the problem's stream)
 // ---------------------------------------------------------------------------
 template <typename T>
 void issue_check(fs_problem* P, Precision<T>& pr, const T* x, const T* b) {
   Krylov<T>& K = pr.kr;
   cudaStream_t s = P->stream;
   launch_spmv_full<T, T>(pr.op, x, b, K.Vb, 1, nullptr, pr.lanes, s);
-  launch_norm2<T>(K.Vb, K.n, K.partial, &K.st->counter[0], &K.st->beta, 0, nullptr, s);
-  launch_cycle_init(K.st, s);
+  launch_seg_norm<T>(K.Vb, P->tl(), K.st, K.partial, 0, s);
 }
 
+// One restart cycle: init (tolerances relative to ||b|| or to beta), v0,
+// m Arnoldi steps, update of x.
 template <typename T>
-void issue_iter(fs_problem* P, Precision<T>& pr, T* x) {
+void issue_iter(fs_problem* P, Precision<T>& pr, T* x, double rtol, int relative_to_beta) {
   Krylov<T>& K = pr.kr;
   cudaStream_t s = P->stream;
-  const int* skip = &K.st->done;
+  const int* skip = &K.ctl->all_done;
   const int64_t n = K.n;
-  launch_scale<T>(K.Vb, n, nullptr, &K.st->beta, 0, skip, s);
+  const TileList tl = P->tl();
+  launch_seg_cycle_init(K.st, K.ctl, rtol, relative_to_beta, s);
+  launch_seg_scale<T>(K.Vb, tl, K.st, 0, s);
   for (int j = 0; j < K.m; ++j) {
     T* vj = K.Vb + (int64_t)j * n;
     T* zj = K.Z + (int64_t)j * n;
@@ -327,37 +433,35 @@ void issue_iter(fs_problem* P, Precision<T>& pr, T* x) {
     launch_precond<T>(pr.op, pr.HA, pr.HK, pr.mplinv_nu, 1.0 / P->desc.dt, P->pinned,
                       P->npinned, vj, zj, K.work_p, K.work_u, skip, s);
     launch_spmv_full<T, T>(pr.op, zj, nullptr, w, 0, skip, pr.lanes, s);
-    launch_cgs2<T>(K.Vb, n, j, K.st, K.partial, skip, s);
-    launch_scale<T>(w, n, nullptr, &K.st->hn, 0, skip, s);
-    launch_givens(K.st, j, s);
+    launch_seg_cgs2<T>(K.Vb, n, j, tl, K.st, K.ctl, K.partial, s);
+    launch_seg_scale<T>(w, tl, K.st, 1, s);
+    launch_seg_givens(K.st, K.ctl, P->nseg, j, s);
   }
-  launch_update_x<T, T>(K.st, K.Z, n, x, 1.0, s);
+  launch_seg_update_x<T, T>(K.st, K.ctl, K.Z, n, tl, x, s);
 }
 
+// Runs `issue` directly or as a cached CUDA graph (keyed by x and b).
 template <typename T>
-int run_part(fs_problem* P, Precision<T>& pr, bool check, const T* x, const T* b,
-             bool use_graph) {
-  Krylov<T>& K = pr.kr;
-  cudaGraphExec_t* g = check ? &K.g_check : &K.g_iter;
-  if (use_graph && (K.g_x != (const void*)x || K.g_b != (const void*)b)) {
+int run_graph(fs_problem* P, Krylov<T>& K, bool check, const void* x, const void* b,
+              bool use_graph, const std::function<void()>& issue) {
+  if (!use_graph) {
+    issue();
+    return check_launch("gmres cycle");
+  }
+  if (K.g_x != x || K.g_b != b) {
     if (K.g_check) cudaGraphExecDestroy(K.g_check);
     if (K.g_iter) cudaGraphExecDestroy(K.g_iter);
     K.g_check = K.g_iter = nullptr;
     K.g_x = x;
     K.g_b = b;
   }
-  if (!use_graph) {
-    if (check) issue_check<T>(P, pr, x, b);
-    else issue_iter<T>(P, pr, const_cast<T*>(x));
-    return check_launch("gmres cycle");
-  }
+  cudaGraphExec_t* g = check ? &K.g_check : &K.g_iter;
   size_t* nodes = check ? &K.n_check : &K.n_iter;
   if (!*g) {
     cudaGraph_t graph;
     FS_CUDA(cudaStreamBeginCapture(P->stream, cudaStreamCaptureModeThreadLocal));
     g_capturing = true;
-    if (check) issue_check<T>(P, pr, x, b);
-    else issue_iter<T>(P, pr, const_cast<T*>(x));
+    issue();
     g_capturing = false;
     FS_CUDA(cudaStreamEndCapture(P->stream, &graph));
     cudaGraphGetNodes(graph, nullptr, nodes);
@@ -373,143 +477,21 @@ int run_part(fs_problem* P, Precision<T>& pr, bool check, const T* x, const T* b
   return FS_OK;
 }
 
-struct CycleInfo {
-  double beta, resid;
-  int done, k, bad;
-};
-
+// Status read-back (64 bytes per segment) and the completion event.
 template <typename T>
-int read_state(fs_problem* P, Precision<T>& pr, CycleInfo& ci) {
-  GmresState* st = pr.kr.st;
-  FS_CUDA(cudaMemcpyAsync(&ci.beta, &st->beta, sizeof(double), cudaMemcpyDeviceToHost, P->stream));
-  FS_CUDA(cudaMemcpyAsync(&ci.resid, &st->resid, sizeof(double), cudaMemcpyDeviceToHost, P->stream));
-  FS_CUDA(cudaMemcpyAsync(&ci.done, &st->done, sizeof(int), cudaMemcpyDeviceToHost, P->stream));
-  FS_CUDA(cudaMemcpyAsync(&ci.k, &st->k, sizeof(int), cudaMemcpyDeviceToHost, P->stream));
-  FS_CUDA(cudaMemcpyAsync(&ci.bad, &st->bad, sizeof(int), cudaMemcpyDeviceToHost, P->stream));
-  FS_CUDA(cudaStreamSynchronize(P->stream));
+int enqueue_status(fs_problem* P, Krylov<T>& K) {
+  FS_CUDA(cudaMemcpy2DAsync(P->host_status, sizeof(SegHost), K.st, sizeof(SegState),
+                            sizeof(SegHost), P->nseg, cudaMemcpyDeviceToHost, P->stream));
+  FS_CUDA(cudaEventRecord(P->ev, P->stream));
   return FS_OK;
 }
 
-// Solves K x = b to ||b - K x|| <= tol_abs (true residual, in the arithmetic
-// of T).  iters is incremented; returns FS_OK / NOT_CONVERGED / NUMERIC.
-// single_cycle: run one restart cycle whose Arnoldi estimate stops at
-// tol_abs and return (the inner solve of the refinement, whose own true
-// residual cannot be trusted below the FP32 rounding floor).
 template <typename T>
-int gmres(fs_problem* P, Precision<T>& pr, T* x, const T* b, double tol_abs, int max_iter,
-          bool use_graph, int& iters, int& cycles, double& final_res,
-          bool single_cycle = false) {
-  Krylov<T>& K = pr.kr;
-  double tol = tol_abs;
-  FS_CUDA(cudaMemcpyAsync(&K.st->tol_abs, &tol, sizeof(double), cudaMemcpyHostToDevice, P->stream));
-  int m = K.m;
-  FS_CUDA(cudaMemcpyAsync(&K.st->m, &m, sizeof(int), cudaMemcpyHostToDevice, P->stream));
-  int start_iters = iters;
-  double prev = INFINITY;
-  while (true) {
-    FS_TRY(run_part<T>(P, pr, true, x, b, use_graph));
-    CycleInfo ci;
-    FS_TRY(read_state<T>(P, pr, ci));
-    final_res = ci.beta;
-    if (ci.bad) {
-      set_error("non-finite residual in GMRES");
-      return FS_ERR_NUMERIC;
-    }
-    if (ci.beta <= tol_abs) return FS_OK;
-    if (iters - start_iters >= max_iter) {
-      set_error("GMRES reached max_iter with residual " + std::to_string(ci.beta));
-      return FS_ERR_NOT_CONVERGED;
-    }
-    // a whole restart cycle that did not reduce the true residual by 10%
-    // means the rounding floor of the arithmetic has been reached: accept it
-    // within 100 tol_abs, else report non-convergence
-    if (!single_cycle && ci.beta > 0.9 * prev) {
-      if (ci.beta <= 100.0 * tol_abs) return FS_OK;
-      set_error("GMRES stagnated at true residual " + std::to_string(ci.beta));
-      return FS_ERR_NOT_CONVERGED;
-    }
-    prev = ci.beta;
-    FS_TRY(run_part<T>(P, pr, false, x, b, use_graph));
-    FS_TRY(read_state<T>(P, pr, ci));
-    iters += ci.k;
-    cycles += 1;
-    if (ci.bad) {
-      set_error("non-finite value in the Arnoldi process");
-      return FS_ERR_NUMERIC;
-    }
-    if (single_cycle) return FS_OK;
-    if (ci.k == 0) {
-      set_error("GMRES stagnated (no Arnoldi step possible)");
-      return FS_ERR_NOT_CONVERGED;
-    }
-  }
-}
-
-int solve_impl(fs_problem* P, const fs_solve_opts& o, double* x, fs_solve_stats& st) {
-  st = fs_solve_stats{};
-  double bn = 0;
-  launch_norm2<double>(P->b, P->ndof, P->partial64, &P->counters[0], &P->scal[0], 0, nullptr,
-                       P->stream);
-  FS_CUDA(cudaMemcpyAsync(&bn, &P->scal[0], sizeof(double), cudaMemcpyDeviceToHost, P->stream));
-  FS_CUDA(cudaStreamSynchronize(P->stream));
-  if (bn == 0) bn = 1;
-  const double tol_abs = o.rtol * bn;
-  int rc = FS_OK;
-  if (P->desc.precision == FS_PREC_FP64) {
-    double res = 0;
-    rc = gmres<double>(P, P->p64, x, P->b, tol_abs, o.max_iter, o.use_graph != 0, st.iters,
-                       st.cycles, res);
-    st.rel_res = res / bn;
-  } else {
-    // FP64 iterative refinement around an FP32 inner FGMRES
-    rc = FS_ERR_NOT_CONVERGED;
-    Precision<float>& pr = P->p32;
-    double prev_rn = INFINITY;
-    for (int it = 0; it <= o.max_refine; ++it) {
-      launch_spmv_full<double, double>(P->p64.op, x, P->b, P->r64, 1, nullptr, P->p64.lanes,
-                                       P->stream);
-      launch_norm2<double>(P->r64, P->ndof, P->partial64, &P->counters[1], &P->scal[1], 0,
-                           nullptr, P->stream);
-      double rn = 0;
-      FS_CUDA(cudaMemcpyAsync(&rn, &P->scal[1], sizeof(double), cudaMemcpyDeviceToHost,
-                              P->stream));
-      FS_CUDA(cudaStreamSynchronize(P->stream));
-      st.rel_res = rn / bn;
-      if (!std::isfinite(rn)) {
-        set_error("non-finite FP64 residual");
-        rc = FS_ERR_NUMERIC;
-        break;
-      }
-      if (rn <= tol_abs) {
-        rc = FS_OK;
-        break;
-      }
-      // refinement no longer contracting: the FP64 rounding floor
-      if (rn > 0.5 * prev_rn && rn <= 100.0 * tol_abs) {
-        rc = FS_OK;
-        break;
-      }
-      prev_rn = rn;
-      if (it == o.max_refine || st.iters >= o.max_iter) {
-        set_error("refinement did not reach rtol: " + std::to_string(rn / bn));
-        break;
-      }
-      st.refinements += 1;
-      launch_convert<double, float>(P->r64, pr.kr.rhs, P->ndof, &P->scal[1], 1, P->stream);
-      FS_CUDA(cudaMemsetAsync(pr.kr.sol, 0, sizeof(float) * P->ndof, P->stream));
-      double ires = 0;
-      int irc = gmres<float>(P, pr, pr.kr.sol, pr.kr.rhs, o.inner_rtol, o.max_iter - st.iters,
-                             o.use_graph != 0, st.iters, st.cycles, ires, true);
-      if (irc == FS_ERR_NUMERIC) {
-        rc = irc;
-        break;
-      }
-      launch_axpy_mixed<float, double>(x, pr.kr.sol, P->ndof, &P->scal[1], P->stream);
-      FS_TRY(check_launch("refinement update"));
-    }
-  }
-  st.status = rc;
-  return rc;
+int push_retired(fs_problem* P, Krylov<T>& K) {
+  for (int s = 0; s < P->nseg; ++s) P->host_retired[s] = P->ctx.retired[s];
+  FS_CUDA(cudaMemcpy2DAsync(&K.st[0].retired, sizeof(SegState), P->host_retired, sizeof(int),
+                            sizeof(int), P->nseg, cudaMemcpyHostToDevice, P->stream));
+  return FS_OK;
 }
 
 int assemble_impl(fs_problem* P, double t_next) {
@@ -522,10 +504,211 @@ int assemble_impl(fs_problem* P, double t_next) {
                        P->valA, s);
   launch_bc_rows<double>(P->dm, P->valA, s);
   launch_eval_load(P->dm, P->ph, t_next, 1.0 / P->desc.dt, P->x, P->F, s);
-  launch_rhs(P->dm, P->ph, t_next, P->Mv, P->F, P->desc.pin_pressure, P->b, s);
+  launch_rhs(P->dm, P->ph, t_next, P->Mv, P->F, P->pinned, P->npinned, P->b, s);
   if (P->has32) launch_convert<double, float>(P->valA, P->valA32, nnzA, nullptr, 0, s);
   FS_TRY(check_launch("assembly"));
   P->assembled = true;
+  return FS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// The solve state machine.  start_solve enqueues the first device part;
+// advance() runs once that part's event has completed: it reads the
+// per-segment status and enqueues the next part (or finishes).
+// ---------------------------------------------------------------------------
+int start_solve(fs_problem* P, double* x) {
+  SolveCtx& c = P->ctx;
+  const int S = P->nseg;
+  c.x = x;
+  c.status.assign(S, FS_OK);
+  c.iters.assign(S, 0);
+  c.cycles.assign(S, 0);
+  c.refines.assign(S, 0);
+  c.relres.assign(S, 0.0);
+  c.prev.assign(S, INFINITY);
+  c.retired.assign(S, 0);
+  cudaStream_t s = P->stream;
+  if (P->desc.precision == FS_PREC_FP64) {
+    Krylov<double>& K = P->p64.kr;
+    FS_TRY(push_retired(P, K));
+    launch_seg_norm<double>(P->b, P->tl(), K.st, K.partial, 1, s);
+    FS_TRY(run_graph<double>(P, K, true, x, P->b, c.o.use_graph != 0,
+                             [&]() { issue_check<double>(P, P->p64, x, P->b); }));
+    FS_TRY(enqueue_status(P, K));
+    c.phase = PH_CHECK;
+  } else {
+    Krylov<float>& K = P->p32.kr;
+    FS_TRY(push_retired(P, K));
+    launch_seg_norm<double>(P->b, P->tl(), K.st, K.partial, 1, s);
+    launch_spmv_full<double, double>(P->p64.op, x, P->b, P->r64, 1, nullptr, P->p64.lanes, s);
+    launch_seg_norm<double>(P->r64, P->tl(), K.st, K.partial, 2, s);
+    FS_TRY(enqueue_status(P, K));
+    c.phase = PH_RES64;
+  }
+  return check_launch("solve start");
+}
+
+void finish_solve(fs_problem* P) {
+  SolveCtx& c = P->ctx;
+  P->last_stats.assign(P->nseg, fs_solve_stats{});
+  for (int s = 0; s < P->nseg; ++s) {
+    fs_solve_stats& st = P->last_stats[s];
+    st.iters = c.iters[s];
+    st.refinements = c.refines[s];
+    st.cycles = c.cycles[s];
+    st.status = c.status[s];
+    st.rel_res = c.relres[s];
+  }
+  c.rc = FS_OK;
+  for (int s = 0; s < P->nseg; ++s)
+    if (c.status[s] != FS_OK && c.rc == FS_OK) c.rc = c.status[s];
+  if (c.rc != FS_OK) set_error("the solve did not reach rtol in every instance");
+  c.phase = PH_DONE;
+}
+
+fs_solve_stats aggregate_stats(const fs_problem* P) {
+  fs_solve_stats a{};
+  for (const auto& st : P->last_stats) {
+    a.iters = std::max(a.iters, st.iters);
+    a.refinements = std::max(a.refinements, st.refinements);
+    a.cycles = std::max(a.cycles, st.cycles);
+    a.rel_res = std::max(a.rel_res, st.rel_res);
+    if (a.status == FS_OK) a.status = st.status;
+  }
+  return a;
+}
+
+// Per segment, after its true residual r (beta, or rnorm in the refinement)
+// is known: converged, stagnated at the rounding floor (accepted within
+// 100 rtol), out of budget, or continue.  Returns true when every segment
+// is retired.
+bool judge(fs_problem* P, bool refinement) {
+  SolveCtx& c = P->ctx;
+  const double rtol = c.o.rtol;
+  bool all = true;
+  for (int s = 0; s < P->nseg; ++s) {
+    if (c.retired[s]) continue;
+    const SegHost& h = P->host_status[s];
+    const double bn = h.bnorm > 0 ? h.bnorm : 1.0;
+    const double r = refinement ? h.rnorm : h.beta;
+    c.relres[s] = r / bn;
+    if (!std::isfinite(r)) {
+      c.status[s] = FS_ERR_NUMERIC;
+      c.retired[s] = 1;
+    } else if (r <= rtol * bn) {
+      c.retired[s] = 1;
+    } else if (r > (refinement ? 0.5 : 0.9) * c.prev[s]) {
+      c.retired[s] = 1;
+      if (r > 100.0 * rtol * bn) c.status[s] = FS_ERR_NOT_CONVERGED;
+    } else if (c.iters[s] >= c.o.max_iter || (refinement && c.refines[s] >= c.o.max_refine)) {
+      c.retired[s] = 1;
+      c.status[s] = FS_ERR_NOT_CONVERGED;
+    }
+    c.prev[s] = r;
+    if (!c.retired[s]) all = false;
+  }
+  return all;
+}
+
+int advance(fs_problem* P) {
+  SolveCtx& c = P->ctx;
+  cudaStream_t s = P->stream;
+  const bool graph = c.o.use_graph != 0;
+  switch (c.phase) {
+    case PH_CHECK: {  // FP64: true residual known
+      if (judge(P, false)) {
+        finish_solve(P);
+        return FS_OK;
+      }
+      Krylov<double>& K = P->p64.kr;
+      FS_TRY(push_retired(P, K));
+      FS_TRY(run_graph<double>(P, K, false, c.x, P->b, graph,
+                               [&]() { issue_iter<double>(P, P->p64, c.x, c.o.rtol, 0); }));
+      FS_TRY(enqueue_status(P, K));
+      c.phase = PH_ITER;
+      return FS_OK;
+    }
+    case PH_ITER: {
+      for (int q = 0; q < P->nseg; ++q) {
+        if (c.retired[q]) continue;
+        c.iters[q] += P->host_status[q].k;
+        c.cycles[q] += 1;
+        if (P->host_status[q].bad) {
+          c.status[q] = FS_ERR_NUMERIC;
+          c.retired[q] = 1;
+        } else if (P->host_status[q].k == 0) {
+          c.status[q] = FS_ERR_NOT_CONVERGED;
+          c.retired[q] = 1;
+        }
+      }
+      Krylov<double>& K = P->p64.kr;
+      FS_TRY(push_retired(P, K));
+      FS_TRY(run_graph<double>(P, K, true, c.x, P->b, graph,
+                               [&]() { issue_check<double>(P, P->p64, c.x, P->b); }));
+      FS_TRY(enqueue_status(P, K));
+      c.phase = PH_CHECK;
+      return FS_OK;
+    }
+    case PH_RES64: {  // refinement: FP64 residual known
+      if (judge(P, true)) {
+        finish_solve(P);
+        return FS_OK;
+      }
+      Precision<float>& pr = P->p32;
+      Krylov<float>& K = pr.kr;
+      FS_TRY(push_retired(P, K));
+      launch_seg_normalise<double, float>(P->r64, K.rhs, P->tl(), K.st, s);
+      FS_CUDA(cudaMemsetAsync(K.sol, 0, sizeof(float) * P->ndof, s));
+      // one inner cycle whose Arnoldi estimate stops at inner_rtol relative
+      // to its own initial residual
+      FS_TRY(run_graph<float>(P, K, false, K.sol, K.rhs, graph, [&]() {
+        issue_check<float>(P, pr, K.sol, K.rhs);
+        issue_iter<float>(P, pr, K.sol, c.o.inner_rtol, 1);
+      }));
+      launch_seg_axpy<float, double>(c.x, K.sol, P->tl(), K.st, s);
+      launch_spmv_full<double, double>(P->p64.op, c.x, P->b, P->r64, 1, nullptr, P->p64.lanes, s);
+      launch_seg_norm<double>(P->r64, P->tl(), K.st, K.partial, 2, s);
+      FS_TRY(enqueue_status(P, K));
+      for (int q = 0; q < P->nseg; ++q)
+        if (!c.retired[q]) c.refines[q] += 1;
+      c.phase = PH_INNER;
+      return check_launch("refinement");
+    }
+    case PH_INNER: {  // inner cycle finished and FP64 residual recomputed
+      for (int q = 0; q < P->nseg; ++q) {
+        if (c.retired[q]) continue;
+        c.iters[q] += P->host_status[q].k;
+        c.cycles[q] += 1;
+        if (P->host_status[q].bad) {
+          c.status[q] = FS_ERR_NUMERIC;
+          c.retired[q] = 1;
+        }
+      }
+      c.phase = PH_RES64;
+      return advance(P);
+    }
+    default:
+      return FS_OK;
+  }
+}
+
+// Blocking drive of the state machine until the solve is done.
+int run_solve(fs_problem* P, double* x) {
+  FS_TRY(start_solve(P, x));
+  while (P->ctx.phase != PH_DONE) {
+    FS_CUDA(cudaEventSynchronize(P->ev));
+    FS_TRY(advance(P));
+  }
+  return P->ctx.rc;
+}
+
+int solve_opts(const fs_solve_opts* opts, fs_solve_opts& o) {
+  fs_default_solve_opts(&o);
+  if (opts) o = *opts;
+  if (o.restart != 30) {
+    set_error("this build runs GMRES(30) restart cycles (restart must be 30)");
+    return FS_ERR_UNSUPPORTED;
+  }
   return FS_OK;
 }
 
@@ -549,14 +732,18 @@ void fs_default_solve_opts(fs_solve_opts* o) {
 }
 
 int fs_mesh_create(const fs_mesh_desc* desc, fs_mesh** out) {
-  if (!desc || !out) {
-    set_error("fs_mesh_create: null argument");
+  return fs_mesh_create_batch(desc, 1, out);
+}
+
+int fs_mesh_create_batch(const fs_mesh_desc* descs, int count, fs_mesh** out) {
+  if (!descs || !out || count < 1) {
+    set_error("fs_mesh_create: null argument or count < 1");
     return FS_ERR_INVALID_ARG;
   }
   *out = nullptr;
   auto* h = new (std::nothrow) fs_mesh;
   if (!h) return FS_ERR_OOM;
-  int rc = build_mesh(*desc, h->m);
+  int rc = count == 1 ? build_mesh(descs[0], h->m) : build_batch_mesh(descs, count, h->m);
   if (rc != FS_OK) {
     delete h;
     return rc;
@@ -568,6 +755,24 @@ int fs_mesh_create(const fs_mesh_desc* desc, fs_mesh** out) {
 int fs_mesh_destroy(fs_mesh* mesh) {
   delete mesh;
   return FS_OK;
+}
+
+int fs_mesh_instances(const fs_mesh* mesh, int64_t* offsets) {
+  if (!mesh) {
+    set_error("fs_mesh_instances: null mesh");
+    return -FS_ERR_INVALID_ARG;
+  }
+  const Mesh& m = mesh->m;
+  if (offsets)
+    for (size_t i = 0; i < m.inst.size(); ++i) {
+      offsets[6 * i + 0] = m.inst[i].voff;
+      offsets[6 * i + 1] = m.inst[i].nv;
+      offsets[6 * i + 2] = m.nv + m.inst[i].eoff;
+      offsets[6 * i + 3] = m.inst[i].ne;
+      offsets[6 * i + 4] = m.inst[i].coff;
+      offsets[6 * i + 5] = m.inst[i].ncell;
+    }
+  return (int)m.inst.size();
 }
 
 int fs_dof_map(const fs_mesh* mesh, fs_dofmap_info* info, double* coords, int32_t* cell2dof,
@@ -602,19 +807,43 @@ int fs_dof_map(const fs_mesh* mesh, fs_dofmap_info* info, double* coords, int32_
 
 int fs_problem_create(fs_mesh* mesh, const fs_problem_desc* desc, void* stream,
                       fs_problem** out) {
-  if (!mesh || !desc || !out) {
+  if (!mesh || !desc) {
+    set_error("fs_problem_create: null argument");
+    return FS_ERR_INVALID_ARG;
+  }
+  // one description for every instance of the mesh
+  std::vector<fs_problem_desc> d(mesh->m.inst.size(), *desc);
+  return fs_problem_create_batch(mesh, d.data(), (int)d.size(), stream, out);
+}
+
+int fs_problem_create_batch(fs_mesh* mesh, const fs_problem_desc* descs, int count,
+                            void* stream, fs_problem** out) {
+  if (!mesh || !descs || !out) {
     set_error("fs_problem_create: null argument");
     return FS_ERR_INVALID_ARG;
   }
   *out = nullptr;
-  if (!(desc->dt > 0) || !(desc->nu > 0) || desc->problem < 0 || desc->problem > 4 ||
-      (desc->precision != FS_PREC_FP64 && desc->precision != FS_PREC_FP32_REFINE)) {
-    set_error("fs_problem_create: need dt > 0, nu > 0, a known problem and precision");
+  const Mesh& me = mesh->m;
+  if (count != (int)me.inst.size()) {
+    set_error("fs_problem_create_batch: one description per mesh instance is required");
     return FS_ERR_INVALID_ARG;
   }
-  const Mesh& me = mesh->m;
-  if ((desc->problem == FS_PROBLEM_CUBE) != (me.dim == 3) &&
-      desc->problem != FS_PROBLEM_POLY_OSEEN) {
+  const fs_problem_desc& d0 = descs[0];
+  for (int i = 0; i < count; ++i) {
+    const fs_problem_desc& d = descs[i];
+    if (!(d.dt > 0) || !(d.nu > 0) || d.problem < 0 || d.problem > 4 ||
+        (d.precision != FS_PREC_FP64 && d.precision != FS_PREC_FP32_REFINE)) {
+      set_error("fs_problem_create: need dt > 0, nu > 0, a known problem and precision");
+      return FS_ERR_INVALID_ARG;
+    }
+    if (d.problem != d0.problem || d.dt != d0.dt || d.t0 != d0.t0 ||
+        d.precision != d0.precision || d.init != d0.init ||
+        std::memcmp(d.wconst, d0.wconst, sizeof(d.wconst)) != 0) {
+      set_error("fs_problem_create_batch: instances may differ only in nu and pin_pressure");
+      return FS_ERR_INVALID_ARG;
+    }
+  }
+  if ((d0.problem == FS_PROBLEM_CUBE) != (me.dim == 3) && d0.problem != FS_PROBLEM_POLY_OSEEN) {
     set_error("fs_problem_create: problem kind does not match the mesh dimension");
     return FS_ERR_INVALID_ARG;
   }
@@ -625,23 +854,27 @@ int fs_problem_create(fs_mesh* mesh, const fs_problem_desc* desc, void* stream,
   }
   std::unique_ptr<fs_problem> P(new fs_problem);
   P->mesh = mesh;
-  P->desc = *desc;
+  P->desc = d0;
+  P->inst_desc.assign(descs, descs + count);
+  P->nseg = count;
   P->dim = me.dim;
   P->n2 = me.n2;
   P->nv = me.nv;
   P->ndof = me.dim * me.n2 + me.nv;
-  P->t = desc->t0;
+  P->t = d0.t0;
   if (stream) {
     P->stream = (cudaStream_t)stream;
   } else {
     FS_CUDA(cudaStreamCreateWithFlags(&P->stream, cudaStreamNonBlocking));
     P->own_stream = true;
   }
-  if (!g_ref_ready) {
+  FS_CUDA(cudaEventCreateWithFlags(&P->ev, cudaEventDisableTiming));
+  FS_CUDA(cudaMallocHost(&P->host_status, sizeof(SegHost) * count));
+  FS_CUDA(cudaMallocHost(&P->host_retired, sizeof(int) * count));
+  std::call_once(g_ref_once, []() {
     ref_tensors(2, g_ref2);
     ref_tensors(3, g_ref3);
-    g_ref_ready = true;
-  }
+  });
   upload_ref_tensors(g_ref2, g_ref3);
   FS_TRY(check_launch("upload reference tensors"));
 
@@ -673,9 +906,26 @@ int fs_problem_create(fs_mesh* mesh, const fs_problem_desc* desc, void* stream,
     FS_TRY(P->upload(&pbt, me.posBT)); FS_TRY(P->upload(&pk, me.posKp));
     dm.posA = pa; dm.posB = pb; dm.posBT = pbt; dm.posK = pk;
   }
-  P->ph.kind = desc->problem;
-  P->ph.nu = desc->nu;
-  for (int a = 0; a < 3; ++a) P->ph.wconst[a] = desc->wconst[a];
+  P->ph.kind = d0.problem;
+  P->ph.nu = d0.nu;
+  for (int a = 0; a < 3; ++a) P->ph.wconst[a] = d0.wconst[a];
+  bool varnu = false;
+  for (int i = 1; i < count; ++i) varnu = varnu || descs[i].nu != d0.nu;
+  std::vector<double> nu_vert(me.nv, d0.nu);
+  if (varnu) {
+    std::vector<double> nu_cell(me.ncell), nu_node(me.n2);
+    for (int i = 0; i < count; ++i) {
+      const Instance& I = me.inst[i];
+      for (int64_t c = 0; c < I.ncell; ++c) nu_cell[I.coff + c] = descs[i].nu;
+      for (int64_t j = 0; j < I.n2(); ++j) nu_node[union_node(me, i, j)] = descs[i].nu;
+      for (int64_t v = 0; v < I.nv; ++v) nu_vert[I.voff + v] = descs[i].nu;
+    }
+    double *nc, *nn;
+    FS_TRY(P->upload(&nc, nu_cell));
+    FS_TRY(P->upload(&nn, nu_node));
+    dm.nu_cell = nc;
+    P->ph.nu_node = nn;
+  }
 
   // step-invariant blocks
   const int64_t nnzA = me.A.nnz(), nnzB = me.B.nnz(), nnzBT = me.BT.nnz(), nnzK = me.Kp.nnz();
@@ -695,8 +945,7 @@ int fs_problem_create(fs_mesh* mesh, const fs_problem_desc* desc, void* stream,
   FS_CUDA(cudaMemsetAsync(P->BT, 0, sizeof(double) * nnzBT * dim, s));
   FS_CUDA(cudaMemsetAsync(P->Kp, 0, sizeof(double) * nnzK, s));
   FS_CUDA(cudaMemsetAsync(P->mpl, 0, sizeof(double) * P->nv, s));
-  launch_assemble_base(dm, 1.0 / desc->dt, desc->nu, P->baseA, P->Mv, P->B, P->BT, P->Kp,
-                       P->mpl, s);
+  launch_assemble_base(dm, 1.0 / d0.dt, d0.nu, P->baseA, P->Mv, P->B, P->BT, P->Kp, P->mpl, s);
   FS_TRY(check_launch("assemble_base"));
   HostCsr A0 = me.A, Kp = me.Kp;
   A0.val.resize(nnzA);
@@ -709,26 +958,34 @@ int fs_problem_create(fs_mesh* mesh, const fs_problem_desc* desc, void* stream,
   FS_CUDA(cudaMemcpyAsync(mplh.data(), P->mpl, sizeof(double) * P->nv, cudaMemcpyDeviceToHost, s));
   FS_CUDA(cudaStreamSynchronize(s));
   // boundary rows: Dirichlet velocity rows -> identity in A0, zero in BT;
-  // pinned pressure row -> zero B row, unit diagonal
+  // pinned pressure rows -> zero B row, unit diagonal
   for (int32_t i : me.dlist) {
     for (int32_t k = A0.rowptr[i]; k < A0.rowptr[i + 1]; ++k) A0.val[k] = (A0.col[k] == i) ? 1.0 : 0.0;
     for (int32_t k = me.BT.rowptr[i]; k < me.BT.rowptr[i + 1]; ++k)
       for (int c = 0; c < dim; ++c) BTh[(int64_t)k * dim + c] = 0.0;
   }
   std::vector<double> dp(P->nv, 0.0);
-  if (desc->pin_pressure) {
-    for (int32_t k = me.B.rowptr[0]; k < me.B.rowptr[1]; ++k)
-      for (int c = 0; c < dim; ++c) Bh[(int64_t)k * dim + c] = 0.0;
-    dp[0] = 1.0;
-    std::vector<int32_t> pin = {0};
-    FS_TRY(P->upload(&P->pinned, pin));
-    P->npinned = 1;
+  std::vector<int32_t> pin, kfix;
+  for (int i = 0; i < count; ++i) {
+    const Instance& I = me.inst[i];
+    if (descs[i].pin_pressure) pin.push_back((int32_t)I.voff);
+    for (int32_t q : poisson_fixed(I.desc, descs[i].pin_pressure != 0))
+      kfix.push_back((int32_t)(I.voff + q));
   }
-  FS_CUDA(cudaMemcpy(P->B, Bh.data(), sizeof(double) * Bh.size(), cudaMemcpyHostToDevice));
-  FS_CUDA(cudaMemcpy(P->BT, BTh.data(), sizeof(double) * BTh.size(), cudaMemcpyHostToDevice));
-  FS_CUDA(cudaMemcpy(P->diagp, dp.data(), sizeof(double) * P->nv, cudaMemcpyHostToDevice));
+  for (int32_t q : pin) {
+    for (int32_t k = me.B.rowptr[q]; k < me.B.rowptr[q + 1]; ++k)
+      for (int c = 0; c < dim; ++c) Bh[(int64_t)k * dim + c] = 0.0;
+    dp[q] = 1.0;
+  }
+  if (!pin.empty()) {
+    FS_TRY(P->upload(&P->pinned, pin));
+    P->npinned = (int)pin.size();
+  }
+  FS_CUDA(cudaMemcpyAsync(P->B, Bh.data(), sizeof(double) * Bh.size(), cudaMemcpyHostToDevice, s));
+  FS_CUDA(cudaMemcpyAsync(P->BT, BTh.data(), sizeof(double) * BTh.size(), cudaMemcpyHostToDevice,
+                          s));
+  FS_CUDA(cudaMemcpyAsync(P->diagp, dp.data(), sizeof(double) * P->nv, cudaMemcpyHostToDevice, s));
   // pressure Poisson of the preconditioner with its fixed rows
-  std::vector<int32_t> kfix = poisson_fixed(me, desc->pin_pressure != 0);
   {
     std::vector<uint8_t> fixed(P->nv, 0);
     for (int32_t q : kfix) fixed[q] = 1;
@@ -736,28 +993,31 @@ int fs_problem_create(fs_mesh* mesh, const fs_problem_desc* desc, void* stream,
       for (int32_t k = Kp.rowptr[q]; k < Kp.rowptr[q + 1]; ++k)
         if (fixed[q] || fixed[Kp.col[k]]) Kp.val[k] = (Kp.col[k] == q) ? 1.0 : 0.0;
   }
-  HostHierarchy HA, HK;
-  build_hierarchy(me, A0, true, me.dlist, 800, HA);
-  build_hierarchy(me, Kp, false, kfix, 800, HK);
+  std::vector<double> mplinv_nu(P->nv);
+  for (int64_t q = 0; q < P->nv; ++q) mplinv_nu[q] = nu_vert[q] / mplh[q];
+  UnionHierarchy HA, HK;
+  const int64_t cmax = count > 1 ? 400 : 800;
+  build_union_hierarchy(me, {}, A0, true, me.dlist, cmax, HA);
+  build_union_hierarchy(me, {}, Kp, false, kfix, cmax, HK);
 
-  // vectors
+  // vectors, work-list
   FS_TRY(P->alloc(&P->x, P->ndof));
   FS_TRY(P->alloc(&P->b, P->ndof));
   FS_TRY(P->alloc(&P->F, (int64_t)dim * P->n2));
   FS_TRY(P->alloc(&P->r64, P->ndof));
-  FS_TRY(P->alloc(&P->scal, 16));
-  FS_TRY(P->alloc(&P->counters, 16));
-  FS_CUDA(cudaMemset(P->counters, 0, sizeof(unsigned) * 16));
-  FS_TRY(P->alloc(&P->partial64, (P->ndof + 4095) / 4096 + 1));
+  std::vector<Tile> tiles;
+  std::vector<int> first, tcount;
+  build_tiles(P.get(), tiles, first, tcount);
+  FS_TRY(P->upload(&P->tiles, tiles));
+  P->ntiles = (int)tiles.size();
   const int m = 30;
-  // FP64 operator is always present (assembly, residual of the refinement)
   {
-    P->has64 = true;
     auto& pr = P->p64;
-    if (desc->precision == FS_PREC_FP64) {
-      FS_TRY(setup_precision<double>(P.get(), pr, HA, HK, mplh, P->valA, P->B, P->BT,
-                                     P->diagp, m));
+    if (d0.precision == FS_PREC_FP64) {
+      FS_TRY(setup_precision<double>(P.get(), pr, HA, HK, mplinv_nu, P->valA, P->B, P->BT,
+                                     P->diagp, m, first, tcount));
     } else {
+      // FP64 operator only: assembly and the residuals of the refinement
       pr.op.dim = dim;
       pr.op.n2 = P->n2;
       pr.op.nv = P->nv;
@@ -769,7 +1029,7 @@ int fs_problem_create(fs_mesh* mesh, const fs_problem_desc* desc, void* stream,
       pr.lanes = avg >= 24.0 ? 8 : 4;
     }
   }
-  if (desc->precision == FS_PREC_FP32_REFINE) {
+  if (d0.precision == FS_PREC_FP32_REFINE) {
     P->has32 = true;
     FS_TRY(P->alloc(&P->valA32, nnzA));
     std::vector<float> b32(Bh.begin(), Bh.end()), bt32(BTh.begin(), BTh.end()),
@@ -777,10 +1037,10 @@ int fs_problem_create(fs_mesh* mesh, const fs_problem_desc* desc, void* stream,
     FS_TRY(P->upload(&P->B32, b32));
     FS_TRY(P->upload(&P->BT32, bt32));
     FS_TRY(P->upload(&P->diagp32, d32));
-    FS_TRY(setup_precision<float>(P.get(), P->p32, HA, HK, mplh, P->valA32, P->B32, P->BT32,
-                                  P->diagp32, m));
+    FS_TRY(setup_precision<float>(P.get(), P->p32, HA, HK, mplinv_nu, P->valA32, P->B32,
+                                  P->BT32, P->diagp32, m, first, tcount));
   }
-  launch_exact_state(dm, P->ph, desc->t0, desc->init == 1, P->x, s);
+  launch_exact_state(dm, P->ph, d0.t0, d0.init == 1, P->x, s);
   FS_TRY(check_launch("initial state"));
   FS_CUDA(cudaStreamSynchronize(s));
   *out = P.release();
@@ -788,10 +1048,7 @@ int fs_problem_create(fs_mesh* mesh, const fs_problem_desc* desc, void* stream,
 }
 
 int fs_problem_destroy(fs_problem* prob) {
-  if (prob) {
-    cudaStreamSynchronize(prob->stream);
-    delete prob;
-  }
+  delete prob;
   return FS_OK;
 }
 
@@ -828,17 +1085,70 @@ int fs_solve(fs_problem* P, const fs_solve_opts* opts, double* x, fs_solve_stats
     set_error("fs_solve: call fs_assemble_step first");
     return FS_ERR_INVALID_ARG;
   }
-  fs_solve_opts o;
-  fs_default_solve_opts(&o);
-  if (opts) o = *opts;
-  if (o.restart != 30) {
-    set_error("fs_solve: this build runs GMRES(30) restart cycles");
-    return FS_ERR_UNSUPPORTED;
+  if (P->ctx.phase != PH_IDLE && P->ctx.phase != PH_DONE) {
+    set_error("fs_solve: an asynchronous step is in progress");
+    return FS_ERR_BUSY;
   }
-  fs_solve_stats st;
-  int rc = solve_impl(P, o, x ? x : P->x, st);
-  if (stats) *stats = st;
+  FS_TRY(solve_opts(opts, P->ctx.o));
+  int rc = run_solve(P, x ? x : P->x);
+  if (P->ctx.phase == PH_DONE && stats) *stats = aggregate_stats(P);
+  P->ctx.phase = PH_IDLE;
   return rc;
+}
+
+int fs_step_begin(fs_problem* P, int nsteps, const fs_solve_opts* opts) {
+  if (!P || nsteps < 1) {
+    set_error("fs_step_begin: bad argument");
+    return FS_ERR_INVALID_ARG;
+  }
+  if (P->ctx.phase != PH_IDLE && P->ctx.phase != PH_DONE) {
+    set_error("fs_step_begin: a step is already in progress");
+    return FS_ERR_BUSY;
+  }
+  FS_TRY(solve_opts(opts, P->ctx.o));
+  P->ctx.steps_left = nsteps;
+  P->ctx.step_index = 0;
+  P->ctx.per_step = nullptr;
+  FS_TRY(assemble_impl(P, P->t + P->desc.dt));
+  return start_solve(P, P->x);
+}
+
+int fs_step_poll(fs_problem* P, int wait, int* done) {
+  if (!P || !done) {
+    set_error("fs_step_poll: null argument");
+    return FS_ERR_INVALID_ARG;
+  }
+  *done = 0;
+  SolveCtx& c = P->ctx;
+  if (c.phase == PH_IDLE) {
+    *done = 1;
+    return FS_OK;
+  }
+  while (true) {
+    if (c.phase == PH_DONE) {
+      fs_solve_stats st = aggregate_stats(P);
+      if (c.per_step) c.per_step[c.step_index] = st;
+      c.step_index += 1;
+      P->t += P->desc.dt;  // the state holds the best iterate even on failure
+      c.steps_left -= 1;
+      if (c.rc != FS_OK || c.steps_left == 0) {
+        int rc = c.rc;
+        c.phase = PH_IDLE;
+        c.per_step = nullptr;
+        *done = 1;
+        return rc;
+      }
+      FS_TRY(assemble_impl(P, P->t + P->desc.dt));
+      FS_TRY(start_solve(P, P->x));
+    }
+    cudaError_t q = wait ? cudaEventSynchronize(P->ev) : cudaEventQuery(P->ev);
+    if (q == cudaErrorNotReady) return FS_OK;
+    if (q != cudaSuccess) {
+      set_error(std::string("fs_step_poll: ") + cudaGetErrorString(q));
+      return FS_ERR_CUDA;
+    }
+    FS_TRY(advance(P));
+  }
 }
 
 int fs_step(fs_problem* P, int nsteps, const fs_solve_opts* opts, fs_solve_stats* per_step) {
@@ -846,18 +1156,21 @@ int fs_step(fs_problem* P, int nsteps, const fs_solve_opts* opts, fs_solve_stats
     set_error("fs_step: bad argument");
     return FS_ERR_INVALID_ARG;
   }
-  fs_solve_opts o;
-  fs_default_solve_opts(&o);
-  if (opts) o = *opts;
-  for (int k = 0; k < nsteps; ++k) {
-    double t1 = P->t + P->desc.dt;
-    FS_TRY(assemble_impl(P, t1));
-    fs_solve_stats st;
-    int rc = solve_impl(P, o, P->x, st);
-    if (per_step) per_step[k] = st;
-    P->t = t1;  // the state holds the best iterate even when rc != FS_OK
-    if (rc != FS_OK) return rc;
+  if (nsteps == 0) return FS_OK;
+  FS_TRY(fs_step_begin(P, nsteps, opts));
+  P->ctx.per_step = per_step;
+  int done = 0;
+  int rc = FS_OK;
+  while (!done) rc = fs_step_poll(P, 1, &done);
+  return rc;
+}
+
+int fs_instance_stats(const fs_problem* P, fs_solve_stats* per_instance) {
+  if (!P || !per_instance) {
+    set_error("fs_instance_stats: null argument");
+    return FS_ERR_INVALID_ARG;
   }
+  for (size_t i = 0; i < P->last_stats.size(); ++i) per_instance[i] = P->last_stats[i];
   return FS_OK;
 }
 
@@ -912,7 +1225,7 @@ int fs_profile_kernel(fs_problem* P, int kernel, int reps, double* avg_ms, doubl
   double bytes = 0;
   std::function<void()> launch;
   switch (kernel) {
-    case FS_KERNEL_SPMV:      // saddle-point SpMV in the solver's arithmetic
+    case FS_KERNEL_SPMV:  // saddle-point SpMV in the solver's arithmetic
     case FS_KERNEL_SPMV_FP64: {
       const bool use32 = f32 && kernel == FS_KERNEL_SPMV;
       const double sz = use32 ? 4.0 : 8.0;
@@ -934,7 +1247,7 @@ int fs_profile_kernel(fs_problem* P, int kernel, int reps, double* avg_ms, doubl
     }
     case FS_KERNEL_CHEB: {  // one fused Chebyshev step on the finest velocity level
       const int64_t n = P->n2;
-      bytes = nnzA * (4 + s) + 4.0 * (n + 1) + n * s + (1 + 4.0) * d * n * s;
+      bytes = nnzA * (4 + s) + 4.0 * (n + 1) + n * s + 5.0 * d * n * s;
       if (f32) {
         auto& H = P->p32.HA;
         launch = [P, &H, d]() { launch_cheb_step<float>(H, d, P->stream); };

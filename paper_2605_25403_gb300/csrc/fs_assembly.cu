@@ -148,6 +148,7 @@ __global__ void __launch_bounds__(128) k_assemble_base(
     double xv[NB][DIM], gl[NB][DIM];
     load_cell<DIM>(m, e, g, xv);
     double D = bary_grads<DIM>(xv, gl);
+    const double nu_e = m.nu_cell ? m.nu_cell[e] : nu;
     double G[NB][NB];
 #pragma unroll
     for (int r = 0; r < NB; ++r)
@@ -171,7 +172,7 @@ __global__ void __launch_bounds__(128) k_assemble_base(
           for (int s = 0; s < NB; ++s) kk += G[r][s] * R.stiff[i][j][r][s];
         kk *= D;
         int32_t slot = rowbase + pos[j];
-        atomicAdd(base + slot, mass_coef * mm + nu * kk);
+        atomicAdd(base + slot, mass_coef * mm + nu_e * kk);
         atomicAdd(Mv + slot, mm);
       }
     }
@@ -288,9 +289,9 @@ __device__ __forceinline__ void g_ders(double s, double (&g)[4]) {
 }
 
 template <int DIM>
-__device__ Fields eval_fields(const DPhys& ph, const double* x, double t, bool want_f) {
+__device__ Fields eval_fields(const DPhys& ph, double nu, const double* x, double t,
+                              bool want_f) {
   Fields F{};
-  const double nu = ph.nu;
   double X = x[0], Y = x[1];
   switch (ph.kind) {
     case FS_PROBLEM_UNSTEADY_BENCH: {
@@ -412,7 +413,8 @@ __global__ void k_eval_load(DMesh m, DPhys ph, double t, double mass_coef,
     double x[DIM];
 #pragma unroll
     for (int a = 0; a < DIM; ++a) x[a] = m.p2xyz[j * DIM + a];
-    Fields f = eval_fields<DIM>(ph, x, t, true);
+    const double nu = ph.nu_node ? ph.nu_node[j] : ph.nu;
+    Fields f = eval_fields<DIM>(ph, nu, x, t, true);
 #pragma unroll
     for (int c = 0; c < DIM; ++c)
       F[c * m.n2 + j] = (u ? mass_coef * u[c * m.n2 + j] : 0.0) + f.f[c];
@@ -448,7 +450,8 @@ __global__ void k_rhs_vel(DMesh m, DPhys ph, double t, const double* __restrict_
       double x[DIM];
 #pragma unroll
       for (int a = 0; a < DIM; ++a) x[a] = m.p2xyz[i * DIM + a];
-      Fields f = eval_fields<DIM>(ph, x, t, false);
+      const double nu = ph.nu_node ? ph.nu_node[i] : ph.nu;
+      Fields f = eval_fields<DIM>(ph, nu, x, t, false);
 #pragma unroll
       for (int c = 0; c < DIM; ++c) b[c * m.n2 + i] = f.u[c];
     } else {
@@ -458,19 +461,25 @@ __global__ void k_rhs_vel(DMesh m, DPhys ph, double t, const double* __restrict_
   }
 }
 
+// b_p = 0, then the pinned rows hold p_exact at their vertex
 template <int DIM>
-__global__ void k_rhs_p(DMesh m, DPhys ph, double t, int pin, double* __restrict__ b) {
+__global__ void k_rhs_p(DMesh m, DPhys ph, double t, const int32_t* __restrict__ pinned,
+                        int npinned, double* __restrict__ b) {
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < m.nv;
-       q += (int64_t)gridDim.x * blockDim.x) {
-    double v = 0.0;
-    if (pin && q == 0) {
-      double x[DIM];
+       q += (int64_t)gridDim.x * blockDim.x)
+    b[DIM * m.n2 + q] = 0.0;
+}
+template <int DIM>
+__global__ void k_rhs_pin(DMesh m, DPhys ph, double t, const int32_t* __restrict__ pinned,
+                          int npinned, double* __restrict__ b) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= npinned) return;
+  const int64_t q = pinned[k];
+  double x[DIM];
 #pragma unroll
-      for (int a = 0; a < DIM; ++a) x[a] = m.p2xyz[a];
-      v = eval_fields<DIM>(ph, x, t, false).p;
-    }
-    b[DIM * m.n2 + q] = v;
-  }
+  for (int a = 0; a < DIM; ++a) x[a] = m.p2xyz[q * DIM + a];
+  const double nu = ph.nu_node ? ph.nu_node[q] : ph.nu;
+  b[DIM * m.n2 + q] = eval_fields<DIM>(ph, nu, x, t, false).p;
 }
 
 template <int DIM>
@@ -481,7 +490,8 @@ __global__ void k_exact_state(DMesh m, DPhys ph, double t, int zero_interior,
     double xx[DIM];
 #pragma unroll
     for (int a = 0; a < DIM; ++a) xx[a] = m.p2xyz[j * DIM + a];
-    Fields f = eval_fields<DIM>(ph, xx, t, false);
+    const double nu = ph.nu_node ? ph.nu_node[j] : ph.nu;
+    Fields f = eval_fields<DIM>(ph, nu, xx, t, false);
     bool keep = !zero_interior || m.dirichlet[j];
 #pragma unroll
     for (int c = 0; c < DIM; ++c) x[c * m.n2 + j] = keep ? f.u[c] : 0.0;
@@ -566,20 +576,21 @@ void launch_eval_load(const DMesh& m, const DPhys& ph, double t,
 }
 
 void launch_rhs(const DMesh& m, const DPhys& ph, double t, const double* Mv,
-                const double* F, int pin, double* b, cudaStream_t s) {
+                const double* F, const int32_t* pinned, int npinned, double* b,
+                cudaStream_t s) {
   constexpr int L = 4;
   unsigned g = (unsigned)((m.n2 * L + 255) / 256);
+  unsigned gp = (unsigned)((npinned + 127) / 128);
   if (m.dim == 2) {
     k_rhs_vel<2, L><<<g, 256, 0, s>>>(m, ph, t, Mv, F, b);
-    count_launches(1);
-    k_rhs_p<2><<<grid_for(m.nv, 256), 256, 0, s>>>(m, ph, t, pin, b);
-    count_launches(1);
+    k_rhs_p<2><<<grid_for(m.nv, 256), 256, 0, s>>>(m, ph, t, pinned, npinned, b);
+    if (npinned > 0) k_rhs_pin<2><<<gp, 128, 0, s>>>(m, ph, t, pinned, npinned, b);
   } else {
     k_rhs_vel<3, L><<<g, 256, 0, s>>>(m, ph, t, Mv, F, b);
-    count_launches(1);
-    k_rhs_p<3><<<grid_for(m.nv, 256), 256, 0, s>>>(m, ph, t, pin, b);
-    count_launches(1);
+    k_rhs_p<3><<<grid_for(m.nv, 256), 256, 0, s>>>(m, ph, t, pinned, npinned, b);
+    if (npinned > 0) k_rhs_pin<3><<<gp, 128, 0, s>>>(m, ph, t, pinned, npinned, b);
   }
+  count_launches(npinned > 0 ? 3 : 2);
 }
 
 void launch_exact_state(const DMesh& m, const DPhys& ph, double t,

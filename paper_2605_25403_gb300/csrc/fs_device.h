@@ -40,12 +40,14 @@ struct DMesh {
   const int32_t *rpBT = nullptr, *ciBT = nullptr;  // P2-P1
   const int32_t *rpK = nullptr, *ciK = nullptr;    // P1-P1
   const uint8_t *posA = nullptr, *posB = nullptr, *posBT = nullptr, *posK = nullptr;
+  const double* nu_cell = nullptr;     // per-cell viscosity (batches) or null
 };
 
 // Physical description of the manufactured problem.
 struct DPhys {
   int kind = 0;
   double nu = 1.0;
+  const double* nu_node = nullptr;  // per-P2-node viscosity (batches) or null
   double wconst[3] = {0, 0, 0};
 };
 
@@ -69,9 +71,10 @@ void launch_eval_load(const DMesh& m, const DPhys& ph, double t,
                       double mass_coef, const double* u, double* F,
                       cudaStream_t s);
 // b = M F (velocity rows), Dirichlet rows = u_exact(t), b_p = 0 except the
-// pinned row (p_exact(x_0, t)).
+// pinned rows (p_exact at their vertex).
 void launch_rhs(const DMesh& m, const DPhys& ph, double t, const double* Mv,
-                const double* F, int pin, double* b, cudaStream_t s);
+                const double* F, const int32_t* pinned, int npinned, double* b,
+                cudaStream_t s);
 // Exact state I_h u, I_h p at time t (zero_interior: 0 off Dirichlet nodes).
 void launch_exact_state(const DMesh& m, const DPhys& ph, double t,
                         int zero_interior, double* x, cudaStream_t s);
@@ -108,7 +111,12 @@ template <typename T>
 struct DHier {
   int nlev = 0;
   DLevel<T> lev[16];
-  const T* cinv = nullptr;  // dense inverse of the coarsest operator
+  // coarsest level: block-diagonal dense inverses (one block per instance)
+  const T* cinv = nullptr;         // concatenated row-major blocks
+  const int32_t* row_blk = nullptr;  // coarsest row -> block
+  const int64_t* blk_row = nullptr;  // block -> first row
+  const int64_t* blk_n = nullptr;    // block -> size
+  const int64_t* blk_dense = nullptr;  // block -> offset in cinv
   int64_t ncoarse = 0;
   // work vectors per level, nc components each (component stride = nrow):
   // xw/xw2 ping-pong iterates (xw also holds the level's result), dw/dw2
@@ -118,6 +126,11 @@ struct DHier {
   T* dw[16] = {};
   T* dw2[16] = {};
   T* bw[16] = {};
+  // level-0 block order vs the caller's vector order (batches): perm[r] is
+  // the caller's row of block row r; null when they coincide
+  const int32_t* perm = nullptr;
+  T* pin = nullptr;   // permuted right-hand side (nc x rows)
+  T* pout = nullptr;  // permuted result
 };
 // x = V-cycle(b) for nc right-hand sides (stride ld between components);
 // x must not alias b.
@@ -130,49 +143,77 @@ void mg_vcycle(const DHier<T>& H, int nc, const T* b, int64_t ld, T* x,
 template <typename T>
 void launch_cheb_step(const DHier<T>& H, int nc, cudaStream_t s);
 
-// Krylov helpers (fs_linalg.cu).  Results land in device doubles.
-struct GmresState;
-template <typename V>
-void launch_norm2(const V* x, int64_t n, double* partial, unsigned* counter,
-                  double* out, int op, const int* skip, cudaStream_t s);
-template <typename V>
-void launch_scale(V* x, int64_t n, const double* num, const double* den,
-                  int inv_sqrt_den, const int* skip, cudaStream_t s);
-template <typename V>
-void launch_cgs2(V* Vb, int64_t n, int j, GmresState* st, double* partial,
-                 const int* skip, cudaStream_t s);
-void launch_givens(GmresState* st, int j, cudaStream_t s);
-void launch_cycle_init(GmresState* st, cudaStream_t s);
-template <typename V, typename X>
-void launch_update_x(GmresState* st, const V* Z, int64_t n, X* x,
-                     double xscale_from_beta, cudaStream_t s);
+// Conversion out = (B)(in * scale) (scale = *scale or 1/*scale when inv).
 template <typename A, typename B>
 void launch_convert(const A* in, B* out, int64_t n, const double* scale,
                     int inv, cudaStream_t s);
-template <typename V, typename X>
-void launch_axpy_mixed(X* x, const V* d, int64_t n, const double* alpha,
-                       cudaStream_t s);
+
 template <typename T>
 void launch_precond(const DOp<T>& op, const DHier<T>& HA, const DHier<T>& HK,
                     const T* mpl_inv_nu, double inv_dt, const int32_t* pinned,
                     int npinned, const T* r, T* z, T* work_p, T* work_u,
                     const int* skip, cudaStream_t s);
 
-// Device-resident restart-cycle state of flexible GMRES(m).
-struct GmresState {
+// ---- segmented Krylov (fs_krylov.cu) -------------------------------------
+constexpr int kTileLen = 2048;  // vector entries per reduction tile
+
+// A contiguous range [start, start + len) of one segment's entries.
+struct Tile {
+  int64_t start;
+  int32_t len;
+  int32_t seg;
+};
+struct TileList {
+  const Tile* tiles = nullptr;
+  int ntiles = 0;
+};
+
+// Per-segment state of the restart cycle.  The first 64 bytes are the
+// status block the host reads back after every part of a solve.
+struct SegState {
+  double beta;      // ||r0|| of the cycle
+  double resid;     // Arnoldi residual estimate
+  double bnorm;     // ||b|| (FP64 right-hand side of the segment)
+  double rnorm;     // FP64 residual norm (refinement)
+  double tol_abs;   // Arnoldi target of the cycle
+  int done;         // converged / retired / broken: kernels skip the segment
+  int k;            // Arnoldi steps taken in this cycle
+  int bad;          // NaN/Inf seen
+  int retired;      // set by the host: the segment no longer iterates
+  int first_tile, ntiles;
+  double hn;        // ||w|| before normalisation
+  unsigned counter[8];
   double H[(kMaxRestart + 1) * kMaxRestart];
   double cs[kMaxRestart], sn[kMaxRestart], g[kMaxRestart + 1];
-  double y[kMaxRestart];
   double h2[kMaxRestart + 1];
-  double beta;      // ||r0|| of the cycle
-  double tol_abs;   // Arnoldi residual target
-  double resid;     // current residual estimate |g_{k}|
-  double hn;        // ||w|| before normalisation
-  int m;            // restart length
-  int done;         // 1: converged (or breakdown) -> kernels skip
-  int k;            // iterations taken in this cycle
-  int bad;          // NaN/Inf seen
-  unsigned counter[4];
 };
+struct KCtl {
+  int m;         // restart length
+  int nseg;      // number of segments
+  int ndone;     // segments done in this cycle
+  int all_done;  // every segment done: the spanning kernels skip
+};
+
+template <typename V>
+void launch_seg_norm(const V* x, const TileList& tl, SegState* st, double* partial,
+                     int field, cudaStream_t s);
+void launch_seg_cycle_init(SegState* st, KCtl* ctl, double rtol, int relative_to_beta,
+                           cudaStream_t s);
+template <typename V>
+void launch_seg_scale(V* x, const TileList& tl, const SegState* st, int field,
+                      cudaStream_t s);
+template <typename V>
+void launch_seg_cgs2(V* Vb, int64_t n, int j, const TileList& tl, SegState* st,
+                     const KCtl* ctl, double* partial, cudaStream_t s);
+void launch_seg_givens(SegState* st, KCtl* ctl, int nseg, int j, cudaStream_t s);
+template <typename V, typename X>
+void launch_seg_update_x(const SegState* st, const KCtl* ctl, const V* Z, int64_t n,
+                         const TileList& tl, X* x, cudaStream_t s);
+template <typename A, typename B>
+void launch_seg_normalise(const A* in, B* out, const TileList& tl, const SegState* st,
+                          cudaStream_t s);
+template <typename V, typename X>
+void launch_seg_axpy(X* x, const V* d, const TileList& tl, const SegState* st,
+                     cudaStream_t s);
 
 }  // namespace fs

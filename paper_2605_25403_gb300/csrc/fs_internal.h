@@ -25,8 +25,19 @@ struct HostCsr {
   int64_t nnz() const { return (int64_t)col.size(); }
 };
 
-struct Mesh {
+// One structured instance of a (possibly batched) mesh: its description and
+// where its vertices, edge nodes and cells sit in the union numbering.
+struct Instance {
   fs_mesh_desc desc{};
+  int64_t voff = 0, nv = 0;   // vertices [voff, voff + nv)
+  int64_t eoff = 0, ne = 0;   // edge nodes [nv_total + eoff, ... + ne)
+  int64_t coff = 0, ncell = 0;
+  int64_t n2() const { return nv + ne; }
+};
+
+struct Mesh {
+  fs_mesh_desc desc{};              // instance 0 (the only one unless batched)
+  std::vector<Instance> inst;       // >= 1 instance; union = disjoint meshes
   int dim = 0, nloc = 0, nb = 0;    // nb = vertices per simplex
   int64_t nv = 0, ne = 0, n2 = 0, ncell = 0;
   std::vector<double> coords;       // nv x dim
@@ -44,6 +55,14 @@ struct Mesh {
 
 // Builds the mesh tables; returns an fs_status.
 int build_mesh(const fs_mesh_desc& d, Mesh& m);
+// Union of several structured meshes (no shared nodes), numbered as one mesh:
+// all vertices (instance by instance), then all edge nodes, then cells.
+int build_batch_mesh(const fs_mesh_desc* d, int count, Mesh& m);
+// Local P2 node id of instance i -> union node id, and its inverse pieces.
+inline int64_t union_node(const Mesh& m, int i, int64_t local) {
+  const Instance& I = m.inst[i];
+  return local < I.nv ? I.voff + local : m.nv + I.eoff + (local - I.nv);
+}
 
 // Monolithic CSR row pointers / columns from the block patterns.
 void monolithic_pattern(const Mesh& m, std::vector<int64_t>& rowptr,
@@ -83,5 +102,29 @@ struct HostHierarchy {
 void build_hierarchy(const Mesh& m, const HostCsr& A0, bool p2_fine,
                      const std::vector<int32_t>& fixed_rows,
                      int64_t coarse_max, HostHierarchy& H);
+
+// Hierarchy of a batched (union) mesh: one hierarchy per instance (built in
+// parallel), combined level by level into block-diagonal operators.  An
+// instance with fewer levels repeats its coarsest operator with identity
+// transfers down to the common depth; the coarsest level is solved with the
+// block-diagonal of the instances' dense inverses.
+//   A0: union operator (rows = union P2 nodes when p2_fine, else vertices);
+//   fixed: union fine rows whose prolongation rows are zeroed.
+struct UnionHierarchy {
+  HostHierarchy H;                   // block-diagonal levels; coarse_inv unused
+  std::vector<int64_t> blk_row;      // coarsest level: row offset per instance
+  std::vector<int64_t> blk_n;        // ... block size per instance
+  std::vector<int64_t> blk_dense;    // ... offset of its dense inverse
+  std::vector<double> dense;         // concatenated dense inverses (row-major)
+  std::vector<int32_t> row_blk;      // coarsest row -> instance
+  // level-0 rows are in instance-major (block) order; when that differs
+  // from the union numbering (P2 nodes of several instances), perm[r] is
+  // the union row of block row r; empty otherwise
+  std::vector<int32_t> perm;
+};
+void build_union_hierarchy(const Mesh& m, const std::vector<Mesh>& local,
+                           const HostCsr& A0, bool p2_fine,
+                           const std::vector<int32_t>& fixed, int64_t coarse_max,
+                           UnionHierarchy& U);
 
 }  // namespace fs

@@ -1,0 +1,393 @@
+// Segmented reductions and updates of flexible GMRES(m) (paper Sec. 3.2,
+// GMRES) on sm_103a.
+//
+// A problem holds one or more independent instances ("segments": the
+// instances of a batch, or the single mesh of an ordinary problem).  Every
+// segment runs its own Arnoldi process: its own Hessenberg matrix, Givens
+// rotations, convergence flag and update, so a segment's iterates do not
+// depend on the other segments.  Vectors are walked through a work-list of
+// tiles, each a contiguous range of one segment (at most kTileLen entries);
+// one thread block per tile.  Per-tile partial sums go to scratch; the last
+// tile of a segment to finish (per-segment atomic ticket, never waited on)
+// reduces them in FP64.  Kernels that span all segments (SpMV, multigrid)
+// skip their work once every segment has converged (KCtl::all_done).
+#include <cuda_runtime.h>
+
+#include <cmath>
+
+#include "fs_device.h"
+
+namespace fs {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kKB = 256;                 // threads per tile block
+constexpr int kKEPT = kTileLen / kKB;    // elements per thread
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
+  return v;
+}
+
+// Block sum (all threads participate); valid in every thread afterwards.
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double sm[kKB / 32];
+  __shared__ double total;
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) sm[w] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int i = 0; i < kKB / 32; ++i) t += sm[i];
+    total = t;
+  }
+  __syncthreads();
+  return total;
+}
+
+// True in every thread of the last tile block of its segment to arrive.
+__device__ __forceinline__ bool last_of_segment(unsigned* counter, int ntiles) {
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(counter, 1u) == (unsigned)(ntiles - 1);
+  __syncthreads();
+  if (last) __threadfence();
+  return last;
+}
+
+// Sum of partial[v * ntiles_total + t] over the segment's tiles, for v <
+// nvec; result in res[v] (shared), all threads of the block participate.
+__device__ void reduce_segment(const double* partial, int64_t stride, int first, int count,
+                               int nvec, double* res) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int v = w; v < nvec; v += nw) {
+    double s = 0;
+    for (int t = lane; t < count; t += 32)
+      s += ((volatile const double*)partial)[(int64_t)v * stride + first + t];
+    s = warp_sum(s);
+    if (lane == 0) res[v] = s;
+  }
+  __syncthreads();
+}
+
+// field: 0 beta, 1 bnorm, 2 rnorm
+template <typename V>
+__global__ void __launch_bounds__(kKB) k_seg_norm(const V* __restrict__ x, const Tile* tiles,
+                                                  int ntiles, SegState* st, double* partial,
+                                                  int field) {
+  const Tile t = tiles[blockIdx.x];
+  SegState& S = st[t.seg];
+  double acc = 0;
+  for (int e = threadIdx.x; e < t.len; e += kKB) {
+    const double v = (double)x[t.start + e];
+    acc += v * v;
+  }
+  const double bs = block_sum(acc);
+  if (threadIdx.x == 0) partial[blockIdx.x] = bs;
+  if (!last_of_segment(&S.counter[4 + field], S.ntiles)) return;
+  __shared__ double res[1];
+  reduce_segment(partial, ntiles, S.first_tile, S.ntiles, 1, res);
+  if (threadIdx.x == 0) {
+    const double n = sqrt(res[0]);
+    if (field == 0) S.beta = n;
+    else if (field == 1) S.bnorm = n;
+    else S.rnorm = n;
+    S.counter[4 + field] = 0;
+  }
+}
+
+// Start of a restart cycle: tolerances, right-hand side of the least-squares
+// problem, done flags (converged, retired by the host, or non-finite).
+// tol_abs = rtol * (relative_to_beta ? beta : bnorm).
+__global__ void k_seg_cycle_init(SegState* st, KCtl* ctl, double rtol, int relative_to_beta) {
+  __shared__ int ndone;
+  if (threadIdx.x == 0) ndone = 0;
+  __syncthreads();
+  const int m = ctl->m;
+  for (int s = threadIdx.x; s < ctl->nseg; s += blockDim.x) {
+    SegState& S = st[s];
+    const double beta = S.beta;
+    S.tol_abs = rtol * (relative_to_beta ? beta : S.bnorm);
+    S.k = 0;
+    S.bad = isfinite(beta) ? 0 : 1;
+    S.resid = beta;
+    for (int i = 0; i <= m; ++i) S.g[i] = 0.0;
+    S.g[0] = beta;
+    S.done = (S.retired || S.bad || beta <= S.tol_abs || beta == 0.0) ? 1 : 0;
+    if (S.done) atomicAdd(&ndone, 1);
+    for (int c = 0; c < 4; ++c) S.counter[c] = 0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ctl->ndone = ndone;
+    ctl->all_done = ndone == ctl->nseg ? 1 : 0;
+  }
+}
+
+// x *= 1 / (field 0: beta, 1: hn) of the tile's segment (skipped once done)
+template <typename V>
+__global__ void __launch_bounds__(kKB) k_seg_scale(V* __restrict__ x, const Tile* tiles,
+                                                   const SegState* st, int field) {
+  const Tile t = tiles[blockIdx.x];
+  const SegState& S = st[t.seg];
+  if (S.done) return;
+  const V f = (V)(1.0 / (field == 0 ? S.beta : S.hn));
+  for (int e = threadIdx.x; e < t.len; e += kKB) x[t.start + e] *= f;
+}
+
+// CGS2 passes on w = V[j+1] (see the file comment of fs_linalg.cu):
+//   1: h = V^T w -> H[:, j];  2: w -= V h, h2 = V^T w -> H[:, j] += h2;
+//   3: w -= V h2, ||w|| -> H[j+1, j] = hn.
+template <typename V, int PASS>
+__global__ void __launch_bounds__(kKB) k_seg_cgs(V* __restrict__ Vb, int64_t n, int j,
+                                                 const Tile* tiles, int ntiles, SegState* st,
+                                                 const KCtl* ctl, double* partial) {
+  const Tile t = tiles[blockIdx.x];
+  SegState& S = st[t.seg];
+  if (S.done) return;
+  constexpr int NV = kMaxRestart + 1;
+  constexpr int NW = kKB / 32;
+  __shared__ double coef[NV];
+  __shared__ double wsum[NV * NW];
+  const int nvec = j + 1;
+  const int m = ctl->m;
+  V* __restrict__ w = Vb + (int64_t)(j + 1) * n;
+  if (PASS >= 2) {
+    for (int i = threadIdx.x; i < nvec; i += blockDim.x)
+      coef[i] = PASS == 2 ? S.H[i * m + j] : S.h2[i];
+    __syncthreads();
+  }
+  V acc[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) acc[v] = V(0);
+#pragma unroll
+  for (int q = 0; q < kKEPT; ++q) {
+    const int e = q * kKB + threadIdx.x;
+    if (e >= t.len) break;
+    const int64_t i = t.start + e;
+    V wi = w[i];
+    if (PASS >= 2) {
+      V u = V(0);
+#pragma unroll
+      for (int v = 0; v < NV; ++v)
+        if (v < nvec) u += (V)coef[v] * Vb[(int64_t)v * n + i];
+      wi -= u;
+      w[i] = wi;
+    }
+    if (PASS <= 2) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v)
+        if (v < nvec) acc[v] += Vb[(int64_t)v * n + i] * wi;
+    } else {
+      acc[0] += wi * wi;
+    }
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nout = PASS <= 2 ? nvec : 1;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    if (v < nout) {
+      const double s = warp_sum((double)acc[v]);
+      if (lane == 0) wsum[v * NW + warp] = s;
+    }
+  }
+  __syncthreads();
+  for (int v = threadIdx.x; v < nout; v += blockDim.x) {
+    double s = 0;
+#pragma unroll
+    for (int w2 = 0; w2 < NW; ++w2) s += wsum[v * NW + w2];
+    partial[(int64_t)v * ntiles + blockIdx.x] = s;
+  }
+  if (!last_of_segment(&S.counter[PASS], S.ntiles)) return;
+  __shared__ double res[NV];
+  reduce_segment(partial, ntiles, S.first_tile, S.ntiles, nout, res);
+  if (threadIdx.x == 0) {
+    if (PASS == 1) {
+      for (int i = 0; i < nvec; ++i) S.H[i * m + j] = res[i];
+    } else if (PASS == 2) {
+      for (int i = 0; i < nvec; ++i) {
+        S.h2[i] = res[i];
+        S.H[i * m + j] += res[i];
+      }
+    } else {
+      const double hn = sqrt(res[0]);
+      S.hn = hn;
+      S.H[(j + 1) * m + j] = hn;
+    }
+    S.counter[PASS] = 0;
+  }
+}
+
+// Givens rotations of column j of every active segment.
+__global__ void k_seg_givens(SegState* st, KCtl* ctl, int j) {
+  const int m = ctl->m;
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < ctl->nseg;
+       s += gridDim.x * blockDim.x) {
+    SegState& S = st[s];
+    if (S.done) continue;
+    double* H = S.H;
+    for (int i = 0; i < j; ++i) {
+      const double a = H[i * m + j], b = H[(i + 1) * m + j];
+      H[i * m + j] = S.cs[i] * a + S.sn[i] * b;
+      H[(i + 1) * m + j] = -S.sn[i] * a + S.cs[i] * b;
+    }
+    const double a = H[j * m + j], b = H[(j + 1) * m + j];
+    const double den = hypot(a, b);
+    const double c = den == 0.0 ? 1.0 : a / den, sn = den == 0.0 ? 0.0 : b / den;
+    S.cs[j] = c;
+    S.sn[j] = sn;
+    H[j * m + j] = den;
+    H[(j + 1) * m + j] = 0.0;
+    S.g[j + 1] = -sn * S.g[j];
+    S.g[j] = c * S.g[j];
+    S.resid = fabs(S.g[j + 1]);
+    S.k = j + 1;
+    bool finish = false;
+    if (!isfinite(S.resid) || !isfinite(den) || den == 0.0) {
+      S.bad = isfinite(S.resid) && isfinite(den) ? S.bad : 1;
+      S.k = j;  // drop the broken column
+      finish = true;
+    } else if (S.resid <= S.tol_abs || b == 0.0 || j + 1 >= m) {
+      finish = true;
+    }
+    if (finish) {
+      S.done = 1;
+      if (atomicAdd(&ctl->ndone, 1) + 1 == ctl->nseg) ctl->all_done = 1;
+    }
+  }
+}
+
+// y = H(0:k,0:k)^-1 g(0:k) of the tile's segment, then x += xscale Z y
+template <typename V, typename X>
+__global__ void __launch_bounds__(kKB) k_seg_update_x(const SegState* st, const KCtl* ctl,
+                                                      const V* __restrict__ Z, int64_t n,
+                                                      const Tile* tiles, X* __restrict__ x) {
+  __shared__ double y[kMaxRestart];
+  const Tile t = tiles[blockIdx.x];
+  const SegState& S = st[t.seg];
+  const int k = S.k;
+  if (k == 0) return;
+  if (threadIdx.x == 0) {
+    const int m = ctl->m;
+    for (int i = k - 1; i >= 0; --i) {
+      double s = S.g[i];
+      for (int c = i + 1; c < k; ++c) s -= S.H[i * m + c] * y[c];
+      y[i] = s / S.H[i * m + i];
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < t.len; e += kKB) {
+    const int64_t i = t.start + e;
+    double s = 0;
+    for (int c = 0; c < k; ++c) s += y[c] * (double)Z[(int64_t)c * n + i];
+    x[i] = (X)((double)x[i] + s);
+  }
+}
+
+// out = in / rnorm of the segment (0 for retired segments)
+template <typename A, typename B>
+__global__ void __launch_bounds__(kKB) k_seg_normalise(const A* __restrict__ in,
+                                                       B* __restrict__ out, const Tile* tiles,
+                                                       const SegState* st) {
+  const Tile t = tiles[blockIdx.x];
+  const SegState& S = st[t.seg];
+  const double f = (S.retired || S.rnorm == 0.0) ? 0.0 : 1.0 / S.rnorm;
+  for (int e = threadIdx.x; e < t.len; e += kKB)
+    out[t.start + e] = (B)((double)in[t.start + e] * f);
+}
+
+// x += rnorm d for the segments that are still refined
+template <typename V, typename X>
+__global__ void __launch_bounds__(kKB) k_seg_axpy(X* __restrict__ x, const V* __restrict__ d,
+                                                  const Tile* tiles, const SegState* st) {
+  const Tile t = tiles[blockIdx.x];
+  const SegState& S = st[t.seg];
+  if (S.retired) return;
+  const double a = S.rnorm;
+  for (int e = threadIdx.x; e < t.len; e += kKB)
+    x[t.start + e] = (X)((double)x[t.start + e] + a * (double)d[t.start + e]);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+template <typename V>
+void launch_seg_norm(const V* x, const TileList& tl, SegState* st, double* partial, int field,
+                     cudaStream_t s) {
+  k_seg_norm<V><<<tl.ntiles, kKB, 0, s>>>(x, tl.tiles, tl.ntiles, st, partial, field);
+  count_launches(1);
+}
+template void launch_seg_norm<double>(const double*, const TileList&, SegState*, double*, int,
+                                      cudaStream_t);
+template void launch_seg_norm<float>(const float*, const TileList&, SegState*, double*, int,
+                                     cudaStream_t);
+
+void launch_seg_cycle_init(SegState* st, KCtl* ctl, double rtol, int relative_to_beta,
+                           cudaStream_t s) {
+  k_seg_cycle_init<<<1, 256, 0, s>>>(st, ctl, rtol, relative_to_beta);
+  count_launches(1);
+}
+
+template <typename V>
+void launch_seg_scale(V* x, const TileList& tl, const SegState* st, int field, cudaStream_t s) {
+  k_seg_scale<V><<<tl.ntiles, kKB, 0, s>>>(x, tl.tiles, st, field);
+  count_launches(1);
+}
+template void launch_seg_scale<double>(double*, const TileList&, const SegState*, int,
+                                       cudaStream_t);
+template void launch_seg_scale<float>(float*, const TileList&, const SegState*, int,
+                                      cudaStream_t);
+
+template <typename V>
+void launch_seg_cgs2(V* Vb, int64_t n, int j, const TileList& tl, SegState* st, const KCtl* ctl,
+                     double* partial, cudaStream_t s) {
+  k_seg_cgs<V, 1><<<tl.ntiles, kKB, 0, s>>>(Vb, n, j, tl.tiles, tl.ntiles, st, ctl, partial);
+  k_seg_cgs<V, 2><<<tl.ntiles, kKB, 0, s>>>(Vb, n, j, tl.tiles, tl.ntiles, st, ctl, partial);
+  k_seg_cgs<V, 3><<<tl.ntiles, kKB, 0, s>>>(Vb, n, j, tl.tiles, tl.ntiles, st, ctl, partial);
+  count_launches(3);
+}
+template void launch_seg_cgs2<double>(double*, int64_t, int, const TileList&, SegState*,
+                                      const KCtl*, double*, cudaStream_t);
+template void launch_seg_cgs2<float>(float*, int64_t, int, const TileList&, SegState*,
+                                     const KCtl*, double*, cudaStream_t);
+
+void launch_seg_givens(SegState* st, KCtl* ctl, int nseg, int j, cudaStream_t s) {
+  k_seg_givens<<<(nseg + 127) / 128, 128, 0, s>>>(st, ctl, j);
+  count_launches(1);
+}
+
+template <typename V, typename X>
+void launch_seg_update_x(const SegState* st, const KCtl* ctl, const V* Z, int64_t n,
+                         const TileList& tl, X* x, cudaStream_t s) {
+  k_seg_update_x<V, X><<<tl.ntiles, kKB, 0, s>>>(st, ctl, Z, n, tl.tiles, x);
+  count_launches(1);
+}
+template void launch_seg_update_x<double, double>(const SegState*, const KCtl*, const double*,
+                                                  int64_t, const TileList&, double*,
+                                                  cudaStream_t);
+template void launch_seg_update_x<float, float>(const SegState*, const KCtl*, const float*,
+                                                int64_t, const TileList&, float*, cudaStream_t);
+
+template <typename A, typename B>
+void launch_seg_normalise(const A* in, B* out, const TileList& tl, const SegState* st,
+                          cudaStream_t s) {
+  k_seg_normalise<A, B><<<tl.ntiles, kKB, 0, s>>>(in, out, tl.tiles, st);
+  count_launches(1);
+}
+template void launch_seg_normalise<double, float>(const double*, float*, const TileList&,
+                                                  const SegState*, cudaStream_t);
+
+template <typename V, typename X>
+void launch_seg_axpy(X* x, const V* d, const TileList& tl, const SegState* st, cudaStream_t s) {
+  k_seg_axpy<V, X><<<tl.ntiles, kKB, 0, s>>>(x, d, tl.tiles, st);
+  count_launches(1);
+}
+template void launch_seg_axpy<float, double>(double*, const float*, const TileList&,
+                                             const SegState*, cudaStream_t);
+
+}  // namespace fs

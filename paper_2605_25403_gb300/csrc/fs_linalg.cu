@@ -11,6 +11,7 @@
 // them in FP64.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 
 #include "fs_device.h"
@@ -192,10 +193,13 @@ __global__ void __launch_bounds__(256) k_csr_nc(DCsr<T> M, int64_t ldx, const T*
   }
 }
 
-// Dense coarsest solve x = Cinv b; one warp per row.
+// Coarsest solve x = blockdiag(Cinv) b; one warp per row, the row's block
+// found through row_blk.
 template <typename T, int NC>
-__global__ void k_dense(const T* __restrict__ C, int64_t n, const T* __restrict__ b,
-                        T* __restrict__ x, const int* skip) {
+__global__ void k_dense(const T* __restrict__ C, const int32_t* __restrict__ row_blk,
+                        const int64_t* __restrict__ blk_row, const int64_t* __restrict__ blk_n,
+                        const int64_t* __restrict__ blk_dense, int64_t n,
+                        const T* __restrict__ b, T* __restrict__ x, const int* skip) {
   if (skip && *skip) return;
   const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32;
   const int lane = threadIdx.x & 31;
@@ -203,10 +207,13 @@ __global__ void k_dense(const T* __restrict__ C, int64_t n, const T* __restrict_
 #pragma unroll
   for (int c = 0; c < NC; ++c) acc[c] = T(0);
   if (row < n) {
-    for (int64_t j = lane; j < n; j += 32) {
-      const T a = C[row * n + j];
+    const int blk = row_blk[row];
+    const int64_t r0 = blk_row[blk], nb = blk_n[blk];
+    const T* Cr = C + blk_dense[blk] + (row - r0) * nb;
+    for (int64_t j = lane; j < nb; j += 32) {
+      const T a = Cr[j];
 #pragma unroll
-      for (int c = 0; c < NC; ++c) acc[c] += a * b[c * n + j];
+      for (int c = 0; c < NC; ++c) acc[c] += a * b[c * n + r0 + j];
     }
   }
 #pragma unroll
@@ -221,7 +228,8 @@ void vcycle_level(const DHier<T>& H, int l, const T* b, T* out, const int* skip,
                   cudaStream_t s) {
   if (l == H.nlev - 1) {
     const int64_t n = H.ncoarse;
-    k_dense<T, NC><<<blocks_for(n * 32), 256, 0, s>>>(H.cinv, n, b, out, skip);
+    k_dense<T, NC><<<blocks_for(n * 32), 256, 0, s>>>(H.cinv, H.row_blk, H.blk_row, H.blk_n,
+                                                      H.blk_dense, n, b, out, skip);
     count_launches(1);
     return;
   }
@@ -267,6 +275,22 @@ void vcycle_level(const DHier<T>& H, int l, const T* b, T* out, const int* skip,
   FS_CHEB(1, X0, D0, a1, b1, X1, D1);
   FS_CHEB(4, X1, D1, a2, b2, out, nullptr);
 #undef FS_CHEB
+}
+
+// out[c][r] = in[c][perm[r]] (gather) or out[c][perm[r]] = in[c][r] (scatter)
+template <typename T>
+__global__ void k_permute(const int32_t* __restrict__ perm, int64_t n, int nc,
+                          const T* __restrict__ in, T* __restrict__ out, int scatter,
+                          const int* skip) {
+  if (skip && *skip) return;
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = perm[r];
+    for (int c = 0; c < nc; ++c) {
+      if (scatter) out[c * n + p] = in[c * n + r];
+      else out[c * n + r] = in[c * n + p];
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -317,257 +341,6 @@ __global__ void __launch_bounds__(256) k_bt_add(DCsr<T> BT, int64_t n2, const T*
     for (int c = 0; c < DIM; ++c) t[c * n2 + row] = r[c * n2 + row] + acc[c];
 }
 
-// ---------------------------------------------------------------------------
-// Reductions
-// ---------------------------------------------------------------------------
-constexpr int kRB = 256;   // threads per reduction block
-constexpr int kEPT = 16;   // elements per thread per tile
-constexpr int kTile = kRB * kEPT;
-
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
-  return v;
-}
-
-// Block-wide sum of one double per thread (result valid in thread 0).
-__device__ __forceinline__ double block_sum(double v, double* sm) {
-  v = warp_sum(v);
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  __syncthreads();
-  if (lane == 0) sm[w] = v;
-  __syncthreads();
-  double t = 0;
-  if (threadIdx.x < 32) {
-    t = threadIdx.x < (blockDim.x >> 5) ? sm[threadIdx.x] : 0.0;
-    t = warp_sum(t);
-  }
-  return t;
-}
-
-// Returns true in every thread of the last block to arrive.
-__device__ __forceinline__ bool last_block(unsigned* counter) {
-  __shared__ bool last;
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned ticket = atomicAdd(counter, 1u);
-    last = (ticket == gridDim.x - 1);
-  }
-  __syncthreads();
-  if (last) __threadfence();
-  return last;
-}
-
-// Sum nvec rows of partial[nvec][nblk] by the whole (last) block; result
-// left in sm_out[i].
-__device__ void reduce_partials(const double* partial, int nvec, int nblk,
-                                double* sm_out) {
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int i = w; i < nvec; i += nw) {
-    double s = 0;
-    for (int k = lane; k < nblk; k += 32) s += ((volatile const double*)partial)[(int64_t)i * nblk + k];
-    s = warp_sum(s);
-    if (lane == 0) sm_out[i] = s;
-  }
-  __syncthreads();
-}
-
-// op 0: out = sqrt(sum x^2); op 1: out = sum x^2
-template <typename V>
-__global__ void __launch_bounds__(kRB) k_norm2(const V* __restrict__ x, int64_t n,
-                                               double* partial, unsigned* counter,
-                                               double* out, int op, const int* skip) {
-  if (skip && *skip) return;
-  __shared__ double sm[32];
-  double acc = 0;
-  const int64_t base = (int64_t)blockIdx.x * kTile + threadIdx.x;
-#pragma unroll
-  for (int e = 0; e < kEPT; ++e) {
-    const int64_t i = base + (int64_t)e * kRB;
-    if (i < n) {
-      const double v = (double)x[i];
-      acc += v * v;
-    }
-  }
-  double t = block_sum(acc, sm);
-  if (threadIdx.x == 0) partial[blockIdx.x] = t;
-  if (!last_block(counter)) return;
-  __shared__ double res[1];
-  reduce_partials(partial, 1, gridDim.x, res);
-  if (threadIdx.x == 0) {
-    *out = op == 0 ? sqrt(res[0]) : res[0];
-    *counter = 0;
-  }
-}
-
-// x *= (*num) / (*den)   (or / sqrt(*den))
-template <typename V>
-__global__ void k_scale(V* __restrict__ x, int64_t n, const double* num, const double* den,
-                        int inv_sqrt, const int* skip) {
-  if (skip && *skip) return;
-  double d = *den;
-  if (inv_sqrt) d = sqrt(d);
-  const double s = (num ? *num : 1.0) / d;
-  const V sv = (V)s;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    x[i] *= sv;
-}
-
-// Classical Gram-Schmidt with one reorthogonalisation (CGS2) of
-// w = V[j+1] against V[0..j]; three grid-stride passes over the basis:
-//   1: h = V^T w                            -> H[:, j] = h
-//   2: w -= V h, then h2 = V^T w            -> H[:, j] += h2, st->h2 = h2
-//      (per element: the update needs only that element, so the re-dot
-//      reuses the basis values just read, from L1)
-//   3: w -= V h2 ; ||w||                    -> H[j+1, j] = st->hn = ||w||
-// Per-thread accumulators live in registers (restart length <= 32); block
-// sums go to partial[v][block]; the last block reduces them in FP64.
-constexpr int kCgsBlocks = 4 * 152;
-
-template <typename V, int PASS>
-__global__ void __launch_bounds__(kRB) k_cgs(V* __restrict__ Vb, int64_t n, int j,
-                                             GmresState* st, double* partial,
-                                             const int* skip) {
-  if (st->done) return;
-  constexpr int NV = kMaxRestart + 1;
-  constexpr int NW = kRB / 32;
-  __shared__ double coef[NV];
-  __shared__ double wsum[NV * NW];
-  const int nvec = j + 1;
-  const int m = st->m;
-  V* __restrict__ w = Vb + (int64_t)(j + 1) * n;
-  if (PASS >= 2) {
-    for (int i = threadIdx.x; i < nvec; i += blockDim.x)
-      coef[i] = PASS == 2 ? st->H[i * m + j] : st->h2[i];
-    __syncthreads();
-  }
-  // accumulators in the vector precision (a thread sums few elements), the
-  // block and grid reductions in FP64
-  V acc[NV];
-#pragma unroll
-  for (int v = 0; v < NV; ++v) acc[v] = V(0);
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
-    V wi = w[i];
-    if (PASS >= 2) {
-      V u = V(0);
-#pragma unroll
-      for (int v = 0; v < NV; ++v)
-        if (v < nvec) u += (V)coef[v] * Vb[(int64_t)v * n + i];
-      wi -= u;
-      w[i] = wi;
-    }
-    if (PASS <= 2) {
-#pragma unroll
-      for (int v = 0; v < NV; ++v)
-        if (v < nvec) acc[v] += Vb[(int64_t)v * n + i] * wi;
-    } else {
-      acc[0] += wi * wi;
-    }
-  }
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nout = PASS <= 2 ? nvec : 1;
-#pragma unroll
-  for (int v = 0; v < NV; ++v) {
-    if (v < nout) {
-      double t = warp_sum((double)acc[v]);
-      if (lane == 0) wsum[v * NW + warp] = t;
-    }
-  }
-  __syncthreads();
-  for (int v = threadIdx.x; v < nout; v += blockDim.x) {
-    double t = 0;
-#pragma unroll
-    for (int w2 = 0; w2 < NW; ++w2) t += wsum[v * NW + w2];
-    partial[(int64_t)v * gridDim.x + blockIdx.x] = t;
-  }
-  if (!last_block(&st->counter[PASS])) return;
-  __shared__ double res[NV];
-  reduce_partials(partial, nout, gridDim.x, res);
-  if (threadIdx.x == 0) {
-    if (PASS == 1) {
-      for (int i = 0; i < nvec; ++i) st->H[i * m + j] = res[i];
-    } else if (PASS == 2) {
-      for (int i = 0; i < nvec; ++i) {
-        st->h2[i] = res[i];
-        st->H[i * m + j] += res[i];
-      }
-    } else {
-      const double hn = sqrt(res[0]);
-      st->hn = hn;
-      st->H[(j + 1) * m + j] = hn;
-    }
-    st->counter[PASS] = 0;
-  }
-}
-
-// Givens rotations of column j; convergence / breakdown test.
-__global__ void k_givens(GmresState* st, int j) {
-  if (st->done || threadIdx.x != 0) return;
-  const int m = st->m;
-  double* H = st->H;
-  for (int i = 0; i < j; ++i) {
-    const double a = H[i * m + j], b = H[(i + 1) * m + j];
-    H[i * m + j] = st->cs[i] * a + st->sn[i] * b;
-    H[(i + 1) * m + j] = -st->sn[i] * a + st->cs[i] * b;
-  }
-  const double a = H[j * m + j], b = H[(j + 1) * m + j];
-  const double den = hypot(a, b);
-  const double c = den == 0.0 ? 1.0 : a / den, s = den == 0.0 ? 0.0 : b / den;
-  st->cs[j] = c;
-  st->sn[j] = s;
-  H[j * m + j] = den;
-  H[(j + 1) * m + j] = 0.0;
-  st->g[j + 1] = -s * st->g[j];
-  st->g[j] = c * st->g[j];
-  st->resid = fabs(st->g[j + 1]);
-  st->k = j + 1;
-  if (!isfinite(st->resid) || !isfinite(den)) {
-    st->bad = 1;
-    st->done = 1;
-    st->k = j;  // drop the broken column
-  } else if (st->resid <= st->tol_abs || b == 0.0 || j + 1 >= m) {
-    st->done = 1;
-  }
-}
-
-__global__ void k_cycle_init(GmresState* st) {
-  if (threadIdx.x != 0) return;
-  const double beta = st->beta;
-  st->k = 0;
-  st->bad = isfinite(beta) ? 0 : 1;
-  st->resid = beta;
-  for (int i = 0; i <= st->m; ++i) st->g[i] = 0.0;
-  st->g[0] = beta;
-  st->done = (!isfinite(beta) || beta <= st->tol_abs || beta == 0.0) ? 1 : 0;
-}
-
-// y = H(0:k,0:k)^-1 g(0:k), then x += xscale * Z(:, 0:k) y
-template <typename V, typename X>
-__global__ void k_update_x(GmresState* st, const V* __restrict__ Z, int64_t n,
-                           X* __restrict__ x, double xscale) {
-  __shared__ double y[kMaxRestart];
-  const int k = st->k;
-  if (k == 0) return;
-  if (threadIdx.x == 0) {
-    const int m = st->m;
-    for (int i = k - 1; i >= 0; --i) {
-      double s = st->g[i];
-      for (int c = i + 1; c < k; ++c) s -= st->H[i * m + c] * y[c];
-      y[i] = s / st->H[i * m + i];
-    }
-  }
-  __syncthreads();
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    double s = 0;
-    for (int c = 0; c < k; ++c) s += y[c] * (double)Z[(int64_t)c * n + i];
-    x[i] = (X)((double)x[i] + xscale * s);
-  }
-}
-
 template <typename A, typename B>
 __global__ void k_convert(const A* __restrict__ in, B* __restrict__ out, int64_t n,
                           const double* scale, int inv) {
@@ -576,15 +349,6 @@ __global__ void k_convert(const A* __restrict__ in, B* __restrict__ out, int64_t
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
     out[i] = (B)((double)in[i] * s);
-}
-
-template <typename V, typename X>
-__global__ void k_axpy_mixed(X* __restrict__ x, const V* __restrict__ d, int64_t n,
-                             const double* alpha) {
-  const double a = *alpha;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    x[i] = (X)((double)x[i] + a * (double)d[i]);
 }
 
 inline unsigned grid_stride_blocks(int64_t n) {
@@ -649,9 +413,23 @@ template <typename T>
 void mg_vcycle(const DHier<T>& H, int nc, const T* b, int64_t ld, T* x, const int* skip,
                cudaStream_t s) {
   (void)ld;  // level-0 vectors are stored with stride = level rows
-  if (nc == 1) vcycle_level<T, 1>(H, 0, b, x, skip, s);
-  else if (nc == 2) vcycle_level<T, 2>(H, 0, b, x, skip, s);
-  else vcycle_level<T, 3>(H, 0, b, x, skip, s);
+  const T* bb = b;
+  T* xx = x;
+  const int64_t n0 = H.lev[0].A.nrow;
+  const unsigned gp = (unsigned)std::min<int64_t>((n0 + 255) / 256, 152 * 16);
+  if (H.perm) {  // into block order
+    k_permute<T><<<gp, 256, 0, s>>>(H.perm, n0, nc, b, H.pin, 0, skip);
+    count_launches(1);
+    bb = H.pin;
+    xx = H.pout;
+  }
+  if (nc == 1) vcycle_level<T, 1>(H, 0, bb, xx, skip, s);
+  else if (nc == 2) vcycle_level<T, 2>(H, 0, bb, xx, skip, s);
+  else vcycle_level<T, 3>(H, 0, bb, xx, skip, s);
+  if (H.perm) {  // back to the caller's order
+    k_permute<T><<<gp, 256, 0, s>>>(H.perm, n0, nc, H.pout, x, 1, skip);
+    count_launches(1);
+  }
 }
 template void mg_vcycle<double>(const DHier<double>&, int, const double*, int64_t, double*,
                                 const int*, cudaStream_t);
@@ -692,61 +470,6 @@ template void launch_precond<float>(const DOp<float>&, const DHier<float>&,
                                     const int32_t*, int, const float*, float*, float*,
                                     float*, const int*, cudaStream_t);
 
-template <typename V>
-void launch_norm2(const V* x, int64_t n, double* partial, unsigned* counter, double* out,
-                  int op, const int* skip, cudaStream_t s) {
-  unsigned g = (unsigned)((n + kTile - 1) / kTile);
-  if (g < 1) g = 1;
-  k_norm2<V><<<g, kRB, 0, s>>>(x, n, partial, counter, out, op, skip);
-  count_launches(1);
-}
-template void launch_norm2<double>(const double*, int64_t, double*, unsigned*, double*, int,
-                                   const int*, cudaStream_t);
-template void launch_norm2<float>(const float*, int64_t, double*, unsigned*, double*, int,
-                                  const int*, cudaStream_t);
-
-template <typename V>
-void launch_scale(V* x, int64_t n, const double* num, const double* den, int inv_sqrt_den,
-                  const int* skip, cudaStream_t s) {
-  k_scale<V><<<grid_stride_blocks(n), 256, 0, s>>>(x, n, num, den, inv_sqrt_den, skip);
-  count_launches(1);
-}
-template void launch_scale<double>(double*, int64_t, const double*, const double*, int,
-                                   const int*, cudaStream_t);
-template void launch_scale<float>(float*, int64_t, const double*, const double*, int,
-                                  const int*, cudaStream_t);
-
-template <typename V>
-void launch_cgs2(V* Vb, int64_t n, int j, GmresState* st, double* partial, const int* skip,
-                 cudaStream_t s) {
-  int64_t gg = (n + kRB - 1) / kRB;
-  unsigned g = (unsigned)(gg < 1 ? 1 : (gg > kCgsBlocks ? kCgsBlocks : gg));
-  k_cgs<V, 1><<<g, kRB, 0, s>>>(Vb, n, j, st, partial, skip);
-  count_launches(1);
-  k_cgs<V, 2><<<g, kRB, 0, s>>>(Vb, n, j, st, partial, skip);
-  count_launches(1);
-  k_cgs<V, 3><<<g, kRB, 0, s>>>(Vb, n, j, st, partial, skip);
-  count_launches(1);
-}
-template void launch_cgs2<double>(double*, int64_t, int, GmresState*, double*, const int*,
-                                  cudaStream_t);
-template void launch_cgs2<float>(float*, int64_t, int, GmresState*, double*, const int*,
-                                 cudaStream_t);
-
-void launch_givens(GmresState* st, int j, cudaStream_t s) { k_givens<<<1, 32, 0, s>>>(st, j); }
-void launch_cycle_init(GmresState* st, cudaStream_t s) { k_cycle_init<<<1, 32, 0, s>>>(st); }
-
-template <typename V, typename X>
-void launch_update_x(GmresState* st, const V* Z, int64_t n, X* x, double xscale,
-                     cudaStream_t s) {
-  k_update_x<V, X><<<grid_stride_blocks(n), 256, 0, s>>>(st, Z, n, x, xscale);
-count_launches(1);
-}
-template void launch_update_x<double, double>(GmresState*, const double*, int64_t, double*,
-                                              double, cudaStream_t);
-template void launch_update_x<float, float>(GmresState*, const float*, int64_t, float*,
-                                            double, cudaStream_t);
-
 template <typename A, typename B>
 void launch_convert(const A* in, B* out, int64_t n, const double* scale, int inv,
                     cudaStream_t s) {
@@ -759,15 +482,5 @@ template void launch_convert<float, double>(const float*, double*, int64_t, cons
                                             cudaStream_t);
 template void launch_convert<double, double>(const double*, double*, int64_t, const double*,
                                              int, cudaStream_t);
-
-template <typename V, typename X>
-void launch_axpy_mixed(X* x, const V* d, int64_t n, const double* alpha, cudaStream_t s) {
-  k_axpy_mixed<V, X><<<grid_stride_blocks(n), 256, 0, s>>>(x, d, n, alpha);
-  count_launches(1);
-}
-template void launch_axpy_mixed<float, double>(double*, const float*, int64_t, const double*,
-                                               cudaStream_t);
-template void launch_axpy_mixed<double, double>(double*, const double*, int64_t,
-                                                const double*, cudaStream_t);
 
 }  // namespace fs

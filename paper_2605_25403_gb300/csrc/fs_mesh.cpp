@@ -85,7 +85,96 @@ bool cell_slots(const Mesh& m, const HostCsr& P, int r0, int nr, int c0,
 
 }  // namespace
 
+namespace {
+int build_local(const fs_mesh_desc& d, Mesh& m);
+int finalize_patterns(Mesh& m);
+}  // namespace
+
 int build_mesh(const fs_mesh_desc& d, Mesh& m) {
+  int rc = build_local(d, m);
+  if (rc != FS_OK) return rc;
+  Instance I;
+  I.desc = d;
+  I.voff = 0;
+  I.nv = m.nv;
+  I.eoff = 0;
+  I.ne = m.ne;
+  I.coff = 0;
+  I.ncell = m.ncell;
+  m.inst.assign(1, I);
+  return finalize_patterns(m);
+}
+
+int build_batch_mesh(const fs_mesh_desc* d, int count, Mesh& m) {
+  if (count < 1 || !d) {
+    set_error("fs_mesh_create_batch: need at least one description");
+    return FS_ERR_INVALID_ARG;
+  }
+  std::vector<Mesh> loc(count);
+  for (int i = 0; i < count; ++i) {
+    if (d[i].dim != d[0].dim) {
+      set_error("fs_mesh_create_batch: all instances must have the same dimension");
+      return FS_ERR_INVALID_ARG;
+    }
+    int rc = build_local(d[i], loc[i]);
+    if (rc != FS_OK) return rc;
+  }
+  const int dim = d[0].dim;
+  m = Mesh();
+  m.desc = d[0];
+  m.dim = dim;
+  m.nb = dim + 1;
+  m.nloc = dim == 2 ? 6 : 10;
+  m.inst.resize(count);
+  for (int i = 0; i < count; ++i) {
+    Instance& I = m.inst[i];
+    I.desc = d[i];
+    I.voff = m.nv;
+    I.nv = loc[i].nv;
+    I.eoff = m.ne;
+    I.ne = loc[i].ne;
+    I.coff = m.ncell;
+    I.ncell = loc[i].ncell;
+    m.nv += I.nv;
+    m.ne += I.ne;
+    m.ncell += I.ncell;
+  }
+  m.n2 = m.nv + m.ne;
+  if (m.ncell * (dim == 2 ? 36 : 100) >= (int64_t)1 << 31) {
+    set_error("fs_mesh_create_batch: batch too large for int32 CSR offsets");
+    return FS_ERR_INVALID_ARG;
+  }
+  m.coords.resize(m.nv * dim);
+  m.p2xyz.resize(m.n2 * dim);
+  m.c2d.resize(m.ncell * m.nloc);
+  m.edges.resize(m.ne * 2);
+  m.dirichlet.resize(m.n2);
+  for (int i = 0; i < count; ++i) {
+    const Mesh& L = loc[i];
+    const Instance& I = m.inst[i];
+    std::memcpy(&m.coords[I.voff * dim], L.coords.data(), sizeof(double) * L.nv * dim);
+    for (int64_t j = 0; j < L.n2; ++j) {
+      int64_t g = union_node(m, i, j);
+      for (int a = 0; a < dim; ++a) m.p2xyz[g * dim + a] = L.p2xyz[j * dim + a];
+      m.dirichlet[g] = L.dirichlet[j];
+    }
+    for (int64_t e = 0; e < L.ne; ++e) {
+      m.edges[2 * (I.eoff + e)] = (int32_t)(I.voff + L.edges[2 * e]);
+      m.edges[2 * (I.eoff + e) + 1] = (int32_t)(I.voff + L.edges[2 * e + 1]);
+    }
+    for (int64_t c = 0; c < L.ncell; ++c)
+      for (int a = 0; a < m.nloc; ++a)
+        m.c2d[(I.coff + c) * m.nloc + a] = (int32_t)union_node(m, i, L.c2d[c * m.nloc + a]);
+  }
+  m.dlist.clear();
+  for (int64_t i = 0; i < m.n2; ++i)
+    if (m.dirichlet[i]) m.dlist.push_back((int32_t)i);
+  return finalize_patterns(m);
+}
+
+namespace {
+
+int build_local(const fs_mesh_desc& d, Mesh& m) {
   if (d.dim != 2 && d.dim != 3) {
     set_error("fs_mesh_create: dim must be 2 or 3");
     return FS_ERR_INVALID_ARG;
@@ -267,7 +356,10 @@ int build_mesh(const fs_mesh_desc& d, Mesh& m) {
   m.dlist.clear();
   for (int64_t i = 0; i < m.n2; ++i)
     if (m.dirichlet[i]) m.dlist.push_back((int32_t)i);
+  return FS_OK;
+}
 
+int finalize_patterns(Mesh& m) {
   // block patterns and slot tables
   cell_pattern(m, m.n2, 0, m.nloc, 0, m.nloc, m.A);
   cell_pattern(m, m.nv, 0, m.nb, 0, m.nloc, m.B);
@@ -283,6 +375,8 @@ int build_mesh(const fs_mesh_desc& d, Mesh& m) {
   }
   return FS_OK;
 }
+
+}  // namespace
 
 void monolithic_pattern(const Mesh& m, std::vector<int64_t>& rowptr,
                         std::vector<int32_t>& col) {

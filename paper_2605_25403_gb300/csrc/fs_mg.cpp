@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <cmath>
 #include <numeric>
+#include <atomic>
 #include <random>
 
 #include "fs_internal.h"
@@ -275,6 +276,181 @@ void build_hierarchy(const Mesh& m, const HostCsr& A0, bool p2_fine,
     for (int64_t i = 0; i < H.ncoarse; ++i)
       H.coarse_inv[i * H.ncoarse + i] = H.levels.back().dinv[i];
   }
+}
+
+}  // namespace fs
+
+// ---------------------------------------------------------------------------
+// Batched (union) hierarchies
+// ---------------------------------------------------------------------------
+#include <thread>
+
+namespace fs {
+
+namespace {
+
+// Edges/sizes of instance i in its own numbering (what build_hierarchy needs).
+Mesh local_view(const Mesh& m, int i) {
+  const Instance& I = m.inst[i];
+  Mesh L;
+  L.desc = I.desc;
+  L.dim = m.dim;
+  L.nb = m.nb;
+  L.nloc = m.nloc;
+  L.nv = I.nv;
+  L.ne = I.ne;
+  L.n2 = I.nv + I.ne;
+  L.ncell = I.ncell;
+  L.edges.resize(2 * I.ne);
+  for (int64_t e = 0; e < I.ne; ++e) {
+    L.edges[2 * e] = (int32_t)(m.edges[2 * (I.eoff + e)] - I.voff);
+    L.edges[2 * e + 1] = (int32_t)(m.edges[2 * (I.eoff + e) + 1] - I.voff);
+  }
+  return L;
+}
+
+HostCsr identity(int64_t n) {
+  HostCsr I;
+  I.nrow = I.ncol = n;
+  I.rowptr.resize(n + 1);
+  I.col.resize(n);
+  I.val.assign(n, 1.0);
+  for (int64_t i = 0; i <= n; ++i) I.rowptr[i] = (int32_t)i;
+  for (int64_t i = 0; i < n; ++i) I.col[i] = (int32_t)i;
+  return I;
+}
+
+// Block-diagonal concatenation.
+HostCsr block_diag(const std::vector<const HostCsr*>& blocks) {
+  HostCsr C;
+  for (auto* b : blocks) {
+    C.nrow += b->nrow;
+    C.ncol += b->ncol;
+  }
+  C.rowptr.assign(C.nrow + 1, 0);
+  int64_t r0 = 0, c0 = 0;
+  for (auto* b : blocks) {
+    for (int64_t r = 0; r < b->nrow; ++r) {
+      for (int32_t k = b->rowptr[r]; k < b->rowptr[r + 1]; ++k) {
+        C.col.push_back((int32_t)(c0 + b->col[k]));
+        C.val.push_back(b->val[k]);
+      }
+      C.rowptr[r0 + r + 1] = (int32_t)C.col.size();
+    }
+    r0 += b->nrow;
+    c0 += b->ncol;
+  }
+  return C;
+}
+
+}  // namespace
+
+void build_union_hierarchy(const Mesh& m, const std::vector<Mesh>& /*local*/,
+                           const HostCsr& A0, bool p2_fine,
+                           const std::vector<int32_t>& fixed, int64_t coarse_max,
+                           UnionHierarchy& U) {
+  const int K = (int)m.inst.size();
+  // union row -> (instance, local row)
+  std::vector<int32_t> owner(A0.nrow, -1);
+  std::vector<int64_t> local(A0.nrow, -1);
+  for (int i = 0; i < K; ++i) {
+    const Instance& I = m.inst[i];
+    int64_t n = p2_fine ? I.n2() : I.nv;
+    for (int64_t j = 0; j < n; ++j) {
+      int64_t g = p2_fine ? union_node(m, i, j) : I.voff + j;
+      owner[g] = i;
+      local[g] = j;
+    }
+  }
+  std::vector<HostHierarchy> H(K);
+  auto work = [&](int i) {
+    const Instance& I = m.inst[i];
+    Mesh L = local_view(m, i);
+    HostCsr Ai;
+    Ai.nrow = Ai.ncol = p2_fine ? I.n2() : I.nv;
+    Ai.rowptr.assign(Ai.nrow + 1, 0);
+    for (int64_t j = 0; j < Ai.nrow; ++j) {
+      int64_t g = p2_fine ? union_node(m, i, j) : I.voff + j;
+      for (int32_t k = A0.rowptr[g]; k < A0.rowptr[g + 1]; ++k) {
+        // block-diagonal: every column belongs to the same instance, and the
+        // union order restricted to one instance is its local order
+        Ai.col.push_back((int32_t)local[A0.col[k]]);
+        Ai.val.push_back(A0.val[k]);
+      }
+      Ai.rowptr[j + 1] = (int32_t)Ai.col.size();
+    }
+    std::vector<int32_t> fx;
+    for (int32_t g : fixed)
+      if (owner[g] == i) fx.push_back((int32_t)local[g]);
+    build_hierarchy(L, Ai, p2_fine, fx, coarse_max, H[i]);
+  };
+  int nthr = (int)std::min<unsigned>(std::max(1u, std::thread::hardware_concurrency()), 16u);
+  if (K == 1 || nthr == 1) {
+    for (int i = 0; i < K; ++i) work(i);
+  } else {
+    std::vector<std::thread> pool;
+    std::atomic<int> next{0};
+    for (int t = 0; t < std::min(nthr, K); ++t)
+      pool.emplace_back([&]() {
+        for (int i = next++; i < K; i = next++) work(i);
+      });
+    for (auto& th : pool) th.join();
+  }
+  int depth = 0;
+  for (int i = 0; i < K; ++i) depth = std::max(depth, (int)H[i].levels.size());
+  U.H.levels.assign(depth, HostLevel());
+  for (int l = 0; l < depth; ++l) {
+    std::vector<const HostCsr*> As, Ps, Rs;
+    std::vector<HostCsr> ids;
+    ids.reserve(K);
+    HostLevel& UL = U.H.levels[l];
+    UL.lmax = 0;
+    for (int i = 0; i < K; ++i) {
+      int li = std::min(l, (int)H[i].levels.size() - 1);
+      const HostLevel& hl = H[i].levels[li];
+      As.push_back(&hl.A);
+      UL.dinv.insert(UL.dinv.end(), hl.dinv.begin(), hl.dinv.end());
+      UL.lmax = std::max(UL.lmax, hl.lmax);
+      if (l + 1 < depth) {
+        if (l + 1 < (int)H[i].levels.size()) {
+          Ps.push_back(&hl.P);
+          Rs.push_back(&hl.R);
+        } else {
+          ids.push_back(identity(hl.A.nrow));
+          Ps.push_back(&ids.back());
+          Rs.push_back(&ids.back());
+        }
+      }
+    }
+    UL.A = block_diag(As);
+    if (l + 1 < depth) {
+      UL.P = block_diag(Ps);
+      UL.R = block_diag(Rs);
+    }
+  }
+  // block order of level 0 vs the union numbering
+  U.perm.clear();
+  if (p2_fine && K > 1) {
+    U.perm.reserve(A0.nrow);
+    for (int i = 0; i < K; ++i)
+      for (int64_t j = 0; j < m.inst[i].n2(); ++j) U.perm.push_back((int32_t)union_node(m, i, j));
+  }
+  // coarsest: block-diagonal dense inverses
+  U.blk_row.assign(K, 0);
+  U.blk_n.assign(K, 0);
+  U.blk_dense.assign(K, 0);
+  U.dense.clear();
+  U.row_blk.clear();
+  int64_t row = 0;
+  for (int i = 0; i < K; ++i) {
+    U.blk_row[i] = row;
+    U.blk_n[i] = H[i].ncoarse;
+    U.blk_dense[i] = (int64_t)U.dense.size();
+    U.dense.insert(U.dense.end(), H[i].coarse_inv.begin(), H[i].coarse_inv.end());
+    for (int64_t r = 0; r < H[i].ncoarse; ++r) U.row_blk.push_back(i);
+    row += H[i].ncoarse;
+  }
+  U.H.ncoarse = row;
 }
 
 }  // namespace fs

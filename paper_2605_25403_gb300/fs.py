@@ -89,6 +89,48 @@ _lib.fs_get_state.argtypes = [_vp, _vp, _int, _P(_d)]
 _lib.fs_set_state.argtypes = [_vp, _vp, _int, _d]
 _lib.fs_problem_device_bytes.restype = _i64
 _lib.fs_problem_device_bytes.argtypes = [_vp]
+_lib.fs_mesh_create_batch.restype = _int
+_lib.fs_mesh_create_batch.argtypes = [_vp, _int, _P(_vp)]
+_lib.fs_mesh_instances.restype = _int
+_lib.fs_mesh_instances.argtypes = [_vp, _vp]
+_lib.fs_problem_create_batch.restype = _int
+_lib.fs_problem_create_batch.argtypes = [_vp, _vp, _int, _vp, _P(_vp)]
+_lib.fs_step_begin.restype = _int
+_lib.fs_step_begin.argtypes = [_vp, _int, _P(fs_solve_opts)]
+_lib.fs_step_poll.restype = _int
+_lib.fs_step_poll.argtypes = [_vp, _int, _P(_int)]
+_lib.fs_instance_stats.restype = _int
+_lib.fs_instance_stats.argtypes = [_vp, _vp]
+class fs_server_desc(ctypes.Structure):
+    _fields_ = [("hbm_budget", _i64), ("max_slots", _int), ("setup_threads", _int)]
+
+
+class fs_request_result(ctypes.Structure):
+    _fields_ = [("id", _i64), ("status", _int), ("nsteps", _int), ("iters", _int),
+                ("arrival", _d), ("admitted", _d), ("started", _d), ("finished", _d),
+                ("device_bytes", _i64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib.fs_server_create.restype = _int
+_lib.fs_server_create.argtypes = [_P(fs_server_desc), _P(_vp)]
+_lib.fs_server_destroy.restype = _int
+_lib.fs_server_destroy.argtypes = [_vp]
+_lib.fs_server_submit.restype = _int
+_lib.fs_server_submit.argtypes = [_vp, _P(fs_mesh_desc), _P(fs_problem_desc), _int, _d, _int,
+                                  _P(_i64)]
+_lib.fs_server_progress.restype = _int
+_lib.fs_server_progress.argtypes = [_vp, _d, _P(_int)]
+_lib.fs_server_pop_completed.restype = _int
+_lib.fs_server_pop_completed.argtypes = [_vp, _vp, _int, _P(_int)]
+_lib.fs_server_take_state.restype = _int
+_lib.fs_server_take_state.argtypes = [_vp, _i64, _vp, _i64]
+_lib.fs_server_status.restype = _int
+_lib.fs_server_status.argtypes = [_vp, _P(_int), _P(_int), _P(_i64)]
+_lib.fs_server_estimate_bytes.restype = _i64
+_lib.fs_server_estimate_bytes.argtypes = [_P(fs_mesh_desc), _int]
 _lib.fs_csr_residual_norm.restype = _int
 _lib.fs_csr_residual_norm.argtypes = [_i64, _vp, _vp, _vp, _vp, _vp, _P(_d), _vp]
 _lib.fs_csr_residual_norm_noalloc.restype = _int
@@ -106,7 +148,12 @@ EXPORTED = ["fs_mesh_create", "fs_mesh_destroy", "fs_dof_map", "fs_problem_creat
             "fs_problem_destroy", "fs_assemble_step", "fs_solve", "fs_step",
             "fs_apply_operator", "fs_get_state", "fs_set_state", "fs_problem_device_bytes",
             "fs_default_solve_opts", "fs_last_error", "fs_launch_count",
-            "fs_profile_kernel", "fs_csr_residual_norm", "fs_csr_residual_norm_noalloc"]
+            "fs_profile_kernel", "fs_csr_residual_norm", "fs_csr_residual_norm_noalloc",
+            "fs_mesh_create_batch", "fs_mesh_instances", "fs_problem_create_batch",
+            "fs_step_begin", "fs_step_poll", "fs_instance_stats", "fs_server_create",
+            "fs_server_destroy", "fs_server_submit", "fs_server_progress",
+            "fs_server_pop_completed", "fs_server_take_state", "fs_server_status",
+            "fs_server_estimate_bytes"]
 FS_KERNEL_SPMV, FS_KERNEL_SPMV_FP64, FS_KERNEL_CHEB, FS_KERNEL_ASSEMBLE_CONV = range(4)
 
 
@@ -131,6 +178,38 @@ def _hptr(a):
 
 
 # ---------------------------------------------------------------------------
+def _mesh_desc(dim, n, lo, hi, jitter=0.0, seed=0, dirichlet_sides=0x3F):
+    d = fs_mesh_desc()
+    d.dim = dim
+    for a in range(3):
+        d.n[a] = int(n[a]) if a < len(n) else 1
+        d.lo[a] = float(lo[a]) if a < len(lo) else 0.0
+        d.hi[a] = float(hi[a]) if a < len(hi) else 1.0
+    d.jitter = float(jitter)
+    d.seed = int(seed) & (2**64 - 1)
+    d.dirichlet_sides = int(dirichlet_sides)
+    return d
+
+
+def fs_mesh_create_batch(descs):
+    """descs: list of (dim, n, lo, hi, jitter, seed, dirichlet_sides)."""
+    arr = (fs_mesh_desc * len(descs))(*[_mesh_desc(*d) for d in descs])
+    h = _vp()
+    _check(_lib.fs_mesh_create_batch(arr, len(descs), ctypes.byref(h)), "fs_mesh_create_batch")
+    return h
+
+
+def fs_mesh_instances(mesh):
+    """(count x 6) int64 array: first vertex, vertex count, first edge node,
+    edge node count, first cell, cell count of every instance."""
+    n = _lib.fs_mesh_instances(mesh, None)
+    if n < 0:
+        raise FsError(-n, "fs_mesh_instances")
+    out = np.zeros((n, 6), np.int64)
+    _lib.fs_mesh_instances(mesh, _hptr(out))
+    return out
+
+
 def fs_mesh_create(dim, n, lo, hi, jitter=0.0, seed=0, dirichlet_sides=0x3F):
     d = fs_mesh_desc()
     d.dim = dim
@@ -174,6 +253,52 @@ def fs_default_solve_opts(**kw):
     return o
 
 
+def _problem_desc(problem, nu, dt, t0=0.0, precision=FS_PREC_FP64, pin_pressure=1, init=0,
+                  wconst=(0.0, 0.0, 0.0)):
+    d = fs_problem_desc()
+    d.problem, d.nu, d.dt, d.t0 = int(problem), float(nu), float(dt), float(t0)
+    d.precision, d.pin_pressure, d.init = int(precision), int(pin_pressure), int(init)
+    for a in range(3):
+        d.wconst[a] = float(wconst[a]) if a < len(wconst) else 0.0
+    return d
+
+
+def fs_problem_create_batch(mesh, descs, stream=None):
+    """descs: list of keyword dicts for _problem_desc, one per instance."""
+    arr = (fs_problem_desc * len(descs))(*[_problem_desc(**d) for d in descs])
+    h = _vp()
+    s = None if stream is None else ctypes.c_void_p(int(stream))
+    _check(_lib.fs_problem_create_batch(mesh, arr, len(descs), s, ctypes.byref(h)),
+           "fs_problem_create_batch")
+    _state_sizes[h.value] = fs_dof_map(mesh, arrays=False)["n_dof"]
+    _instance_counts[h.value] = len(descs)
+    return h
+
+
+def fs_step_begin(prob, nsteps, opts=None):
+    o = opts if opts is not None else fs_default_solve_opts()
+    _check(_lib.fs_step_begin(prob, int(nsteps), ctypes.byref(o)), "fs_step_begin")
+
+
+def fs_step_poll(prob, wait=False, raise_on_error=True):
+    """(done, status)."""
+    done = _int(0)
+    rc = _lib.fs_step_poll(prob, 1 if wait else 0, ctypes.byref(done))
+    if raise_on_error and rc != FS_OK:
+        raise FsError(rc, "fs_step_poll")
+    return bool(done.value), rc
+
+
+def fs_instance_stats(prob):
+    n = _instance_counts.get(prob.value, 1)
+    arr = (fs_solve_stats * n)()
+    _check(_lib.fs_instance_stats(prob, arr), "fs_instance_stats")
+    return [arr[i].as_dict() for i in range(n)]
+
+
+_instance_counts = {}
+
+
 def fs_problem_create(mesh, problem, nu, dt, t0=0.0, precision=FS_PREC_FP64, pin_pressure=1,
                       init=0, wconst=(0.0, 0.0, 0.0), stream=None):
     d = fs_problem_desc()
@@ -185,11 +310,13 @@ def fs_problem_create(mesh, problem, nu, dt, t0=0.0, precision=FS_PREC_FP64, pin
     s = None if stream is None else ctypes.c_void_p(int(stream))
     _check(_lib.fs_problem_create(mesh, ctypes.byref(d), s, ctypes.byref(h)), "fs_problem_create")
     _state_sizes[h.value] = fs_dof_map(mesh, arrays=False)["n_dof"]
+    _instance_counts[h.value] = int(_lib.fs_mesh_instances(mesh, None))
     return h
 
 
 def fs_problem_destroy(prob):
     _state_sizes.pop(prob.value, None)
+    _instance_counts.pop(prob.value, None)
     _check(_lib.fs_problem_destroy(prob), "fs_problem_destroy")
 
 
@@ -308,6 +435,31 @@ class Stepper:
                                  wl.wconst or (0.0, 0.0, 0.0), stream)
         return cls(mesh, prob, info)
 
+    @classmethod
+    def from_workloads(cls, wls, precision=FS_PREC_FP64, stream=None):
+        """One batched problem over several independent workloads (same dim,
+        problem kind and dt; nu may differ)."""
+        mesh = fs_mesh_create_batch([(w.dim, w.n, w.lo, w.hi, w.jitter, w.seed, w.side_mask)
+                                     for w in wls])
+        info = fs_dof_map(mesh, arrays=False)
+        prob = fs_problem_create_batch(mesh, [dict(
+            problem=_KIND[w.problem], nu=w.nu, dt=w.dt, precision=precision,
+            pin_pressure=1 if w.pin_p0 else 0, init=1 if w.init == "zero_interior" else 0,
+            wconst=w.wconst or (0.0, 0.0, 0.0)) for w in wls], stream)
+        info["instances"] = fs_mesh_instances(mesh)
+        return cls(mesh, prob, info)
+
+    def instance_state(self, x, i):
+        """Instance i's entries of a union state vector, in its own layout
+        [u_x | u_y | (u_z) | p]."""
+        v0, nv, e0, ne = (int(a) for a in self.info["instances"][i][:4])
+        n2, d = self.info["n_p2"], self.info["dim"]
+        parts = []
+        for c in range(d):
+            parts += [x[c * n2 + v0:c * n2 + v0 + nv], x[c * n2 + e0:c * n2 + e0 + ne]]
+        parts.append(x[d * n2 + v0:d * n2 + v0 + nv])
+        return np.concatenate(parts)
+
     def state(self):
         return fs_get_state(self.prob)
 
@@ -324,3 +476,62 @@ class Stepper:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------------------
+# Continuous-batching request loop
+# ---------------------------------------------------------------------------
+class Server:
+    """Thin wrapper of the fs_server_* calls (the scheduler itself is native)."""
+
+    def __init__(self, hbm_budget, max_slots, setup_threads=4):
+        d = fs_server_desc(int(hbm_budget), int(max_slots), int(setup_threads))
+        self.h = _vp()
+        _check(_lib.fs_server_create(ctypes.byref(d), ctypes.byref(self.h)), "fs_server_create")
+        self.ndof = {}
+
+    def submit(self, wl, nsteps, arrival, precision=FS_PREC_FP32_REFINE, keep_state=False):
+        md = _mesh_desc(wl.dim, wl.n, wl.lo, wl.hi, wl.jitter, wl.seed, wl.side_mask)
+        pd = _problem_desc(_KIND[wl.problem], wl.nu, wl.dt, 0.0, precision,
+                           1 if wl.pin_p0 else 0, 1 if wl.init == "zero_interior" else 0,
+                           wl.wconst or (0.0, 0.0, 0.0))
+        rid = _i64()
+        _check(_lib.fs_server_submit(self.h, ctypes.byref(md), ctypes.byref(pd), int(nsteps),
+                                     float(arrival), 1 if keep_state else 0, ctypes.byref(rid)),
+               "fs_server_submit")
+        self.ndof[rid.value] = wl.ndof
+        return rid.value
+
+    def progress(self, now):
+        n = _int(0)
+        _check(_lib.fs_server_progress(self.h, float(now), ctypes.byref(n)), "fs_server_progress")
+        return n.value
+
+    def completed(self, max_n=4096):
+        arr = (fs_request_result * max_n)()
+        n = _int(0)
+        _check(_lib.fs_server_pop_completed(self.h, arr, max_n, ctypes.byref(n)),
+               "fs_server_pop_completed")
+        return [arr[i].as_dict() for i in range(n.value)]
+
+    def take_state(self, rid):
+        x = np.zeros(self.ndof[rid])
+        _check(_lib.fs_server_take_state(self.h, int(rid), _hptr(x), x.shape[0]),
+               "fs_server_take_state")
+        return x
+
+    def status(self):
+        q, r, b = _int(0), _int(0), _i64(0)
+        _check(_lib.fs_server_status(self.h, ctypes.byref(q), ctypes.byref(r), ctypes.byref(b)),
+               "fs_server_status")
+        return {"queued": q.value, "resident": r.value, "bytes_reserved": b.value}
+
+    def close(self):
+        if self.h:
+            _lib.fs_server_destroy(self.h)
+            self.h = None
+
+
+def fs_server_estimate_bytes(wl, precision=FS_PREC_FP32_REFINE):
+    md = _mesh_desc(wl.dim, wl.n, wl.lo, wl.hi, wl.jitter, wl.seed, wl.side_mask)
+    return int(_lib.fs_server_estimate_bytes(ctypes.byref(md), int(precision)))

@@ -73,3 +73,45 @@ def test_invalid_arguments(fs):
         fs.fs_mesh_create(2, (0, 2), (0, 0), (1, 1))
     with pytest.raises(fs.FsError, match="INVALID_ARG"):
         fs.fs_mesh_create(2, (2, 2), (0, 0), (1, 1), jitter=0.3)
+
+
+def test_batch_mesh_is_union_of_instances(fs):
+    """A batched mesh numbers the instances' meshes as one mesh: instance
+    vertices consecutive, then all edge nodes, then cells; mapped back, each
+    piece is bit-exact against the oracle's mesh of that instance."""
+    wls = [W.unit_square(3), W.unit_square(5, jitter=0.1, seed=2), W.channel(6, 2)]
+    mesh = fs.fs_mesh_create_batch([(w.dim, w.n, w.lo, w.hi, w.jitter, w.seed, w.side_mask)
+                                    for w in wls])
+    try:
+        d = fs.fs_dof_map(mesh)
+        off = fs.fs_mesh_instances(mesh)
+    finally:
+        fs.fs_mesh_destroy(mesh)
+    nv_total = d["n_vert"]
+    assert off.shape == (3, 6)
+    for i, wl in enumerate(wls):
+        P = oracle_problem(wl)
+        v0, nv, e0, ne, c0, nc = (int(a) for a in off[i])
+        assert (nv, ne, nc) == (P.nv, P.n2 - P.nv, P.cells.shape[0])
+        assert np.array_equal(d["coords"][v0:v0 + nv], P.coords)
+        g = d["cell2dof"][c0:c0 + nc].astype(np.int64)
+        local = np.where(g < nv_total, g - v0, g - e0 + nv)
+        assert np.array_equal(local, P.c2d)
+        dmask = np.concatenate([d["dirichlet"][v0:v0 + nv], d["dirichlet"][e0:e0 + ne]])
+        assert np.array_equal(dmask, P.mask)
+
+
+def test_server_estimate_and_rejection(fs):
+    """The admission estimate grows with the mesh and a request larger than
+    the whole budget is refused at submission (host-side, no device work)."""
+    small = fs.fs_server_estimate_bytes(W.unit_square(16))
+    big = fs.fs_server_estimate_bytes(W.unit_square(64))
+    cube = fs.fs_server_estimate_bytes(W.cube(16))
+    assert 0 < small < big < cube
+    srv = fs.Server(small // 2, 2)
+    try:
+        with pytest.raises(fs.FsError, match="OOM"):
+            srv.submit(W.unit_square(16), 1, 0.0)
+        assert srv.status() == {"queued": 0, "resident": 0, "bytes_reserved": 0}
+    finally:
+        srv.close()

@@ -1,0 +1,81 @@
+"""The continuous-batching request loop: requests admitted as slots and
+memory free up, resident requests overlapping on the device, and each
+request's result the same alone and in the mix (within the parity
+tolerance, 1e-9 relative L2)."""
+import time
+
+import numpy as np
+import pytest
+
+import fs_workloads as W
+from tests.gpu_helpers import rel_l2
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+MIX = [(W.unit_square(12, nu=1.0 / 50, jitter=0.0, dt=1e-3), 4),
+       (W.cube(4, nu=1.0 / 20, jitter=0.0, dt=1e-3), 3),
+       (W.unit_square(20, nu=1.0 / 900, jitter=0.0, dt=1e-3), 5),
+       (W.unit_square(7, nu=1.0, jitter=0.0, dt=1e-3), 6),
+       (W.cube(3, nu=1.0 / 300, jitter=0.0, dt=1e-3), 2)]
+
+
+@pytest.fixture(scope="module")
+def fs():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2605_25403_gb300 import build
+    build.build()
+    from paper_2605_25403_gb300 import fs as mod
+    return mod
+
+
+def _run(fs, reqs, budget, slots, keep=True, watch=None):
+    srv = fs.Server(budget, slots)
+    try:
+        t0 = time.perf_counter()
+        ids = [srv.submit(wl, n, 0.0, keep_state=keep) for wl, n in reqs]
+        done = {}
+        while len(done) < len(ids):
+            srv.progress(time.perf_counter() - t0)
+            for r in srv.completed():
+                done[r["id"]] = r
+            if watch is not None:
+                watch(srv.status())
+            assert time.perf_counter() - t0 < 300
+        states = [srv.take_state(i) for i in ids] if keep else None
+        return [done[i] for i in ids], states
+    finally:
+        srv.close()
+
+
+def test_results_same_alone_and_in_the_mix(fs):
+    alone = []
+    for wl, n in MIX:
+        res, st = _run(fs, [(wl, n)], 8 << 30, 1)
+        assert res[0]["status"] == 0
+        alone.append(st[0])
+    res, mixed = _run(fs, MIX, 8 << 30, len(MIX))
+    for (wl, n), r, xa, xm in zip(MIX, res, alone, mixed):
+        assert r["status"] == 0 and r["nsteps"] == n
+        assert rel_l2(xm, xa) <= 1e-9, (wl.name, rel_l2(xm, xa))
+    # the mix ran concurrently: some request started before another finished
+    starts = sorted(r["started"] for r in res)
+    ends = sorted(r["finished"] for r in res)
+    assert starts[1] < ends[0]
+
+
+def test_admission_respects_budget_and_slots(fs):
+    reqs = [(W.unit_square(16, nu=1.0 / 100, jitter=0.0, dt=1e-3), 3) for _ in range(6)]
+    est = fs.fs_server_estimate_bytes(reqs[0][0])
+    seen = []
+    budget = int(2.5 * est)  # room for two requests at a time
+    res, _ = _run(fs, reqs, budget, 4, keep=False, watch=lambda s: seen.append(s))
+    assert all(r["status"] == 0 for r in res)
+    assert max(s["resident"] for s in seen) <= 2
+    assert max(s["bytes_reserved"] for s in seen) <= budget
+    # the estimate bounds the measured footprint
+    assert all(r["device_bytes"] <= est for r in res)
+    # FIFO admission
+    adm = [r["admitted"] for r in res]
+    assert adm == sorted(adm)
