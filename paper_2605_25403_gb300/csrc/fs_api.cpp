@@ -243,6 +243,7 @@ template <typename T>
 int upload_hierarchy(fs_problem* P, const UnionHierarchy& U, int nc, DHier<T>& D) {
   const HostHierarchy& H = U.H;
   D.nlev = (int)H.levels.size();
+  D.ncp = nc == 3 ? 4 : nc;
   if (D.nlev > 16) {
     set_error("multigrid hierarchy deeper than 16 levels");
     return FS_ERR_UNSUPPORTED;
@@ -262,12 +263,12 @@ int upload_hierarchy(fs_problem* P, const UnionHierarchy& U, int nc, DHier<T>& D
     cheb_coeffs<T>(hl.lmax, dl);
     double avg = hl.A.nrow ? (double)hl.A.nnz() / (double)hl.A.nrow : 0;
     dl.lanes = avg >= 20.0 ? 8 : 4;
-    int64_t len = (int64_t)nc * hl.A.nrow;
-    FS_TRY(P->alloc(&D.xw[l], len));
-    FS_TRY(P->alloc(&D.xw2[l], len));
-    FS_TRY(P->alloc(&D.dw[l], len));
-    FS_TRY(P->alloc(&D.dw2[l], len));
-    FS_TRY(P->alloc(&D.bw[l], len));
+    const int64_t rows = hl.A.nrow;
+    // padded components stay zero
+    for (T** v : {&D.b[l], &D.G0[l], &D.G1[l], &D.D0[l], &D.D1[l]}) {
+      FS_TRY(P->alloc(v, (int64_t)D.ncp * rows));
+      FS_CUDA(cudaMemsetAsync(*v, 0, sizeof(T) * D.ncp * rows, P->stream));
+    }
   }
   std::vector<T> ci(U.dense.begin(), U.dense.end());
   T* cinv;
@@ -285,11 +286,13 @@ int upload_hierarchy(fs_problem* P, const UnionHierarchy& U, int nc, DHier<T>& D
   D.blk_dense = bd;
   D.ncoarse = H.ncoarse;
   if (!U.perm.empty()) {
-    int32_t* pm;
+    std::vector<int32_t> inv(U.perm.size());
+    for (size_t r = 0; r < U.perm.size(); ++r) inv[U.perm[r]] = (int32_t)r;
+    int32_t *pm, *ip;
     FS_TRY(P->upload(&pm, U.perm));
+    FS_TRY(P->upload(&ip, inv));
     D.perm = pm;
-    FS_TRY(P->alloc(&D.pin, (int64_t)nc * H.levels[0].A.nrow));
-    FS_TRY(P->alloc(&D.pout, (int64_t)nc * H.levels[0].A.nrow));
+    D.iperm = ip;
   }
   return FS_OK;
 }

@@ -110,33 +110,28 @@ struct DLevel {
 template <typename T>
 struct DHier {
   int nlev = 0;
+  int ncp = 1;  // components per row in the level vectors (1, 2 or 4)
   DLevel<T> lev[16];
   // coarsest level: block-diagonal dense inverses (one block per instance)
-  const T* cinv = nullptr;         // concatenated row-major blocks
+  const T* cinv = nullptr;           // concatenated row-major blocks
   const int32_t* row_blk = nullptr;  // coarsest row -> block
   const int64_t* blk_row = nullptr;  // block -> first row
   const int64_t* blk_n = nullptr;    // block -> size
   const int64_t* blk_dense = nullptr;  // block -> offset in cinv
   int64_t ncoarse = 0;
-  // work vectors per level, nc components each (component stride = nrow):
-  // xw/xw2 ping-pong iterates (xw also holds the level's result), dw/dw2
-  // ping-pong Chebyshev directions, bw the level's right-hand side
-  T* xw[16] = {};
-  T* xw2[16] = {};
-  T* dw[16] = {};
-  T* dw2[16] = {};
-  T* bw[16] = {};
+  // per level (all rows x ncp, row-interleaved components): right-hand
+  // side b, and ping-pong pairs of the gather vector G (x + d, the point the
+  // next residual is taken at) and the Chebyshev direction D
+  T* b[16] = {};
+  T* G0[16] = {};
+  T* G1[16] = {};
+  T* D0[16] = {};
+  T* D1[16] = {};
   // level-0 block order vs the caller's vector order (batches): perm[r] is
-  // the caller's row of block row r; null when they coincide
+  // the caller's row of block row r, iperm its inverse; null when equal
   const int32_t* perm = nullptr;
-  T* pin = nullptr;   // permuted right-hand side (nc x rows)
-  T* pout = nullptr;  // permuted result
+  const int32_t* iperm = nullptr;
 };
-// x = V-cycle(b) for nc right-hand sides (stride ld between components);
-// x must not alias b.
-template <typename T>
-void mg_vcycle(const DHier<T>& H, int nc, const T* b, int64_t ld, T* x,
-               const int* skip, cudaStream_t s);
 
 // One fused Chebyshev step (mode STEP) on level 0 of H with its own work
 // vectors, for kernel timing.

@@ -13,6 +13,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 
 #include "fs_device.h"
 
@@ -53,11 +54,25 @@ __global__ void __launch_bounds__(256) k_spmv_full(DOp<T> op, const V* __restric
   for (int c = 0; c < DIM; ++c) acc[c] = V(0);
   if (row < n2) {
     const int32_t b0 = op.A.rp[row], b1 = op.A.rp[row + 1];
-    for (int32_t k = b0 + lane; k < b1; k += L) {
-      const V a = (V)op.A.v[k];
-      const int32_t c0 = op.A.ci[k];
+    for (int32_t k = b0 + lane; k < b1; k += 4 * L) {
+      V a[4];
+      int32_t j[4];
 #pragma unroll
-      for (int c = 0; c < DIM; ++c) acc[c] += a * x[c * n2 + c0];
+      for (int u = 0; u < 4; ++u) {
+        const int32_t kk = k + u * L;
+        const bool ok = kk < b1;
+        a[u] = ok ? (V)op.A.v[kk] : V(0);
+        j[u] = ok ? op.A.ci[kk] : (int32_t)row;
+      }
+      V xv[4][DIM];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) xv[u][c] = x[c * n2 + j[u]];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) acc[c] += a[u] * xv[u][c];
     }
     const int32_t t0 = op.BT.rp[row], t1 = op.BT.rp[row + 1];
     for (int32_t k = t0 + lane; k < t1; k += L) {
@@ -92,216 +107,345 @@ __global__ void __launch_bounds__(256) k_spmv_full(DOp<T> op, const V* __restric
 }
 
 // ---------------------------------------------------------------------------
-// Multigrid kernels (NC right-hand sides, component stride = level rows)
+// Multigrid V-cycle.  Level vectors are row-major with the components of a
+// row contiguous (nc padded to NCP in {1, 2, 4}), and the Chebyshev iterate x
+// and direction d of a row interleaved: XD[row] = (x[0..NCP), d[0..NCP)).  A
+// neighbour's (x, d) is one 32-byte sector for NCP = 4 in FP32, instead of
+// six scattered loads in a component-blocked layout.
+//
 // Chebyshev smoothing (Saad, Iterative Methods, Alg. 12.1) with Jacobi
-// scaling, one fused SpMV kernel per step:
-//   mode 0 FIRST: x_in = 0, d_in = D^-1 b / theta (implicit)
-//   mode 1 STEP : y = x_in + d_in; r = b - A y; x_out = y;
-//                 d_out = alpha d_in + beta D^-1 r
-//   mode 2 RESID: y = x_in + d_in; x_out = y; d_out = r = b - A y
-//   mode 3 START: y = x_in; d_out = D^-1 (b - A y) / theta
-//   mode 4 LAST : y = x_in + d_in; d = alpha d_in + beta D^-1 r;
-//                 x_out = y + d
+// scaling, one fused SpMV kernel per step; the first step's direction
+// d0 = D^-1 b / theta is written by whichever kernel produces the level's
+// right-hand side (restriction, or the preconditioner's load kernels):
+//   STEP : y = x + d (neighbours); r = b - A y; XDout = (x + d, a d + b D^-1 r)
+//   RESID: y = x + d; XDout = (x + d, r = b - A y)        (r is restricted)
+//   START: y = x;     XDout = (x, D^-1 (b - A y) / theta)
+//   LAST : y = x + d; dn = a d + b D^-1 r; result x + d + dn
 // ---------------------------------------------------------------------------
-template <typename T, int NC, int L, int MODE>
-__global__ void __launch_bounds__(256) k_cheb(DCsr<T> A, const T* __restrict__ dinv,
-                                              const T* __restrict__ b,
-                                              const T* __restrict__ x_in,
-                                              const T* __restrict__ d_in, T inv_theta,
-                                              T alpha, T beta, T* __restrict__ x_out,
-                                              T* __restrict__ d_out, const int* skip) {
+enum { MG_STEP = 0, MG_RESID = 1, MG_START = 2, MG_LAST = 3 };
+
+template <typename T, int N>
+__device__ __forceinline__ void vload(const T* __restrict__ p, T (&v)[N]) {
+  if constexpr (std::is_same<T, float>::value && N == 4) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+  } else if constexpr (std::is_same<T, float>::value && N == 2) {
+    const float2 q = *reinterpret_cast<const float2*>(p);
+    v[0] = q.x; v[1] = q.y;
+  } else if constexpr (std::is_same<T, double>::value && N >= 2) {
+#pragma unroll
+    for (int i = 0; i < N; i += 2) {
+      const double2 q = *reinterpret_cast<const double2*>(p + i);
+      v[i] = q.x; v[i + 1] = q.y;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < N; ++i) v[i] = p[i];
+  }
+}
+
+template <typename T, int N>
+__device__ __forceinline__ void vstore(T* __restrict__ p, const T (&v)[N]) {
+  if constexpr (std::is_same<T, float>::value && N == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  } else if constexpr (std::is_same<T, float>::value && N == 2) {
+    *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+  } else if constexpr (std::is_same<T, double>::value && N >= 2) {
+#pragma unroll
+    for (int i = 0; i < N; i += 2) *reinterpret_cast<double2*>(p + i) = make_double2(v[i], v[i + 1]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < N; ++i) p[i] = v[i];
+  }
+}
+
+// Row loops take kU matrix entries per lane at a time (loads issued before
+// the FMAs); padding entries point at the row itself with coefficient 0.
+constexpr int kU = 4;
+
+// One Chebyshev kernel of a level.  A level's state is kept as two vectors:
+// the gather vector G (the point the next residual is taken at, x + d, read
+// at every neighbour) and the direction D (read at the own row only), so a
+// neighbour costs one NCP-wide load.  Modes, with r = b - A Gin:
+//   STEP : dn = alpha D + beta Dinv r;  Gout = Gin + dn, Dout = dn
+//   RESID: Gout = r                      (Gin = x3 stays for the correction)
+//   START: d0 = Dinv r / theta;         Gout = Gin + d0, Dout = d0  (Gin = x0)
+//   LAST : Gin + alpha D + beta Dinv r, the level's result, to Gout, or on
+//          level 0 (out != null) its first nc components to the caller's
+//          blocked vector at row perm[r].
+template <typename T, int NC, int NCP, int L, int MODE>
+__global__ void __launch_bounds__(256) k_mg(DCsr<T> A, const T* __restrict__ dinv,
+                                            const T* __restrict__ b,
+                                            const T* __restrict__ Gin,
+                                            const T* __restrict__ Din,
+                                            T* __restrict__ Gout, T* __restrict__ Dout,
+                                            T alpha, T beta, T inv_theta, T* __restrict__ out,
+                                            int64_t out_ld, const int32_t* __restrict__ perm,
+                                            int nc, const int* skip) {
   if (skip && *skip) return;
   const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t row = gt / L;
   const int lane = (int)(gt % L);
   const int64_t n = A.nrow;
-  T acc[NC];
+  T acc[NCP];
 #pragma unroll
-  for (int c = 0; c < NC; ++c) acc[c] = T(0);
+  for (int c = 0; c < NCP; ++c) acc[c] = T(0);
   if (row < n) {
     const int32_t b0 = A.rp[row], b1 = A.rp[row + 1];
-    for (int32_t k = b0 + lane; k < b1; k += L) {
-      const T a = A.v[k];
-      const int32_t j = A.ci[k];
+    for (int32_t k = b0 + lane; k < b1; k += kU * L) {
+      T a[kU];
+      int32_t j[kU];
 #pragma unroll
-      for (int c = 0; c < NC; ++c) {
-        const int64_t o = c * n + j;
-        T yj;
-        if (MODE == 0) yj = dinv[j] * b[o] * inv_theta;
-        else if (MODE == 3) yj = x_in[o];
-        else yj = x_in[o] + d_in[o];
-        acc[c] += a * yj;
+      for (int u = 0; u < kU; ++u) {
+        const int32_t kk = k + u * L;
+        const bool ok = kk < b1;
+        a[u] = ok ? A.v[kk] : T(0);
+        j[u] = ok ? A.ci[kk] : (int32_t)row;
       }
+      T g[kU][NCP];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) vload<T, NCP>(Gin + (int64_t)j[u] * NCP, g[u]);
+#pragma unroll
+      for (int u = 0; u < kU; ++u)
+#pragma unroll
+        for (int c = 0; c < NC; ++c) acc[c] += a[u] * g[u][c];
     }
   }
 #pragma unroll
   for (int c = 0; c < NC; ++c) acc[c] = group_sum<L>(acc[c]);
   if (lane != 0 || row >= n) return;
+  T gx[NCP], d[NCP], bb[NCP];
+  vload<T, NCP>(Gin + row * NCP, gx);
+  if (MODE == MG_STEP || MODE == MG_LAST) vload<T, NCP>(Din + row * NCP, d);
+  vload<T, NCP>(b + row * NCP, bb);
   const T di = dinv[row];
+  T go[NCP], dout[NCP];
+#pragma unroll
+  for (int c = 0; c < NCP; ++c) {
+    go[c] = T(0);
+    dout[c] = T(0);
+  }
 #pragma unroll
   for (int c = 0; c < NC; ++c) {
-    const int64_t o = c * n + row;
-    const T r = b[o] - acc[c];
-    if (MODE == 0) {
-      const T d0 = di * b[o] * inv_theta;
-      x_out[o] = d0;
-      d_out[o] = alpha * d0 + beta * di * r;
-    } else if (MODE == 1) {
-      const T dd = d_in[o];
-      x_out[o] = x_in[o] + dd;
-      d_out[o] = alpha * dd + beta * di * r;
-    } else if (MODE == 2) {
-      x_out[o] = x_in[o] + d_in[o];
-      d_out[o] = r;
-    } else if (MODE == 3) {
-      d_out[o] = di * r * inv_theta;
+    const T r = bb[c] - acc[c];
+    if (MODE == MG_STEP) {
+      dout[c] = alpha * d[c] + beta * di * r;
+      go[c] = gx[c] + dout[c];
+    } else if (MODE == MG_RESID) {
+      go[c] = r;
+    } else if (MODE == MG_START) {
+      dout[c] = di * r * inv_theta;
+      go[c] = gx[c] + dout[c];
     } else {
-      const T dd = d_in[o];
-      const T dn = alpha * dd + beta * di * r;
-      x_out[o] = x_in[o] + dd + dn;
+      go[c] = gx[c] + (alpha * d[c] + beta * di * r);
     }
   }
+  if (MODE == MG_LAST && out) {
+    const int64_t dst = perm ? perm[row] : row;
+    for (int c = 0; c < nc; ++c) out[c * out_ld + dst] = go[c];
+    return;
+  }
+  vstore<T, NCP>(Gout + row * NCP, go);
+  if (MODE == MG_STEP || MODE == MG_START) vstore<T, NCP>(Dout + row * NCP, dout);
 }
 
-// y (+)= M x for NC components: add == 0 stores, add == 1 accumulates.
-template <typename T, int NC, int L>
-__global__ void __launch_bounds__(256) k_csr_nc(DCsr<T> M, int64_t ldx, const T* __restrict__ x,
-                                                int64_t ldy, T* __restrict__ y, int add,
-                                                const int* skip) {
+// Restriction of the fine residual Rf to the coarse level: bc = R r, and the
+// coarse level's first step from x = 0: Gc = Dc = d0 = Dinv_c bc / theta.
+template <typename T, int NCP, int L>
+__global__ void __launch_bounds__(256) k_mg_restrict(DCsr<T> R, const T* __restrict__ Rf,
+                                                     T* __restrict__ bc, T* __restrict__ Gc,
+                                                     T* __restrict__ Dc,
+                                                     const T* __restrict__ dinvc,
+                                                     T inv_theta_c, const int* skip) {
   if (skip && *skip) return;
   const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t row = gt / L;
   const int lane = (int)(gt % L);
-  T acc[NC];
+  T acc[NCP];
 #pragma unroll
-  for (int c = 0; c < NC; ++c) acc[c] = T(0);
-  if (row < M.nrow) {
-    for (int32_t k = M.rp[row] + lane; k < M.rp[row + 1]; k += L) {
-      const T a = M.v[k];
-      const int32_t j = M.ci[k];
+  for (int c = 0; c < NCP; ++c) acc[c] = T(0);
+  if (row < R.nrow) {
+    for (int32_t k = R.rp[row] + lane; k < R.rp[row + 1]; k += L) {
+      const T a = R.v[k];
+      T rj[NCP];
+      vload<T, NCP>(Rf + (int64_t)R.ci[k] * NCP, rj);
 #pragma unroll
-      for (int c = 0; c < NC; ++c) acc[c] += a * x[c * ldx + j];
+      for (int c = 0; c < NCP; ++c) acc[c] += a * rj[c];
     }
   }
 #pragma unroll
-  for (int c = 0; c < NC; ++c) acc[c] = group_sum<L>(acc[c]);
-  if (lane != 0 || row >= M.nrow) return;
+  for (int c = 0; c < NCP; ++c) acc[c] = group_sum<L>(acc[c]);
+  if (lane != 0 || row >= R.nrow) return;
+  vstore<T, NCP>(bc + row * NCP, acc);
+  if (!dinvc) return;  // the coarse level is solved densely from bc
+  T d0[NCP];
+  const T s = dinvc[row] * inv_theta_c;
 #pragma unroll
-  for (int c = 0; c < NC; ++c) {
-    const int64_t o = c * ldy + row;
-    y[o] = add ? y[o] + acc[c] : acc[c];
-  }
+  for (int c = 0; c < NCP; ++c) d0[c] = s * acc[c];
+  vstore<T, NCP>(Gc + row * NCP, d0);
+  vstore<T, NCP>(Dc + row * NCP, d0);
 }
 
-// Coarsest solve x = blockdiag(Cinv) b; one warp per row, the row's block
-// found through row_blk.
-template <typename T, int NC>
-__global__ void k_dense(const T* __restrict__ C, const int32_t* __restrict__ row_blk,
-                        const int64_t* __restrict__ blk_row, const int64_t* __restrict__ blk_n,
-                        const int64_t* __restrict__ blk_dense, int64_t n,
-                        const T* __restrict__ b, T* __restrict__ x, const int* skip) {
+// Correction x0 = x3 + P xc, in place in the fine gather vector Gf (each row
+// reads and writes only its own entry there; the gathers are from Xc).
+template <typename T, int NCP, int L>
+__global__ void __launch_bounds__(256) k_mg_prolong(DCsr<T> P, const T* __restrict__ Xc,
+                                                    T* __restrict__ Gf, const int* skip) {
+  if (skip && *skip) return;
+  const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t row = gt / L;
+  const int lane = (int)(gt % L);
+  T acc[NCP];
+#pragma unroll
+  for (int c = 0; c < NCP; ++c) acc[c] = T(0);
+  if (row < P.nrow) {
+    for (int32_t k = P.rp[row] + lane; k < P.rp[row + 1]; k += L) {
+      const T a = P.v[k];
+      T xj[NCP];
+      vload<T, NCP>(Xc + (int64_t)P.ci[k] * NCP, xj);
+#pragma unroll
+      for (int c = 0; c < NCP; ++c) acc[c] += a * xj[c];
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < NCP; ++c) acc[c] = group_sum<L>(acc[c]);
+  if (lane != 0 || row >= P.nrow) return;
+  T x[NCP];
+  vload<T, NCP>(Gf + row * NCP, x);
+#pragma unroll
+  for (int c = 0; c < NCP; ++c) x[c] += acc[c];
+  vstore<T, NCP>(Gf + row * NCP, x);
+}
+
+// Coarsest solve x = blockdiag(Cinv) b, one warp per row; the result goes to
+// X (gathered by the parent's prolongation), or (level 0 being the coarsest)
+// to the caller's blocked out.
+template <typename T, int NCP>
+__global__ void k_mg_dense(const T* __restrict__ C, const int32_t* __restrict__ row_blk,
+                           const int64_t* __restrict__ blk_row, const int64_t* __restrict__ blk_n,
+                           const int64_t* __restrict__ blk_dense, int64_t n,
+                           const T* __restrict__ b, T* __restrict__ X, T* __restrict__ out,
+                           int64_t out_ld, const int32_t* __restrict__ perm, int nc,
+                           const int* skip) {
   if (skip && *skip) return;
   const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32;
   const int lane = threadIdx.x & 31;
-  T acc[NC];
+  T acc[NCP];
 #pragma unroll
-  for (int c = 0; c < NC; ++c) acc[c] = T(0);
+  for (int c = 0; c < NCP; ++c) acc[c] = T(0);
   if (row < n) {
     const int blk = row_blk[row];
     const int64_t r0 = blk_row[blk], nb = blk_n[blk];
     const T* Cr = C + blk_dense[blk] + (row - r0) * nb;
     for (int64_t j = lane; j < nb; j += 32) {
       const T a = Cr[j];
+      T bj[NCP];
+      vload<T, NCP>(b + (r0 + j) * NCP, bj);
 #pragma unroll
-      for (int c = 0; c < NC; ++c) acc[c] += a * b[c * n + r0 + j];
+      for (int c = 0; c < NCP; ++c) acc[c] += a * bj[c];
     }
   }
 #pragma unroll
-  for (int c = 0; c < NC; ++c) acc[c] = group_sum<32>(acc[c]);
-  if (lane == 0 && row < n)
-#pragma unroll
-    for (int c = 0; c < NC; ++c) x[c * n + row] = acc[c];
+  for (int c = 0; c < NCP; ++c) acc[c] = group_sum<32>(acc[c]);
+  if (lane != 0 || row >= n) return;
+  if (out) {
+    const int64_t dst = perm ? perm[row] : row;
+    for (int c = 0; c < nc; ++c) out[c * out_ld + dst] = acc[c];
+  } else {
+    vstore<T, NCP>(X + row * NCP, acc);
+  }
 }
 
-template <typename T, int NC>
-void vcycle_level(const DHier<T>& H, int l, const T* b, T* out, const int* skip,
+template <typename T, int NCP>
+void launch_mg(int mode, const DLevel<T>& L, const T* b, const T* Gin, const T* Din, T* Gout,
+               T* Dout, T alpha, T beta, T* out, int64_t out_ld, const int32_t* perm, int nc,
+               const int* skip, cudaStream_t s) {
+  const int64_t n = L.A.nrow;
+  const T it = (T)L.inv_theta;
+  constexpr int NC = NCP == 4 ? 3 : NCP;  // real components (3D pads 3 to 4)
+#define FS_MG(M, LN)                                                                         \
+  k_mg<T, NC, NCP, LN, M><<<blocks_for(n * LN), 256, 0, s>>>(L.A, L.dinv, b, Gin, Din, Gout, \
+                                                             Dout, alpha, beta, it, out,    \
+                                                             out_ld, perm, nc, skip)
+  if (L.lanes == 8) {
+    if (mode == MG_STEP) FS_MG(MG_STEP, 8);
+    else if (mode == MG_RESID) FS_MG(MG_RESID, 8);
+    else if (mode == MG_START) FS_MG(MG_START, 8);
+    else FS_MG(MG_LAST, 8);
+  } else {
+    if (mode == MG_STEP) FS_MG(MG_STEP, 4);
+    else if (mode == MG_RESID) FS_MG(MG_RESID, 4);
+    else if (mode == MG_START) FS_MG(MG_START, 4);
+    else FS_MG(MG_LAST, 4);
+  }
+#undef FS_MG
+  count_launches(1);
+}
+
+// V-cycle below a level whose right-hand side b_l and first step (G0, D0)
+// are in place; the level's result ends in G1[l], or in `out` for level 0.
+template <typename T, int NCP>
+void vcycle_level(const DHier<T>& H, int l, T* out, int64_t out_ld, int nc, const int* skip,
                   cudaStream_t s) {
+  const bool top = l == 0;
   if (l == H.nlev - 1) {
     const int64_t n = H.ncoarse;
-    k_dense<T, NC><<<blocks_for(n * 32), 256, 0, s>>>(H.cinv, H.row_blk, H.blk_row, H.blk_n,
-                                                      H.blk_dense, n, b, out, skip);
+    k_mg_dense<T, NCP><<<blocks_for(n * 32), 256, 0, s>>>(
+        H.cinv, H.row_blk, H.blk_row, H.blk_n, H.blk_dense, n, H.b[l], H.G1[l],
+        top ? out : nullptr, out_ld, top ? H.perm : nullptr, nc, skip);
     count_launches(1);
     return;
   }
   const DLevel<T>& L = H.lev[l];
-  const int64_t n = L.A.nrow;
-  const unsigned g4 = blocks_for(n * 4), g8 = blocks_for(n * 8);
-  T *X0 = H.xw[l], *X1 = H.xw2[l], *D0 = H.dw[l], *D1 = H.dw2[l];
-  // the coarse right-hand side lives in bw[l+1] and its solution in xw[l+1]
-  const T it = (T)L.inv_theta, a1 = (T)L.a1, b1 = (T)L.b1, a2 = (T)L.a2, b2 = (T)L.b2;
-#define FS_CHEB(MODE, XI, DI, AL, BE, XO, DO)                                          \
-  do {                                                                                \
-    if (L.lanes == 8)                                                                 \
-      k_cheb<T, NC, 8, MODE><<<g8, 256, 0, s>>>(L.A, L.dinv, b, XI, DI, it, AL, BE, XO, \
-                                                DO, skip);                            \
-    else                                                                              \
-      k_cheb<T, NC, 4, MODE><<<g4, 256, 0, s>>>(L.A, L.dinv, b, XI, DI, it, AL, BE, XO, \
-                                                DO, skip);                            \
-    count_launches(1);                                                                \
-  } while (0)
-  // pre-smoothing: x1 = d0, d1; x2, d2; x3 = x2 + d2, r3
-  FS_CHEB(0, nullptr, nullptr, a1, b1, X0, D0);
-  FS_CHEB(1, X0, D0, a2, b2, X1, D1);
-  FS_CHEB(2, X1, D1, T(0), T(0), X0, D0);
-  // restrict r3 to the coarse right-hand side
   const DLevel<T>& C = H.lev[l + 1];
-  const int64_t nc_rows = C.A.nrow;
-  {
-    DCsr<T> R = L.R;
-    k_csr_nc<T, NC, 4><<<blocks_for(R.nrow * 4), 256, 0, s>>>(R, n, D0, nc_rows, H.bw[l + 1], 0,
-                                                               skip);
-    count_launches(1);
-  }
-  vcycle_level<T, NC>(H, l + 1, H.bw[l + 1], H.xw[l + 1], skip, s);
-  // prolongate and correct
-  {
-    DCsr<T> P = L.P;
-    k_csr_nc<T, NC, 4><<<blocks_for(P.nrow * 4), 256, 0, s>>>(P, nc_rows, H.xw[l + 1], n, X0, 1,
-                                                               skip);
-    count_launches(1);
-  }
-  // post-smoothing from x0 = X0
-  FS_CHEB(3, X0, nullptr, T(0), T(0), nullptr, D0);
-  FS_CHEB(1, X0, D0, a1, b1, X1, D1);
-  FS_CHEB(4, X1, D1, a2, b2, out, nullptr);
-#undef FS_CHEB
-}
-
-// out[c][r] = in[c][perm[r]] (gather) or out[c][perm[r]] = in[c][r] (scatter)
-template <typename T>
-__global__ void k_permute(const int32_t* __restrict__ perm, int64_t n, int nc,
-                          const T* __restrict__ in, T* __restrict__ out, int scatter,
-                          const int* skip) {
-  if (skip && *skip) return;
-  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
-       r += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t p = perm[r];
-    for (int c = 0; c < nc; ++c) {
-      if (scatter) out[c * n + p] = in[c * n + r];
-      else out[c * n + r] = in[c * n + p];
-    }
-  }
+  const T a1 = (T)L.a1, b1 = (T)L.b1, a2 = (T)L.a2, b2 = (T)L.b2;
+  T *G0 = H.G0[l], *G1 = H.G1[l], *D0 = H.D0[l], *D1 = H.D1[l];
+  const T* b = H.b[l];
+  launch_mg<T, NCP>(MG_STEP, L, b, G0, D0, G1, D1, a1, b1, nullptr, 0, nullptr, nc, skip, s);
+  launch_mg<T, NCP>(MG_STEP, L, b, G1, D1, G0, D0, a2, b2, nullptr, 0, nullptr, nc, skip, s);
+  // residual of x3 = G0 into G1; G0 keeps x3 for the correction
+  launch_mg<T, NCP>(MG_RESID, L, b, G0, D0, G1, nullptr, T(0), T(0), nullptr, 0, nullptr, nc,
+                    skip, s);
+  const bool coarsest_next = l + 1 == H.nlev - 1;
+  k_mg_restrict<T, NCP, 4><<<blocks_for(L.R.nrow * 4), 256, 0, s>>>(
+      L.R, G1, H.b[l + 1], H.G0[l + 1], H.D0[l + 1], coarsest_next ? nullptr : C.dinv,
+      (T)C.inv_theta, skip);
+  count_launches(1);
+  vcycle_level<T, NCP>(H, l + 1, nullptr, 0, nc, skip, s);
+  k_mg_prolong<T, NCP, 4><<<blocks_for(L.P.nrow * 4), 256, 0, s>>>(L.P, H.G1[l + 1], G0, skip);
+  count_launches(1);
+  launch_mg<T, NCP>(MG_START, L, b, G0, nullptr, G1, D1, T(0), T(0), nullptr, 0, nullptr, nc,
+                    skip, s);
+  launch_mg<T, NCP>(MG_STEP, L, b, G1, D1, G0, D0, a1, b1, nullptr, 0, nullptr, nc, skip, s);
+  launch_mg<T, NCP>(MG_LAST, L, b, G0, D0, G1, nullptr, a2, b2, top ? out : nullptr, out_ld,
+                    top ? H.perm : nullptr, nc, skip, s);
 }
 
 // ---------------------------------------------------------------------------
 // Block preconditioner pieces
 // ---------------------------------------------------------------------------
-// z_p = nu Mp^-1 r_p + dt^-1 y_K ; pinned rows: z_p = r_p
+// Load of a single-component level-0 right-hand side: b0 = r and the first
+// step from x = 0, G0 = D0 = D^-1 r / theta.
+template <typename T>
+__global__ void k_mg_load1(int64_t n, const T* __restrict__ r, const T* __restrict__ dinv0,
+                           T inv_theta0, T* __restrict__ b0, T* __restrict__ G0,
+                           T* __restrict__ D0, const int* skip) {
+  if (skip && *skip) return;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const T v = r[q];
+    const T d0 = dinv0 ? dinv0[q] * v * inv_theta0 : T(0);
+    b0[q] = v;
+    G0[q] = d0;
+    D0[q] = d0;
+  }
+}
+
+// z_p = nu Mp^-1 r_p + dt^-1 y_K ; then pinned rows: z_p = r_p
 template <typename T>
 __global__ void k_prec_p(int64_t nv, const T* __restrict__ rp, const T* __restrict__ yk,
-                         const T* __restrict__ mpl_inv_nu, T inv_dt,
-                         const int32_t* __restrict__ pinned, int npinned,
-                         T* __restrict__ zp, const int* skip) {
+                         const T* __restrict__ mpl_inv_nu, T inv_dt, T* __restrict__ zp,
+                         const int* skip) {
   if (skip && *skip) return;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nv;
        q += (int64_t)gridDim.x * blockDim.x)
@@ -315,11 +459,18 @@ __global__ void k_pin_rows(const int32_t* __restrict__ pinned, int npinned,
   if (t < npinned) zp[pinned[t]] = rp[pinned[t]];
 }
 
-// t_c = r_c + BT_c z_p over the velocity rows
-template <typename T, int DIM, int L>
-__global__ void __launch_bounds__(256) k_bt_add(DCsr<T> BT, int64_t n2, const T* __restrict__ r,
-                                                const T* __restrict__ zp, T* __restrict__ t,
-                                                const int* skip) {
+// Velocity right-hand side of the V-cycle, written straight into level 0:
+// t_c = r_c + BT_c z_p over the velocity rows (caller order), stored at the
+// level-0 (block-order) row iperm[i] as b0, with the first step from x = 0,
+// G0 = D0 = D^-1 t / theta.
+template <typename T, int DIM, int NCP, int L>
+__global__ void __launch_bounds__(256) k_bt_add_mg(DCsr<T> BT, int64_t n2,
+                                                   const T* __restrict__ r,
+                                                   const T* __restrict__ zp,
+                                                   const int32_t* __restrict__ iperm,
+                                                   const T* __restrict__ dinv0, T inv_theta0,
+                                                   T* __restrict__ b0, T* __restrict__ G0,
+                                                   T* __restrict__ D0, const int* skip) {
   if (skip && *skip) return;
   const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t row = gt / L;
@@ -336,9 +487,18 @@ __global__ void __launch_bounds__(256) k_bt_add(DCsr<T> BT, int64_t n2, const T*
   }
 #pragma unroll
   for (int c = 0; c < DIM; ++c) acc[c] = group_sum<L>(acc[c]);
-  if (lane == 0 && row < n2)
+  if (lane != 0 || row >= n2) return;
+  const int64_t dst = iperm ? iperm[row] : row;
+  T t[NCP], d0[NCP];
+  const T s = dinv0 ? dinv0[dst] * inv_theta0 : T(0);
 #pragma unroll
-    for (int c = 0; c < DIM; ++c) t[c * n2 + row] = r[c * n2 + row] + acc[c];
+  for (int c = 0; c < NCP; ++c) {
+    t[c] = c < DIM ? r[c * n2 + row] + acc[c] : T(0);
+    d0[c] = s * t[c];
+  }
+  vstore<T, NCP>(b0 + dst * NCP, t);
+  vstore<T, NCP>(G0 + dst * NCP, d0);
+  vstore<T, NCP>(D0 + dst * NCP, d0);
 }
 
 template <typename A, typename B>
@@ -368,14 +528,13 @@ void launch_spmv_full(const DOp<T>& op, const V* x, const V* b, V* y, int resid,
       k_spmv_full<T, V, 2, 8><<<blocks_for(rows * 8), 256, 0, s>>>(op, x, b, y, resid, skip);
     else
       k_spmv_full<T, V, 2, 4><<<blocks_for(rows * 4), 256, 0, s>>>(op, x, b, y, resid, skip);
-      count_launches(1);
   } else {
     if (lanes == 4)
       k_spmv_full<T, V, 3, 4><<<blocks_for(rows * 4), 256, 0, s>>>(op, x, b, y, resid, skip);
     else
       k_spmv_full<T, V, 3, 8><<<blocks_for(rows * 8), 256, 0, s>>>(op, x, b, y, resid, skip);
-      count_launches(1);
   }
+  count_launches(1);
 }
 template void launch_spmv_full<double, double>(const DOp<double>&, const double*, const double*,
                                                double*, int, const int*, int, cudaStream_t);
@@ -384,82 +543,62 @@ template void launch_spmv_full<float, float>(const DOp<float>&, const float*, co
 
 template <typename T>
 void launch_cheb_step(const DHier<T>& H, int nc, cudaStream_t s) {
+  (void)nc;
   const DLevel<T>& L = H.lev[0];
-  const int64_t n = L.A.nrow;
-  const T it = (T)L.inv_theta, a1 = (T)L.a1, b1 = (T)L.b1;
-#define FS_STEP(NCV)                                                                   \
-  if (L.lanes == 8)                                                                    \
-    k_cheb<T, NCV, 8, 1><<<blocks_for(n * 8), 256, 0, s>>>(L.A, L.dinv, H.bw[0], H.xw[0], \
-                                                           H.dw[0], it, a1, b1, H.xw2[0],  \
-                                                           H.dw2[0], nullptr);          \
-  else                                                                                 \
-    k_cheb<T, NCV, 4, 1><<<blocks_for(n * 4), 256, 0, s>>>(L.A, L.dinv, H.bw[0], H.xw[0], \
-                                                           H.dw[0], it, a1, b1, H.xw2[0],  \
-                                                           H.dw2[0], nullptr);
-  if (nc == 2) {
-    FS_STEP(2)
-  } else if (nc == 3) {
-    FS_STEP(3)
-  } else {
-    FS_STEP(1)
-  }
-#undef FS_STEP
-  count_launches(1);
+  if (H.ncp == 4)
+    launch_mg<T, 4>(MG_STEP, L, H.b[0], H.G0[0], H.D0[0], H.G1[0], H.D1[0], (T)L.a1, (T)L.b1,
+                    nullptr, 0, nullptr, 3, nullptr, s);
+  else if (H.ncp == 2)
+    launch_mg<T, 2>(MG_STEP, L, H.b[0], H.G0[0], H.D0[0], H.G1[0], H.D1[0], (T)L.a1, (T)L.b1,
+                    nullptr, 0, nullptr, 2, nullptr, s);
+  else
+    launch_mg<T, 1>(MG_STEP, L, H.b[0], H.G0[0], H.D0[0], H.G1[0], H.D1[0], (T)L.a1, (T)L.b1,
+                    nullptr, 0, nullptr, 1, nullptr, s);
 }
 template void launch_cheb_step<double>(const DHier<double>&, int, cudaStream_t);
 template void launch_cheb_step<float>(const DHier<float>&, int, cudaStream_t);
-
-template <typename T>
-void mg_vcycle(const DHier<T>& H, int nc, const T* b, int64_t ld, T* x, const int* skip,
-               cudaStream_t s) {
-  (void)ld;  // level-0 vectors are stored with stride = level rows
-  const T* bb = b;
-  T* xx = x;
-  const int64_t n0 = H.lev[0].A.nrow;
-  const unsigned gp = (unsigned)std::min<int64_t>((n0 + 255) / 256, 152 * 16);
-  if (H.perm) {  // into block order
-    k_permute<T><<<gp, 256, 0, s>>>(H.perm, n0, nc, b, H.pin, 0, skip);
-    count_launches(1);
-    bb = H.pin;
-    xx = H.pout;
-  }
-  if (nc == 1) vcycle_level<T, 1>(H, 0, bb, xx, skip, s);
-  else if (nc == 2) vcycle_level<T, 2>(H, 0, bb, xx, skip, s);
-  else vcycle_level<T, 3>(H, 0, bb, xx, skip, s);
-  if (H.perm) {  // back to the caller's order
-    k_permute<T><<<gp, 256, 0, s>>>(H.perm, n0, nc, H.pout, x, 1, skip);
-    count_launches(1);
-  }
-}
-template void mg_vcycle<double>(const DHier<double>&, int, const double*, int64_t, double*,
-                                const int*, cudaStream_t);
-template void mg_vcycle<float>(const DHier<float>&, int, const float*, int64_t, float*,
-                               const int*, cudaStream_t);
 
 template <typename T>
 void launch_precond(const DOp<T>& op, const DHier<T>& HA, const DHier<T>& HK,
                     const T* mpl_inv_nu, double inv_dt, const int32_t* pinned,
                     int npinned, const T* r, T* z, T* work_p, T* work_u,
                     const int* skip, cudaStream_t s) {
+  (void)work_u;
   const int64_t n2 = op.n2, nv = op.nv;
   const int dim = op.dim;
   const T* rp = r + dim * n2;
   T* zp = z + dim * n2;
   // pressure: Cahouet-Chabard  z_p = nu Mp^-1 r_p + dt^-1 Kp^-1 r_p
-  mg_vcycle<T>(HK, 1, rp, nv, work_p, skip, s);
-  k_prec_p<T><<<grid_stride_blocks(nv), 256, 0, s>>>(nv, rp, work_p, mpl_inv_nu, (T)inv_dt,
-                                                     pinned, npinned, zp, skip);
+  {
+    const bool k1 = HK.nlev > 1;
+    k_mg_load1<T><<<grid_stride_blocks(nv), 256, 0, s>>>(
+        nv, rp, k1 ? HK.lev[0].dinv : nullptr, (T)HK.lev[0].inv_theta, HK.b[0], HK.G0[0],
+        HK.D0[0], skip);
+    count_launches(1);
+    vcycle_level<T, 1>(HK, 0, work_p, nv, 1, skip, s);
+  }
+  k_prec_p<T><<<grid_stride_blocks(nv), 256, 0, s>>>(nv, rp, work_p, mpl_inv_nu, (T)inv_dt, zp,
+                                                     skip);
   count_launches(1);
-  if (npinned > 0)
+  if (npinned > 0) {
     k_pin_rows<T><<<blocks_for(npinned), 256, 0, s>>>(pinned, npinned, rp, zp, skip);
     count_launches(1);
+  }
   // velocity: z_u = A^-1 (r_u + BT z_p) by one V-cycle on all components
-  if (dim == 2)
-    k_bt_add<T, 2, 4><<<blocks_for(n2 * 4), 256, 0, s>>>(op.BT, n2, r, zp, work_u, skip);
-  else
-    k_bt_add<T, 3, 4><<<blocks_for(n2 * 4), 256, 0, s>>>(op.BT, n2, r, zp, work_u, skip);
+  const bool a1 = HA.nlev > 1;
+  const T* d0 = a1 ? HA.lev[0].dinv : nullptr;
+  const T it0 = (T)HA.lev[0].inv_theta;
+  if (dim == 2) {
+    k_bt_add_mg<T, 2, 2, 4><<<blocks_for(n2 * 4), 256, 0, s>>>(op.BT, n2, r, zp, HA.iperm, d0, it0,
+                                                             HA.b[0], HA.G0[0], HA.D0[0], skip);
     count_launches(1);
-  mg_vcycle<T>(HA, dim, work_u, n2, z, skip, s);
+    vcycle_level<T, 2>(HA, 0, z, n2, 2, skip, s);
+  } else {
+    k_bt_add_mg<T, 3, 4, 4><<<blocks_for(n2 * 4), 256, 0, s>>>(op.BT, n2, r, zp, HA.iperm, d0, it0,
+                                                             HA.b[0], HA.G0[0], HA.D0[0], skip);
+    count_launches(1);
+    vcycle_level<T, 4>(HA, 0, z, n2, 3, skip, s);
+  }
 }
 template void launch_precond<double>(const DOp<double>&, const DHier<double>&,
                                      const DHier<double>&, const double*, double,

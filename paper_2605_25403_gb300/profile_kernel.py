@@ -1,0 +1,48 @@
+"""Times one hot kernel of the step on a workload's own data (CUDA events on
+the problem's stream) and prints one JSON line: mean duration, algorithmic
+bytes per launch and the resulting GB/s.
+
+    python -m paper_2605_25403_gb300.profile_kernel --workload cube --kernel cheb --reps 20
+
+The kernel runs exactly `3 + reps` times after the problem's set-up and one
+assembly, so a profiler can select its first launches by name.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def main(argv=None):
+    p = argparse.ArgumentParser()
+    p.add_argument("--workload", default="cube", choices=["channel", "cube", "unit_square"])
+    p.add_argument("--kernel", default="cheb", choices=["cheb", "spmv", "spmv_fp64", "assemble"])
+    p.add_argument("--precision", default="fp32_refine", choices=["fp32_refine", "fp64"])
+    p.add_argument("--reps", type=int, default=20)
+    a = p.parse_args(argv)
+    import fs_workloads as W
+    from paper_2605_25403_gb300 import build
+    build.build()
+    from paper_2605_25403_gb300 import fs
+    wl = {"channel": W.C2, "cube": W.C3, "unit_square": W.C1}[a.workload]
+    prec = fs.FS_PREC_FP32_REFINE if a.precision == "fp32_refine" else fs.FS_PREC_FP64
+    kid = {"cheb": fs.FS_KERNEL_CHEB, "spmv": fs.FS_KERNEL_SPMV,
+           "spmv_fp64": fs.FS_KERNEL_SPMV_FP64, "assemble": fs.FS_KERNEL_ASSEMBLE_CONV}[a.kernel]
+    S = fs.Stepper.from_workload(wl, precision=prec)
+    try:
+        ms, by = fs.fs_profile_kernel(S.prob, kid, reps=a.reps)
+    finally:
+        S.close()
+    print(json.dumps({"workload": wl.name, "kernel": a.kernel, "precision": a.precision,
+                      "ms": ms, "alg_bytes": by, "gbs": by / ms / 1e6}))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
