@@ -223,6 +223,50 @@ int upload_csr(fs_problem* P, const HostCsr& H, DCsr<T>& d) {
   return FS_OK;
 }
 
+// Sliced ELLPACK copy of a CSR matrix (slices of 32 rows, slot-major within
+// a slice, padding slots with coefficient 0 pointing at the row itself).
+template <typename T>
+int upload_sell(fs_problem* P, const HostCsr& H, DSell<T>& d) {
+  const int64_t n = H.nrow, ns = (n + 31) / 32;
+  std::vector<int64_t> off(ns + 1, 0);
+  for (int64_t sl = 0; sl < ns; ++sl) {
+    int64_t w = 0;
+    for (int64_t r = 32 * sl; r < std::min(n, 32 * sl + 32); ++r)
+      w = std::max<int64_t>(w, H.rowptr[r + 1] - H.rowptr[r]);
+    off[sl + 1] = off[sl] + 32 * w;
+  }
+  std::vector<int32_t> ci(off[ns], 0);
+  std::vector<T> v(off[ns], T(0));
+  for (int64_t sl = 0; sl < ns; ++sl) {
+    const int64_t w = (off[sl + 1] - off[sl]) / 32;
+    for (int t = 0; t < 32; ++t) {
+      const int64_t r = 32 * sl + t;
+      if (r >= n) break;
+      const int64_t len = H.rowptr[r + 1] - H.rowptr[r];
+      for (int64_t u = 0; u < w; ++u) {
+        const int64_t o = off[sl] + 32 * u + t;
+        if (u < len) {
+          ci[o] = H.col[H.rowptr[r] + u];
+          v[o] = (T)H.val[H.rowptr[r] + u];
+        } else {
+          ci[o] = (int32_t)r;
+        }
+      }
+    }
+  }
+  int64_t* doff;
+  int32_t* dci;
+  T* dv;
+  FS_TRY(P->upload(&doff, off));
+  FS_TRY(P->upload(&dci, ci));
+  FS_TRY(P->upload(&dv, v));
+  d.nrow = n;
+  d.off = doff;
+  d.ci = dci;
+  d.v = dv;
+  return FS_OK;
+}
+
 // Chebyshev(3) coefficients on [lmax/8, 1.1 lmax] of D^-1 A.
 template <typename T>
 void cheb_coeffs(double lmax, DLevel<T>& L) {
@@ -251,7 +295,7 @@ int upload_hierarchy(fs_problem* P, const UnionHierarchy& U, int nc, DHier<T>& D
   for (int l = 0; l < D.nlev; ++l) {
     const HostLevel& hl = H.levels[l];
     DLevel<T>& dl = D.lev[l];
-    FS_TRY(upload_csr<T>(P, hl.A, dl.A));
+    FS_TRY(upload_sell<T>(P, hl.A, dl.A));
     if (l + 1 < D.nlev) {
       FS_TRY(upload_csr<T>(P, hl.P, dl.P));
       FS_TRY(upload_csr<T>(P, hl.R, dl.R));
@@ -261,8 +305,6 @@ int upload_hierarchy(fs_problem* P, const UnionHierarchy& U, int nc, DHier<T>& D
     FS_TRY(P->upload(&dinv, di));
     dl.dinv = dinv;
     cheb_coeffs<T>(hl.lmax, dl);
-    double avg = hl.A.nrow ? (double)hl.A.nnz() / (double)hl.A.nrow : 0;
-    dl.lanes = avg >= 20.0 ? 8 : 4;
     const int64_t rows = hl.A.nrow;
     // padded components stay zero
     for (T** v : {&D.b[l], &D.G0[l], &D.G1[l], &D.D0[l], &D.D1[l]}) {

@@ -26,6 +26,18 @@ struct DCsr {
   const T* v = nullptr;
 };
 
+// Sliced ELLPACK with slices of 32 rows (one thread per row): the entries of
+// row 32 s + t sit at off[s] + 32 u + t for the slot u < (off[s+1] - off[s]) / 32,
+// so a warp's loads of one slot are contiguous.  Slots past a row's length
+// hold coefficient 0 and the row itself as column.
+template <typename T>
+struct DSell {
+  int64_t nrow = 0;
+  const int64_t* off = nullptr;
+  const int32_t* ci = nullptr;
+  const T* v = nullptr;
+};
+
 // Mesh tables and block patterns of one problem on the device.
 struct DMesh {
   int dim = 0, nloc = 0, nb = 0;
@@ -102,10 +114,10 @@ void launch_spmv_full(const DOp<T>& op, const V* x, const V* b, V* y,
 // Multigrid level on the device.
 template <typename T>
 struct DLevel {
-  DCsr<T> A, P, R;      // P: prolongation from level+1, R = P^T
+  DSell<T> A;           // level operator
+  DCsr<T> P, R;         // P: prolongation from level+1, R = P^T
   const T* dinv = nullptr;
   double inv_theta = 0, a1 = 0, b1 = 0, a2 = 0, b2 = 0;  // Chebyshev(3)
-  int lanes = 4;
 };
 template <typename T>
 struct DHier {

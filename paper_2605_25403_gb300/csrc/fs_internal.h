@@ -89,11 +89,16 @@ struct HostLevel {
   HostCsr R;          // restriction = P^T
   std::vector<double> dinv;
   double lmax = 0;    // estimate of the largest eigenvalue of D^-1 A
+  int grid[3] = {1, 1, 1};  // structured mesh of the level (cells per axis)
+  bool p2 = false;          // the level is the P2 space of that mesh
 };
 struct HostHierarchy {
   std::vector<HostLevel> levels;   // levels[0] finest; last = coarsest
   std::vector<double> coarse_inv;  // dense inverse of the coarsest operator
   int64_t ncoarse = 0;
+  // Level-0 rows of a P2 hierarchy are stored grouped by node class (see
+  // the multigrid builder); order0[r] is the mesh-numbered row of level-0 row r.
+  std::vector<int32_t> order0;
 };
 // Builds a hierarchy: A0 (square CSR with values), the structured mesh size
 // n0 (cells per axis) of the P1 levels, whether level 0 is the P2 space of
@@ -117,9 +122,8 @@ struct UnionHierarchy {
   std::vector<int64_t> blk_dense;    // ... offset of its dense inverse
   std::vector<double> dense;         // concatenated dense inverses (row-major)
   std::vector<int32_t> row_blk;      // coarsest row -> instance
-  // level-0 rows are in instance-major (block) order; when that differs
-  // from the union numbering (P2 nodes of several instances), perm[r] is
-  // the union row of block row r; empty otherwise
+  // level-0 rows are in instance-major (block) order, each instance's rows
+  // in class order; perm[r] is the union row of block row r
   std::vector<int32_t> perm;
 };
 void build_union_hierarchy(const Mesh& m, const std::vector<Mesh>& local,

@@ -173,8 +173,8 @@ constexpr int kU = 4;
 //   LAST : Gin + alpha D + beta Dinv r, the level's result, to Gout, or on
 //          level 0 (out != null) its first nc components to the caller's
 //          blocked vector at row perm[r].
-template <typename T, int NC, int NCP, int L, int MODE>
-__global__ void __launch_bounds__(256) k_mg(DCsr<T> A, const T* __restrict__ dinv,
+template <typename T, int NC, int NCP, int MODE>
+__global__ void __launch_bounds__(256) k_mg(DSell<T> A, const T* __restrict__ dinv,
                                             const T* __restrict__ b,
                                             const T* __restrict__ Gin,
                                             const T* __restrict__ Din,
@@ -183,37 +183,31 @@ __global__ void __launch_bounds__(256) k_mg(DCsr<T> A, const T* __restrict__ din
                                             int64_t out_ld, const int32_t* __restrict__ perm,
                                             int nc, const int* skip) {
   if (skip && *skip) return;
-  const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t row = gt / L;
-  const int lane = (int)(gt % L);
-  const int64_t n = A.nrow;
+  const int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (row >= A.nrow) return;
+  const int64_t o0 = A.off[row >> 5] + (row & 31), o1 = A.off[(row >> 5) + 1];
   T acc[NCP];
 #pragma unroll
   for (int c = 0; c < NCP; ++c) acc[c] = T(0);
-  if (row < n) {
-    const int32_t b0 = A.rp[row], b1 = A.rp[row + 1];
-    for (int32_t k = b0 + lane; k < b1; k += kU * L) {
-      T a[kU];
-      int32_t j[kU];
+  // the slot count is the same for the whole slice: no divergence
+  for (int64_t o = o0; o < o1; o += kU * 32) {
+    T a[kU];
+    int32_t j[kU];
 #pragma unroll
-      for (int u = 0; u < kU; ++u) {
-        const int32_t kk = k + u * L;
-        const bool ok = kk < b1;
-        a[u] = ok ? A.v[kk] : T(0);
-        j[u] = ok ? A.ci[kk] : (int32_t)row;
-      }
-      T g[kU][NCP];
-#pragma unroll
-      for (int u = 0; u < kU; ++u) vload<T, NCP>(Gin + (int64_t)j[u] * NCP, g[u]);
-#pragma unroll
-      for (int u = 0; u < kU; ++u)
-#pragma unroll
-        for (int c = 0; c < NC; ++c) acc[c] += a[u] * g[u][c];
+    for (int u = 0; u < kU; ++u) {
+      const int64_t oo = o + u * 32;
+      const bool ok = oo < o1;
+      a[u] = ok ? A.v[oo] : T(0);
+      j[u] = ok ? A.ci[oo] : (int32_t)row;
     }
-  }
+    T g[kU][NCP];
 #pragma unroll
-  for (int c = 0; c < NC; ++c) acc[c] = group_sum<L>(acc[c]);
-  if (lane != 0 || row >= n) return;
+    for (int u = 0; u < kU; ++u) vload<T, NCP>(Gin + (int64_t)j[u] * NCP, g[u]);
+#pragma unroll
+    for (int u = 0; u < kU; ++u)
+#pragma unroll
+      for (int c = 0; c < NC; ++c) acc[c] += a[u] * g[u][c];
+  }
   T gx[NCP], d[NCP], bb[NCP];
   vload<T, NCP>(Gin + row * NCP, gx);
   if (MODE == MG_STEP || MODE == MG_LAST) vload<T, NCP>(Din + row * NCP, d);
@@ -363,21 +357,13 @@ void launch_mg(int mode, const DLevel<T>& L, const T* b, const T* Gin, const T* 
   const int64_t n = L.A.nrow;
   const T it = (T)L.inv_theta;
   constexpr int NC = NCP == 4 ? 3 : NCP;  // real components (3D pads 3 to 4)
-#define FS_MG(M, LN)                                                                         \
-  k_mg<T, NC, NCP, LN, M><<<blocks_for(n * LN), 256, 0, s>>>(L.A, L.dinv, b, Gin, Din, Gout, \
-                                                             Dout, alpha, beta, it, out,    \
-                                                             out_ld, perm, nc, skip)
-  if (L.lanes == 8) {
-    if (mode == MG_STEP) FS_MG(MG_STEP, 8);
-    else if (mode == MG_RESID) FS_MG(MG_RESID, 8);
-    else if (mode == MG_START) FS_MG(MG_START, 8);
-    else FS_MG(MG_LAST, 8);
-  } else {
-    if (mode == MG_STEP) FS_MG(MG_STEP, 4);
-    else if (mode == MG_RESID) FS_MG(MG_RESID, 4);
-    else if (mode == MG_START) FS_MG(MG_START, 4);
-    else FS_MG(MG_LAST, 4);
-  }
+#define FS_MG(M)                                                                        \
+  k_mg<T, NC, NCP, M><<<blocks_for(n), 256, 0, s>>>(L.A, L.dinv, b, Gin, Din, Gout, Dout, \
+                                                    alpha, beta, it, out, out_ld, perm, nc, skip)
+  if (mode == MG_STEP) FS_MG(MG_STEP);
+  else if (mode == MG_RESID) FS_MG(MG_RESID);
+  else if (mode == MG_START) FS_MG(MG_START);
+  else FS_MG(MG_LAST);
 #undef FS_MG
   count_launches(1);
 }
@@ -424,20 +410,23 @@ void vcycle_level(const DHier<T>& H, int l, T* out, int64_t out_ld, int nc, cons
 // ---------------------------------------------------------------------------
 // Block preconditioner pieces
 // ---------------------------------------------------------------------------
-// Load of a single-component level-0 right-hand side: b0 = r and the first
-// step from x = 0, G0 = D0 = D^-1 r / theta.
+// Load of a single-component level-0 right-hand side (caller row q goes to
+// level-0 row iperm[q]): b0 = r and the first step from x = 0,
+// G0 = D0 = D^-1 r / theta.
 template <typename T>
-__global__ void k_mg_load1(int64_t n, const T* __restrict__ r, const T* __restrict__ dinv0,
+__global__ void k_mg_load1(int64_t n, const T* __restrict__ r,
+                           const int32_t* __restrict__ iperm, const T* __restrict__ dinv0,
                            T inv_theta0, T* __restrict__ b0, T* __restrict__ G0,
                            T* __restrict__ D0, const int* skip) {
   if (skip && *skip) return;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
        q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t dst = iperm ? iperm[q] : q;
     const T v = r[q];
-    const T d0 = dinv0 ? dinv0[q] * v * inv_theta0 : T(0);
-    b0[q] = v;
-    G0[q] = d0;
-    D0[q] = d0;
+    const T d0 = dinv0 ? dinv0[dst] * v * inv_theta0 : T(0);
+    b0[dst] = v;
+    G0[dst] = d0;
+    D0[dst] = d0;
   }
 }
 
@@ -572,7 +561,7 @@ void launch_precond(const DOp<T>& op, const DHier<T>& HA, const DHier<T>& HK,
   {
     const bool k1 = HK.nlev > 1;
     k_mg_load1<T><<<grid_stride_blocks(nv), 256, 0, s>>>(
-        nv, rp, k1 ? HK.lev[0].dinv : nullptr, (T)HK.lev[0].inv_theta, HK.b[0], HK.G0[0],
+        nv, rp, HK.iperm, k1 ? HK.lev[0].dinv : nullptr, (T)HK.lev[0].inv_theta, HK.b[0], HK.G0[0],
         HK.D0[0], skip);
     count_launches(1);
     vcycle_level<T, 1>(HK, 0, work_p, nv, 1, skip, s);

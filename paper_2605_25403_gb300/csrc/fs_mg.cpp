@@ -202,6 +202,110 @@ bool dense_inverse(const HostCsr& A, std::vector<double>& inv) {
   return true;
 }
 
+// Order of the rows of a P2 level: the nodes sit on the doubled lattice of
+// the mesh (a vertex at twice its grid indices, an edge node at the sum of its
+// end points' indices); they are grouped by the parity class of their
+// doubled coordinates (vertices, then each edge direction) and ordered
+// lexicographically (x fastest) within a class.  Rows of one class along a
+// grid line then have the same stencil shifted by one, so the neighbours that
+// 32 consecutive rows read at one matrix slot are contiguous.  Returns sigma
+// (new row -> mesh row); vertices keep their numbers.
+std::vector<int32_t> class_order(const Mesh& m, const HostLevel& L) {
+  const int dim = m.dim;
+  const int64_t sx = L.grid[0] + 1, sy = L.grid[1] + 1, sz = dim == 3 ? L.grid[2] + 1 : 1;
+  const int64_t nv = sx * sy * sz;
+  auto ijk = [&](int64_t v, int64_t* c) {
+    c[0] = v % sx;
+    c[1] = (v / sx) % sy;
+    c[2] = v / (sx * sy);
+  };
+  const int64_t n = L.A.nrow;
+  const int64_t X = 2 * sx, Y = 2 * sy;
+  std::vector<std::pair<int64_t, int32_t>> key(n);
+  for (int64_t r = 0; r < n; ++r) {
+    int64_t c[3];
+    if (r < nv) {
+      ijk(r, c);
+      for (int a = 0; a < 3; ++a) c[a] *= 2;
+    } else {
+      int64_t ca[3], cb[3];
+      ijk(m.edges[2 * (r - nv)], ca);
+      ijk(m.edges[2 * (r - nv) + 1], cb);
+      for (int a = 0; a < 3; ++a) c[a] = ca[a] + cb[a];
+    }
+    const int64_t cls = (c[0] & 1) | (c[1] & 1) << 1 | (c[2] & 1) << 2;
+    key[r] = {((cls * (2 * sz) + c[2]) * Y + c[1]) * X + c[0], (int32_t)r};
+  }
+  std::sort(key.begin(), key.end());
+  std::vector<int32_t> sigma(n);
+  for (int64_t r = 0; r < n; ++r) sigma[r] = key[r].second;
+  return sigma;
+}
+
+// M' with M'[r] = M[rows[r]] and columns renumbered by cinv (old -> new),
+// columns sorted per row.
+HostCsr permute(const HostCsr& M, const std::vector<int32_t>& rows,
+                const std::vector<int32_t>& cinv) {
+  HostCsr O;
+  O.nrow = M.nrow;
+  O.ncol = M.ncol;
+  O.rowptr.assign(O.nrow + 1, 0);
+  O.col.reserve(M.nnz());
+  O.val.reserve(M.nnz());
+  std::vector<std::pair<int32_t, double>> row;
+  for (int64_t r = 0; r < O.nrow; ++r) {
+    const int32_t o = rows[r];
+    row.clear();
+    for (int32_t k = M.rowptr[o]; k < M.rowptr[o + 1]; ++k)
+      row.push_back({cinv[M.col[k]], M.val[k]});
+    std::sort(row.begin(), row.end());
+    for (auto& e : row) {
+      O.col.push_back(e.first);
+      O.val.push_back(e.second);
+    }
+    O.rowptr[r + 1] = (int32_t)O.col.size();
+  }
+  return O;
+}
+
+std::vector<int32_t> inverse(const std::vector<int32_t>& sigma) {
+  std::vector<int32_t> inv(sigma.size());
+  for (size_t r = 0; r < sigma.size(); ++r) inv[sigma[r]] = (int32_t)r;
+  return inv;
+}
+
+// Renumbers the rows of a P2 finest level in class order (a symmetric
+// permutation of its operator, with the transfer to the next level and the
+// diagonal following); P1 levels keep the grid numbering, which already has
+// that property.
+void class_order_hierarchy(const Mesh& m, HostHierarchy& H) {
+  H.order0.clear();
+  HostLevel& L = H.levels[0];
+  if (!L.p2) {
+    H.order0.resize(L.A.nrow);
+    std::iota(H.order0.begin(), H.order0.end(), 0);
+    return;
+  }
+  std::vector<int32_t> sg = class_order(m, L), inv = inverse(sg);
+  L.A = permute(L.A, sg, inv);
+  std::vector<double> d(L.dinv.size());
+  for (size_t r = 0; r < d.size(); ++r) d[r] = L.dinv[sg[r]];
+  L.dinv.swap(d);
+  if (H.levels.size() > 1) {
+    std::vector<int32_t> id(L.P.ncol);
+    std::iota(id.begin(), id.end(), 0);
+    L.P = permute(L.P, sg, id);
+    L.R = permute(L.R, id, inv);
+  } else {
+    const int64_t nc = H.ncoarse;
+    std::vector<double> ci(nc * nc);
+    for (int64_t r = 0; r < nc; ++r)
+      for (int64_t c = 0; c < nc; ++c) ci[r * nc + c] = H.coarse_inv[sg[r] * nc + sg[c]];
+    H.coarse_inv.swap(ci);
+  }
+  H.order0 = sg;
+}
+
 }  // namespace
 
 void build_hierarchy(const Mesh& m, const HostCsr& A0, bool p2_fine,
@@ -212,6 +316,8 @@ void build_hierarchy(const Mesh& m, const HostCsr& A0, bool p2_fine,
   H.levels[0].A = A0;
   int dim = m.dim;
   int ncur[3] = {m.desc.n[0], m.desc.n[1], dim == 3 ? m.desc.n[2] : 1};
+  for (int a = 0; a < 3; ++a) H.levels[0].grid[a] = ncur[a];
+  H.levels[0].p2 = p2_fine;
   bool first = true;
   while (H.levels.back().A.nrow > coarse_max) {
     HostLevel& fine = H.levels.back();
@@ -267,6 +373,7 @@ void build_hierarchy(const Mesh& m, const HostCsr& A0, bool p2_fine,
     fine.R = R;
     H.levels.emplace_back();
     H.levels.back().A = Ac;
+    for (int a = 0; a < 3; ++a) H.levels.back().grid[a] = ncur[a];
   }
   for (auto& L : H.levels) finish_level(L);
   H.ncoarse = H.levels.back().A.nrow;
@@ -276,6 +383,7 @@ void build_hierarchy(const Mesh& m, const HostCsr& A0, bool p2_fine,
     for (int64_t i = 0; i < H.ncoarse; ++i)
       H.coarse_inv[i * H.ncoarse + i] = H.levels.back().dinv[i];
   }
+  class_order_hierarchy(m, H);
 }
 
 }  // namespace fs
@@ -428,13 +536,12 @@ void build_union_hierarchy(const Mesh& m, const std::vector<Mesh>& /*local*/,
       UL.R = block_diag(Rs);
     }
   }
-  // block order of level 0 vs the union numbering
+  // level-0 rows (instance blocks, each in Z-order) vs the union numbering
   U.perm.clear();
-  if (p2_fine && K > 1) {
-    U.perm.reserve(A0.nrow);
-    for (int i = 0; i < K; ++i)
-      for (int64_t j = 0; j < m.inst[i].n2(); ++j) U.perm.push_back((int32_t)union_node(m, i, j));
-  }
+  U.perm.reserve(A0.nrow);
+  for (int i = 0; i < K; ++i)
+    for (int32_t j : H[i].order0)
+      U.perm.push_back((int32_t)(p2_fine ? union_node(m, i, j) : m.inst[i].voff + j));
   // coarsest: block-diagonal dense inverses
   U.blk_row.assign(K, 0);
   U.blk_n.assign(K, 0);
