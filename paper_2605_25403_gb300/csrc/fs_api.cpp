@@ -100,7 +100,6 @@ struct Precision {
   DHier<T> HA, HK;
   T* mplinv_nu = nullptr;
   Krylov<T> kr;
-  int lanes = 4;
 };
 
 // Resumable solve / step state.
@@ -140,9 +139,16 @@ struct fs_problem {
   double *x = nullptr, *b = nullptr, *F = nullptr, *r64 = nullptr;
   int32_t* pinned = nullptr;
   int npinned = 0;
-  int64_t* mrp = nullptr;  // monolithic row pointers (export)
+  int64_t* mrp = nullptr;  // paper-order monolithic row pointers (export)
+  const int32_t* nat = nullptr;          // internal P2 node -> paper id
+  double *natbuf = nullptr, *natbuf2 = nullptr;  // boundary conversions (lazy)
+  // SELL-32 copies of the blocks for the iteration path (slice offsets and
+  // columns shared by both precisions)
+  const int64_t *offA = nullptr, *offB = nullptr, *offBT = nullptr;
+  const int32_t *sciA = nullptr, *sciB = nullptr, *sciBT = nullptr;
+  double *sA64 = nullptr, *sB64 = nullptr, *sBT64 = nullptr;
   // FP32 data (precision mode)
-  float *valA32 = nullptr, *B32 = nullptr, *BT32 = nullptr, *diagp32 = nullptr;
+  float *sA32 = nullptr, *sB32 = nullptr, *sBT32 = nullptr, *diagp32 = nullptr;
   Precision<double> p64;
   Precision<float> p32;
   bool has32 = false;
@@ -208,6 +214,13 @@ int check_launch(const char* what) {
   return FS_OK;
 }
 
+// Scratch vectors of the paper-order conversions at the boundary.
+int nat_buffers(fs_problem* P) {
+  if (!P->natbuf) FS_TRY(P->alloc(&P->natbuf, P->ndof));
+  if (!P->natbuf2) FS_TRY(P->alloc(&P->natbuf2, P->ndof));
+  return FS_OK;
+}
+
 template <typename T>
 int upload_csr(fs_problem* P, const HostCsr& H, DCsr<T>& d) {
   int32_t *rp, *ci;
@@ -223,44 +236,58 @@ int upload_csr(fs_problem* P, const HostCsr& H, DCsr<T>& d) {
   return FS_OK;
 }
 
-// Sliced ELLPACK copy of a CSR matrix (slices of 32 rows, slot-major within
-// a slice, padding slots with coefficient 0 pointing at the row itself).
-template <typename T>
-int upload_sell(fs_problem* P, const HostCsr& H, DSell<T>& d) {
+// SELL-32 layout of a CSR pattern: slice offsets (slices of 32 rows, width
+// = the longest row of the slice) and slot-major columns.  Padding slots
+// point at the row itself in a square matrix (a read the row makes anyway)
+// and at column 0 in a rectangular one, so that every column is in range.
+void sell_layout(const HostCsr& H, std::vector<int64_t>& off, std::vector<int32_t>& ci) {
+  const bool square = H.nrow == H.ncol;
   const int64_t n = H.nrow, ns = (n + 31) / 32;
-  std::vector<int64_t> off(ns + 1, 0);
+  off.assign(ns + 1, 0);
   for (int64_t sl = 0; sl < ns; ++sl) {
     int64_t w = 0;
     for (int64_t r = 32 * sl; r < std::min(n, 32 * sl + 32); ++r)
       w = std::max<int64_t>(w, H.rowptr[r + 1] - H.rowptr[r]);
     off[sl + 1] = off[sl] + 32 * w;
   }
-  std::vector<int32_t> ci(off[ns], 0);
-  std::vector<T> v(off[ns], T(0));
-  for (int64_t sl = 0; sl < ns; ++sl) {
-    const int64_t w = (off[sl + 1] - off[sl]) / 32;
-    for (int t = 0; t < 32; ++t) {
-      const int64_t r = 32 * sl + t;
-      if (r >= n) break;
-      const int64_t len = H.rowptr[r + 1] - H.rowptr[r];
-      for (int64_t u = 0; u < w; ++u) {
-        const int64_t o = off[sl] + 32 * u + t;
-        if (u < len) {
-          ci[o] = H.col[H.rowptr[r] + u];
-          v[o] = (T)H.val[H.rowptr[r] + u];
-        } else {
-          ci[o] = (int32_t)r;
-        }
-      }
-    }
+  ci.assign(off[ns], 0);
+  for (int64_t r = 0; r < n; ++r) {
+    const int64_t sl = r >> 5, t = r & 31, w = (off[sl + 1] - off[sl]) / 32;
+    const int64_t len = H.rowptr[r + 1] - H.rowptr[r];
+    for (int64_t u = 0; u < w; ++u)
+      ci[off[sl] + 32 * u + t] = u < len ? H.col[H.rowptr[r] + u] : (square ? (int32_t)r : 0);
   }
+}
+
+// Values of a CSR matrix with dimv values per entry (vals, entry-major) in
+// the SELL-32 layout off: component c of slot u of row 32 s + t at
+// (off[s] + 32 u) dimv + 32 c + t; padding slots hold 0.
+template <typename T>
+std::vector<T> sell_values(const HostCsr& H, const std::vector<int64_t>& off, const double* vals,
+                           int dimv) {
+  std::vector<T> v(off.back() * dimv, T(0));
+  for (int64_t r = 0; r < H.nrow; ++r) {
+    const int64_t sl = r >> 5, t = r & 31;
+    for (int64_t u = 0; u < H.rowptr[r + 1] - H.rowptr[r]; ++u)
+      for (int c = 0; c < dimv; ++c)
+        v[(off[sl] + 32 * u) * dimv + 32 * c + t] = (T)vals[(H.rowptr[r] + u) * dimv + c];
+  }
+  return v;
+}
+
+template <typename T>
+int upload_sell(fs_problem* P, const HostCsr& H, DSell<T>& d) {
+  std::vector<int64_t> off;
+  std::vector<int32_t> ci;
+  sell_layout(H, off, ci);
+  std::vector<T> v = sell_values<T>(H, off, H.val.data(), 1);
   int64_t* doff;
   int32_t* dci;
   T* dv;
   FS_TRY(P->upload(&doff, off));
   FS_TRY(P->upload(&dci, ci));
   FS_TRY(P->upload(&dv, v));
-  d.nrow = n;
+  d.nrow = H.nrow;
   d.off = doff;
   d.ci = dci;
   d.v = dv;
@@ -426,21 +453,22 @@ std::vector<int32_t> poisson_fixed(const fs_mesh_desc& d, bool pin) {
   return out;
 }
 
+// The iteration-path operator of one precision from its SELL-32 values.
+template <typename T>
+void set_op(fs_problem* P, DOp<T>& op, const T* A, const T* B, const T* BT, const T* diagp) {
+  op.dim = P->dim;
+  op.n2 = P->n2;
+  op.nv = P->nv;
+  op.A = {P->n2, P->offA, P->sciA, A};
+  op.B = {P->nv, P->offB, P->sciB, B};
+  op.BT = {P->n2, P->offBT, P->sciBT, BT};
+  op.diagp = diagp;
+}
+
 template <typename T>
 int setup_precision(fs_problem* P, Precision<T>& pr, const UnionHierarchy& HA,
-                    const UnionHierarchy& HK, const std::vector<double>& mplinv_nu,
-                    const T* valA, const T* B, const T* BT, const T* diagp, int m,
+                    const UnionHierarchy& HK, const std::vector<double>& mplinv_nu, int m,
                     const std::vector<int>& first, const std::vector<int>& count) {
-  const Mesh& me = P->mesh->m;
-  pr.op.dim = P->dim;
-  pr.op.n2 = P->n2;
-  pr.op.nv = P->nv;
-  pr.op.A = {(int32_t)P->n2, P->dm.rpA, P->dm.ciA, valA};
-  pr.op.B = {(int32_t)P->nv, P->dm.rpB, P->dm.ciB, B};
-  pr.op.BT = {(int32_t)P->n2, P->dm.rpBT, P->dm.ciBT, BT};
-  pr.op.diagp = diagp;
-  double avg = (double)(me.A.nnz() + me.BT.nnz()) / (double)P->n2;
-  pr.lanes = avg >= 24.0 ? 8 : 4;
   FS_TRY(upload_hierarchy<T>(P, HA, P->dim, pr.HA));
   FS_TRY(upload_hierarchy<T>(P, HK, 1, pr.HK));
   std::vector<T> mi(mplinv_nu.begin(), mplinv_nu.end());
@@ -456,7 +484,7 @@ template <typename T>
 void issue_check(fs_problem* P, Precision<T>& pr, const T* x, const T* b) {
   Krylov<T>& K = pr.kr;
   cudaStream_t s = P->stream;
-  launch_spmv_full<T, T>(pr.op, x, b, K.Vb, 1, nullptr, pr.lanes, s);
+  launch_spmv_full<T, T>(pr.op, x, b, K.Vb, 1, nullptr, s);
   launch_seg_norm<T>(K.Vb, P->tl(), K.st, K.partial, 0, s);
 }
 
@@ -477,7 +505,7 @@ void issue_iter(fs_problem* P, Precision<T>& pr, T* x, double rtol, int relative
     T* w = K.Vb + (int64_t)(j + 1) * n;
     launch_precond<T>(pr.op, pr.HA, pr.HK, pr.mplinv_nu, 1.0 / P->desc.dt, P->pinned,
                       P->npinned, vj, zj, K.work_p, K.work_u, skip, s);
-    launch_spmv_full<T, T>(pr.op, zj, nullptr, w, 0, skip, pr.lanes, s);
+    launch_spmv_full<T, T>(pr.op, zj, nullptr, w, 0, skip, s);
     launch_seg_cgs2<T>(K.Vb, n, j, tl, K.st, K.ctl, K.partial, s);
     launch_seg_scale<T>(w, tl, K.st, 1, s);
     launch_seg_givens(K.st, K.ctl, P->nseg, j, s);
@@ -550,7 +578,8 @@ int assemble_impl(fs_problem* P, double t_next) {
   launch_bc_rows<double>(P->dm, P->valA, s);
   launch_eval_load(P->dm, P->ph, t_next, 1.0 / P->desc.dt, P->x, P->F, s);
   launch_rhs(P->dm, P->ph, t_next, P->Mv, P->F, P->pinned, P->npinned, P->b, s);
-  if (P->has32) launch_convert<double, float>(P->valA, P->valA32, nnzA, nullptr, 0, s);
+  launch_csr_to_sell(P->n2, P->dm.rpA, P->valA, P->offA, P->sA64, P->has32 ? P->sA32 : nullptr,
+                     s);
   FS_TRY(check_launch("assembly"));
   P->assembled = true;
   return FS_OK;
@@ -585,7 +614,7 @@ int start_solve(fs_problem* P, double* x) {
     Krylov<float>& K = P->p32.kr;
     FS_TRY(push_retired(P, K));
     launch_seg_norm<double>(P->b, P->tl(), K.st, K.partial, 1, s);
-    launch_spmv_full<double, double>(P->p64.op, x, P->b, P->r64, 1, nullptr, P->p64.lanes, s);
+    launch_spmv_full<double, double>(P->p64.op, x, P->b, P->r64, 1, nullptr, s);
     launch_seg_norm<double>(P->r64, P->tl(), K.st, K.partial, 2, s);
     FS_TRY(enqueue_status(P, K));
     c.phase = PH_RES64;
@@ -711,7 +740,7 @@ int advance(fs_problem* P) {
         issue_iter<float>(P, pr, K.sol, c.o.inner_rtol, 1);
       }));
       launch_seg_axpy<float, double>(c.x, K.sol, P->tl(), K.st, s);
-      launch_spmv_full<double, double>(P->p64.op, c.x, P->b, P->r64, 1, nullptr, P->p64.lanes, s);
+      launch_spmv_full<double, double>(P->p64.op, c.x, P->b, P->r64, 1, nullptr, s);
       launch_seg_norm<double>(P->r64, P->tl(), K.st, K.partial, 2, s);
       FS_TRY(enqueue_status(P, K));
       for (int q = 0; q < P->nseg; ++q)
@@ -838,12 +867,15 @@ int fs_dof_map(const fs_mesh* mesh, fs_dofmap_info* info, double* coords, int32_
   info->nnz_b = m.B.nnz();
   info->nnz = m.dim * (m.A.nnz() + m.BT.nnz() + m.B.nnz()) + m.nv;
   if (coords) std::memcpy(coords, m.coords.data(), sizeof(double) * m.coords.size());
-  if (cell2dof) std::memcpy(cell2dof, m.c2d.data(), sizeof(int32_t) * m.c2d.size());
-  if (dirichlet) std::memcpy(dirichlet, m.dirichlet.data(), m.dirichlet.size());
-  if (rowptr || col) {
+  if (cell2dof || dirichlet || rowptr || col) {
+    // the device works in an internal node order; this is the paper's
+    std::vector<int32_t> c2d, ci;
+    std::vector<uint8_t> dir;
     std::vector<int64_t> rp;
-    std::vector<int32_t> ci;
-    monolithic_pattern(m, rp, ci);
+    natural_dof_map(m, cell2dof ? &c2d : nullptr, dirichlet ? &dir : nullptr,
+                    rowptr ? &rp : nullptr, col ? &ci : nullptr);
+    if (cell2dof) std::memcpy(cell2dof, c2d.data(), sizeof(int32_t) * c2d.size());
+    if (dirichlet) std::memcpy(dirichlet, dir.data(), dir.size());
     if (rowptr) std::memcpy(rowptr, rp.data(), sizeof(int64_t) * rp.size());
     if (col) std::memcpy(col, ci.data(), sizeof(int32_t) * ci.size());
   }
@@ -1055,36 +1087,44 @@ int fs_problem_create_batch(fs_mesh* mesh, const fs_problem_desc* descs, int cou
   build_tiles(P.get(), tiles, first, tcount);
   FS_TRY(P->upload(&P->tiles, tiles));
   P->ntiles = (int)tiles.size();
-  const int m = 30;
+  // SELL-32 blocks of the iteration path: layouts once, B and BT values
+  // once (step-invariant), A values scattered after every assembly
   {
-    auto& pr = P->p64;
-    if (d0.precision == FS_PREC_FP64) {
-      FS_TRY(setup_precision<double>(P.get(), pr, HA, HK, mplinv_nu, P->valA, P->B, P->BT,
-                                     P->diagp, m, first, tcount));
-    } else {
-      // FP64 operator only: assembly and the residuals of the refinement
-      pr.op.dim = dim;
-      pr.op.n2 = P->n2;
-      pr.op.nv = P->nv;
-      pr.op.A = {(int32_t)P->n2, dm.rpA, dm.ciA, P->valA};
-      pr.op.B = {(int32_t)P->nv, dm.rpB, dm.ciB, P->B};
-      pr.op.BT = {(int32_t)P->n2, dm.rpBT, dm.ciBT, P->BT};
-      pr.op.diagp = P->diagp;
-      double avg = (double)(me.A.nnz() + me.BT.nnz()) / (double)P->n2;
-      pr.lanes = avg >= 24.0 ? 8 : 4;
+    std::vector<int64_t> oA, oB, oBT;
+    std::vector<int32_t> cA, cB, cBT;
+    sell_layout(me.A, oA, cA);
+    sell_layout(me.B, oB, cB);
+    sell_layout(me.BT, oBT, cBT);
+    int64_t *a, *b, *c;
+    int32_t *ca, *cb, *cc;
+    FS_TRY(P->upload(&a, oA)); FS_TRY(P->upload(&ca, cA));
+    FS_TRY(P->upload(&b, oB)); FS_TRY(P->upload(&cb, cB));
+    FS_TRY(P->upload(&c, oBT)); FS_TRY(P->upload(&cc, cBT));
+    P->offA = a; P->sciA = ca; P->offB = b; P->sciB = cb; P->offBT = c; P->sciBT = cc;
+    FS_TRY(P->alloc(&P->sA64, oA.back()));
+    FS_CUDA(cudaMemsetAsync(P->sA64, 0, sizeof(double) * oA.back(), s));
+    FS_TRY(P->upload(&P->sB64, sell_values<double>(me.B, oB, Bh.data(), dim)));
+    FS_TRY(P->upload(&P->sBT64, sell_values<double>(me.BT, oBT, BTh.data(), dim)));
+    set_op<double>(P.get(), P->p64.op, P->sA64, P->sB64, P->sBT64, P->diagp);
+    if (d0.precision == FS_PREC_FP32_REFINE) {
+      P->has32 = true;
+      FS_TRY(P->alloc(&P->sA32, oA.back()));
+      FS_CUDA(cudaMemsetAsync(P->sA32, 0, sizeof(float) * oA.back(), s));
+      FS_TRY(P->upload(&P->sB32, sell_values<float>(me.B, oB, Bh.data(), dim)));
+      FS_TRY(P->upload(&P->sBT32, sell_values<float>(me.BT, oBT, BTh.data(), dim)));
+      std::vector<float> d32(dp.begin(), dp.end());
+      FS_TRY(P->upload(&P->diagp32, d32));
+      set_op<float>(P.get(), P->p32.op, P->sA32, P->sB32, P->sBT32, P->diagp32);
     }
+    int32_t* nat;
+    FS_TRY(P->upload(&nat, me.node_nat));
+    P->nat = nat;
   }
-  if (d0.precision == FS_PREC_FP32_REFINE) {
-    P->has32 = true;
-    FS_TRY(P->alloc(&P->valA32, nnzA));
-    std::vector<float> b32(Bh.begin(), Bh.end()), bt32(BTh.begin(), BTh.end()),
-        d32(dp.begin(), dp.end());
-    FS_TRY(P->upload(&P->B32, b32));
-    FS_TRY(P->upload(&P->BT32, bt32));
-    FS_TRY(P->upload(&P->diagp32, d32));
-    FS_TRY(setup_precision<float>(P.get(), P->p32, HA, HK, mplinv_nu, P->valA32, P->B32,
-                                  P->BT32, P->diagp32, m, first, tcount));
-  }
+  const int m = 30;
+  if (d0.precision == FS_PREC_FP64)
+    FS_TRY(setup_precision<double>(P.get(), P->p64, HA, HK, mplinv_nu, m, first, tcount));
+  else
+    FS_TRY(setup_precision<float>(P.get(), P->p32, HA, HK, mplinv_nu, m, first, tcount));
   launch_exact_state(dm, P->ph, d0.t0, d0.init == 1, P->x, s);
   FS_TRY(check_launch("initial state"));
   FS_CUDA(cudaStreamSynchronize(s));
@@ -1107,17 +1147,27 @@ int fs_assemble_step(fs_problem* P, double t_next, double* val_out, double* b_ou
   FS_TRY(assemble_impl(P, t_next));
   if (val_out) {
     if (!P->mrp) {
-      std::vector<int64_t> rp;
-      std::vector<int32_t> ci;
-      monolithic_pattern(P->mesh->m, rp, ci);
+      // paper-order row pointers from the internal row lengths
+      const Mesh& me = P->mesh->m;
+      const int64_t n2 = me.n2, dim = me.dim;
+      std::vector<int64_t> rp(P->ndof + 1, 0);
+      for (int64_t q = 0; q < n2; ++q)
+        for (int64_t c = 0; c < dim; ++c)
+          rp[c * n2 + me.node_nat[q] + 1] =
+              (me.A.rowptr[q + 1] - me.A.rowptr[q]) + (me.BT.rowptr[q + 1] - me.BT.rowptr[q]);
+      for (int64_t q = 0; q < me.nv; ++q)
+        rp[dim * n2 + q + 1] = dim * (me.B.rowptr[q + 1] - me.B.rowptr[q]) + 1;
+      for (int64_t r = 0; r < P->ndof; ++r) rp[r + 1] += rp[r];
       FS_TRY(P->upload(&P->mrp, rp));
     }
-    launch_expand_monolithic(P->dm, P->valA, P->B, P->BT, P->diagp, P->mrp, val_out, P->stream);
+    launch_expand_monolithic(P->dm, P->nat, P->valA, P->B, P->BT, P->diagp, P->mrp, val_out,
+                             P->stream);
     FS_TRY(check_launch("expand_monolithic"));
   }
-  if (b_out)
-    FS_CUDA(cudaMemcpyAsync(b_out, P->b, sizeof(double) * P->ndof, cudaMemcpyDeviceToDevice,
-                            P->stream));
+  if (b_out) {
+    launch_dofs_perm(P->dm, P->nat, P->b, b_out, 1, P->stream);
+    FS_TRY(check_launch("fs_assemble_step export"));
+  }
   return FS_OK;
 }
 
@@ -1135,9 +1185,19 @@ int fs_solve(fs_problem* P, const fs_solve_opts* opts, double* x, fs_solve_stats
     return FS_ERR_BUSY;
   }
   FS_TRY(solve_opts(opts, P->ctx.o));
-  int rc = run_solve(P, x ? x : P->x);
+  if (x) {  // the caller's vector is in paper order
+    FS_TRY(nat_buffers(P));
+    launch_dofs_perm(P->dm, P->nat, x, P->natbuf, 0, P->stream);
+    FS_TRY(check_launch("fs_solve"));
+  }
+  int rc = run_solve(P, x ? P->natbuf : P->x);
   if (P->ctx.phase == PH_DONE && stats) *stats = aggregate_stats(P);
   P->ctx.phase = PH_IDLE;
+  if (x) {
+    launch_dofs_perm(P->dm, P->nat, P->natbuf, x, 1, P->stream);
+    FS_TRY(check_launch("fs_solve"));
+    FS_CUDA(cudaStreamSynchronize(P->stream));
+  }
   return rc;
 }
 
@@ -1224,7 +1284,15 @@ int fs_apply_operator(fs_problem* P, const double* x, double* y) {
     set_error("fs_apply_operator: null argument");
     return FS_ERR_INVALID_ARG;
   }
-  launch_spmv_full<double, double>(P->p64.op, x, nullptr, y, 0, nullptr, P->p64.lanes, P->stream);
+  if (!P->assembled) {
+    set_error("fs_apply_operator: call fs_assemble_step first");
+    return FS_ERR_INVALID_ARG;
+  }
+  FS_TRY(nat_buffers(P));
+  launch_dofs_perm(P->dm, P->nat, x, P->natbuf, 0, P->stream);
+  launch_spmv_full<double, double>(P->p64.op, P->natbuf, nullptr, P->natbuf2, 0, nullptr,
+                                   P->stream);
+  launch_dofs_perm(P->dm, P->nat, P->natbuf2, y, 1, P->stream);
   return check_launch("fs_apply_operator");
 }
 
@@ -1233,9 +1301,13 @@ int fs_get_state(fs_problem* P, double* x_out, int host, double* t_out) {
     set_error("fs_get_state: null problem");
     return FS_ERR_INVALID_ARG;
   }
-  if (x_out)
-    FS_CUDA(cudaMemcpyAsync(x_out, P->x, sizeof(double) * P->ndof,
+  if (x_out) {
+    FS_TRY(nat_buffers(P));
+    launch_dofs_perm(P->dm, P->nat, P->x, P->natbuf, 1, P->stream);
+    FS_TRY(check_launch("fs_get_state"));
+    FS_CUDA(cudaMemcpyAsync(x_out, P->natbuf, sizeof(double) * P->ndof,
                             host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, P->stream));
+  }
   FS_CUDA(cudaStreamSynchronize(P->stream));
   if (t_out) *t_out = P->t;
   return FS_OK;
@@ -1246,9 +1318,13 @@ int fs_set_state(fs_problem* P, const double* x_in, int host, double t) {
     set_error("fs_set_state: null problem");
     return FS_ERR_INVALID_ARG;
   }
-  if (x_in)
-    FS_CUDA(cudaMemcpyAsync(P->x, x_in, sizeof(double) * P->ndof,
+  if (x_in) {
+    FS_TRY(nat_buffers(P));
+    FS_CUDA(cudaMemcpyAsync(P->natbuf, x_in, sizeof(double) * P->ndof,
                             host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, P->stream));
+    launch_dofs_perm(P->dm, P->nat, P->natbuf, P->x, 0, P->stream);
+    FS_TRY(check_launch("fs_set_state"));
+  }
   FS_CUDA(cudaStreamSynchronize(P->stream));
   P->t = t;
   return FS_OK;
@@ -1280,12 +1356,12 @@ int fs_profile_kernel(fs_problem* P, int kernel, int reps, double* avg_ms, doubl
         auto& pr = P->p32;
         launch = [P, &pr]() {
           launch_spmv_full<float, float>(pr.op, pr.kr.Vb, nullptr, pr.kr.Vb + P->ndof, 0, nullptr,
-                                         pr.lanes, P->stream);
+                                         P->stream);
         };
       } else {
         launch = [P]() {
           launch_spmv_full<double, double>(P->p64.op, P->x, nullptr, P->r64, 0, nullptr,
-                                           P->p64.lanes, P->stream);
+                                           P->stream);
         };
       }
       break;

@@ -499,7 +499,15 @@ __global__ void k_exact_state(DMesh m, DPhys ph, double t, int zero_interior,
   }
 }
 
-__global__ void k_expand_monolithic(DMesh m, const double* __restrict__ valA,
+// Monolithic values in paper order, one internal row per thread.  The
+// paper-order row of internal velocity row (c, q) is c n2 + nat[q]; its
+// columns are the row's P2 neighbours in paper order (the rank of nat[j]
+// among the row's entries gives the place), then its pressure neighbours
+// (vertex ids are the same in both orders).  A pressure row keeps its place
+// and holds, per component, its P2 neighbours ranked the same way, then the
+// diagonal.
+__global__ void k_expand_monolithic(DMesh m, const int32_t* __restrict__ nat,
+                                    const double* __restrict__ valA,
                                     const double* __restrict__ B,
                                     const double* __restrict__ BT,
                                     const double* __restrict__ diagp,
@@ -509,17 +517,52 @@ __global__ void k_expand_monolithic(DMesh m, const double* __restrict__ valA,
   const int64_t nrow = dim * m.n2 + m.nv;
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nrow;
        r += (int64_t)gridDim.x * blockDim.x) {
-    int64_t o = mrp[r];
     if (r < dim * m.n2) {
-      int c = (int)(r / m.n2);
-      int64_t i = r % m.n2;
-      for (int32_t k = m.rpA[i]; k < m.rpA[i + 1]; ++k) out[o++] = valA[k];
+      const int c = (int)(r / m.n2);
+      const int64_t i = r % m.n2;
+      int64_t o = mrp[c * m.n2 + nat[i]];
+      const int32_t k0 = m.rpA[i], k1 = m.rpA[i + 1];
+      for (int32_t k = k0; k < k1; ++k) {
+        const int32_t key = nat[m.ciA[k]];
+        int rank = 0;
+        for (int32_t k2 = k0; k2 < k1; ++k2) rank += nat[m.ciA[k2]] < key;
+        out[o + rank] = valA[k];
+      }
+      o += k1 - k0;
       for (int32_t k = m.rpBT[i]; k < m.rpBT[i + 1]; ++k) out[o++] = -BT[(int64_t)k * dim + c];
     } else {
-      int64_t q = r - dim * m.n2;
-      for (int c = 0; c < dim; ++c)
-        for (int32_t k = m.rpB[q]; k < m.rpB[q + 1]; ++k) out[o++] = B[(int64_t)k * dim + c];
-      out[o++] = diagp[q];
+      const int64_t q = r - dim * m.n2;
+      int64_t o = mrp[r];
+      const int32_t k0 = m.rpB[q], k1 = m.rpB[q + 1];
+      for (int c = 0; c < dim; ++c) {
+        for (int32_t k = k0; k < k1; ++k) {
+          const int32_t key = nat[m.ciB[k]];
+          int rank = 0;
+          for (int32_t k2 = k0; k2 < k1; ++k2) rank += nat[m.ciB[k2]] < key;
+          out[o + rank] = B[(int64_t)k * dim + c];
+        }
+        o += k1 - k0;
+      }
+      out[o] = diagp[q];
+    }
+  }
+}
+
+__global__ void k_dofs_perm(int dim, int64_t n2, int64_t nv, const int32_t* __restrict__ nat,
+                            const double* __restrict__ in, double* __restrict__ out,
+                            int to_nat) {
+  const int64_t n = dim * n2 + nv;
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    if (r < dim * n2) {
+      const int64_t c = r / n2, q = r % n2;
+      const int64_t rn = c * n2 + nat[q];
+      if (to_nat)
+        out[rn] = in[r];
+      else
+        out[r] = in[rn];
+    } else {
+      out[r] = in[r];
     }
   }
 }
@@ -603,12 +646,18 @@ void launch_exact_state(const DMesh& m, const DPhys& ph, double t,
     count_launches(1);
 }
 
-void launch_expand_monolithic(const DMesh& m, const double* valA,
-                              const double* B, const double* BT,
-                              const double* diagp, const int64_t* mrp,
-                              double* out, cudaStream_t s) {
+void launch_expand_monolithic(const DMesh& m, const int32_t* nat, const double* valA,
+                              const double* B, const double* BT, const double* diagp,
+                              const int64_t* mrp, double* out, cudaStream_t s) {
   int64_t nrow = m.dim * m.n2 + m.nv;
-  k_expand_monolithic<<<grid_for(nrow, 256), 256, 0, s>>>(m, valA, B, BT, diagp, mrp, out);
+  k_expand_monolithic<<<grid_for(nrow, 256), 256, 0, s>>>(m, nat, valA, B, BT, diagp, mrp, out);
+  count_launches(1);
+}
+
+void launch_dofs_perm(const DMesh& m, const int32_t* nat, const double* in, double* out,
+                      int to_nat, cudaStream_t s) {
+  int64_t n = m.dim * m.n2 + m.nv;
+  k_dofs_perm<<<grid_for(n, 256), 256, 0, s>>>(m.dim, m.n2, m.nv, nat, in, out, to_nat);
   count_launches(1);
 }
 

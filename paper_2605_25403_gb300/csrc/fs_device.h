@@ -91,10 +91,17 @@ void launch_rhs(const DMesh& m, const DPhys& ph, double t, const double* Mv,
 void launch_exact_state(const DMesh& m, const DPhys& ph, double t,
                         int zero_interior, double* x, cudaStream_t s);
 // Monolithic CSR values from the block values (export for parity checks).
-void launch_expand_monolithic(const DMesh& m, const double* valA,
-                              const double* B, const double* BT,
-                              const double* diagp, const int64_t* mrp,
-                              double* out, cudaStream_t s);
+// Monolithic CSR values in paper order (rows and columns of fs_dof_map):
+// mrp holds that CSR's row pointers and nat the paper id of each internal
+// P2 node; an entry's place in its row is the rank of its paper column.
+void launch_expand_monolithic(const DMesh& m, const int32_t* nat, const double* valA,
+                              const double* B, const double* BT, const double* diagp,
+                              const int64_t* mrp, double* out, cudaStream_t s);
+// n_dof vectors between the internal and the paper order of the P2 nodes:
+// to_nat = 1: out[c n2 + nat[q]] = in[c n2 + q]; to_nat = 0: the inverse;
+// pressure entries are copied.
+void launch_dofs_perm(const DMesh& m, const int32_t* nat, const double* in, double* out,
+                      int to_nat, cudaStream_t s);
 
 // ---- linear algebra (fs_linalg.cu) ---------------------------------------
 // Saddle-point operator in block form.
@@ -102,14 +109,22 @@ template <typename T>
 struct DOp {
   int dim = 0;
   int64_t n2 = 0, nv = 0;
-  DCsr<T> A, B, BT;     // B, BT values hold dim entries per nonzero
+  // SELL-32 blocks.  B and BT hold dim values per slot, component-major
+  // within a slot: the value of component c of row 32 s + t at slot u is at
+  // (off[s] + 32 u) dim + 32 c + t.
+  DSell<T> A, B, BT;
   const T* diagp = nullptr;
 };
 
 // y = K x (resid == 0) or y = b - K x (resid == 1); vectors of type V.
 template <typename T, typename V>
 void launch_spmv_full(const DOp<T>& op, const V* x, const V* b, V* y,
-                      int resid, const int* skip, int lanes, cudaStream_t s);
+                      int resid, const int* skip, cudaStream_t s);
+
+// Scalar CSR values (row pointers rp) into a SELL-32 layout with slice
+// offsets off: out64 (and out32 when not null) receive the n-row matrix.
+void launch_csr_to_sell(int64_t n, const int32_t* rp, const double* in, const int64_t* off,
+                        double* out64, float* out32, cudaStream_t s);
 
 // Multigrid level on the device.
 template <typename T>

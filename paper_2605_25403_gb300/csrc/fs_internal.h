@@ -51,7 +51,17 @@ struct Mesh {
   std::vector<uint8_t> posB;        // ncell x nb x nloc
   std::vector<uint8_t> posBT;       // ncell x nloc x nb
   std::vector<uint8_t> posKp;       // ncell x nb x nb
+  // P2 nodes are numbered internally with the edge nodes of every instance
+  // grouped by the parity class of their doubled-lattice position (see
+  // build_local); node_nat[q] is the paper-order (vertices, then edges ranked
+  // lexicographically) id of internal node q.  Vertices keep their ids.
+  std::vector<int32_t> node_nat;    // n2
 };
+
+// The DOF map in paper order (the numbering of fs_dof_map): cell-to-node
+// table, Dirichlet flags and the monolithic CSR pattern.
+void natural_dof_map(const Mesh& m, std::vector<int32_t>* c2d, std::vector<uint8_t>* dir,
+                     std::vector<int64_t>* rowptr, std::vector<int32_t>* col);
 
 // Builds the mesh tables; returns an fs_status.
 int build_mesh(const fs_mesh_desc& d, Mesh& m);
@@ -123,7 +133,8 @@ struct UnionHierarchy {
   std::vector<double> dense;         // concatenated dense inverses (row-major)
   std::vector<int32_t> row_blk;      // coarsest row -> instance
   // level-0 rows are in instance-major (block) order, each instance's rows
-  // in class order; perm[r] is the union row of block row r
+  // in class order; perm[r] is the union row of block row r (empty when
+  // the two orders agree)
   std::vector<int32_t> perm;
 };
 void build_union_hierarchy(const Mesh& m, const std::vector<Mesh>& local,

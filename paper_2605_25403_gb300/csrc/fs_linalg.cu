@@ -2,13 +2,16 @@
 // SpMV in block form, the multigrid V-cycle and block preconditioner, and the
 // reductions of flexible GMRES(m) (paper Sec. 3.2: GMRES).
 //
-// Row kernels use "L lanes per row": a group of L consecutive lanes walks one
-// CSR row with stride L (coalesced within the group) and reduces with
-// xor-shuffles inside the group.  The scalar P2 block A is stored once and
-// applied to all velocity components in the same pass (one read of the
-// matrix for d right-hand sides).  Reductions are two-level: per-block
-// partials, then the last block to finish (atomic ticket, no waiting) sums
-// them in FP64.
+// Matrices on the iteration path are sliced ELLPACK with 32-row slices, one
+// thread per row: a warp reads one slot of 32 consecutive rows at a time, so
+// matrix loads are contiguous, and with the P2 nodes numbered by parity
+// class (see the mesh builder) the x entries the warp gathers at a slot are
+// contiguous too.  The scalar P2 block A is stored once and applied to all
+// velocity components in the same pass (one read of the matrix for d
+// right-hand sides).  Transfer operators of the multigrid stay CSR with a
+// few lanes per row reducing by xor-shuffles.  Reductions are two-level:
+// per-block partials, then the last block to finish (atomic ticket, no
+// waiting) sums them in FP64.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -35,74 +38,105 @@ __device__ __forceinline__ V group_sum(V v) {
   return v;
 }
 
+// Row loops take kU slots at a time (loads issued before the FMAs); padding
+// slots have coefficient 0 and the row itself as column.
+constexpr int kU = 4;
+
 // ---------------------------------------------------------------------------
 // y = K x  or  y = b - K x with K = [A (per component), -BT; B, diag(D)]
+// Threads [0, w2) take the velocity rows (w2 = n2 rounded up to a warp), the
+// following ones the pressure rows, so no warp mixes the two.
 // ---------------------------------------------------------------------------
-template <typename T, typename V, int DIM, int L>
+template <typename T, typename V, int DIM>
 __global__ void __launch_bounds__(256) k_spmv_full(DOp<T> op, const V* __restrict__ x,
                                                    const V* __restrict__ b,
                                                    V* __restrict__ y, int resid,
                                                    const int* skip) {
   if (skip && *skip) return;
-  const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t row = gt / L;
-  const int lane = (int)(gt % L);
-  const int64_t n2 = op.n2, ntot = op.n2 + op.nv;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t n2 = op.n2, nv = op.nv, w2 = (n2 + 31) & ~(int64_t)31;
   const V* __restrict__ xp = x + DIM * n2;
-  V acc[DIM];
+  if (t < w2) {
+    const int64_t row = t;
+    if (row >= n2) return;
+    V acc[DIM];
 #pragma unroll
-  for (int c = 0; c < DIM; ++c) acc[c] = V(0);
-  if (row < n2) {
-    const int32_t b0 = op.A.rp[row], b1 = op.A.rp[row + 1];
-    for (int32_t k = b0 + lane; k < b1; k += 4 * L) {
-      V a[4];
-      int32_t j[4];
+    for (int c = 0; c < DIM; ++c) acc[c] = V(0);
+    {
+      const int64_t o1 = op.A.off[(row >> 5) + 1];
+      for (int64_t o = op.A.off[row >> 5] + (row & 31); o < o1; o += kU * 32) {
+        V a[kU];
+        int32_t j[kU];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int32_t kk = k + u * L;
-        const bool ok = kk < b1;
-        a[u] = ok ? (V)op.A.v[kk] : V(0);
-        j[u] = ok ? op.A.ci[kk] : (int32_t)row;
+        for (int u = 0; u < kU; ++u) {
+          const int64_t oo = o + u * 32;
+          const bool ok = oo < o1;
+          a[u] = ok ? (V)op.A.v[oo] : V(0);
+          j[u] = ok ? op.A.ci[oo] : (int32_t)row;
+        }
+        V xv[kU][DIM];
+#pragma unroll
+        for (int u = 0; u < kU; ++u)
+#pragma unroll
+          for (int c = 0; c < DIM; ++c) xv[u][c] = x[c * n2 + j[u]];
+#pragma unroll
+        for (int u = 0; u < kU; ++u)
+#pragma unroll
+          for (int c = 0; c < DIM; ++c) acc[c] += a[u] * xv[u][c];
       }
-      V xv[4][DIM];
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int c = 0; c < DIM; ++c) xv[u][c] = x[c * n2 + j[u]];
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int c = 0; c < DIM; ++c) acc[c] += a[u] * xv[u][c];
     }
-    const int32_t t0 = op.BT.rp[row], t1 = op.BT.rp[row + 1];
-    for (int32_t k = t0 + lane; k < t1; k += L) {
-      const V p = xp[op.BT.ci[k]];
+    {
+      const int64_t s0 = op.BT.off[row >> 5], o1 = op.BT.off[(row >> 5) + 1];
+      for (int64_t o = s0 + (row & 31); o < o1; o += 32) {
+        const int64_t base = (o - (row & 31)) * DIM + (row & 31);
+        const V p = xp[op.BT.ci[o]];
 #pragma unroll
-      for (int c = 0; c < DIM; ++c) acc[c] -= (V)op.BT.v[(int64_t)k * DIM + c] * p;
+        for (int c = 0; c < DIM; ++c) acc[c] -= (V)op.BT.v[base + 32 * c] * p;
+      }
     }
-  } else if (row < ntot) {
-    const int64_t q = row - n2;
-    const int32_t b0 = op.B.rp[q], b1 = op.B.rp[q + 1];
-    for (int32_t k = b0 + lane; k < b1; k += L) {
-      const int32_t c0 = op.B.ci[k];
-#pragma unroll
-      for (int c = 0; c < DIM; ++c) acc[0] += (V)op.B.v[(int64_t)k * DIM + c] * x[c * n2 + c0];
-    }
-  }
-#pragma unroll
-  for (int c = 0; c < DIM; ++c) acc[c] = group_sum<L>(acc[c]);
-  if (lane != 0 || row >= ntot) return;
-  if (row < n2) {
 #pragma unroll
     for (int c = 0; c < DIM; ++c) {
       const int64_t r = c * n2 + row;
       y[r] = resid ? b[r] - acc[c] : acc[c];
     }
   } else {
-    const int64_t q = row - n2;
-    const V v = acc[0] + (V)op.diagp[q] * xp[q];
+    const int64_t q = t - w2;
+    if (q >= nv) return;
+    V acc = V(0);
+    const int64_t o1 = op.B.off[(q >> 5) + 1];
+    for (int64_t o = op.B.off[q >> 5] + (q & 31); o < o1; o += kU * 32) {
+      int32_t j[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int64_t oo = o + u * 32;
+        j[u] = oo < o1 ? op.B.ci[oo] : -1;
+      }
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        if (j[u] < 0) break;
+        const int64_t base = (o + u * 32 - (q & 31)) * DIM + (q & 31);
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) acc += (V)op.B.v[base + 32 * c] * x[c * n2 + j[u]];
+      }
+    }
+    const V v = acc + (V)op.diagp[q] * xp[q];
     const int64_t r = DIM * n2 + q;
     y[r] = resid ? b[r] - v : v;
+  }
+}
+
+// CSR -> SELL-32 value scatter, one thread per row.
+__global__ void k_csr_to_sell(int64_t n, const int32_t* __restrict__ rp,
+                              const double* __restrict__ in, const int64_t* __restrict__ off,
+                              double* __restrict__ out64, float* __restrict__ out32) {
+  const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  const int64_t base = off[r >> 5] + (r & 31);
+  const int32_t k0 = rp[r], len = rp[r + 1] - k0;
+  for (int32_t u = 0; u < len; ++u) {
+    const double v = in[k0 + u];
+    out64[base + 32 * u] = v;
+    if (out32) out32[base + 32 * u] = (float)v;
   }
 }
 
@@ -158,10 +192,6 @@ __device__ __forceinline__ void vstore(T* __restrict__ p, const T (&v)[N]) {
     for (int i = 0; i < N; ++i) p[i] = v[i];
   }
 }
-
-// Row loops take kU matrix entries per lane at a time (loads issued before
-// the FMAs); padding entries point at the row itself with coefficient 0.
-constexpr int kU = 4;
 
 // One Chebyshev kernel of a level.  A level's state is kept as two vectors:
 // the gather vector G (the point the next residual is taken at, x + d, read
@@ -452,8 +482,8 @@ __global__ void k_pin_rows(const int32_t* __restrict__ pinned, int npinned,
 // t_c = r_c + BT_c z_p over the velocity rows (caller order), stored at the
 // level-0 (block-order) row iperm[i] as b0, with the first step from x = 0,
 // G0 = D0 = D^-1 t / theta.
-template <typename T, int DIM, int NCP, int L>
-__global__ void __launch_bounds__(256) k_bt_add_mg(DCsr<T> BT, int64_t n2,
+template <typename T, int DIM, int NCP>
+__global__ void __launch_bounds__(256) k_bt_add_mg(DSell<T> BT, int64_t n2,
                                                    const T* __restrict__ r,
                                                    const T* __restrict__ zp,
                                                    const int32_t* __restrict__ iperm,
@@ -461,22 +491,18 @@ __global__ void __launch_bounds__(256) k_bt_add_mg(DCsr<T> BT, int64_t n2,
                                                    T* __restrict__ b0, T* __restrict__ G0,
                                                    T* __restrict__ D0, const int* skip) {
   if (skip && *skip) return;
-  const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t row = gt / L;
-  const int lane = (int)(gt % L);
+  const int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (row >= n2) return;
   T acc[DIM];
 #pragma unroll
   for (int c = 0; c < DIM; ++c) acc[c] = T(0);
-  if (row < n2) {
-    for (int32_t k = BT.rp[row] + lane; k < BT.rp[row + 1]; k += L) {
-      const T p = zp[BT.ci[k]];
+  const int64_t o1 = BT.off[(row >> 5) + 1];
+  for (int64_t o = BT.off[row >> 5] + (row & 31); o < o1; o += 32) {
+    const int64_t base = (o - (row & 31)) * DIM + (row & 31);
+    const T p = zp[BT.ci[o]];
 #pragma unroll
-      for (int c = 0; c < DIM; ++c) acc[c] += BT.v[(int64_t)k * DIM + c] * p;
-    }
+    for (int c = 0; c < DIM; ++c) acc[c] += BT.v[base + 32 * c] * p;
   }
-#pragma unroll
-  for (int c = 0; c < DIM; ++c) acc[c] = group_sum<L>(acc[c]);
-  if (lane != 0 || row >= n2) return;
   const int64_t dst = iperm ? iperm[row] : row;
   T t[NCP], d0[NCP];
   const T s = dinv0 ? dinv0[dst] * inv_theta0 : T(0);
@@ -510,25 +536,24 @@ inline unsigned grid_stride_blocks(int64_t n) {
 
 template <typename T, typename V>
 void launch_spmv_full(const DOp<T>& op, const V* x, const V* b, V* y, int resid,
-                      const int* skip, int lanes, cudaStream_t s) {
-  const int64_t rows = op.n2 + op.nv;
-  if (op.dim == 2) {
-    if (lanes == 8)
-      k_spmv_full<T, V, 2, 8><<<blocks_for(rows * 8), 256, 0, s>>>(op, x, b, y, resid, skip);
-    else
-      k_spmv_full<T, V, 2, 4><<<blocks_for(rows * 4), 256, 0, s>>>(op, x, b, y, resid, skip);
-  } else {
-    if (lanes == 4)
-      k_spmv_full<T, V, 3, 4><<<blocks_for(rows * 4), 256, 0, s>>>(op, x, b, y, resid, skip);
-    else
-      k_spmv_full<T, V, 3, 8><<<blocks_for(rows * 8), 256, 0, s>>>(op, x, b, y, resid, skip);
-  }
+                      const int* skip, cudaStream_t s) {
+  const int64_t threads = ((op.n2 + 31) & ~(int64_t)31) + op.nv;
+  if (op.dim == 2)
+    k_spmv_full<T, V, 2><<<blocks_for(threads), 256, 0, s>>>(op, x, b, y, resid, skip);
+  else
+    k_spmv_full<T, V, 3><<<blocks_for(threads), 256, 0, s>>>(op, x, b, y, resid, skip);
   count_launches(1);
 }
 template void launch_spmv_full<double, double>(const DOp<double>&, const double*, const double*,
-                                               double*, int, const int*, int, cudaStream_t);
+                                               double*, int, const int*, cudaStream_t);
 template void launch_spmv_full<float, float>(const DOp<float>&, const float*, const float*,
-                                             float*, int, const int*, int, cudaStream_t);
+                                             float*, int, const int*, cudaStream_t);
+
+void launch_csr_to_sell(int64_t n, const int32_t* rp, const double* in, const int64_t* off,
+                        double* out64, float* out32, cudaStream_t s) {
+  k_csr_to_sell<<<blocks_for(n), 256, 0, s>>>(n, rp, in, off, out64, out32);
+  count_launches(1);
+}
 
 template <typename T>
 void launch_cheb_step(const DHier<T>& H, int nc, cudaStream_t s) {
@@ -578,13 +603,13 @@ void launch_precond(const DOp<T>& op, const DHier<T>& HA, const DHier<T>& HK,
   const T* d0 = a1 ? HA.lev[0].dinv : nullptr;
   const T it0 = (T)HA.lev[0].inv_theta;
   if (dim == 2) {
-    k_bt_add_mg<T, 2, 2, 4><<<blocks_for(n2 * 4), 256, 0, s>>>(op.BT, n2, r, zp, HA.iperm, d0, it0,
-                                                             HA.b[0], HA.G0[0], HA.D0[0], skip);
+    k_bt_add_mg<T, 2, 2><<<blocks_for(n2), 256, 0, s>>>(op.BT, n2, r, zp, HA.iperm, d0, it0,
+                                                        HA.b[0], HA.G0[0], HA.D0[0], skip);
     count_launches(1);
     vcycle_level<T, 2>(HA, 0, z, n2, 2, skip, s);
   } else {
-    k_bt_add_mg<T, 3, 4, 4><<<blocks_for(n2 * 4), 256, 0, s>>>(op.BT, n2, r, zp, HA.iperm, d0, it0,
-                                                             HA.b[0], HA.G0[0], HA.D0[0], skip);
+    k_bt_add_mg<T, 3, 4><<<blocks_for(n2), 256, 0, s>>>(op.BT, n2, r, zp, HA.iperm, d0, it0,
+                                                        HA.b[0], HA.G0[0], HA.D0[0], skip);
     count_launches(1);
     vcycle_level<T, 4>(HA, 0, z, n2, 3, skip, s);
   }

@@ -149,9 +149,12 @@ int build_batch_mesh(const fs_mesh_desc* d, int count, Mesh& m) {
   m.c2d.resize(m.ncell * m.nloc);
   m.edges.resize(m.ne * 2);
   m.dirichlet.resize(m.n2);
+  m.node_nat.resize(m.n2);
   for (int i = 0; i < count; ++i) {
     const Mesh& L = loc[i];
     const Instance& I = m.inst[i];
+    for (int64_t j = 0; j < L.n2; ++j)
+      m.node_nat[union_node(m, i, j)] = (int32_t)union_node(m, i, L.node_nat[j]);
     std::memcpy(&m.coords[I.voff * dim], L.coords.data(), sizeof(double) * L.nv * dim);
     for (int64_t j = 0; j < L.n2; ++j) {
       int64_t g = union_node(m, i, j);
@@ -329,6 +332,44 @@ int build_local(const fs_mesh_desc& d, Mesh& m) {
       g[m.nb + e] = (int32_t)(m.nv + (it - uniq.begin()));
     }
   }
+  // Internal order of the edge nodes: grouped by the parity class of their
+  // position on the doubled lattice (the sum of their end points' grid
+  // indices: one class per edge direction), lexicographic (x fastest) within a
+  // class.  Consecutive nodes of a class along a grid line then have the same
+  // stencil shifted by one, so the neighbours that a warp's rows read at one
+  // matrix slot are contiguous.  node_nat keeps the paper order.
+  {
+    const int64_t X = 2 * sx, Y = 2 * sy, Z = 2 * (dim == 3 ? n[2] + 1 : 1);
+    std::vector<std::pair<int64_t, int32_t>> key(m.ne);
+    for (int64_t e = 0; e < m.ne; ++e) {
+      int64_t c[3] = {0, 0, 0};
+      for (int end = 0; end < 2; ++end) {
+        const int64_t v = m.edges[2 * e + end];
+        c[0] += v % sx;
+        c[1] += (v / sx) % sy;
+        c[2] += dim == 3 ? v / (sx * sy) : 0;
+      }
+      const int64_t cls = (c[0] & 1) | (c[1] & 1) << 1 | (c[2] & 1) << 2;
+      key[e] = {((cls * Z + c[2]) * Y + c[1]) * X + c[0], (int32_t)e};
+    }
+    std::sort(key.begin(), key.end());
+    std::vector<int32_t> newid(m.ne), ed(2 * m.ne);
+    m.node_nat.resize(m.n2);
+    for (int64_t v = 0; v < m.nv; ++v) m.node_nat[v] = (int32_t)v;
+    for (int64_t e = 0; e < m.ne; ++e) {
+      const int32_t old = key[e].second;
+      newid[old] = (int32_t)e;
+      ed[2 * e] = m.edges[2 * old];
+      ed[2 * e + 1] = m.edges[2 * old + 1];
+      m.node_nat[m.nv + e] = (int32_t)(m.nv + old);
+    }
+    m.edges.swap(ed);
+    for (int64_t c = 0; c < m.ncell; ++c)
+      for (int e = 0; e < nle; ++e) {
+        int32_t& g = m.c2d[c * m.nloc + m.nb + e];
+        g = (int32_t)(m.nv + newid[g - m.nv]);
+      }
+  }
   m.p2xyz.resize(m.n2 * dim);
   std::memcpy(m.p2xyz.data(), m.coords.data(), sizeof(double) * m.nv * dim);
   for (int64_t e = 0; e < m.ne; ++e)
@@ -400,6 +441,35 @@ void monolithic_pattern(const Mesh& m, std::vector<int64_t>& rowptr,
     col.push_back((int32_t)(dim * m.n2 + q));
     rowptr[dim * m.n2 + q + 1] = (int64_t)col.size();
   }
+}
+
+void natural_dof_map(const Mesh& m, std::vector<int32_t>* c2d, std::vector<uint8_t>* dir,
+                     std::vector<int64_t>* rowptr, std::vector<int32_t>* col) {
+  Mesh nm;
+  nm.dim = m.dim;
+  nm.nloc = m.nloc;
+  nm.nb = m.nb;
+  nm.nv = m.nv;
+  nm.ne = m.ne;
+  nm.n2 = m.n2;
+  nm.ncell = m.ncell;
+  nm.c2d.resize(m.c2d.size());
+  for (size_t k = 0; k < m.c2d.size(); ++k) nm.c2d[k] = m.node_nat[m.c2d[k]];
+  if (dir) {
+    dir->assign(m.n2, 0);
+    for (int64_t q = 0; q < m.n2; ++q) (*dir)[m.node_nat[q]] = m.dirichlet[q];
+  }
+  if (rowptr || col) {
+    cell_pattern(nm, nm.n2, 0, nm.nloc, 0, nm.nloc, nm.A);
+    cell_pattern(nm, nm.nv, 0, nm.nb, 0, nm.nloc, nm.B);
+    cell_pattern(nm, nm.n2, 0, nm.nloc, 0, nm.nb, nm.BT);
+    std::vector<int64_t> rp;
+    std::vector<int32_t> ci;
+    monolithic_pattern(nm, rp, ci);
+    if (rowptr) rowptr->swap(rp);
+    if (col) col->swap(ci);
+  }
+  if (c2d) c2d->swap(nm.c2d);
 }
 
 // ---------------------------------------------------------------------------

@@ -539,9 +539,14 @@ void build_union_hierarchy(const Mesh& m, const std::vector<Mesh>& /*local*/,
   // level-0 rows (instance blocks, each in Z-order) vs the union numbering
   U.perm.clear();
   U.perm.reserve(A0.nrow);
+  bool identity = true;
   for (int i = 0; i < K; ++i)
-    for (int32_t j : H[i].order0)
-      U.perm.push_back((int32_t)(p2_fine ? union_node(m, i, j) : m.inst[i].voff + j));
+    for (int32_t j : H[i].order0) {
+      const int32_t g = (int32_t)(p2_fine ? union_node(m, i, j) : m.inst[i].voff + j);
+      identity = identity && g == (int32_t)U.perm.size();
+      U.perm.push_back(g);
+    }
+  if (identity) U.perm.clear();
   // coarsest: block-diagonal dense inverses
   U.blk_row.assign(K, 0);
   U.blk_n.assign(K, 0);
