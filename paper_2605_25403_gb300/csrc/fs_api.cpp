@@ -157,6 +157,7 @@ struct fs_problem {
   int ntiles = 0;
   SegHost* host_status = nullptr;  // pinned, nseg entries
   int* host_retired = nullptr;     // pinned, nseg entries
+  double* host_rtol = nullptr;     // pinned, nseg entries
   cudaEvent_t ev = nullptr;
   SolveCtx ctx;
   std::vector<fs_solve_stats> last_stats;  // per instance, last solve
@@ -198,6 +199,7 @@ struct fs_problem {
     if (stream) cudaStreamSynchronize(stream);
     if (host_status) cudaFreeHost(host_status);
     if (host_retired) cudaFreeHost(host_retired);
+    if (host_rtol) cudaFreeHost(host_rtol);
     if (ev) cudaEventDestroy(ev);
     if (own_stream && stream) cudaStreamDestroy(stream);
   }
@@ -491,13 +493,13 @@ void issue_check(fs_problem* P, Precision<T>& pr, const T* x, const T* b) {
 // One restart cycle: init (tolerances relative to ||b|| or to beta), v0,
 // m Arnoldi steps, update of x.
 template <typename T>
-void issue_iter(fs_problem* P, Precision<T>& pr, T* x, double rtol, int relative_to_beta) {
+void issue_iter(fs_problem* P, Precision<T>& pr, T* x, int relative_to_beta) {
   Krylov<T>& K = pr.kr;
   cudaStream_t s = P->stream;
   const int* skip = &K.ctl->all_done;
   const int64_t n = K.n;
   const TileList tl = P->tl();
-  launch_seg_cycle_init(K.st, K.ctl, rtol, relative_to_beta, s);
+  launch_seg_cycle_init(K.st, K.ctl, relative_to_beta, s);
   launch_seg_scale<T>(K.Vb, tl, K.st, 0, s);
   for (int j = 0; j < K.m; ++j) {
     T* vj = K.Vb + (int64_t)j * n;
@@ -564,6 +566,15 @@ int push_retired(fs_problem* P, Krylov<T>& K) {
   for (int s = 0; s < P->nseg; ++s) P->host_retired[s] = P->ctx.retired[s];
   FS_CUDA(cudaMemcpy2DAsync(&K.st[0].retired, sizeof(SegState), P->host_retired, sizeof(int),
                             sizeof(int), P->nseg, cudaMemcpyHostToDevice, P->stream));
+  return FS_OK;
+}
+
+// Per-segment cycle targets (read by the cycle-init kernel).
+template <typename T>
+int push_rtol(fs_problem* P, Krylov<T>& K, const std::vector<double>& rtol) {
+  for (int s = 0; s < P->nseg; ++s) P->host_rtol[s] = rtol[s];
+  FS_CUDA(cudaMemcpy2DAsync(&K.st[0].rtol, sizeof(SegState), P->host_rtol, sizeof(double),
+                            sizeof(double), P->nseg, cudaMemcpyHostToDevice, P->stream));
   return FS_OK;
 }
 
@@ -696,8 +707,9 @@ int advance(fs_problem* P) {
       }
       Krylov<double>& K = P->p64.kr;
       FS_TRY(push_retired(P, K));
+      FS_TRY(push_rtol(P, K, std::vector<double>(P->nseg, c.o.rtol)));
       FS_TRY(run_graph<double>(P, K, false, c.x, P->b, graph,
-                               [&]() { issue_iter<double>(P, P->p64, c.x, c.o.rtol, 0); }));
+                               [&]() { issue_iter<double>(P, P->p64, c.x, 0); }));
       FS_TRY(enqueue_status(P, K));
       c.phase = PH_ITER;
       return FS_OK;
@@ -731,13 +743,27 @@ int advance(fs_problem* P) {
       Precision<float>& pr = P->p32;
       Krylov<float>& K = pr.kr;
       FS_TRY(push_retired(P, K));
+      // One inner cycle per refinement, whose Arnoldi estimate stops at a
+      // target relative to its own initial residual: inner_rtol, or the
+      // reduction still missing to reach rtol (with a 0.3 margin) when that
+      // is less, so the last refinement does not run a full cycle.  The
+      // FP32 operator limits what one refinement gains (about 1e-5 here),
+      // so deeper targets only cost iterations.
+      {
+        std::vector<double> tgt(P->nseg, c.o.inner_rtol);
+        for (int q = 0; q < P->nseg; ++q) {
+          const SegHost& h = P->host_status[q];
+          const double bn = h.bnorm > 0 ? h.bnorm : 1.0;
+          if (!c.retired[q] && h.rnorm > 0)
+            tgt[q] = std::min(0.5, std::max(c.o.inner_rtol, 0.3 * c.o.rtol * bn / h.rnorm));
+        }
+        FS_TRY(push_rtol(P, K, tgt));
+      }
       launch_seg_normalise<double, float>(P->r64, K.rhs, P->tl(), K.st, s);
       FS_CUDA(cudaMemsetAsync(K.sol, 0, sizeof(float) * P->ndof, s));
-      // one inner cycle whose Arnoldi estimate stops at inner_rtol relative
-      // to its own initial residual
       FS_TRY(run_graph<float>(P, K, false, K.sol, K.rhs, graph, [&]() {
         issue_check<float>(P, pr, K.sol, K.rhs);
-        issue_iter<float>(P, pr, K.sol, c.o.inner_rtol, 1);
+        issue_iter<float>(P, pr, K.sol, 1);
       }));
       launch_seg_axpy<float, double>(c.x, K.sol, P->tl(), K.st, s);
       launch_spmv_full<double, double>(P->p64.op, c.x, P->b, P->r64, 1, nullptr, s);
@@ -948,6 +974,7 @@ int fs_problem_create_batch(fs_mesh* mesh, const fs_problem_desc* descs, int cou
   FS_CUDA(cudaEventCreateWithFlags(&P->ev, cudaEventDisableTiming));
   FS_CUDA(cudaMallocHost(&P->host_status, sizeof(SegHost) * count));
   FS_CUDA(cudaMallocHost(&P->host_retired, sizeof(int) * count));
+  FS_CUDA(cudaMallocHost(&P->host_rtol, sizeof(double) * count));
   std::call_once(g_ref_once, []() {
     ref_tensors(2, g_ref2);
     ref_tensors(3, g_ref3);

@@ -203,6 +203,9 @@ struct SegState {
   int bad;          // NaN/Inf seen
   int retired;      // set by the host: the segment no longer iterates
   int first_tile, ntiles;
+  double rtol;      // set by the host: target of the next cycle, relative to
+                    // beta or to bnorm (device data, so captured graphs stay
+                    // valid when it changes)
   double hn;        // ||w|| before normalisation
   unsigned counter[8];
   double H[(kMaxRestart + 1) * kMaxRestart];
@@ -219,8 +222,7 @@ struct KCtl {
 template <typename V>
 void launch_seg_norm(const V* x, const TileList& tl, SegState* st, double* partial,
                      int field, cudaStream_t s);
-void launch_seg_cycle_init(SegState* st, KCtl* ctl, double rtol, int relative_to_beta,
-                           cudaStream_t s);
+void launch_seg_cycle_init(SegState* st, KCtl* ctl, int relative_to_beta, cudaStream_t s);
 template <typename V>
 void launch_seg_scale(V* x, const TileList& tl, const SegState* st, int field,
                       cudaStream_t s);

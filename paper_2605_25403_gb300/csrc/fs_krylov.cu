@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(kKB) k_seg_norm(const V* __restrict__ x, const
 // Start of a restart cycle: tolerances, right-hand side of the least-squares
 // problem, done flags (converged, retired by the host, or non-finite).
 // tol_abs = rtol * (relative_to_beta ? beta : bnorm).
-__global__ void k_seg_cycle_init(SegState* st, KCtl* ctl, double rtol, int relative_to_beta) {
+__global__ void k_seg_cycle_init(SegState* st, KCtl* ctl, int relative_to_beta) {
   __shared__ int ndone;
   if (threadIdx.x == 0) ndone = 0;
   __syncthreads();
@@ -112,7 +112,7 @@ __global__ void k_seg_cycle_init(SegState* st, KCtl* ctl, double rtol, int relat
   for (int s = threadIdx.x; s < ctl->nseg; s += blockDim.x) {
     SegState& S = st[s];
     const double beta = S.beta;
-    S.tol_abs = rtol * (relative_to_beta ? beta : S.bnorm);
+    S.tol_abs = S.rtol * (relative_to_beta ? beta : S.bnorm);
     S.k = 0;
     S.bad = isfinite(beta) ? 0 : 1;
     S.resid = beta;
@@ -327,9 +327,8 @@ template void launch_seg_norm<double>(const double*, const TileList&, SegState*,
 template void launch_seg_norm<float>(const float*, const TileList&, SegState*, double*, int,
                                      cudaStream_t);
 
-void launch_seg_cycle_init(SegState* st, KCtl* ctl, double rtol, int relative_to_beta,
-                           cudaStream_t s) {
-  k_seg_cycle_init<<<1, 256, 0, s>>>(st, ctl, rtol, relative_to_beta);
+void launch_seg_cycle_init(SegState* st, KCtl* ctl, int relative_to_beta, cudaStream_t s) {
+  k_seg_cycle_init<<<1, 256, 0, s>>>(st, ctl, relative_to_beta);
   count_launches(1);
 }
 

@@ -158,6 +158,36 @@ def test_graph_and_direct_launch_agree(fs):
     assert rel_l2(xs[0], xs[1]) <= 1e-12
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32_refine"])
+def test_solve_options_take_effect_between_solves(fs, prec):
+    """Restart cycles run as captured CUDA graphs; tolerances are device
+    data, so a second solve on the same problem with other options meets
+    those options (a graph holding the first call's tolerance would not)."""
+    p = fs.FS_PREC_FP64 if prec == "fp64" else fs.FS_PREC_FP32_REFINE
+    S = fs.Stepper.from_workload(W.channel(24, 8), precision=p)
+    try:
+        fs.fs_step(S.prob, 1)
+        x0, t0 = S.state()
+        fs.fs_assemble_step(S.prob, t0 + W.channel(24, 8).dt)
+        out = {}
+        for rtol in (1e-6, 1e-13, 1e-6):
+            fs.fs_set_state(S.prob, x0, t0)
+            st = fs.fs_solve(S.prob, fs.fs_default_solve_opts(rtol=rtol))
+            assert st["status"] == 0 and st["rel_res"] <= rtol
+            out.setdefault(rtol, []).append(st["iters"])
+        assert out[1e-6][0] == out[1e-6][1] < out[1e-13][0]
+        if prec == "fp32_refine":
+            its = []
+            for inner in (1e-2, 1e-5):
+                fs.fs_set_state(S.prob, x0, t0)
+                st = fs.fs_solve(S.prob, fs.fs_default_solve_opts(inner_rtol=inner))
+                assert st["status"] == 0 and st["rel_res"] <= 1e-14 * 100
+                its.append(st["refinements"])
+            assert its[0] > its[1]
+    finally:
+        S.close()
+
+
 @pytest.mark.parametrize("wl", [W.C1, W.cube(3)], ids=lambda w: w.name)
 def test_csr_residual_norm_matches_host(fs, wl):
     """The device residual check of an exported monolithic system agrees with
