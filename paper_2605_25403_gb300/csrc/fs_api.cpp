@@ -89,7 +89,8 @@ struct Krylov {
   SegState* st = nullptr;
   KCtl* ctl = nullptr;
   cudaGraphExec_t g_check = nullptr, g_iter = nullptr;
-  size_t n_check = 0, n_iter = 0;  // kernel nodes per graph
+  size_t n_check = 0, n_iter = 0;  // top-level nodes per graph
+  size_t n_body = 0;               // kernels of one Arnoldi step (loop body)
   const void* g_x = nullptr;       // buffers the graphs were captured with
   const void* g_b = nullptr;
 };
@@ -127,6 +128,7 @@ struct fs_problem {
   std::vector<fs_problem_desc> inst_desc;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  cudaStream_t side = nullptr;  // captures the body of the Arnoldi loop node
   int dim = 0, nseg = 1;
   int64_t n2 = 0, nv = 0, ndof = 0;
   std::vector<void*> allocs;
@@ -202,6 +204,7 @@ struct fs_problem {
     if (host_rtol) cudaFreeHost(host_rtol);
     if (ev) cudaEventDestroy(ev);
     if (own_stream && stream) cudaStreamDestroy(stream);
+    if (side) cudaStreamDestroy(side);
   }
 };
 
@@ -491,36 +494,76 @@ void issue_check(fs_problem* P, Precision<T>& pr, const T* x, const T* b) {
 }
 
 // One restart cycle: init (tolerances relative to ||b|| or to beta), v0,
-// m Arnoldi steps, update of x.
+// up to m Arnoldi steps, update of x.  Launched directly, the m steps are
+// issued one by one (steps after convergence exit at once).  Captured in a
+// graph, one step is captured as the body of a conditional WHILE node whose
+// condition the device sets (the cycle init, then every step's Givens
+// kernel), so the graph runs exactly the steps the cycle needs.
 template <typename T>
-void issue_iter(fs_problem* P, Precision<T>& pr, T* x, int relative_to_beta) {
+int issue_iter(fs_problem* P, Precision<T>& pr, T* x, int relative_to_beta) {
   Krylov<T>& K = pr.kr;
   cudaStream_t s = P->stream;
   const int* skip = &K.ctl->all_done;
   const int64_t n = K.n;
   const TileList tl = P->tl();
-  launch_seg_cycle_init(K.st, K.ctl, relative_to_beta, s);
+  const bool loop = g_capturing;
+  cudaGraphConditionalHandle cond = 0;
+  if (loop) {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t cg;
+    FS_CUDA(cudaStreamGetCaptureInfo(s, &cs, nullptr, &cg, nullptr, nullptr, nullptr));
+    FS_CUDA(cudaGraphConditionalHandleCreate(&cond, cg, 0, 0));
+  }
+  launch_seg_cycle_init(K.st, K.ctl, relative_to_beta, cond, s);
   launch_seg_scale<T>(K.Vb, tl, K.st, 0, s);
-  for (int j = 0; j < K.m; ++j) {
-    T* vj = K.Vb + (int64_t)j * n;
-    T* zj = K.Z + (int64_t)j * n;
-    T* w = K.Vb + (int64_t)(j + 1) * n;
+  const int* jp = &K.ctl->j;
+  auto step = [&](cudaStream_t q) {
+    const JVec<const T> vj(K.Vb, jp, n);
+    const JVec<T> zj(K.Z, jp, n);
+    const JVec<const T> zjc(K.Z, jp, n);
+    const JVec<T> w(K.Vb + n, jp, n);
     launch_precond<T>(pr.op, pr.HA, pr.HK, pr.mplinv_nu, 1.0 / P->desc.dt, P->pinned,
-                      P->npinned, vj, zj, K.work_p, K.work_u, skip, s);
-    launch_spmv_full<T, T>(pr.op, zj, nullptr, w, 0, skip, s);
-    launch_seg_cgs2<T>(K.Vb, n, j, tl, K.st, K.ctl, K.partial, s);
-    launch_seg_scale<T>(w, tl, K.st, 1, s);
-    launch_seg_givens(K.st, K.ctl, P->nseg, j, s);
+                      P->npinned, vj, zj, K.work_p, K.work_u, skip, q);
+    launch_spmv_full<T, T>(pr.op, zjc, nullptr, w, 0, skip, q);
+    launch_seg_cgs2<T>(K.Vb, n, tl, K.st, K.ctl, K.partial, q);
+    launch_seg_scale<T>(w, tl, K.st, 1, q);
+    launch_seg_givens(K.st, K.ctl, P->nseg, cond, q);
+  };
+  if (loop) {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t cg;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    FS_CUDA(cudaStreamGetCaptureInfo(s, &cs, nullptr, &cg, &deps, nullptr, &nd));
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = cond;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t cn;
+    FS_CUDA(cudaGraphAddNode(&cn, cg, deps, nullptr, nd, &np));
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    FS_CUDA(cudaStreamUpdateCaptureDependencies(s, &cn, nullptr, 1,
+                                                cudaStreamSetCaptureDependencies));
+    FS_CUDA(cudaStreamBeginCaptureToGraph(P->side, body, nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeThreadLocal));
+    step(P->side);
+    cudaGraph_t got;
+    FS_CUDA(cudaStreamEndCapture(P->side, &got));
+    FS_CUDA(cudaGraphGetNodes(body, nullptr, &K.n_body));
+  } else {
+    for (int j = 0; j < K.m; ++j) step(s);
   }
   launch_seg_update_x<T, T>(K.st, K.ctl, K.Z, n, tl, x, s);
+  return FS_OK;
 }
 
 // Runs `issue` directly or as a cached CUDA graph (keyed by x and b).
 template <typename T>
 int run_graph(fs_problem* P, Krylov<T>& K, bool check, const void* x, const void* b,
-              bool use_graph, const std::function<void()>& issue) {
+              bool use_graph, const std::function<int()>& issue) {
   if (!use_graph) {
-    issue();
+    FS_TRY(issue());
     return check_launch("gmres cycle");
   }
   if (K.g_x != x || K.g_b != b) {
@@ -536,9 +579,18 @@ int run_graph(fs_problem* P, Krylov<T>& K, bool check, const void* x, const void
     cudaGraph_t graph;
     FS_CUDA(cudaStreamBeginCapture(P->stream, cudaStreamCaptureModeThreadLocal));
     g_capturing = true;
-    issue();
+    int rc = issue();
     g_capturing = false;
-    FS_CUDA(cudaStreamEndCapture(P->stream, &graph));
+    cudaError_t ec = cudaStreamEndCapture(P->stream, &graph);
+    if (rc != FS_OK) {
+      if (ec == cudaSuccess) cudaGraphDestroy(graph);
+      return rc;
+    }
+    if (ec != cudaSuccess) {
+      set_error(std::string("graph capture: ") + cudaGetErrorString(ec));
+      return FS_ERR_CUDA;
+    }
+    // kernel nodes at the top level (a loop node counts as one)
     cudaGraphGetNodes(graph, nullptr, nodes);
     cudaError_t e = cudaGraphInstantiate(g, graph, 0);
     cudaGraphDestroy(graph);
@@ -617,8 +669,10 @@ int start_solve(fs_problem* P, double* x) {
     Krylov<double>& K = P->p64.kr;
     FS_TRY(push_retired(P, K));
     launch_seg_norm<double>(P->b, P->tl(), K.st, K.partial, 1, s);
-    FS_TRY(run_graph<double>(P, K, true, x, P->b, c.o.use_graph != 0,
-                             [&]() { issue_check<double>(P, P->p64, x, P->b); }));
+    FS_TRY(run_graph<double>(P, K, true, x, P->b, c.o.use_graph != 0, [&]() {
+      issue_check<double>(P, P->p64, x, P->b);
+      return FS_OK;
+    }));
     FS_TRY(enqueue_status(P, K));
     c.phase = PH_CHECK;
   } else {
@@ -695,6 +749,17 @@ bool judge(fs_problem* P, bool refinement) {
   return all;
 }
 
+// Kernels run by a graph's Arnoldi loop node: the body ran until every
+// segment was done, i.e. as many times as the most steps a segment took.
+template <typename T>
+void count_body_launches(fs_problem* P, const Krylov<T>& K, bool graph) {
+  if (!graph) return;
+  int kmax = 0;
+  for (int q = 0; q < P->nseg; ++q)
+    if (!P->ctx.retired[q]) kmax = std::max(kmax, P->host_status[q].k);
+  count_launches((int64_t)K.n_body * kmax);
+}
+
 int advance(fs_problem* P) {
   SolveCtx& c = P->ctx;
   cudaStream_t s = P->stream;
@@ -709,12 +774,13 @@ int advance(fs_problem* P) {
       FS_TRY(push_retired(P, K));
       FS_TRY(push_rtol(P, K, std::vector<double>(P->nseg, c.o.rtol)));
       FS_TRY(run_graph<double>(P, K, false, c.x, P->b, graph,
-                               [&]() { issue_iter<double>(P, P->p64, c.x, 0); }));
+                               [&]() { return issue_iter<double>(P, P->p64, c.x, 0); }));
       FS_TRY(enqueue_status(P, K));
       c.phase = PH_ITER;
       return FS_OK;
     }
     case PH_ITER: {
+      count_body_launches(P, P->p64.kr, graph);
       for (int q = 0; q < P->nseg; ++q) {
         if (c.retired[q]) continue;
         c.iters[q] += P->host_status[q].k;
@@ -729,8 +795,10 @@ int advance(fs_problem* P) {
       }
       Krylov<double>& K = P->p64.kr;
       FS_TRY(push_retired(P, K));
-      FS_TRY(run_graph<double>(P, K, true, c.x, P->b, graph,
-                               [&]() { issue_check<double>(P, P->p64, c.x, P->b); }));
+      FS_TRY(run_graph<double>(P, K, true, c.x, P->b, graph, [&]() {
+        issue_check<double>(P, P->p64, c.x, P->b);
+        return FS_OK;
+      }));
       FS_TRY(enqueue_status(P, K));
       c.phase = PH_CHECK;
       return FS_OK;
@@ -763,7 +831,7 @@ int advance(fs_problem* P) {
       FS_CUDA(cudaMemsetAsync(K.sol, 0, sizeof(float) * P->ndof, s));
       FS_TRY(run_graph<float>(P, K, false, K.sol, K.rhs, graph, [&]() {
         issue_check<float>(P, pr, K.sol, K.rhs);
-        issue_iter<float>(P, pr, K.sol, 1);
+        return issue_iter<float>(P, pr, K.sol, 1);
       }));
       launch_seg_axpy<float, double>(c.x, K.sol, P->tl(), K.st, s);
       launch_spmv_full<double, double>(P->p64.op, c.x, P->b, P->r64, 1, nullptr, s);
@@ -775,6 +843,7 @@ int advance(fs_problem* P) {
       return check_launch("refinement");
     }
     case PH_INNER: {  // inner cycle finished and FP64 residual recomputed
+      count_body_launches(P, P->p32.kr, graph);
       for (int q = 0; q < P->nseg; ++q) {
         if (c.retired[q]) continue;
         c.iters[q] += P->host_status[q].k;
@@ -972,6 +1041,7 @@ int fs_problem_create_batch(fs_mesh* mesh, const fs_problem_desc* descs, int cou
     P->own_stream = true;
   }
   FS_CUDA(cudaEventCreateWithFlags(&P->ev, cudaEventDisableTiming));
+  FS_CUDA(cudaStreamCreateWithFlags(&P->side, cudaStreamNonBlocking));
   FS_CUDA(cudaMallocHost(&P->host_status, sizeof(SegHost) * count));
   FS_CUDA(cudaMallocHost(&P->host_retired, sizeof(int) * count));
   FS_CUDA(cudaMallocHost(&P->host_rtol, sizeof(double) * count));

@@ -38,6 +38,22 @@ struct DSell {
   const T* v = nullptr;
 };
 
+// A vector addressed through the device-side Arnoldi step index: base +
+// (*j) stride (base itself when j is null).  The kernels of one Arnoldi step
+// take their Krylov vectors this way, so that one captured step can be
+// replayed by a conditional loop node while j advances on the device.
+template <typename T>
+struct JVec {
+  T* base = nullptr;
+  const int* j = nullptr;
+  int64_t stride = 0;
+  JVec() = default;
+  JVec(T* b) : base(b) {}
+  JVec(T* b, const int* jj, int64_t st) : base(b), j(jj), stride(st) {}
+  JVec<T> shifted(int64_t o) const { return JVec<T>(base + o, j, stride); }
+  __device__ __forceinline__ T* get() const { return j ? base + (int64_t)(*j) * stride : base; }
+};
+
 // Mesh tables and block patterns of one problem on the device.
 struct DMesh {
   int dim = 0, nloc = 0, nb = 0;
@@ -118,7 +134,7 @@ struct DOp {
 
 // y = K x (resid == 0) or y = b - K x (resid == 1); vectors of type V.
 template <typename T, typename V>
-void launch_spmv_full(const DOp<T>& op, const V* x, const V* b, V* y,
+void launch_spmv_full(const DOp<T>& op, JVec<const V> x, const V* b, JVec<V> y,
                       int resid, const int* skip, cudaStream_t s);
 
 // Scalar CSR values (row pointers rp) into a SELL-32 layout with slice
@@ -173,7 +189,7 @@ void launch_convert(const A* in, B* out, int64_t n, const double* scale,
 template <typename T>
 void launch_precond(const DOp<T>& op, const DHier<T>& HA, const DHier<T>& HK,
                     const T* mpl_inv_nu, double inv_dt, const int32_t* pinned,
-                    int npinned, const T* r, T* z, T* work_p, T* work_u,
+                    int npinned, JVec<const T> r, JVec<T> z, T* work_p, T* work_u,
                     const int* skip, cudaStream_t s);
 
 // ---- segmented Krylov (fs_krylov.cu) -------------------------------------
@@ -217,19 +233,27 @@ struct KCtl {
   int nseg;      // number of segments
   int ndone;     // segments done in this cycle
   int all_done;  // every segment done: the spanning kernels skip
+  int j;         // Arnoldi step of the cycle (reset by the cycle init,
+                 // advanced by the Givens kernel)
 };
 
 template <typename V>
 void launch_seg_norm(const V* x, const TileList& tl, SegState* st, double* partial,
                      int field, cudaStream_t s);
-void launch_seg_cycle_init(SegState* st, KCtl* ctl, int relative_to_beta, cudaStream_t s);
+// cond: the handle of a conditional loop node replaying the Arnoldi step
+// (0 when the steps are launched one by one); the cycle init sets it to
+// "not every segment done", the Givens kernel to "not done and j < m".
+void launch_seg_cycle_init(SegState* st, KCtl* ctl, int relative_to_beta,
+                           cudaGraphConditionalHandle cond, cudaStream_t s);
 template <typename V>
-void launch_seg_scale(V* x, const TileList& tl, const SegState* st, int field,
+void launch_seg_scale(JVec<V> x, const TileList& tl, const SegState* st, int field,
                       cudaStream_t s);
+// CGS2 on w = V[j + 1] with j = ctl->j
 template <typename V>
-void launch_seg_cgs2(V* Vb, int64_t n, int j, const TileList& tl, SegState* st,
+void launch_seg_cgs2(V* Vb, int64_t n, const TileList& tl, SegState* st,
                      const KCtl* ctl, double* partial, cudaStream_t s);
-void launch_seg_givens(SegState* st, KCtl* ctl, int nseg, int j, cudaStream_t s);
+void launch_seg_givens(SegState* st, KCtl* ctl, int nseg, cudaGraphConditionalHandle cond,
+                       cudaStream_t s);
 template <typename V, typename X>
 void launch_seg_update_x(const SegState* st, const KCtl* ctl, const V* Z, int64_t n,
                          const TileList& tl, X* x, cudaStream_t s);

@@ -104,7 +104,8 @@ __global__ void __launch_bounds__(kKB) k_seg_norm(const V* __restrict__ x, const
 // Start of a restart cycle: tolerances, right-hand side of the least-squares
 // problem, done flags (converged, retired by the host, or non-finite).
 // tol_abs = rtol * (relative_to_beta ? beta : bnorm).
-__global__ void k_seg_cycle_init(SegState* st, KCtl* ctl, int relative_to_beta) {
+__global__ void k_seg_cycle_init(SegState* st, KCtl* ctl, int relative_to_beta,
+                                 cudaGraphConditionalHandle cond) {
   __shared__ int ndone;
   if (threadIdx.x == 0) ndone = 0;
   __syncthreads();
@@ -126,16 +127,19 @@ __global__ void k_seg_cycle_init(SegState* st, KCtl* ctl, int relative_to_beta) 
   if (threadIdx.x == 0) {
     ctl->ndone = ndone;
     ctl->all_done = ndone == ctl->nseg ? 1 : 0;
+    ctl->j = 0;
+    if (cond) cudaGraphSetConditional(cond, ndone == ctl->nseg ? 0u : 1u);
   }
 }
 
 // x *= 1 / (field 0: beta, 1: hn) of the tile's segment (skipped once done)
 template <typename V>
-__global__ void __launch_bounds__(kKB) k_seg_scale(V* __restrict__ x, const Tile* tiles,
+__global__ void __launch_bounds__(kKB) k_seg_scale(JVec<V> xv, const Tile* tiles,
                                                    const SegState* st, int field) {
   const Tile t = tiles[blockIdx.x];
   const SegState& S = st[t.seg];
   if (S.done) return;
+  V* __restrict__ x = xv.get();
   const V f = (V)(1.0 / (field == 0 ? S.beta : S.hn));
   for (int e = threadIdx.x; e < t.len; e += kKB) x[t.start + e] *= f;
 }
@@ -144,12 +148,13 @@ __global__ void __launch_bounds__(kKB) k_seg_scale(V* __restrict__ x, const Tile
 //   1: h = V^T w -> H[:, j];  2: w -= V h, h2 = V^T w -> H[:, j] += h2;
 //   3: w -= V h2, ||w|| -> H[j+1, j] = hn.
 template <typename V, int PASS>
-__global__ void __launch_bounds__(kKB) k_seg_cgs(V* __restrict__ Vb, int64_t n, int j,
+__global__ void __launch_bounds__(kKB) k_seg_cgs(V* __restrict__ Vb, int64_t n,
                                                  const Tile* tiles, int ntiles, SegState* st,
                                                  const KCtl* ctl, double* partial) {
   const Tile t = tiles[blockIdx.x];
   SegState& S = st[t.seg];
   if (S.done) return;
+  const int j = ctl->j;
   constexpr int NV = kMaxRestart + 1;
   constexpr int NW = kKB / 32;
   __shared__ double coef[NV];
@@ -223,11 +228,14 @@ __global__ void __launch_bounds__(kKB) k_seg_cgs(V* __restrict__ Vb, int64_t n, 
   }
 }
 
-// Givens rotations of column j of every active segment.
-__global__ void k_seg_givens(SegState* st, KCtl* ctl, int j) {
+// Givens rotations of column j = ctl->j of every active segment (one block,
+// segments strided over its threads); then the step index advances and the
+// condition of the loop node (if any) becomes "a segment is still active and
+// j < m".
+__global__ void k_seg_givens(SegState* st, KCtl* ctl, cudaGraphConditionalHandle cond) {
   const int m = ctl->m;
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < ctl->nseg;
-       s += gridDim.x * blockDim.x) {
+  const int j = ctl->j;
+  for (int s = threadIdx.x; s < ctl->nseg; s += blockDim.x) {
     SegState& S = st[s];
     if (S.done) continue;
     double* H = S.H;
@@ -259,6 +267,12 @@ __global__ void k_seg_givens(SegState* st, KCtl* ctl, int j) {
       S.done = 1;
       if (atomicAdd(&ctl->ndone, 1) + 1 == ctl->nseg) ctl->all_done = 1;
     }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int all = atomicAdd(&ctl->all_done, 0);
+    ctl->j = j + 1;
+    if (cond) cudaGraphSetConditional(cond, (!all && j + 1 < m) ? 1u : 0u);
   }
 }
 
@@ -327,36 +341,40 @@ template void launch_seg_norm<double>(const double*, const TileList&, SegState*,
 template void launch_seg_norm<float>(const float*, const TileList&, SegState*, double*, int,
                                      cudaStream_t);
 
-void launch_seg_cycle_init(SegState* st, KCtl* ctl, int relative_to_beta, cudaStream_t s) {
-  k_seg_cycle_init<<<1, 256, 0, s>>>(st, ctl, relative_to_beta);
+void launch_seg_cycle_init(SegState* st, KCtl* ctl, int relative_to_beta,
+                           cudaGraphConditionalHandle cond, cudaStream_t s) {
+  k_seg_cycle_init<<<1, 256, 0, s>>>(st, ctl, relative_to_beta, cond);
   count_launches(1);
 }
 
 template <typename V>
-void launch_seg_scale(V* x, const TileList& tl, const SegState* st, int field, cudaStream_t s) {
+void launch_seg_scale(JVec<V> x, const TileList& tl, const SegState* st, int field,
+                      cudaStream_t s) {
   k_seg_scale<V><<<tl.ntiles, kKB, 0, s>>>(x, tl.tiles, st, field);
   count_launches(1);
 }
-template void launch_seg_scale<double>(double*, const TileList&, const SegState*, int,
+template void launch_seg_scale<double>(JVec<double>, const TileList&, const SegState*, int,
                                        cudaStream_t);
-template void launch_seg_scale<float>(float*, const TileList&, const SegState*, int,
+template void launch_seg_scale<float>(JVec<float>, const TileList&, const SegState*, int,
                                       cudaStream_t);
 
 template <typename V>
-void launch_seg_cgs2(V* Vb, int64_t n, int j, const TileList& tl, SegState* st, const KCtl* ctl,
+void launch_seg_cgs2(V* Vb, int64_t n, const TileList& tl, SegState* st, const KCtl* ctl,
                      double* partial, cudaStream_t s) {
-  k_seg_cgs<V, 1><<<tl.ntiles, kKB, 0, s>>>(Vb, n, j, tl.tiles, tl.ntiles, st, ctl, partial);
-  k_seg_cgs<V, 2><<<tl.ntiles, kKB, 0, s>>>(Vb, n, j, tl.tiles, tl.ntiles, st, ctl, partial);
-  k_seg_cgs<V, 3><<<tl.ntiles, kKB, 0, s>>>(Vb, n, j, tl.tiles, tl.ntiles, st, ctl, partial);
+  k_seg_cgs<V, 1><<<tl.ntiles, kKB, 0, s>>>(Vb, n, tl.tiles, tl.ntiles, st, ctl, partial);
+  k_seg_cgs<V, 2><<<tl.ntiles, kKB, 0, s>>>(Vb, n, tl.tiles, tl.ntiles, st, ctl, partial);
+  k_seg_cgs<V, 3><<<tl.ntiles, kKB, 0, s>>>(Vb, n, tl.tiles, tl.ntiles, st, ctl, partial);
   count_launches(3);
 }
-template void launch_seg_cgs2<double>(double*, int64_t, int, const TileList&, SegState*,
-                                      const KCtl*, double*, cudaStream_t);
-template void launch_seg_cgs2<float>(float*, int64_t, int, const TileList&, SegState*,
-                                     const KCtl*, double*, cudaStream_t);
+template void launch_seg_cgs2<double>(double*, int64_t, const TileList&, SegState*, const KCtl*,
+                                      double*, cudaStream_t);
+template void launch_seg_cgs2<float>(float*, int64_t, const TileList&, SegState*, const KCtl*,
+                                     double*, cudaStream_t);
 
-void launch_seg_givens(SegState* st, KCtl* ctl, int nseg, int j, cudaStream_t s) {
-  k_seg_givens<<<(nseg + 127) / 128, 128, 0, s>>>(st, ctl, j);
+void launch_seg_givens(SegState* st, KCtl* ctl, int nseg, cudaGraphConditionalHandle cond,
+                       cudaStream_t s) {
+  (void)nseg;
+  k_seg_givens<<<1, 256, 0, s>>>(st, ctl, cond);
   count_launches(1);
 }
 

@@ -48,11 +48,12 @@ constexpr int kU = 4;
 // following ones the pressure rows, so no warp mixes the two.
 // ---------------------------------------------------------------------------
 template <typename T, typename V, int DIM>
-__global__ void __launch_bounds__(256) k_spmv_full(DOp<T> op, const V* __restrict__ x,
-                                                   const V* __restrict__ b,
-                                                   V* __restrict__ y, int resid,
-                                                   const int* skip) {
+__global__ void __launch_bounds__(256) k_spmv_full(DOp<T> op, JVec<const V> xv,
+                                                   const V* __restrict__ b, JVec<V> yv,
+                                                   int resid, const int* skip) {
   if (skip && *skip) return;
+  const V* __restrict__ x = xv.get();
+  V* __restrict__ y = yv.get();
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t n2 = op.n2, nv = op.nv, w2 = (n2 + 31) & ~(int64_t)31;
   const V* __restrict__ xp = x + DIM * n2;
@@ -209,7 +210,7 @@ __global__ void __launch_bounds__(256) k_mg(DSell<T> A, const T* __restrict__ di
                                             const T* __restrict__ Gin,
                                             const T* __restrict__ Din,
                                             T* __restrict__ Gout, T* __restrict__ Dout,
-                                            T alpha, T beta, T inv_theta, T* __restrict__ out,
+                                            T alpha, T beta, T inv_theta, JVec<T> outv,
                                             int64_t out_ld, const int32_t* __restrict__ perm,
                                             int nc, const int* skip) {
   if (skip && *skip) return;
@@ -264,6 +265,7 @@ __global__ void __launch_bounds__(256) k_mg(DSell<T> A, const T* __restrict__ di
       go[c] = gx[c] + (alpha * d[c] + beta * di * r);
     }
   }
+  T* __restrict__ out = MODE == MG_LAST ? outv.get() : nullptr;
   if (MODE == MG_LAST && out) {
     const int64_t dst = perm ? perm[row] : row;
     for (int c = 0; c < nc; ++c) out[c * out_ld + dst] = go[c];
@@ -348,7 +350,7 @@ template <typename T, int NCP>
 __global__ void k_mg_dense(const T* __restrict__ C, const int32_t* __restrict__ row_blk,
                            const int64_t* __restrict__ blk_row, const int64_t* __restrict__ blk_n,
                            const int64_t* __restrict__ blk_dense, int64_t n,
-                           const T* __restrict__ b, T* __restrict__ X, T* __restrict__ out,
+                           const T* __restrict__ b, T* __restrict__ X, JVec<T> outv,
                            int64_t out_ld, const int32_t* __restrict__ perm, int nc,
                            const int* skip) {
   if (skip && *skip) return;
@@ -372,6 +374,7 @@ __global__ void k_mg_dense(const T* __restrict__ C, const int32_t* __restrict__ 
 #pragma unroll
   for (int c = 0; c < NCP; ++c) acc[c] = group_sum<32>(acc[c]);
   if (lane != 0 || row >= n) return;
+  T* __restrict__ out = outv.get();
   if (out) {
     const int64_t dst = perm ? perm[row] : row;
     for (int c = 0; c < nc; ++c) out[c * out_ld + dst] = acc[c];
@@ -382,7 +385,7 @@ __global__ void k_mg_dense(const T* __restrict__ C, const int32_t* __restrict__ 
 
 template <typename T, int NCP>
 void launch_mg(int mode, const DLevel<T>& L, const T* b, const T* Gin, const T* Din, T* Gout,
-               T* Dout, T alpha, T beta, T* out, int64_t out_ld, const int32_t* perm, int nc,
+               T* Dout, T alpha, T beta, JVec<T> out, int64_t out_ld, const int32_t* perm, int nc,
                const int* skip, cudaStream_t s) {
   const int64_t n = L.A.nrow;
   const T it = (T)L.inv_theta;
@@ -401,14 +404,14 @@ void launch_mg(int mode, const DLevel<T>& L, const T* b, const T* Gin, const T* 
 // V-cycle below a level whose right-hand side b_l and first step (G0, D0)
 // are in place; the level's result ends in G1[l], or in `out` for level 0.
 template <typename T, int NCP>
-void vcycle_level(const DHier<T>& H, int l, T* out, int64_t out_ld, int nc, const int* skip,
-                  cudaStream_t s) {
+void vcycle_level(const DHier<T>& H, int l, JVec<T> out, int64_t out_ld, int nc,
+                  const int* skip, cudaStream_t s) {
   const bool top = l == 0;
   if (l == H.nlev - 1) {
     const int64_t n = H.ncoarse;
     k_mg_dense<T, NCP><<<blocks_for(n * 32), 256, 0, s>>>(
         H.cinv, H.row_blk, H.blk_row, H.blk_n, H.blk_dense, n, H.b[l], H.G1[l],
-        top ? out : nullptr, out_ld, top ? H.perm : nullptr, nc, skip);
+        top ? out : JVec<T>(), out_ld, top ? H.perm : nullptr, nc, skip);
     count_launches(1);
     return;
   }
@@ -417,8 +420,8 @@ void vcycle_level(const DHier<T>& H, int l, T* out, int64_t out_ld, int nc, cons
   const T a1 = (T)L.a1, b1 = (T)L.b1, a2 = (T)L.a2, b2 = (T)L.b2;
   T *G0 = H.G0[l], *G1 = H.G1[l], *D0 = H.D0[l], *D1 = H.D1[l];
   const T* b = H.b[l];
-  launch_mg<T, NCP>(MG_STEP, L, b, G0, D0, G1, D1, a1, b1, nullptr, 0, nullptr, nc, skip, s);
-  launch_mg<T, NCP>(MG_STEP, L, b, G1, D1, G0, D0, a2, b2, nullptr, 0, nullptr, nc, skip, s);
+  launch_mg<T, NCP>(MG_STEP, L, b, G0, D0, G1, D1, a1, b1, JVec<T>(), 0, nullptr, nc, skip, s);
+  launch_mg<T, NCP>(MG_STEP, L, b, G1, D1, G0, D0, a2, b2, JVec<T>(), 0, nullptr, nc, skip, s);
   // residual of x3 = G0 into G1; G0 keeps x3 for the correction
   launch_mg<T, NCP>(MG_RESID, L, b, G0, D0, G1, nullptr, T(0), T(0), nullptr, 0, nullptr, nc,
                     skip, s);
@@ -427,13 +430,13 @@ void vcycle_level(const DHier<T>& H, int l, T* out, int64_t out_ld, int nc, cons
       L.R, G1, H.b[l + 1], H.G0[l + 1], H.D0[l + 1], coarsest_next ? nullptr : C.dinv,
       (T)C.inv_theta, skip);
   count_launches(1);
-  vcycle_level<T, NCP>(H, l + 1, nullptr, 0, nc, skip, s);
+  vcycle_level<T, NCP>(H, l + 1, JVec<T>(), 0, nc, skip, s);
   k_mg_prolong<T, NCP, 4><<<blocks_for(L.P.nrow * 4), 256, 0, s>>>(L.P, H.G1[l + 1], G0, skip);
   count_launches(1);
   launch_mg<T, NCP>(MG_START, L, b, G0, nullptr, G1, D1, T(0), T(0), nullptr, 0, nullptr, nc,
                     skip, s);
-  launch_mg<T, NCP>(MG_STEP, L, b, G1, D1, G0, D0, a1, b1, nullptr, 0, nullptr, nc, skip, s);
-  launch_mg<T, NCP>(MG_LAST, L, b, G0, D0, G1, nullptr, a2, b2, top ? out : nullptr, out_ld,
+  launch_mg<T, NCP>(MG_STEP, L, b, G1, D1, G0, D0, a1, b1, JVec<T>(), 0, nullptr, nc, skip, s);
+  launch_mg<T, NCP>(MG_LAST, L, b, G0, D0, G1, nullptr, a2, b2, top ? out : JVec<T>(), out_ld,
                     top ? H.perm : nullptr, nc, skip, s);
 }
 
@@ -444,11 +447,12 @@ void vcycle_level(const DHier<T>& H, int l, T* out, int64_t out_ld, int nc, cons
 // level-0 row iperm[q]): b0 = r and the first step from x = 0,
 // G0 = D0 = D^-1 r / theta.
 template <typename T>
-__global__ void k_mg_load1(int64_t n, const T* __restrict__ r,
+__global__ void k_mg_load1(int64_t n, JVec<const T> rv,
                            const int32_t* __restrict__ iperm, const T* __restrict__ dinv0,
                            T inv_theta0, T* __restrict__ b0, T* __restrict__ G0,
                            T* __restrict__ D0, const int* skip) {
   if (skip && *skip) return;
+  const T* __restrict__ r = rv.get();
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
        q += (int64_t)gridDim.x * blockDim.x) {
     const int64_t dst = iperm ? iperm[q] : q;
@@ -462,20 +466,22 @@ __global__ void k_mg_load1(int64_t n, const T* __restrict__ r,
 
 // z_p = nu Mp^-1 r_p + dt^-1 y_K ; then pinned rows: z_p = r_p
 template <typename T>
-__global__ void k_prec_p(int64_t nv, const T* __restrict__ rp, const T* __restrict__ yk,
-                         const T* __restrict__ mpl_inv_nu, T inv_dt, T* __restrict__ zp,
+__global__ void k_prec_p(int64_t nv, JVec<const T> rpv, const T* __restrict__ yk,
+                         const T* __restrict__ mpl_inv_nu, T inv_dt, JVec<T> zpv,
                          const int* skip) {
   if (skip && *skip) return;
+  const T* __restrict__ rp = rpv.get();
+  T* __restrict__ zp = zpv.get();
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nv;
        q += (int64_t)gridDim.x * blockDim.x)
     zp[q] = mpl_inv_nu[q] * rp[q] + inv_dt * yk[q];
 }
 template <typename T>
-__global__ void k_pin_rows(const int32_t* __restrict__ pinned, int npinned,
-                           const T* __restrict__ rp, T* __restrict__ zp, const int* skip) {
+__global__ void k_pin_rows(const int32_t* __restrict__ pinned, int npinned, JVec<const T> rpv,
+                           JVec<T> zpv, const int* skip) {
   if (skip && *skip) return;
   int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < npinned) zp[pinned[t]] = rp[pinned[t]];
+  if (t < npinned) zpv.get()[pinned[t]] = rpv.get()[pinned[t]];
 }
 
 // Velocity right-hand side of the V-cycle, written straight into level 0:
@@ -483,9 +489,8 @@ __global__ void k_pin_rows(const int32_t* __restrict__ pinned, int npinned,
 // level-0 (block-order) row iperm[i] as b0, with the first step from x = 0,
 // G0 = D0 = D^-1 t / theta.
 template <typename T, int DIM, int NCP>
-__global__ void __launch_bounds__(256) k_bt_add_mg(DSell<T> BT, int64_t n2,
-                                                   const T* __restrict__ r,
-                                                   const T* __restrict__ zp,
+__global__ void __launch_bounds__(256) k_bt_add_mg(DSell<T> BT, int64_t n2, JVec<const T> rv,
+                                                   JVec<const T> zpv,
                                                    const int32_t* __restrict__ iperm,
                                                    const T* __restrict__ dinv0, T inv_theta0,
                                                    T* __restrict__ b0, T* __restrict__ G0,
@@ -493,6 +498,8 @@ __global__ void __launch_bounds__(256) k_bt_add_mg(DSell<T> BT, int64_t n2,
   if (skip && *skip) return;
   const int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (row >= n2) return;
+  const T* __restrict__ r = rv.get();
+  const T* __restrict__ zp = zpv.get();
   T acc[DIM];
 #pragma unroll
   for (int c = 0; c < DIM; ++c) acc[c] = T(0);
@@ -535,7 +542,7 @@ inline unsigned grid_stride_blocks(int64_t n) {
 }  // namespace
 
 template <typename T, typename V>
-void launch_spmv_full(const DOp<T>& op, const V* x, const V* b, V* y, int resid,
+void launch_spmv_full(const DOp<T>& op, JVec<const V> x, const V* b, JVec<V> y, int resid,
                       const int* skip, cudaStream_t s) {
   const int64_t threads = ((op.n2 + 31) & ~(int64_t)31) + op.nv;
   if (op.dim == 2)
@@ -544,10 +551,11 @@ void launch_spmv_full(const DOp<T>& op, const V* x, const V* b, V* y, int resid,
     k_spmv_full<T, V, 3><<<blocks_for(threads), 256, 0, s>>>(op, x, b, y, resid, skip);
   count_launches(1);
 }
-template void launch_spmv_full<double, double>(const DOp<double>&, const double*, const double*,
-                                               double*, int, const int*, cudaStream_t);
-template void launch_spmv_full<float, float>(const DOp<float>&, const float*, const float*,
-                                             float*, int, const int*, cudaStream_t);
+template void launch_spmv_full<double, double>(const DOp<double>&, JVec<const double>,
+                                               const double*, JVec<double>, int, const int*,
+                                               cudaStream_t);
+template void launch_spmv_full<float, float>(const DOp<float>&, JVec<const float>, const float*,
+                                             JVec<float>, int, const int*, cudaStream_t);
 
 void launch_csr_to_sell(int64_t n, const int32_t* rp, const double* in, const int64_t* off,
                         double* out64, float* out32, cudaStream_t s) {
@@ -575,13 +583,14 @@ template void launch_cheb_step<float>(const DHier<float>&, int, cudaStream_t);
 template <typename T>
 void launch_precond(const DOp<T>& op, const DHier<T>& HA, const DHier<T>& HK,
                     const T* mpl_inv_nu, double inv_dt, const int32_t* pinned,
-                    int npinned, const T* r, T* z, T* work_p, T* work_u,
+                    int npinned, JVec<const T> r, JVec<T> z, T* work_p, T* work_u,
                     const int* skip, cudaStream_t s) {
   (void)work_u;
   const int64_t n2 = op.n2, nv = op.nv;
   const int dim = op.dim;
-  const T* rp = r + dim * n2;
-  T* zp = z + dim * n2;
+  const JVec<const T> rp = r.shifted(dim * n2);
+  const JVec<T> zp = z.shifted(dim * n2);
+  const JVec<const T> zpc(zp.base, zp.j, zp.stride);
   // pressure: Cahouet-Chabard  z_p = nu Mp^-1 r_p + dt^-1 Kp^-1 r_p
   {
     const bool k1 = HK.nlev > 1;
@@ -589,7 +598,7 @@ void launch_precond(const DOp<T>& op, const DHier<T>& HA, const DHier<T>& HK,
         nv, rp, HK.iperm, k1 ? HK.lev[0].dinv : nullptr, (T)HK.lev[0].inv_theta, HK.b[0], HK.G0[0],
         HK.D0[0], skip);
     count_launches(1);
-    vcycle_level<T, 1>(HK, 0, work_p, nv, 1, skip, s);
+    vcycle_level<T, 1>(HK, 0, JVec<T>(work_p), nv, 1, skip, s);
   }
   k_prec_p<T><<<grid_stride_blocks(nv), 256, 0, s>>>(nv, rp, work_p, mpl_inv_nu, (T)inv_dt, zp,
                                                      skip);
@@ -603,12 +612,12 @@ void launch_precond(const DOp<T>& op, const DHier<T>& HA, const DHier<T>& HK,
   const T* d0 = a1 ? HA.lev[0].dinv : nullptr;
   const T it0 = (T)HA.lev[0].inv_theta;
   if (dim == 2) {
-    k_bt_add_mg<T, 2, 2><<<blocks_for(n2), 256, 0, s>>>(op.BT, n2, r, zp, HA.iperm, d0, it0,
+    k_bt_add_mg<T, 2, 2><<<blocks_for(n2), 256, 0, s>>>(op.BT, n2, r, zpc, HA.iperm, d0, it0,
                                                         HA.b[0], HA.G0[0], HA.D0[0], skip);
     count_launches(1);
     vcycle_level<T, 2>(HA, 0, z, n2, 2, skip, s);
   } else {
-    k_bt_add_mg<T, 3, 4><<<blocks_for(n2), 256, 0, s>>>(op.BT, n2, r, zp, HA.iperm, d0, it0,
+    k_bt_add_mg<T, 3, 4><<<blocks_for(n2), 256, 0, s>>>(op.BT, n2, r, zpc, HA.iperm, d0, it0,
                                                         HA.b[0], HA.G0[0], HA.D0[0], skip);
     count_launches(1);
     vcycle_level<T, 4>(HA, 0, z, n2, 3, skip, s);
@@ -616,11 +625,11 @@ void launch_precond(const DOp<T>& op, const DHier<T>& HA, const DHier<T>& HK,
 }
 template void launch_precond<double>(const DOp<double>&, const DHier<double>&,
                                      const DHier<double>&, const double*, double,
-                                     const int32_t*, int, const double*, double*, double*,
-                                     double*, const int*, cudaStream_t);
+                                     const int32_t*, int, JVec<const double>, JVec<double>,
+                                     double*, double*, const int*, cudaStream_t);
 template void launch_precond<float>(const DOp<float>&, const DHier<float>&,
                                     const DHier<float>&, const float*, double,
-                                    const int32_t*, int, const float*, float*, float*,
+                                    const int32_t*, int, JVec<const float>, JVec<float>, float*,
                                     float*, const int*, cudaStream_t);
 
 template <typename A, typename B>
