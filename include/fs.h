@@ -328,9 +328,38 @@ int fs_csr_residual_norm_noalloc(int64_t n, const int64_t* rowptr,
                                  const double* x, const double* b,
                                  double* out2, void* stream);
 
+/* Execution schedule of the multigrid preconditioner (no counterpart in
+ * the paper, whose solver is a library call).  The levels of a hierarchy
+ * with at most tail_rows rows (and every level below them) run as one kernel
+ * on one thread-block cluster, their passes separated by cluster barriers;
+ * larger levels run one kernel per pass.  0 = no fused levels.  The choice
+ * changes launch counts and timing only: results are identical (the same
+ * per-row arithmetic in the same order).
+ * fs_set_schedule drops the problem's captured CUDA graphs (they are
+ * re-captured by the next solve); FS_ERR_BUSY while a step is in progress.
+ * fs_autotune times one application of the preconditioner (a CUDA graph of
+ * `reps` applications, CUDA events) for every pair of candidate thresholds
+ * {0, 4096, 16384, 65536} of the velocity and pressure hierarchies, installs
+ * the fastest and reports it.  Leaves the state and assembled system
+ * unchanged.  Synchronises. */
+typedef struct {
+  int64_t tail_rows_velocity;
+  int64_t tail_rows_pressure;
+} fs_schedule;
+typedef struct {
+  int candidates;        /* schedules timed                                  */
+  double default_ms;     /* one preconditioner application, schedule before */
+  double best_ms;        /* ... with the installed schedule                  */
+  fs_schedule best;
+} fs_tune_report;
+int fs_get_schedule(const fs_problem* prob, fs_schedule* out);
+int fs_set_schedule(fs_problem* prob, const fs_schedule* sched);
+int fs_autotune(fs_problem* prob, int reps, fs_tune_report* report);
+
 /* Instrumentation (no counterpart in the paper).
  * fs_launch_count: kernels launched by this library since load, counting
- * every node of each replayed CUDA graph (host-side counter).
+ * every node of each replayed CUDA graph and every pass of a graph's
+ * Arnoldi loop node (host-side counter).
  * fs_profile_kernel: times `reps` back-to-back launches of one hot kernel on
  * the problem's own data and stream with CUDA events (after 3 warm-up
  * launches) and returns the mean duration and the kernel's algorithmic bytes
@@ -340,7 +369,11 @@ enum {
   FS_KERNEL_SPMV = 0,           /* saddle-point SpMV, solver arithmetic      */
   FS_KERNEL_SPMV_FP64 = 1,      /* saddle-point SpMV, FP64                   */
   FS_KERNEL_CHEB = 2,           /* fused Chebyshev step, finest P2 level     */
-  FS_KERNEL_ASSEMBLE_CONV = 3   /* per-step convection assembly (FP64)       */
+  FS_KERNEL_ASSEMBLE_CONV = 3,  /* per-step convection assembly (FP64)       */
+  FS_KERNEL_PRECOND = 4         /* one block-preconditioner application in
+                                   the solver arithmetic, timed as a CUDA
+                                   graph of `reps` applications; alg_bytes
+                                   is 0 (a latency unit of many kernels)   */
 };
 int64_t fs_launch_count(void);
 int fs_profile_kernel(fs_problem* prob, int kernel, int reps, double* avg_ms,

@@ -165,6 +165,7 @@ struct fs_problem {
   std::vector<fs_solve_stats> last_stats;  // per instance, last solve
   double t = 0;
   bool assembled = false;
+  fs_schedule sched{0, 0};
 
   TileList tl() const { return TileList{tiles, ntiles}; }
 
@@ -368,6 +369,28 @@ int upload_hierarchy(fs_problem* P, const UnionHierarchy& U, int nc, DHier<T>& D
     D.perm = pm;
     D.iperm = ip;
   }
+  DHier<T>* dev;
+  FS_TRY(P->alloc(&dev, 1));
+  D.dev = dev;
+  return FS_OK;
+}
+
+// The fused cluster kernel takes the levels with at most tail_rows rows
+// (from the first such level that still has a level below it; 0 = none);
+// the device copy of the hierarchy is refreshed.
+template <typename T>
+int apply_tail(fs_problem* P, DHier<T>& D, int64_t tail_rows) {
+  D.tail = -1;
+  if (tail_rows > 0)
+    for (int l = 0; l + 1 < D.nlev; ++l)
+      if (D.lev[l].A.nrow <= tail_rows) {
+        D.tail = l;
+        break;
+      }
+  if (D.tail >= 0) D.tail_cluster = mg_tail_cluster<T>(D.ncp);
+  FS_CUDA(cudaMemcpyAsync((void*)D.dev, &D, sizeof(DHier<T>), cudaMemcpyHostToDevice,
+                          P->stream));
+  FS_CUDA(cudaStreamSynchronize(P->stream));
   return FS_OK;
 }
 
@@ -476,6 +499,8 @@ int setup_precision(fs_problem* P, Precision<T>& pr, const UnionHierarchy& HA,
                     const std::vector<int>& first, const std::vector<int>& count) {
   FS_TRY(upload_hierarchy<T>(P, HA, P->dim, pr.HA));
   FS_TRY(upload_hierarchy<T>(P, HK, 1, pr.HK));
+  FS_TRY(apply_tail<T>(P, pr.HA, P->sched.tail_rows_velocity));
+  FS_TRY(apply_tail<T>(P, pr.HK, P->sched.tail_rows_pressure));
   std::vector<T> mi(mplinv_nu.begin(), mplinv_nu.end());
   FS_TRY(P->upload(&pr.mplinv_nu, mi));
   FS_TRY(alloc_krylov<T>(P, pr.kr, m, first, count));
@@ -526,7 +551,6 @@ int issue_iter(fs_problem* P, Precision<T>& pr, T* x, int relative_to_beta) {
                       P->npinned, vj, zj, K.work_p, K.work_u, skip, q);
     launch_spmv_full<T, T>(pr.op, zjc, nullptr, w, 0, skip, q);
     launch_seg_cgs2<T>(K.Vb, n, tl, K.st, K.ctl, K.partial, q);
-    launch_seg_scale<T>(w, tl, K.st, 1, q);
     launch_seg_givens(K.st, K.ctl, P->nseg, cond, q);
   };
   if (loop) {
@@ -869,6 +893,80 @@ int run_solve(fs_problem* P, double* x) {
     FS_TRY(advance(P));
   }
   return P->ctx.rc;
+}
+
+// Captured CUDA graphs depend on the schedule: drop them.
+template <typename T>
+void drop_graphs(Krylov<T>& K) {
+  if (K.g_check) cudaGraphExecDestroy(K.g_check);
+  if (K.g_iter) cudaGraphExecDestroy(K.g_iter);
+  K.g_check = K.g_iter = nullptr;
+  K.g_x = K.g_b = nullptr;
+}
+
+template <typename T>
+int install_schedule(fs_problem* P, Precision<T>& pr, const fs_schedule& sc) {
+  FS_TRY(apply_tail<T>(P, pr.HA, sc.tail_rows_velocity));
+  FS_TRY(apply_tail<T>(P, pr.HK, sc.tail_rows_pressure));
+  drop_graphs(pr.kr);
+  return FS_OK;
+}
+
+int install_schedule(fs_problem* P, const fs_schedule& sc) {
+  if (P->desc.precision == FS_PREC_FP64)
+    FS_TRY(install_schedule<double>(P, P->p64, sc));
+  else
+    FS_TRY(install_schedule<float>(P, P->p32, sc));
+  P->sched = sc;
+  return FS_OK;
+}
+
+// One application of the block preconditioner (mean over a CUDA graph of
+// `reps` applications on the Krylov scratch vectors, after one warm launch).
+template <typename T>
+int time_precond(fs_problem* P, Precision<T>& pr, int reps, double* ms) {
+  Krylov<T>& K = pr.kr;
+  cudaStream_t s = P->stream;
+  FS_CUDA(cudaMemsetAsync(K.Vb, 0, sizeof(T) * K.n, s));
+  cudaGraph_t g;
+  FS_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  g_capturing = true;
+  for (int i = 0; i < reps; ++i)
+    launch_precond<T>(pr.op, pr.HA, pr.HK, pr.mplinv_nu, 1.0 / P->desc.dt, P->pinned,
+                      P->npinned, K.Vb, K.Z, K.work_p, K.work_u, nullptr, s);
+  g_capturing = false;
+  FS_CUDA(cudaStreamEndCapture(s, &g));
+  size_t nodes = 0;
+  cudaGraphGetNodes(g, nullptr, &nodes);
+  cudaGraphExec_t ge;
+  cudaError_t e = cudaGraphInstantiate(&ge, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    set_error(std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+    return FS_ERR_CUDA;
+  }
+  cudaEvent_t e0, e1;
+  FS_CUDA(cudaEventCreate(&e0));
+  FS_CUDA(cudaEventCreate(&e1));
+  FS_CUDA(cudaGraphLaunch(ge, s));
+  FS_CUDA(cudaEventRecord(e0, s));
+  for (int i = 0; i < 3; ++i) FS_CUDA(cudaGraphLaunch(ge, s));
+  FS_CUDA(cudaEventRecord(e1, s));
+  FS_CUDA(cudaEventSynchronize(e1));
+  float t = 0;
+  cudaEventElapsedTime(&t, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaGraphExecDestroy(ge);
+  count_launches((int64_t)nodes * 4);
+  FS_TRY(check_launch("preconditioner timing"));
+  *ms = t / (3.0 * reps);
+  return FS_OK;
+}
+
+int time_precond(fs_problem* P, int reps, double* ms) {
+  if (P->desc.precision == FS_PREC_FP64) return time_precond<double>(P, P->p64, reps, ms);
+  return time_precond<float>(P, P->p32, reps, ms);
 }
 
 int solve_opts(const fs_solve_opts* opts, fs_solve_opts& o) {
@@ -1483,6 +1581,11 @@ int fs_profile_kernel(fs_problem* P, int kernel, int reps, double* avg_ms, doubl
       };
       break;
     }
+    case FS_KERNEL_PRECOND: {
+      FS_TRY(time_precond(P, reps, avg_ms));
+      *alg_bytes = 0;
+      return FS_OK;
+    }
     default:
       set_error("fs_profile_kernel: unknown kernel id");
       return FS_ERR_INVALID_ARG;
@@ -1503,6 +1606,77 @@ int fs_profile_kernel(fs_problem* P, int kernel, int reps, double* avg_ms, doubl
   *avg_ms = ms / reps;
   *alg_bytes = bytes;
   if (kernel == FS_KERNEL_ASSEMBLE_CONV) FS_TRY(assemble_impl(P, P->t + P->desc.dt));
+  return FS_OK;
+}
+
+int fs_get_schedule(const fs_problem* P, fs_schedule* out) {
+  if (!P || !out) {
+    set_error("fs_get_schedule: null argument");
+    return FS_ERR_INVALID_ARG;
+  }
+  *out = P->sched;
+  return FS_OK;
+}
+
+int fs_set_schedule(fs_problem* P, const fs_schedule* sc) {
+  if (!P || !sc || sc->tail_rows_velocity < 0 || sc->tail_rows_pressure < 0) {
+    set_error("fs_set_schedule: bad argument");
+    return FS_ERR_INVALID_ARG;
+  }
+  if (P->ctx.phase != PH_IDLE && P->ctx.phase != PH_DONE) {
+    set_error("fs_set_schedule: a step is in progress");
+    return FS_ERR_BUSY;
+  }
+  return install_schedule(P, *sc);
+}
+
+int fs_autotune(fs_problem* P, int reps, fs_tune_report* report) {
+  if (!P || reps < 1) {
+    set_error("fs_autotune: bad argument");
+    return FS_ERR_INVALID_ARG;
+  }
+  if (P->ctx.phase != PH_IDLE && P->ctx.phase != PH_DONE) {
+    set_error("fs_autotune: a step is in progress");
+    return FS_ERR_BUSY;
+  }
+  if (!P->assembled) FS_TRY(assemble_impl(P, P->t + P->desc.dt));
+  const int64_t cand[4] = {0, 4096, 16384, 65536};
+  fs_tune_report r{};
+  r.best = P->sched;
+  FS_TRY(time_precond(P, reps, &r.default_ms));
+  r.best_ms = r.default_ms;
+  r.candidates = 1;
+  // distinct schedules only: thresholds that select the same levels agree
+  auto levels = [&](const fs_schedule& sc) {
+    std::pair<int, int> k;
+    if (P->desc.precision == FS_PREC_FP64) {
+      apply_tail<double>(P, P->p64.HA, sc.tail_rows_velocity);
+      apply_tail<double>(P, P->p64.HK, sc.tail_rows_pressure);
+      k = {P->p64.HA.tail, P->p64.HK.tail};
+    } else {
+      apply_tail<float>(P, P->p32.HA, sc.tail_rows_velocity);
+      apply_tail<float>(P, P->p32.HK, sc.tail_rows_pressure);
+      k = {P->p32.HA.tail, P->p32.HK.tail};
+    }
+    return k;
+  };
+  std::vector<std::pair<int, int>> seen{levels(P->sched)};
+  for (int64_t v : cand)
+    for (int64_t p : cand) {
+      fs_schedule sc{v, p};
+      std::pair<int, int> k = levels(sc);
+      if (std::find(seen.begin(), seen.end(), k) != seen.end()) continue;
+      seen.push_back(k);
+      double ms = 0;
+      FS_TRY(time_precond(P, reps, &ms));
+      r.candidates += 1;
+      if (ms < r.best_ms) {
+        r.best_ms = ms;
+        r.best = sc;
+      }
+    }
+  FS_TRY(install_schedule(P, r.best));
+  if (report) *report = r;
   return FS_OK;
 }
 

@@ -174,7 +174,17 @@ struct DHier {
   // the caller's row of block row r, iperm its inverse; null when equal
   const int32_t* perm = nullptr;
   const int32_t* iperm = nullptr;
+  // first level run by the fused cluster kernel (-1: none), its cluster size
+  int tail = -1;
+  int tail_cluster = 8;
+  // a copy of this struct in device memory (read by the coarse kernels)
+  const DHier<T>* dev = nullptr;
 };
+
+// Cluster size (16 or 8 blocks) of the fused kernel for this arithmetic and
+// row width.
+template <typename T>
+int mg_tail_cluster(int ncp);
 
 // One fused Chebyshev step (mode STEP) on level 0 of H with its own work
 // vectors, for kernel timing.
@@ -248,7 +258,7 @@ void launch_seg_cycle_init(SegState* st, KCtl* ctl, int relative_to_beta,
 template <typename V>
 void launch_seg_scale(JVec<V> x, const TileList& tl, const SegState* st, int field,
                       cudaStream_t s);
-// CGS2 on w = V[j + 1] with j = ctl->j
+// CGS2 on w = V[j + 1] with j = ctl->j, ending with V[j + 1] normalised
 template <typename V>
 void launch_seg_cgs2(V* Vb, int64_t n, const TileList& tl, SegState* st,
                      const KCtl* ctl, double* partial, cudaStream_t s);

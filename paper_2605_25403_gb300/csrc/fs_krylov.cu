@@ -144,87 +144,146 @@ __global__ void __launch_bounds__(kKB) k_seg_scale(JVec<V> xv, const Tile* tiles
   for (int e = threadIdx.x; e < t.len; e += kKB) x[t.start + e] *= f;
 }
 
-// CGS2 passes on w = V[j+1] (see the file comment of fs_linalg.cu):
-//   1: h = V^T w -> H[:, j];  2: w -= V h, h2 = V^T w -> H[:, j] += h2;
-//   3: w -= V h2, ||w|| -> H[j+1, j] = hn.
-template <typename V, int PASS>
-__global__ void __launch_bounds__(kKB) k_seg_cgs(V* __restrict__ Vb, int64_t n,
+// Classical Gram-Schmidt with one reorthogonalisation (CGS2) of the new
+// Arnoldi vector w = V[j+1] against V[0..j], j = ctl->j, in three passes:
+//   dot : h = V^T w                                    -> H[0..j, j]
+//   upd : w' = w - V h;  h2 = V^T w';  ||w'||^2         -> H[0..j, j] += h2,
+//         H[j+1, j] = hn = sqrt(||w'||^2 - ||h2||^2)
+//   fin : V[j+1] = (w' - V h2) / hn
+// hn is the norm of w'' = w' - V h2 by Pythagoras (V^T w' = h2 and V
+// orthonormal); h2 is a rounding-size correction, so the difference loses
+// nothing.  A block takes one tile: its slice of w is staged in shared
+// memory, the dots are taken by warps over (vector, chunk) units with the
+// per-lane sums in the vector type and the cross-lane and cross-tile sums in
+// FP64, and the updates by threads over elements with the coefficients in
+// shared memory.
+
+// Dots of the staged tile slice ws with the first nvec basis vectors (and
+// ws . ws as entry nvec when `norm`), added into sums[] (shared).
+template <typename V>
+__device__ __forceinline__ void tile_dots(const V* __restrict__ Vb, int64_t n, const Tile& t,
+                                          const V* ws, int nvec, bool norm, double* sums) {
+  constexpr int NW = kKB / 32;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nout = nvec + (norm ? 1 : 0);
+  const int split = nout >= NW ? 1 : (NW + nout - 1) / nout;
+  const int chunk = ((t.len + split - 1) / split + 31) & ~31;
+  for (int u = warp; u < nout * split; u += NW) {
+    const int v = u / split, c = u % split;
+    const int e0 = c * chunk, e1 = min(t.len, e0 + chunk);
+    V acc = V(0);
+    if (v < nvec) {
+      const V* __restrict__ vv = Vb + (int64_t)v * n + t.start;
+#pragma unroll 4
+      for (int e = e0 + lane; e < e1; e += 32) acc += vv[e] * ws[e];
+    } else {
+#pragma unroll 4
+      for (int e = e0 + lane; e < e1; e += 32) acc += ws[e] * ws[e];
+    }
+    const double sv = warp_sum((double)acc);
+    if (lane == 0) atomicAdd(&sums[v], sv);
+  }
+}
+
+// w_e - sum_v coef[v] V[v]_e for the tile's elements (thread per element).
+template <typename V>
+__device__ __forceinline__ V tile_update(const V* __restrict__ Vb, int64_t n, int64_t i,
+                                         const V* coef, int nvec, V wi) {
+  V u0 = V(0), u1 = V(0);
+  int v = 0;
+  for (; v + 1 < nvec; v += 2) {
+    u0 += coef[v] * Vb[(int64_t)v * n + i];
+    u1 += coef[v + 1] * Vb[(int64_t)(v + 1) * n + i];
+  }
+  if (v < nvec) u0 += coef[v] * Vb[(int64_t)v * n + i];
+  return wi - (u0 + u1);
+}
+
+template <typename V>
+__global__ void __launch_bounds__(kKB) k_seg_dot(const V* __restrict__ Vb, int64_t n,
                                                  const Tile* tiles, int ntiles, SegState* st,
                                                  const KCtl* ctl, double* partial) {
   const Tile t = tiles[blockIdx.x];
   SegState& S = st[t.seg];
   if (S.done) return;
-  const int j = ctl->j;
-  constexpr int NV = kMaxRestart + 1;
-  constexpr int NW = kKB / 32;
-  __shared__ double coef[NV];
-  __shared__ double wsum[NV * NW];
-  const int nvec = j + 1;
-  const int m = ctl->m;
+  const int j = ctl->j, m = ctl->m, nvec = j + 1;
+  __shared__ V ws[kTileLen];
+  __shared__ double sums[kMaxRestart + 2];
+  const V* __restrict__ w = Vb + (int64_t)(j + 1) * n + t.start;
+  for (int e = threadIdx.x; e < t.len; e += kKB) ws[e] = w[e];
+  for (int v = threadIdx.x; v < nvec; v += kKB) sums[v] = 0.0;
+  __syncthreads();
+  tile_dots<V>(Vb, n, t, ws, nvec, false, sums);
+  __syncthreads();
+  for (int v = threadIdx.x; v < nvec; v += kKB) partial[(int64_t)v * ntiles + blockIdx.x] = sums[v];
+  if (!last_of_segment(&S.counter[1], S.ntiles)) return;
+  __shared__ double res[kMaxRestart + 2];
+  reduce_segment(partial, ntiles, S.first_tile, S.ntiles, nvec, res);
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < nvec; ++i) S.H[i * m + j] = res[i];
+    S.counter[1] = 0;
+  }
+}
+
+template <typename V>
+__global__ void __launch_bounds__(kKB) k_seg_upd(V* __restrict__ Vb, int64_t n,
+                                                 const Tile* tiles, int ntiles, SegState* st,
+                                                 const KCtl* ctl, double* partial) {
+  const Tile t = tiles[blockIdx.x];
+  SegState& S = st[t.seg];
+  if (S.done) return;
+  const int j = ctl->j, m = ctl->m, nvec = j + 1;
+  __shared__ V ws[kTileLen];
+  __shared__ V coef[kMaxRestart + 1];
+  __shared__ double sums[kMaxRestart + 2];
+  for (int v = threadIdx.x; v < nvec; v += kKB) coef[v] = (V)S.H[v * m + j];
+  for (int v = threadIdx.x; v <= nvec; v += kKB) sums[v] = 0.0;
+  __syncthreads();
   V* __restrict__ w = Vb + (int64_t)(j + 1) * n;
-  if (PASS >= 2) {
-    for (int i = threadIdx.x; i < nvec; i += blockDim.x)
-      coef[i] = PASS == 2 ? S.H[i * m + j] : S.h2[i];
-    __syncthreads();
-  }
-  V acc[NV];
-#pragma unroll
-  for (int v = 0; v < NV; ++v) acc[v] = V(0);
-#pragma unroll
-  for (int q = 0; q < kKEPT; ++q) {
-    const int e = q * kKB + threadIdx.x;
-    if (e >= t.len) break;
+  for (int e = threadIdx.x; e < t.len; e += kKB) {
     const int64_t i = t.start + e;
-    V wi = w[i];
-    if (PASS >= 2) {
-      V u = V(0);
-#pragma unroll
-      for (int v = 0; v < NV; ++v)
-        if (v < nvec) u += (V)coef[v] * Vb[(int64_t)v * n + i];
-      wi -= u;
-      w[i] = wi;
-    }
-    if (PASS <= 2) {
-#pragma unroll
-      for (int v = 0; v < NV; ++v)
-        if (v < nvec) acc[v] += Vb[(int64_t)v * n + i] * wi;
-    } else {
-      acc[0] += wi * wi;
-    }
-  }
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nout = PASS <= 2 ? nvec : 1;
-#pragma unroll
-  for (int v = 0; v < NV; ++v) {
-    if (v < nout) {
-      const double s = warp_sum((double)acc[v]);
-      if (lane == 0) wsum[v * NW + warp] = s;
-    }
+    const V wi = tile_update<V>(Vb, n, i, coef, nvec, w[i]);
+    ws[e] = wi;
+    w[i] = wi;
   }
   __syncthreads();
-  for (int v = threadIdx.x; v < nout; v += blockDim.x) {
-    double s = 0;
-#pragma unroll
-    for (int w2 = 0; w2 < NW; ++w2) s += wsum[v * NW + w2];
-    partial[(int64_t)v * ntiles + blockIdx.x] = s;
-  }
-  if (!last_of_segment(&S.counter[PASS], S.ntiles)) return;
-  __shared__ double res[NV];
-  reduce_segment(partial, ntiles, S.first_tile, S.ntiles, nout, res);
+  tile_dots<V>(Vb, n, t, ws, nvec, true, sums);
+  __syncthreads();
+  for (int v = threadIdx.x; v <= nvec; v += kKB)
+    partial[(int64_t)v * ntiles + blockIdx.x] = sums[v];
+  if (!last_of_segment(&S.counter[2], S.ntiles)) return;
+  __shared__ double res[kMaxRestart + 2];
+  reduce_segment(partial, ntiles, S.first_tile, S.ntiles, nvec + 1, res);
   if (threadIdx.x == 0) {
-    if (PASS == 1) {
-      for (int i = 0; i < nvec; ++i) S.H[i * m + j] = res[i];
-    } else if (PASS == 2) {
-      for (int i = 0; i < nvec; ++i) {
-        S.h2[i] = res[i];
-        S.H[i * m + j] += res[i];
-      }
-    } else {
-      const double hn = sqrt(res[0]);
-      S.hn = hn;
-      S.H[(j + 1) * m + j] = hn;
+    double hh = 0;
+    for (int i = 0; i < nvec; ++i) {
+      S.h2[i] = res[i];
+      S.H[i * m + j] += res[i];
+      hh += res[i] * res[i];
     }
-    S.counter[PASS] = 0;
+    const double hn = sqrt(fmax(res[nvec] - hh, 0.0));
+    S.hn = hn;
+    S.H[(j + 1) * m + j] = hn;
+    S.counter[2] = 0;
+  }
+}
+
+template <typename V>
+__global__ void __launch_bounds__(kKB) k_seg_fin(V* __restrict__ Vb, int64_t n,
+                                                 const Tile* tiles, SegState* st,
+                                                 const KCtl* ctl) {
+  const Tile t = tiles[blockIdx.x];
+  const SegState& S = st[t.seg];
+  if (S.done) return;
+  const int j = ctl->j, nvec = j + 1;
+  __shared__ V coef[kMaxRestart + 1];
+  for (int v = threadIdx.x; v < nvec; v += kKB) coef[v] = (V)S.h2[v];
+  __syncthreads();
+  const V f = (V)(1.0 / S.hn);
+  V* __restrict__ w = Vb + (int64_t)(j + 1) * n;
+  for (int e = threadIdx.x; e < t.len; e += kKB) {
+    const int64_t i = t.start + e;
+    w[i] = tile_update<V>(Vb, n, i, coef, nvec, w[i]) * f;
   }
 }
 
@@ -361,9 +420,9 @@ template void launch_seg_scale<float>(JVec<float>, const TileList&, const SegSta
 template <typename V>
 void launch_seg_cgs2(V* Vb, int64_t n, const TileList& tl, SegState* st, const KCtl* ctl,
                      double* partial, cudaStream_t s) {
-  k_seg_cgs<V, 1><<<tl.ntiles, kKB, 0, s>>>(Vb, n, tl.tiles, tl.ntiles, st, ctl, partial);
-  k_seg_cgs<V, 2><<<tl.ntiles, kKB, 0, s>>>(Vb, n, tl.tiles, tl.ntiles, st, ctl, partial);
-  k_seg_cgs<V, 3><<<tl.ntiles, kKB, 0, s>>>(Vb, n, tl.tiles, tl.ntiles, st, ctl, partial);
+  k_seg_dot<V><<<tl.ntiles, kKB, 0, s>>>(Vb, n, tl.tiles, tl.ntiles, st, ctl, partial);
+  k_seg_upd<V><<<tl.ntiles, kKB, 0, s>>>(Vb, n, tl.tiles, tl.ntiles, st, ctl, partial);
+  k_seg_fin<V><<<tl.ntiles, kKB, 0, s>>>(Vb, n, tl.tiles, st, ctl);
   count_launches(3);
 }
 template void launch_seg_cgs2<double>(double*, int64_t, const TileList&, SegState*, const KCtl*,

@@ -18,6 +18,8 @@
 #include <cmath>
 #include <type_traits>
 
+#include <cooperative_groups.h>
+
 #include "fs_device.h"
 
 namespace fs {
@@ -143,19 +145,29 @@ __global__ void k_csr_to_sell(int64_t n, const int32_t* __restrict__ rp,
 
 // ---------------------------------------------------------------------------
 // Multigrid V-cycle.  Level vectors are row-major with the components of a
-// row contiguous (nc padded to NCP in {1, 2, 4}), and the Chebyshev iterate x
-// and direction d of a row interleaved: XD[row] = (x[0..NCP), d[0..NCP)).  A
-// neighbour's (x, d) is one 32-byte sector for NCP = 4 in FP32, instead of
-// six scattered loads in a component-blocked layout.
+// row contiguous (nc padded to NCP in {1, 2, 4}), so a neighbour is one
+// NCP-wide load.  A level's Chebyshev state is kept as the gather vector G
+// (the point the next residual is taken at, x + d, read at every neighbour)
+// and the direction D (read at the own row only).
 //
 // Chebyshev smoothing (Saad, Iterative Methods, Alg. 12.1) with Jacobi
-// scaling, one fused SpMV kernel per step; the first step's direction
-// d0 = D^-1 b / theta is written by whichever kernel produces the level's
-// right-hand side (restriction, or the preconditioner's load kernels):
-//   STEP : y = x + d (neighbours); r = b - A y; XDout = (x + d, a d + b D^-1 r)
-//   RESID: y = x + d; XDout = (x + d, r = b - A y)        (r is restricted)
-//   START: y = x;     XDout = (x, D^-1 (b - A y) / theta)
-//   LAST : y = x + d; dn = a d + b D^-1 r; result x + d + dn
+// scaling, one fused SpMV pass per step; the first step's direction
+// d0 = D^-1 b / theta is written by whichever pass produces the level's
+// right-hand side (restriction, or the preconditioner's load kernels).
+// Modes, with r = b - A Gin:
+//   STEP : dn = alpha D + beta Dinv r;  Gout = Gin + dn, Dout = dn
+//   RESID: Gout = r                      (Gin = x3 stays for the correction)
+//   START: d0 = Dinv r / theta;         Gout = Gin + d0, Dout = d0  (Gin = x0)
+//   LAST : Gin + alpha D + beta Dinv r, the level's result, to Gout, or on
+//          level 0 (out != null) its first nc components to the caller's
+//          blocked vector at row perm[r].
+//
+// The levels below a per-problem row threshold (the schedule; see
+// fs_autotune) can run as one kernel on one thread-block cluster
+// (k_mg_tail): the passes that are separate kernels on the large levels
+// become phases separated by cluster barriers, which removes a kernel launch
+// per pass where the levels are too small to fill the GPU.  Both forms share
+// the per-row code below, so they compute the same values.
 // ---------------------------------------------------------------------------
 enum { MG_STEP = 0, MG_RESID = 1, MG_START = 2, MG_LAST = 3 };
 
@@ -194,28 +206,14 @@ __device__ __forceinline__ void vstore(T* __restrict__ p, const T (&v)[N]) {
   }
 }
 
-// One Chebyshev kernel of a level.  A level's state is kept as two vectors:
-// the gather vector G (the point the next residual is taken at, x + d, read
-// at every neighbour) and the direction D (read at the own row only), so a
-// neighbour costs one NCP-wide load.  Modes, with r = b - A Gin:
-//   STEP : dn = alpha D + beta Dinv r;  Gout = Gin + dn, Dout = dn
-//   RESID: Gout = r                      (Gin = x3 stays for the correction)
-//   START: d0 = Dinv r / theta;         Gout = Gin + d0, Dout = d0  (Gin = x0)
-//   LAST : Gin + alpha D + beta Dinv r, the level's result, to Gout, or on
-//          level 0 (out != null) its first nc components to the caller's
-//          blocked vector at row perm[r].
+// One row of a Chebyshev pass (thread per row on the SELL-32 operator).
 template <typename T, int NC, int NCP, int MODE>
-__global__ void __launch_bounds__(256) k_mg(DSell<T> A, const T* __restrict__ dinv,
-                                            const T* __restrict__ b,
-                                            const T* __restrict__ Gin,
-                                            const T* __restrict__ Din,
-                                            T* __restrict__ Gout, T* __restrict__ Dout,
-                                            T alpha, T beta, T inv_theta, JVec<T> outv,
-                                            int64_t out_ld, const int32_t* __restrict__ perm,
-                                            int nc, const int* skip) {
-  if (skip && *skip) return;
-  const int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (row >= A.nrow) return;
+__device__ __forceinline__ void mg_row(const DSell<T>& A, const T* __restrict__ dinv,
+                                       const T* __restrict__ b, const T* __restrict__ Gin,
+                                       const T* __restrict__ Din, T* __restrict__ Gout,
+                                       T* __restrict__ Dout, T alpha, T beta, T inv_theta,
+                                       T* __restrict__ out, int64_t out_ld,
+                                       const int32_t* __restrict__ perm, int nc, int64_t row) {
   const int64_t o0 = A.off[row >> 5] + (row & 31), o1 = A.off[(row >> 5) + 1];
   T acc[NCP];
 #pragma unroll
@@ -265,7 +263,6 @@ __global__ void __launch_bounds__(256) k_mg(DSell<T> A, const T* __restrict__ di
       go[c] = gx[c] + (alpha * d[c] + beta * di * r);
     }
   }
-  T* __restrict__ out = MODE == MG_LAST ? outv.get() : nullptr;
   if (MODE == MG_LAST && out) {
     const int64_t dst = perm ? perm[row] : row;
     for (int c = 0; c < nc; ++c) out[c * out_ld + dst] = go[c];
@@ -275,22 +272,19 @@ __global__ void __launch_bounds__(256) k_mg(DSell<T> A, const T* __restrict__ di
   if (MODE == MG_STEP || MODE == MG_START) vstore<T, NCP>(Dout + row * NCP, dout);
 }
 
-// Restriction of the fine residual Rf to the coarse level: bc = R r, and the
-// coarse level's first step from x = 0: Gc = Dc = d0 = Dinv_c bc / theta.
+// Restriction row (L lanes; every lane of the group calls it, `active`
+// false past the last row): bc = R r, and the coarse level's first step from
+// x = 0: Gc = Dc = d0 = Dinv_c bc / theta (bc only when dinvc is null: the
+// coarse level is solved densely).
 template <typename T, int NCP, int L>
-__global__ void __launch_bounds__(256) k_mg_restrict(DCsr<T> R, const T* __restrict__ Rf,
-                                                     T* __restrict__ bc, T* __restrict__ Gc,
-                                                     T* __restrict__ Dc,
-                                                     const T* __restrict__ dinvc,
-                                                     T inv_theta_c, const int* skip) {
-  if (skip && *skip) return;
-  const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t row = gt / L;
-  const int lane = (int)(gt % L);
+__device__ __forceinline__ void restrict_row(const DCsr<T>& R, const T* __restrict__ Rf,
+                                             T* __restrict__ bc, T* __restrict__ Gc,
+                                             T* __restrict__ Dc, const T* __restrict__ dinvc,
+                                             T inv_theta_c, int64_t row, int lane, bool active) {
   T acc[NCP];
 #pragma unroll
   for (int c = 0; c < NCP; ++c) acc[c] = T(0);
-  if (row < R.nrow) {
+  if (active) {
     for (int32_t k = R.rp[row] + lane; k < R.rp[row + 1]; k += L) {
       const T a = R.v[k];
       T rj[NCP];
@@ -301,9 +295,9 @@ __global__ void __launch_bounds__(256) k_mg_restrict(DCsr<T> R, const T* __restr
   }
 #pragma unroll
   for (int c = 0; c < NCP; ++c) acc[c] = group_sum<L>(acc[c]);
-  if (lane != 0 || row >= R.nrow) return;
+  if (lane != 0 || !active) return;
   vstore<T, NCP>(bc + row * NCP, acc);
-  if (!dinvc) return;  // the coarse level is solved densely from bc
+  if (!dinvc) return;
   T d0[NCP];
   const T s = dinvc[row] * inv_theta_c;
 #pragma unroll
@@ -312,19 +306,16 @@ __global__ void __launch_bounds__(256) k_mg_restrict(DCsr<T> R, const T* __restr
   vstore<T, NCP>(Dc + row * NCP, d0);
 }
 
-// Correction x0 = x3 + P xc, in place in the fine gather vector Gf (each row
-// reads and writes only its own entry there; the gathers are from Xc).
+// Correction row x0 = x3 + P xc, in place in the fine gather vector Gf
+// (each row reads and writes only its own entry there).
 template <typename T, int NCP, int L>
-__global__ void __launch_bounds__(256) k_mg_prolong(DCsr<T> P, const T* __restrict__ Xc,
-                                                    T* __restrict__ Gf, const int* skip) {
-  if (skip && *skip) return;
-  const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t row = gt / L;
-  const int lane = (int)(gt % L);
+__device__ __forceinline__ void prolong_row(const DCsr<T>& P, const T* __restrict__ Xc,
+                                            T* __restrict__ Gf, int64_t row, int lane,
+                                            bool active) {
   T acc[NCP];
 #pragma unroll
   for (int c = 0; c < NCP; ++c) acc[c] = T(0);
-  if (row < P.nrow) {
+  if (active) {
     for (int32_t k = P.rp[row] + lane; k < P.rp[row + 1]; k += L) {
       const T a = P.v[k];
       T xj[NCP];
@@ -335,7 +326,7 @@ __global__ void __launch_bounds__(256) k_mg_prolong(DCsr<T> P, const T* __restri
   }
 #pragma unroll
   for (int c = 0; c < NCP; ++c) acc[c] = group_sum<L>(acc[c]);
-  if (lane != 0 || row >= P.nrow) return;
+  if (lane != 0 || !active) return;
   T x[NCP];
   vload<T, NCP>(Gf + row * NCP, x);
 #pragma unroll
@@ -343,26 +334,20 @@ __global__ void __launch_bounds__(256) k_mg_prolong(DCsr<T> P, const T* __restri
   vstore<T, NCP>(Gf + row * NCP, x);
 }
 
-// Coarsest solve x = blockdiag(Cinv) b, one warp per row; the result goes to
-// X (gathered by the parent's prolongation), or (level 0 being the coarsest)
-// to the caller's blocked out.
+// Coarsest-level row x = blockdiag(Cinv) b (a warp per row); the result goes
+// to X, or (level 0 being the coarsest) to the caller's blocked out.
 template <typename T, int NCP>
-__global__ void k_mg_dense(const T* __restrict__ C, const int32_t* __restrict__ row_blk,
-                           const int64_t* __restrict__ blk_row, const int64_t* __restrict__ blk_n,
-                           const int64_t* __restrict__ blk_dense, int64_t n,
-                           const T* __restrict__ b, T* __restrict__ X, JVec<T> outv,
-                           int64_t out_ld, const int32_t* __restrict__ perm, int nc,
-                           const int* skip) {
-  if (skip && *skip) return;
-  const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32;
-  const int lane = threadIdx.x & 31;
+__device__ __forceinline__ void dense_row(const DHier<T>& H, const T* __restrict__ b,
+                                          T* __restrict__ X, T* __restrict__ out,
+                                          int64_t out_ld, const int32_t* __restrict__ perm,
+                                          int nc, int64_t row, int lane, bool active) {
   T acc[NCP];
 #pragma unroll
   for (int c = 0; c < NCP; ++c) acc[c] = T(0);
-  if (row < n) {
-    const int blk = row_blk[row];
-    const int64_t r0 = blk_row[blk], nb = blk_n[blk];
-    const T* Cr = C + blk_dense[blk] + (row - r0) * nb;
+  if (active) {
+    const int blk = H.row_blk[row];
+    const int64_t r0 = H.blk_row[blk], nb = H.blk_n[blk];
+    const T* Cr = H.cinv + H.blk_dense[blk] + (row - r0) * nb;
     for (int64_t j = lane; j < nb; j += 32) {
       const T a = Cr[j];
       T bj[NCP];
@@ -373,13 +358,152 @@ __global__ void k_mg_dense(const T* __restrict__ C, const int32_t* __restrict__ 
   }
 #pragma unroll
   for (int c = 0; c < NCP; ++c) acc[c] = group_sum<32>(acc[c]);
-  if (lane != 0 || row >= n) return;
-  T* __restrict__ out = outv.get();
+  if (lane != 0 || !active) return;
   if (out) {
     const int64_t dst = perm ? perm[row] : row;
     for (int c = 0; c < nc; ++c) out[c * out_ld + dst] = acc[c];
   } else {
     vstore<T, NCP>(X + row * NCP, acc);
+  }
+}
+
+template <typename T, int NC, int NCP, int MODE>
+__global__ void __launch_bounds__(256) k_mg(DSell<T> A, const T* __restrict__ dinv,
+                                            const T* __restrict__ b,
+                                            const T* __restrict__ Gin,
+                                            const T* __restrict__ Din,
+                                            T* __restrict__ Gout, T* __restrict__ Dout,
+                                            T alpha, T beta, T inv_theta, JVec<T> outv,
+                                            int64_t out_ld, const int32_t* __restrict__ perm,
+                                            int nc, const int* skip) {
+  if (skip && *skip) return;
+  const int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (row >= A.nrow) return;
+  mg_row<T, NC, NCP, MODE>(A, dinv, b, Gin, Din, Gout, Dout, alpha, beta, inv_theta,
+                                  MODE == MG_LAST ? outv.get() : nullptr, out_ld, perm, nc, row);
+}
+
+template <typename T, int NCP, int L>
+__global__ void __launch_bounds__(256) k_mg_restrict(DCsr<T> R, const T* __restrict__ Rf,
+                                                     T* __restrict__ bc, T* __restrict__ Gc,
+                                                     T* __restrict__ Dc,
+                                                     const T* __restrict__ dinvc,
+                                                     T inv_theta_c, const int* skip) {
+  if (skip && *skip) return;
+  const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t row = gt / L;
+  restrict_row<T, NCP, L>(R, Rf, bc, Gc, Dc, dinvc, inv_theta_c, row, (int)(gt % L),
+                                 row < R.nrow);
+}
+
+template <typename T, int NCP, int L>
+__global__ void __launch_bounds__(256) k_mg_prolong(DCsr<T> P, const T* __restrict__ Xc,
+                                                    T* __restrict__ Gf, const int* skip) {
+  if (skip && *skip) return;
+  const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t row = gt / L;
+  prolong_row<T, NCP, L>(P, Xc, Gf, row, (int)(gt % L), row < P.nrow);
+}
+
+template <typename T, int NCP>
+__global__ void k_mg_dense(const DHier<T>* __restrict__ Hp, int l, JVec<T> outv, int64_t out_ld,
+                           int nc, const int* skip) {
+  if (skip && *skip) return;
+  const DHier<T>& H = *Hp;
+  const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32;
+  dense_row<T, NCP>(H, H.b[l], H.G1[l], outv.get(), out_ld, l == 0 ? H.perm : nullptr,
+                           nc, row, threadIdx.x & 31, row < H.ncoarse);
+}
+
+// The V-cycle from level l0 (its right-hand side and first step in place)
+// down to the coarsest level and back, on one thread-block cluster: each
+// pass of the kernel form is a phase here, every thread takes rows strided
+// by the cluster's thread count (a warp still takes 32 consecutive rows of
+// the SELL operator), and a cluster barrier (release/acquire) separates the
+// phases.  Every thread reaches every barrier.  The level's result ends in
+// G1[l0], or in `out` when l0 = 0.  Vectors written in one phase and read in
+// the next go through plain loads: the barrier (barrier.cluster arrive with
+// release, wait with acquire semantics) orders them at cluster scope.
+template <typename T, int NCP, int NT>
+__global__ void __launch_bounds__(NT, 1) k_mg_tail(const DHier<T>* __restrict__ Hp, int l0,
+                                                   JVec<T> outv, int64_t out_ld, int nc,
+                                                   const int* skip) {
+  if (skip && *skip) return;  // the same value for every thread of the cluster
+  namespace cgr = cooperative_groups;
+  cgr::cluster_group cl = cgr::this_cluster();
+  constexpr int NC = NCP == 4 ? 3 : NCP;
+  const DHier<T>& H = *Hp;
+  const int64_t tid = (int64_t)blockIdx.x * NT + threadIdx.x;
+  const int64_t nth = (int64_t)gridDim.x * NT;
+  const int last = H.nlev - 1;
+  const int lane4 = threadIdx.x & 3, lane32 = threadIdx.x & 31;
+  for (int l = l0; l < last; ++l) {
+    const DLevel<T>& L = H.lev[l];
+    const int64_t n = L.A.nrow;
+    T *G0 = H.G0[l], *G1 = H.G1[l], *D0 = H.D0[l], *D1 = H.D1[l];
+    const T* b = H.b[l];
+    const T a1 = (T)L.a1, b1 = (T)L.b1, a2 = (T)L.a2, b2 = (T)L.b2, it = (T)L.inv_theta;
+    for (int64_t r = tid; r < n; r += nth)
+      mg_row<T, NC, NCP, MG_STEP>(L.A, L.dinv, b, G0, D0, G1, D1, a1, b1, it, nullptr, 0,
+                                        nullptr, nc, r);
+    cl.sync();
+    for (int64_t r = tid; r < n; r += nth)
+      mg_row<T, NC, NCP, MG_STEP>(L.A, L.dinv, b, G1, D1, G0, D0, a2, b2, it, nullptr, 0,
+                                        nullptr, nc, r);
+    cl.sync();
+    for (int64_t r = tid; r < n; r += nth)
+      mg_row<T, NC, NCP, MG_RESID>(L.A, L.dinv, b, G0, D0, G1, nullptr, T(0), T(0), it,
+                                         nullptr, 0, nullptr, nc, r);
+    cl.sync();
+    const DLevel<T>& C = H.lev[l + 1];
+    const bool dense_next = l + 1 == last;
+    const int64_t nr = L.R.nrow, groups = nth / 4, sweeps = (nr + groups - 1) / groups;
+    for (int64_t q = 0; q < sweeps; ++q) {
+      const int64_t r = q * groups + tid / 4;
+      restrict_row<T, NCP, 4>(L.R, G1, H.b[l + 1], H.G0[l + 1], H.D0[l + 1],
+                                    dense_next ? nullptr : C.dinv, (T)C.inv_theta, r, lane4,
+                                    r < nr);
+    }
+    cl.sync();
+  }
+  {
+    const int64_t nr = H.ncoarse, groups = nth / 32, sweeps = (nr + groups - 1) / groups;
+    for (int64_t q = 0; q < sweeps; ++q) {
+      const int64_t r = q * groups + tid / 32;
+      dense_row<T, NCP>(H, H.b[last], H.G1[last], nullptr, 0, nullptr, nc, r, lane32,
+                              r < nr);
+    }
+    cl.sync();
+  }
+  T* out = outv.get();
+  for (int l = last - 1; l >= l0; --l) {
+    const DLevel<T>& L = H.lev[l];
+    const int64_t n = L.A.nrow;
+    T *G0 = H.G0[l], *G1 = H.G1[l], *D0 = H.D0[l], *D1 = H.D1[l];
+    const T* b = H.b[l];
+    const T a1 = (T)L.a1, b1 = (T)L.b1, a2 = (T)L.a2, b2 = (T)L.b2, it = (T)L.inv_theta;
+    {
+      const int64_t nr = L.P.nrow, groups = nth / 4, sweeps = (nr + groups - 1) / groups;
+      for (int64_t q = 0; q < sweeps; ++q) {
+        const int64_t r = q * groups + tid / 4;
+        prolong_row<T, NCP, 4>(L.P, H.G1[l + 1], G0, r, lane4, r < nr);
+      }
+    }
+    cl.sync();
+    for (int64_t r = tid; r < n; r += nth)
+      mg_row<T, NC, NCP, MG_START>(L.A, L.dinv, b, G0, nullptr, G1, D1, T(0), T(0), it,
+                                         nullptr, 0, nullptr, nc, r);
+    cl.sync();
+    for (int64_t r = tid; r < n; r += nth)
+      mg_row<T, NC, NCP, MG_STEP>(L.A, L.dinv, b, G1, D1, G0, D0, a1, b1, it, nullptr, 0,
+                                        nullptr, nc, r);
+    cl.sync();
+    const bool top = l == 0 && out;
+    for (int64_t r = tid; r < n; r += nth)
+      mg_row<T, NC, NCP, MG_LAST>(L.A, L.dinv, b, G0, D0, G1, nullptr, a2, b2, it,
+                                        top ? out : nullptr, out_ld, top ? H.perm : nullptr, nc,
+                                        r);
+    if (l > l0) cl.sync();
   }
 }
 
@@ -401,17 +525,46 @@ void launch_mg(int mode, const DLevel<T>& L, const T* b, const T* Gin, const T* 
   count_launches(1);
 }
 
+// Threads per block of the cluster kernel: FP64 rows need twice the
+// registers of FP32 ones.
+template <typename T>
+constexpr int tail_threads() {
+  return std::is_same<T, float>::value ? 1024 : 512;
+}
+
+template <typename T, int NCP>
+void launch_tail(const DHier<T>& H, int l0, JVec<T> out, int64_t out_ld, int nc, const int* skip,
+                 cudaStream_t s) {
+  constexpr int NT = tail_threads<T>();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(H.tail_cluster);
+  cfg.blockDim = dim3(NT);
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = H.tail_cluster;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k_mg_tail<T, NCP, NT>, H.dev, l0, out, out_ld, nc, skip);
+  count_launches(1);
+}
+
 // V-cycle below a level whose right-hand side b_l and first step (G0, D0)
 // are in place; the level's result ends in G1[l], or in `out` for level 0.
 template <typename T, int NCP>
 void vcycle_level(const DHier<T>& H, int l, JVec<T> out, int64_t out_ld, int nc,
                   const int* skip, cudaStream_t s) {
   const bool top = l == 0;
+  if (H.tail >= 0 && l == H.tail) {
+    launch_tail<T, NCP>(H, l, top ? out : JVec<T>(), out_ld, nc, skip, s);
+    return;
+  }
   if (l == H.nlev - 1) {
-    const int64_t n = H.ncoarse;
-    k_mg_dense<T, NCP><<<blocks_for(n * 32), 256, 0, s>>>(
-        H.cinv, H.row_blk, H.blk_row, H.blk_n, H.blk_dense, n, H.b[l], H.G1[l],
-        top ? out : JVec<T>(), out_ld, top ? H.perm : nullptr, nc, skip);
+    k_mg_dense<T, NCP><<<blocks_for(H.ncoarse * 32), 256, 0, s>>>(H.dev, l,
+                                                                   top ? out : JVec<T>(), out_ld,
+                                                                   nc, skip);
     count_launches(1);
     return;
   }
@@ -423,7 +576,7 @@ void vcycle_level(const DHier<T>& H, int l, JVec<T> out, int64_t out_ld, int nc,
   launch_mg<T, NCP>(MG_STEP, L, b, G0, D0, G1, D1, a1, b1, JVec<T>(), 0, nullptr, nc, skip, s);
   launch_mg<T, NCP>(MG_STEP, L, b, G1, D1, G0, D0, a2, b2, JVec<T>(), 0, nullptr, nc, skip, s);
   // residual of x3 = G0 into G1; G0 keeps x3 for the correction
-  launch_mg<T, NCP>(MG_RESID, L, b, G0, D0, G1, nullptr, T(0), T(0), nullptr, 0, nullptr, nc,
+  launch_mg<T, NCP>(MG_RESID, L, b, G0, D0, G1, nullptr, T(0), T(0), JVec<T>(), 0, nullptr, nc,
                     skip, s);
   const bool coarsest_next = l + 1 == H.nlev - 1;
   k_mg_restrict<T, NCP, 4><<<blocks_for(L.R.nrow * 4), 256, 0, s>>>(
@@ -433,11 +586,36 @@ void vcycle_level(const DHier<T>& H, int l, JVec<T> out, int64_t out_ld, int nc,
   vcycle_level<T, NCP>(H, l + 1, JVec<T>(), 0, nc, skip, s);
   k_mg_prolong<T, NCP, 4><<<blocks_for(L.P.nrow * 4), 256, 0, s>>>(L.P, H.G1[l + 1], G0, skip);
   count_launches(1);
-  launch_mg<T, NCP>(MG_START, L, b, G0, nullptr, G1, D1, T(0), T(0), nullptr, 0, nullptr, nc,
+  launch_mg<T, NCP>(MG_START, L, b, G0, nullptr, G1, D1, T(0), T(0), JVec<T>(), 0, nullptr, nc,
                     skip, s);
   launch_mg<T, NCP>(MG_STEP, L, b, G1, D1, G0, D0, a1, b1, JVec<T>(), 0, nullptr, nc, skip, s);
   launch_mg<T, NCP>(MG_LAST, L, b, G0, D0, G1, nullptr, a2, b2, top ? out : JVec<T>(), out_ld,
                     top ? H.perm : nullptr, nc, skip, s);
+}
+
+// Cluster size of the fused V-cycle tail: 16 blocks (one per SM) where the
+// device schedules such clusters, else the portable 8.
+template <typename T, int NCP>
+int tail_cluster_size() {
+  constexpr int NT = tail_threads<T>();
+  auto k = k_mg_tail<T, NCP, NT>;
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(16);
+    cfg.blockDim = dim3(NT);
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 16;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, k, &cfg) == cudaSuccess && nclusters > 0)
+      return 16;
+  }
+  cudaGetLastError();
+  return 8;
 }
 
 // ---------------------------------------------------------------------------
@@ -577,6 +755,14 @@ void launch_cheb_step(const DHier<T>& H, int nc, cudaStream_t s) {
     launch_mg<T, 1>(MG_STEP, L, H.b[0], H.G0[0], H.D0[0], H.G1[0], H.D1[0], (T)L.a1, (T)L.b1,
                     nullptr, 0, nullptr, 1, nullptr, s);
 }
+template <typename T>
+int mg_tail_cluster(int ncp) {
+  return ncp == 4 ? tail_cluster_size<T, 4>()
+                  : ncp == 2 ? tail_cluster_size<T, 2>() : tail_cluster_size<T, 1>();
+}
+template int mg_tail_cluster<double>(int);
+template int mg_tail_cluster<float>(int);
+
 template void launch_cheb_step<double>(const DHier<double>&, int, cudaStream_t);
 template void launch_cheb_step<float>(const DHier<float>&, int, cudaStream_t);
 

@@ -105,6 +105,21 @@ class fs_server_desc(ctypes.Structure):
     _fields_ = [("hbm_budget", _i64), ("max_slots", _int), ("setup_threads", _int)]
 
 
+class fs_schedule(ctypes.Structure):
+    _fields_ = [("tail_rows_velocity", _i64), ("tail_rows_pressure", _i64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class fs_tune_report(ctypes.Structure):
+    _fields_ = [("candidates", _int), ("default_ms", _d), ("best_ms", _d), ("best", fs_schedule)]
+
+    def as_dict(self):
+        return {"candidates": self.candidates, "default_ms": self.default_ms,
+                "best_ms": self.best_ms, "best": self.best.as_dict()}
+
+
 class fs_request_result(ctypes.Structure):
     _fields_ = [("id", _i64), ("status", _int), ("nsteps", _int), ("iters", _int),
                 ("arrival", _d), ("admitted", _d), ("started", _d), ("finished", _d),
@@ -139,6 +154,12 @@ _lib.fs_launch_count.restype = _i64
 _lib.fs_launch_count.argtypes = []
 _lib.fs_profile_kernel.restype = _int
 _lib.fs_profile_kernel.argtypes = [_vp, _int, _int, _P(_d), _P(_d)]
+_lib.fs_get_schedule.restype = _int
+_lib.fs_get_schedule.argtypes = [_vp, _P(fs_schedule)]
+_lib.fs_set_schedule.restype = _int
+_lib.fs_set_schedule.argtypes = [_vp, _P(fs_schedule)]
+_lib.fs_autotune.restype = _int
+_lib.fs_autotune.argtypes = [_vp, _int, _P(fs_tune_report)]
 for _name in ("fs_mesh_create", "fs_mesh_destroy", "fs_dof_map", "fs_problem_create",
               "fs_problem_destroy", "fs_assemble_step", "fs_solve", "fs_step",
               "fs_apply_operator", "fs_get_state", "fs_set_state"):
@@ -153,8 +174,9 @@ EXPORTED = ["fs_mesh_create", "fs_mesh_destroy", "fs_dof_map", "fs_problem_creat
             "fs_step_begin", "fs_step_poll", "fs_instance_stats", "fs_server_create",
             "fs_server_destroy", "fs_server_submit", "fs_server_progress",
             "fs_server_pop_completed", "fs_server_take_state", "fs_server_status",
-            "fs_server_estimate_bytes"]
-FS_KERNEL_SPMV, FS_KERNEL_SPMV_FP64, FS_KERNEL_CHEB, FS_KERNEL_ASSEMBLE_CONV = range(4)
+            "fs_server_estimate_bytes", "fs_get_schedule", "fs_set_schedule", "fs_autotune"]
+(FS_KERNEL_SPMV, FS_KERNEL_SPMV_FP64, FS_KERNEL_CHEB, FS_KERNEL_ASSEMBLE_CONV,
+ FS_KERNEL_PRECOND) = range(5)
 
 
 def _check(rc, where):
@@ -395,6 +417,25 @@ def fs_csr_residual_norm_noalloc(rowptr, col, val, x, b, stream=None, n=None):
 
 def fs_launch_count():
     return int(_lib.fs_launch_count())
+
+
+def fs_get_schedule(prob):
+    sc = fs_schedule()
+    _check(_lib.fs_get_schedule(prob, ctypes.byref(sc)), "fs_get_schedule")
+    return sc.as_dict()
+
+
+def fs_set_schedule(prob, tail_rows_velocity, tail_rows_pressure):
+    sc = fs_schedule(int(tail_rows_velocity), int(tail_rows_pressure))
+    _check(_lib.fs_set_schedule(prob, ctypes.byref(sc)), "fs_set_schedule")
+
+
+def fs_autotune(prob, reps=10):
+    """Times the preconditioner under every candidate schedule, installs
+    the fastest and returns the report as a dict."""
+    r = fs_tune_report()
+    _check(_lib.fs_autotune(prob, int(reps), ctypes.byref(r)), "fs_autotune")
+    return r.as_dict()
 
 
 def fs_profile_kernel(prob, kernel, reps=20):

@@ -1,0 +1,89 @@
+"""Execution schedules of the multigrid preconditioner.
+
+The coarse levels can run as separate kernels or inside one cluster kernel
+(fs_set_schedule); both forms evaluate the same per-row formulas, so a
+schedule changes launch counts and timing, not the solution: the
+preconditioner outputs differ at most by rounding (FMA contraction may differ
+between the two compiled forms), and the two solves then stop at different
+iterates that both meet rtol = 1e-14, so the step results agree to the
+conditioning times rtol.  Bars: FP64 1e-11 (the preconditioner differs by
+FP64 rounding only, which the FP64 Krylov iterates follow closely); FP32
+inner solves with FP64 refinement 1e-9, the parity bar (batched and solo
+solves of the same instance already differ by about 1e-10 there).
+fs_autotune times the candidates and installs the fastest.
+"""
+TOL = {"fp64": 1e-11, "fp32_refine": 1e-9}
+import numpy as np
+import pytest
+
+import fs_workloads as W
+from tests.gpu_helpers import rel_l2
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+SCHEDULES = [(0, 0), (65536, 65536), (4096, 16384), (16384, 0)]
+
+
+@pytest.fixture(scope="module")
+def fs():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2605_25403_gb300 import build
+    build.build()
+    from paper_2605_25403_gb300 import fs as mod
+    return mod
+
+
+def _run(fs, make, sched, prec, nsteps=2):
+    S = make(prec)
+    try:
+        fs.fs_set_schedule(S.prob, *sched)
+        assert fs.fs_get_schedule(S.prob) == {"tail_rows_velocity": sched[0],
+                                              "tail_rows_pressure": sched[1]}
+        st = fs.fs_step(S.prob, nsteps)
+        assert all(s["status"] == 0 for s in st)
+        return S.state()[0]
+    finally:
+        S.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_refine"])
+def test_schedules_agree_single(fs, prec):
+    p = fs.FS_PREC_FP64 if prec == "fp64" else fs.FS_PREC_FP32_REFINE
+    wl = W.channel(64, 16)
+    xs = [_run(fs, lambda q: fs.Stepper.from_workload(wl, precision=q), sc, p)
+          for sc in SCHEDULES]
+    for x in xs[1:]:
+        assert rel_l2(x, xs[0]) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_refine"])
+def test_schedules_agree_batch(fs, prec):
+    """A batch: level 0 of the hierarchies is in instance-block order, so the
+    fused kernel's result goes through the block-order map."""
+    p = fs.FS_PREC_FP64 if prec == "fp64" else fs.FS_PREC_FP32_REFINE
+    wls = [W.unit_square(12, jitter=0.1, seed=1), W.unit_square(20, jitter=0.1, seed=2),
+           W.unit_square(9, jitter=0.1, seed=3)]
+    make = lambda q: fs.Stepper.from_workloads(wls, precision=q)
+    xs = [_run(fs, make, sc, p) for sc in SCHEDULES[:2]]
+    assert rel_l2(xs[1], xs[0]) <= TOL[prec]
+
+
+def test_autotune_installs_a_candidate(fs):
+    S = fs.Stepper.from_workload(W.channel(64, 16), precision=fs.FS_PREC_FP32_REFINE)
+    try:
+        x0, t0 = S.state()
+        rep = fs.fs_autotune(S.prob, reps=3)
+        assert rep["candidates"] >= 2 and 0 < rep["best_ms"] <= rep["default_ms"]
+        assert fs.fs_get_schedule(S.prob) == rep["best"]
+        x1, t1 = S.state()
+        assert t1 == t0 and np.array_equal(x0, x1)  # state untouched
+        st = fs.fs_step(S.prob, 1)[0]
+        assert st["status"] == 0 and st["rel_res"] <= 1e-12
+        ms, _ = fs.fs_profile_kernel(S.prob, fs.FS_KERNEL_PRECOND, reps=3)
+        assert ms > 0
+        with pytest.raises(fs.FsError):
+            fs.fs_set_schedule(S.prob, -1, 0)
+    finally:
+        S.close()
