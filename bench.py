@@ -198,6 +198,7 @@ def batched_run(torch, fs, steps, warmup=1):
     B = fs.Stepper.from_workloads(wls, precision=fs.FS_PREC_FP32_REFINE)
     setup_s = time.perf_counter() - t0
     try:
+        tune = fs.fs_autotune(B.prob, reps=3)
         for _ in range(warmup):
             fs.fs_step(B.prob, 1)
         torch.cuda.synchronize()
@@ -219,7 +220,7 @@ def batched_run(torch, fs, steps, warmup=1):
                         "dt 1e-3, seed 0", "instances": len(wls), "ndof_total": ndof,
             "ms_per_step": 1e3 * per_step, "steps_per_s": 1.0 / per_step,
             "instance_steps_per_s": len(wls) / per_step, "dof_per_s": ndof / per_step,
-            "setup_s": setup_s, "timed_steps": steps,
+            "setup_s": setup_s, "timed_steps": steps, "schedule": tune,
             "iters_max": max(x["iters"] for x in st),
             "iters_median": float(np.median([x["iters"] for x in st])),
             "status_ok": all(x["status"] == 0 for x in st),
@@ -318,17 +319,20 @@ def main():
     k64 = args.fp64_steps
     if prec != fs.FS_PREC_FP64 and k64 > 0:
         S64 = fs.Stepper.from_workload(wl, precision=fs.FS_PREC_FP64, stream=stream.cuda_stream)
+        tune64 = fs.fs_autotune(S64.prob, reps=5)
         for _ in range(args.warmup):
             fs.fs_step(S64.prob, 1)
         t64, st64 = time_steps(torch, fs, S64, stream, k64, flush)
         fp64 = {"steps_per_s": 1e3 * len(t64) / sum(t64),
                 "ms_per_step": sum(t64) / len(t64),
                 "iters_per_step": float(np.mean([s["iters"] for s in st64])),
-                "rel_res_max": max(s["rel_res"] for s in st64)}
+                "rel_res_max": max(s["rel_res"] for s in st64), "schedule": tune64}
         S64.close()
 
     # ---- the timed path ----------------------------------------------------
     S = fs.Stepper.from_workload(wl, precision=prec, stream=stream.cuda_stream)
+    # set-up, untimed: pick the multigrid schedule by timing the candidates
+    tune = fs.fs_autotune(S.prob, reps=5)
     for _ in range(args.warmup):
         fs.fs_step(S.prob, 1)
     sampler = ClockSampler(local)
@@ -356,6 +360,9 @@ def main():
     tcur = t0
     e2e_ms = []
     for k in range(max(2, args.steps // 2) + 1):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        stream.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -378,13 +385,16 @@ def main():
                     ("assemble", fs.FS_KERNEL_ASSEMBLE_CONV)):
         ms, by = fs.fs_profile_kernel(S.prob, k, reps=20)
         kernels[name] = {"ms": ms, "alg_bytes": by, "gbs": by / ms / 1e6}
+    kernels["precond"] = {"ms": fs.fs_profile_kernel(S.prob, fs.FS_KERNEL_PRECOND, reps=10)[0],
+                          "unit": "one block-preconditioner application (graph of 10)"}
     peak, peak_kind = measured_peak_hbm()
     kname = args.roofline_kernel
     achieved = kernels[kname]["gbs"]
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": peak_kind,
-                "kernel": {"cheb": "k_cheb (fused Chebyshev step, finest P2 level)",
-                           "spmv": "k_spmv_full", "assemble": "k_assemble_conv"}[kname],
+                "kernel": {"cheb": "k_mg (Chebyshev step, finest P2 level, SELL-32)",
+                           "spmv": "k_spmv_full (SELL-32)",
+                           "assemble": "k_assemble_conv"}[kname],
                 "traffic": traffic_from_profiles(kname, wl.name)}
 
     # ---- CPU baseline: the oracle on a bounded sample ---------------------
@@ -412,7 +422,7 @@ def main():
         "data": "synthetic",
         "config": {"workload": wl.name, "ndof": ndof, "cells": wl.ncell, "nu": wl.nu,
                    "dt": wl.dt, "precision": args.precision, "rtol": 1e-14,
-                   "l2": "flushed before every timed step (256 MB write)",
+                   "l2": "flushed before every timed step and every e2e step (256 MB write)",
                    "parallelism": "replicas" if world > 1 else "single"},
         "dof_per_s": value * ndof,
         "step_ms_p50": statistics.median(times),
@@ -426,6 +436,7 @@ def main():
         "e2e": {"value": e2e_val, "unit": "steps/s", "h2d_bytes_per_step": 8 * ndof,
                 "d2h_bytes_per_step": 8 * ndof},
         "gpu_launches": launches,
+        "schedule": tune,
         "roofline": roofline,
         "kernels": kernels,
         "cpu_baseline": cpu,
