@@ -40,6 +40,14 @@ def parse(argv=None):
     p.add_argument("--fp64-steps", type=int, default=20,
                    help="steps of the plain FP64 path timed for the comparison")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--schedule", default="auto",
+                   help="multigrid schedule 'V,P' (fused-tail row thresholds of the velocity "
+                        "and pressure hierarchies), or 'auto' to run the autotuner at set-up; "
+                        "fix it when a profiler distorts the autotuner's timings")
+    p.add_argument("--no-graph", action="store_true",
+                   help="launch the solver's kernels one by one instead of replaying captured "
+                        "CUDA graphs (for per-kernel profilers, which cannot see kernels inside "
+                        "graphs with conditional nodes)")
     p.add_argument("--roofline-kernel", default="cheb", choices=["cheb", "spmv", "assemble"])
     p.add_argument("--batch-steps", type=int, default=3,
                    help="timed steps of the 96-instance batched workload (0: skip)")
@@ -266,7 +274,7 @@ def serving_run(fs, count, rate=200.0, budget=150 << 30, slots=32):
 
 
 # ---------------------------------------------------------------------------
-def time_steps(torch, fs, S, stream, steps, flush):
+def time_steps(torch, fs, S, stream, steps, flush, opts=None):
     """Per-step CUDA-event times (ms) of fs_step on the problem's stream;
     L2 flushed (256 MB write) before each step, outside the timed window."""
     out = []
@@ -278,7 +286,7 @@ def time_steps(torch, fs, S, stream, steps, flush):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        st = fs.fs_step(S.prob, 1)[0]
+        st = fs.fs_step(S.prob, 1, opts)[0]
         e1.record(stream)
         e1.synchronize()
         out.append(e0.elapsed_time(e1))
@@ -332,7 +340,12 @@ def main():
     # ---- the timed path ----------------------------------------------------
     S = fs.Stepper.from_workload(wl, precision=prec, stream=stream.cuda_stream)
     # set-up, untimed: pick the multigrid schedule by timing the candidates
-    tune = fs.fs_autotune(S.prob, reps=5)
+    if args.schedule == "auto":
+        tune = fs.fs_autotune(S.prob, reps=5)
+    else:
+        v, p_ = (int(q) for q in args.schedule.split(","))
+        fs.fs_set_schedule(S.prob, v, p_)
+        tune = {"fixed": fs.fs_get_schedule(S.prob)}
     for _ in range(args.warmup):
         fs.fs_step(S.prob, 1)
     sampler = ClockSampler(local)
@@ -341,7 +354,10 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     l0 = fs.fs_launch_count()
-    times, stats = time_steps(torch, fs, S, stream, args.steps, flush)
+    opts = fs.fs_default_solve_opts(use_graph=0) if args.no_graph else None
+    torch.cuda.nvtx.range_push("bench_timed")  # profilers can select the timed steps
+    times, stats = time_steps(torch, fs, S, stream, args.steps, flush, opts)
+    torch.cuda.nvtx.range_pop()
     launches = fs.fs_launch_count() - l0
     torch.cuda.synchronize()
     if dist:
@@ -423,7 +439,8 @@ def main():
         "config": {"workload": wl.name, "ndof": ndof, "cells": wl.ncell, "nu": wl.nu,
                    "dt": wl.dt, "precision": args.precision, "rtol": 1e-14,
                    "l2": "flushed before every timed step and every e2e step (256 MB write)",
-                   "parallelism": "replicas" if world > 1 else "single"},
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "graphs": not args.no_graph},
         "dof_per_s": value * ndof,
         "step_ms_p50": statistics.median(times),
         "step_ms_p99": float(np.percentile(times, 99)),

@@ -46,8 +46,11 @@ constexpr int kU = 4;
 
 // ---------------------------------------------------------------------------
 // y = K x  or  y = b - K x with K = [A (per component), -BT; B, diag(D)]
-// Threads [0, w2) take the velocity rows (w2 = n2 rounded up to a warp), the
-// following ones the pressure rows, so no warp mixes the two.
+// Threads [0, wp) take the pressure rows (wp = nv rounded up to a warp), the
+// following ones the velocity rows, so no warp mixes the two.  The pressure
+// rows come first: each holds d components of every P2 neighbour (62 slots
+// x 3 values in 3D), the longest work per thread, and the blocks scheduled
+// first start first instead of forming a tail.
 // ---------------------------------------------------------------------------
 template <typename T, typename V, int DIM>
 __global__ void __launch_bounds__(256) k_spmv_full(DOp<T> op, JVec<const V> xv,
@@ -57,10 +60,10 @@ __global__ void __launch_bounds__(256) k_spmv_full(DOp<T> op, JVec<const V> xv,
   const V* __restrict__ x = xv.get();
   V* __restrict__ y = yv.get();
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t n2 = op.n2, nv = op.nv, w2 = (n2 + 31) & ~(int64_t)31;
+  const int64_t n2 = op.n2, nv = op.nv, wp = (nv + 31) & ~(int64_t)31;
   const V* __restrict__ xp = x + DIM * n2;
-  if (t < w2) {
-    const int64_t row = t;
+  if (t >= wp) {
+    const int64_t row = t - wp;
     if (row >= n2) return;
     V acc[DIM];
 #pragma unroll
@@ -103,7 +106,7 @@ __global__ void __launch_bounds__(256) k_spmv_full(DOp<T> op, JVec<const V> xv,
       y[r] = resid ? b[r] - acc[c] : acc[c];
     }
   } else {
-    const int64_t q = t - w2;
+    const int64_t q = t;
     if (q >= nv) return;
     V acc = V(0);
     const int64_t o1 = op.B.off[(q >> 5) + 1];
@@ -722,7 +725,7 @@ inline unsigned grid_stride_blocks(int64_t n) {
 template <typename T, typename V>
 void launch_spmv_full(const DOp<T>& op, JVec<const V> x, const V* b, JVec<V> y, int resid,
                       const int* skip, cudaStream_t s) {
-  const int64_t threads = ((op.n2 + 31) & ~(int64_t)31) + op.nv;
+  const int64_t threads = ((op.nv + 31) & ~(int64_t)31) + op.n2;
   if (op.dim == 2)
     k_spmv_full<T, V, 2><<<blocks_for(threads), 256, 0, s>>>(op, x, b, y, resid, skip);
   else

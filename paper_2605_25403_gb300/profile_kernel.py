@@ -22,25 +22,32 @@ if ROOT not in sys.path:
 def main(argv=None):
     p = argparse.ArgumentParser()
     p.add_argument("--workload", default="cube", choices=["channel", "cube", "unit_square"])
-    p.add_argument("--kernel", default="cheb", choices=["cheb", "spmv", "spmv_fp64", "assemble"])
+    p.add_argument("--kernel", default="cheb",
+                   choices=["cheb", "spmv", "spmv_fp64", "assemble", "precond"])
     p.add_argument("--precision", default="fp32_refine", choices=["fp32_refine", "fp64"])
     p.add_argument("--reps", type=int, default=20)
+    p.add_argument("--n", type=int, default=0,
+                   help="cells per axis instead of the workload's own (cube and channel x)")
     a = p.parse_args(argv)
     import fs_workloads as W
     from paper_2605_25403_gb300 import build
     build.build()
     from paper_2605_25403_gb300 import fs
     wl = {"channel": W.C2, "cube": W.C3, "unit_square": W.C1}[a.workload]
+    if a.n > 0:
+        wl = W.cube(a.n, jitter=0.05, seed=W.C3.seed) if a.workload == "cube" else \
+            W.channel(a.n, max(2, a.n * 96 // 512)) if a.workload == "channel" else W.unit_square(a.n)
     prec = fs.FS_PREC_FP32_REFINE if a.precision == "fp32_refine" else fs.FS_PREC_FP64
     kid = {"cheb": fs.FS_KERNEL_CHEB, "spmv": fs.FS_KERNEL_SPMV,
-           "spmv_fp64": fs.FS_KERNEL_SPMV_FP64, "assemble": fs.FS_KERNEL_ASSEMBLE_CONV}[a.kernel]
+           "spmv_fp64": fs.FS_KERNEL_SPMV_FP64, "assemble": fs.FS_KERNEL_ASSEMBLE_CONV,
+           "precond": fs.FS_KERNEL_PRECOND}[a.kernel]
     S = fs.Stepper.from_workload(wl, precision=prec)
     try:
         ms, by = fs.fs_profile_kernel(S.prob, kid, reps=a.reps)
     finally:
         S.close()
     print(json.dumps({"workload": wl.name, "kernel": a.kernel, "precision": a.precision,
-                      "ms": ms, "alg_bytes": by, "gbs": by / ms / 1e6}))
+                      "ms": ms, "alg_bytes": by, "gbs": by / ms / 1e6 if by else None}))
     return 0
 
 
