@@ -307,12 +307,11 @@ int fs_csr_residual_norm(int64_t n, const int64_t* rowptr, const int32_t* col,
                          double* out2, void* stream);
 
 /* The same residual check for callers that cannot allocate device memory
- * (the paper has no counterpart: it is a deployment aid).  Callers that run
- * while a stream is being captured into a CUDA graph, serving processes whose
- * device memory is committed to resident problems under a fixed budget, and
- * host applications that forbid libraries to grow their footprint after
- * start-up cannot call cudaMalloc; this entry point calls no allocator at
- * all.  Its scratch is a fixed array in the library's static device memory
+ * (the paper has no counterpart: it is a deployment aid).  Serving processes
+ * whose device memory is already committed to resident problems under a
+ * fixed budget, and host applications that forbid libraries to grow their
+ * device footprint after start-up, cannot call cudaMalloc when they want to
+ * check a solution; this entry point calls no allocator at all.  Its scratch is a fixed array in the library's static device memory
  * (about 128 KB, held by every GPU that loads the library until the process
  * exits), sized for systems of at most 4,194,304 rows: larger n returns
  * FS_ERR_INVALID_ARG with a message, before any device work.  Arguments,

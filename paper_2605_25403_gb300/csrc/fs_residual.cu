@@ -151,10 +151,9 @@ extern "C" int fs_csr_residual_norm(int64_t n, const int64_t* rowptr, const int3
 // Allocation-free variant of the same check.
 //
 // Some callers cannot allocate device memory when they want to check a
-// solution: code that runs while a stream is being captured into a CUDA
-// graph, a serving process whose device memory is already committed to
+// solution: a serving process whose device memory is already committed to
 // resident problems under a fixed budget, or a host application that does
-// not let libraries grow their footprint after start-up.  This entry point
+// not let libraries grow their device footprint after start-up.  This entry point
 // runs the same kernel with its scratch (per-block partial sums, the ticket
 // counter and the two results) in a fixed array of the library's static
 // device memory instead: kNoAllocBlocks blocks of 512 rows each, so systems

@@ -1,8 +1,9 @@
 """The allocation-free residual check against the allocating one.
 
 fs_csr_residual_norm_noalloc exists for callers that cannot allocate device
-memory (graph capture, fixed serving budgets, hosts that forbid a library to
-grow after start-up); it runs the same reduction with static device scratch.
+memory (serving processes whose memory is committed under a fixed budget,
+hosts that forbid a library to grow after start-up); it runs the same
+reduction with static device scratch.
 Two calls in a row must agree with fs_csr_residual_norm within the tolerance
 of the other residual tests.  Collected last so that a failure here comes
 after every other test has run."""
