@@ -18,8 +18,7 @@
  *         - (p, div v) = (f^{n+1}, v),      (div u, q) = 0;
  *   - Sec. 3.3 / 4.1: the manufactured solutions (steady polynomial example
  *     of Sec. 3.3, the unsteady benchmark of Sec. 4.1).
- * Readings where the paper is silent are listed in the design doc; the ones that
- * shape this file: the load (f, v) is taken as (I_h f, v) = M I_h f with P2
+ * Where the paper is silent this file reads it as follows: the load (f, v) is taken as (I_h f, v) = M I_h f with P2
  * nodal interpolation; Dirichlet rows are replaced by identity rows keeping
  * their pattern; when all of the boundary is Dirichlet the row of pressure
  * DOF 0 is replaced by an identity row holding p_exact(x_0, t).

@@ -1,6 +1,6 @@
 """Parity of the CUDA path (through the C ABI) against the oracle.
 
-Bars ("Tolerances"):
+Bars:
   * DOF map / CSR structure: bit-exact (tests/test_abi.py);
   * assembled matrix and right-hand side: every entry within 1e-12 of the
     largest entry of its row (both sides integrate exactly; they differ only
