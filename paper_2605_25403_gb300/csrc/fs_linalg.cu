@@ -41,8 +41,12 @@ __device__ __forceinline__ V group_sum(V v) {
 }
 
 // Row loops take kU slots at a time (loads issued before the FMAs); padding
-// slots have coefficient 0 and the row itself as column.
+// slots have coefficient 0 and a valid column.  The FP32 saddle-point SpMV
+// takes kUSpmv: its rows read more per slot (d gathers, or d values), and
+// deeper groups measured faster there (cube 48^3: 0.115 -> 0.090 ms), while
+// the smoothing pass and the FP64 SpMV are fastest at 4.
 constexpr int kU = 4;
+constexpr int kUSpmv = 6;
 
 // ---------------------------------------------------------------------------
 // y = K x  or  y = b - K x with K = [A (per component), -BT; B, diag(D)]
@@ -62,6 +66,9 @@ __global__ void __launch_bounds__(256) k_spmv_full(DOp<T> op, JVec<const V> xv,
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t n2 = op.n2, nv = op.nv, wp = (nv + 31) & ~(int64_t)31;
   const V* __restrict__ xp = x + DIM * n2;
+  // slots per group: FP64 rows are partly bound by FP64 arithmetic and do
+  // best at the shallower depth
+  constexpr int kUS = std::is_same<V, float>::value ? kUSpmv : kU;
   if (t >= wp) {
     const int64_t row = t - wp;
     if (row >= n2) return;
@@ -70,34 +77,46 @@ __global__ void __launch_bounds__(256) k_spmv_full(DOp<T> op, JVec<const V> xv,
     for (int c = 0; c < DIM; ++c) acc[c] = V(0);
     {
       const int64_t o1 = op.A.off[(row >> 5) + 1];
-      for (int64_t o = op.A.off[row >> 5] + (row & 31); o < o1; o += kU * 32) {
-        V a[kU];
-        int32_t j[kU];
+      for (int64_t o = op.A.off[row >> 5] + (row & 31); o < o1; o += kUS * 32) {
+        V a[kUS];
+        int32_t j[kUS];
 #pragma unroll
-        for (int u = 0; u < kU; ++u) {
+        for (int u = 0; u < kUS; ++u) {
           const int64_t oo = o + u * 32;
           const bool ok = oo < o1;
           a[u] = ok ? (V)op.A.v[oo] : V(0);
           j[u] = ok ? op.A.ci[oo] : (int32_t)row;
         }
-        V xv[kU][DIM];
+        V xv[kUS][DIM];
 #pragma unroll
-        for (int u = 0; u < kU; ++u)
+        for (int u = 0; u < kUS; ++u)
 #pragma unroll
           for (int c = 0; c < DIM; ++c) xv[u][c] = x[c * n2 + j[u]];
 #pragma unroll
-        for (int u = 0; u < kU; ++u)
+        for (int u = 0; u < kUS; ++u)
 #pragma unroll
           for (int c = 0; c < DIM; ++c) acc[c] += a[u] * xv[u][c];
       }
     }
     {
-      const int64_t s0 = op.BT.off[row >> 5], o1 = op.BT.off[(row >> 5) + 1];
-      for (int64_t o = s0 + (row & 31); o < o1; o += 32) {
-        const int64_t base = (o - (row & 31)) * DIM + (row & 31);
-        const V p = xp[op.BT.ci[o]];
+      // d values per slot, component-major: component c of slot u at
+      // (slice offset + 32 u) d + 32 c + t
+      const int64_t t32 = row & 31, o1 = op.BT.off[(row >> 5) + 1];
+      for (int64_t o = op.BT.off[row >> 5] + t32; o < o1; o += kU * 32) {
+        V p[kU], bv[kU][DIM];
 #pragma unroll
-        for (int c = 0; c < DIM; ++c) acc[c] -= (V)op.BT.v[base + 32 * c] * p;
+        for (int u = 0; u < kU; ++u) {
+          const int64_t oo = o + u * 32;
+          const bool ok = oo < o1;
+          const int64_t base = (oo - t32) * DIM + t32;
+          p[u] = ok ? xp[op.BT.ci[oo]] : V(0);
+#pragma unroll
+          for (int c = 0; c < DIM; ++c) bv[u][c] = ok ? (V)op.BT.v[base + 32 * c] : V(0);
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u)
+#pragma unroll
+          for (int c = 0; c < DIM; ++c) acc[c] -= bv[u][c] * p[u];
       }
     }
 #pragma unroll
@@ -109,21 +128,25 @@ __global__ void __launch_bounds__(256) k_spmv_full(DOp<T> op, JVec<const V> xv,
     const int64_t q = t;
     if (q >= nv) return;
     V acc = V(0);
-    const int64_t o1 = op.B.off[(q >> 5) + 1];
-    for (int64_t o = op.B.off[q >> 5] + (q & 31); o < o1; o += kU * 32) {
-      int32_t j[kU];
+    const int64_t t32 = q & 31, o1 = op.B.off[(q >> 5) + 1];
+    for (int64_t o = op.B.off[q >> 5] + t32; o < o1; o += kUS * 32) {
+      V bv[kUS][DIM], xv[kUS][DIM];
 #pragma unroll
-      for (int u = 0; u < kU; ++u) {
+      for (int u = 0; u < kUS; ++u) {
         const int64_t oo = o + u * 32;
-        j[u] = oo < o1 ? op.B.ci[oo] : -1;
+        const bool ok = oo < o1;
+        const int64_t base = (oo - t32) * DIM + t32;
+        const int32_t j = ok ? op.B.ci[oo] : 0;
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) {
+          bv[u][c] = ok ? (V)op.B.v[base + 32 * c] : V(0);
+          xv[u][c] = x[c * n2 + j];
+        }
       }
 #pragma unroll
-      for (int u = 0; u < kU; ++u) {
-        if (j[u] < 0) break;
-        const int64_t base = (o + u * 32 - (q & 31)) * DIM + (q & 31);
+      for (int u = 0; u < kUS; ++u)
 #pragma unroll
-        for (int c = 0; c < DIM; ++c) acc += (V)op.B.v[base + 32 * c] * x[c * n2 + j[u]];
-      }
+        for (int c = 0; c < DIM; ++c) acc += bv[u][c] * xv[u][c];
     }
     const V v = acc + (V)op.diagp[q] * xp[q];
     const int64_t r = DIM * n2 + q;
