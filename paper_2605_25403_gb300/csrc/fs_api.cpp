@@ -1461,7 +1461,16 @@ int fs_step(fs_problem* P, int nsteps, const fs_solve_opts* opts, fs_solve_stats
   P->ctx.per_step = per_step;
   int done = 0;
   int rc = FS_OK;
-  while (!done) rc = fs_step_poll(P, 1, &done);
+  while (!done) {
+    rc = fs_step_poll(P, 1, &done);
+    if (rc != FS_OK && !done) {
+      // an error before the steps finished (a failed CUDA call, e.g. after a
+      // device fault): give up on the remaining steps instead of polling on
+      P->ctx.phase = PH_IDLE;
+      P->ctx.per_step = nullptr;
+      break;
+    }
+  }
   return rc;
 }
 
