@@ -41,9 +41,10 @@ def parse(argv=None):
                    help="steps of the plain FP64 path timed for the comparison")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--schedule", default="auto",
-                   help="multigrid schedule 'V,P' (fused-tail row thresholds of the velocity "
-                        "and pressure hierarchies), or 'auto' to run the autotuner at set-up; "
-                        "fix it when a profiler distorts the autotuner's timings")
+                   help="schedule 'V,P[,S,M]' (fused-tail row thresholds of the velocity and "
+                        "pressure hierarchies, SpMV and smoothing slot-group depths), or 'auto' "
+                        "to run the autotuner at set-up; fix it when a profiler distorts the "
+                        "autotuner's timings")
     p.add_argument("--no-graph", action="store_true",
                    help="launch the solver's kernels one by one instead of replaying captured "
                         "CUDA graphs (for per-kernel profilers, which cannot see kernels inside "
@@ -343,8 +344,7 @@ def main():
     if args.schedule == "auto":
         tune = fs.fs_autotune(S.prob, reps=5)
     else:
-        v, p_ = (int(q) for q in args.schedule.split(","))
-        fs.fs_set_schedule(S.prob, v, p_)
+        fs.fs_set_schedule(S.prob, *(int(q) for q in args.schedule.split(",")))
         tune = {"fixed": fs.fs_get_schedule(S.prob)}
     for _ in range(args.warmup):
         fs.fs_step(S.prob, 1)

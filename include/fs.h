@@ -338,17 +338,23 @@ int fs_csr_residual_norm_noalloc(int64_t n, const int64_t* rowptr,
  * re-captured by the next solve); FS_ERR_BUSY while a step is in progress.
  * fs_autotune times one application of the preconditioner (a CUDA graph of
  * `reps` applications, CUDA events) for every pair of candidate thresholds
- * {0, 4096, 16384, 65536} of the velocity and pressure hierarchies, installs
- * the fastest and reports it.  Leaves the state and assembled system
+ * {0, 4096, 16384, 65536} of the velocity and pressure hierarchies and both
+ * smoothing group depths, and the saddle-point SpMV (`reps` launches) for
+ * every SpMV group depth; it installs the fastest of each and reports them.  Leaves the state and assembled system
  * unchanged.  Synchronises. */
 typedef struct {
   int64_t tail_rows_velocity;
   int64_t tail_rows_pressure;
+  int32_t spmv_group;    /* SELL slots a thread issues together in the SpMV:
+                            4, 6 or 8; 0 = 6 in FP32, 4 in FP64 */
+  int32_t smooth_group;  /* ... in the smoothing passes: 4 or 6; 0 = 4    */
 } fs_schedule;
 typedef struct {
   int candidates;        /* schedules timed                                  */
   double default_ms;     /* one preconditioner application, schedule before */
   double best_ms;        /* ... with the installed schedule                  */
+  double spmv_default_ms;  /* one SpMV, schedule before                      */
+  double spmv_best_ms;     /* ... with the installed schedule                */
   fs_schedule best;
 } fs_tune_report;
 int fs_get_schedule(const fs_problem* prob, fs_schedule* out);

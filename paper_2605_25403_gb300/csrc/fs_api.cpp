@@ -16,6 +16,7 @@
 #include <cstdio>
 #include <cstring>
 #include <functional>
+#include <initializer_list>
 #include <memory>
 #include <mutex>
 #include <string>
@@ -165,7 +166,7 @@ struct fs_problem {
   std::vector<fs_solve_stats> last_stats;  // per instance, last solve
   double t = 0;
   bool assembled = false;
-  fs_schedule sched{0, 0};
+  fs_schedule sched{0, 0, 0, 0};
 
   TileList tl() const { return TileList{tiles, ntiles}; }
 
@@ -375,6 +376,17 @@ int upload_hierarchy(fs_problem* P, const UnionHierarchy& U, int nc, DHier<T>& D
   return FS_OK;
 }
 
+// Slot-group depths of the SpMV (this precision's operator; the FP64
+// residual operator of the refinement keeps its default) and of the
+// smoothing passes; the device copies of the hierarchies are refreshed by
+// apply_tail.
+template <typename T>
+void apply_groups(fs_problem* P, Precision<T>& pr, const fs_schedule& sc) {
+  (void)P;
+  pr.op.group = sc.spmv_group;
+  pr.HA.group = pr.HK.group = sc.smooth_group ? sc.smooth_group : 4;
+}
+
 // The fused cluster kernel takes the levels with at most tail_rows rows
 // (from the first such level that still has a level below it; 0 = none);
 // the device copy of the hierarchy is refreshed.
@@ -501,6 +513,7 @@ int setup_precision(fs_problem* P, Precision<T>& pr, const UnionHierarchy& HA,
   FS_TRY(upload_hierarchy<T>(P, HK, 1, pr.HK));
   FS_TRY(apply_tail<T>(P, pr.HA, P->sched.tail_rows_velocity));
   FS_TRY(apply_tail<T>(P, pr.HK, P->sched.tail_rows_pressure));
+  apply_groups<T>(P, pr, P->sched);
   std::vector<T> mi(mplinv_nu.begin(), mplinv_nu.end());
   FS_TRY(P->upload(&pr.mplinv_nu, mi));
   FS_TRY(alloc_krylov<T>(P, pr.kr, m, first, count));
@@ -906,6 +919,7 @@ void drop_graphs(Krylov<T>& K) {
 
 template <typename T>
 int install_schedule(fs_problem* P, Precision<T>& pr, const fs_schedule& sc) {
+  apply_groups<T>(P, pr, sc);
   FS_TRY(apply_tail<T>(P, pr.HA, sc.tail_rows_velocity));
   FS_TRY(apply_tail<T>(P, pr.HK, sc.tail_rows_pressure));
   drop_graphs(pr.kr);
@@ -967,6 +981,36 @@ int time_precond(fs_problem* P, Precision<T>& pr, int reps, double* ms) {
 int time_precond(fs_problem* P, int reps, double* ms) {
   if (P->desc.precision == FS_PREC_FP64) return time_precond<double>(P, P->p64, reps, ms);
   return time_precond<float>(P, P->p32, reps, ms);
+}
+
+// One saddle-point SpMV in the solver arithmetic (mean of `reps` launches
+// on the Krylov scratch vectors, after 3 warm-up launches).
+template <typename T>
+int time_spmv(fs_problem* P, Precision<T>& pr, int reps, double* ms) {
+  cudaStream_t s = P->stream;
+  auto launch = [&]() {
+    launch_spmv_full<T, T>(pr.op, pr.kr.Vb, nullptr, pr.kr.Vb + P->ndof, 0, nullptr, s);
+  };
+  cudaEvent_t e0, e1;
+  FS_CUDA(cudaEventCreate(&e0));
+  FS_CUDA(cudaEventCreate(&e1));
+  for (int i = 0; i < 3; ++i) launch();
+  FS_CUDA(cudaEventRecord(e0, s));
+  for (int i = 0; i < reps; ++i) launch();
+  FS_CUDA(cudaEventRecord(e1, s));
+  FS_CUDA(cudaEventSynchronize(e1));
+  float t = 0;
+  cudaEventElapsedTime(&t, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  FS_TRY(check_launch("SpMV timing"));
+  *ms = t / reps;
+  return FS_OK;
+}
+
+int time_spmv(fs_problem* P, int reps, double* ms) {
+  if (P->desc.precision == FS_PREC_FP64) return time_spmv<double>(P, P->p64, reps, ms);
+  return time_spmv<float>(P, P->p32, reps, ms);
 }
 
 int solve_opts(const fs_solve_opts* opts, fs_solve_opts& o) {
@@ -1628,7 +1672,11 @@ int fs_get_schedule(const fs_problem* P, fs_schedule* out) {
 }
 
 int fs_set_schedule(fs_problem* P, const fs_schedule* sc) {
-  if (!P || !sc || sc->tail_rows_velocity < 0 || sc->tail_rows_pressure < 0) {
+  const auto in = [](int v, std::initializer_list<int> ok) {
+    return std::find(ok.begin(), ok.end(), v) != ok.end();
+  };
+  if (!P || !sc || sc->tail_rows_velocity < 0 || sc->tail_rows_pressure < 0 ||
+      !in(sc->spmv_group, {0, 4, 6, 8}) || !in(sc->smooth_group, {0, 4, 6})) {
     set_error("fs_set_schedule: bad argument");
     return FS_ERR_INVALID_ARG;
   }
@@ -1650,40 +1698,67 @@ int fs_autotune(fs_problem* P, int reps, fs_tune_report* report) {
   }
   if (!P->assembled) FS_TRY(assemble_impl(P, P->t + P->desc.dt));
   const int64_t cand[4] = {0, 4096, 16384, 65536};
+  const int sgroups[2] = {4, 6}, pgroups[3] = {4, 6, 8};
   fs_tune_report r{};
   r.best = P->sched;
   FS_TRY(time_precond(P, reps, &r.default_ms));
+  FS_TRY(time_spmv(P, reps, &r.spmv_default_ms));
   r.best_ms = r.default_ms;
+  r.spmv_best_ms = r.spmv_default_ms;
   r.candidates = 1;
-  // distinct schedules only: thresholds that select the same levels agree
-  auto levels = [&](const fs_schedule& sc) {
-    std::pair<int, int> k;
+  // puts a schedule in place without dropping graphs (timing only) and
+  // returns the choices it makes, so equal choices are timed once
+  auto apply = [&](const fs_schedule& sc) {
+    std::array<int, 4> k;
     if (P->desc.precision == FS_PREC_FP64) {
-      apply_tail<double>(P, P->p64.HA, sc.tail_rows_velocity);
-      apply_tail<double>(P, P->p64.HK, sc.tail_rows_pressure);
-      k = {P->p64.HA.tail, P->p64.HK.tail};
+      auto& pr = P->p64;
+      apply_groups<double>(P, pr, sc);
+      apply_tail<double>(P, pr.HA, sc.tail_rows_velocity);
+      apply_tail<double>(P, pr.HK, sc.tail_rows_pressure);
+      k = {pr.HA.tail, pr.HK.tail, pr.HA.group, pr.op.group};
     } else {
-      apply_tail<float>(P, P->p32.HA, sc.tail_rows_velocity);
-      apply_tail<float>(P, P->p32.HK, sc.tail_rows_pressure);
-      k = {P->p32.HA.tail, P->p32.HK.tail};
+      auto& pr = P->p32;
+      apply_groups<float>(P, pr, sc);
+      apply_tail<float>(P, pr.HA, sc.tail_rows_velocity);
+      apply_tail<float>(P, pr.HK, sc.tail_rows_pressure);
+      k = {pr.HA.tail, pr.HK.tail, pr.HA.group, pr.op.group};
     }
     return k;
   };
-  std::vector<std::pair<int, int>> seen{levels(P->sched)};
-  for (int64_t v : cand)
-    for (int64_t p : cand) {
-      fs_schedule sc{v, p};
-      std::pair<int, int> k = levels(sc);
-      if (std::find(seen.begin(), seen.end(), k) != seen.end()) continue;
-      seen.push_back(k);
-      double ms = 0;
-      FS_TRY(time_precond(P, reps, &ms));
-      r.candidates += 1;
-      if (ms < r.best_ms) {
-        r.best_ms = ms;
-        r.best = sc;
+  // the preconditioner: fused-tail thresholds x smoothing group depths
+  std::vector<std::array<int, 4>> seen{apply(P->sched)};
+  const fs_schedule base = P->sched;
+  for (int g : sgroups)
+    for (int64_t v : cand)
+      for (int64_t p : cand) {
+        fs_schedule sc = base;
+        sc.tail_rows_velocity = v;
+        sc.tail_rows_pressure = p;
+        sc.smooth_group = g;
+        std::array<int, 4> k = apply(sc);
+        if (std::find(seen.begin(), seen.end(), k) != seen.end()) continue;
+        seen.push_back(k);
+        double ms = 0;
+        FS_TRY(time_precond(P, reps, &ms));
+        r.candidates += 1;
+        if (ms < r.best_ms) {
+          r.best_ms = ms;
+          r.best = sc;
+        }
       }
+  // the SpMV: group depths, with the preconditioner's choice in place
+  for (int g : pgroups) {
+    fs_schedule sc = r.best;
+    sc.spmv_group = g;
+    apply(sc);
+    double ms = 0;
+    FS_TRY(time_spmv(P, reps, &ms));
+    r.candidates += 1;
+    if (ms < r.spmv_best_ms) {
+      r.spmv_best_ms = ms;
+      r.best.spmv_group = g;
     }
+  }
   FS_TRY(install_schedule(P, r.best));
   if (report) *report = r;
   return FS_OK;

@@ -130,6 +130,7 @@ struct DOp {
   // (off[s] + 32 u) dim + 32 c + t.
   DSell<T> A, B, BT;
   const T* diagp = nullptr;
+  int group = 0;  // slots issued together per thread (0: the default)
 };
 
 // y = K x (resid == 0) or y = b - K x (resid == 1); vectors of type V.
@@ -174,6 +175,8 @@ struct DHier {
   // the caller's row of block row r, iperm its inverse; null when equal
   const int32_t* perm = nullptr;
   const int32_t* iperm = nullptr;
+  // slots issued together per thread in the smoothing passes (4 or 6)
+  int group = 4;
   // first level run by the fused cluster kernel (-1: none), its cluster size
   int tail = -1;
   int tail_cluster = 8;

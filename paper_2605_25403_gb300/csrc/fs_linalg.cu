@@ -56,7 +56,7 @@ constexpr int kUSpmv = 6;
 // x 3 values in 3D), the longest work per thread, and the blocks scheduled
 // first start first instead of forming a tail.
 // ---------------------------------------------------------------------------
-template <typename T, typename V, int DIM>
+template <typename T, typename V, int DIM, int kUS>
 __global__ void __launch_bounds__(256) k_spmv_full(DOp<T> op, JVec<const V> xv,
                                                    const V* __restrict__ b, JVec<V> yv,
                                                    int resid, const int* skip) {
@@ -66,9 +66,6 @@ __global__ void __launch_bounds__(256) k_spmv_full(DOp<T> op, JVec<const V> xv,
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t n2 = op.n2, nv = op.nv, wp = (nv + 31) & ~(int64_t)31;
   const V* __restrict__ xp = x + DIM * n2;
-  // slots per group: FP64 rows are partly bound by FP64 arithmetic and do
-  // best at the shallower depth
-  constexpr int kUS = std::is_same<V, float>::value ? kUSpmv : kU;
   if (t >= wp) {
     const int64_t row = t - wp;
     if (row >= n2) return;
@@ -233,7 +230,7 @@ __device__ __forceinline__ void vstore(T* __restrict__ p, const T (&v)[N]) {
 }
 
 // One row of a Chebyshev pass (thread per row on the SELL-32 operator).
-template <typename T, int NC, int NCP, int MODE>
+template <typename T, int NC, int NCP, int MODE, int G = kU>
 __device__ __forceinline__ void mg_row(const DSell<T>& A, const T* __restrict__ dinv,
                                        const T* __restrict__ b, const T* __restrict__ Gin,
                                        const T* __restrict__ Din, T* __restrict__ Gout,
@@ -245,21 +242,21 @@ __device__ __forceinline__ void mg_row(const DSell<T>& A, const T* __restrict__ 
 #pragma unroll
   for (int c = 0; c < NCP; ++c) acc[c] = T(0);
   // the slot count is the same for the whole slice: no divergence
-  for (int64_t o = o0; o < o1; o += kU * 32) {
-    T a[kU];
-    int32_t j[kU];
+  for (int64_t o = o0; o < o1; o += G * 32) {
+    T a[G];
+    int32_t j[G];
 #pragma unroll
-    for (int u = 0; u < kU; ++u) {
+    for (int u = 0; u < G; ++u) {
       const int64_t oo = o + u * 32;
       const bool ok = oo < o1;
       a[u] = ok ? A.v[oo] : T(0);
       j[u] = ok ? A.ci[oo] : (int32_t)row;
     }
-    T g[kU][NCP];
+    T g[G][NCP];
 #pragma unroll
-    for (int u = 0; u < kU; ++u) vload<T, NCP>(Gin + (int64_t)j[u] * NCP, g[u]);
+    for (int u = 0; u < G; ++u) vload<T, NCP>(Gin + (int64_t)j[u] * NCP, g[u]);
 #pragma unroll
-    for (int u = 0; u < kU; ++u)
+    for (int u = 0; u < G; ++u)
 #pragma unroll
       for (int c = 0; c < NC; ++c) acc[c] += a[u] * g[u][c];
   }
@@ -393,7 +390,7 @@ __device__ __forceinline__ void dense_row(const DHier<T>& H, const T* __restrict
   }
 }
 
-template <typename T, int NC, int NCP, int MODE>
+template <typename T, int NC, int NCP, int MODE, int G>
 __global__ void __launch_bounds__(256) k_mg(DSell<T> A, const T* __restrict__ dinv,
                                             const T* __restrict__ b,
                                             const T* __restrict__ Gin,
@@ -405,7 +402,7 @@ __global__ void __launch_bounds__(256) k_mg(DSell<T> A, const T* __restrict__ di
   if (skip && *skip) return;
   const int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (row >= A.nrow) return;
-  mg_row<T, NC, NCP, MODE>(A, dinv, b, Gin, Din, Gout, Dout, alpha, beta, inv_theta,
+  mg_row<T, NC, NCP, MODE, G>(A, dinv, b, Gin, Din, Gout, Dout, alpha, beta, inv_theta,
                                   MODE == MG_LAST ? outv.get() : nullptr, out_ld, perm, nc, row);
 }
 
@@ -536,17 +533,24 @@ __global__ void __launch_bounds__(NT, 1) k_mg_tail(const DHier<T>* __restrict__ 
 template <typename T, int NCP>
 void launch_mg(int mode, const DLevel<T>& L, const T* b, const T* Gin, const T* Din, T* Gout,
                T* Dout, T alpha, T beta, JVec<T> out, int64_t out_ld, const int32_t* perm, int nc,
-               const int* skip, cudaStream_t s) {
+               const int* skip, int group, cudaStream_t s) {
   const int64_t n = L.A.nrow;
   const T it = (T)L.inv_theta;
   constexpr int NC = NCP == 4 ? 3 : NCP;  // real components (3D pads 3 to 4)
-#define FS_MG(M)                                                                        \
-  k_mg<T, NC, NCP, M><<<blocks_for(n), 256, 0, s>>>(L.A, L.dinv, b, Gin, Din, Gout, Dout, \
-                                                    alpha, beta, it, out, out_ld, perm, nc, skip)
-  if (mode == MG_STEP) FS_MG(MG_STEP);
-  else if (mode == MG_RESID) FS_MG(MG_RESID);
-  else if (mode == MG_START) FS_MG(MG_START);
-  else FS_MG(MG_LAST);
+#define FS_MG(M, G)                                                                        \
+  k_mg<T, NC, NCP, M, G><<<blocks_for(n), 256, 0, s>>>(L.A, L.dinv, b, Gin, Din, Gout, Dout, \
+                                                       alpha, beta, it, out, out_ld, perm, nc, skip)
+  if (group == 6) {
+    if (mode == MG_STEP) FS_MG(MG_STEP, 6);
+    else if (mode == MG_RESID) FS_MG(MG_RESID, 6);
+    else if (mode == MG_START) FS_MG(MG_START, 6);
+    else FS_MG(MG_LAST, 6);
+  } else {
+    if (mode == MG_STEP) FS_MG(MG_STEP, 4);
+    else if (mode == MG_RESID) FS_MG(MG_RESID, 4);
+    else if (mode == MG_START) FS_MG(MG_START, 4);
+    else FS_MG(MG_LAST, 4);
+  }
 #undef FS_MG
   count_launches(1);
 }
@@ -599,11 +603,13 @@ void vcycle_level(const DHier<T>& H, int l, JVec<T> out, int64_t out_ld, int nc,
   const T a1 = (T)L.a1, b1 = (T)L.b1, a2 = (T)L.a2, b2 = (T)L.b2;
   T *G0 = H.G0[l], *G1 = H.G1[l], *D0 = H.D0[l], *D1 = H.D1[l];
   const T* b = H.b[l];
-  launch_mg<T, NCP>(MG_STEP, L, b, G0, D0, G1, D1, a1, b1, JVec<T>(), 0, nullptr, nc, skip, s);
-  launch_mg<T, NCP>(MG_STEP, L, b, G1, D1, G0, D0, a2, b2, JVec<T>(), 0, nullptr, nc, skip, s);
+  launch_mg<T, NCP>(MG_STEP, L, b, G0, D0, G1, D1, a1, b1, JVec<T>(), 0, nullptr, nc, skip,
+                    H.group, s);
+  launch_mg<T, NCP>(MG_STEP, L, b, G1, D1, G0, D0, a2, b2, JVec<T>(), 0, nullptr, nc, skip,
+                    H.group, s);
   // residual of x3 = G0 into G1; G0 keeps x3 for the correction
   launch_mg<T, NCP>(MG_RESID, L, b, G0, D0, G1, nullptr, T(0), T(0), JVec<T>(), 0, nullptr, nc,
-                    skip, s);
+                    skip, H.group, s);
   const bool coarsest_next = l + 1 == H.nlev - 1;
   k_mg_restrict<T, NCP, 4><<<blocks_for(L.R.nrow * 4), 256, 0, s>>>(
       L.R, G1, H.b[l + 1], H.G0[l + 1], H.D0[l + 1], coarsest_next ? nullptr : C.dinv,
@@ -613,10 +619,12 @@ void vcycle_level(const DHier<T>& H, int l, JVec<T> out, int64_t out_ld, int nc,
   k_mg_prolong<T, NCP, 4><<<blocks_for(L.P.nrow * 4), 256, 0, s>>>(L.P, H.G1[l + 1], G0, skip);
   count_launches(1);
   launch_mg<T, NCP>(MG_START, L, b, G0, nullptr, G1, D1, T(0), T(0), JVec<T>(), 0, nullptr, nc,
-                    skip, s);
-  launch_mg<T, NCP>(MG_STEP, L, b, G1, D1, G0, D0, a1, b1, JVec<T>(), 0, nullptr, nc, skip, s);
+                    skip, H.group, s);
+  launch_mg<T, NCP>(MG_STEP, L, b, G1, D1, G0, D0, a1, b1, JVec<T>(), 0, nullptr, nc, skip,
+                    H.group, s);
   launch_mg<T, NCP>(MG_LAST, L, b, G0, D0, G1, nullptr, a2, b2, top ? out : JVec<T>(), out_ld,
-                    top ? H.perm : nullptr, nc, skip, s);
+                    top ? H.perm : nullptr, nc, skip,
+                    H.group, s);
 }
 
 // Cluster size of the fused V-cycle tail: 16 blocks (one per SM) where the
@@ -749,10 +757,21 @@ template <typename T, typename V>
 void launch_spmv_full(const DOp<T>& op, JVec<const V> x, const V* b, JVec<V> y, int resid,
                       const int* skip, cudaStream_t s) {
   const int64_t threads = ((op.nv + 31) & ~(int64_t)31) + op.n2;
-  if (op.dim == 2)
-    k_spmv_full<T, V, 2><<<blocks_for(threads), 256, 0, s>>>(op, x, b, y, resid, skip);
-  else
-    k_spmv_full<T, V, 3><<<blocks_for(threads), 256, 0, s>>>(op, x, b, y, resid, skip);
+  // slots per group: the schedule's, else 6 in FP32 and 4 in FP64 (FP64
+  // rows are partly bound by FP64 arithmetic and do best shallower)
+  const int g = op.group ? op.group : (std::is_same<V, float>::value ? kUSpmv : kU);
+#define FS_SPMV(D, G) \
+  k_spmv_full<T, V, D, G><<<blocks_for(threads), 256, 0, s>>>(op, x, b, y, resid, skip)
+  if (op.dim == 2) {
+    if (g == 8) FS_SPMV(2, 8);
+    else if (g == 6) FS_SPMV(2, 6);
+    else FS_SPMV(2, 4);
+  } else {
+    if (g == 8) FS_SPMV(3, 8);
+    else if (g == 6) FS_SPMV(3, 6);
+    else FS_SPMV(3, 4);
+  }
+#undef FS_SPMV
   count_launches(1);
 }
 template void launch_spmv_full<double, double>(const DOp<double>&, JVec<const double>,
@@ -773,13 +792,13 @@ void launch_cheb_step(const DHier<T>& H, int nc, cudaStream_t s) {
   const DLevel<T>& L = H.lev[0];
   if (H.ncp == 4)
     launch_mg<T, 4>(MG_STEP, L, H.b[0], H.G0[0], H.D0[0], H.G1[0], H.D1[0], (T)L.a1, (T)L.b1,
-                    nullptr, 0, nullptr, 3, nullptr, s);
+                    nullptr, 0, nullptr, 3, nullptr, H.group, s);
   else if (H.ncp == 2)
     launch_mg<T, 2>(MG_STEP, L, H.b[0], H.G0[0], H.D0[0], H.G1[0], H.D1[0], (T)L.a1, (T)L.b1,
-                    nullptr, 0, nullptr, 2, nullptr, s);
+                    nullptr, 0, nullptr, 2, nullptr, H.group, s);
   else
     launch_mg<T, 1>(MG_STEP, L, H.b[0], H.G0[0], H.D0[0], H.G1[0], H.D1[0], (T)L.a1, (T)L.b1,
-                    nullptr, 0, nullptr, 1, nullptr, s);
+                    nullptr, 0, nullptr, 1, nullptr, H.group, s);
 }
 template <typename T>
 int mg_tail_cluster(int ncp) {

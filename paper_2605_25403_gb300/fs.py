@@ -106,18 +106,21 @@ class fs_server_desc(ctypes.Structure):
 
 
 class fs_schedule(ctypes.Structure):
-    _fields_ = [("tail_rows_velocity", _i64), ("tail_rows_pressure", _i64)]
+    _fields_ = [("tail_rows_velocity", _i64), ("tail_rows_pressure", _i64),
+                ("spmv_group", _int), ("smooth_group", _int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class fs_tune_report(ctypes.Structure):
-    _fields_ = [("candidates", _int), ("default_ms", _d), ("best_ms", _d), ("best", fs_schedule)]
+    _fields_ = [("candidates", _int), ("default_ms", _d), ("best_ms", _d),
+                ("spmv_default_ms", _d), ("spmv_best_ms", _d), ("best", fs_schedule)]
 
     def as_dict(self):
         return {"candidates": self.candidates, "default_ms": self.default_ms,
-                "best_ms": self.best_ms, "best": self.best.as_dict()}
+                "best_ms": self.best_ms, "spmv_default_ms": self.spmv_default_ms,
+                "spmv_best_ms": self.spmv_best_ms, "best": self.best.as_dict()}
 
 
 class fs_request_result(ctypes.Structure):
@@ -425,8 +428,9 @@ def fs_get_schedule(prob):
     return sc.as_dict()
 
 
-def fs_set_schedule(prob, tail_rows_velocity, tail_rows_pressure):
-    sc = fs_schedule(int(tail_rows_velocity), int(tail_rows_pressure))
+def fs_set_schedule(prob, tail_rows_velocity, tail_rows_pressure, spmv_group=0, smooth_group=0):
+    sc = fs_schedule(int(tail_rows_velocity), int(tail_rows_pressure), int(spmv_group),
+                     int(smooth_group))
     _check(_lib.fs_set_schedule(prob, ctypes.byref(sc)), "fs_set_schedule")
 
 

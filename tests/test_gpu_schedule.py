@@ -1,9 +1,10 @@
 """Execution schedules of the multigrid preconditioner.
 
-The coarse levels can run as separate kernels or inside one cluster kernel
-(fs_set_schedule); both forms evaluate the same per-row formulas, so a
-schedule changes launch counts and timing, not the solution: the
-preconditioner outputs differ at most by rounding (FMA contraction may differ
+The coarse levels can run as separate kernels or inside one cluster kernel,
+and the SpMV and smoothing passes can issue 4, 6 or 8 matrix slots per
+thread at a time (fs_set_schedule).  Every form evaluates the same per-row
+formulas, so a schedule changes launch counts and timing, not the solution:
+the preconditioner outputs differ at most by rounding (FMA contraction may differ
 between the two compiled forms), and the two solves then stop at different
 iterates that both meet rtol = 1e-14, so the step results agree to the
 conditioning times rtol.  Bars: FP64 1e-11 (the preconditioner differs by
@@ -22,7 +23,9 @@ from tests.gpu_helpers import rel_l2
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-SCHEDULES = [(0, 0), (65536, 65536), (4096, 16384), (16384, 0)]
+# (tail rows velocity, tail rows pressure, SpMV group, smoothing group)
+SCHEDULES = [(0, 0, 0, 0), (65536, 65536, 8, 6), (4096, 16384, 4, 4), (16384, 0, 6, 6)]
+KEYS = ("tail_rows_velocity", "tail_rows_pressure", "spmv_group", "smooth_group")
 
 
 @pytest.fixture(scope="module")
@@ -39,8 +42,7 @@ def _run(fs, make, sched, prec, nsteps=2):
     S = make(prec)
     try:
         fs.fs_set_schedule(S.prob, *sched)
-        assert fs.fs_get_schedule(S.prob) == {"tail_rows_velocity": sched[0],
-                                              "tail_rows_pressure": sched[1]}
+        assert fs.fs_get_schedule(S.prob) == dict(zip(KEYS, sched))
         st = fs.fs_step(S.prob, nsteps)
         assert all(s["status"] == 0 for s in st)
         return S.state()[0]
@@ -76,6 +78,7 @@ def test_autotune_installs_a_candidate(fs):
         x0, t0 = S.state()
         rep = fs.fs_autotune(S.prob, reps=3)
         assert rep["candidates"] >= 2 and 0 < rep["best_ms"] <= rep["default_ms"]
+        assert 0 < rep["spmv_best_ms"] <= rep["spmv_default_ms"]
         assert fs.fs_get_schedule(S.prob) == rep["best"]
         x1, t1 = S.state()
         assert t1 == t0 and np.array_equal(x0, x1)  # state untouched
@@ -85,5 +88,9 @@ def test_autotune_installs_a_candidate(fs):
         assert ms > 0
         with pytest.raises(fs.FsError):
             fs.fs_set_schedule(S.prob, -1, 0)
+        with pytest.raises(fs.FsError):
+            fs.fs_set_schedule(S.prob, 0, 0, spmv_group=5)
+        with pytest.raises(fs.FsError):
+            fs.fs_set_schedule(S.prob, 0, 0, smooth_group=8)
     finally:
         S.close()
