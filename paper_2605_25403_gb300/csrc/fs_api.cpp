@@ -20,6 +20,7 @@
 #include <memory>
 #include <mutex>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "fs_device.h"
@@ -317,6 +318,75 @@ void cheb_coeffs(double lmax, DLevel<T>& L) {
   L.b2 = 2.0 * rho2 / delta;
 }
 
+// Inverse of a coarsest operator too large for the host (set-up only):
+// Gauss-Jordan with partial pivoting on the device in FP64, in temporary
+// device memory; the result, in the solver's precision, goes to *out.  It
+// is accepted only if A times it is the identity to within the solver
+// precision's rounding on four sampled columns.
+template <typename T>
+int invert_on_device(fs_problem* P, const HostCsr& A, T** out) {
+  const int64_t n = A.nrow;
+  if (n < 1 || n > 65535) {
+    set_error("coarsest operator of unsupported size for the device inverse");
+    return FS_ERR_UNSUPPORTED;
+  }
+  cudaStream_t s = P->stream;
+  std::vector<double> W((size_t)(n * 2 * n), 0.0);
+  for (int64_t r = 0; r < n; ++r) {
+    for (int32_t k = A.rowptr[r]; k < A.rowptr[r + 1]; ++k) W[r * 2 * n + A.col[k]] += A.val[k];
+    W[r * 2 * n + n + r] = 1.0;
+  }
+  double *dW = nullptr, *pval = nullptr;
+  int64_t* piv = nullptr;
+  int* bad = nullptr;
+  auto release = [&]() {
+    for (void* q : {(void*)dW, (void*)pval, (void*)piv, (void*)bad})
+      if (q) cudaFreeAsync(q, s);
+    cudaStreamSynchronize(s);
+  };
+  cudaError_t e = cudaMallocAsync((void**)&dW, sizeof(double) * W.size(), s);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&pval, sizeof(double), s);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&piv, sizeof(int64_t), s);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&bad, sizeof(int), s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dW, W.data(), sizeof(double) * W.size(),
+                                            cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(bad, 0, sizeof(int), s);
+  if (e != cudaSuccess) {
+    release();
+    set_error(std::string("device inverse: ") + cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? FS_ERR_OOM : FS_ERR_CUDA;
+  }
+  for (int64_t c = 0; c < n; ++c) launch_gj_step(dW, n, c, piv, pval, bad, s);
+  int rc = P->alloc(out, n * n);
+  if (rc == FS_OK) launch_gj_extract<T>(dW, n, *out, s);
+  int hbad = 0;
+  std::vector<T> inv;
+  if (rc == FS_OK) {
+    inv.resize((size_t)(n * n));
+    cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(inv.data(), *out, sizeof(T) * inv.size(), cudaMemcpyDeviceToHost, s);
+  }
+  release();
+  if (rc != FS_OK) return rc;
+  FS_TRY(check_launch("device inverse"));
+  double err = hbad ? INFINITY : 0.0;
+  for (int64_t k : {(int64_t)0, n / 3, (2 * n) / 3, n - 1}) {
+    for (int64_t r = 0; r < n && std::isfinite(err); ++r) {
+      double y = 0;
+      for (int32_t q = A.rowptr[r]; q < A.rowptr[r + 1]; ++q)
+        y += A.val[q] * (double)inv[(size_t)(A.col[q] * n + k)];
+      err = std::max(err, std::fabs(y - (r == k ? 1.0 : 0.0)));
+    }
+  }
+  const double tol = std::is_same<T, float>::value ? 1e-2 : 1e-8;
+  if (!(err <= tol)) {
+    set_error("device inverse of the coarsest operator failed its check (singular or "
+              "too badly conditioned)");
+    return FS_ERR_NUMERIC;
+  }
+  return FS_OK;
+}
+
 template <typename T>
 int upload_hierarchy(fs_problem* P, const UnionHierarchy& U, int nc, DHier<T>& D) {
   const HostHierarchy& H = U.H;
@@ -346,9 +416,13 @@ int upload_hierarchy(fs_problem* P, const UnionHierarchy& U, int nc, DHier<T>& D
       FS_CUDA(cudaMemsetAsync(*v, 0, sizeof(T) * D.ncp * rows, P->stream));
     }
   }
-  std::vector<T> ci(U.dense.begin(), U.dense.end());
   T* cinv;
-  FS_TRY(P->upload(&cinv, ci));
+  if (!U.dense.empty()) {
+    std::vector<T> ci(U.dense.begin(), U.dense.end());
+    FS_TRY(P->upload(&cinv, ci));
+  } else {
+    FS_TRY(invert_on_device<T>(P, U.H.levels.back().A, &cinv));
+  }
   D.cinv = cinv;
   int32_t* rb;
   int64_t *br, *bn, *bd;
@@ -1312,7 +1386,13 @@ int fs_problem_create_batch(fs_mesh* mesh, const fs_problem_desc* descs, int cou
   std::vector<double> mplinv_nu(P->nv);
   for (int64_t q = 0; q < P->nv; ++q) mplinv_nu[q] = nu_vert[q] / mplh[q];
   UnionHierarchy HA, HK;
-  const int64_t cmax = count > 1 ? 400 : 800;
+  // coarsest size.  Large single problems stop coarsening at 3500 rows: the
+  // dense inverse (on the device, ~0.1 s of set-up) then replaces the one or
+  // two latency-bound coarsest levels of each V-cycle with one dense matvec.
+  // Small problems would pay that inversion in their set-up latency (the
+  // serving loop creates many), so they keep 800 rows; batches keep small
+  // per-instance blocks.
+  const int64_t cmax = count > 1 ? 400 : me.n2 >= 100000 ? 3500 : 800;
   build_union_hierarchy(me, {}, A0, true, me.dlist, cmax, HA);
   build_union_hierarchy(me, {}, Kp, false, kfix, cmax, HK);
 

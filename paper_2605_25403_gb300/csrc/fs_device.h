@@ -184,6 +184,17 @@ struct DHier {
   const DHier<T>* dev = nullptr;
 };
 
+// Gauss-Jordan inversion with partial pivoting of a dense n x n FP64
+// matrix, held row-major as the augmented n x 2n array W = [A | I]; after
+// the n pivot steps the right half holds A^-1 (the left half is not kept
+// up to date).  piv, pval: device scratch for the pivot row and value; bad:
+// device flag set when a pivot column is zero.  Set-up only.
+void launch_gj_step(double* W, int64_t n, int64_t c, int64_t* piv, double* pval, int* bad,
+                    cudaStream_t s);
+// out (n x n, row-major) = the right half of W, converted to T.
+template <typename T>
+void launch_gj_extract(const double* W, int64_t n, T* out, cudaStream_t s);
+
 // Cluster size (16 or 8 blocks) of the fused kernel for this arithmetic and
 // row width.
 template <typename T>

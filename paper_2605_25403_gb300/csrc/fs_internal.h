@@ -102,6 +102,10 @@ struct HostLevel {
   int grid[3] = {1, 1, 1};  // structured mesh of the level (cells per axis)
   bool p2 = false;          // the level is the P2 space of that mesh
 };
+// Coarsest operators of at most this many rows are inverted on the host at
+// set-up; larger ones (single problems only) are inverted on the device.
+constexpr int64_t kHostInverseMax = 800;
+
 struct HostHierarchy {
   std::vector<HostLevel> levels;   // levels[0] finest; last = coarsest
   std::vector<double> coarse_inv;  // dense inverse of the coarsest operator
@@ -130,7 +134,10 @@ struct UnionHierarchy {
   std::vector<int64_t> blk_row;      // coarsest level: row offset per instance
   std::vector<int64_t> blk_n;        // ... block size per instance
   std::vector<int64_t> blk_dense;    // ... offset of its dense inverse
-  std::vector<double> dense;         // concatenated dense inverses (row-major)
+  std::vector<double> dense;         // concatenated dense inverses (row-major);
+                                     // empty: invert the coarsest level's A
+                                     // on the device (one block above
+                                     // kHostInverseMax rows)
   std::vector<int32_t> row_blk;      // coarsest row -> instance
   // level-0 rows are in instance-major (block) order, each instance's rows
   // in class order; perm[r] is the union row of block row r (empty when

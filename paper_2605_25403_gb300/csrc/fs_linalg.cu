@@ -358,7 +358,11 @@ __device__ __forceinline__ void prolong_row(const DCsr<T>& P, const T* __restric
 }
 
 // Coarsest-level row x = blockdiag(Cinv) b (a warp per row); the result goes
-// to X, or (level 0 being the coarsest) to the caller's blocked out.
+// to X, or (level 0 being the coarsest) to the caller's blocked out.  The row
+// of Cinv is read in 16-byte loads (a scalar head up to the first 16-byte
+// boundary and a scalar tail), eight per lane in flight: a 3,500-row block
+// has only ~23 rows per SM, so the loads of one warp must cover the memory
+// latency.  b is re-read by every row from L1/L2.
 template <typename T, int NCP>
 __device__ __forceinline__ void dense_row(const DHier<T>& H, const T* __restrict__ b,
                                           T* __restrict__ X, T* __restrict__ out,
@@ -371,13 +375,43 @@ __device__ __forceinline__ void dense_row(const DHier<T>& H, const T* __restrict
     const int blk = H.row_blk[row];
     const int64_t r0 = H.blk_row[blk], nb = H.blk_n[blk];
     const T* Cr = H.cinv + H.blk_dense[blk] + (row - r0) * nb;
-    for (int64_t j = lane; j < nb; j += 32) {
-      const T a = Cr[j];
+    const T* bb = b + r0 * NCP;
+    auto add = [&](T a, int64_t j) {
       T bj[NCP];
-      vload<T, NCP>(b + (r0 + j) * NCP, bj);
+      vload<T, NCP>(bb + j * NCP, bj);
 #pragma unroll
       for (int c = 0; c < NCP; ++c) acc[c] += a * bj[c];
+    };
+    using V = typename std::conditional<std::is_same<T, float>::value, float4, double2>::type;
+    constexpr int E = 16 / sizeof(T);
+    int64_t h = (int64_t)(((16 - ((uintptr_t)Cr & 15)) & 15) / sizeof(T));
+    if (h > nb) h = nb;
+    if (lane < h) add(Cr[lane], lane);
+    const int64_t nvec = (nb - h) / E;
+    const V* Cv = reinterpret_cast<const V*>(Cr + h);
+    constexpr int U = 8;  // 16-byte loads per lane issued together
+    for (int64_t v0 = lane; v0 < nvec; v0 += 32 * U) {
+      V q[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (v0 + 32 * u < nvec) q[u] = Cv[v0 + 32 * u];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (v0 + 32 * u >= nvec) break;
+        const int64_t j = h + (v0 + 32 * u) * E;
+        if constexpr (E == 4) {
+          add(q[u].x, j);
+          add(q[u].y, j + 1);
+          add(q[u].z, j + 2);
+          add(q[u].w, j + 3);
+        } else {
+          add(q[u].x, j);
+          add(q[u].y, j + 1);
+        }
+      }
     }
+    const int64_t t0 = h + nvec * E;  // fewer than E entries remain
+    if (t0 + lane < nb) add(Cr[t0 + lane], t0 + lane);
   }
 #pragma unroll
   for (int c = 0; c < NCP; ++c) acc[c] = group_sum<32>(acc[c]);
@@ -735,6 +769,69 @@ __global__ void __launch_bounds__(256) k_bt_add_mg(DSell<T> BT, int64_t n2, JVec
   vstore<T, NCP>(D0 + dst * NCP, d0);
 }
 
+// Gauss-Jordan step c on W = [A | I] (n x 2n, row-major).  The pivot is the
+// largest |W[r][c]| over r >= c (one block); the pivot row is swapped into
+// row c and scaled by 1 / pivot; every other row r then subtracts
+// W[r][c] times row c over the columns j > c.  Column c itself is left as it
+// is (later steps never read it), so no thread writes what another reads.
+__global__ void __launch_bounds__(1024) k_gj_pivot(const double* __restrict__ W, int64_t n,
+                                                   int64_t c, int64_t* piv, double* pval,
+                                                   int* bad) {
+  __shared__ double bv[1024];
+  __shared__ int64_t br[1024];
+  double best = -1.0;
+  int64_t arg = c;
+  for (int64_t r = c + threadIdx.x; r < n; r += blockDim.x) {
+    const double v = fabs(W[r * 2 * n + c]);
+    if (v > best) {
+      best = v;
+      arg = r;
+    }
+  }
+  bv[threadIdx.x] = best;
+  br[threadIdx.x] = arg;
+  __syncthreads();
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st && bv[threadIdx.x + st] > bv[threadIdx.x]) {
+      bv[threadIdx.x] = bv[threadIdx.x + st];
+      br[threadIdx.x] = br[threadIdx.x + st];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    *piv = br[0];
+    *pval = W[br[0] * 2 * n + c];
+    if (!(bv[0] > 0.0)) *bad = 1;
+  }
+}
+
+__global__ void k_gj_swap_scale(double* __restrict__ W, int64_t n, int64_t c,
+                                const int64_t* __restrict__ piv,
+                                const double* __restrict__ pval) {
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= 2 * n) return;
+  const int64_t p = *piv;
+  const double inv = 1.0 / *pval;
+  const double a = W[c * 2 * n + j], b = W[p * 2 * n + j];
+  W[c * 2 * n + j] = b * inv;
+  if (p != c) W[p * 2 * n + j] = a;
+}
+
+__global__ void k_gj_eliminate(double* __restrict__ W, int64_t n, int64_t c) {
+  const int64_t r = blockIdx.y;
+  const int64_t j = c + 1 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (r == c || j >= 2 * n) return;
+  const double f = W[r * 2 * n + c];
+  if (f != 0.0) W[r * 2 * n + j] -= f * W[c * 2 * n + j];
+}
+
+template <typename T>
+__global__ void k_gj_extract(const double* __restrict__ W, int64_t n, T* __restrict__ out) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n * n;
+       q += (int64_t)gridDim.x * blockDim.x)
+    out[q] = (T)W[(q / n) * 2 * n + n + q % n];
+}
+
 template <typename A, typename B>
 __global__ void k_convert(const A* __restrict__ in, B* __restrict__ out, int64_t n,
                           const double* scale, int inv) {
@@ -862,6 +959,23 @@ template void launch_precond<float>(const DOp<float>&, const DHier<float>&,
                                     const DHier<float>&, const float*, double,
                                     const int32_t*, int, JVec<const float>, JVec<float>, float*,
                                     float*, const int*, cudaStream_t);
+
+void launch_gj_step(double* W, int64_t n, int64_t c, int64_t* piv, double* pval, int* bad,
+                    cudaStream_t s) {
+  k_gj_pivot<<<1, 1024, 0, s>>>(W, n, c, piv, pval, bad);
+  k_gj_swap_scale<<<blocks_for(2 * n), 256, 0, s>>>(W, n, c, piv, pval);
+  const int64_t cols = 2 * n - c - 1;  // >= n >= 1
+  k_gj_eliminate<<<dim3(blocks_for(cols), (unsigned)n), 256, 0, s>>>(W, n, c);
+  count_launches(3);
+}
+
+template <typename T>
+void launch_gj_extract(const double* W, int64_t n, T* out, cudaStream_t s) {
+  k_gj_extract<T><<<grid_stride_blocks(n * n), 256, 0, s>>>(W, n, out);
+  count_launches(1);
+}
+template void launch_gj_extract<double>(const double*, int64_t, double*, cudaStream_t);
+template void launch_gj_extract<float>(const double*, int64_t, float*, cudaStream_t);
 
 template <typename A, typename B>
 void launch_convert(const A* in, B* out, int64_t n, const double* scale, int inv,

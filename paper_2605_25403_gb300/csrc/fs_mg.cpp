@@ -296,7 +296,7 @@ void class_order_hierarchy(const Mesh& m, HostHierarchy& H) {
     std::iota(id.begin(), id.end(), 0);
     L.P = permute(L.P, sg, id);
     L.R = permute(L.R, id, inv);
-  } else {
+  } else if (!H.coarse_inv.empty()) {
     const int64_t nc = H.ncoarse;
     std::vector<double> ci(nc * nc);
     for (int64_t r = 0; r < nc; ++r)
@@ -377,7 +377,9 @@ void build_hierarchy(const Mesh& m, const HostCsr& A0, bool p2_fine,
   }
   for (auto& L : H.levels) finish_level(L);
   H.ncoarse = H.levels.back().A.nrow;
-  if (!dense_inverse(H.levels.back().A, H.coarse_inv)) {
+  if (H.ncoarse > kHostInverseMax) {
+    H.coarse_inv.clear();  // inverted on the device after the upload
+  } else if (!dense_inverse(H.levels.back().A, H.coarse_inv)) {
     // singular coarsest operator: fall back to its Jacobi inverse
     H.coarse_inv.assign(H.ncoarse * H.ncoarse, 0.0);
     for (int64_t i = 0; i < H.ncoarse; ++i)
@@ -558,6 +560,14 @@ void build_union_hierarchy(const Mesh& m, const std::vector<Mesh>& /*local*/,
     U.blk_row[i] = row;
     U.blk_n[i] = H[i].ncoarse;
     U.blk_dense[i] = (int64_t)U.dense.size();
+    if (H[i].coarse_inv.empty() && K > 1 &&
+        !dense_inverse(H[i].levels.back().A, H[i].coarse_inv)) {
+      // (batches keep their coarsest blocks small; a large one is inverted
+      // here, singular ones fall back to Jacobi)
+      H[i].coarse_inv.assign(H[i].ncoarse * H[i].ncoarse, 0.0);
+      for (int64_t q = 0; q < H[i].ncoarse; ++q)
+        H[i].coarse_inv[q * H[i].ncoarse + q] = H[i].levels.back().dinv[q];
+    }
     U.dense.insert(U.dense.end(), H[i].coarse_inv.begin(), H[i].coarse_inv.end());
     for (int64_t r = 0; r < H[i].ncoarse; ++r) U.row_blk.push_back(i);
     row += H[i].ncoarse;
