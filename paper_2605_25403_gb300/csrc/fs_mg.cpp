@@ -2,8 +2,13 @@
 // preconditioner (not in the paper, which names no preconditioner; see the
 // Cahouet-Chabard reading in the design notes).  Prolongations are linear
 // interpolation in the index space of the structured simplicial meshes:
-// P1 on mesh n_{l+1} -> P1 on mesh n_l (nested when n_l is even), and, for
-// the velocity block, P1 -> P2 on the finest mesh.  Coarse operators are
+// P1 on mesh n_{l+1} -> P1 on mesh n_l with n_{l+1} = ceil(n_l / 4) cells
+// per axis (nested when 4 divides n_l), and, for the velocity block,
+// P1 -> P2 on the finest mesh.  Coarsening by 4 per axis halves the number
+// of levels against 2 (each level costs eight dependent passes of a V-cycle);
+// the Chebyshev(3) interval [lmax/8, 1.1 lmax] of the smoother reaches down
+// to the smallest eigenvalues (~0.15 lmax) of the modes a coarser grid of
+// 4h spacing cannot represent.  Coarse operators are
 // Galerkin products R A P with R = P^T.  The coarsest operator is inverted
 // densely.  Built once per problem; the values are FP64.
 #include <algorithm>
@@ -328,7 +333,7 @@ void build_hierarchy(const Mesh& m, const HostCsr& A0, bool p2_fine,
       int nn[3] = {ncur[0], ncur[1], ncur[2]};
       bool changed = false;
       for (int a = 0; a < dim; ++a) {
-        nn[a] = std::max(1, (ncur[a] + 1) / 2);
+        nn[a] = std::max(1, (ncur[a] + 3) / 4);
         changed = changed || nn[a] != ncur[a];
       }
       if (!changed) break;
