@@ -218,6 +218,11 @@ int fs_solve(fs_problem* prob, const fs_solve_opts* opts, double* x,
              fs_solve_stats* stats);
 
 /* nsteps backward-Euler Oseen steps: assemble (w = u^n), solve, t += dt.
+ * Each solve starts from 2 x^n - x^(n-1), the linear extrapolation in time
+ * of the two latest states (x^n on the first step after problem creation,
+ * fs_solve, or fs_set_state to a time other than the current one); the
+ * converged state does not depend on the starting point beyond the solver
+ * tolerance.
  * per_step (host, nsteps entries, may be NULL) receives each solve's stats.
  * Synchronises. */
 int fs_step(fs_problem* prob, int nsteps, const fs_solve_opts* opts,
@@ -242,7 +247,10 @@ int fs_instance_stats(const fs_problem* prob, fs_solve_stats* per_instance);
 int fs_apply_operator(fs_problem* prob, const double* x, double* y);
 
 /* State access: x (n_dof FP64) and the current time.  x_out/x_in are host
- * pointers when `host` is 1, device pointers otherwise.  Synchronises. */
+ * pointers when `host` is 1, device pointers otherwise.  Synchronises.
+ * fs_set_state at the problem's current time continues the stepped history
+ * (the initial guess of fs_step extrapolates from the previous state); at
+ * another time it starts a new history. */
 int fs_get_state(fs_problem* prob, double* x_out, int host, double* t_out);
 int fs_set_state(fs_problem* prob, const double* x_in, int host, double t);
 

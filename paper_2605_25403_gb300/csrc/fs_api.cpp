@@ -141,6 +141,11 @@ struct fs_problem {
   double *baseA = nullptr, *Mv = nullptr, *valA = nullptr, *B = nullptr, *BT = nullptr;
   double *Kp = nullptr, *mpl = nullptr, *diagp = nullptr;
   double *x = nullptr, *b = nullptr, *F = nullptr, *r64 = nullptr;
+  // the state before the latest step, for the initial guess of the next
+  // step's solve; hist = 0 while it is not valid (new problem, state set by
+  // the caller, or a direct solve)
+  double* xprev = nullptr;
+  int hist = 0;
   int32_t* pinned = nullptr;
   int npinned = 0;
   int64_t* mrp = nullptr;  // paper-order monolithic row pointers (export)
@@ -1398,6 +1403,7 @@ int fs_problem_create_batch(fs_mesh* mesh, const fs_problem_desc* descs, int cou
 
   // vectors, work-list
   FS_TRY(P->alloc(&P->x, P->ndof));
+  FS_TRY(P->alloc(&P->xprev, P->ndof));
   FS_TRY(P->alloc(&P->b, P->ndof));
   FS_TRY(P->alloc(&P->F, (int64_t)dim * P->n2));
   FS_TRY(P->alloc(&P->r64, P->ndof));
@@ -1504,6 +1510,7 @@ int fs_solve(fs_problem* P, const fs_solve_opts* opts, double* x, fs_solve_stats
     return FS_ERR_BUSY;
   }
   FS_TRY(solve_opts(opts, P->ctx.o));
+  P->hist = 0;  // the state no longer follows the stepped history
   if (x) {  // the caller's vector is in paper order
     FS_TRY(nat_buffers(P));
     launch_dofs_perm(P->dm, P->nat, x, P->natbuf, 0, P->stream);
@@ -1520,6 +1527,18 @@ int fs_solve(fs_problem* P, const fs_solve_opts* opts, double* x, fs_solve_stats
   return rc;
 }
 
+// Solve of the step whose system was just assembled (from the state x^n):
+// the Krylov solve starts from 2 x^n - x^(n-1), the linear extrapolation of
+// the two latest states (x^n itself on the first step of a history), whose
+// residual is O(dt^2) instead of O(dt).  The converged state does not depend
+// on the starting point beyond the solver tolerance.
+static int start_step_solve(fs_problem* P) {
+  launch_extrapolate(P->x, P->xprev, P->ndof, P->hist > 0, P->stream);
+  FS_TRY(check_launch("extrapolate"));
+  P->hist = 1;
+  return start_solve(P, P->x);
+}
+
 int fs_step_begin(fs_problem* P, int nsteps, const fs_solve_opts* opts) {
   if (!P || nsteps < 1) {
     set_error("fs_step_begin: bad argument");
@@ -1534,7 +1553,7 @@ int fs_step_begin(fs_problem* P, int nsteps, const fs_solve_opts* opts) {
   P->ctx.step_index = 0;
   P->ctx.per_step = nullptr;
   FS_TRY(assemble_impl(P, P->t + P->desc.dt));
-  return start_solve(P, P->x);
+  return start_step_solve(P);
 }
 
 int fs_step_poll(fs_problem* P, int wait, int* done) {
@@ -1563,7 +1582,7 @@ int fs_step_poll(fs_problem* P, int wait, int* done) {
         return rc;
       }
       FS_TRY(assemble_impl(P, P->t + P->desc.dt));
-      FS_TRY(start_solve(P, P->x));
+      FS_TRY(start_step_solve(P));
     }
     cudaError_t q = wait ? cudaEventSynchronize(P->ev) : cudaEventQuery(P->ev);
     if (q == cudaErrorNotReady) return FS_OK;
@@ -1654,6 +1673,9 @@ int fs_set_state(fs_problem* P, const double* x_in, int host, double t) {
     FS_TRY(check_launch("fs_set_state"));
   }
   FS_CUDA(cudaStreamSynchronize(P->stream));
+  // a state at the current time continues the history (e.g. a round trip
+  // through host memory); any other time starts a new one
+  if (t != P->t) P->hist = 0;
   P->t = t;
   return FS_OK;
 }

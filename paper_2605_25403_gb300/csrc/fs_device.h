@@ -205,6 +205,10 @@ int mg_tail_cluster(int ncp);
 template <typename T>
 void launch_cheb_step(const DHier<T>& H, int nc, cudaStream_t s);
 
+// x <- 2 x - xprev and xprev <- the old x (n entries); with have_prev = 0
+// only xprev <- x.
+void launch_extrapolate(double* x, double* xprev, int64_t n, int have_prev, cudaStream_t s);
+
 // Conversion out = (B)(in * scale) (scale = *scale or 1/*scale when inv).
 template <typename A, typename B>
 void launch_convert(const A* in, B* out, int64_t n, const double* scale,

@@ -832,6 +832,17 @@ __global__ void k_gj_extract(const double* __restrict__ W, int64_t n, T* __restr
     out[q] = (T)W[(q / n) * 2 * n + n + q % n];
 }
 
+// Initial guess of a step's solve by linear extrapolation in time.
+__global__ void k_extrapolate(double* __restrict__ x, double* __restrict__ xprev, int64_t n,
+                              int have_prev) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double a = x[i];
+    if (have_prev) x[i] = 2.0 * a - xprev[i];
+    xprev[i] = a;
+  }
+}
+
 template <typename A, typename B>
 __global__ void k_convert(const A* __restrict__ in, B* __restrict__ out, int64_t n,
                           const double* scale, int inv) {
@@ -976,6 +987,11 @@ void launch_gj_extract(const double* W, int64_t n, T* out, cudaStream_t s) {
 }
 template void launch_gj_extract<double>(const double*, int64_t, double*, cudaStream_t);
 template void launch_gj_extract<float>(const double*, int64_t, float*, cudaStream_t);
+
+void launch_extrapolate(double* x, double* xprev, int64_t n, int have_prev, cudaStream_t s) {
+  k_extrapolate<<<grid_stride_blocks(n), 256, 0, s>>>(x, xprev, n, have_prev);
+  count_launches(1);
+}
 
 template <typename A, typename B>
 void launch_convert(const A* in, B* out, int64_t n, const double* scale, int inv,
