@@ -334,7 +334,11 @@ def main():
         t64, st64 = time_steps(torch, fs, S64, stream, k64, flush)
         fp64 = {"steps_per_s": 1e3 * len(t64) / sum(t64),
                 "ms_per_step": sum(t64) / len(t64),
+                "step_ms_p50": float(np.percentile(t64, 50)),
+                "step_ms_max": float(max(t64)),
                 "iters_per_step": float(np.mean([s["iters"] for s in st64])),
+                "iters_max": int(max(s["iters"] for s in st64)),
+                "cycles_per_step": float(np.mean([s["cycles"] for s in st64])),
                 "rel_res_max": max(s["rel_res"] for s in st64), "schedule": tune64}
         S64.close()
 
@@ -368,29 +372,44 @@ def main():
     ms_per_step = 1e3 * total_s / args.steps
 
     # ---- end to end through the C ABI with host buffers --------------------
+    # a second problem of the same workload, schedule and warm-up, so that
+    # its steps cover the same window of the run as the device-timed ones
+    # (the solves' starting guesses extrapolate the state history, so later
+    # steps of a transient can be cheaper)
     ndof = S.info["n_dof"]
+    sched = fs.fs_get_schedule(S.prob)
+    SE = fs.Stepper.from_workload(wl, precision=prec, stream=stream.cuda_stream)
+    fs.fs_set_schedule(SE.prob, sched["tail_rows_velocity"], sched["tail_rows_pressure"],
+                       sched["spmv_group"], sched["smooth_group"])
+    for _ in range(max(0, args.warmup - 1)):
+        fs.fs_step(SE.prob, 1)
     xh = torch.empty(ndof, dtype=torch.float64).pin_memory()
     xn = xh.numpy()
-    x0, t0 = fs.fs_get_state(S.prob)
+    x0, t0 = fs.fs_get_state(SE.prob)
     xn[:] = x0
     tcur = t0
     e2e_ms = []
-    for k in range(max(2, args.steps // 2) + 1):
+    e2e_iters = []
+    # the first pass (the last warm-up step) is not timed: the timed passes
+    # are steps warmup+1 .. warmup+steps, as on the device-timed path
+    for k in range(args.steps + 1):
         with torch.cuda.stream(stream):
             flush.zero_()
         stream.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        fs.fs_set_state(S.prob, xn, tcur)                 # H2D of the step's input
-        fs.fs_step(S.prob, 1)
-        x_new, tcur = fs.fs_get_state(S.prob)            # D2H of the step's result
+        fs.fs_set_state(SE.prob, xn, tcur)                # H2D of the step's input
+        st = fs.fs_step(SE.prob, 1)[0]
+        x_new, tcur = fs.fs_get_state(SE.prob)           # D2H of the step's result
         e1.record(stream)
         e1.synchronize()
         xn[:] = x_new
         if k > 0:
             e2e_ms.append(e0.elapsed_time(e1))
+            e2e_iters.append(st["iters"])
     e2e_val = world * len(e2e_ms) / (sum(e2e_ms) / 1e3)
+    SE.close()
 
     # ---- roofline of the dominant kernel ----------------------------------
     kid = {"cheb": fs.FS_KERNEL_CHEB, "spmv": fs.FS_KERNEL_SPMV,
@@ -446,12 +465,14 @@ def main():
         "step_ms_p99": float(np.percentile(times, 99)),
         "iters_per_step": float(np.mean(iters)),
         "refinements_per_step": float(np.mean([s["refinements"] for s in stats])),
+        "cycles_per_step": float(np.mean([s["cycles"] for s in stats])),
         "rel_res_max": max(s["rel_res"] for s in stats),
         "fp64_path": fp64,
         "vs_fp64_path": (value / world) / fp64["steps_per_s"] if fp64 else None,
         "clocks": clocks,
         "e2e": {"value": e2e_val, "unit": "steps/s", "h2d_bytes_per_step": 8 * ndof,
                 "d2h_bytes_per_step": 8 * ndof},
+        "e2e_iters_per_step": float(np.mean(e2e_iters)),
         "gpu_launches": launches,
         "schedule": tune,
         "roofline": roofline,

@@ -218,11 +218,11 @@ int fs_solve(fs_problem* prob, const fs_solve_opts* opts, double* x,
              fs_solve_stats* stats);
 
 /* nsteps backward-Euler Oseen steps: assemble (w = u^n), solve, t += dt.
- * Each solve starts from 2 x^n - x^(n-1), the linear extrapolation in time
- * of the two latest states (x^n on the first step after problem creation,
- * fs_solve, or fs_set_state to a time other than the current one); the
- * converged state does not depend on the starting point beyond the solver
- * tolerance.
+ * Each solve starts from the extrapolation in time of the latest states:
+ * 3 x^n - 3 x^(n-1) + x^(n-2), or 2 x^n - x^(n-1) and x^n while fewer
+ * previous states are known (after problem creation, fs_solve, or
+ * fs_set_state to a time other than the current one); the converged state
+ * does not depend on the starting point beyond the solver tolerance.
  * per_step (host, nsteps entries, may be NULL) receives each solve's stats.
  * Synchronises. */
 int fs_step(fs_problem* prob, int nsteps, const fs_solve_opts* opts,

@@ -141,11 +141,12 @@ struct fs_problem {
   double *baseA = nullptr, *Mv = nullptr, *valA = nullptr, *B = nullptr, *BT = nullptr;
   double *Kp = nullptr, *mpl = nullptr, *diagp = nullptr;
   double *x = nullptr, *b = nullptr, *F = nullptr, *r64 = nullptr;
-  // the state before the latest step, for the initial guess of the next
-  // step's solve; hist = 0 while it is not valid (new problem, state set by
-  // the caller, or a direct solve)
-  double* xprev = nullptr;
-  int hist = 0;
+  // the states before the latest step, x^(n-1-j) in hist_buf[(hist_head - j)
+  // mod kExtrapMax] for j < hist, for the initial guess of the next step's
+  // solve; hist = how many are valid (0 after problem creation, a state set
+  // by the caller at another time, or a direct solve)
+  double* hist_buf[kExtrapMax] = {};
+  int hist = 0, hist_head = 0;
   int32_t* pinned = nullptr;
   int npinned = 0;
   int64_t* mrp = nullptr;  // paper-order monolithic row pointers (export)
@@ -1403,7 +1404,7 @@ int fs_problem_create_batch(fs_mesh* mesh, const fs_problem_desc* descs, int cou
 
   // vectors, work-list
   FS_TRY(P->alloc(&P->x, P->ndof));
-  FS_TRY(P->alloc(&P->xprev, P->ndof));
+  for (double*& h : P->hist_buf) FS_TRY(P->alloc(&h, P->ndof));
   FS_TRY(P->alloc(&P->b, P->ndof));
   FS_TRY(P->alloc(&P->F, (int64_t)dim * P->n2));
   FS_TRY(P->alloc(&P->r64, P->ndof));
@@ -1528,14 +1529,21 @@ int fs_solve(fs_problem* P, const fs_solve_opts* opts, double* x, fs_solve_stats
 }
 
 // Solve of the step whose system was just assembled (from the state x^n):
-// the Krylov solve starts from 2 x^n - x^(n-1), the linear extrapolation of
-// the two latest states (x^n itself on the first step of a history), whose
-// residual is O(dt^2) instead of O(dt).  The converged state does not depend
-// on the starting point beyond the solver tolerance.
+// the Krylov solve starts from the polynomial extrapolation in time through
+// x^n and the hist previous states (order hist <= kExtrapMax; x^n itself on
+// the first step of a history), whose residual is O(dt^(hist+1)) instead of
+// the O(dt) of x^n.  The converged state does not depend on the starting
+// point beyond the solver tolerance.  x^n goes to the ring slot after the
+// newest one (the oldest, read first by the same thread).
 static int start_step_solve(fs_problem* P) {
-  launch_extrapolate(P->x, P->xprev, P->ndof, P->hist > 0, P->stream);
+  const double* prev[kExtrapMax] = {};
+  for (int j = 0; j < P->hist; ++j)
+    prev[j] = P->hist_buf[(P->hist_head - j + kExtrapMax) % kExtrapMax];
+  const int next = (P->hist_head + 1) % kExtrapMax;
+  launch_extrapolate(P->x, prev, P->hist, P->hist_buf[next], P->ndof, P->stream);
   FS_TRY(check_launch("extrapolate"));
-  P->hist = 1;
+  P->hist_head = next;
+  P->hist = P->hist < kExtrapMax ? P->hist + 1 : kExtrapMax;
   return start_solve(P, P->x);
 }
 

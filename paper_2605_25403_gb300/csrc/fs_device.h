@@ -205,9 +205,15 @@ int mg_tail_cluster(int ncp);
 template <typename T>
 void launch_cheb_step(const DHier<T>& H, int nc, cudaStream_t s);
 
-// x <- 2 x - xprev and xprev <- the old x (n entries); with have_prev = 0
-// only xprev <- x.
-void launch_extrapolate(double* x, double* xprev, int64_t n, int have_prev, cudaStream_t s);
+// Previous states kept for the initial guess of a step's solve.
+constexpr int kExtrapMax = 4;
+// Polynomial extrapolation in time of the state x (x^n) through it and its
+// nprev <= kExtrapMax previous values prev[j] = x^(n-1-j) to the next time
+// level: x <- sum_j (-1)^j C(nprev+1, j+1) x^(n-j) over j = 0..nprev (x
+// itself for nprev = 0); the old x goes to dst, which may be prev[nprev-1]
+// (each entry is read before it is written).  n entries each.
+void launch_extrapolate(double* x, const double* const* prev, int nprev, double* dst, int64_t n,
+                        cudaStream_t s);
 
 // Conversion out = (B)(in * scale) (scale = *scale or 1/*scale when inv).
 template <typename A, typename B>

@@ -832,14 +832,22 @@ __global__ void k_gj_extract(const double* __restrict__ W, int64_t n, T* __restr
     out[q] = (T)W[(q / n) * 2 * n + n + q % n];
 }
 
-// Initial guess of a step's solve by linear extrapolation in time.
-__global__ void k_extrapolate(double* __restrict__ x, double* __restrict__ xprev, int64_t n,
-                              int have_prev) {
+// Initial guess of a step's solve by extrapolation in time.
+// x^(n+1) guess = sum_j c[j] x^(n-j): c[0] for x itself, c[j + 1] for p[j].
+struct Extrap {
+  const double* p[kExtrapMax];
+  double c[kExtrapMax + 1];
+};
+__global__ void k_extrapolate(double* x, Extrap e, int nprev, double* dst, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const double a = x[i];
-    if (have_prev) x[i] = 2.0 * a - xprev[i];
-    xprev[i] = a;
+    double g = e.c[0] * a;
+#pragma unroll
+    for (int j = 0; j < kExtrapMax; ++j)
+      if (j < nprev) g += e.c[j + 1] * e.p[j][i];
+    dst[i] = a;
+    x[i] = g;
   }
 }
 
@@ -988,8 +996,18 @@ void launch_gj_extract(const double* W, int64_t n, T* out, cudaStream_t s) {
 template void launch_gj_extract<double>(const double*, int64_t, double*, cudaStream_t);
 template void launch_gj_extract<float>(const double*, int64_t, float*, cudaStream_t);
 
-void launch_extrapolate(double* x, double* xprev, int64_t n, int have_prev, cudaStream_t s) {
-  k_extrapolate<<<grid_stride_blocks(n), 256, 0, s>>>(x, xprev, n, have_prev);
+void launch_extrapolate(double* x, const double* const* prev, int nprev, double* dst, int64_t n,
+                        cudaStream_t s) {
+  // Lagrange extrapolation to the next level of equally spaced levels:
+  // (-1)^j C(nprev+1, j+1) for x^(n-j), j = 0..nprev
+  Extrap e{};
+  double binom = 1.0;  // C(nprev+1, j+1), built up over j
+  for (int j = 0; j <= nprev; ++j) {
+    binom = binom * (nprev + 1 - j) / (j + 1);
+    e.c[j] = (j % 2 ? -1.0 : 1.0) * binom;
+    if (j < nprev) e.p[j] = prev[j];
+  }
+  k_extrapolate<<<grid_stride_blocks(n), 256, 0, s>>>(x, e, nprev, dst, n);
   count_launches(1);
 }
 
