@@ -22,8 +22,10 @@ namespace fs {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kKB = 256;                 // threads per tile block
-constexpr int kKEPT = kTileLen / kKB;    // elements per thread
+// threads per tile block: the orthogonalisation passes stream the basis
+// with few blocks (one per tile), so each block brings many warps, and each
+// thread issues several independent loads, to keep enough bytes in flight
+constexpr int kKB = 512;
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -174,10 +176,10 @@ __device__ __forceinline__ void tile_dots(const V* __restrict__ Vb, int64_t n, c
     V acc = V(0);
     if (v < nvec) {
       const V* __restrict__ vv = Vb + (int64_t)v * n + t.start;
-#pragma unroll 4
+#pragma unroll 8
       for (int e = e0 + lane; e < e1; e += 32) acc += vv[e] * ws[e];
     } else {
-#pragma unroll 4
+#pragma unroll 8
       for (int e = e0 + lane; e < e1; e += 32) acc += ws[e] * ws[e];
     }
     const double sv = warp_sum((double)acc);
@@ -185,18 +187,27 @@ __device__ __forceinline__ void tile_dots(const V* __restrict__ Vb, int64_t n, c
   }
 }
 
-// w_e - sum_v coef[v] V[v]_e for the tile's elements (thread per element).
+// w_e - sum_v coef[v] V[v]_e for the tile's elements (thread per element;
+// the basis vectors are loaded eight at a time into separate sums).
 template <typename V>
 __device__ __forceinline__ V tile_update(const V* __restrict__ Vb, int64_t n, int64_t i,
                                          const V* coef, int nvec, V wi) {
-  V u0 = V(0), u1 = V(0);
+  constexpr int U = 8;
+  V u[U];
+#pragma unroll
+  for (int k = 0; k < U; ++k) u[k] = V(0);
   int v = 0;
-  for (; v + 1 < nvec; v += 2) {
-    u0 += coef[v] * Vb[(int64_t)v * n + i];
-    u1 += coef[v + 1] * Vb[(int64_t)(v + 1) * n + i];
+  for (; v + U <= nvec; v += U) {
+#pragma unroll
+    for (int k = 0; k < U; ++k) u[k] += coef[v + k] * Vb[(int64_t)(v + k) * n + i];
   }
-  if (v < nvec) u0 += coef[v] * Vb[(int64_t)v * n + i];
-  return wi - (u0 + u1);
+#pragma unroll
+  for (int k = 0; k < U; ++k)
+    if (v + k < nvec) u[k] += coef[v + k] * Vb[(int64_t)(v + k) * n + i];
+  V sum = V(0);
+#pragma unroll
+  for (int k = 0; k < U; ++k) sum += u[k];
+  return wi - sum;
 }
 
 template <typename V>
