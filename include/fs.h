@@ -383,10 +383,14 @@ enum {
   FS_KERNEL_SPMV_FP64 = 1,      /* saddle-point SpMV, FP64                   */
   FS_KERNEL_CHEB = 2,           /* fused Chebyshev step, finest P2 level     */
   FS_KERNEL_ASSEMBLE_CONV = 3,  /* per-step convection assembly (FP64)       */
-  FS_KERNEL_PRECOND = 4         /* one block-preconditioner application in
+  FS_KERNEL_PRECOND = 4,        /* one block-preconditioner application in
                                    the solver arithmetic, timed as a CUDA
                                    graph of `reps` applications; alg_bytes
                                    is 0 (a latency unit of many kernels)   */
+  FS_KERNEL_CGS = 5             /* one CGS2 orthogonalisation (its three
+                                   passes) at Arnoldi step j = m/2 on the
+                                   Krylov scratch; alg_bytes counts the
+                                   4j + 9 basis-vector sweeps              */
 };
 int64_t fs_launch_count(void);
 int fs_profile_kernel(fs_problem* prob, int kernel, int reps, double* avg_ms,

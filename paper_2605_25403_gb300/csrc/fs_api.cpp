@@ -489,32 +489,66 @@ int apply_tail(fs_problem* P, DHier<T>& D, int64_t tail_rows) {
 // Work-list over the n_dof entries: for every instance its vertex and edge
 // ranges in each component block and its pressure range, cut into tiles of
 // at most kTileLen entries; tiles of one instance are consecutive.
-void build_tiles(const fs_problem* P, std::vector<Tile>& tiles, std::vector<int>& first,
-                 std::vector<int>& count) {
+void build_tiles(const fs_problem* P, int sms, std::vector<Tile>& tiles,
+                 std::vector<int>& first, std::vector<int>& count) {
   const Mesh& me = P->mesh->m;
   const int d = P->dim;
+  struct Range {
+    int64_t start, len;
+    int seg;
+  };
+  std::vector<Range> ranges;
+  for (int s = 0; s < P->nseg; ++s) {
+    const Instance& I = me.inst[s];
+    for (int c = 0; c < d; ++c) {
+      ranges.push_back({c * me.n2 + I.voff, I.nv, s});
+      ranges.push_back({c * me.n2 + me.nv + I.eoff, I.ne, s});
+    }
+    ranges.push_back({(int64_t)d * me.n2 + I.voff, I.nv, s});
+  }
+  // tile length: one block per tile in the Krylov passes.  With fewer than
+  // four tiles of kTileLen per SM the SMs holding one tile more than others
+  // set the time, so the count is brought to at most a multiple of the SM
+  // count (every SM then holds the same number): the smallest multiple of
+  // 32 whose count fits that bound.  With more tiles the imbalance is small
+  // and longer tiles cost less overhead.
+  auto ntiles_for = [&](int64_t L) {
+    int64_t k = 0;
+    for (const Range& r : ranges) k += (r.len + L - 1) / L;
+    return k;
+  };
+  int64_t total = 0;
+  for (const Range& r : ranges) total += r.len;
+  const int64_t S = std::max(1, sms);
+  const int64_t waves = std::max<int64_t>(1, (total + S * kTileLen - 1) / (S * kTileLen));
+  int64_t L = kTileLen;
+  const bool balance = ntiles_for(kTileLen) < 4 * S;
+  for (int64_t w = waves; balance && L == kTileLen && w < waves + 4; ++w) {
+    const int64_t bound = S * w;
+    for (int64_t c = 32; c <= kTileLen; c += 32)
+      if (ntiles_for(c) <= bound) {
+        L = c;
+        break;
+      }
+    if (ntiles_for(L) <= bound) break;
+  }
+  // ranges are in segment order, so the tiles of a segment are consecutive
   tiles.clear();
   first.assign(P->nseg, 0);
   count.assign(P->nseg, 0);
-  auto add = [&](int64_t start, int64_t len, int seg) {
-    for (int64_t o = 0; o < len; o += kTileLen) {
+  int seg = -1;
+  for (const Range& r : ranges) {
+    for (; seg < r.seg; ++seg) first[seg + 1] = (int)tiles.size();
+    for (int64_t o = 0; o < r.len; o += L) {
       Tile t;
-      t.start = start + o;
-      t.len = (int32_t)std::min<int64_t>(kTileLen, len - o);
-      t.seg = seg;
+      t.start = r.start + o;
+      t.len = (int32_t)std::min<int64_t>(L, r.len - o);
+      t.seg = r.seg;
       tiles.push_back(t);
+      count[r.seg] += 1;
     }
-  };
-  for (int s = 0; s < P->nseg; ++s) {
-    const Instance& I = me.inst[s];
-    first[s] = (int)tiles.size();
-    for (int c = 0; c < d; ++c) {
-      add(c * me.n2 + I.voff, I.nv, s);
-      add(c * me.n2 + me.nv + I.eoff, I.ne, s);
-    }
-    add((int64_t)d * me.n2 + I.voff, I.nv, s);
-    count[s] = (int)tiles.size() - first[s];
   }
+  for (; seg + 1 < P->nseg; ++seg) first[seg + 1] = (int)tiles.size();
 }
 
 template <typename V>
@@ -1410,7 +1444,10 @@ int fs_problem_create_batch(fs_mesh* mesh, const fs_problem_desc* descs, int cou
   FS_TRY(P->alloc(&P->r64, P->ndof));
   std::vector<Tile> tiles;
   std::vector<int> first, tcount;
-  build_tiles(P.get(), tiles, first, tcount);
+  int dev = 0, sms = 0;
+  FS_CUDA(cudaGetDevice(&dev));
+  FS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  build_tiles(P.get(), sms, tiles, first, tcount);
   FS_TRY(P->upload(&P->tiles, tiles));
   P->ntiles = (int)tiles.size();
   // SELL-32 blocks of the iteration path: layouts once, B and BT values
@@ -1748,6 +1785,36 @@ int fs_profile_kernel(fs_problem* P, int kernel, int reps, double* avg_ms, doubl
       FS_TRY(time_precond(P, reps, avg_ms));
       *alg_bytes = 0;
       return FS_OK;
+    }
+    case FS_KERNEL_CGS: {  // one CGS2 step of the Arnoldi process at j = m/2
+      // Krylov scratch only (basis, cycle state): the next solve rebuilds it.
+      // Step index j and active segments are set on the device first.
+      auto prime = [P](auto& K, int* jout) -> int {
+        const int j = K.m / 2;
+        *jout = j;
+        std::vector<int> zero(P->nseg, 0);
+        FS_CUDA(cudaMemcpyAsync(&K.ctl->j, &j, sizeof(int), cudaMemcpyHostToDevice, P->stream));
+        FS_CUDA(cudaMemcpy2DAsync(&K.st[0].done, sizeof(SegState), zero.data(), sizeof(int),
+                                  sizeof(int), P->nseg, cudaMemcpyHostToDevice, P->stream));
+        FS_CUDA(cudaStreamSynchronize(P->stream));
+        return FS_OK;
+      };
+      int j = 0;
+      if (f32) {
+        auto& K = P->p32.kr;
+        FS_TRY(prime(K, &j));
+        launch = [P, &K]() {
+          launch_seg_cgs2<float>(K.Vb, K.n, P->tl(), K.st, K.ctl, K.partial, P->stream);
+        };
+      } else {
+        auto& K = P->p64.kr;
+        FS_TRY(prime(K, &j));
+        launch = [P, &K]() {
+          launch_seg_cgs2<double>(K.Vb, K.n, P->tl(), K.st, K.ctl, K.partial, P->stream);
+        };
+      }
+      bytes = (4.0 * j + 9.0) * (double)P->ndof * s;
+      break;
     }
     default:
       set_error("fs_profile_kernel: unknown kernel id");

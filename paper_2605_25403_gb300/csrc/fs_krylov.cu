@@ -15,6 +15,8 @@
 
 #include <cmath>
 
+#include <type_traits>
+
 #include "fs_device.h"
 
 namespace fs {
@@ -174,10 +176,35 @@ __device__ __forceinline__ void tile_dots(const V* __restrict__ Vb, int64_t n, c
     const int v = u / split, c = u % split;
     const int e0 = c * chunk, e1 = min(t.len, e0 + chunk);
     V acc = V(0);
-    if (v < nvec) {
-      const V* __restrict__ vv = Vb + (int64_t)v * n + t.start;
-#pragma unroll 8
-      for (int e = e0 + lane; e < e1; e += 32) acc += vv[e] * ws[e];
+    if (e1 <= e0) {
+      // an empty chunk (the last ones of a short tile)
+    } else if (v < nvec) {
+      // 16-byte loads of the basis vector: a scalar head up to its first
+      // 16-byte boundary in [e0, e1), the aligned body, a scalar tail (the
+      // stride n is arbitrary, so the boundary differs between vectors);
+      // ws is read with scalar shared loads
+      using VV = typename std::conditional<sizeof(V) == 4, float4, double2>::type;
+      constexpr int E = 16 / sizeof(V);
+      const V* __restrict__ p = Vb + (int64_t)v * n + t.start + e0;
+      const int len = e1 - e0;
+      int h = (int)(((16 - ((uintptr_t)p & 15)) & 15) / sizeof(V));
+      if (h > len) h = len;
+      if (lane < h) acc += p[lane] * ws[e0 + lane];
+      const int nq = (len - h) / E;
+      const VV* __restrict__ q = reinterpret_cast<const VV*>(p + h);
+      const V* wq = ws + e0 + h;
+#pragma unroll 4
+      for (int k = lane; k < nq; k += 32) {
+        const VV x = q[k];
+        if constexpr (E == 4) {
+          acc += x.x * wq[4 * k] + x.y * wq[4 * k + 1] + x.z * wq[4 * k + 2] +
+                 x.w * wq[4 * k + 3];
+        } else {
+          acc += x.x * wq[2 * k] + x.y * wq[2 * k + 1];
+        }
+      }
+      const int t0 = h + nq * E;  // fewer than E entries remain
+      if (t0 + lane < len) acc += p[t0 + lane] * ws[e0 + t0 + lane];
     } else {
 #pragma unroll 8
       for (int e = e0 + lane; e < e1; e += 32) acc += ws[e] * ws[e];
@@ -187,27 +214,50 @@ __device__ __forceinline__ void tile_dots(const V* __restrict__ Vb, int64_t n, c
   }
 }
 
-// w_e - sum_v coef[v] V[v]_e for the tile's elements (thread per element;
-// the basis vectors are loaded eight at a time into separate sums).
+// The thread's elements of a tile: e = threadIdx.x + k kKB, k < kElems.
+constexpr int kElems = kTileLen / kKB;
+static_assert(kElems * kKB == kTileLen, "tile length must be a multiple of the block size");
+
+// w_e <- w_e - sum_v coef[v] V[v]_e for all the thread's elements at once
+// (w[k] for element k; entries past the tile are left alone): U basis
+// vectors at a time for every element (4 in FP32, 2 in FP64 to keep the
+// registers for two blocks per SM), so up to U kElems loads are in flight
+// per thread.
 template <typename V>
-__device__ __forceinline__ V tile_update(const V* __restrict__ Vb, int64_t n, int64_t i,
-                                         const V* coef, int nvec, V wi) {
-  constexpr int U = 8;
-  V u[U];
+__device__ __forceinline__ void tile_update(const V* __restrict__ Vb, int64_t n, const Tile& t,
+                                            const V* coef, int nvec, V (&w)[kElems]) {
+  constexpr int U = sizeof(V) == 4 ? 4 : 2;
+  V acc[kElems][U];
 #pragma unroll
-  for (int k = 0; k < U; ++k) u[k] = V(0);
+  for (int k = 0; k < kElems; ++k)
+#pragma unroll
+    for (int u = 0; u < U; ++u) acc[k][u] = V(0);
   int v = 0;
   for (; v + U <= nvec; v += U) {
 #pragma unroll
-    for (int k = 0; k < U; ++k) u[k] += coef[v + k] * Vb[(int64_t)(v + k) * n + i];
+    for (int k = 0; k < kElems; ++k) {
+      const int e = threadIdx.x + k * kKB;
+      if (e < t.len) {
+        const V* __restrict__ p = Vb + (int64_t)v * n + t.start + e;
+#pragma unroll
+        for (int u = 0; u < U; ++u) acc[k][u] += coef[v + u] * p[(int64_t)u * n];
+      }
+    }
+  }
+  for (; v < nvec; ++v) {
+#pragma unroll
+    for (int k = 0; k < kElems; ++k) {
+      const int e = threadIdx.x + k * kKB;
+      if (e < t.len) acc[k][0] += coef[v] * Vb[(int64_t)v * n + t.start + e];
+    }
   }
 #pragma unroll
-  for (int k = 0; k < U; ++k)
-    if (v + k < nvec) u[k] += coef[v + k] * Vb[(int64_t)(v + k) * n + i];
-  V sum = V(0);
+  for (int k = 0; k < kElems; ++k) {
+    V sum = V(0);
 #pragma unroll
-  for (int k = 0; k < U; ++k) sum += u[k];
-  return wi - sum;
+    for (int u = 0; u < U; ++u) sum += acc[k][u];
+    w[k] -= sum;
+  }
 }
 
 template <typename V>
@@ -251,11 +301,20 @@ __global__ void __launch_bounds__(kKB) k_seg_upd(V* __restrict__ Vb, int64_t n,
   for (int v = threadIdx.x; v <= nvec; v += kKB) sums[v] = 0.0;
   __syncthreads();
   V* __restrict__ w = Vb + (int64_t)(j + 1) * n;
-  for (int e = threadIdx.x; e < t.len; e += kKB) {
-    const int64_t i = t.start + e;
-    const V wi = tile_update<V>(Vb, n, i, coef, nvec, w[i]);
-    ws[e] = wi;
-    w[i] = wi;
+  V wv[kElems];
+#pragma unroll
+  for (int k = 0; k < kElems; ++k) {
+    const int e = threadIdx.x + k * kKB;
+    wv[k] = e < t.len ? w[t.start + e] : V(0);
+  }
+  tile_update<V>(Vb, n, t, coef, nvec, wv);
+#pragma unroll
+  for (int k = 0; k < kElems; ++k) {
+    const int e = threadIdx.x + k * kKB;
+    if (e < t.len) {
+      ws[e] = wv[k];
+      w[t.start + e] = wv[k];
+    }
   }
   __syncthreads();
   tile_dots<V>(Vb, n, t, ws, nvec, true, sums);
@@ -292,9 +351,17 @@ __global__ void __launch_bounds__(kKB) k_seg_fin(V* __restrict__ Vb, int64_t n,
   __syncthreads();
   const V f = (V)(1.0 / S.hn);
   V* __restrict__ w = Vb + (int64_t)(j + 1) * n;
-  for (int e = threadIdx.x; e < t.len; e += kKB) {
-    const int64_t i = t.start + e;
-    w[i] = tile_update<V>(Vb, n, i, coef, nvec, w[i]) * f;
+  V wv[kElems];
+#pragma unroll
+  for (int k = 0; k < kElems; ++k) {
+    const int e = threadIdx.x + k * kKB;
+    wv[k] = e < t.len ? w[t.start + e] : V(0);
+  }
+  tile_update<V>(Vb, n, t, coef, nvec, wv);
+#pragma unroll
+  for (int k = 0; k < kElems; ++k) {
+    const int e = threadIdx.x + k * kKB;
+    if (e < t.len) w[t.start + e] = wv[k] * f;
   }
 }
 

@@ -179,7 +179,7 @@ EXPORTED = ["fs_mesh_create", "fs_mesh_destroy", "fs_dof_map", "fs_problem_creat
             "fs_server_pop_completed", "fs_server_take_state", "fs_server_status",
             "fs_server_estimate_bytes", "fs_get_schedule", "fs_set_schedule", "fs_autotune"]
 (FS_KERNEL_SPMV, FS_KERNEL_SPMV_FP64, FS_KERNEL_CHEB, FS_KERNEL_ASSEMBLE_CONV,
- FS_KERNEL_PRECOND) = range(5)
+ FS_KERNEL_PRECOND, FS_KERNEL_CGS) = range(6)
 
 
 def _check(rc, where):

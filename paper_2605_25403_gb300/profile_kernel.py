@@ -23,7 +23,7 @@ def main(argv=None):
     p = argparse.ArgumentParser()
     p.add_argument("--workload", default="cube", choices=["channel", "cube", "unit_square"])
     p.add_argument("--kernel", default="cheb",
-                   choices=["cheb", "spmv", "spmv_fp64", "assemble", "precond"])
+                   choices=["cheb", "spmv", "spmv_fp64", "assemble", "precond", "cgs"])
     p.add_argument("--precision", default="fp32_refine", choices=["fp32_refine", "fp64"])
     p.add_argument("--reps", type=int, default=20)
     p.add_argument("--n", type=int, default=0,
@@ -40,7 +40,7 @@ def main(argv=None):
     prec = fs.FS_PREC_FP32_REFINE if a.precision == "fp32_refine" else fs.FS_PREC_FP64
     kid = {"cheb": fs.FS_KERNEL_CHEB, "spmv": fs.FS_KERNEL_SPMV,
            "spmv_fp64": fs.FS_KERNEL_SPMV_FP64, "assemble": fs.FS_KERNEL_ASSEMBLE_CONV,
-           "precond": fs.FS_KERNEL_PRECOND}[a.kernel]
+           "precond": fs.FS_KERNEL_PRECOND, "cgs": fs.FS_KERNEL_CGS}[a.kernel]
     S = fs.Stepper.from_workload(wl, precision=prec)
     try:
         ms, by = fs.fs_profile_kernel(S.prob, kid, reps=a.reps)
