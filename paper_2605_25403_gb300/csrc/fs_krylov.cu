@@ -434,9 +434,15 @@ __global__ void __launch_bounds__(kKB) k_seg_update_x(const SegState* st, const 
   __syncthreads();
   for (int e = threadIdx.x; e < t.len; e += kKB) {
     const int64_t i = t.start + e;
-    double s = 0;
-    for (int c = 0; c < k; ++c) s += y[c] * (double)Z[(int64_t)c * n + i];
-    x[i] = (X)((double)x[i] + s);
+    // four directions at a time into separate sums (independent loads)
+    double s[4] = {0, 0, 0, 0};
+    int c = 0;
+    for (; c + 4 <= k; c += 4) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) s[u] += y[c + u] * (double)Z[(int64_t)(c + u) * n + i];
+    }
+    for (; c < k; ++c) s[0] += y[c] * (double)Z[(int64_t)c * n + i];
+    x[i] = (X)((double)x[i] + ((s[0] + s[1]) + (s[2] + s[3])));
   }
 }
 
