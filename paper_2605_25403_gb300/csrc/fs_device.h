@@ -205,8 +205,6 @@ int mg_tail_cluster(int ncp);
 template <typename T>
 void launch_cheb_step(const DHier<T>& H, int nc, cudaStream_t s);
 
-// Previous states kept for the initial guess of a step's solve.
-constexpr int kExtrapMax = 4;
 // Polynomial extrapolation in time of the state x (x^n) through it and its
 // nprev <= kExtrapMax previous values prev[j] = x^(n-1-j) to the next time
 // level: x <- sum_j (-1)^j C(nprev+1, j+1) x^(n-j) over j = 0..nprev (x

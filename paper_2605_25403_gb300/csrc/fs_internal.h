@@ -12,6 +12,7 @@ namespace fs {
 
 constexpr int kMaxLoc = 10;  // P2 nodes per tetrahedron
 constexpr int kMaxRestart = 32;
+constexpr int kExtrapMax = 4;  // previous states kept for a step's starting guess
 
 // Thread-local error message behind fs_last_error().
 void set_error(const std::string& msg);
