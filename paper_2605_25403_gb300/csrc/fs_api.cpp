@@ -655,10 +655,14 @@ template <typename T>
 int issue_iter(fs_problem* P, Precision<T>& pr, T* x, int relative_to_beta) {
   Krylov<T>& K = pr.kr;
   cudaStream_t s = P->stream;
-  const int* skip = &K.ctl->all_done;
   const int64_t n = K.n;
   const TileList tl = P->tl();
   const bool loop = g_capturing;
+  // Steps launched directly run to m and exit at once after convergence,
+  // through the cycle's all-done flag.  The loop node runs its body only
+  // while that flag is clear (the condition is checked before every pass),
+  // so captured steps skip the check and the load it costs each kernel.
+  const int* skip = loop ? nullptr : &K.ctl->all_done;
   cudaGraphConditionalHandle cond = 0;
   if (loop) {
     cudaStreamCaptureStatus cs;
