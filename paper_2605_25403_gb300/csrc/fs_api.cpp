@@ -441,6 +441,7 @@ int upload_hierarchy(fs_problem* P, const UnionHierarchy& U, int nc, DHier<T>& D
   D.blk_n = bn;
   D.blk_dense = bd;
   D.ncoarse = H.ncoarse;
+  D.dense_nb0 = U.blk_n.size() == 1 ? H.ncoarse : 0;
   if (!U.perm.empty()) {
     std::vector<int32_t> inv(U.perm.size());
     for (size_t r = 0; r < U.perm.size(); ++r) inv[U.perm[r]] = (int32_t)r;

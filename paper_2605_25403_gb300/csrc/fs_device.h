@@ -163,6 +163,7 @@ struct DHier {
   const int64_t* blk_n = nullptr;    // block -> size
   const int64_t* blk_dense = nullptr;  // block -> offset in cinv
   int64_t ncoarse = 0;
+  int64_t dense_nb0 = 0;  // ncoarse when the coarsest level is one block, else 0
   // per level (all rows x ncp, row-interleaved components): right-hand
   // side b, and ping-pong pairs of the gather vector G (x + d, the point the
   // next residual is taken at) and the Chebyshev direction D

@@ -357,6 +357,21 @@ __device__ __forceinline__ void prolong_row(const DCsr<T>& P, const T* __restric
   vstore<T, NCP>(Gf + row * NCP, x);
 }
 
+// The coarsest level's dense blocks as a kernel reads them: one block of
+// nb0 rows at offset 0 (a single problem, no lookups), or per row its block
+// from the tables.
+template <typename T>
+struct DenseView {
+  const T* cinv;
+  const int32_t* row_blk;
+  const int64_t *blk_row, *blk_n, *blk_dense;
+  int64_t nb0;
+};
+template <typename T>
+__host__ __device__ __forceinline__ DenseView<T> dense_view(const DHier<T>& H) {
+  return DenseView<T>{H.cinv, H.row_blk, H.blk_row, H.blk_n, H.blk_dense, H.dense_nb0};
+}
+
 // Coarsest-level row x = blockdiag(Cinv) b (a warp per row); the result goes
 // to X, or (level 0 being the coarsest) to the caller's blocked out.  The row
 // of Cinv is read in 16-byte loads (a scalar head up to the first 16-byte
@@ -364,7 +379,7 @@ __device__ __forceinline__ void prolong_row(const DCsr<T>& P, const T* __restric
 // has only ~23 rows per SM, so the loads of one warp must cover the memory
 // latency.  b is re-read by every row from L1/L2.
 template <typename T, int NCP>
-__device__ __forceinline__ void dense_row(const DHier<T>& H, const T* __restrict__ b,
+__device__ __forceinline__ void dense_row(const DenseView<T>& D, const T* __restrict__ b,
                                           T* __restrict__ X, T* __restrict__ out,
                                           int64_t out_ld, const int32_t* __restrict__ perm,
                                           int nc, int64_t row, int lane, bool active) {
@@ -372,9 +387,14 @@ __device__ __forceinline__ void dense_row(const DHier<T>& H, const T* __restrict
 #pragma unroll
   for (int c = 0; c < NCP; ++c) acc[c] = T(0);
   if (active) {
-    const int blk = H.row_blk[row];
-    const int64_t r0 = H.blk_row[blk], nb = H.blk_n[blk];
-    const T* Cr = H.cinv + H.blk_dense[blk] + (row - r0) * nb;
+    int64_t r0 = 0, nb = D.nb0, off = 0;
+    if (nb == 0) {
+      const int blk = D.row_blk[row];
+      r0 = D.blk_row[blk];
+      nb = D.blk_n[blk];
+      off = D.blk_dense[blk];
+    }
+    const T* Cr = D.cinv + off + (row - r0) * nb;
     const T* bb = b + r0 * NCP;
     auto add = [&](T a, int64_t j) {
       T bj[NCP];
@@ -462,14 +482,16 @@ __global__ void __launch_bounds__(256) k_mg_prolong(DCsr<T> P, const T* __restri
   prolong_row<T, NCP, L>(P, Xc, Gf, row, (int)(gt % L), row < P.nrow);
 }
 
+// The coarsest level's solve; every pointer and size comes by value, so no
+// load precedes the rows' streams.
 template <typename T, int NCP>
-__global__ void k_mg_dense(const DHier<T>* __restrict__ Hp, int l, JVec<T> outv, int64_t out_ld,
-                           int nc, const int* skip) {
+__global__ void k_mg_dense(DenseView<T> D, int64_t ncoarse, const T* __restrict__ b,
+                           T* __restrict__ X, const int32_t* __restrict__ perm, JVec<T> outv,
+                           int64_t out_ld, int nc, const int* skip) {
   if (skip && *skip) return;
-  const DHier<T>& H = *Hp;
   const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32;
-  dense_row<T, NCP>(H, H.b[l], H.G1[l], outv.get(), out_ld, l == 0 ? H.perm : nullptr,
-                           nc, row, threadIdx.x & 31, row < H.ncoarse);
+  dense_row<T, NCP>(D, b, X, outv.get(), out_ld, perm, nc, row, threadIdx.x & 31,
+                    row < ncoarse);
 }
 
 // The V-cycle from level l0 (its right-hand side and first step in place)
@@ -527,7 +549,7 @@ __global__ void __launch_bounds__(NT, 1) k_mg_tail(const DHier<T>* __restrict__ 
     const int64_t nr = H.ncoarse, groups = nth / 32, sweeps = (nr + groups - 1) / groups;
     for (int64_t q = 0; q < sweeps; ++q) {
       const int64_t r = q * groups + tid / 32;
-      dense_row<T, NCP>(H, H.b[last], H.G1[last], nullptr, 0, nullptr, nc, r, lane32,
+      dense_row<T, NCP>(dense_view(H), H.b[last], H.G1[last], nullptr, 0, nullptr, nc, r, lane32,
                               r < nr);
     }
     cl.sync();
@@ -626,9 +648,9 @@ void vcycle_level(const DHier<T>& H, int l, JVec<T> out, int64_t out_ld, int nc,
     return;
   }
   if (l == H.nlev - 1) {
-    k_mg_dense<T, NCP><<<blocks_for(H.ncoarse * 32), 256, 0, s>>>(H.dev, l,
-                                                                   top ? out : JVec<T>(), out_ld,
-                                                                   nc, skip);
+    k_mg_dense<T, NCP><<<blocks_for(H.ncoarse * 32), 256, 0, s>>>(
+        dense_view(H), H.ncoarse, H.b[l], H.G1[l], top ? H.perm : nullptr,
+        top ? out : JVec<T>(), out_ld, nc, skip);
     count_launches(1);
     return;
   }
