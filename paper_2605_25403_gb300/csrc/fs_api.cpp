@@ -254,16 +254,27 @@ int upload_csr(fs_problem* P, const HostCsr& H, DCsr<T>& d) {
 // = the longest row of the slice) and slot-major columns.  Padding slots
 // point at the row itself in a square matrix (a read the row makes anyway)
 // and at column 0 in a rectangular one, so that every column is in range.
-void sell_layout(const HostCsr& H, std::vector<int64_t>& off, std::vector<int32_t>& ci) {
+// uniform_slack > 0: when padding every slice to the widest costs at most
+// that fraction more slots, all slices get that width; *width receives it
+// (0 when the slices keep their own widths).
+void sell_layout(const HostCsr& H, std::vector<int64_t>& off, std::vector<int32_t>& ci,
+                 double uniform_slack = 0.0, int64_t* width = nullptr) {
   const bool square = H.nrow == H.ncol;
   const int64_t n = H.nrow, ns = (n + 31) / 32;
-  off.assign(ns + 1, 0);
+  std::vector<int64_t> ws(ns, 0);
+  int64_t wmax = 0, sum = 0;
   for (int64_t sl = 0; sl < ns; ++sl) {
     int64_t w = 0;
     for (int64_t r = 32 * sl; r < std::min(n, 32 * sl + 32); ++r)
       w = std::max<int64_t>(w, H.rowptr[r + 1] - H.rowptr[r]);
-    off[sl + 1] = off[sl] + 32 * w;
+    ws[sl] = w;
+    wmax = std::max(wmax, w);
+    sum += w;
   }
+  const bool uniform = uniform_slack > 0 && ns > 0 && wmax * ns <= (1.0 + uniform_slack) * sum;
+  if (width) *width = uniform ? wmax : 0;
+  off.assign(ns + 1, 0);
+  for (int64_t sl = 0; sl < ns; ++sl) off[sl + 1] = off[sl] + 32 * (uniform ? wmax : ws[sl]);
   ci.assign(off[ns], 0);
   for (int64_t r = 0; r < n; ++r) {
     const int64_t sl = r >> 5, t = r & 31, w = (off[sl + 1] - off[sl]) / 32;
@@ -290,10 +301,11 @@ std::vector<T> sell_values(const HostCsr& H, const std::vector<int64_t>& off, co
 }
 
 template <typename T>
-int upload_sell(fs_problem* P, const HostCsr& H, DSell<T>& d) {
+int upload_sell(fs_problem* P, const HostCsr& H, DSell<T>& d, double uniform_slack = 0.0) {
   std::vector<int64_t> off;
   std::vector<int32_t> ci;
-  sell_layout(H, off, ci);
+  int64_t width = 0;
+  sell_layout(H, off, ci, uniform_slack, &width);
   std::vector<T> v = sell_values<T>(H, off, H.val.data(), 1);
   int64_t* doff;
   int32_t* dci;
@@ -305,6 +317,7 @@ int upload_sell(fs_problem* P, const HostCsr& H, DSell<T>& d) {
   d.off = doff;
   d.ci = dci;
   d.v = dv;
+  d.width = width;
   return FS_OK;
 }
 
@@ -405,7 +418,10 @@ int upload_hierarchy(fs_problem* P, const UnionHierarchy& U, int nc, DHier<T>& D
   for (int l = 0; l < D.nlev; ++l) {
     const HostLevel& hl = H.levels[l];
     DLevel<T>& dl = D.lev[l];
-    FS_TRY(upload_sell<T>(P, hl.A, dl.A));
+    // level operators: one slice width where padding costs at most 15%
+    // more slots (the structured P1 levels); the class-ordered P2 level
+    // keeps its per-slice widths
+    FS_TRY(upload_sell<T>(P, hl.A, dl.A, 0.15));
     if (l + 1 < D.nlev) {
       FS_TRY(upload_csr<T>(P, hl.P, dl.P));
       FS_TRY(upload_csr<T>(P, hl.R, dl.R));

@@ -36,6 +36,9 @@ struct DSell {
   const int64_t* off = nullptr;
   const int32_t* ci = nullptr;
   const T* v = nullptr;
+  // > 0: every slice has this many slots (off[s] = 32 s width), so a
+  // thread finds its slice without loading off
+  int64_t width = 0;
 };
 
 // A vector addressed through the device-side Arnoldi step index: base +

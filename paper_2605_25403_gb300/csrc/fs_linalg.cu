@@ -237,7 +237,9 @@ __device__ __forceinline__ void mg_row(const DSell<T>& A, const T* __restrict__ 
                                        T* __restrict__ Dout, T alpha, T beta, T inv_theta,
                                        T* __restrict__ out, int64_t out_ld,
                                        const int32_t* __restrict__ perm, int nc, int64_t row) {
-  const int64_t o0 = A.off[row >> 5] + (row & 31), o1 = A.off[(row >> 5) + 1];
+  const int64_t sl = row >> 5;
+  const int64_t o0 = (A.width ? sl * 32 * A.width : A.off[sl]) + (row & 31);
+  const int64_t o1 = A.width ? (sl + 1) * 32 * A.width : A.off[sl + 1];
   T acc[NCP];
 #pragma unroll
   for (int c = 0; c < NCP; ++c) acc[c] = T(0);
