@@ -41,3 +41,12 @@ def test_single_process_is_identity():
     assert bench.aggregate_time(2.25, None) == 2.25
     a = bench.parse(["--steps", "7", "--batch-steps", "0"])
     assert a.steps == 7 and a.batch_steps == 0 and a.gpus == 1
+
+
+def test_traffic_of_the_roofline_kernel_comes_from_the_committed_capture():
+    """The bench line's roofline `traffic` is read from profiles/traffic.txt
+    (DRAM bytes per launch of one ncu capture of the current kernel)."""
+    import bench
+    t = bench.traffic_from_profiles("cheb", "channel_512x96")
+    assert t is not None and 20e6 < t < 30e6      # ~ the 27.6 MB algorithmic
+    assert bench.traffic_from_profiles("cheb", "no_such_workload") is None
