@@ -181,7 +181,7 @@ int fs_assemble_step(fs_problem* prob, double t_next, double* val_out,
                      double* b_out);
 
 typedef struct {
-  int restart;        /* GMRES(m) restart length m (this build: 30)         */
+  int restart;        /* GMRES(m) restart length m (must be 30)             */
   int max_iter;       /* cap on (inner) Krylov iterations per solve         */
   double rtol;        /* stop at ||b - A x||_2 <= rtol ||b||_2, FP64 true
                          residual; a residual that stops decreasing (a

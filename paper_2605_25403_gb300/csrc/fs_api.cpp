@@ -893,7 +893,7 @@ fs_solve_stats aggregate_stats(const fs_problem* P) {
 // is known: converged, stagnated at the rounding floor (accepted within
 // 100 rtol), out of budget, or continue.  Returns true when every segment
 // is retired.
-bool judge(fs_problem* P, bool refinement) {
+bool retire_segments(fs_problem* P, bool refinement) {
   SolveCtx& c = P->ctx;
   const double rtol = c.o.rtol;
   bool all = true;
@@ -938,7 +938,7 @@ int advance(fs_problem* P) {
   const bool graph = c.o.use_graph != 0;
   switch (c.phase) {
     case PH_CHECK: {  // FP64: true residual known
-      if (judge(P, false)) {
+      if (retire_segments(P, false)) {
         finish_solve(P);
         return FS_OK;
       }
@@ -976,7 +976,7 @@ int advance(fs_problem* P) {
       return FS_OK;
     }
     case PH_RES64: {  // refinement: FP64 residual known
-      if (judge(P, true)) {
+      if (retire_segments(P, true)) {
         finish_solve(P);
         return FS_OK;
       }
@@ -1152,7 +1152,7 @@ int solve_opts(const fs_solve_opts* opts, fs_solve_opts& o) {
   fs_default_solve_opts(&o);
   if (opts) o = *opts;
   if (o.restart != 30) {
-    set_error("this build runs GMRES(30) restart cycles (restart must be 30)");
+    set_error("the library runs GMRES(30) restart cycles (restart must be 30)");
     return FS_ERR_UNSUPPORTED;
   }
   return FS_OK;
