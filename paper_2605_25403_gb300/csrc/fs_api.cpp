@@ -698,8 +698,10 @@ int issue_iter(fs_problem* P, Precision<T>& pr, T* x, int relative_to_beta) {
     launch_precond<T>(pr.op, pr.HA, pr.HK, pr.mplinv_nu, 1.0 / P->desc.dt, P->pinned,
                       P->npinned, vj, zj, K.work_p, K.work_u, skip, q);
     launch_spmv_full<T, T>(pr.op, zjc, nullptr, w, 0, skip, q);
-    launch_seg_cgs2<T>(K.Vb, n, tl, K.st, K.ctl, K.partial, q);
-    launch_seg_givens(K.st, K.ctl, P->nseg, cond, q);
+    // one segment: the Givens step rides in the second CGS2 pass
+    const bool fuse = P->nseg == 1;
+    launch_seg_cgs2<T>(K.Vb, n, tl, K.st, K.ctl, K.partial, fuse, cond, q);
+    if (!fuse) launch_seg_givens(K.st, K.ctl, P->nseg, cond, q);
   };
   if (loop) {
     cudaStreamCaptureStatus cs;
@@ -1825,13 +1827,15 @@ int fs_profile_kernel(fs_problem* P, int kernel, int reps, double* avg_ms, doubl
         auto& K = P->p32.kr;
         FS_TRY(prime(K, &j));
         launch = [P, &K]() {
-          launch_seg_cgs2<float>(K.Vb, K.n, P->tl(), K.st, K.ctl, K.partial, P->stream);
+          launch_seg_cgs2<float>(K.Vb, K.n, P->tl(), K.st, K.ctl, K.partial, false, 0,
+                                 P->stream);
         };
       } else {
         auto& K = P->p64.kr;
         FS_TRY(prime(K, &j));
         launch = [P, &K]() {
-          launch_seg_cgs2<double>(K.Vb, K.n, P->tl(), K.st, K.ctl, K.partial, P->stream);
+          launch_seg_cgs2<double>(K.Vb, K.n, P->tl(), K.st, K.ctl, K.partial, false, 0,
+                                  P->stream);
         };
       }
       bytes = (4.0 * j + 9.0) * (double)P->ndof * s;

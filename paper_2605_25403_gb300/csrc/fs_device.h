@@ -284,10 +284,14 @@ void launch_seg_cycle_init(SegState* st, KCtl* ctl, int relative_to_beta,
 template <typename V>
 void launch_seg_scale(JVec<V> x, const TileList& tl, const SegState* st, int field,
                       cudaStream_t s);
-// CGS2 on w = V[j + 1] with j = ctl->j, ending with V[j + 1] normalised
+// CGS2 on w = V[j + 1] with j = ctl->j, ending with V[j + 1] normalised.
+// with_givens (problems of one segment): the Givens step of column j and the
+// advance of the step index (setting cond when not 0) are done by the
+// second pass, in place of launch_seg_givens.
 template <typename V>
-void launch_seg_cgs2(V* Vb, int64_t n, const TileList& tl, SegState* st,
-                     const KCtl* ctl, double* partial, cudaStream_t s);
+void launch_seg_cgs2(V* Vb, int64_t n, const TileList& tl, SegState* st, KCtl* ctl,
+                     double* partial, bool with_givens, cudaGraphConditionalHandle cond,
+                     cudaStream_t s);
 void launch_seg_givens(SegState* st, KCtl* ctl, int nseg, cudaGraphConditionalHandle cond,
                        cudaStream_t s);
 template <typename V, typename X>

@@ -260,6 +260,49 @@ __device__ __forceinline__ void tile_update(const V* __restrict__ Vb, int64_t n,
   }
 }
 
+// Givens rotations of column j of one active segment's Hessenberg matrix,
+// its least-squares residual, and the end of its cycle (converged, broken
+// or at the restart length): the segment is then marked done and counted.
+__device__ void givens_segment(SegState& S, KCtl* ctl, int j, int m) {
+  double* H = S.H;
+  for (int i = 0; i < j; ++i) {
+    const double a = H[i * m + j], b = H[(i + 1) * m + j];
+    H[i * m + j] = S.cs[i] * a + S.sn[i] * b;
+    H[(i + 1) * m + j] = -S.sn[i] * a + S.cs[i] * b;
+  }
+  const double a = H[j * m + j], b = H[(j + 1) * m + j];
+  const double den = hypot(a, b);
+  const double c = den == 0.0 ? 1.0 : a / den, sn = den == 0.0 ? 0.0 : b / den;
+  S.cs[j] = c;
+  S.sn[j] = sn;
+  H[j * m + j] = den;
+  H[(j + 1) * m + j] = 0.0;
+  S.g[j + 1] = -sn * S.g[j];
+  S.g[j] = c * S.g[j];
+  S.resid = fabs(S.g[j + 1]);
+  S.k = j + 1;
+  bool finish = false;
+  if (!isfinite(S.resid) || !isfinite(den) || den == 0.0) {
+    S.bad = isfinite(S.resid) && isfinite(den) ? S.bad : 1;
+    S.k = j;  // drop the broken column
+    finish = true;
+  } else if (S.resid <= S.tol_abs || b == 0.0 || j + 1 >= m) {
+    finish = true;
+  }
+  if (finish) {
+    S.done = 1;
+    if (atomicAdd(&ctl->ndone, 1) + 1 == ctl->nseg) ctl->all_done = 1;
+  }
+}
+
+// The step index advances and the loop node's condition (if any) becomes
+// "a segment is still active and j + 1 < m" (one thread).
+__device__ void end_arnoldi_step(KCtl* ctl, int j, int m, cudaGraphConditionalHandle cond) {
+  const int all = atomicAdd(&ctl->all_done, 0);
+  ctl->j = j + 1;
+  if (cond) cudaGraphSetConditional(cond, (!all && j + 1 < m) ? 1u : 0u);
+}
+
 template <typename V>
 __global__ void __launch_bounds__(kKB) k_seg_dot(const V* __restrict__ Vb, int64_t n,
                                                  const Tile* tiles, int ntiles, SegState* st,
@@ -286,10 +329,14 @@ __global__ void __launch_bounds__(kKB) k_seg_dot(const V* __restrict__ Vb, int64
   }
 }
 
-template <typename V>
+// GIV (problems of one segment): the last block also takes the step's
+// Givens rotations and advances the step index (no separate Givens kernel);
+// the final pass then reads j as ctl->j - 1.
+template <typename V, bool GIV>
 __global__ void __launch_bounds__(kKB) k_seg_upd(V* __restrict__ Vb, int64_t n,
                                                  const Tile* tiles, int ntiles, SegState* st,
-                                                 const KCtl* ctl, double* partial) {
+                                                 KCtl* ctl, double* partial,
+                                                 cudaGraphConditionalHandle cond) {
   const Tile t = tiles[blockIdx.x];
   SegState& S = st[t.seg];
   if (S.done) return;
@@ -335,17 +382,21 @@ __global__ void __launch_bounds__(kKB) k_seg_upd(V* __restrict__ Vb, int64_t n,
     S.hn = hn;
     S.H[(j + 1) * m + j] = hn;
     S.counter[2] = 0;
+    if constexpr (GIV) {
+      givens_segment(S, ctl, j, m);
+      end_arnoldi_step(ctl, j, m, cond);
+    }
   }
 }
 
 template <typename V>
 __global__ void __launch_bounds__(kKB) k_seg_fin(V* __restrict__ Vb, int64_t n,
                                                  const Tile* tiles, SegState* st,
-                                                 const KCtl* ctl) {
+                                                 const KCtl* ctl, int jshift) {
   const Tile t = tiles[blockIdx.x];
   const SegState& S = st[t.seg];
   if (S.done) return;
-  const int j = ctl->j, nvec = j + 1;
+  const int j = ctl->j - jshift, nvec = j + 1;
   __shared__ V coef[kMaxRestart + 1];
   for (int v = threadIdx.x; v < nvec; v += kKB) coef[v] = (V)S.h2[v];
   __syncthreads();
@@ -374,43 +425,10 @@ __global__ void k_seg_givens(SegState* st, KCtl* ctl, cudaGraphConditionalHandle
   const int j = ctl->j;
   for (int s = threadIdx.x; s < ctl->nseg; s += blockDim.x) {
     SegState& S = st[s];
-    if (S.done) continue;
-    double* H = S.H;
-    for (int i = 0; i < j; ++i) {
-      const double a = H[i * m + j], b = H[(i + 1) * m + j];
-      H[i * m + j] = S.cs[i] * a + S.sn[i] * b;
-      H[(i + 1) * m + j] = -S.sn[i] * a + S.cs[i] * b;
-    }
-    const double a = H[j * m + j], b = H[(j + 1) * m + j];
-    const double den = hypot(a, b);
-    const double c = den == 0.0 ? 1.0 : a / den, sn = den == 0.0 ? 0.0 : b / den;
-    S.cs[j] = c;
-    S.sn[j] = sn;
-    H[j * m + j] = den;
-    H[(j + 1) * m + j] = 0.0;
-    S.g[j + 1] = -sn * S.g[j];
-    S.g[j] = c * S.g[j];
-    S.resid = fabs(S.g[j + 1]);
-    S.k = j + 1;
-    bool finish = false;
-    if (!isfinite(S.resid) || !isfinite(den) || den == 0.0) {
-      S.bad = isfinite(S.resid) && isfinite(den) ? S.bad : 1;
-      S.k = j;  // drop the broken column
-      finish = true;
-    } else if (S.resid <= S.tol_abs || b == 0.0 || j + 1 >= m) {
-      finish = true;
-    }
-    if (finish) {
-      S.done = 1;
-      if (atomicAdd(&ctl->ndone, 1) + 1 == ctl->nseg) ctl->all_done = 1;
-    }
+    if (!S.done) givens_segment(S, ctl, j, m);
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    const int all = atomicAdd(&ctl->all_done, 0);
-    ctl->j = j + 1;
-    if (cond) cudaGraphSetConditional(cond, (!all && j + 1 < m) ? 1u : 0u);
-  }
+  if (threadIdx.x == 0) end_arnoldi_step(ctl, j, m, cond);
 }
 
 // y = H(0:k,0:k)^-1 g(0:k) of the tile's segment, then x += xscale Z y
@@ -502,17 +520,23 @@ template void launch_seg_scale<float>(JVec<float>, const TileList&, const SegSta
                                       cudaStream_t);
 
 template <typename V>
-void launch_seg_cgs2(V* Vb, int64_t n, const TileList& tl, SegState* st, const KCtl* ctl,
-                     double* partial, cudaStream_t s) {
+void launch_seg_cgs2(V* Vb, int64_t n, const TileList& tl, SegState* st, KCtl* ctl,
+                     double* partial, bool with_givens, cudaGraphConditionalHandle cond,
+                     cudaStream_t s) {
   k_seg_dot<V><<<tl.ntiles, kKB, 0, s>>>(Vb, n, tl.tiles, tl.ntiles, st, ctl, partial);
-  k_seg_upd<V><<<tl.ntiles, kKB, 0, s>>>(Vb, n, tl.tiles, tl.ntiles, st, ctl, partial);
-  k_seg_fin<V><<<tl.ntiles, kKB, 0, s>>>(Vb, n, tl.tiles, st, ctl);
+  if (with_givens)
+    k_seg_upd<V, true><<<tl.ntiles, kKB, 0, s>>>(Vb, n, tl.tiles, tl.ntiles, st, ctl, partial,
+                                                 cond);
+  else
+    k_seg_upd<V, false><<<tl.ntiles, kKB, 0, s>>>(Vb, n, tl.tiles, tl.ntiles, st, ctl, partial,
+                                                  0);
+  k_seg_fin<V><<<tl.ntiles, kKB, 0, s>>>(Vb, n, tl.tiles, st, ctl, with_givens ? 1 : 0);
   count_launches(3);
 }
-template void launch_seg_cgs2<double>(double*, int64_t, const TileList&, SegState*, const KCtl*,
-                                      double*, cudaStream_t);
-template void launch_seg_cgs2<float>(float*, int64_t, const TileList&, SegState*, const KCtl*,
-                                     double*, cudaStream_t);
+template void launch_seg_cgs2<double>(double*, int64_t, const TileList&, SegState*, KCtl*,
+                                      double*, bool, cudaGraphConditionalHandle, cudaStream_t);
+template void launch_seg_cgs2<float>(float*, int64_t, const TileList&, SegState*, KCtl*, double*,
+                                     bool, cudaGraphConditionalHandle, cudaStream_t);
 
 void launch_seg_givens(SegState* st, KCtl* ctl, int nseg, cudaGraphConditionalHandle cond,
                        cudaStream_t s) {
