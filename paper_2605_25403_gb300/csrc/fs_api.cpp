@@ -591,7 +591,7 @@ int alloc_krylov(fs_problem* P, Krylov<V>& K, int m, const std::vector<int>& fir
   }
   FS_CUDA(cudaMemcpy2DAsync(K.st, sizeof(SegState), init.data(), sizeof(SegHost),
                             sizeof(SegHost), P->nseg, cudaMemcpyHostToDevice, P->stream));
-  KCtl c{m, P->nseg, 0, 0};
+  KCtl c{m, P->nseg, 0, 0, 0};
   FS_CUDA(cudaMemcpyAsync(K.ctl, &c, sizeof(KCtl), cudaMemcpyHostToDevice, P->stream));
   FS_CUDA(cudaStreamSynchronize(P->stream));  // host sources go out of scope
   return FS_OK;

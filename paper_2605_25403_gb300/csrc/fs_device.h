@@ -270,7 +270,8 @@ struct KCtl {
   int ndone;     // segments done in this cycle
   int all_done;  // every segment done: the spanning kernels skip
   int j;         // Arnoldi step of the cycle (reset by the cycle init,
-                 // advanced by the Givens kernel)
+                 // advanced by the Givens step: its own kernel, or the
+                 // second CGS2 pass for problems of one segment)
 };
 
 template <typename V>

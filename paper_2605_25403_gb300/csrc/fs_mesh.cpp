@@ -505,7 +505,7 @@ double fact(int k) {
 }  // namespace
 
 void ref_tensors(int dim, RefTensors& R) {
-  std::memset(&R, 0, sizeof(R));
+  R = RefTensors{};  // every table zero
   R.dim = dim;
   R.nb = dim + 1;
   R.nloc = dim == 2 ? 6 : 10;
