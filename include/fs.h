@@ -66,8 +66,13 @@ typedef enum {
   FS_PROBLEM_CUBE = 3,           /* 3D: u = sin t curl(Phi (1,1,1)),
                                     Phi = sin^2(pi x) sin^2(pi y) sin^2(pi z),
                                     p = sin t (x^2 y z - 1/12)            */
-  FS_PROBLEM_POLY_OSEEN = 4      /* u in P2 (div-free), p in P1, constant
+  FS_PROBLEM_POLY_OSEEN = 4,     /* u in P2 (div-free), p in P1, constant
                                     convecting field wconst (exactness)   */
+  FS_PROBLEM_POLY_OSEEN_T = 5    /* (1 + t) times the fields of problem 4:
+                                    affine in time, so backward Euler
+                                    reproduces it exactly at every step
+                                    (checks the time level of f, of the
+                                    Dirichlet data and of the pin)        */
 } fs_problem_kind;
 
 typedef enum {

@@ -241,7 +241,8 @@ enum {
   OR_STEADY_POLY = 1,  /* Sec. 3.3 steady example, 2D (no time)          */
   OR_CHANNEL = 2,      /* Poiseuille profile, U_max 1.5, H 0.41, L 2.2   */
   OR_CUBE = 3,         /* 3D: u = sin t curl(Phi (1,1,1)), Phi=prod sin^2 */
-  OR_POLY_OSEEN = 4    /* u in P2 div-free, p in P1, constant w           */
+  OR_POLY_OSEEN = 4,   /* u in P2 div-free, p in P1, constant w           */
+  OR_POLY_OSEEN_T = 5  /* (1 + t) times the fields of OR_POLY_OSEEN       */
 };
 
 /* g(s) = sin^2(pi s) and its derivatives up to order 3. */
@@ -355,9 +356,13 @@ static void exact_fields(int problem, int dim, double t, const double* x,
       dp[2] = S * X * X * Y;
       break;
     }
-    case OR_POLY_OSEEN: {
+    case OR_POLY_OSEEN:
+    case OR_POLY_OSEEN_T: {
       /* 2D: u = (x^2, -2xy), p = x + y - 1.
-       * 3D: u = (x^2, -2xy, xy), p = x + y + z - 1. */
+       * 3D: u = (x^2, -2xy, xy), p = x + y + z - 1.
+       * OR_POLY_OSEEN_T multiplies u and p by (1 + t), so u_t is the
+       * spatial field itself: affine in time, which backward Euler
+       * differentiates exactly. */
       u[0] = X * X;
       u[1] = -2 * X * Y;
       du[0 * dim + 0] = 2 * X;
@@ -372,6 +377,17 @@ static void exact_fields(int problem, int dim, double t, const double* x,
         du[2 * 3 + 1] = X;
         *p = X + Y + x[2] - 1;
         dp[2] = 1;
+      }
+      if (problem == OR_POLY_OSEEN_T) {
+        double s = 1.0 + t;
+        for (int i = 0; i < dim; ++i) {
+          ut[i] = u[i];
+          u[i] *= s;
+          lap[i] *= s;
+          dp[i] *= s;
+          for (int j = 0; j < dim; ++j) du[i * dim + j] *= s;
+        }
+        *p *= s;
       }
       break;
     }
@@ -391,7 +407,8 @@ void or_exact(int problem, int dim, double t, double nu, const double* wconst,
   }
   double w[3];
   for (int i = 0; i < dim; ++i)
-    w[i] = (problem == OR_POLY_OSEEN && wconst) ? wconst[i] : uu[i];
+    w[i] = ((problem == OR_POLY_OSEEN || problem == OR_POLY_OSEEN_T) && wconst)
+               ? wconst[i] : uu[i];
   if (u) for (int i = 0; i < dim; ++i) u[i] = uu[i];
   if (p) *p = pp;
   if (f)

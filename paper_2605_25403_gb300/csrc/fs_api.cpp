@@ -809,7 +809,8 @@ int assemble_impl(fs_problem* P, double t_next) {
   const Mesh& me = P->mesh->m;
   const int64_t nnzA = me.A.nnz();
   FS_CUDA(cudaMemcpyAsync(P->valA, P->baseA, sizeof(double) * nnzA, cudaMemcpyDeviceToDevice, s));
-  const bool constw = P->desc.problem == FS_PROBLEM_POLY_OSEEN;
+  const bool constw = P->desc.problem == FS_PROBLEM_POLY_OSEEN ||
+                      P->desc.problem == FS_PROBLEM_POLY_OSEEN_T;
   launch_assemble_conv(P->dm, constw ? nullptr : P->x, P->n2, constw ? P->desc.wconst : nullptr,
                        P->valA, s);
   launch_bc_rows<double>(P->dm, P->valA, s);
@@ -1282,7 +1283,7 @@ int fs_problem_create_batch(fs_mesh* mesh, const fs_problem_desc* descs, int cou
   const fs_problem_desc& d0 = descs[0];
   for (int i = 0; i < count; ++i) {
     const fs_problem_desc& d = descs[i];
-    if (!(d.dt > 0) || !(d.nu > 0) || d.problem < 0 || d.problem > 4 ||
+    if (!(d.dt > 0) || !(d.nu > 0) || d.problem < 0 || d.problem > 5 ||
         (d.precision != FS_PREC_FP64 && d.precision != FS_PREC_FP32_REFINE)) {
       set_error("fs_problem_create: need dt > 0, nu > 0, a known problem and precision");
       return FS_ERR_INVALID_ARG;
@@ -1294,7 +1295,8 @@ int fs_problem_create_batch(fs_mesh* mesh, const fs_problem_desc* descs, int cou
       return FS_ERR_INVALID_ARG;
     }
   }
-  if ((d0.problem == FS_PROBLEM_CUBE) != (me.dim == 3) && d0.problem != FS_PROBLEM_POLY_OSEEN) {
+  if ((d0.problem == FS_PROBLEM_CUBE) != (me.dim == 3) && d0.problem != FS_PROBLEM_POLY_OSEEN &&
+      d0.problem != FS_PROBLEM_POLY_OSEEN_T) {
     set_error("fs_problem_create: problem kind does not match the mesh dimension");
     return FS_ERR_INVALID_ARG;
   }

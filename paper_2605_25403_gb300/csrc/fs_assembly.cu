@@ -385,17 +385,23 @@ __device__ Fields eval_fields(const DPhys& ph, double nu, const double* x, doubl
       }
       break;
     }
-    case FS_PROBLEM_POLY_OSEEN: {
+    case FS_PROBLEM_POLY_OSEEN:
+    case FS_PROBLEM_POLY_OSEEN_T: {
+      // spatial fields u0 = (x^2, -2xy[, xy]), p0 = x + y [+ z] - 1 and the
+      // steady Oseen load g0 = -nu Lap u0 + (w.grad) u0 + grad p0; the
+      // time-affine kind is (1 + t)(u0, p0) with load u0 + (1 + t) g0
       double w1 = ph.wconst[0], w2 = ph.wconst[1];
-      F.u[0] = X * X;
-      F.u[1] = -2 * X * Y;
-      F.p = X + Y - 1;
-      F.f[0] = -2 * nu + 2 * X * w1 + 1;
-      F.f[1] = -2 * Y * w1 - 2 * X * w2 + 1;
+      double s = ph.kind == FS_PROBLEM_POLY_OSEEN_T ? 1.0 + t : 1.0;
+      double ut = ph.kind == FS_PROBLEM_POLY_OSEEN_T ? 1.0 : 0.0;
+      F.u[0] = s * (X * X);
+      F.u[1] = s * (-2 * X * Y);
+      F.p = s * (X + Y - 1);
+      F.f[0] = ut * (X * X) + s * (-2 * nu + 2 * X * w1 + 1);
+      F.f[1] = ut * (-2 * X * Y) + s * (-2 * Y * w1 - 2 * X * w2 + 1);
       if constexpr (DIM == 3) {
-        F.u[2] = X * Y;
-        F.p = X + Y + x[2] - 1;
-        F.f[2] = Y * w1 + X * w2 + 1;
+        F.u[2] = s * (X * Y);
+        F.p = s * (X + Y + x[2] - 1);
+        F.f[2] = ut * (X * Y) + s * (Y * w1 + X * w2 + 1);
       }
       break;
     }

@@ -33,7 +33,7 @@ STATUS = {0: "FS_OK", 1: "FS_ERR_INVALID_ARG", 2: "FS_ERR_INVALID_MESH", 3: "FS_
           7: "FS_ERR_TIMEOUT", 8: "FS_ERR_BUSY", 9: "FS_ERR_UNSUPPORTED"}
 FS_PREC_FP64, FS_PREC_FP32_REFINE = 0, 1
 FS_PROBLEM_UNSTEADY_BENCH, FS_PROBLEM_STEADY_POLY, FS_PROBLEM_CHANNEL, FS_PROBLEM_CUBE, \
-    FS_PROBLEM_POLY_OSEEN = range(5)
+    FS_PROBLEM_POLY_OSEEN, FS_PROBLEM_POLY_OSEEN_T = range(6)
 
 
 class FsError(RuntimeError):
@@ -462,7 +462,7 @@ def fs_set_state(prob, x, t):
 # Convenience wrapper: one problem built from a workload description
 # ---------------------------------------------------------------------------
 _KIND = {0: FS_PROBLEM_UNSTEADY_BENCH, 1: FS_PROBLEM_STEADY_POLY, 2: FS_PROBLEM_CHANNEL,
-         3: FS_PROBLEM_CUBE, 4: FS_PROBLEM_POLY_OSEEN}
+         3: FS_PROBLEM_CUBE, 4: FS_PROBLEM_POLY_OSEEN, 5: FS_PROBLEM_POLY_OSEEN_T}
 
 
 @dataclass

@@ -21,3 +21,10 @@ def poly_oseen(dim, n, jitter=0.1, seed=9):
                       hi=(1.0,) * dim, problem=W.POLY_OSEEN, nu=0.7, dt=0.05, steps=2,
                       jitter=jitter, seed=seed, side_mask=0x3F if dim == 3 else 0x0F,
                       pin_p0=True, wconst=(1.0, 0.5, 0.25)[:dim])
+
+
+def poly_oseen_t(dim, n, jitter=0.1, seed=9, steps=3):
+    """The time-affine polynomial Oseen problem: (1 + t) times the fields of
+    poly_oseen, reproduced exactly by backward Euler at every step."""
+    return poly_oseen(dim, n, jitter, seed).with_(name=f"poly_oseen_t_{dim}d",
+                                                  problem=W.POLY_OSEEN_T, steps=steps)

@@ -3,8 +3,10 @@
 these systems in test time, so it checks them one row at a time:
 
   * sampled rows of the GPU-assembled monolithic system (values and right-hand
-    side) against the same rows computed by the oracle from the elements that
-    contain the sampled nodes (1e-12 of the row's largest entry);
+    side; the velocity rows of every sampled node and the pressure rows of
+    every sampled vertex, B entries and b_p included) against the same rows
+    computed by the oracle from the elements that contain the sampled nodes
+    (1e-12 of the row's largest entry);
   * after one solved step: the global FP64 residual of the GPU solution with
     the GPU's exported system (<= 1e-12 relative, fs_csr_residual_norm), and
     the residual of sampled rows recomputed by the oracle (the solution
@@ -36,6 +38,7 @@ def _sample_nodes(P, k=24, seed=0):
     nodes = set(rng.choice(P.n2, k, replace=False).tolist())
     nodes |= {0, P.nv - 1, P.nv, P.n2 - 1}          # corners, first/last edge
     nodes |= set(np.where(P.mask)[0][:3].tolist())  # Dirichlet rows
+    nodes |= set(rng.choice(P.nv, 8, replace=False).tolist())  # pressure rows
     return sorted(nodes)
 
 
@@ -50,8 +53,6 @@ def _gather_rows(rp, rows, val_dev):
 @pytest.mark.parametrize("prec", [1, 0], ids=["fp32_refine", "fp64"])
 @pytest.mark.parametrize("wl", [W.C2, W.C3], ids=lambda w: w.name)
 def test_fullsize_sampled_rows_and_residual(fs, wl, prec):
-    if wl is W.C3 and prec == 0:
-        pytest.skip("the FP64 solve of the cube is covered by the smaller parity tests")
     S = fs.Stepper.from_workload(wl, precision=prec, dofmap_arrays=True)
     try:
         info = S.info

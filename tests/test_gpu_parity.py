@@ -14,13 +14,14 @@ import pytest
 
 import fs_workloads as W
 from oracle import oracle as O
-from tests.gpu_helpers import oracle_problem, poly_oseen, rel_l2
+from tests.gpu_helpers import oracle_problem, poly_oseen, poly_oseen_t, rel_l2
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 SMALL = [W.C1, W.unit_square(11, jitter=0.1, seed=3), W.channel(24, 8), W.cube(3),
-         W.cube(4, jitter=0.1, seed=2), poly_oseen(2, (5, 4)), poly_oseen(3, (2, 3, 2))]
+         W.cube(4, jitter=0.1, seed=2), poly_oseen(2, (5, 4)), poly_oseen(3, (2, 3, 2)),
+         poly_oseen_t(2, (5, 4)), poly_oseen_t(3, (2, 3, 2))]
 
 
 @pytest.fixture(scope="module")
@@ -113,6 +114,29 @@ def test_polynomial_exactness_on_gpu(fs, dim, n, prec):
         fs.fs_step(S.prob, 2)
         x, _ = S.state()
         assert np.abs(x - x0).max() <= 1e-10 * max(1.0, np.abs(x0).max())
+    finally:
+        S.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("dim,n", [(2, (5, 4)), (3, (2, 3, 2))])
+def test_time_affine_solution_exact_at_every_step(fs, dim, n, prec):
+    """(1 + t)(u0, p0) with (u0, p0) in P2 x P1 and a constant convecting
+    field: backward Euler with the load, Dirichlet data and pressure pin at
+    t^{n+1} reproduces the interpolant of the exact solution at every step
+    (paper Sec. 2.2.1, the time-discrete Oseen system); any of them at t^n
+    would leave an O(1) error."""
+    wl = poly_oseen_t(dim, n)
+    S = fs.Stepper.from_workload(wl, precision=prec)
+    try:
+        P = oracle_problem(wl)
+        for k in range(wl.steps):
+            st = fs.fs_step(S.prob, 1)[0]
+            assert st["status"] == 0
+            x, t = S.state()
+            u, p, _ = O.exact(wl.problem, dim, t, wl.nu, P.p2xyz, wl.wconst)
+            ref = np.concatenate([u.T.reshape(-1), p[:P.nv]])
+            assert np.abs(x - ref).max() <= 1e-10 * np.abs(ref).max(), k
     finally:
         S.close()
 

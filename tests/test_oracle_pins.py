@@ -441,3 +441,132 @@ def test_quadrature_rule_integrates_monomials():
                                                 (t, 0, 1 - s)), (s, 0, 1))
             q = np.sum(w * np.prod(lam ** np.array(ex), 1))
             assert abs(q - float(val)) < 1e-15
+
+
+# --------------------------------------------------------------------------
+# the time loop: time level of the load, the Dirichlet data and the pin
+# --------------------------------------------------------------------------
+def _poly_t(dim, n):
+    return W.Workload(name="poly_t", dim=dim, n=n, lo=(0.0,) * dim, hi=(1.0,) * dim,
+                      problem=W.POLY_OSEEN_T, nu=0.7, dt=0.05, steps=3, jitter=0.1,
+                      seed=9, side_mask=0x3F if dim == 3 else 0xF, pin_p0=True,
+                      wconst=(1.0, 0.5, 0.25)[:dim], init="exact")
+
+
+def _affine_fields(dim, x, t):
+    """Closed form of the time-affine polynomial solution, written out here:
+    u = (1 + t)(x^2, -2xy[, xy]), p = (1 + t)(x + y [+ z] - 1)."""
+    X, Y = x[:, 0], x[:, 1]
+    u = [X * X, -2 * X * Y] + ([X * Y] if dim == 3 else [])
+    p = X + Y - 1 + (x[:, 2] if dim == 3 else 0.0)
+    s = 1.0 + t
+    return s * np.concatenate(u), s * p
+
+
+def _run_affine(dim, n, steps=3):
+    P = _prob(_poly_t(dim, n))
+    errs = []
+    for _ in range(steps):
+        P.step()
+        ue, pe = _affine_fields(dim, P.p2xyz, P.t)
+        errs.append(max(np.abs(P.u - ue).max(), np.abs(P.p - pe[:P.nv]).max()))
+    return errs
+
+
+@pytest.mark.parametrize("dim,n", [(2, (4, 3)), (3, (2, 2, 2))])
+def test_time_loop_exact_for_field_affine_in_time(dim, n):
+    """Backward Euler differentiates a field affine in time exactly, and with
+    (u, p) in P2 x P1 and a constant convecting field the load is in P2, so
+    the stepper (load, Dirichlet data and pressure pin at t^{n+1}; paper
+    Sec. 2.2.1, the time-discrete Oseen system with f^{n+1}) reproduces the
+    interpolant of the exact solution at every step."""
+    errs = _run_affine(dim, n)
+    assert max(errs) < 1e-11, errs
+
+
+@pytest.mark.parametrize("what", ["load", "boundary"])
+def test_time_loop_pin_detects_data_at_the_old_time(monkeypatch, what):
+    """The pin above fails when the oracle takes the load, or the Dirichlet
+    data and pin, at t^n instead of t^{n+1} (a mistake planted in the oracle
+    for this test only)."""
+    if what == "load":
+        real = O.rhs
+
+        def lagged(dim, nv, n2, c2d, p2xyz, u_prev, problem, t, nu, inv_dt, wconst=None):
+            return real(dim, nv, n2, c2d, p2xyz, u_prev, problem, t - 0.05, nu, inv_dt, wconst)
+        monkeypatch.setattr(O, "rhs", lagged)
+    else:
+        real = O.apply_bc
+
+        def lagged(dim, nv, n2, rowptr, col, val, b, mask, p2xyz, problem, t, nu,
+                   pin_p0, wconst=None):
+            return real(dim, nv, n2, rowptr, col, val, b, mask, p2xyz, problem,
+                        t - 0.05, nu, pin_p0, wconst)
+        monkeypatch.setattr(O, "apply_bc", lagged)
+    errs = _run_affine(2, (4, 3))
+    assert max(errs) > 1e-4, errs
+
+
+# --------------------------------------------------------------------------
+# sampled rows (used by the full-size GPU checks) vs whole-mesh assembly
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("case", ["square", "cube", "channel"])
+def test_assemble_rows_match_global_assembly(case):
+    """O.assemble_rows computes rows of the system from the elements around
+    sampled nodes; it must equal the same rows of assemble + rhs + apply_bc
+    on the whole mesh, velocity and pressure rows alike (B entries, explicit
+    pressure diagonal, b_p = 0, the pinned row)."""
+    if case == "square":
+        P = _prob(W.unit_square(6))
+        P.t = 0.3
+        P.u, P.p = _exact_state(P, 0.3)
+    elif case == "cube":
+        P = _prob(W.cube(3, jitter=0.1, seed=4))
+        P.t = 0.4
+        P.u, P.p = _exact_state(P, 0.4)
+    else:
+        P = _prob(W.channel(8, 4, init="exact"))
+    rp, col, val, b = P.system(P.t + P.dt)
+    rng = np.random.default_rng(1)
+    nodes = sorted(set(rng.choice(P.n2, 12, replace=False).tolist())
+                   | {0, 1, P.nv - 1, P.nv, P.n2 - 1}
+                   | set(rng.choice(P.nv, 6, replace=False).tolist()))
+    rows, rhs = O.assemble_rows(P, nodes)
+    d, n2 = P.dim, P.n2
+    expect = set()
+    for g in nodes:
+        expect |= {a * n2 + g for a in range(d)}
+        if g < P.nv:
+            expect.add(d * n2 + g)
+    assert set(rows) == expect
+    for r, ref in rows.items():
+        cols = col[rp[r]:rp[r + 1]]
+        assert set(ref) == set(int(c) for c in cols), r
+        v = val[rp[r]:rp[r + 1]]
+        got = np.array([ref[int(c)] for c in cols])
+        scale = max(np.abs(v).max(), 1e-300)
+        assert np.abs(got - v).max() <= 1e-13 * scale, r
+        assert abs(rhs[r] - b[r]) <= 1e-13 * max(1.0, np.abs(b).max()), r
+    assert any(r >= d * n2 for r in rows)          # pressure rows were checked
+
+
+def _exact_state(P, t):
+    u, p, _ = O.exact(P.problem, P.dim, t, P.nu, P.p2xyz, P.wconst)
+    return np.ascontiguousarray(u.T.reshape(-1)), p[:P.nv].copy()
+
+
+def test_sparse_lu_matches_dense_lu_and_gmres():
+    """The sparse direct path (SuperLU + refinement) agrees with the dense LU
+    on the 8x8 square and with ILU(0)-GMRES on a jittered cube."""
+    P = _prob(W.C1)
+    rp, col, val, b = P.system(P.dt)
+    xd = O.dense_solve(O.csr_to_dense(rp, col, val), b)
+    xs, rr = O.sparse_lu_solve(rp, col, val, b)
+    assert rr <= 1e-14
+    assert np.linalg.norm(xs - xd) <= 1e-11 * np.linalg.norm(xd)
+    P = _prob(W.cube(4, jitter=0.1, seed=2))
+    rp, col, val, b = P.system(P.dt)
+    xs, rr = O.sparse_lu_solve(rp, col, val, b)
+    xg, rc, it, rg = O.gmres_ilu0(rp, col, val, b, rtol=1e-14)
+    assert rr <= 1e-14 and rc == 0
+    assert np.linalg.norm(xs - xg) <= 1e-11 * np.linalg.norm(xg)
