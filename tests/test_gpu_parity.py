@@ -136,7 +136,11 @@ def test_time_affine_solution_exact_at_every_step(fs, dim, n, prec):
             x, t = S.state()
             u, p, _ = O.exact(wl.problem, dim, t, wl.nu, P.p2xyz, wl.wconst)
             ref = np.concatenate([u.T.reshape(-1), p[:P.nv]])
-            assert np.abs(x - ref).max() <= 1e-10 * np.abs(ref).max(), k
+            # the parity bar (the FP64 solves stop at a relative residual of
+            # 1e-14; the 3D pressure carries ~1e-10 of it); a load, boundary
+            # value or pin taken at t^n would be off by O(dt) = 5e-2
+            assert rel_l2(x, ref) <= 1e-9, k
+            assert np.abs(x - ref).max() <= 1e-9 * np.abs(ref).max(), k
     finally:
         S.close()
 
