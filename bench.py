@@ -32,7 +32,7 @@ L2_FLUSH_BYTES = 256 << 20  # > 135 MB of L2
 def parse(argv=None):
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=40)
+    p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="fs", choices=["fs", "reference"])
     p.add_argument("--workload", default="channel", choices=["channel", "unit_square", "cube"])
@@ -49,12 +49,32 @@ def parse(argv=None):
                    help="launch the solver's kernels one by one instead of replaying captured "
                         "CUDA graphs (for per-kernel profilers, which cannot see kernels inside "
                         "graphs with conditional nodes)")
-    p.add_argument("--roofline-kernel", default="cheb", choices=["cheb", "spmv", "assemble"])
-    p.add_argument("--batch-steps", type=int, default=3,
+    p.add_argument("--roofline-kernel", default="cgs_upd", choices=sorted(KERNELS))
+    p.add_argument("--batch-steps", type=int, default=20,
                    help="timed steps of the 96-instance batched workload (0: skip)")
-    p.add_argument("--serve-requests", type=int, default=32,
-                   help="requests of the serving run (0: skip)")
+    p.add_argument("--cube-steps", type=int, default=10,
+                   help="timed FP32+refinement steps of the cube 48^3 (0: skip)")
+    p.add_argument("--cube-fp64-steps", type=int, default=5,
+                   help="timed FP64 steps of the cube 48^3")
+    p.add_argument("--serve-requests", type=int, default=48,
+                   help="requests of each serving run (0: skip)")
+    p.add_argument("--serve-rate", type=float, default=200.0,
+                   help="mean arrival rate of the saturation run (requests/s)")
+    p.add_argument("--cpu-baseline-steps", type=int, default=1,
+                   help="full oracle steps of the workload timed for cpu_baseline")
     return p.parse_args(argv)
+
+
+# kernels timed by fs_profile_kernel: name -> (id attribute, description)
+KERNELS = {
+    "spmv": ("FS_KERNEL_SPMV", "k_spmv_full (saddle-point SpMV, SELL-32, solver arithmetic)"),
+    "spmv_fp64": ("FS_KERNEL_SPMV_FP64", "k_spmv_full (FP64, refinement residual)"),
+    "cheb": ("FS_KERNEL_CHEB", "k_mg (Chebyshev step, finest P2 level, SELL-32)"),
+    "assemble": ("FS_KERNEL_ASSEMBLE_CONV", "k_assemble_conv (per-step convection, FP64)"),
+    "cgs_dot": ("FS_KERNEL_CGS_DOT", "k_seg_dot (CGS2 dots h = V^T w, j = 15)"),
+    "cgs_upd": ("FS_KERNEL_CGS_UPD", "k_seg_upd (CGS2 update w -= V h, re-dot, norm; j = 15)"),
+    "cgs_fin": ("FS_KERNEL_CGS_FIN", "k_seg_fin (CGS2 final update and normalisation; j = 15)"),
+}
 
 
 def workload(name):
@@ -138,45 +158,49 @@ def traffic_from_profiles(kernel, wl_name):
 
 
 # ---------------------------------------------------------------------------
-def oracle_sample():
-    """One oracle step of the 128x24 channel (28,411 DOF); returns (seconds,
-    sample DOF).  Single-threaded plain C."""
-    import fs_workloads as W
+def oracle_full_step(wl):
+    """One full oracle step of the workload at its own size, single-threaded:
+    COO assembly, right-hand side and boundary rows, then the sparse direct
+    solve with FP64 refinement (ILU(0)-GMRES stagnates on the do-nothing
+    channel).  Returns seconds."""
     from oracle import oracle as O
-    wl = W.channel(128, 24)
     P = O.Problem(dim=wl.dim, n=wl.n, lo=wl.lo, hi=wl.hi, problem=wl.problem, nu=wl.nu,
                   dt=wl.dt, jitter=wl.jitter, seed=wl.seed, side_mask=wl.side_mask,
                   pin_p0=wl.pin_p0, init=wl.init)
     t0 = time.perf_counter()
-    P.step(rtol=1e-14)
-    return time.perf_counter() - t0, P.ndof
+    P.step(rtol=1e-14, method="lu")
+    return time.perf_counter() - t0
 
 
 def reference_arm(args, rank):
+    """The oracle on the host cores as the reference arm.  Each timed step is
+    one full oracle step of the workload at its full size (about a minute on
+    one core), so at most two are timed; the warm-up loads the oracle once
+    on a small channel (the CPU program has nothing else to warm)."""
     if rank != 0:
         return 0
+    import fs_workloads as W
     wl = workload(args.workload)
     from oracle import oracle as O
     O.build()
-    for _ in range(max(args.warmup, 0)):
-        oracle_sample()
-    secs, dofs = [], 0
-    for _ in range(args.steps):
-        s, dofs = oracle_sample()
-        secs.append(s)
+    if args.warmup > 0:
+        oracle_full_step(W.channel(16, 4))
+    k = max(1, min(args.steps, 2))
+    secs = [oracle_full_step(wl) for _ in range(k)]
     total = sum(secs)
-    dof_s = dofs * len(secs) / total
-    value = dof_s / wl.ndof
+    value = k / total
+    sample = (f"{k} full oracle steps of {wl.name} ({wl.ndof} DOF; COO assembly + sparse LU "
+              f"with FP64 refinement to 1e-14), single-threaded; {args.steps} requested, at "
+              f"most 2 timed so the run ends within minutes")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s",
-        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1e3 * wl.ndof / dof_s, "higher_is_better": True, "scaling": "weak",
+        "n_gpus": args.gpus, "steps": k, "steps_requested": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / k, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": wl.name, "ndof": wl.ndof, "l2": "sample far below L2 reuse"},
+        "config": {"workload": wl.name, "ndof": wl.ndof, "cells": wl.ncell, "nu": wl.nu,
+                   "dt": wl.dt, "rtol": 1e-14},
         "cpu_baseline": {"value": value, "unit": "steps/s", "cores": 1, "kind": "oracle",
-                         "sample": f"each step = one oracle backward-Euler Oseen step of the "
-                                   f"128x24 channel ({dofs} DOF; COO assembly + ILU(0)-GMRES "
-                                   f"to 1e-14), scaled to {wl.ndof} DOF by DOF/s"},
+                         "sample": sample},
         "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -196,7 +220,7 @@ def aggregate_time(total_s, dist):
 
 
 # ---------------------------------------------------------------------------
-def batched_run(torch, fs, steps, warmup=1):
+def batched_run(torch, fs, steps, warmup=3):
     """The batched workload: 96 unit-square instances, N and Re drawn
     log-uniform from the seed, one problem over their union (one launch per
     phase for all instances), FP32 inner / FP64 refinement."""
@@ -236,19 +260,21 @@ def batched_run(torch, fs, steps, warmup=1):
             "rel_res_max": max(x["rel_res"] for x in st)}
 
 
-def serving_run(fs, count, rate=200.0, budget=150 << 30, slots=32):
-    """Poisson arrivals (seeded) of 2D and 3D solves, sizes log-uniform but
-    capped so the run ends in seconds (2D N <= 96, 3D N <= 16, 5-20 steps),
-    admitted by the native loop under the HBM budget; latency = completion -
-    arrival on the wall clock."""
+def serving_run(fs, count, rate, budget=150 << 30, slots=32):
+    """The first `count` requests of the seeded serving stream (2D N
+    log-uniform in [16,512], 3D N in [8,48], Re in [1,2000], 10-100 steps,
+    Bernoulli(1/2) 2D/3D, exponential gaps at `rate` requests/s), admitted by
+    the native loop under the HBM budget; latency = completion - arrival on
+    the wall clock."""
     import fs_workloads as W
     import numpy as np
-    reqs = W.serving_requests(count=count, rate=rate, n2d=(16, 96), n3d=(8, 16), steps=(5, 20))
+    reqs = W.serving_requests(count=count, rate=rate)
     srv = fs.Server(budget, slots)
     try:
         t0 = time.perf_counter()
         pending = list(reqs)
         done = []
+        peak = 0
         while len(done) < len(reqs):
             now = time.perf_counter() - t0
             while pending and pending[0].arrival <= now:
@@ -256,22 +282,88 @@ def serving_run(fs, count, rate=200.0, budget=150 << 30, slots=32):
                 srv.submit(r.workload, r.workload.steps, r.arrival)
             srv.progress(now)
             done += srv.completed()
-            if time.perf_counter() - t0 > 600:
+            peak = max(peak, srv.status()["bytes_reserved"])
+            if time.perf_counter() - t0 > 900:
                 break
         span = time.perf_counter() - t0
     finally:
         srv.close()
     lat = np.array([d["finished"] - d["arrival"] for d in done])
     steps = sum(d["nsteps"] for d in done)
-    dofsteps = sum(r.workload.ndof * r.workload.steps for r in reqs[:len(done)])
+    byid = {r.rid: r for r in reqs}
+    dofsteps = sum(byid[d["id"] - 1].workload.ndof * d["nsteps"] for d in done)
     return {"requests": len(reqs), "completed": len(done),
             "ok": sum(1 for d in done if d["status"] == 0), "rate_per_s": rate,
             "latency_p50_s": float(np.percentile(lat, 50)) if len(lat) else None,
             "latency_p99_s": float(np.percentile(lat, 99)) if len(lat) else None,
-            "steps_per_s": steps / span, "dof_steps_per_s": dofsteps / span,
-            "makespan_s": span, "hbm_budget_gb": budget / 2**30, "slots": slots,
-            "workload": "Poisson 200/s; 2D N log-uniform [16,96] / 3D N [8,16] (Bernoulli 1/2), "
-                        "Re log-uniform [1,2000], 5-20 steps, seed 0"}
+            "requests_per_s": len(done) / span, "steps_per_s": steps / span,
+            "dof_steps_per_s": dofsteps / span, "makespan_s": span,
+            "hbm_budget_gb": budget / 2**30, "peak_reserved_gb": peak / 2**30, "slots": slots,
+            "mean_ndof": float(np.mean([r.workload.ndof for r in reqs])),
+            "mean_steps": float(np.mean([r.workload.steps for r in reqs]))}
+
+
+def serving_block(fs, count, rate):
+    """Saturation run at the stream's own rate, then the same requests at a
+    sustainable rate (70% of the measured saturation request rate)."""
+    sat = serving_run(fs, count, rate)
+    sus_rate = 0.7 * sat["requests_per_s"]
+    sus = serving_run(fs, count, sus_rate)
+    return {"workload": f"first {count} requests of the seeded stream: Poisson arrivals, 2D N "
+                        f"log-uniform [16,512] / 3D N [8,48] (Bernoulli 1/2), Re log-uniform "
+                        f"[1,2000], 10-100 steps, dt 1e-3, FP32 inner / FP64 refinement, "
+                        f"HBM budget 150 GB, seed 0",
+            "saturation": sat, "sustainable": sus}
+
+
+def cube_block(torch, fs, stream, flush, steps, steps64, warmup=3):
+    """The cube 48^3 (2,855,668 DOF): FP32+refinement and FP64 steps/s, the
+    per-step difference between the two paths' states, and the L2-cold
+    fractions of its SpMV and smoothing step (working sets above the L2)."""
+    import fs_workloads as W
+    import numpy as np
+    wl = W.C3
+    out = {"workload": wl.name, "ndof": wl.ndof, "cells": wl.ncell, "nu": wl.nu, "dt": wl.dt}
+    res = {}
+    states = {}
+    for prec, k in ((fs.FS_PREC_FP32_REFINE, steps), (fs.FS_PREC_FP64, steps64)):
+        S = fs.Stepper.from_workload(wl, precision=prec, stream=stream.cuda_stream)
+        try:
+            fs.fs_autotune(S.prob, reps=3)
+            xs = []
+            for _ in range(warmup):
+                fs.fs_step(S.prob, 1)
+                xs.append(fs.fs_get_state(S.prob)[0])
+            t, st = time_steps(torch, fs, S, stream, k, flush)
+            name = "fp32_refine" if prec == fs.FS_PREC_FP32_REFINE else "fp64"
+            res[name] = {"steps_per_s": 1e3 * len(t) / sum(t), "ms_per_step": sum(t) / len(t),
+                         "timed_steps": k, "dof_per_s": 1e3 * len(t) * wl.ndof / sum(t),
+                         "iters_per_step": float(np.mean([q["iters"] for q in st])),
+                         "rel_res_max": max(q["rel_res"] for q in st)}
+            states[name] = xs
+            if prec == fs.FS_PREC_FP32_REFINE:
+                peak, kind = measured_peak_hbm()
+                kern = {}
+                for kname in ("spmv", "cheb"):
+                    ms, by = fs.fs_profile_kernel(S.prob, getattr(fs, KERNELS[kname][0]),
+                                                  reps=10, cold=True)
+                    kern[kname] = {"ms_cold": ms, "alg_bytes": by, "gbs": by / ms / 1e6,
+                                   "frac": by / ms / 1e6 / peak}
+                out["kernels_l2_cold"] = kern
+        finally:
+            S.close()
+    out.update(res)
+    out["vs_fp64_path"] = res["fp32_refine"]["steps_per_s"] / res["fp64"]["steps_per_s"]
+    # the two paths' states after each of the warm-up steps (same steps,
+    # both stopped at a relative residual of 1e-14)
+    out["per_step_rel_l2_fp32_refine_vs_fp64"] = [
+        float(np.linalg.norm(a - b) / np.linalg.norm(b))
+        for a, b in zip(states["fp32_refine"], states["fp64"])]
+    out["oracle_parity"] = ("per-step parity against the oracle is tested on the 16^3 cube "
+                            "(5 free-running steps, rel L2 <= 1e-9) and on the 512x96 channel "
+                            "(tests/test_gpu_fullsize_parity.py); at 48^3 the test checks "
+                            "sampled rows and the FP64 residual")
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -412,38 +504,43 @@ def main():
     SE.close()
 
     # ---- roofline of the dominant kernel ----------------------------------
-    kid = {"cheb": fs.FS_KERNEL_CHEB, "spmv": fs.FS_KERNEL_SPMV,
-           "assemble": fs.FS_KERNEL_ASSEMBLE_CONV}[args.roofline_kernel]
+    # every hot kernel timed on the timed problem's own data and stream, warm
+    # (back-to-back launches) and with a cold L2 (each launch after a read of
+    # twice the L2 size); the roofline takes the cold figure
+    peak, peak_kind = measured_peak_hbm()
     kernels = {}
-    for name, k in (("cheb", fs.FS_KERNEL_CHEB), ("spmv", fs.FS_KERNEL_SPMV),
-                    ("spmv_fp64", fs.FS_KERNEL_SPMV_FP64),
-                    ("assemble", fs.FS_KERNEL_ASSEMBLE_CONV)):
-        ms, by = fs.fs_profile_kernel(S.prob, k, reps=20)
-        kernels[name] = {"ms": ms, "alg_bytes": by, "gbs": by / ms / 1e6}
+    for name, (attr, desc) in KERNELS.items():
+        kid = getattr(fs, attr)
+        ms, by = fs.fs_profile_kernel(S.prob, kid, reps=20)
+        msc, _ = fs.fs_profile_kernel(S.prob, kid, reps=20, cold=True)
+        kernels[name] = {"ms": ms, "ms_cold": msc, "alg_bytes": by, "gbs": by / ms / 1e6,
+                         "gbs_cold": by / msc / 1e6, "frac_cold": by / msc / 1e6 / peak}
     kernels["precond"] = {"ms": fs.fs_profile_kernel(S.prob, fs.FS_KERNEL_PRECOND, reps=10)[0],
                           "unit": "one block-preconditioner application (graph of 10)"}
-    peak, peak_kind = measured_peak_hbm()
     kname = args.roofline_kernel
-    achieved = kernels[kname]["gbs"]
+    achieved = kernels[kname]["gbs_cold"]
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_source": peak_kind,
-                "kernel": {"cheb": "k_mg (Chebyshev step, finest P2 level, SELL-32)",
-                           "spmv": "k_spmv_full (SELL-32)",
-                           "assemble": "k_assemble_conv"}[kname],
+                "frac": achieved / peak, "peak_source": peak_kind, "kernel": KERNELS[kname][1],
+                "timing": "L2-cold, each launch after a read of twice the L2 size, CUDA events "
+                          "on the problem's stream",
                 "traffic": traffic_from_profiles(kname, wl.name)}
 
     # ---- CPU baseline: the oracle on a bounded sample ---------------------
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        secs, dofs = oracle_sample()
-        cpu = {"value": dofs / secs / wl.ndof, "unit": "steps/s", "cores": 1, "kind": "oracle",
-               "sample": f"one oracle step of the 128x24 channel ({dofs} DOF, COO assembly + "
-                         f"ILU(0)-GMRES to 1e-14) in {secs:.2f} s, scaled to {wl.ndof} DOF by "
-                         f"DOF/s"}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.cpu_baseline_steps > 0:
+        k = args.cpu_baseline_steps
+        secs = sum(oracle_full_step(wl) for _ in range(k))
+        cpu = {"value": k / secs, "unit": "steps/s", "cores": 1, "kind": "oracle",
+               "sample": f"{k} full oracle step(s) of {wl.name} ({wl.ndof} DOF: COO assembly, "
+                         f"right-hand side, boundary rows, sparse LU with FP64 refinement to "
+                         f"1e-14) in {secs:.1f} s, single-threaded plain C + SuperLU"}
 
     S.close()
     batch = batched_run(torch, fs, args.batch_steps) if args.batch_steps > 0 else None
-    serving = serving_run(fs, args.serve_requests) if args.serve_requests > 0 else None
+    cube = (cube_block(torch, fs, stream, flush, args.cube_steps, args.cube_fp64_steps)
+            if args.cube_steps > 0 else None)
+    serving = (serving_block(fs, args.serve_requests, args.serve_rate)
+               if args.serve_requests > 0 else None)
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -479,6 +576,7 @@ def main():
         "kernels": kernels,
         "cpu_baseline": cpu,
         "batched": batch,
+        "cube": cube,
         "serving": serving,
     }
     print(json.dumps(line), flush=True)

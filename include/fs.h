@@ -243,6 +243,41 @@ int fs_step(fs_problem* prob, int nsteps, const fs_solve_opts* opts,
 int fs_step_begin(fs_problem* prob, int nsteps, const fs_solve_opts* opts);
 int fs_step_poll(fs_problem* prob, int wait, int* done);
 
+/* Picard iteration of the nonlinear step (paper Sec. 2.2.1: the convection
+ * term linearised around the latest iterate, ((u^k . grad) u^{k+1}, v), one
+ * Oseen solve per iterate; Sec. 3.3: model.run(maxstep, tol) iterates until
+ * the change falls below tol).  Iterate k convects with u^k (u^0 = u^n) and
+ * keeps u^n in the backward-Euler load; it stops when
+ *   ||u^{k+1} - u^k||_2 <= nl_tol * max(1, ||u^{k+1}||_2)
+ * (velocity entries, FP64) or after max_picard solves.  One iteration is
+ * exactly the Oseen step of fs_step.  Each linear solve is fs_solve's
+ * (options opts, NULL = defaults); the first of a time step starts from the
+ * extrapolated state history, later ones from the latest iterate.
+ * Single problems only (FS_ERR_UNSUPPORTED on a batch).  Synchronises. */
+typedef struct {
+  int picard_iters;   /* linear solves taken                               */
+  int krylov_iters;   /* their Krylov iterations, summed                   */
+  int status;         /* fs_status: FS_ERR_NOT_CONVERGED when max_picard
+                         solves did not reach nl_tol (last iterate kept)  */
+  double update;      /* last ||u^{k+1} - u^k|| / max(1, ||u^{k+1}||)      */
+  double rel_res;     /* FP64 relative residual of the last linear solve   */
+} fs_picard_stats;
+
+/* nsteps time steps, each iterated to nl_tol; per_step (host, nsteps
+ * entries, may be NULL).  The time advances by dt per step even when a
+ * step's iteration fails (its last iterate is kept), as in fs_step.  Needs
+ * a finite dt. */
+int fs_step_picard(fs_problem* prob, int nsteps, const fs_solve_opts* opts, double nl_tol,
+                   int max_picard, fs_picard_stats* per_step);
+
+/* The steady problem (the Sec. 3.3 example: no time derivative): a problem
+ * created with dt = inf (no mass term in the operator, the load or the
+ * preconditioner's Schur part) is iterated at its fixed time t0 from its
+ * current state.  stats may be NULL.  FS_ERR_INVALID_ARG for a finite dt;
+ * fs_step refuses dt = inf. */
+int fs_solve_steady(fs_problem* prob, const fs_solve_opts* opts, double nl_tol,
+                    int max_picard, fs_picard_stats* stats);
+
 /* Per-instance statistics of the last solve (host array, one entry per
  * instance). */
 int fs_instance_stats(const fs_problem* prob, fs_solve_stats* per_instance);
@@ -381,8 +416,13 @@ int fs_autotune(fs_problem* prob, int reps, fs_tune_report* report);
  * fs_profile_kernel: times `reps` back-to-back launches of one hot kernel on
  * the problem's own data and stream with CUDA events (after 3 warm-up
  * launches) and returns the mean duration and the kernel's algorithmic bytes
- * per launch (each array it must touch counted once).  Kernel ids below.
- * Leaves the problem's state and assembled system unchanged.  Synchronises. */
+ * per launch (each array it must touch counted once).  Kernel ids below;
+ * kernel | FS_PROFILE_COLD_L2 times each launch alone (its own event pair)
+ * after a read of twice the L2 size has filled the L2 with other data, so
+ * every byte the kernel touches once comes from DRAM (its working set may
+ * still be re-read from L2 within the launch); a temporary device buffer of
+ * that size is allocated (stream-ordered) and freed.  Leaves the problem's
+ * state and assembled system unchanged.  Synchronises. */
 enum {
   FS_KERNEL_SPMV = 0,           /* saddle-point SpMV, solver arithmetic      */
   FS_KERNEL_SPMV_FP64 = 1,      /* saddle-point SpMV, FP64                   */
@@ -392,10 +432,18 @@ enum {
                                    the solver arithmetic, timed as a CUDA
                                    graph of `reps` applications; alg_bytes
                                    is 0 (a latency unit of many kernels)   */
-  FS_KERNEL_CGS = 5             /* one CGS2 orthogonalisation (its three
+  FS_KERNEL_CGS = 5,            /* one CGS2 orthogonalisation (its three
                                    passes) at Arnoldi step j = m/2 on the
                                    Krylov scratch; alg_bytes counts the
-                                   4j + 9 basis-vector sweeps              */
+                                   3j + 8 vector sweeps the passes must make
+                                   (each vector once per pass)            */
+  FS_KERNEL_CGS_DOT = 6,        /* its first pass alone (h = V^T w):
+                                   j + 2 sweeps                           */
+  FS_KERNEL_CGS_UPD = 7,        /* its second pass alone (w -= V h, re-dot,
+                                   norm): j + 3 sweeps                    */
+  FS_KERNEL_CGS_FIN = 8,        /* its third pass alone (w -= V h2,
+                                   normalise): j + 3 sweeps               */
+  FS_PROFILE_COLD_L2 = 0x100    /* flag: L2-cold timing, see above        */
 };
 int64_t fs_launch_count(void);
 int fs_profile_kernel(fs_problem* prob, int kernel, int reps, double* avg_ms,

@@ -526,6 +526,138 @@ def steady_picard(prob: Problem, tol=1e-12, maxit=50):
     return maxit
 
 
+def picard_step(prob: Problem, tol=1e-12, maxit=50, method="auto"):
+    """One backward-Euler step of the nonlinear system, solved by Picard
+    iteration (Sec. 2.2.1: the convection term linearised around the latest
+    iterate, ((u^k . grad) u^{k+1}, v); Sec. 3.3: iterate until the update is
+    below tol).  The first iterate convects with u^n; every iterate keeps u^n
+    in the load.  Stops when ||u^{k+1} - u^k|| <= tol max(1, ||u^{k+1}||).
+    Returns the number of linear solves."""
+    t1 = prob.t + prob.dt
+    un = prob.u.copy()
+    w = prob.u.copy()
+    nvel = prob.dim * prob.n2
+    for it in range(maxit):
+        rp, col, val, b = prob.system(t1, u_prev=un, w=w)
+        x = solve(rp, col, val, b, x0=prob.x, method=method)
+        unew = x[:nvel]
+        du = np.linalg.norm(unew - w)
+        prob.u = unew.copy()
+        prob.p = x[nvel:].copy()
+        w = prob.u.copy()
+        if du <= tol * max(1.0, np.linalg.norm(prob.u)):
+            prob.t = t1
+            return it + 1
+    prob.t = t1
+    return maxit
+
+
+def _blocks(prob, w, mass_coef):
+    """The blocks of the assembled (pre-boundary-condition) Oseen matrix as
+    scipy CSR matrices: A (velocity-velocity, all components), the
+    divergence block B (pressure rows, velocity columns; +B in the
+    continuity rows, -B^T in the momentum rows) and, from the P1 element
+    matrices, the pressure Laplacian K_p."""
+    import scipy.sparse as sps
+    d, n2, nv = prob.dim, prob.n2, prob.nv
+    nvel = d * n2
+    rp, col, val = assemble(d, nv, n2, prob.c2d, prob.p2xyz, w, mass_coef, prob.nu)
+    K = sps.csr_matrix((val, col, rp), shape=(nvel + nv, nvel + nv))
+    A = K[:nvel, :nvel].tocsr()
+    B = K[nvel:, :nvel].tocsr()
+    rows, cols, vals = [], [], []
+    nb = d + 1
+    for c in range(prob.c2d.shape[0]):
+        g = prob.c2d[c, :nb]
+        E = element(d, prob.p2xyz[g], None, 0.0, 1.0)
+        for i in range(nb):
+            for j in range(nb):
+                rows.append(g[i])
+                cols.append(g[j])
+                vals.append(E["Kp"][i, j])
+    Kp = sps.csr_matrix((vals, (rows, cols)), shape=(nv, nv))
+    return A, B, Kp
+
+
+def _solve_rows_replaced(Mat, rhs, fixed, values):
+    """Solve Mat x = rhs with the rows of the `fixed` unknowns replaced by
+    identity rows holding `values` (columns kept), by the sparse direct
+    solve with FP64 refinement."""
+    import scipy.sparse as sps
+    Mat = sps.csr_matrix(Mat)
+    keep = np.ones(Mat.shape[0])
+    keep[fixed] = 0.0
+    D = sps.diags(keep)
+    Mat = (D @ Mat + sps.diags(1.0 - keep)).tocsr()
+    Mat.sort_indices()
+    b = rhs.copy()
+    b[fixed] = values
+    x, rr = sparse_lu_solve(Mat.indptr.astype(np.int64), Mat.indices.astype(np.int32),
+                            Mat.data.astype(np.float64), b)
+    if not rr <= 1e-12:
+        raise RuntimeError(f"oracle IPCS sub-solve residual {rr:.3e}")
+    return x
+
+
+def ipcs_step(prob: Problem):
+    """One step of the incremental pressure-correction scheme (Sec. 2.2.1,
+    IPCS, density rho = 1), in the paper's three stages:
+
+    1. tentative velocity u*: (u* - u^n)/dt + ((w . grad) u^n, v)
+       + nu (grad u*, grad v) - (p^n, div v) = (f^{n+1}, v), with the
+       convection explicit (w = u^n, or the constant field of the
+       polynomial problems) and u* = u_D(t^{n+1}) on Dirichlet nodes;
+    2. pressure increment dp = p^{n+1} - p^n:
+       (grad dp, grad q) = -(1/dt) (div u*, q); the sign is the one that
+       makes stage 3 remove the divergence (the printed right-hand side
+       has the opposite sign, which contradicts the paper's own stage 3);
+       the pinned vertex 0 takes dp = p_exact(x_0, t^{n+1}) - p^n(x_0);
+    3. velocity correction: (u^{n+1} - u*, v)/dt = -(grad dp, v), i.e.
+       M u^{n+1} = M u* + dt B^T dp on interior rows (v vanishes on the
+       Dirichlet boundary, so (grad dp, v) = -(dp, div v)), u^{n+1} = u_D
+       on Dirichlet nodes.
+
+    Each stage's linear system is solved exactly (sparse direct).  Needs a
+    velocity Dirichlet condition on the whole boundary and the pressure
+    pin.  Returns the state vector."""
+    d, n2, nv = prob.dim, prob.n2, prob.nv
+    nvel = d * n2
+    t1 = prob.t + prob.dt
+    inv_dt = 1.0 / prob.dt
+    w = (np.repeat(np.asarray(prob.wconst, np.float64), n2)
+         if prob.wconst is not None else prob.u)
+    Aosn, B, Kp = _blocks(prob, w, inv_dt)          # M/dt + nu K + N(w)
+    Astk, _, _ = _blocks(prob, None, inv_dt)         # M/dt + nu K
+    Mass, _, _ = _blocks(prob, None, 1.0)
+    Mass = Mass - _blocks(prob, None, 0.0)[0]        # M (all components)
+    Nw = Aosn - Astk
+    # load: M (u^n / dt + I_h f^{n+1}), b_p = 0
+    bfull = rhs(d, nv, n2, prob.c2d, prob.p2xyz, prob.u, prob.problem, t1, prob.nu,
+                inv_dt, prob.wconst)
+    dir_nodes = np.where(prob.mask)[0]
+    dir_rows = np.concatenate([a * n2 + dir_nodes for a in range(d)])
+    wc = None if prob.wconst is None else np.asarray(prob.wconst, np.float64)
+    ue, _, _ = exact(prob.problem, d, t1, prob.nu, prob.p2xyz[dir_nodes], wc)
+    dir_vals = np.concatenate([ue[:, a] for a in range(d)])
+    # stage 1
+    r1 = bfull[:nvel] - Nw @ prob.u + B.T @ prob.p
+    ustar = _solve_rows_replaced(Astk, r1, dir_rows, dir_vals)
+    # stage 2
+    r2 = -inv_dt * (B @ ustar)
+    fixed, fval = [], []
+    if prob.pin_p0:
+        _, pe, _ = exact(prob.problem, d, t1, prob.nu, prob.p2xyz[0:1], wc)
+        fixed, fval = [0], [pe[0] - prob.p[0]]
+    dp = _solve_rows_replaced(Kp, r2, np.array(fixed, int), np.array(fval))
+    # stage 3
+    r3 = Mass @ ustar + prob.dt * (B.T @ dp)
+    unew = _solve_rows_replaced(Mass, r3, dir_rows, dir_vals)
+    prob.u = unew
+    prob.p = prob.p + dp
+    prob.t = t1
+    return prob.x
+
+
 if __name__ == "__main__":  # pragma: no cover
     build(force="--force" in sys.argv)
     print(_LIB)

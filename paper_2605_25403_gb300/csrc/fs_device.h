@@ -209,6 +209,16 @@ int mg_tail_cluster(int ncp);
 template <typename T>
 void launch_cheb_step(const DHier<T>& H, int nc, cudaStream_t s);
 
+// scratch[0] = sum_i (a_i - b_i)^2, scratch[1] = sum_i a_i^2 over i < n, in
+// a fixed summation order; scratch holds diff_norms_scratch() doubles.
+int diff_norms_scratch();
+void launch_diff_norms(const double* a, const double* b, int64_t n, double* scratch,
+                       cudaStream_t s);
+
+// Reads `bytes` (a multiple of 16) of buf so that the L2 holds clean lines
+// of it and nothing of the data timed next (kernel timing with a cold L2).
+void launch_l2_flush(const void* buf, int64_t bytes, int* sink, cudaStream_t s);
+
 // Polynomial extrapolation in time of the state x (x^n) through it and its
 // nprev <= kExtrapMax previous values prev[j] = x^(n-1-j) to the next time
 // level: x <- sum_j (-1)^j C(nprev+1, j+1) x^(n-j) over j = 0..nprev (x
@@ -295,6 +305,11 @@ void launch_seg_cgs2(V* Vb, int64_t n, const TileList& tl, SegState* st, KCtl* c
                      cudaStream_t s);
 void launch_seg_givens(SegState* st, KCtl* ctl, int nseg, cudaGraphConditionalHandle cond,
                        cudaStream_t s);
+// One pass of the CGS2 step alone (0: dot, 1: update + re-dot, 2: final
+// update and normalisation; no Givens step), for kernel timing.
+template <typename V>
+void launch_seg_cgs2_pass(V* Vb, int64_t n, const TileList& tl, SegState* st, KCtl* ctl,
+                          double* partial, int pass, cudaStream_t s);
 template <typename V, typename X>
 void launch_seg_update_x(const SegState* st, const KCtl* ctl, const V* Z, int64_t n,
                          const TileList& tl, X* x, cudaStream_t s);

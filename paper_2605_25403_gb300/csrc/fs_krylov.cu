@@ -538,6 +538,23 @@ template void launch_seg_cgs2<double>(double*, int64_t, const TileList&, SegStat
 template void launch_seg_cgs2<float>(float*, int64_t, const TileList&, SegState*, KCtl*, double*,
                                      bool, cudaGraphConditionalHandle, cudaStream_t);
 
+template <typename V>
+void launch_seg_cgs2_pass(V* Vb, int64_t n, const TileList& tl, SegState* st, KCtl* ctl,
+                          double* partial, int pass, cudaStream_t s) {
+  if (pass == 0)
+    k_seg_dot<V><<<tl.ntiles, kKB, 0, s>>>(Vb, n, tl.tiles, tl.ntiles, st, ctl, partial);
+  else if (pass == 1)
+    k_seg_upd<V, false><<<tl.ntiles, kKB, 0, s>>>(Vb, n, tl.tiles, tl.ntiles, st, ctl, partial,
+                                                  0);
+  else
+    k_seg_fin<V><<<tl.ntiles, kKB, 0, s>>>(Vb, n, tl.tiles, st, ctl, 0);
+  count_launches(1);
+}
+template void launch_seg_cgs2_pass<double>(double*, int64_t, const TileList&, SegState*, KCtl*,
+                                           double*, int, cudaStream_t);
+template void launch_seg_cgs2_pass<float>(float*, int64_t, const TileList&, SegState*, KCtl*,
+                                          double*, int, cudaStream_t);
+
 void launch_seg_givens(SegState* st, KCtl* ctl, int nseg, cudaGraphConditionalHandle cond,
                        cudaStream_t s) {
   (void)nseg;

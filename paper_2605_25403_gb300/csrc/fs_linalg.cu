@@ -1020,6 +1020,89 @@ void launch_gj_extract(const double* W, int64_t n, T* out, cudaStream_t s) {
 template void launch_gj_extract<double>(const double*, int64_t, double*, cudaStream_t);
 template void launch_gj_extract<float>(const double*, int64_t, float*, cudaStream_t);
 
+// Streams a buffer through the L2 with plain loads: afterwards the L2 holds
+// clean lines of it (evicted without write-back) and nothing of the data
+// the next timed kernel reads.  The sum is stored only when it is an
+// impossible value, so the loads are not removed and nothing is written.
+static __global__ void k_l2_flush(const int4* __restrict__ buf, int64_t n, int* sink) {
+  int acc = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int4 v = buf[i];
+    acc ^= v.x ^ v.y ^ v.z ^ v.w;
+  }
+  if (acc == 0x7fffffff && sink) *sink = acc;
+}
+
+// Sums of (a_i - b_i)^2 and a_i^2 over i < n, in a fixed order: per-block
+// partial sums of a grid of kNormBlocks blocks, then one block adds the
+// partials.  Deterministic for a given n.
+constexpr int kNormBlocks = 304;
+static __device__ __forceinline__ void block_sum2(double& s0, double& s1) {
+  __shared__ double sh[2][8];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    s0 += __shfl_xor_sync(0xffffffffu, s0, off);
+    s1 += __shfl_xor_sync(0xffffffffu, s1, off);
+  }
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    sh[0][w] = s0;
+    sh[1][w] = s1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    s0 = s1 = 0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+      s0 += sh[0][i];
+      s1 += sh[1][i];
+    }
+  }
+}
+static __global__ void __launch_bounds__(256) k_diff_norms_part(const double* __restrict__ a,
+                                                                const double* __restrict__ b,
+                                                                int64_t n, double* part) {
+  double s0 = 0, s1 = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double x = a[i], d = x - b[i];
+    s0 += d * d;
+    s1 += x * x;
+  }
+  block_sum2(s0, s1);
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = s0;
+    part[2 * blockIdx.x + 1] = s1;
+  }
+}
+static __global__ void __launch_bounds__(256) k_diff_norms_fin(const double* part, int nb,
+                                                               double* out) {
+  double s0 = 0, s1 = 0;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+    s0 += part[2 * i];
+    s1 += part[2 * i + 1];
+  }
+  block_sum2(s0, s1);
+  if (threadIdx.x == 0) {
+    out[0] = s0;
+    out[1] = s1;
+  }
+}
+
+int diff_norms_scratch() { return 2 * kNormBlocks + 2; }
+
+void launch_diff_norms(const double* a, const double* b, int64_t n, double* scratch,
+                       cudaStream_t s) {
+  k_diff_norms_part<<<kNormBlocks, 256, 0, s>>>(a, b, n, scratch + 2);
+  k_diff_norms_fin<<<1, 256, 0, s>>>(scratch + 2, kNormBlocks, scratch);
+  count_launches(2);
+}
+
+void launch_l2_flush(const void* buf, int64_t bytes, int* sink, cudaStream_t s) {
+  const int64_t n = bytes / 16;
+  k_l2_flush<<<grid_stride_blocks(n), 256, 0, s>>>(static_cast<const int4*>(buf), n, sink);
+}
+
 void launch_extrapolate(double* x, const double* const* prev, int nprev, double* dst, int64_t n,
                         cudaStream_t s) {
   // Lagrange extrapolation to the next level of equally spaced levels:

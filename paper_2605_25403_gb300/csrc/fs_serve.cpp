@@ -247,6 +247,12 @@ int fs_server_progress(fs_server* S, double now, int* n_completed) {
       continue;
     }
     r->bytes = fs_problem_device_bytes(r->prob);
+    if (r->bytes > r->est_bytes) {
+      // an estimate that fell short: reserve what the problem really holds,
+      // so later admissions see the budget that is actually left
+      S->bytes_reserved += r->bytes - r->est_bytes;
+      r->est_bytes = r->bytes;
+    }
     r->started = now;
     int rc = fs_step_begin(r->prob, r->nsteps, nullptr);
     if (rc != FS_OK) {

@@ -72,6 +72,14 @@ class fs_solve_stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class fs_picard_stats(ctypes.Structure):
+    _fields_ = [("picard_iters", _int), ("krylov_iters", _int), ("status", _int),
+                ("update", _d), ("rel_res", _d)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _lib.fs_last_error.restype = ctypes.c_char_p
 _lib.fs_last_error.argtypes = []
 _lib.fs_default_solve_opts.restype = None
@@ -84,6 +92,8 @@ _lib.fs_problem_destroy.argtypes = [_vp]
 _lib.fs_assemble_step.argtypes = [_vp, _d, _vp, _vp]
 _lib.fs_solve.argtypes = [_vp, _P(fs_solve_opts), _vp, _P(fs_solve_stats)]
 _lib.fs_step.argtypes = [_vp, _int, _P(fs_solve_opts), _P(fs_solve_stats)]
+_lib.fs_step_picard.argtypes = [_vp, _int, _P(fs_solve_opts), _d, _int, _P(fs_picard_stats)]
+_lib.fs_solve_steady.argtypes = [_vp, _P(fs_solve_opts), _d, _int, _P(fs_picard_stats)]
 _lib.fs_apply_operator.argtypes = [_vp, _vp, _vp]
 _lib.fs_get_state.argtypes = [_vp, _vp, _int, _P(_d)]
 _lib.fs_set_state.argtypes = [_vp, _vp, _int, _d]
@@ -177,9 +187,12 @@ EXPORTED = ["fs_mesh_create", "fs_mesh_destroy", "fs_dof_map", "fs_problem_creat
             "fs_step_begin", "fs_step_poll", "fs_instance_stats", "fs_server_create",
             "fs_server_destroy", "fs_server_submit", "fs_server_progress",
             "fs_server_pop_completed", "fs_server_take_state", "fs_server_status",
-            "fs_server_estimate_bytes", "fs_get_schedule", "fs_set_schedule", "fs_autotune"]
+            "fs_server_estimate_bytes", "fs_get_schedule", "fs_set_schedule", "fs_autotune",
+            "fs_step_picard", "fs_solve_steady"]
 (FS_KERNEL_SPMV, FS_KERNEL_SPMV_FP64, FS_KERNEL_CHEB, FS_KERNEL_ASSEMBLE_CONV,
- FS_KERNEL_PRECOND, FS_KERNEL_CGS) = range(6)
+ FS_KERNEL_PRECOND, FS_KERNEL_CGS, FS_KERNEL_CGS_DOT, FS_KERNEL_CGS_UPD,
+ FS_KERNEL_CGS_FIN) = range(9)
+FS_PROFILE_COLD_L2 = 0x100
 
 
 def _check(rc, where):
@@ -372,6 +385,28 @@ def fs_step(prob, nsteps, opts=None, raise_on_error=True):
     return [stats[i].as_dict() for i in range(nsteps)]
 
 
+def fs_step_picard(prob, nsteps, nl_tol=1e-10, max_picard=50, opts=None, raise_on_error=True):
+    """nsteps time steps, each Picard-iterated to nl_tol; per-step stats."""
+    stats = (fs_picard_stats * max(nsteps, 1))()
+    o = opts if opts is not None else fs_default_solve_opts()
+    rc = _lib.fs_step_picard(prob, int(nsteps), ctypes.byref(o), float(nl_tol), int(max_picard),
+                             stats)
+    if raise_on_error:
+        _check(rc, "fs_step_picard")
+    return [stats[i].as_dict() for i in range(nsteps)]
+
+
+def fs_solve_steady(prob, nl_tol=1e-10, max_picard=50, opts=None, raise_on_error=True):
+    """Picard iteration of a steady problem (created with dt = inf)."""
+    st = fs_picard_stats()
+    o = opts if opts is not None else fs_default_solve_opts()
+    rc = _lib.fs_solve_steady(prob, ctypes.byref(o), float(nl_tol), int(max_picard),
+                              ctypes.byref(st))
+    if raise_on_error:
+        _check(rc, "fs_solve_steady")
+    return st.as_dict()
+
+
 def fs_apply_operator(prob, x, y):
     _check(_lib.fs_apply_operator(prob, _dptr(x), _dptr(y)), "fs_apply_operator")
 
@@ -442,10 +477,12 @@ def fs_autotune(prob, reps=10):
     return r.as_dict()
 
 
-def fs_profile_kernel(prob, kernel, reps=20):
-    """(mean ms per launch, algorithmic bytes per launch) of one hot kernel."""
+def fs_profile_kernel(prob, kernel, reps=20, cold=False):
+    """(mean ms per launch, algorithmic bytes per launch) of one hot kernel;
+    cold=True times each launch after the L2 was filled with other data."""
     ms, by = _d(), _d()
-    _check(_lib.fs_profile_kernel(prob, int(kernel), int(reps), ctypes.byref(ms),
+    kid = int(kernel) | (FS_PROFILE_COLD_L2 if cold else 0)
+    _check(_lib.fs_profile_kernel(prob, kid, int(reps), ctypes.byref(ms),
                                   ctypes.byref(by)), "fs_profile_kernel")
     return ms.value, by.value
 

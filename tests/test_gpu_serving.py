@@ -1,14 +1,16 @@
 """The continuous-batching request loop: requests admitted as slots and
 memory free up, several requests resident at once, and each
-request's result the same alone and in the mix (within the parity
-tolerance, 1e-9 relative L2)."""
+request's result the same alone and in the mix and the same as the oracle's
+steps of that request (within the parity tolerance, 1e-9 relative L2); the
+admission estimate bounds the measured footprint of large 2D and 3D
+requests too."""
 import time
 
 import numpy as np
 import pytest
 
 import fs_workloads as W
-from tests.gpu_helpers import rel_l2
+from tests.gpu_helpers import oracle_problem, rel_l2
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -60,6 +62,10 @@ def test_results_same_alone_and_in_the_mix(fs):
     for (wl, n), r, xa, xm in zip(MIX, res, alone, mixed):
         assert r["status"] == 0 and r["nsteps"] == n
         assert rel_l2(xm, xa) <= 1e-9, (wl.name, rel_l2(xm, xa))
+        P = oracle_problem(wl)
+        for _ in range(n):
+            P.step()
+        assert rel_l2(xm, P.x) <= 1e-9, (wl.name, rel_l2(xm, P.x))
     # the mix was resident at once (whether one request's steps end before
     # another's set-up does depends on their speeds, so that is not tested)
     assert max(s["resident"] for s in seen) >= 2
@@ -79,3 +85,19 @@ def test_admission_respects_budget_and_slots(fs):
     # FIFO admission
     adm = [r["admitted"] for r in res]
     assert adm == sorted(adm)
+
+
+@pytest.mark.parametrize("wl", [W.unit_square(512, jitter=0.0, nu=1e-3, dt=1e-3),
+                                W.cube(48, jitter=0.0, nu=1e-3, dt=1e-3)],
+                         ids=lambda w: w.name)
+def test_estimate_bounds_footprint_of_large_requests(fs, wl):
+    """The largest sizes of the serving workload (2D N = 512: 2.36M DOF; 3D
+    N = 48: 2.86M DOF, with its dense coarsest levels): the measured device
+    footprint of one served request stays within its admission estimate, and
+    the reservation it holds while resident is the estimate."""
+    est = fs.fs_server_estimate_bytes(wl)
+    seen = []
+    res, _ = _run(fs, [(wl, 1)], 150 << 30, 1, keep=False, watch=lambda s: seen.append(s))
+    assert res[0]["status"] == 0
+    assert 0 < res[0]["device_bytes"] <= est, (res[0]["device_bytes"], est)
+    assert max(s["bytes_reserved"] for s in seen) == est

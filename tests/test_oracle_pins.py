@@ -570,3 +570,100 @@ def test_sparse_lu_matches_dense_lu_and_gmres():
     xg, rc, it, rg = O.gmres_ilu0(rp, col, val, b, rtol=1e-14)
     assert rr <= 1e-14 and rc == 0
     assert np.linalg.norm(xs - xg) <= 1e-11 * np.linalg.norm(xg)
+
+
+# --------------------------------------------------------------------------
+# the nonlinear (Picard) step: its fixed point solves the discrete
+# Navier-Stokes step, and one iterate is the Oseen step
+# --------------------------------------------------------------------------
+def test_picard_step_reaches_the_discrete_navier_stokes_solution():
+    """The converged Picard step solves the nonlinear backward-Euler system
+    (Sec. 2.2.1 with the convection taken at u^{n+1} itself): re-assembling
+    with w = u^{n+1} and applying the matrix to x^{n+1} gives b to the
+    tolerance; the plain Oseen step (w = u^n) does not."""
+    wl = W.unit_square(6, nu=0.02, dt=0.05)
+    P = _prob(wl)
+    P.t = 0.5
+    P.u, P.p = _exact_state(P, 0.5)
+    un = P.u.copy()
+    Q = _prob(wl)
+    Q.t, Q.u, Q.p = P.t, P.u.copy(), P.p.copy()
+    its = O.picard_step(P, tol=1e-13)
+    assert 3 <= its < 50
+    rp, col, val, b = P.system(P.t, u_prev=un, w=P.u)
+    r = b - O.spmv(rp, col, val, P.x)
+    assert np.linalg.norm(r) <= 1e-10 * np.linalg.norm(b)
+    Q.step()
+    rp, col, val, b = Q.system(Q.t, u_prev=un, w=Q.u)
+    r = b - O.spmv(rp, col, val, Q.x)
+    assert np.linalg.norm(r) > 1e-6 * np.linalg.norm(b)
+    # one Picard iterate is exactly the Oseen step
+    R = _prob(wl)
+    R.t, R.u, R.p = 0.5, un.copy(), Q.p.copy()
+    O.picard_step(R, tol=1e300, maxit=1)
+    assert np.abs(R.x - Q.x).max() <= 1e-13 * np.abs(Q.x).max()
+
+
+# --------------------------------------------------------------------------
+# IPCS (incremental pressure correction, Sec. 2.2.1)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("dim,n", [(2, (4, 3)), (3, (2, 2, 2))])
+def test_ipcs_keeps_an_exact_discrete_steady_state(dim, n):
+    """(u, p) in P2 x P1, time-independent, constant convecting field: the
+    tentative velocity of stage 1 equals u^n (the steady Oseen equations hold
+    with p^n), its divergence vanishes (div-free P2 field), so stage 2 gives
+    dp = 0 and stage 3 returns u^n: every step keeps I_h u, I_h p."""
+    P = _prob(W.Workload(name="poly", dim=dim, n=n, lo=(0.0,) * dim, hi=(1.0,) * dim,
+                         problem=W.POLY_OSEEN, nu=0.7, dt=0.05, steps=3, jitter=0.1,
+                         seed=9, side_mask=0x3F if dim == 3 else 0xF, pin_p0=True,
+                         wconst=(1.0, 0.5, 0.25)[:dim]))
+    u0, p0 = P.u.copy(), P.p.copy()
+    for _ in range(3):
+        O.ipcs_step(P)
+    assert np.abs(P.u - u0).max() < 1e-12
+    assert np.abs(P.p - p0).max() < 1e-11
+
+
+def _ipcs_errors(n, T, nt, monkey=None):
+    P = _prob(W.unit_square(n, jitter=0.0, nu=1.0, dt=T / nt))
+    for _ in range(nt):
+        O.ipcs_step(P)
+    return P.errors()
+
+
+def test_ipcs_converges_in_time_to_the_coupled_solution():
+    """The splitting is consistent: on a fixed (jittered) mesh the IPCS
+    states at T = 0.2 approach, as dt shrinks, the coupled backward-Euler
+    solution of a 16x finer step (itself pinned above), at least at first
+    order in dt (velocity distance ratios >= 1.8 per halving; the pressure's
+    >= 1.5).  A wrong sign in any stage breaks this."""
+    def run(nt, ipcs):
+        P = _prob(W.unit_square(4, jitter=0.1, seed=2, nu=1.0, dt=0.2 / nt))
+        for _ in range(nt):
+            O.ipcs_step(P) if ipcs else P.step()
+        return P.u.copy(), P.p.copy()
+    ur, pr = run(1024, False)
+    d = [run(nt, True) for nt in (16, 32, 64)]
+    du = [np.linalg.norm(u - ur) for u, _ in d]
+    dp = [np.linalg.norm(p - pr) for _, p in d]
+    assert du[0] / du[1] >= 1.8 and du[1] / du[2] >= 1.8, du
+    assert dp[0] / dp[1] >= 1.5 and dp[1] / dp[2] >= 1.5, dp
+    assert du[2] <= 2e-3 * np.linalg.norm(ur), du
+
+
+def test_ipcs_spatial_rates_match_the_paper_table():
+    """Sec. 4.1 solution with nu = 1 at T = 0.1 and dt = 1e-4 (time error
+    far below the spatial one on these meshes): the velocity L2 rate goes to
+    3 and the pressure rate to about 2, as in the paper's IPCS table (2.93,
+    2.98, 2.99 and 3.05, 2.42, 2.07).  The table's absolute values (dt and
+    final time not stated) are not reproduced."""
+    g = _golden("ipcs_table.json")
+    eu, ep = [], []
+    for n in (4, 8, 16):
+        a, b = _ipcs_errors(n, 0.02, 200)
+        eu.append(a)
+        ep.append(b)
+    ru = [math.log2(eu[k - 1] / eu[k]) for k in (1, 2)]
+    rp = [math.log2(ep[k - 1] / ep[k]) for k in (1, 2)]
+    assert abs(ru[-1] - g["u_rate"][2]) < 0.15, (ru, rp)
+    assert 1.7 < rp[-1] < 2.6, (ru, rp)
