@@ -278,6 +278,33 @@ int fs_step_picard(fs_problem* prob, int nsteps, const fs_solve_opts* opts, doub
 int fs_solve_steady(fs_problem* prob, const fs_solve_opts* opts, double nl_tol,
                     int max_picard, fs_picard_stats* stats);
 
+/* Incremental pressure-correction stepping (paper Sec. 2.2.1, IPCS, with
+ * density 1): each step solves, in this order,
+ *   1. (u* - u^n)/dt + ((w . grad) u^n, v) + nu (grad u*, grad v)
+ *        - (p^n, div v) = (f^{n+1}, v)      (w = u^n, convection explicit;
+ *                                             u* = u_D(t^{n+1}) on the boundary)
+ *   2. (grad dp, grad q) = -(1/dt) (div u*, q),  dp = p^{n+1} - p^n
+ *        (the pinned vertex takes p_exact(x_0, t^{n+1}) - p^n(x_0); the
+ *        paper prints the right-hand side with the opposite sign, which
+ *        contradicts its own step 3)
+ *   3. (u^{n+1} - u*, v)/dt = -(grad dp, v)  (u^{n+1} = u_D(t^{n+1}) on the
+ *        boundary), p^{n+1} = p^n + dp.
+ * The three systems (M/dt + nu K, the P1 Laplacian, M) are symmetric
+ * positive definite once their boundary unknowns are eliminated; each is
+ * solved in FP64 by Jacobi-preconditioned conjugate gradients to a relative
+ * residual of rtol (checked every 8 iterations; FS_ERR_NOT_CONVERGED when
+ * the true residual is above 100 rtol after max_iter iterations), whatever
+ * the problem's precision.  Needs a single problem with Dirichlet velocity on
+ * the whole boundary and the pressure pin (FS_ERR_UNSUPPORTED otherwise).
+ * per_step (host, nsteps entries, may be NULL).  Synchronises. */
+typedef struct {
+  int iters[3];       /* CG iterations of the three stages                  */
+  int status;         /* fs_status of the step                             */
+  double rel_res[3];  /* their true relative residuals                     */
+} fs_ipcs_stats;
+int fs_step_ipcs(fs_problem* prob, int nsteps, double rtol, int max_iter,
+                 fs_ipcs_stats* per_step);
+
 /* Per-instance statistics of the last solve (host array, one entry per
  * instance). */
 int fs_instance_stats(const fs_problem* prob, fs_solve_stats* per_instance);

@@ -149,9 +149,18 @@ struct fs_problem {
   int hist = 0, hist_head = 0;
   int32_t* pinned = nullptr;
   int npinned = 0;
+  std::vector<int32_t> pinned_host;  // the same vertices, on the host
   // Picard iteration (allocated on first use): the state at the start of the
   // step, the convecting field of the current iterate, norm scratch
   double *xn = nullptr, *wpic = nullptr, *nrm = nullptr;
+  // IPCS stepping (allocated on first use): tentative velocity, pressure
+  // increment, right-hand side and CG vectors (velocity-sized), inverse
+  // diagonals of the three operators, partials, CG scalars, fixed vertices
+  double *ip_us = nullptr, *ip_dp = nullptr, *ip_rhs = nullptr, *ip_r = nullptr;
+  double *ip_z = nullptr, *ip_p = nullptr, *ip_q = nullptr;
+  double *ip_dA = nullptr, *ip_dM = nullptr, *ip_dK = nullptr, *ip_part = nullptr;
+  double *ip_sc = nullptr, *ip_nrm = nullptr;
+  uint8_t* ip_fixed = nullptr;
   int64_t* mrp = nullptr;  // paper-order monolithic row pointers (export)
   const int32_t* nat = nullptr;          // internal P2 node -> paper id
   double *natbuf = nullptr, *natbuf2 = nullptr;  // boundary conversions (lazy)
@@ -1444,6 +1453,7 @@ int fs_problem_create_batch(fs_mesh* mesh, const fs_problem_desc* descs, int cou
   if (!pin.empty()) {
     FS_TRY(P->upload(&P->pinned, pin));
     P->npinned = (int)pin.size();
+    P->pinned_host = pin;
   }
   FS_CUDA(cudaMemcpyAsync(P->B, Bh.data(), sizeof(double) * Bh.size(), cudaMemcpyHostToDevice, s));
   FS_CUDA(cudaMemcpyAsync(P->BT, BTh.data(), sizeof(double) * BTh.size(), cudaMemcpyHostToDevice,
@@ -1817,6 +1827,148 @@ int fs_solve_steady(fs_problem* P, const fs_solve_opts* opts, double nl_tol, int
   const int rc = picard_iterate(P, P->t, false, nl_tol, max_picard, &st);
   if (stats) *stats = st;
   return rc;
+}
+
+// ---------------------------------------------------------------------------
+// Incremental pressure-correction stepping (paper Sec. 2.2.1, IPCS): three
+// symmetric positive definite systems per step, each solved by
+// Jacobi-preconditioned CG in FP64 (kernels in fs_ipcs.cu).
+// ---------------------------------------------------------------------------
+static int ipcs_setup(fs_problem* P) {
+  if (P->ip_us) return FS_OK;
+  const int64_t nvel = (int64_t)P->dim * P->n2, nv = P->nv;
+  for (double** v : {&P->ip_us, &P->ip_rhs, &P->ip_r, &P->ip_z, &P->ip_p, &P->ip_q, &P->ip_dA,
+                     &P->ip_dM})
+    FS_TRY(P->alloc(v, nvel));
+  FS_TRY(P->alloc(&P->ip_dp, nv));
+  FS_TRY(P->alloc(&P->ip_dK, nv));
+  FS_TRY(P->alloc(&P->ip_part, ipcs_part_size(P->dm)));
+  FS_TRY(P->alloc(&P->ip_sc, 4));
+  FS_TRY(P->alloc(&P->ip_nrm, diff_norms_scratch()));
+  std::vector<uint8_t> fixed(nv, 0);
+  for (int32_t q : P->pinned_host) fixed[q] = 1;
+  FS_TRY(P->upload(&P->ip_fixed, fixed));
+  cudaStream_t s = P->stream;
+  launch_ipcs_dinv(P->dm, 0, P->baseA, nullptr, P->ip_dA, s);
+  launch_ipcs_dinv(P->dm, 0, P->Mv, nullptr, P->ip_dM, s);
+  launch_ipcs_dinv(P->dm, 1, P->Kp, P->ip_fixed, P->ip_dK, s);
+  return check_launch("ipcs set-up");
+}
+
+// Solves A x = rhs (which 0: scalar P2 block `vals` on every component; 1:
+// the P1 Laplacian) by Jacobi-preconditioned CG from the guess in x (whose
+// fixed unknowns are set first), to a recursive relative residual of rtol,
+// checked every 8 iterations; reports the true relative residual.
+static int ipcs_cg(fs_problem* P, int which, const double* vals, const double* dinv,
+                   const double* rhs, double* x, double rtol, int max_iter, int* iters,
+                   double* relres) {
+  cudaStream_t s = P->stream;
+  const DMesh& m = P->dm;
+  const int64_t n = which == 1 ? P->nv : (int64_t)P->dim * P->n2;
+  const uint8_t* fixed = which == 1 ? P->ip_fixed : nullptr;
+  launch_ipcs_fix(m, which, fixed, rhs, x, s);
+  launch_diff_norms(rhs, rhs, n, P->ip_nrm, s);
+  launch_ipcs_apply(m, which, vals, fixed, x, P->ip_q, nullptr, s);
+  launch_cg_init(n, rhs, P->ip_q, dinv, P->ip_r, P->ip_z, P->ip_p, P->ip_part, P->ip_sc, s);
+  FS_TRY(check_launch("ipcs cg init"));
+  double h[4] = {0, 0, 0, 0};
+  FS_CUDA(cudaMemcpyAsync(h, P->ip_nrm, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  FS_CUDA(cudaMemcpyAsync(h + 2, P->ip_sc, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  FS_CUDA(cudaStreamSynchronize(s));
+  const double bn = std::sqrt(h[1]);
+  const double tol2 = (rtol * bn) * (rtol * bn);
+  double rr = h[2 + 3];
+  int it = 0;
+  while (rr > tol2 && it < max_iter && std::isfinite(rr)) {
+    for (int c = 0; c < 8 && it < max_iter; ++c, ++it) {
+      const int nb = launch_ipcs_apply(m, which, vals, fixed, P->ip_p, P->ip_q, P->ip_part, s);
+      launch_cg_alpha(P->ip_part, nb, P->ip_sc, s);
+      launch_cg_update(n, P->ip_sc, P->ip_p, P->ip_q, dinv, x, P->ip_r, P->ip_z, P->ip_part, s);
+      launch_cg_dir(n, P->ip_sc, P->ip_z, P->ip_p, s);
+    }
+    FS_TRY(check_launch("ipcs cg"));
+    FS_CUDA(cudaMemcpyAsync(&rr, P->ip_sc + 3, sizeof(double), cudaMemcpyDeviceToHost, s));
+    FS_CUDA(cudaStreamSynchronize(s));
+  }
+  // true residual
+  launch_ipcs_apply(m, which, vals, fixed, x, P->ip_q, nullptr, s);
+  launch_diff_norms(rhs, P->ip_q, n, P->ip_nrm, s);
+  FS_TRY(check_launch("ipcs cg residual"));
+  FS_CUDA(cudaMemcpyAsync(h, P->ip_nrm, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  FS_CUDA(cudaStreamSynchronize(s));
+  *iters = it;
+  *relres = bn > 0 ? std::sqrt(h[0]) / bn : std::sqrt(h[0]);
+  if (!std::isfinite(*relres)) return FS_ERR_NUMERIC;
+  return *relres <= 100.0 * rtol ? FS_OK : FS_ERR_NOT_CONVERGED;
+}
+
+static int ipcs_step_impl(fs_problem* P, double rtol, int max_iter, fs_ipcs_stats* st) {
+  cudaStream_t s = P->stream;
+  const int64_t nvel = (int64_t)P->dim * P->n2;
+  const double t1 = P->t + P->desc.dt, dt = P->desc.dt;
+  *st = fs_ipcs_stats{};
+  // convection matrix N(u^n) and the load M (u^n/dt + I_h f^{n+1}) with the
+  // boundary values of t^{n+1}
+  FS_TRY(assemble_impl(P, t1));
+  // stage 1: tentative velocity, from u^n
+  launch_ipcs_rhs1(P->dm, P->valA, P->baseA, P->BT, P->b, P->x, P->ip_rhs, s);
+  FS_CUDA(cudaMemcpyAsync(P->ip_us, P->x, sizeof(double) * nvel, cudaMemcpyDeviceToDevice, s));
+  int rc = ipcs_cg(P, 0, P->baseA, P->ip_dA, P->ip_rhs, P->ip_us, rtol, max_iter, &st->iters[0],
+                   &st->rel_res[0]);
+  // stage 2: pressure increment, from 0
+  if (rc == FS_OK) {
+    launch_ipcs_rhs2(P->dm, P->B, P->ip_us, 1.0 / dt, P->ip_fixed, P->b, P->x, P->ip_rhs, s);
+    FS_CUDA(cudaMemsetAsync(P->ip_dp, 0, sizeof(double) * P->nv, s));
+    rc = ipcs_cg(P, 1, P->Kp, P->ip_dK, P->ip_rhs, P->ip_dp, rtol, max_iter, &st->iters[1],
+                 &st->rel_res[1]);
+  }
+  // stage 3: corrected velocity, from u*; then p^{n+1} = p^n + dp
+  if (rc == FS_OK) {
+    launch_ipcs_rhs3(P->dm, P->Mv, P->BT, P->b, P->ip_us, P->ip_dp, dt, P->ip_rhs, s);
+    FS_CUDA(cudaMemcpyAsync(P->x, P->ip_us, sizeof(double) * nvel, cudaMemcpyDeviceToDevice, s));
+    rc = ipcs_cg(P, 0, P->Mv, P->ip_dM, P->ip_rhs, P->x, rtol, max_iter, &st->iters[2],
+                 &st->rel_res[2]);
+    launch_ipcs_add(P->nv, P->ip_dp, P->x + nvel, s);
+    FS_TRY(check_launch("ipcs pressure update"));
+  }
+  P->t = t1;
+  P->hist = 0;  // the coupled solve's state history does not cover these states
+  st->status = rc;
+  return rc;
+}
+
+int fs_step_ipcs(fs_problem* P, int nsteps, double rtol, int max_iter, fs_ipcs_stats* per_step) {
+  if (!P || nsteps < 0 || !(rtol > 0) || max_iter < 1) {
+    set_error("fs_step_ipcs: bad argument");
+    return FS_ERR_INVALID_ARG;
+  }
+  if (P->nseg != 1) {
+    set_error("fs_step_ipcs: batched problems are stepped by fs_step");
+    return FS_ERR_UNSUPPORTED;
+  }
+  const fs_mesh_desc& md = P->mesh->m.inst[0].desc;
+  const int all = md.dim == 2 ? 0x0F : 0x3F;
+  if ((md.dirichlet_sides & all) != all || !P->desc.pin_pressure ||
+      !std::isfinite(P->desc.dt)) {
+    set_error("fs_step_ipcs: needs Dirichlet velocity on the whole boundary, the pressure "
+              "pin and a finite dt");
+    return FS_ERR_UNSUPPORTED;
+  }
+  if (P->ctx.phase != PH_IDLE && P->ctx.phase != PH_DONE) {
+    set_error("fs_step_ipcs: a step is in progress");
+    return FS_ERR_BUSY;
+  }
+  FS_TRY(ipcs_setup(P));
+  for (int k = 0; k < nsteps; ++k) {
+    fs_ipcs_stats st;
+    const int rc = ipcs_step_impl(P, rtol, max_iter, &st);
+    if (per_step) per_step[k] = st;
+    if (rc != FS_OK) {
+      set_error("fs_step_ipcs: a stage's CG did not reach rtol");
+      return rc;
+    }
+  }
+  return FS_OK;
 }
 
 int fs_instance_stats(const fs_problem* P, fs_solve_stats* per_instance) {

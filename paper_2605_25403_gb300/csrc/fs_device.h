@@ -238,6 +238,40 @@ void launch_precond(const DOp<T>& op, const DHier<T>& HA, const DHier<T>& HK,
                     int npinned, JVec<const T> r, JVec<T> z, T* work_p, T* work_u,
                     const int* skip, cudaStream_t s);
 
+// ---- incremental pressure correction (fs_ipcs.cu) -----------------------
+// Right-hand sides of the three stages (x = [u^n | p^n], b = the assembled
+// load with the Dirichlet and pinned values of t^{n+1}); see fs_ipcs.cu.
+void launch_ipcs_rhs1(const DMesh& m, const double* valA, const double* base, const double* BT,
+                      const double* b, const double* x, double* r, cudaStream_t s);
+void launch_ipcs_rhs2(const DMesh& m, const double* B, const double* ustar, double inv_dt,
+                      const uint8_t* fixed, const double* b, const double* x, double* r,
+                      cudaStream_t s);
+void launch_ipcs_rhs3(const DMesh& m, const double* Mv, const double* BT, const double* b,
+                      const double* ustar, const double* dp, double dt, double* r,
+                      cudaStream_t s);
+// y = A x for which = 0 (scalar P2 block `vals` on every component,
+// identity at Dirichlet nodes) or 1 (P1 Laplacian `vals`, identity at the
+// fixed vertices); part (may be null) receives per-block partials of x . y;
+// returns the number of blocks.
+int launch_ipcs_apply(const DMesh& m, int which, const double* vals, const uint8_t* fixed,
+                      const double* x, double* y, double* part, cudaStream_t s);
+void launch_ipcs_dinv(const DMesh& m, int which, const double* vals, const uint8_t* fixed,
+                      double* dinv, cudaStream_t s);
+void launch_ipcs_fix(const DMesh& m, int which, const uint8_t* fixed, const double* rhs,
+                     double* x, cudaStream_t s);
+void launch_ipcs_add(int64_t n, const double* x, double* y, cudaStream_t s);
+// doubles of block-partial scratch the CG kernels need on this mesh
+int ipcs_part_size(const DMesh& m);
+// Jacobi-preconditioned CG steps; sc (4 doubles on the device): rz, alpha,
+// beta, rr.
+void launch_cg_init(int64_t n, const double* rhs, const double* y, const double* dinv, double* r,
+                    double* z, double* p, double* part, double* sc, cudaStream_t s);
+void launch_cg_alpha(const double* part, int nb, double* sc, cudaStream_t s);
+void launch_cg_update(int64_t n, double* sc, const double* p, const double* q,
+                      const double* dinv, double* x, double* r, double* z, double* part,
+                      cudaStream_t s);
+void launch_cg_dir(int64_t n, const double* sc, const double* z, double* p, cudaStream_t s);
+
 // ---- segmented Krylov (fs_krylov.cu) -------------------------------------
 constexpr int kTileLen = 2048;  // vector entries per reduction tile
 

@@ -29,7 +29,8 @@ constexpr unsigned kFull = 0xffffffffu;
 // thread issues several independent loads, to keep enough bytes in flight
 constexpr int kKB = 512;
 
-__device__ __forceinline__ double warp_sum(double v) {
+template <typename V>
+__device__ __forceinline__ V warp_sum(V v) {
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
   return v;
@@ -156,107 +157,118 @@ __global__ void __launch_bounds__(kKB) k_seg_scale(JVec<V> xv, const Tile* tiles
 //   fin : V[j+1] = (w' - V h2) / hn
 // hn is the norm of w'' = w' - V h2 by Pythagoras (V^T w' = h2 and V
 // orthonormal); h2 is a rounding-size correction, so the difference loses
-// nothing.  A block takes one tile: its slice of w is staged in shared
-// memory, the dots are taken by warps over (vector, chunk) units with the
-// per-lane sums in the vector type and the cross-lane and cross-tile sums in
-// FP64, and the updates by threads over elements with the coefficients in
-// shared memory.
+// nothing.
+//
+// A block takes one tile (at most kTileLen = 2,048 entries); thread t of the
+// block takes the entries t + 512 k, k < kLE = 4, so every warp has entries
+// while the tile is longer than 1,536 (coalesced scalar loads whatever the
+// alignment of a vector, whose stride n is arbitrary).  A lane reads the
+// basis vectors in batches of kNB (8 in FP32, 4 in FP64): the kNB x kLE loads
+// of a batch are issued together and held in registers, so a pass takes
+// ceil((j + 1) / kNB) load rounds, and the update pass takes the dots of the
+// updated w' with its last batch from the registers, re-reading only the
+// earlier batches.  Dot products are summed per lane in the vector type,
+// across the warp by shuffles in the vector type too (four products per
+// lane, then a reduce-scatter over the batch's vectors: in FP32 a sum of 128
+// terms with far less rounding than a sequential one; FP64 arithmetic runs
+// at 1/58 of the FP32 rate on this GPU, and one FP64 warp reduction per
+// vector per warp made the whole pass 2.3x slower), then in FP64 across
+// warps in a fixed order and across tiles by the segment's last block.
+constexpr int kLE = kTileLen / kKB;
+static_assert(kLE * kKB == kTileLen, "tile length must be a multiple of the block size");
+static_assert(kLE == 4, "a lane takes four entries of its warp's 128");
+constexpr int kNW = kKB / 32;  // warps per block
 
-// Dots of the staged tile slice ws with the first nvec basis vectors (and
-// ws . ws as entry nvec when `norm`), added into sums[] (shared).
 template <typename V>
-__device__ __forceinline__ void tile_dots(const V* __restrict__ Vb, int64_t n, const Tile& t,
-                                          const V* ws, int nvec, bool norm, double* sums) {
-  constexpr int NW = kKB / 32;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nout = nvec + (norm ? 1 : 0);
-  const int split = nout >= NW ? 1 : (NW + nout - 1) / nout;
-  const int chunk = ((t.len + split - 1) / split + 31) & ~31;
-  for (int u = warp; u < nout * split; u += NW) {
-    const int v = u / split, c = u % split;
-    const int e0 = c * chunk, e1 = min(t.len, e0 + chunk);
-    V acc = V(0);
-    if (e1 <= e0) {
-      // an empty chunk (the last ones of a short tile)
-    } else if (v < nvec) {
-      // 16-byte loads of the basis vector: a scalar head up to its first
-      // 16-byte boundary in [e0, e1), the aligned body, a scalar tail (the
-      // stride n is arbitrary, so the boundary differs between vectors);
-      // ws is read with scalar shared loads
-      using VV = typename std::conditional<sizeof(V) == 4, float4, double2>::type;
-      constexpr int E = 16 / sizeof(V);
-      const V* __restrict__ p = Vb + (int64_t)v * n + t.start + e0;
-      const int len = e1 - e0;
-      int h = (int)(((16 - ((uintptr_t)p & 15)) & 15) / sizeof(V));
-      if (h > len) h = len;
-      if (lane < h) acc += p[lane] * ws[e0 + lane];
-      const int nq = (len - h) / E;
-      const VV* __restrict__ q = reinterpret_cast<const VV*>(p + h);
-      const V* wq = ws + e0 + h;
-#pragma unroll 4
-      for (int k = lane; k < nq; k += 32) {
-        const VV x = q[k];
-        if constexpr (E == 4) {
-          acc += x.x * wq[4 * k] + x.y * wq[4 * k + 1] + x.z * wq[4 * k + 2] +
-                 x.w * wq[4 * k + 3];
-        } else {
-          acc += x.x * wq[2 * k] + x.y * wq[2 * k + 1];
-        }
-      }
-      const int t0 = h + nq * E;  // fewer than E entries remain
-      if (t0 + lane < len) acc += p[t0 + lane] * ws[e0 + t0 + lane];
-    } else {
-#pragma unroll 8
-      for (int e = e0 + lane; e < e1; e += 32) acc += ws[e] * ws[e];
-    }
-    const double sv = warp_sum((double)acc);
-    if (lane == 0) atomicAdd(&sums[v], sv);
-  }
+struct Batch {
+  static constexpr int NB = sizeof(V) == 4 ? 8 : 4;  // basis vectors per load round
+};
+
+// The thread's entries of one vector of the tile (0 past the tile's end).
+template <typename V>
+__device__ __forceinline__ void lane_load(const V* __restrict__ p, int e0, int len,
+                                          V (&x)[kLE]) {
+#pragma unroll
+  for (int k = 0; k < kLE; ++k) x[k] = e0 + kKB * k < len ? p[e0 + kKB * k] : V(0);
 }
 
-// The thread's elements of a tile: e = threadIdx.x + k kKB, k < kElems.
-constexpr int kElems = kTileLen / kKB;
-static_assert(kElems * kKB == kTileLen, "tile length must be a multiple of the block size");
+// Loads basis vectors v0 .. v0 + nb - 1 (nb <= NB) of the tile at once.
+template <typename V, int NB>
+__device__ __forceinline__ void batch_load(const V* __restrict__ base, int64_t n, int v0, int nb,
+                                           int e0, int len, V (&x)[NB][kLE]) {
+#pragma unroll
+  for (int b = 0; b < NB; ++b)
+    if (b < nb) lane_load(base + (int64_t)(v0 + b) * n, e0, len, x[b]);
+}
 
-// w_e <- w_e - sum_v coef[v] V[v]_e for all the thread's elements at once
-// (w[k] for element k; entries past the tile are left alone): U basis
-// vectors at a time for every element (4 in FP32, 2 in FP64 to keep the
-// registers for two blocks per SM), so up to U kElems loads are in flight
-// per thread.
-template <typename V>
-__device__ __forceinline__ void tile_update(const V* __restrict__ Vb, int64_t n, const Tile& t,
-                                            const V* coef, int nvec, V (&w)[kElems]) {
-  constexpr int U = sizeof(V) == 4 ? 4 : 2;
-  V acc[kElems][U];
+// Reduce-scatter of NB per-lane values over a warp (NB a power of two):
+// at the level with xor offset o, a lane keeps half of its slots (the upper
+// half when bit o of its index is set) and adds the partner's copy of them,
+// so after log2(NB) levels lane l holds slot l / (32 / NB) summed over the
+// lanes that share it, and the remaining levels finish that sum.  NB - 1 +
+// 5 - log2(NB) additions per lane instead of 5 NB for NB separate sums.
+template <int NB, typename R>
+__device__ __forceinline__ R warp_transpose_sum(R (&v)[NB]) {
+  const int lane = threadIdx.x & 31;
 #pragma unroll
-  for (int k = 0; k < kElems; ++k)
+  for (int half = NB / 2, off = 16; half >= 1; half /= 2, off /= 2) {
+    const bool hi = (lane & off) != 0;
 #pragma unroll
-    for (int u = 0; u < U; ++u) acc[k][u] = V(0);
-  int v = 0;
-  for (; v + U <= nvec; v += U) {
-#pragma unroll
-    for (int k = 0; k < kElems; ++k) {
-      const int e = threadIdx.x + k * kKB;
-      if (e < t.len) {
-        const V* __restrict__ p = Vb + (int64_t)v * n + t.start + e;
-#pragma unroll
-        for (int u = 0; u < U; ++u) acc[k][u] += coef[v + u] * p[(int64_t)u * n];
-      }
+    for (int i = 0; i < half; ++i) {
+      const R send = hi ? v[i] : v[i + half];
+      const R keep = hi ? v[i + half] : v[i];
+      v[i] = keep + __shfl_xor_sync(kFull, send, off);
     }
   }
-  for (; v < nvec; ++v) {
+  R s = v[0];
 #pragma unroll
-    for (int k = 0; k < kElems; ++k) {
-      const int e = threadIdx.x + k * kKB;
-      if (e < t.len) acc[k][0] += coef[v] * Vb[(int64_t)v * n + t.start + e];
+  for (int off = 16 / NB; off > 0; off >>= 1) s += __shfl_xor_sync(kFull, s, off);
+  return s;
+}
+
+// wpart[warp][v0 + b] = warp sum of x[b] . y over the lane's entries, b < nb.
+template <typename V, int NB>
+__device__ __forceinline__ void batch_dots(const V (&x)[NB][kLE], const V (&y)[kLE], int v0,
+                                           int nb, double (*wpart)[kMaxRestart + 2]) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  V d[NB];
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    d[b] = V(0);
+    if (b < nb) {
+#pragma unroll
+      for (int k = 0; k < kLE; ++k) d[b] += x[b][k] * y[k];
     }
   }
+  const V s = warp_transpose_sum<NB, V>(d);
+  constexpr int kShare = 32 / NB;  // lanes holding one slot's sum
+  const int slot = lane / kShare;
+  if (lane % kShare == 0 && slot < nb) wpart[warp][v0 + slot] = (double)s;
+}
+
+// acc -= sum_b coef[v0 + b] x[b] (per entry)
+template <typename V, int NB>
+__device__ __forceinline__ void batch_axpy(const V (&x)[NB][kLE], const V* coef, int v0, int nb,
+                                           V (&acc)[kLE]) {
 #pragma unroll
-  for (int k = 0; k < kElems; ++k) {
-    V sum = V(0);
+  for (int b = 0; b < NB; ++b)
+    if (b < nb) {
+      const V c = coef[v0 + b];
 #pragma unroll
-    for (int u = 0; u < U; ++u) sum += acc[k][u];
-    w[k] -= sum;
+      for (int k = 0; k < kLE; ++k) acc[k] += c * x[b][k];
+    }
+}
+
+// partial[v ntiles + tile] = sum over the block's warps (fixed order) of
+// wpart[.][v], v < nout.
+__device__ __forceinline__ void block_partials(double (*wpart)[kMaxRestart + 2], int nout,
+                                               double* partial, int ntiles) {
+  __syncthreads();
+  for (int v = threadIdx.x; v < nout; v += kKB) {
+    double sum = 0;
+#pragma unroll
+    for (int q = 0; q < kNW; ++q) sum += wpart[q][v];
+    partial[(int64_t)v * ntiles + blockIdx.x] = sum;
   }
 }
 
@@ -304,22 +316,26 @@ __device__ void end_arnoldi_step(KCtl* ctl, int j, int m, cudaGraphConditionalHa
 }
 
 template <typename V>
-__global__ void __launch_bounds__(kKB) k_seg_dot(const V* __restrict__ Vb, int64_t n,
-                                                 const Tile* tiles, int ntiles, SegState* st,
-                                                 const KCtl* ctl, double* partial) {
+__global__ void __launch_bounds__(kKB, 2) k_seg_dot(const V* __restrict__ Vb, int64_t n,
+                                                    const Tile* tiles, int ntiles, SegState* st,
+                                                    const KCtl* ctl, double* partial) {
+  constexpr int NB = Batch<V>::NB;
   const Tile t = tiles[blockIdx.x];
   SegState& S = st[t.seg];
   if (S.done) return;
   const int j = ctl->j, m = ctl->m, nvec = j + 1;
-  __shared__ V ws[kTileLen];
-  __shared__ double sums[kMaxRestart + 2];
-  const V* __restrict__ w = Vb + (int64_t)(j + 1) * n + t.start;
-  for (int e = threadIdx.x; e < t.len; e += kKB) ws[e] = w[e];
-  for (int v = threadIdx.x; v < nvec; v += kKB) sums[v] = 0.0;
-  __syncthreads();
-  tile_dots<V>(Vb, n, t, ws, nvec, false, sums);
-  __syncthreads();
-  for (int v = threadIdx.x; v < nvec; v += kKB) partial[(int64_t)v * ntiles + blockIdx.x] = sums[v];
+  __shared__ double wpart[kNW][kMaxRestart + 2];
+  const int e0 = threadIdx.x;
+  const V* __restrict__ base = Vb + t.start;
+  V w[kLE];
+  lane_load(base + (int64_t)(j + 1) * n, e0, t.len, w);
+  V x[NB][kLE];
+  for (int v0 = 0; v0 < nvec; v0 += NB) {
+    const int nb = min(NB, nvec - v0);
+    batch_load<V, NB>(base, n, v0, nb, e0, t.len, x);
+    batch_dots<V, NB>(x, w, v0, nb, wpart);
+  }
+  block_partials(wpart, nvec, partial, ntiles);
   if (!last_of_segment(&S.counter[1], S.ntiles)) return;
   __shared__ double res[kMaxRestart + 2];
   reduce_segment(partial, ntiles, S.first_tile, S.ntiles, nvec, res);
@@ -333,41 +349,51 @@ __global__ void __launch_bounds__(kKB) k_seg_dot(const V* __restrict__ Vb, int64
 // Givens rotations and advances the step index (no separate Givens kernel);
 // the final pass then reads j as ctl->j - 1.
 template <typename V, bool GIV>
-__global__ void __launch_bounds__(kKB) k_seg_upd(V* __restrict__ Vb, int64_t n,
-                                                 const Tile* tiles, int ntiles, SegState* st,
-                                                 KCtl* ctl, double* partial,
-                                                 cudaGraphConditionalHandle cond) {
+__global__ void __launch_bounds__(kKB, 2) k_seg_upd(V* __restrict__ Vb, int64_t n,
+                                                    const Tile* tiles, int ntiles, SegState* st,
+                                                    KCtl* ctl, double* partial,
+                                                    cudaGraphConditionalHandle cond) {
+  constexpr int NB = Batch<V>::NB;
   const Tile t = tiles[blockIdx.x];
   SegState& S = st[t.seg];
   if (S.done) return;
   const int j = ctl->j, m = ctl->m, nvec = j + 1;
-  __shared__ V ws[kTileLen];
   __shared__ V coef[kMaxRestart + 1];
-  __shared__ double sums[kMaxRestart + 2];
+  __shared__ double wpart[kNW][kMaxRestart + 2];
   for (int v = threadIdx.x; v < nvec; v += kKB) coef[v] = (V)S.H[v * m + j];
-  for (int v = threadIdx.x; v <= nvec; v += kKB) sums[v] = 0.0;
   __syncthreads();
-  V* __restrict__ w = Vb + (int64_t)(j + 1) * n;
-  V wv[kElems];
+  const int e0 = threadIdx.x, lane = threadIdx.x & 31;
+  const V* __restrict__ base = Vb + t.start;
+  V* __restrict__ wp = Vb + (int64_t)(j + 1) * n + t.start;
+  V w[kLE], acc[kLE];
+  lane_load(wp, e0, t.len, w);
 #pragma unroll
-  for (int k = 0; k < kElems; ++k) {
-    const int e = threadIdx.x + k * kKB;
-    wv[k] = e < t.len ? w[t.start + e] : V(0);
+  for (int k = 0; k < kLE; ++k) acc[k] = V(0);
+  V x[NB][kLE];
+  int last0 = 0;
+  for (int v0 = 0; v0 < nvec; v0 += NB) {
+    const int nb = min(NB, nvec - v0);
+    batch_load<V, NB>(base, n, v0, nb, e0, t.len, x);
+    batch_axpy<V, NB>(x, coef, v0, nb, acc);
+    last0 = v0;
   }
-  tile_update<V>(Vb, n, t, coef, nvec, wv);
+  V nn = V(0);
 #pragma unroll
-  for (int k = 0; k < kElems; ++k) {
-    const int e = threadIdx.x + k * kKB;
-    if (e < t.len) {
-      ws[e] = wv[k];
-      w[t.start + e] = wv[k];
-    }
+  for (int k = 0; k < kLE; ++k) {
+    w[k] -= acc[k];
+    nn += w[k] * w[k];
+    if (e0 + kKB * k < t.len) wp[e0 + kKB * k] = w[k];
   }
-  __syncthreads();
-  tile_dots<V>(Vb, n, t, ws, nvec, true, sums);
-  __syncthreads();
-  for (int v = threadIdx.x; v <= nvec; v += kKB)
-    partial[(int64_t)v * ntiles + blockIdx.x] = sums[v];
+  // re-dot: the last batch is still in registers, the earlier ones are
+  // read again
+  batch_dots<V, NB>(x, w, last0, nvec - last0, wpart);
+  for (int v0 = 0; v0 < last0; v0 += NB) {
+    batch_load<V, NB>(base, n, v0, NB, e0, t.len, x);
+    batch_dots<V, NB>(x, w, v0, NB, wpart);
+  }
+  nn = warp_sum(nn);
+  if (lane == 0) wpart[threadIdx.x >> 5][nvec] = (double)nn;
+  block_partials(wpart, nvec + 1, partial, ntiles);
   if (!last_of_segment(&S.counter[2], S.ntiles)) return;
   __shared__ double res[kMaxRestart + 2];
   reduce_segment(partial, ntiles, S.first_tile, S.ntiles, nvec + 1, res);
@@ -390,9 +416,10 @@ __global__ void __launch_bounds__(kKB) k_seg_upd(V* __restrict__ Vb, int64_t n,
 }
 
 template <typename V>
-__global__ void __launch_bounds__(kKB) k_seg_fin(V* __restrict__ Vb, int64_t n,
-                                                 const Tile* tiles, SegState* st,
-                                                 const KCtl* ctl, int jshift) {
+__global__ void __launch_bounds__(kKB, 2) k_seg_fin(V* __restrict__ Vb, int64_t n,
+                                                    const Tile* tiles, SegState* st,
+                                                    const KCtl* ctl, int jshift) {
+  constexpr int NB = Batch<V>::NB;
   const Tile t = tiles[blockIdx.x];
   const SegState& S = st[t.seg];
   if (S.done) return;
@@ -401,19 +428,22 @@ __global__ void __launch_bounds__(kKB) k_seg_fin(V* __restrict__ Vb, int64_t n,
   for (int v = threadIdx.x; v < nvec; v += kKB) coef[v] = (V)S.h2[v];
   __syncthreads();
   const V f = (V)(1.0 / S.hn);
-  V* __restrict__ w = Vb + (int64_t)(j + 1) * n;
-  V wv[kElems];
+  const int e0 = threadIdx.x;
+  const V* __restrict__ base = Vb + t.start;
+  V* __restrict__ wp = Vb + (int64_t)(j + 1) * n + t.start;
+  V w[kLE], acc[kLE];
+  lane_load(wp, e0, t.len, w);
 #pragma unroll
-  for (int k = 0; k < kElems; ++k) {
-    const int e = threadIdx.x + k * kKB;
-    wv[k] = e < t.len ? w[t.start + e] : V(0);
+  for (int k = 0; k < kLE; ++k) acc[k] = V(0);
+  V x[NB][kLE];
+  for (int v0 = 0; v0 < nvec; v0 += NB) {
+    const int nb = min(NB, nvec - v0);
+    batch_load<V, NB>(base, n, v0, nb, e0, t.len, x);
+    batch_axpy<V, NB>(x, coef, v0, nb, acc);
   }
-  tile_update<V>(Vb, n, t, coef, nvec, wv);
 #pragma unroll
-  for (int k = 0; k < kElems; ++k) {
-    const int e = threadIdx.x + k * kKB;
-    if (e < t.len) w[t.start + e] = wv[k] * f;
-  }
+  for (int k = 0; k < kLE; ++k)
+    if (e0 + kKB * k < t.len) wp[e0 + kKB * k] = (w[k] - acc[k]) * f;
 }
 
 // Givens rotations of column j = ctl->j of every active segment (one block,

@@ -80,6 +80,14 @@ class fs_picard_stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class fs_ipcs_stats(ctypes.Structure):
+    _fields_ = [("iters", _int * 3), ("status", _int), ("rel_res", _d * 3)]
+
+    def as_dict(self):
+        return {"iters": list(self.iters), "status": self.status,
+                "rel_res": list(self.rel_res)}
+
+
 _lib.fs_last_error.restype = ctypes.c_char_p
 _lib.fs_last_error.argtypes = []
 _lib.fs_default_solve_opts.restype = None
@@ -94,6 +102,7 @@ _lib.fs_solve.argtypes = [_vp, _P(fs_solve_opts), _vp, _P(fs_solve_stats)]
 _lib.fs_step.argtypes = [_vp, _int, _P(fs_solve_opts), _P(fs_solve_stats)]
 _lib.fs_step_picard.argtypes = [_vp, _int, _P(fs_solve_opts), _d, _int, _P(fs_picard_stats)]
 _lib.fs_solve_steady.argtypes = [_vp, _P(fs_solve_opts), _d, _int, _P(fs_picard_stats)]
+_lib.fs_step_ipcs.argtypes = [_vp, _int, _d, _int, _P(fs_ipcs_stats)]
 _lib.fs_apply_operator.argtypes = [_vp, _vp, _vp]
 _lib.fs_get_state.argtypes = [_vp, _vp, _int, _P(_d)]
 _lib.fs_set_state.argtypes = [_vp, _vp, _int, _d]
@@ -188,7 +197,7 @@ EXPORTED = ["fs_mesh_create", "fs_mesh_destroy", "fs_dof_map", "fs_problem_creat
             "fs_server_destroy", "fs_server_submit", "fs_server_progress",
             "fs_server_pop_completed", "fs_server_take_state", "fs_server_status",
             "fs_server_estimate_bytes", "fs_get_schedule", "fs_set_schedule", "fs_autotune",
-            "fs_step_picard", "fs_solve_steady"]
+            "fs_step_picard", "fs_solve_steady", "fs_step_ipcs"]
 (FS_KERNEL_SPMV, FS_KERNEL_SPMV_FP64, FS_KERNEL_CHEB, FS_KERNEL_ASSEMBLE_CONV,
  FS_KERNEL_PRECOND, FS_KERNEL_CGS, FS_KERNEL_CGS_DOT, FS_KERNEL_CGS_UPD,
  FS_KERNEL_CGS_FIN) = range(9)
@@ -405,6 +414,15 @@ def fs_solve_steady(prob, nl_tol=1e-10, max_picard=50, opts=None, raise_on_error
     if raise_on_error:
         _check(rc, "fs_solve_steady")
     return st.as_dict()
+
+
+def fs_step_ipcs(prob, nsteps, rtol=1e-13, max_iter=20000, raise_on_error=True):
+    """nsteps incremental pressure-correction steps; per-step stats."""
+    stats = (fs_ipcs_stats * max(nsteps, 1))()
+    rc = _lib.fs_step_ipcs(prob, int(nsteps), float(rtol), int(max_iter), stats)
+    if raise_on_error:
+        _check(rc, "fs_step_ipcs")
+    return [stats[i].as_dict() for i in range(nsteps)]
 
 
 def fs_apply_operator(prob, x, y):

@@ -23,7 +23,10 @@ def main(argv=None):
     p = argparse.ArgumentParser()
     p.add_argument("--workload", default="cube", choices=["channel", "cube", "unit_square"])
     p.add_argument("--kernel", default="cheb",
-                   choices=["cheb", "spmv", "spmv_fp64", "assemble", "precond", "cgs"])
+                   choices=["cheb", "spmv", "spmv_fp64", "assemble", "precond", "cgs",
+                            "cgs_dot", "cgs_upd", "cgs_fin"])
+    p.add_argument("--cold", action="store_true",
+                   help="time each launch after the L2 was filled with other data")
     p.add_argument("--precision", default="fp32_refine", choices=["fp32_refine", "fp64"])
     p.add_argument("--reps", type=int, default=20)
     p.add_argument("--n", type=int, default=0,
@@ -40,13 +43,16 @@ def main(argv=None):
     prec = fs.FS_PREC_FP32_REFINE if a.precision == "fp32_refine" else fs.FS_PREC_FP64
     kid = {"cheb": fs.FS_KERNEL_CHEB, "spmv": fs.FS_KERNEL_SPMV,
            "spmv_fp64": fs.FS_KERNEL_SPMV_FP64, "assemble": fs.FS_KERNEL_ASSEMBLE_CONV,
-           "precond": fs.FS_KERNEL_PRECOND, "cgs": fs.FS_KERNEL_CGS}[a.kernel]
+           "precond": fs.FS_KERNEL_PRECOND, "cgs": fs.FS_KERNEL_CGS,
+           "cgs_dot": fs.FS_KERNEL_CGS_DOT, "cgs_upd": fs.FS_KERNEL_CGS_UPD,
+           "cgs_fin": fs.FS_KERNEL_CGS_FIN}[a.kernel]
     S = fs.Stepper.from_workload(wl, precision=prec)
     try:
-        ms, by = fs.fs_profile_kernel(S.prob, kid, reps=a.reps)
+        ms, by = fs.fs_profile_kernel(S.prob, kid, reps=a.reps, cold=a.cold)
     finally:
         S.close()
     print(json.dumps({"workload": wl.name, "kernel": a.kernel, "precision": a.precision,
+                      "cold": a.cold,
                       "ms": ms, "alg_bytes": by, "gbs": by / ms / 1e6 if by else None}))
     return 0
 

@@ -89,7 +89,7 @@ def test_autotune_installs_a_candidate(fs):
         # one CGS2 step on the Krylov scratch, then the next step solves as
         # before (the solve rebuilds its basis and cycle state)
         ms, by = fs.fs_profile_kernel(S.prob, fs.FS_KERNEL_CGS, reps=3)
-        assert ms > 0 and by == (4 * 15 + 9) * S.info["n_dof"] * 4
+        assert ms > 0 and by == (3 * 15 + 8) * S.info["n_dof"] * 4
         st = fs.fs_step(S.prob, 1)[0]
         assert st["status"] == 0 and st["rel_res"] <= 1e-12
         with pytest.raises(fs.FsError):
