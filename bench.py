@@ -49,7 +49,7 @@ def parse(argv=None):
                    help="launch the solver's kernels one by one instead of replaying captured "
                         "CUDA graphs (for per-kernel profilers, which cannot see kernels inside "
                         "graphs with conditional nodes)")
-    p.add_argument("--roofline-kernel", default="cgs_upd", choices=sorted(KERNELS))
+    p.add_argument("--roofline-kernel", default="cheb", choices=sorted(KERNELS))
     p.add_argument("--batch-steps", type=int, default=20,
                    help="timed steps of the 96-instance batched workload (0: skip)")
     p.add_argument("--cube-steps", type=int, default=10,
@@ -60,6 +60,10 @@ def parse(argv=None):
                    help="requests of each serving run (0: skip)")
     p.add_argument("--serve-rate", type=float, default=200.0,
                    help="mean arrival rate of the saturation run (requests/s)")
+    p.add_argument("--ipcs-steps", type=int, default=10,
+                   help="timed IPCS steps of the 256x256 unit square (0: skip)")
+    p.add_argument("--picard", type=int, default=1,
+                   help="time the steady Picard solve of the Sec. 3.3 example (0: skip)")
     p.add_argument("--cpu-baseline-steps", type=int, default=1,
                    help="full oracle steps of the workload timed for cpu_baseline")
     return p.parse_args(argv)
@@ -316,6 +320,71 @@ def serving_block(fs, count, rate):
             "saturation": sat, "sustainable": sus}
 
 
+def ipcs_block(torch, fs, stream, flush, steps, warmup=3):
+    """Incremental pressure correction (three FP64 CG solves per step) on the
+    256x256 unit square with the Sec. 4.1 solution, nu = 1e-2, dt = 1e-3,
+    beside the coupled Oseen step (FP32 inner / FP64 refinement) of the same
+    workload."""
+    import fs_workloads as W
+    import numpy as np
+    wl = W.unit_square(256, jitter=0.0, nu=1e-2, dt=1e-3)
+    out = {"workload": wl.name, "ndof": wl.ndof, "nu": wl.nu, "dt": wl.dt, "timed_steps": steps}
+    S = fs.Stepper.from_workload(wl, precision=fs.FS_PREC_FP64, stream=stream.cuda_stream)
+    try:
+        fs.fs_step_ipcs(S.prob, warmup)
+        ms, its = [], []
+        for _ in range(steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            stream.synchronize()
+            t0 = time.perf_counter()
+            st = fs.fs_step_ipcs(S.prob, 1)[0]   # synchronises
+            ms.append(1e3 * (time.perf_counter() - t0))
+            its.append(st["iters"])
+        out["ipcs"] = {"steps_per_s": 1e3 * len(ms) / sum(ms), "ms_per_step": sum(ms) / len(ms),
+                       "cg_iters_per_stage": [float(np.mean([i[k] for i in its]))
+                                              for k in range(3)],
+                       "timing": "host wall clock around the synchronising call"}
+    finally:
+        S.close()
+    S = fs.Stepper.from_workload(wl, precision=fs.FS_PREC_FP32_REFINE, stream=stream.cuda_stream)
+    try:
+        for _ in range(warmup):
+            fs.fs_step(S.prob, 1)
+        t, st = time_steps(torch, fs, S, stream, steps, flush)
+        out["coupled_fp32_refine"] = {"steps_per_s": 1e3 * len(t) / sum(t),
+                                      "ms_per_step": sum(t) / len(t),
+                                      "iters_per_step": float(np.mean([q["iters"] for q in st]))}
+    finally:
+        S.close()
+    return out
+
+
+def picard_block(fs, n=64):
+    """The steady example of Sec. 3.3 (nu = 1, no time derivative) on an
+    n x n square: Picard iteration to 1e-10 from zero, each linear solve
+    FP32 inner / FP64 refinement to 1e-12 (without the mass term the system
+    is far worse conditioned than a time step's)."""
+    import math
+    import numpy as np
+    import fs_workloads as W
+    wl = W.unit_square(n, problem=W.STEADY_POLY, jitter=0.0, nu=1.0, dt=math.inf)
+    S = fs.Stepper.from_workload(wl, precision=fs.FS_PREC_FP32_REFINE)
+    try:
+        x0, t0 = S.state()
+        fs.fs_set_state(S.prob, np.zeros_like(x0), t0)
+        t = time.perf_counter()
+        st = fs.fs_solve_steady(S.prob, nl_tol=1e-10, opts=fs.fs_default_solve_opts(rtol=1e-12),
+                                raise_on_error=False)
+        secs = time.perf_counter() - t
+    finally:
+        S.close()
+    return {"workload": f"steady example (Sec. 3.3) on {wl.name}, nu = 1", "ndof": wl.ndof,
+            "seconds": secs, "status": st["status"], "picard_iters": st["picard_iters"],
+            "krylov_iters": st["krylov_iters"], "update": st["update"],
+            "rel_res": st["rel_res"]}
+
+
 def cube_block(torch, fs, stream, flush, steps, steps64, warmup=3):
     """The cube 48^3 (2,855,668 DOF): FP32+refinement and FP64 steps/s, the
     per-step difference between the two paths' states, and the L2-cold
@@ -536,11 +605,24 @@ def main():
                          f"1e-14) in {secs:.1f} s, single-threaded plain C + SuperLU"}
 
     S.close()
-    batch = batched_run(torch, fs, args.batch_steps) if args.batch_steps > 0 else None
-    cube = (cube_block(torch, fs, stream, flush, args.cube_steps, args.cube_fp64_steps)
-            if args.cube_steps > 0 else None)
-    serving = (serving_block(fs, args.serve_requests, args.serve_rate)
-               if args.serve_requests > 0 else None)
+
+    def block(enabled, fn, *a):
+        """A secondary workload: its result, or the error that stopped it (the
+        headline line is printed either way)."""
+        if not enabled:
+            return None
+        try:
+            return fn(*a)
+        except Exception as e:  # noqa: BLE001 - recorded in the JSON line
+            return {"error": f"{type(e).__name__}: {e}"}
+
+    batch = block(args.batch_steps > 0, batched_run, torch, fs, args.batch_steps)
+    cube = block(args.cube_steps > 0, cube_block, torch, fs, stream, flush, args.cube_steps,
+                 args.cube_fp64_steps)
+    serving = block(args.serve_requests > 0, serving_block, fs, args.serve_requests,
+                    args.serve_rate)
+    ipcs = block(args.ipcs_steps > 0, ipcs_block, torch, fs, stream, flush, args.ipcs_steps)
+    picard = block(args.picard > 0, picard_block, fs)
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -578,6 +660,8 @@ def main():
         "batched": batch,
         "cube": cube,
         "serving": serving,
+        "ipcs": ipcs,
+        "picard_steady": picard,
     }
     print(json.dumps(line), flush=True)
     if dist:

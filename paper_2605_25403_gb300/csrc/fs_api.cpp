@@ -829,8 +829,8 @@ int assemble_impl(fs_problem* P, double t_next, const double* w = nullptr,
   FS_CUDA(cudaMemcpyAsync(P->valA, P->baseA, sizeof(double) * nnzA, cudaMemcpyDeviceToDevice, s));
   const bool constw = P->desc.problem == FS_PROBLEM_POLY_OSEEN ||
                       P->desc.problem == FS_PROBLEM_POLY_OSEEN_T;
-  launch_assemble_conv(P->dm, constw ? nullptr : w, P->n2, constw ? P->desc.wconst : nullptr,
-                       P->valA, s);
+  launch_assemble_conv(P->dm, me.color_ptr, constw ? nullptr : w, P->n2,
+                       constw ? P->desc.wconst : nullptr, P->valA, P->desc.deterministic != 0, s);
   launch_bc_rows<double>(P->dm, P->valA, s);
   launch_eval_load(P->dm, P->ph, t_next, 1.0 / P->desc.dt, u_old, P->F, s);
   launch_rhs(P->dm, P->ph, t_next, P->Mv, P->F, P->pinned, P->npinned, P->b, s);
@@ -1308,7 +1308,8 @@ int fs_problem_create_batch(fs_mesh* mesh, const fs_problem_desc* descs, int cou
     }
     if (d.problem != d0.problem || d.dt != d0.dt || d.t0 != d0.t0 ||
         d.precision != d0.precision || d.init != d0.init ||
-        std::memcmp(d.wconst, d0.wconst, sizeof(d.wconst)) != 0) {
+        std::memcmp(d.wconst, d0.wconst, sizeof(d.wconst)) != 0 ||
+        d.deterministic != d0.deterministic) {
       set_error("fs_problem_create_batch: instances may differ only in nu and pin_pressure");
       return FS_ERR_INVALID_ARG;
     }
@@ -1378,6 +1379,9 @@ int fs_problem_create_batch(fs_mesh* mesh, const fs_problem_desc* descs, int cou
     FS_TRY(P->upload(&pa, me.posA)); FS_TRY(P->upload(&pb, me.posB));
     FS_TRY(P->upload(&pbt, me.posBT)); FS_TRY(P->upload(&pk, me.posKp));
     dm.posA = pa; dm.posB = pb; dm.posBT = pbt; dm.posK = pk;
+    int32_t* cc;
+    FS_TRY(P->upload(&cc, me.color_cells));
+    dm.color_cells = cc;
   }
   P->ph.kind = d0.problem;
   P->ph.nu = d0.nu;
@@ -1418,7 +1422,8 @@ int fs_problem_create_batch(fs_mesh* mesh, const fs_problem_desc* descs, int cou
   FS_CUDA(cudaMemsetAsync(P->BT, 0, sizeof(double) * nnzBT * dim, s));
   FS_CUDA(cudaMemsetAsync(P->Kp, 0, sizeof(double) * nnzK, s));
   FS_CUDA(cudaMemsetAsync(P->mpl, 0, sizeof(double) * P->nv, s));
-  launch_assemble_base(dm, 1.0 / d0.dt, d0.nu, P->baseA, P->Mv, P->B, P->BT, P->Kp, P->mpl, s);
+  launch_assemble_base(dm, me.color_ptr, 1.0 / d0.dt, d0.nu, P->baseA, P->Mv, P->B, P->BT, P->Kp,
+                       P->mpl, s);
   FS_TRY(check_launch("assemble_base"));
   HostCsr A0 = me.A, Kp = me.Kp;
   A0.val.resize(nnzA);
@@ -2092,7 +2097,8 @@ int fs_profile_kernel(fs_problem* P, int kernel, int reps, double* avg_ms, doubl
       bytes = me.ncell * (double)me.nloc * (4 + me.nloc) + me.nv * d * 8.0 +
               (double)d * P->n2 * 8.0 + 4.0 * (P->n2 + 1) + P->n2 + 16.0 * nnzA;
       launch = [P]() {
-        launch_assemble_conv(P->dm, P->x, P->n2, nullptr, P->valA, P->stream);
+        launch_assemble_conv(P->dm, P->mesh->m.color_ptr, P->x, P->n2, nullptr, P->valA,
+                             P->desc.deterministic != 0, P->stream);
       };
       break;
     }

@@ -137,13 +137,14 @@ __device__ __forceinline__ void load_cell(const DMesh& m, int64_t e,
 
 template <int DIM>
 __global__ void __launch_bounds__(128) k_assemble_base(
-    DMesh m, double mass_coef, double nu, double* __restrict__ base,
+    DMesh m, int64_t c0, int64_t c1, double mass_coef, double nu, double* __restrict__ base,
     double* __restrict__ Mv, double* __restrict__ B, double* __restrict__ BT,
     double* __restrict__ Kp, double* __restrict__ mpl) {
   constexpr int NB = DIM + 1, NL = Loc<DIM>::nl;
   const CRef& R = c_ref[DIM - 2];
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m.ncell;
-       e += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t idx = c0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < c1;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = m.color_cells[idx];
     int32_t g[NL];
     double xv[NB][DIM], gl[NB][DIM];
     load_cell<DIM>(m, e, g, xv);
@@ -172,8 +173,8 @@ __global__ void __launch_bounds__(128) k_assemble_base(
           for (int s = 0; s < NB; ++s) kk += G[r][s] * R.stiff[i][j][r][s];
         kk *= D;
         int32_t slot = rowbase + pos[j];
-        atomicAdd(base + slot, mass_coef * mm + nu_e * kk);
-        atomicAdd(Mv + slot, mm);
+        base[slot] += mass_coef * mm + nu_e * kk;
+        Mv[slot] += mm;
       }
     }
 #pragma unroll
@@ -191,8 +192,8 @@ __global__ void __launch_bounds__(128) k_assemble_base(
         int64_t sBT = __ldg(m.rpBT + g[j]) + m.posBT[(e * NL + j) * NB + q];
 #pragma unroll
         for (int c = 0; c < DIM; ++c) {
-          atomicAdd(B + sB * DIM + c, bv[c]);
-          atomicAdd(BT + sBT * DIM + c, bv[c]);
+          B[sB * DIM + c] += bv[c];
+          BT[sBT * DIM + c] += bv[c];
         }
       }
     const double vol = D / (DIM == 2 ? 2.0 : 6.0);
@@ -200,14 +201,120 @@ __global__ void __launch_bounds__(128) k_assemble_base(
     for (int q = 0; q < NB; ++q) {
       int32_t rb = __ldg(m.rpK + g[q]);
 #pragma unroll
-      for (int s = 0; s < NB; ++s) atomicAdd(Kp + rb + m.posK[(e * NB + q) * NB + s], vol * G[q][s]);
-      atomicAdd(mpl + g[q], vol / NB);
+      for (int s = 0; s < NB; ++s) Kp[rb + m.posK[(e * NB + q) * NB + s]] += vol * G[q][s];
+      mpl[g[q]] += vol / NB;
     }
   }
 }
 
+// Convection element matrices N_K(w) (the per-step part of the Oseen
+// operator), added into valA colour by colour: a launch takes the cells
+// color_cells[c0 .. c1) of one colour (they share no node, so the plain
+// read-modify-writes of different cells never meet, and every value is
+// summed in the colour order on every run).  One thread per (cell, row i):
+// a block takes kConvCells cells; one thread per cell computes D = |det J|
+// and the barycentric gradients, every thread the coefficients
+// cw[k][r] = D (w_k . grad lambda_r) of its node k = i, and then its row
+//   N_ij = sum_k sum_(j,r) cw[k][r] conv_ik(j,r)
+// from the reference tensor staged in shared memory.  Rows of Dirichlet
+// nodes are skipped.  A thread does one row's nloc x pairs FMAs (160 in 3D)
+// instead of a cell's ten rows: ten times the threads and a fifth of the
+// registers, which keeps the FP64 pipe busy even when a colour holds a
+// sixteenth of the cells.
 template <int DIM>
-__global__ void __launch_bounds__(128) k_assemble_conv(DMesh m,
+struct ConvCfg {
+  static constexpr int NL = Loc<DIM>::nl, NB = DIM + 1, NP = Pairs<DIM>::n;
+  static constexpr int CPB = 128 / NL;  // cells per block (21 / 12)
+  // shared-memory row strides (doubles) padded so that the rows the threads
+  // of a warp read at one (k, q) fall in different banks: 3D 160 -> 161
+  // (a multiple of 32 banks put the ten rows of a cell in one bank)
+  static constexpr int RS = NL * NP + (DIM == 3 ? 1 : 0);
+  static constexpr int CS = NL * NB + (DIM == 3 ? 1 : 0);
+};
+
+template <int DIM>
+__global__ void __launch_bounds__(128) k_conv_elem(DMesh m, int64_t c0, int64_t c1,
+                                                   const double* __restrict__ w, int64_t ldw,
+                                                   double wc0, double wc1, double wc2,
+                                                   double* __restrict__ valA) {
+  using C = ConvCfg<DIM>;
+  constexpr int NL = C::NL, NB = C::NB, NP = C::NP, CPB = C::CPB;
+  constexpr int RS = C::RS, CS = C::CS;
+  __shared__ double s_conv[NL * RS];  // row i of the tensor at i RS + k NP + q
+  __shared__ double s_gl[CPB][NB][DIM];
+  __shared__ double s_D[CPB];
+  __shared__ double s_cw[CPB * CS];   // cell c's cw[k][r] at c CS + k NB + r
+  __shared__ int32_t s_g[CPB][NL];
+  const CRef& R = c_ref[DIM - 2];
+  for (int t = threadIdx.x; t < NL * NL * NP; t += blockDim.x) {
+    const int i = t / (NL * NP), k = (t / NP) % NL, q = t % NP;
+    s_conv[i * RS + k * NP + q] = R.conv[i][k][q];
+  }
+  const int cl = threadIdx.x / NL, i = threadIdx.x % NL;
+  const int64_t idx = c0 + blockIdx.x * (int64_t)CPB + cl;
+  const bool active = cl < CPB && idx < c1;
+  const int64_t e = active ? __ldg(m.color_cells + idx) : 0;
+  int32_t gi = 0;
+  if (active) {
+    gi = __ldg(m.c2d + e * NL + i);
+    s_g[cl][i] = gi;
+  }
+  __syncthreads();
+  if (active && i == 0) {
+    double xv[NB][DIM], gl[NB][DIM];
+#pragma unroll
+    for (int v = 0; v < NB; ++v)
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) xv[v][a] = __ldg(m.p2xyz + (int64_t)s_g[cl][v] * DIM + a);
+    s_D[cl] = bary_grads<DIM>(xv, gl);
+#pragma unroll
+    for (int r = 0; r < NB; ++r)
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) s_gl[cl][r][a] = gl[r][a];
+  }
+  __syncthreads();
+  if (active) {
+    double wk[DIM];
+    if (w) {
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) wk[c] = __ldg(w + c * ldw + gi);
+    } else {
+      wk[0] = wc0;
+      wk[1] = wc1;
+      if constexpr (DIM == 3) wk[2] = wc2;
+    }
+    const double D = s_D[cl];
+#pragma unroll
+    for (int r = 0; r < NB; ++r) {
+      double t = 0;
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) t += wk[c] * s_gl[cl][r][c];
+      s_cw[cl * CS + i * NB + r] = D * t;
+    }
+  }
+  __syncthreads();
+  if (!active || __ldg(m.dirichlet + gi)) return;
+  double acc[NL];
+#pragma unroll
+  for (int j = 0; j < NL; ++j) acc[j] = 0.0;
+#pragma unroll
+  for (int k = 0; k < NL; ++k)
+#pragma unroll
+    for (int q = 0; q < NP; ++q)
+      acc[Pairs<DIM>::j(q)] +=
+          s_cw[cl * CS + k * NB + Pairs<DIM>::r(q)] * s_conv[i * RS + k * NP + q];
+  double* __restrict__ row = valA + __ldg(m.rpA + gi);
+  const uint8_t* pos = m.posA + (e * NL + i) * NL;
+#pragma unroll
+  for (int j = 0; j < NL; ++j) row[__ldg(pos + j)] += acc[j];
+}
+
+// The same element matrices, a thread per cell over all cells at once,
+// added with FP64 atomics: the fastest form (one launch, no colour
+// serialisation), but the order in which a value's contributions arrive,
+// and so its last bits, changes from run to run.
+template <int DIM>
+__global__ void __launch_bounds__(128) k_conv_atomic(DMesh m,
                                                        const double* __restrict__ w,
                                                        int64_t ldw, double wc0,
                                                        double wc1, double wc2,
@@ -258,6 +365,7 @@ __global__ void __launch_bounds__(128) k_assemble_conv(DMesh m,
     }
   }
 }
+
 
 template <typename T>
 __global__ void k_bc_rows(DMesh m, T* __restrict__ valA) {
@@ -582,26 +690,46 @@ inline unsigned grid_for(int64_t n, int block) {
 
 }  // namespace
 
-void launch_assemble_base(const DMesh& m, double mass_coef, double nu,
-                          double* base, double* Mv, double* B, double* BT,
-                          double* Kp, double* mpl, cudaStream_t s) {
-  unsigned g = grid_for(m.ncell, 128);
-  if (m.dim == 2)
-    k_assemble_base<2><<<g, 128, 0, s>>>(m, mass_coef, nu, base, Mv, B, BT, Kp, mpl);
-  else
-    k_assemble_base<3><<<g, 128, 0, s>>>(m, mass_coef, nu, base, Mv, B, BT, Kp, mpl);
+void launch_assemble_base(const DMesh& m, const std::vector<int64_t>& color_ptr,
+                          double mass_coef, double nu, double* base, double* Mv, double* B,
+                          double* BT, double* Kp, double* mpl, cudaStream_t s) {
+  for (size_t c = 0; c + 1 < color_ptr.size(); ++c) {
+    const int64_t c0 = color_ptr[c], c1 = color_ptr[c + 1];
+    const unsigned g = grid_for(c1 - c0, 128);
+    if (m.dim == 2)
+      k_assemble_base<2><<<g, 128, 0, s>>>(m, c0, c1, mass_coef, nu, base, Mv, B, BT, Kp, mpl);
+    else
+      k_assemble_base<3><<<g, 128, 0, s>>>(m, c0, c1, mass_coef, nu, base, Mv, B, BT, Kp, mpl);
     count_launches(1);
+  }
 }
 
-void launch_assemble_conv(const DMesh& m, const double* w, int64_t ldw,
-                          const double* wc, double* valA, cudaStream_t s) {
-  unsigned g = grid_for(m.ncell, 128);
-  double w0 = wc ? wc[0] : 0, w1 = wc ? wc[1] : 0, w2 = wc ? wc[2] : 0;
-  if (m.dim == 2)
-    k_assemble_conv<2><<<g, 128, 0, s>>>(m, w, ldw, w0, w1, w2, valA);
-  else
-    k_assemble_conv<3><<<g, 128, 0, s>>>(m, w, ldw, w0, w1, w2, valA);
+void launch_assemble_conv(const DMesh& m, const std::vector<int64_t>& color_ptr,
+                          const double* w, int64_t ldw, const double* wc, double* valA,
+                          bool deterministic, cudaStream_t s) {
+  const double w0 = wc ? wc[0] : 0, w1 = wc ? wc[1] : 0, w2 = wc ? wc[2] : 0;
+  if (!deterministic) {
+    const unsigned g = grid_for(m.ncell, 128);
+    if (m.dim == 2)
+      k_conv_atomic<2><<<g, 128, 0, s>>>(m, w, ldw, w0, w1, w2, valA);
+    else
+      k_conv_atomic<3><<<g, 128, 0, s>>>(m, w, ldw, w0, w1, w2, valA);
     count_launches(1);
+    return;
+  }
+  for (size_t c = 0; c + 1 < color_ptr.size(); ++c) {
+    const int64_t c0 = color_ptr[c], c1 = color_ptr[c + 1];
+    if (m.dim == 2) {
+      constexpr int CPB = ConvCfg<2>::CPB;
+      const unsigned g = (unsigned)((c1 - c0 + CPB - 1) / CPB);
+      k_conv_elem<2><<<g, 128, 0, s>>>(m, c0, c1, w, ldw, w0, w1, w2, valA);
+    } else {
+      constexpr int CPB = ConvCfg<3>::CPB;
+      const unsigned g = (unsigned)((c1 - c0 + CPB - 1) / CPB);
+      k_conv_elem<3><<<g, 128, 0, s>>>(m, c0, c1, w, ldw, w0, w1, w2, valA);
+    }
+    count_launches(1);
+  }
 }
 
 template <typename T>

@@ -72,6 +72,7 @@ struct DMesh {
   const int32_t *rpK = nullptr, *ciK = nullptr;    // P1-P1
   const uint8_t *posA = nullptr, *posB = nullptr, *posBT = nullptr, *posK = nullptr;
   const double* nu_cell = nullptr;     // per-cell viscosity (batches) or null
+  const int32_t* color_cells = nullptr;  // cells grouped by colour (Mesh)
 };
 
 // Physical description of the manufactured problem.
@@ -83,17 +84,26 @@ struct DPhys {
 };
 
 // ---- assembly (fs_assembly.cu) -------------------------------------------
-// Step-invariant blocks, accumulated with atomics into zeroed arrays:
+// Colour-ordered element kernels (color_ptr: the host copy of
+// Mesh::color_ptr, one launch per colour): the cells of a colour share no
+// node, so they add into the block values with plain read-modify-writes, no
+// atomics, and every value is summed in the same order on every run.
+// Step-invariant blocks (always colour-ordered), accumulated into zeroed
+// arrays:
 // base = mass_coef M + nu K (P2-P2), Mv = M, B (P1-P2, dim values per entry),
 // BT (P2-P1, dim values), Kp (P1 stiffness), mpl (lumped P1 mass).
-void launch_assemble_base(const DMesh& m, double mass_coef, double nu,
-                          double* base, double* Mv, double* B, double* BT,
-                          double* Kp, double* mpl, cudaStream_t s);
+void launch_assemble_base(const DMesh& m, const std::vector<int64_t>& color_ptr,
+                          double mass_coef, double nu, double* base, double* Mv, double* B,
+                          double* BT, double* Kp, double* mpl, cudaStream_t s);
 // valA += N(w) with w taken from the component-blocked vector w (ldw =
 // component stride) or the constant field wc when w == nullptr; rows of
-// Dirichlet nodes are skipped.
-void launch_assemble_conv(const DMesh& m, const double* w, int64_t ldw,
-                          const double* wc, double* valA, cudaStream_t s);
+// Dirichlet nodes are skipped.  deterministic: colour by colour as the
+// step-invariant blocks, a thread per (cell, row); otherwise one launch over
+// all cells, a thread per cell, FP64 atomics (faster; the last bits of a
+// value depend on the order its contributions arrive in).
+void launch_assemble_conv(const DMesh& m, const std::vector<int64_t>& color_ptr,
+                          const double* w, int64_t ldw, const double* wc, double* valA,
+                          bool deterministic, cudaStream_t s);
 // Dirichlet rows of the scalar block become identity rows.
 template <typename T>
 void launch_bc_rows(const DMesh& m, T* valA, cudaStream_t s);

@@ -57,6 +57,13 @@ struct Mesh {
   // build_local); node_nat[q] is the paper-order (vertices, then edges ranked
   // lexicographically) id of internal node q.  Vertices keep their ids.
   std::vector<int32_t> node_nat;    // n2
+  // Cells grouped by colour: no two cells of one colour share a P2 node, so
+  // the cells of a colour add their element matrices into the block values
+  // without atomics, and the colours run in a fixed order: every assembled
+  // value is summed in the same order on every run.  Colour c holds the
+  // cells color_cells[color_ptr[c] .. color_ptr[c + 1]), ascending.
+  std::vector<int32_t> color_cells;
+  std::vector<int64_t> color_ptr;
 };
 
 // The DOF map in paper order (the numbering of fs_dof_map): cell-to-node

@@ -67,14 +67,26 @@ __device__ __forceinline__ bool last_of_segment(unsigned* counter, int ntiles) {
 
 // Sum of partial[v * ntiles_total + t] over the segment's tiles, for v <
 // nvec; result in res[v] (shared), all threads of the block participate.
+// A warp per vector; a lane reads its tiles four at a time (loads from L2,
+// where the other blocks' partials are visible after the ticket) into four
+// sums, added in a fixed order.
 __device__ void reduce_segment(const double* partial, int64_t stride, int first, int count,
                                int nvec, double* res) {
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int v = w; v < nvec; v += nw) {
-    double s = 0;
-    for (int t = lane; t < count; t += 32)
-      s += ((volatile const double*)partial)[(int64_t)v * stride + first + t];
-    s = warp_sum(s);
+    const double* p = partial + (int64_t)v * stride + first;
+    double s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+    int t = lane;
+    for (; t + 96 < count; t += 128) {
+      const double a0 = __ldcg(p + t), a1 = __ldcg(p + t + 32), a2 = __ldcg(p + t + 64),
+                   a3 = __ldcg(p + t + 96);
+      s0 += a0;
+      s1 += a1;
+      s2 += a2;
+      s3 += a3;
+    }
+    for (; t < count; t += 32) s0 += __ldcg(p + t);
+    double s = warp_sum((s0 + s1) + (s2 + s3));
     if (lane == 0) res[v] = s;
   }
   __syncthreads();

@@ -95,7 +95,7 @@ int64_t estimate_bytes(const fs_mesh_desc& md, int precision) {
   const double nnzA = n2 * (dim == 2 ? 13.5 : 28.5), nnzB = nv * (dim == 2 ? 15 : 62);
   const double s = precision == FS_PREC_FP32_REFINE ? 4.0 : 8.0;
   double b = 0;
-  b += cells * (4 * nloc + nloc * nloc + 2 * nb * nloc + nb * nb);   // c2d + slots
+  b += cells * (4 * nloc + nloc * nloc + 2 * nb * nloc + nb * nb + 4);  // c2d, slots, colours
   b += n2 * (8 * dim + 1 + 4) + 4 * (2 * nnzA + 2 * nnzB) + 16 * (n2 + nv);  // geometry, patterns
   b += 8 * (3 * nnzA + 2 * dim * nnzB + nnzB + 3 * nv);              // FP64 values
   b += 8 * (4 * ndof + dim * n2);                                    // x, b, r, F

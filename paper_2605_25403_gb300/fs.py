@@ -56,7 +56,8 @@ class fs_dofmap_info(ctypes.Structure):
 
 class fs_problem_desc(ctypes.Structure):
     _fields_ = [("problem", _int), ("nu", _d), ("dt", _d), ("t0", _d), ("precision", _int),
-                ("pin_pressure", _int), ("init", _int), ("wconst", _d * 3)]
+                ("pin_pressure", _int), ("init", _int), ("wconst", _d * 3),
+                ("deterministic", _int)]
 
 
 class fs_solve_opts(ctypes.Structure):
@@ -301,12 +302,13 @@ def fs_default_solve_opts(**kw):
 
 
 def _problem_desc(problem, nu, dt, t0=0.0, precision=FS_PREC_FP64, pin_pressure=1, init=0,
-                  wconst=(0.0, 0.0, 0.0)):
+                  wconst=(0.0, 0.0, 0.0), deterministic=0):
     d = fs_problem_desc()
     d.problem, d.nu, d.dt, d.t0 = int(problem), float(nu), float(dt), float(t0)
     d.precision, d.pin_pressure, d.init = int(precision), int(pin_pressure), int(init)
     for a in range(3):
         d.wconst[a] = float(wconst[a]) if a < len(wconst) else 0.0
+    d.deterministic = int(bool(deterministic))
     return d
 
 
@@ -347,12 +349,8 @@ _instance_counts = {}
 
 
 def fs_problem_create(mesh, problem, nu, dt, t0=0.0, precision=FS_PREC_FP64, pin_pressure=1,
-                      init=0, wconst=(0.0, 0.0, 0.0), stream=None):
-    d = fs_problem_desc()
-    d.problem, d.nu, d.dt, d.t0 = int(problem), float(nu), float(dt), float(t0)
-    d.precision, d.pin_pressure, d.init = int(precision), int(pin_pressure), int(init)
-    for a in range(3):
-        d.wconst[a] = float(wconst[a]) if a < len(wconst) else 0.0
+                      init=0, wconst=(0.0, 0.0, 0.0), stream=None, deterministic=0):
+    d = _problem_desc(problem, nu, dt, t0, precision, pin_pressure, init, wconst, deterministic)
     h = _vp()
     s = None if stream is None else ctypes.c_void_p(int(stream))
     _check(_lib.fs_problem_create(mesh, ctypes.byref(d), s, ctypes.byref(h)), "fs_problem_create")
@@ -527,12 +525,13 @@ class Stepper:
     info: dict
 
     @classmethod
-    def from_workload(cls, wl, precision=FS_PREC_FP64, stream=None, dofmap_arrays=False):
+    def from_workload(cls, wl, precision=FS_PREC_FP64, stream=None, dofmap_arrays=False,
+                      deterministic=False):
         mesh = fs_mesh_create(wl.dim, wl.n, wl.lo, wl.hi, wl.jitter, wl.seed, wl.side_mask)
         info = fs_dof_map(mesh, arrays=dofmap_arrays)
         prob = fs_problem_create(mesh, _KIND[wl.problem], wl.nu, wl.dt, 0.0, precision,
                                  1 if wl.pin_p0 else 0, 1 if wl.init == "zero_interior" else 0,
-                                 wl.wconst or (0.0, 0.0, 0.0), stream)
+                                 wl.wconst or (0.0, 0.0, 0.0), stream, deterministic)
         return cls(mesh, prob, info)
 
     @classmethod
@@ -590,11 +589,12 @@ class Server:
         _check(_lib.fs_server_create(ctypes.byref(d), ctypes.byref(self.h)), "fs_server_create")
         self.ndof = {}
 
-    def submit(self, wl, nsteps, arrival, precision=FS_PREC_FP32_REFINE, keep_state=False):
+    def submit(self, wl, nsteps, arrival, precision=FS_PREC_FP32_REFINE, keep_state=False,
+               deterministic=False):
         md = _mesh_desc(wl.dim, wl.n, wl.lo, wl.hi, wl.jitter, wl.seed, wl.side_mask)
         pd = _problem_desc(_KIND[wl.problem], wl.nu, wl.dt, 0.0, precision,
                            1 if wl.pin_p0 else 0, 1 if wl.init == "zero_interior" else 0,
-                           wl.wconst or (0.0, 0.0, 0.0))
+                           wl.wconst or (0.0, 0.0, 0.0), deterministic)
         rid = _i64()
         _check(_lib.fs_server_submit(self.h, ctypes.byref(md), ctypes.byref(pd), int(nsteps),
                                      float(arrival), 1 if keep_state else 0, ctypes.byref(rid)),
