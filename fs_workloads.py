@@ -15,7 +15,7 @@ import math
 from dataclasses import dataclass, field, replace
 
 # problem ids shared by both sides of every comparison
-JOHN, STEADY_POLY, CHANNEL, CUBE, POLY_OSEEN, POLY_OSEEN_T = 0, 1, 2, 3, 4, 5
+JOHN, STEADY_POLY, CHANNEL, CUBE, POLY_OSEEN, POLY_OSEEN_T, POLY3 = 0, 1, 2, 3, 4, 5, 6
 
 # Dirichlet side masks: bit s set = side s Dirichlet;
 # sides 0: x=lo, 1: x=hi, 2: y=lo, 3: y=hi, 4: z=lo, 5: z=hi

@@ -242,7 +242,8 @@ enum {
   OR_CHANNEL = 2,      /* Poiseuille profile, U_max 1.5, H 0.41, L 2.2   */
   OR_CUBE = 3,         /* 3D: u = sin t curl(Phi (1,1,1)), Phi=prod sin^2 */
   OR_POLY_OSEEN = 4,   /* u in P2 div-free, p in P1, constant w           */
-  OR_POLY_OSEEN_T = 5  /* (1 + t) times the fields of OR_POLY_OSEEN       */
+  OR_POLY_OSEEN_T = 5, /* (1 + t) times the fields of OR_POLY_OSEEN       */
+  OR_POLY3 = 6         /* 2D: u in P3 div-free, p in P2, constant w       */
 };
 
 /* g(s) = sin^2(pi s) and its derivatives up to order 3. */
@@ -391,6 +392,21 @@ static void exact_fields(int problem, int dim, double t, const double* x,
       }
       break;
     }
+    case OR_POLY3: {
+      /* u = (x^3, -3 x^2 y) (div u = 3x^2 - 3x^2 = 0), p = x^2 - y^2 */
+      u[0] = X * X * X;
+      u[1] = -3 * X * X * Y;
+      du[0] = 3 * X * X;
+      du[1] = 0;
+      du[2] = -6 * X * Y;
+      du[3] = -3 * X * X;
+      lap[0] = 6 * X;
+      lap[1] = -6 * Y;
+      *p = X * X - Y * Y;
+      dp[0] = 2 * X;
+      dp[1] = -2 * Y;
+      break;
+    }
   }
 }
 
@@ -407,7 +423,8 @@ void or_exact(int problem, int dim, double t, double nu, const double* wconst,
   }
   double w[3];
   for (int i = 0; i < dim; ++i)
-    w[i] = ((problem == OR_POLY_OSEEN || problem == OR_POLY_OSEEN_T) && wconst)
+    w[i] = ((problem == OR_POLY_OSEEN || problem == OR_POLY_OSEEN_T ||
+             problem == OR_POLY3) && wconst)
                ? wconst[i] : uu[i];
   if (u) for (int i = 0; i < dim; ++i) u[i] = uu[i];
   if (p) *p = pp;

@@ -28,7 +28,7 @@ _LIB_DIR = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_LIB_DIR, "liboracle.so")
 
 # problem ids (mirrors the enum in fs_oracle.c)
-JOHN, STEADY_POLY, CHANNEL, CUBE, POLY_OSEEN, POLY_OSEEN_T = 0, 1, 2, 3, 4, 5
+JOHN, STEADY_POLY, CHANNEL, CUBE, POLY_OSEEN, POLY_OSEEN_T, POLY3 = 0, 1, 2, 3, 4, 5, 6
 
 _P = ctypes.POINTER
 _d = ctypes.c_double
