@@ -45,6 +45,12 @@ def parse(argv=None):
                         "pressure hierarchies, SpMV and smoothing slot-group depths), or 'auto' "
                         "to run the autotuner at set-up; fix it when a profiler distorts the "
                         "autotuner's timings")
+    p.add_argument("--coarse-degree", type=int, default=0, choices=[0, 2, 3],
+                   help="Chebyshev degree of the smoothing below the finest multigrid level "
+                        "(0: the library default, 2)")
+    p.add_argument("--serial-launches", type=int, default=0, choices=[0, 1],
+                   help="1: plain serialised kernel launches instead of programmatic dependent "
+                        "launches (the library default)")
     p.add_argument("--no-graph", action="store_true",
                    help="launch the solver's kernels one by one instead of replaying captured "
                         "CUDA graphs (for per-kernel profilers, which cannot see kernels inside "
@@ -224,7 +230,7 @@ def aggregate_time(total_s, dist):
 
 
 # ---------------------------------------------------------------------------
-def batched_run(torch, fs, steps, warmup=3):
+def batched_run(torch, fs, steps, warmup=3, opts=None):
     """The batched workload: 96 unit-square instances, N and Re drawn
     log-uniform from the seed, one problem over their union (one launch per
     phase for all instances), FP32 inner / FP64 refinement."""
@@ -237,14 +243,16 @@ def batched_run(torch, fs, steps, warmup=3):
     try:
         tune = fs.fs_autotune(B.prob, reps=3)
         for _ in range(warmup):
-            fs.fs_step(B.prob, 1)
+            fs.fs_step(B.prob, 1, opts)
         torch.cuda.synchronize()
         ms = []
         for _ in range(steps):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record()
-            fs.fs_step(B.prob, 1)
+            torch.cuda.nvtx.range_push("batch_step")  # profilers can select these steps
+            fs.fs_step(B.prob, 1, opts)
+            torch.cuda.nvtx.range_pop()
             e1.record()
             e1.synchronize()
             ms.append(e0.elapsed_time(e1))
@@ -489,6 +497,7 @@ def main():
     k64 = args.fp64_steps
     if prec != fs.FS_PREC_FP64 and k64 > 0:
         S64 = fs.Stepper.from_workload(wl, precision=fs.FS_PREC_FP64, stream=stream.cuda_stream)
+        fs.fs_set_schedule(S64.prob, 0, 0, 0, 0, args.coarse_degree, args.serial_launches)
         tune64 = fs.fs_autotune(S64.prob, reps=5)
         for _ in range(args.warmup):
             fs.fs_step(S64.prob, 1)
@@ -507,6 +516,7 @@ def main():
     S = fs.Stepper.from_workload(wl, precision=prec, stream=stream.cuda_stream)
     # set-up, untimed: pick the multigrid schedule by timing the candidates
     if args.schedule == "auto":
+        fs.fs_set_schedule(S.prob, 0, 0, 0, 0, args.coarse_degree, args.serial_launches)
         tune = fs.fs_autotune(S.prob, reps=5)
     else:
         fs.fs_set_schedule(S.prob, *(int(q) for q in args.schedule.split(",")))
@@ -541,7 +551,8 @@ def main():
     sched = fs.fs_get_schedule(S.prob)
     SE = fs.Stepper.from_workload(wl, precision=prec, stream=stream.cuda_stream)
     fs.fs_set_schedule(SE.prob, sched["tail_rows_velocity"], sched["tail_rows_pressure"],
-                       sched["spmv_group"], sched["smooth_group"])
+                       sched["spmv_group"], sched["smooth_group"], sched["coarse_degree"],
+                       sched["serial_launches"])
     for _ in range(max(0, args.warmup - 1)):
         fs.fs_step(SE.prob, 1)
     xh = torch.empty(ndof, dtype=torch.float64).pin_memory()
@@ -616,7 +627,7 @@ def main():
         except Exception as e:  # noqa: BLE001 - recorded in the JSON line
             return {"error": f"{type(e).__name__}: {e}"}
 
-    batch = block(args.batch_steps > 0, batched_run, torch, fs, args.batch_steps)
+    batch = block(args.batch_steps > 0, batched_run, torch, fs, args.batch_steps, 3, opts)
     cube = block(args.cube_steps > 0, cube_block, torch, fs, stream, flush, args.cube_steps,
                  args.cube_fp64_steps)
     serving = block(args.serve_requests > 0, serving_block, fs, args.serve_requests,

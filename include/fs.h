@@ -68,11 +68,14 @@ typedef enum {
                                     p = sin t (x^2 y z - 1/12)            */
   FS_PROBLEM_POLY_OSEEN = 4,     /* u in P2 (div-free), p in P1, constant
                                     convecting field wconst (exactness)   */
-  FS_PROBLEM_POLY_OSEEN_T = 5    /* (1 + t) times the fields of problem 4:
+  FS_PROBLEM_POLY_OSEEN_T = 5,   /* (1 + t) times the fields of problem 4:
                                     affine in time, so backward Euler
                                     reproduces it exactly at every step
                                     (checks the time level of f, of the
                                     Dirichlet data and of the pin)        */
+  FS_PROBLEM_POLY3 = 6           /* 2D: u = (x^3, -3 x^2 y) (div-free, P3),
+                                    p = x^2 - y^2 (P2), constant convecting
+                                    field wconst: exact for P3/P2         */
 } fs_problem_kind;
 
 typedef enum {
@@ -179,6 +182,23 @@ int fs_problem_destroy(fs_problem* prob);
  * on a batched mesh applies one description to all instances. */
 int fs_problem_create_batch(fs_mesh* mesh, const fs_problem_desc* descs,
                             int count, void* stream, fs_problem** out);
+
+/* A Taylor-Hood P3/P2 problem on a single 2D mesh (paper Sec. 4.1, the
+ * P3-P2 experiment, which the paper solves by IPCS): P3 velocity (vertices,
+ * then two nodes per edge in the lexicographic order of the edges, the one
+ * nearer the edge's smaller vertex first, then one interior node per cell)
+ * and P2 pressure (vertices, then one node per edge).  State layout
+ * [u_x (n3) | u_y (n3) | p (np)] in that numbering (fs_problem_sizes).
+ * Assembles the step-invariant blocks on the GPU; stepped by fs_step_ipcs,
+ * with fs_get_state / fs_set_state and fs_assemble_step (no export) also
+ * available; the coupled solver calls answer FS_ERR_UNSUPPORTED.  dt must be
+ * finite; FS_ERR_UNSUPPORTED for a batched or 3D mesh.  Synchronises. */
+int fs_problem_create_p3(fs_mesh* mesh, const fs_problem_desc* desc, void* stream,
+                         fs_problem** out);
+
+/* Sizes of a problem's unknowns (host array of 3): velocity nodes per
+ * component, pressure nodes, n_dof. */
+int fs_problem_sizes(const fs_problem* prob, int64_t* sizes);
 
 /* Assembles the Oseen system of the step t -> t_next (paper Sec. 2.2.1,
  * Oseen equation; BForm/LForm of Sec. 3.1) with the convecting velocity
@@ -435,6 +455,19 @@ typedef struct {
   int32_t spmv_group;    /* SELL slots a thread issues together in the SpMV:
                             4, 6 or 8; 0 = 6 in FP32, 4 in FP64 */
   int32_t smooth_group;  /* ... in the smoothing passes: 4 or 6; 0 = 4    */
+  int32_t coarse_degree; /* degree of the Chebyshev smoother on the levels
+                            below the finest (pre and post): 3 or 2; 0 = 2.
+                            Unlike the other fields it changes the
+                            preconditioner, so iteration counts (not the
+                            solution beyond rtol) depend on it; the
+                            autotuner keeps the value in place          */
+  int32_t serial_launches; /* 0: the solver's kernels are launched as
+                            programmatic dependent launches (a kernel may
+                            be scheduled while its predecessor drains and
+                            waits for that predecessor's completion before
+                            its first memory access); 1: plain serialised
+                            launches.  Timing only: results are identical.
+                            The autotuner keeps the value in place       */
 } fs_schedule;
 typedef struct {
   int candidates;        /* schedules timed                                  */

@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libfs.so")
 SOURCES = ["fs_mesh.cpp", "fs_mg.cpp", "fs_api.cpp", "fs_assembly.cu", "fs_linalg.cu",
-           "fs_krylov.cu", "fs_residual.cu", "fs_serve.cpp", "fs_ipcs.cu"]
+           "fs_krylov.cu", "fs_residual.cu", "fs_serve.cpp", "fs_ipcs.cu", "fs_p3.cpp"]
 HEADERS = ["fs_internal.h", "fs_device.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -35,6 +35,9 @@ namespace fs {
 namespace {
 thread_local std::string g_err;
 thread_local bool g_capturing = false;
+// launch mode of the calling thread's current API call: -1 outside a call
+// on a problem (overlap on), else 1 / 0 from the problem's schedule
+thread_local int g_overlap = -1;
 std::atomic<int64_t> g_launches{0};
 
 RefTensors g_ref2, g_ref3;
@@ -46,6 +49,8 @@ void set_error(const std::string& msg) { g_err = msg; }
 void count_launches(int64_t n) {
   if (!g_capturing) g_launches.fetch_add(n, std::memory_order_relaxed);
 }
+
+bool launch_overlap() { return g_overlap != 0; }
 
 }  // namespace fs
 
@@ -150,6 +155,13 @@ struct fs_problem {
   int32_t* pinned = nullptr;
   int npinned = 0;
   std::vector<int32_t> pinned_host;  // the same vertices, on the host
+  // Taylor-Hood P3/P2 problems (fs_problem_create_p3): the P2 pressure map,
+  // pressure node coordinates, reference integrals; stepped by IPCS only
+  bool p3 = false;
+  int32_t* c2p = nullptr;
+  double* pxyz = nullptr;
+  RefP3* p3ref = nullptr;
+  int64_t p3nnzA = 0;
   // Picard iteration (allocated on first use): the state at the start of the
   // step, the convecting field of the current iterate, norm scratch
   double *xn = nullptr, *wpic = nullptr, *nrm = nullptr;
@@ -161,6 +173,11 @@ struct fs_problem {
   double *ip_dA = nullptr, *ip_dM = nullptr, *ip_dK = nullptr, *ip_part = nullptr;
   double *ip_sc = nullptr, *ip_nrm = nullptr;
   uint8_t* ip_fixed = nullptr;
+  // pressure stage preconditioned by a V-cycle of the pressure Laplacian
+  // hierarchy (P2/P1 problems): old residual, FP32 copies for an FP32 hierarchy
+  bool ip_mg = false;
+  double* ip_t = nullptr;
+  float *ip_rf = nullptr, *ip_zf = nullptr;
   int64_t* mrp = nullptr;  // paper-order monolithic row pointers (export)
   const int32_t* nat = nullptr;          // internal P2 node -> paper id
   double *natbuf = nullptr, *natbuf2 = nullptr;  // boundary conversions (lazy)
@@ -494,6 +511,7 @@ void apply_groups(fs_problem* P, Precision<T>& pr, const fs_schedule& sc) {
   (void)P;
   pr.op.group = sc.spmv_group;
   pr.HA.group = pr.HK.group = sc.smooth_group ? sc.smooth_group : 4;
+  pr.HA.coarse_deg = pr.HK.coarse_deg = sc.coarse_degree == 3 ? 3 : 2;
 }
 
 // The fused cluster kernel takes the levels with at most tail_rows rows
@@ -826,9 +844,23 @@ int assemble_impl(fs_problem* P, double t_next, const double* w = nullptr,
   const int64_t nnzA = me.A.nnz();
   if (!w) w = P->x;
   if (!u_old) u_old = P->x;
-  FS_CUDA(cudaMemcpyAsync(P->valA, P->baseA, sizeof(double) * nnzA, cudaMemcpyDeviceToDevice, s));
   const bool constw = P->desc.problem == FS_PROBLEM_POLY_OSEEN ||
-                      P->desc.problem == FS_PROBLEM_POLY_OSEEN_T;
+                      P->desc.problem == FS_PROBLEM_POLY_OSEEN_T ||
+                      P->desc.problem == FS_PROBLEM_POLY3;
+  if (P->p3) {
+    const int64_t nnz3 = P->p3nnzA;
+    FS_CUDA(cudaMemcpyAsync(P->valA, P->baseA, sizeof(double) * nnz3, cudaMemcpyDeviceToDevice,
+                            s));
+    launch_p3_conv(P->dm, P->p3ref, constw ? nullptr : w, P->n2,
+                   constw ? P->desc.wconst : nullptr, P->valA, s);
+    launch_bc_rows<double>(P->dm, P->valA, s);
+    launch_eval_load(P->dm, P->ph, t_next, 1.0 / P->desc.dt, u_old, P->F, s);
+    launch_rhs(P->dm, P->ph, t_next, P->Mv, P->F, P->pinned, P->npinned, P->b, s);
+    FS_TRY(check_launch("P3/P2 assembly"));
+    P->assembled = true;
+    return FS_OK;
+  }
+  FS_CUDA(cudaMemcpyAsync(P->valA, P->baseA, sizeof(double) * nnzA, cudaMemcpyDeviceToDevice, s));
   launch_assemble_conv(P->dm, me.color_ptr, constw ? nullptr : w, P->n2,
                        constw ? P->desc.wconst : nullptr, P->valA, P->desc.deterministic != 0, s);
   launch_bc_rows<double>(P->dm, P->valA, s);
@@ -1179,6 +1211,16 @@ int solve_opts(const fs_solve_opts* opts, fs_solve_opts& o) {
   return FS_OK;
 }
 
+// Sets the calling thread's launch mode from the problem's schedule for the
+// duration of one API call.
+struct OverlapScope {
+  int old;
+  explicit OverlapScope(const fs_problem* P) : old(g_overlap) {
+    g_overlap = (P && P->sched.serial_launches) ? 0 : 1;
+  }
+  ~OverlapScope() { g_overlap = old; }
+};
+
 }  // namespace
 
 // ===========================================================================
@@ -1286,6 +1328,140 @@ int fs_problem_create(fs_mesh* mesh, const fs_problem_desc* desc, void* stream,
   return fs_problem_create_batch(mesh, d.data(), (int)d.size(), stream, out);
 }
 
+int fs_problem_create_p3(fs_mesh* mesh, const fs_problem_desc* desc, void* stream,
+                         fs_problem** out) {
+  if (!mesh || !desc || !out) {
+    set_error("fs_problem_create_p3: null argument");
+    return FS_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  const Mesh& me = mesh->m;
+  const fs_problem_desc& d = *desc;
+  if (me.dim != 2 || me.inst.size() != 1) {
+    set_error("fs_problem_create_p3: P3/P2 problems need a single 2D mesh");
+    return FS_ERR_UNSUPPORTED;
+  }
+  if (!(d.dt > 0) || !std::isfinite(d.dt) || !(d.nu > 0) || d.problem < 0 || d.problem > 6 ||
+      d.problem == FS_PROBLEM_CUBE) {
+    set_error("fs_problem_create_p3: need a finite dt > 0, nu > 0 and a 2D problem kind");
+    return FS_ERR_INVALID_ARG;
+  }
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    set_error("fs_problem_create_p3: no CUDA device");
+    return FS_ERR_CUDA;
+  }
+  P3Tables T;
+  FS_TRY(build_p3_tables(me, T));
+  std::unique_ptr<fs_problem> P(new fs_problem);
+  P->mesh = mesh;
+  P->desc = d;
+  P->inst_desc.assign(1, d);
+  P->nseg = 1;
+  P->dim = 2;
+  P->p3 = true;
+  P->n2 = T.n3;
+  P->nv = T.np;
+  P->ndof = 2 * T.n3 + T.np;
+  P->t = d.t0;
+  if (stream) {
+    P->stream = (cudaStream_t)stream;
+  } else {
+    FS_CUDA(cudaStreamCreateWithFlags(&P->stream, cudaStreamNonBlocking));
+    P->own_stream = true;
+  }
+  FS_CUDA(cudaEventCreateWithFlags(&P->ev, cudaEventDisableTiming));
+  cudaStream_t s = P->stream;
+  DMesh& dm = P->dm;
+  dm.dim = 2;
+  dm.nloc = 10;
+  dm.nb = 6;
+  dm.nv = T.np;
+  dm.n2 = T.n3;
+  dm.ncell = T.ncell;
+  dm.ndir = (int64_t)T.dlist.size();
+  {
+    int32_t *c2u, *dl, *c2p;
+    double *xyz, *pxyz;
+    uint8_t* dir;
+    FS_TRY(P->upload(&c2u, T.c2u));
+    FS_TRY(P->upload(&xyz, T.xyz));
+    FS_TRY(P->upload(&dir, T.dir));
+    FS_TRY(P->upload(&dl, T.dlist));
+    FS_TRY(P->upload(&c2p, T.c2p));
+    FS_TRY(P->upload(&pxyz, T.pxyz));
+    dm.c2d = c2u; dm.p2xyz = xyz; dm.dirichlet = dir; dm.dlist = dl;
+    P->c2p = c2p;
+    P->pxyz = pxyz;
+    int32_t *a, *b, *c, *e, *f, *g, *h, *k;
+    FS_TRY(P->upload(&a, T.A.rowptr)); FS_TRY(P->upload(&b, T.A.col));
+    FS_TRY(P->upload(&c, T.B.rowptr)); FS_TRY(P->upload(&e, T.B.col));
+    FS_TRY(P->upload(&f, T.BT.rowptr)); FS_TRY(P->upload(&g, T.BT.col));
+    FS_TRY(P->upload(&h, T.Kp.rowptr)); FS_TRY(P->upload(&k, T.Kp.col));
+    dm.rpA = a; dm.ciA = b; dm.rpB = c; dm.ciB = e; dm.rpBT = f; dm.ciBT = g;
+    dm.rpK = h; dm.ciK = k;
+    uint8_t *pa, *pb, *pbt, *pk;
+    FS_TRY(P->upload(&pa, T.posA)); FS_TRY(P->upload(&pb, T.posB));
+    FS_TRY(P->upload(&pbt, T.posBT)); FS_TRY(P->upload(&pk, T.posK));
+    dm.posA = pa; dm.posB = pb; dm.posBT = pbt; dm.posK = pk;
+    static RefP3 ref;
+    static bool have_ref = false;
+    static std::mutex ref_mu;
+    {
+      std::lock_guard<std::mutex> lk(ref_mu);
+      if (!have_ref) {
+        p3_ref_tensors(ref);
+        have_ref = true;
+      }
+    }
+    std::vector<RefP3> rv(1, ref);
+    FS_TRY(P->upload(&P->p3ref, rv));
+  }
+  P->ph.kind = d.problem;
+  P->ph.nu = d.nu;
+  for (int a = 0; a < 3; ++a) P->ph.wconst[a] = d.wconst[a];
+  const int64_t nnzA = T.A.nnz(), nnzB = T.B.nnz(), nnzBT = T.BT.nnz(), nnzK = T.Kp.nnz();
+  P->p3nnzA = nnzA;
+  FS_TRY(P->alloc(&P->baseA, nnzA));
+  FS_TRY(P->alloc(&P->Mv, nnzA));
+  FS_TRY(P->alloc(&P->valA, nnzA));
+  FS_TRY(P->alloc(&P->B, nnzB * 2));
+  FS_TRY(P->alloc(&P->BT, nnzBT * 2));
+  FS_TRY(P->alloc(&P->Kp, nnzK));
+  for (auto pr : {std::make_pair(P->baseA, nnzA), std::make_pair(P->Mv, nnzA),
+                  std::make_pair(P->B, nnzB * 2), std::make_pair(P->BT, nnzBT * 2),
+                  std::make_pair(P->Kp, nnzK)})
+    FS_CUDA(cudaMemsetAsync(pr.first, 0, sizeof(double) * pr.second, s));
+  launch_p3_base(dm, P->c2p, P->p3ref, 1.0 / d.dt, d.nu, P->baseA, P->Mv, P->B, P->BT, P->Kp,
+                 s);
+  FS_TRY(check_launch("P3/P2 step-invariant blocks"));
+  if (d.pin_pressure) {
+    std::vector<int32_t> pin(1, 0);
+    FS_TRY(P->upload(&P->pinned, pin));
+    P->npinned = 1;
+    P->pinned_host = pin;
+  }
+  FS_TRY(P->alloc(&P->x, P->ndof));
+  FS_TRY(P->alloc(&P->b, P->ndof));
+  FS_TRY(P->alloc(&P->F, 2 * T.n3));
+  launch_p3_exact_state(dm, P->ph, d.t0, d.init == 1, P->pxyz, P->x, s);
+  FS_TRY(check_launch("P3/P2 initial state"));
+  FS_CUDA(cudaStreamSynchronize(s));
+  *out = P.release();
+  return FS_OK;
+}
+
+int fs_problem_sizes(const fs_problem* P, int64_t* sizes) {
+  if (!P || !sizes) {
+    set_error("fs_problem_sizes: null argument");
+    return FS_ERR_INVALID_ARG;
+  }
+  sizes[0] = P->n2;
+  sizes[1] = P->nv;
+  sizes[2] = P->ndof;
+  return FS_OK;
+}
+
 int fs_problem_create_batch(fs_mesh* mesh, const fs_problem_desc* descs, int count,
                             void* stream, fs_problem** out) {
   if (!mesh || !descs || !out) {
@@ -1301,7 +1477,7 @@ int fs_problem_create_batch(fs_mesh* mesh, const fs_problem_desc* descs, int cou
   const fs_problem_desc& d0 = descs[0];
   for (int i = 0; i < count; ++i) {
     const fs_problem_desc& d = descs[i];
-    if (!(d.dt > 0) || !(d.nu > 0) || d.problem < 0 || d.problem > 5 ||
+    if (!(d.dt > 0) || !(d.nu > 0) || d.problem < 0 || d.problem > 6 ||
         (d.precision != FS_PREC_FP64 && d.precision != FS_PREC_FP32_REFINE)) {
       set_error("fs_problem_create: need dt > 0, nu > 0, a known problem and precision");
       return FS_ERR_INVALID_ARG;
@@ -1556,6 +1732,10 @@ int fs_assemble_step(fs_problem* P, double t_next, double* val_out, double* b_ou
     set_error("fs_assemble_step: null problem");
     return FS_ERR_INVALID_ARG;
   }
+  if (P->p3 && (val_out || b_out)) {
+    set_error("fs_assemble_step: no monolithic export for P3/P2 problems");
+    return FS_ERR_UNSUPPORTED;
+  }
   FS_TRY(assemble_impl(P, t_next));
   if (val_out) {
     if (!P->mrp) {
@@ -1584,6 +1764,11 @@ int fs_assemble_step(fs_problem* P, double t_next, double* val_out, double* b_ou
 }
 
 int fs_solve(fs_problem* P, const fs_solve_opts* opts, double* x, fs_solve_stats* stats) {
+  OverlapScope overlap(P);
+  if (P && P->p3) {
+    set_error("fs_solve: P3/P2 problems are stepped by fs_step_ipcs");
+    return FS_ERR_UNSUPPORTED;
+  }
   if (!P) {
     set_error("fs_solve: null problem");
     return FS_ERR_INVALID_ARG;
@@ -1634,6 +1819,11 @@ static int start_step_solve(fs_problem* P) {
 }
 
 int fs_step_begin(fs_problem* P, int nsteps, const fs_solve_opts* opts) {
+  OverlapScope overlap(P);
+  if (P && P->p3) {
+    set_error("fs_step: P3/P2 problems are stepped by fs_step_ipcs");
+    return FS_ERR_UNSUPPORTED;
+  }
   if (!P || nsteps < 1) {
     set_error("fs_step_begin: bad argument");
     return FS_ERR_INVALID_ARG;
@@ -1655,6 +1845,7 @@ int fs_step_begin(fs_problem* P, int nsteps, const fs_solve_opts* opts) {
 }
 
 int fs_step_poll(fs_problem* P, int wait, int* done) {
+  OverlapScope overlap(P);
   if (!P || !done) {
     set_error("fs_step_poll: null argument");
     return FS_ERR_INVALID_ARG;
@@ -1693,6 +1884,7 @@ int fs_step_poll(fs_problem* P, int wait, int* done) {
 }
 
 int fs_step(fs_problem* P, int nsteps, const fs_solve_opts* opts, fs_solve_stats* per_step) {
+  OverlapScope overlap(P);
   if (!P || nsteps < 0) {
     set_error("fs_step: bad argument");
     return FS_ERR_INVALID_ARG;
@@ -1787,6 +1979,10 @@ static int picard_iterate(fs_problem* P, double t1, bool extrapolate, double tol
 
 static int picard_args(fs_problem* P, const fs_solve_opts* opts, double tol, int maxit,
                        const char* who) {
+  if (P && P->p3) {
+    set_error("Picard iteration: P3/P2 problems are stepped by fs_step_ipcs");
+    return FS_ERR_UNSUPPORTED;
+  }
   if (!P || !(tol > 0) || maxit < 1) {
     set_error(std::string(who) + ": bad argument");
     return FS_ERR_INVALID_ARG;
@@ -1805,6 +2001,7 @@ static int picard_args(fs_problem* P, const fs_solve_opts* opts, double tol, int
 
 int fs_step_picard(fs_problem* P, int nsteps, const fs_solve_opts* opts, double nl_tol,
                    int max_picard, fs_picard_stats* per_step) {
+  OverlapScope overlap(P);
   FS_TRY(picard_args(P, opts, nl_tol, max_picard, "fs_step_picard"));
   if (nsteps < 0 || !std::isfinite(P->desc.dt)) {
     set_error("fs_step_picard: need nsteps >= 0 and a finite dt");
@@ -1822,6 +2019,7 @@ int fs_step_picard(fs_problem* P, int nsteps, const fs_solve_opts* opts, double 
 
 int fs_solve_steady(fs_problem* P, const fs_solve_opts* opts, double nl_tol, int max_picard,
                     fs_picard_stats* stats) {
+  OverlapScope overlap(P);
   FS_TRY(picard_args(P, opts, nl_tol, max_picard, "fs_solve_steady"));
   if (!std::isinf(P->desc.dt)) {
     set_error("fs_solve_steady: create the problem with dt = inf (no mass term)");
@@ -1836,8 +2034,9 @@ int fs_solve_steady(fs_problem* P, const fs_solve_opts* opts, double nl_tol, int
 
 // ---------------------------------------------------------------------------
 // Incremental pressure-correction stepping (paper Sec. 2.2.1, IPCS): three
-// symmetric positive definite systems per step, each solved by
-// Jacobi-preconditioned CG in FP64 (kernels in fs_ipcs.cu).
+// symmetric positive definite systems per step, each solved by CG in FP64
+// (kernels in fs_ipcs.cu): Jacobi-preconditioned for the velocity stages,
+// multigrid-preconditioned for the P2/P1 pressure stage.
 // ---------------------------------------------------------------------------
 static int ipcs_setup(fs_problem* P) {
   if (P->ip_us) return FS_OK;
@@ -1853,6 +2052,18 @@ static int ipcs_setup(fs_problem* P) {
   std::vector<uint8_t> fixed(nv, 0);
   for (int32_t q : P->pinned_host) fixed[q] = 1;
   FS_TRY(P->upload(&P->ip_fixed, fixed));
+  // The pressure hierarchy's Laplacian fixes the same rows as the stage-2
+  // operator (the pin, on a closed domain), so one V-cycle of it is a
+  // spectrally equivalent preconditioner there.
+  const bool fp64 = P->desc.precision == FS_PREC_FP64;
+  P->ip_mg = !P->p3 && (fp64 ? P->p64.HK.nlev : P->p32.HK.nlev) > 0;
+  if (P->ip_mg) {
+    FS_TRY(P->alloc(&P->ip_t, nv));
+    if (!fp64) {
+      FS_TRY(P->alloc(&P->ip_rf, nv));
+      FS_TRY(P->alloc(&P->ip_zf, nv));
+    }
+  }
   cudaStream_t s = P->stream;
   launch_ipcs_dinv(P->dm, 0, P->baseA, nullptr, P->ip_dA, s);
   launch_ipcs_dinv(P->dm, 0, P->Mv, nullptr, P->ip_dM, s);
@@ -1860,10 +2071,27 @@ static int ipcs_setup(fs_problem* P) {
   return check_launch("ipcs set-up");
 }
 
+// z = one V-cycle of the pressure hierarchy on r (FP64 I/O; an FP32
+// hierarchy works on converted copies).
+static void ipcs_vcycle(fs_problem* P, const double* r, double* z) {
+  cudaStream_t s = P->stream;
+  const int64_t n = P->nv;
+  if (P->desc.precision == FS_PREC_FP64) {
+    launch_vcycle_scalar<double>(P->p64.HK, r, z, n, s);
+  } else {
+    launch_convert<double, float>(r, P->ip_rf, n, nullptr, 0, s);
+    launch_vcycle_scalar<float>(P->p32.HK, P->ip_rf, P->ip_zf, n, s);
+    launch_convert<float, double>(P->ip_zf, z, n, nullptr, 0, s);
+  }
+}
+
 // Solves A x = rhs (which 0: scalar P2 block `vals` on every component; 1:
-// the P1 Laplacian) by Jacobi-preconditioned CG from the guess in x (whose
-// fixed unknowns are set first), to a recursive relative residual of rtol,
-// checked every 8 iterations; reports the true relative residual.
+// the pressure Laplacian) by CG from the guess in x (whose fixed unknowns are
+// set first), to a recursive relative residual of rtol, checked every 8
+// iterations; reports the true relative residual.  The velocity stages and
+// P3/P2 pressure take Jacobi preconditioning; the P2/P1 pressure stage takes
+// one V-cycle per iteration in flexible CG (Polak-Ribiere beta), which keeps
+// the iteration count flat in the mesh size.
 static int ipcs_cg(fs_problem* P, int which, const double* vals, const double* dinv,
                    const double* rhs, double* x, double rtol, int max_iter, int* iters,
                    double* relres) {
@@ -1871,10 +2099,15 @@ static int ipcs_cg(fs_problem* P, int which, const double* vals, const double* d
   const DMesh& m = P->dm;
   const int64_t n = which == 1 ? P->nv : (int64_t)P->dim * P->n2;
   const uint8_t* fixed = which == 1 ? P->ip_fixed : nullptr;
+  const bool mg = which == 1 && P->ip_mg;
   launch_ipcs_fix(m, which, fixed, rhs, x, s);
   launch_diff_norms(rhs, rhs, n, P->ip_nrm, s);
   launch_ipcs_apply(m, which, vals, fixed, x, P->ip_q, nullptr, s);
   launch_cg_init(n, rhs, P->ip_q, dinv, P->ip_r, P->ip_z, P->ip_p, P->ip_part, P->ip_sc, s);
+  if (mg) {
+    ipcs_vcycle(P, P->ip_r, P->ip_z);
+    launch_cg_dots_flex(n, fixed, P->ip_r, P->ip_t, P->ip_z, P->ip_p, 1, P->ip_part, P->ip_sc, s);
+  }
   FS_TRY(check_launch("ipcs cg init"));
   double h[4] = {0, 0, 0, 0};
   FS_CUDA(cudaMemcpyAsync(h, P->ip_nrm, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -1888,7 +2121,15 @@ static int ipcs_cg(fs_problem* P, int which, const double* vals, const double* d
     for (int c = 0; c < 8 && it < max_iter; ++c, ++it) {
       const int nb = launch_ipcs_apply(m, which, vals, fixed, P->ip_p, P->ip_q, P->ip_part, s);
       launch_cg_alpha(P->ip_part, nb, P->ip_sc, s);
-      launch_cg_update(n, P->ip_sc, P->ip_p, P->ip_q, dinv, x, P->ip_r, P->ip_z, P->ip_part, s);
+      if (mg) {
+        launch_cg_update_flex(n, P->ip_sc, P->ip_p, P->ip_q, x, P->ip_r, P->ip_t, P->ip_part, s);
+        ipcs_vcycle(P, P->ip_r, P->ip_z);
+        launch_cg_dots_flex(n, fixed, P->ip_r, P->ip_t, P->ip_z, P->ip_p, 0, P->ip_part,
+                            P->ip_sc, s);
+      } else {
+        launch_cg_update(n, P->ip_sc, P->ip_p, P->ip_q, dinv, x, P->ip_r, P->ip_z, P->ip_part,
+                         s);
+      }
       launch_cg_dir(n, P->ip_sc, P->ip_z, P->ip_p, s);
     }
     FS_TRY(check_launch("ipcs cg"));
@@ -1943,6 +2184,7 @@ static int ipcs_step_impl(fs_problem* P, double rtol, int max_iter, fs_ipcs_stat
 }
 
 int fs_step_ipcs(fs_problem* P, int nsteps, double rtol, int max_iter, fs_ipcs_stats* per_step) {
+  OverlapScope overlap(P);
   if (!P || nsteps < 0 || !(rtol > 0) || max_iter < 1) {
     set_error("fs_step_ipcs: bad argument");
     return FS_ERR_INVALID_ARG;
@@ -1986,6 +2228,11 @@ int fs_instance_stats(const fs_problem* P, fs_solve_stats* per_instance) {
 }
 
 int fs_apply_operator(fs_problem* P, const double* x, double* y) {
+  OverlapScope overlap(P);
+  if (P && P->p3) {
+    set_error("fs_apply_operator: P3/P2 problems are stepped by fs_step_ipcs");
+    return FS_ERR_UNSUPPORTED;
+  }
   if (!P || !x || !y) {
     set_error("fs_apply_operator: null argument");
     return FS_ERR_INVALID_ARG;
@@ -2007,7 +2254,10 @@ int fs_get_state(fs_problem* P, double* x_out, int host, double* t_out) {
     set_error("fs_get_state: null problem");
     return FS_ERR_INVALID_ARG;
   }
-  if (x_out) {
+  if (x_out && P->p3) {  // the P3/P2 state is stored in its boundary order
+    FS_CUDA(cudaMemcpyAsync(x_out, P->x, sizeof(double) * P->ndof,
+                            host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, P->stream));
+  } else if (x_out) {
     FS_TRY(nat_buffers(P));
     launch_dofs_perm(P->dm, P->nat, P->x, P->natbuf, 1, P->stream);
     FS_TRY(check_launch("fs_get_state"));
@@ -2024,7 +2274,10 @@ int fs_set_state(fs_problem* P, const double* x_in, int host, double t) {
     set_error("fs_set_state: null problem");
     return FS_ERR_INVALID_ARG;
   }
-  if (x_in) {
+  if (x_in && P->p3) {
+    FS_CUDA(cudaMemcpyAsync(P->x, x_in, sizeof(double) * P->ndof,
+                            host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, P->stream));
+  } else if (x_in) {
     FS_TRY(nat_buffers(P));
     FS_CUDA(cudaMemcpyAsync(P->natbuf, x_in, sizeof(double) * P->ndof,
                             host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, P->stream));
@@ -2042,6 +2295,11 @@ int fs_set_state(fs_problem* P, const double* x_in, int host, double t) {
 int64_t fs_launch_count(void) { return g_launches.load(); }
 
 int fs_profile_kernel(fs_problem* P, int kernel, int reps, double* avg_ms, double* alg_bytes) {
+  OverlapScope overlap(P);
+  if (P && P->p3) {
+    set_error("fs_profile_kernel: P3/P2 problems are stepped by fs_step_ipcs");
+    return FS_ERR_UNSUPPORTED;
+  }
   if (!P || reps < 1 || !avg_ms || !alg_bytes) {
     set_error("fs_profile_kernel: bad argument");
     return FS_ERR_INVALID_ARG;
@@ -2226,11 +2484,16 @@ int fs_get_schedule(const fs_problem* P, fs_schedule* out) {
 }
 
 int fs_set_schedule(fs_problem* P, const fs_schedule* sc) {
+  if (P && P->p3) {
+    set_error("fs_set_schedule: P3/P2 problems are stepped by fs_step_ipcs");
+    return FS_ERR_UNSUPPORTED;
+  }
   const auto in = [](int v, std::initializer_list<int> ok) {
     return std::find(ok.begin(), ok.end(), v) != ok.end();
   };
   if (!P || !sc || sc->tail_rows_velocity < 0 || sc->tail_rows_pressure < 0 ||
-      !in(sc->spmv_group, {0, 4, 6, 8}) || !in(sc->smooth_group, {0, 4, 6})) {
+      !in(sc->spmv_group, {0, 4, 6, 8}) || !in(sc->smooth_group, {0, 4, 6}) ||
+      !in(sc->coarse_degree, {0, 2, 3}) || !in(sc->serial_launches, {0, 1})) {
     set_error("fs_set_schedule: bad argument");
     return FS_ERR_INVALID_ARG;
   }
@@ -2242,6 +2505,11 @@ int fs_set_schedule(fs_problem* P, const fs_schedule* sc) {
 }
 
 int fs_autotune(fs_problem* P, int reps, fs_tune_report* report) {
+  OverlapScope overlap(P);
+  if (P && P->p3) {
+    set_error("fs_autotune: P3/P2 problems are stepped by fs_step_ipcs");
+    return FS_ERR_UNSUPPORTED;
+  }
   if (!P || reps < 1) {
     set_error("fs_autotune: bad argument");
     return FS_ERR_INVALID_ARG;

@@ -513,6 +513,16 @@ __device__ Fields eval_fields(const DPhys& ph, double nu, const double* x, doubl
       }
       break;
     }
+    case FS_PROBLEM_POLY3: {
+      // u = (x^3, -3 x^2 y), p = x^2 - y^2; f = -nu Lap u + (w.grad) u + grad p
+      const double w1 = ph.wconst[0], w2 = ph.wconst[1];
+      F.u[0] = X * X * X;
+      F.u[1] = -3 * X * X * Y;
+      F.p = X * X - Y * Y;
+      F.f[0] = -6 * nu * X + 3 * X * X * w1 + 2 * X;
+      F.f[1] = 6 * nu * Y - 6 * X * Y * w1 - 3 * X * X * w2 - 2 * Y;
+      break;
+    }
     default:
       break;
   }
@@ -792,6 +802,173 @@ void launch_dofs_perm(const DMesh& m, const int32_t* nat, const double* in, doub
                       int to_nat, cudaStream_t s) {
   int64_t n = m.dim * m.n2 + m.nv;
   k_dofs_perm<<<grid_for(n, 256), 256, 0, s>>>(m.dim, m.n2, m.nv, nat, in, out, to_nat);
+  count_launches(1);
+}
+
+// ---------------------------------------------------------------------------
+// Taylor-Hood P3/P2 on triangles (paper Sec. 4.1, the P3-P2 experiment):
+// the same blocks with the P3 velocity map c2u (m.c2d, 10 nodes per cell)
+// and the P2 pressure map c2p (6 per cell); reference integrals R (a RefP3
+// in device memory; see fs_internal.h) times |det J|.  A thread per cell,
+// FP64 atomics into the slot-indexed values.
+// ---------------------------------------------------------------------------
+namespace {
+
+__device__ __forceinline__ double p3_grads(const DMesh& m, int64_t e, int32_t (&g)[10],
+                                           double (&gl)[3][2]) {
+#pragma unroll
+  for (int a = 0; a < 10; ++a) g[a] = __ldg(m.c2d + e * 10 + a);
+  double xv[3][2];
+#pragma unroll
+  for (int v = 0; v < 3; ++v)
+#pragma unroll
+    for (int a = 0; a < 2; ++a) xv[v][a] = __ldg(m.p2xyz + (int64_t)g[v] * 2 + a);
+  return bary_grads<2>(xv, gl);
+}
+
+__global__ void __launch_bounds__(128) k_p3_base(DMesh m, const int32_t* __restrict__ c2p,
+                                                 const RefP3* __restrict__ R, double mass_coef,
+                                                 double nu, double* __restrict__ base,
+                                                 double* __restrict__ Mv,
+                                                 double* __restrict__ B,
+                                                 double* __restrict__ BT,
+                                                 double* __restrict__ Kp) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m.ncell;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int32_t g[10], gp[6];
+    double gl[3][2];
+    const double D = p3_grads(m, e, g, gl);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) gp[q] = __ldg(c2p + e * 6 + q);
+    double G[3][3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int t = 0; t < 3; ++t) G[r][t] = gl[r][0] * gl[t][0] + gl[r][1] * gl[t][1];
+    for (int i = 0; i < 10; ++i) {
+      const int32_t rb = __ldg(m.rpA + g[i]);
+      const uint8_t* pos = m.posA + (e * 10 + i) * 10;
+      for (int j = 0; j < 10; ++j) {
+        double kk = 0;
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+          for (int t = 0; t < 3; ++t) kk += G[r][t] * R->stiff[i][j][r][t];
+        const double mm = D * R->mass[i][j];
+        atomicAdd(base + rb + pos[j], mass_coef * mm + nu * D * kk);
+        atomicAdd(Mv + rb + pos[j], mm);
+      }
+    }
+    for (int q = 0; q < 6; ++q)
+      for (int j = 0; j < 10; ++j) {
+        double bv[2];
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          double s = 0;
+#pragma unroll
+          for (int r = 0; r < 3; ++r) s += gl[r][c] * R->div[q][j][r];
+          bv[c] = D * s;
+        }
+        const int64_t sB = __ldg(m.rpB + gp[q]) + m.posB[(e * 6 + q) * 10 + j];
+        const int64_t sBT = __ldg(m.rpBT + g[j]) + m.posBT[(e * 10 + j) * 6 + q];
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          atomicAdd(B + sB * 2 + c, bv[c]);
+          atomicAdd(BT + sBT * 2 + c, bv[c]);
+        }
+      }
+    for (int q = 0; q < 6; ++q) {
+      const int32_t rb = __ldg(m.rpK + gp[q]);
+      for (int s2 = 0; s2 < 6; ++s2) {
+        double kk = 0;
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+          for (int t = 0; t < 3; ++t) kk += G[r][t] * R->pstiff[q][s2][r][t];
+        atomicAdd(Kp + rb + m.posK[(e * 6 + q) * 6 + s2], D * kk);
+      }
+    }
+  }
+}
+
+// valA += N(w) of every cell (rows of Dirichlet nodes skipped):
+//   N_ij = D sum_k sum_r (w_k . grad lambda_r) conv[i][k][j][r]
+__global__ void __launch_bounds__(128) k_p3_conv(DMesh m, const RefP3* __restrict__ R,
+                                                 const double* __restrict__ w, int64_t ldw,
+                                                 double wc0, double wc1,
+                                                 double* __restrict__ valA) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m.ncell;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int32_t g[10];
+    double gl[3][2];
+    const double D = p3_grads(m, e, g, gl);
+    double cw[10][3];
+#pragma unroll
+    for (int k = 0; k < 10; ++k) {
+      const double w0 = w ? __ldg(w + g[k]) : wc0, w1 = w ? __ldg(w + ldw + g[k]) : wc1;
+#pragma unroll
+      for (int r = 0; r < 3; ++r) cw[k][r] = D * (w0 * gl[r][0] + w1 * gl[r][1]);
+    }
+    for (int i = 0; i < 10; ++i) {
+      if (__ldg(m.dirichlet + g[i])) continue;
+      double acc[10];
+#pragma unroll
+      for (int j = 0; j < 10; ++j) acc[j] = 0;
+      for (int k = 0; k < 10; ++k)
+#pragma unroll
+        for (int j = 0; j < 10; ++j)
+#pragma unroll
+          for (int r = 0; r < 3; ++r) acc[j] += cw[k][r] * R->conv[i][k][j][r];
+      const int32_t rb = __ldg(m.rpA + g[i]);
+      const uint8_t* pos = m.posA + (e * 10 + i) * 10;
+#pragma unroll
+      for (int j = 0; j < 10; ++j) atomicAdd(valA + rb + pos[j], acc[j]);
+    }
+  }
+}
+
+// Interpolant of the exact state at t: u at the P3 nodes, p at the P2
+// nodes (coordinates pxyz); zero_interior: u = 0 off the Dirichlet nodes.
+__global__ void k_p3_exact_state(DMesh m, DPhys ph, double t, int zero_interior,
+                                 const double* __restrict__ pxyz, double* __restrict__ x) {
+  const int64_t n = m.n2 + m.nv;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    if (k < m.n2) {
+      const double xy[2] = {m.p2xyz[k * 2], m.p2xyz[k * 2 + 1]};
+      Fields f = eval_fields<2>(ph, ph.nu, xy, t, false);
+      const bool keep = !zero_interior || m.dirichlet[k];
+      x[k] = keep ? f.u[0] : 0.0;
+      x[m.n2 + k] = keep ? f.u[1] : 0.0;
+    } else {
+      const int64_t q = k - m.n2;
+      const double xy[2] = {pxyz[q * 2], pxyz[q * 2 + 1]};
+      x[2 * m.n2 + q] = eval_fields<2>(ph, ph.nu, xy, t, false).p;
+    }
+  }
+}
+
+}  // namespace
+
+void launch_p3_base(const DMesh& m, const int32_t* c2p, const RefP3* R, double mass_coef,
+                    double nu, double* base, double* Mv, double* B, double* BT, double* Kp,
+                    cudaStream_t s) {
+  k_p3_base<<<grid_for(m.ncell, 128), 128, 0, s>>>(m, c2p, R, mass_coef, nu, base, Mv, B, BT,
+                                                   Kp);
+  count_launches(1);
+}
+
+void launch_p3_conv(const DMesh& m, const RefP3* R, const double* w, int64_t ldw,
+                    const double* wc, double* valA, cudaStream_t s) {
+  k_p3_conv<<<grid_for(m.ncell, 128), 128, 0, s>>>(m, R, w, ldw, wc ? wc[0] : 0.0,
+                                                   wc ? wc[1] : 0.0, valA);
+  count_launches(1);
+}
+
+void launch_p3_exact_state(const DMesh& m, const DPhys& ph, double t, int zero_interior,
+                           const double* pxyz, double* x, cudaStream_t s) {
+  k_p3_exact_state<<<grid_for(m.n2 + m.nv, 256), 256, 0, s>>>(m, ph, t, zero_interior, pxyz,
+                                                              x);
   count_launches(1);
 }
 

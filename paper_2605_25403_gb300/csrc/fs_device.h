@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <utility>
 
 #include "fs_internal.h"
 
@@ -14,6 +15,39 @@ namespace fs {
 // Counts kernel launches issued from the host (ignored while a stream is
 // being captured into a graph; graph replays add their node count).
 void count_launches(int64_t n);
+
+// Programmatic dependent launch.  The solver's kernels run as chains of
+// short dependent passes (a V-cycle's levels, the Gram-Schmidt passes), so
+// the gap between one kernel's last block and the next kernel's first is a
+// large part of a step.  A kernel launched by launch_k with the overlap mode
+// on may be scheduled while its predecessor in the stream drains; its first
+// statement is pdl_wait() (griddepcontrol.wait), which returns once every
+// prerequisite grid has completed and its memory operations are visible, so
+// no global access of the kernel can overlap the predecessor.  Without the
+// attribute griddepcontrol.wait returns at once and the launch is an
+// ordinary serialised one.  The mode is per calling thread, taken from the
+// problem's schedule by the API entry points.
+bool launch_overlap();
+
+#ifdef __CUDACC__
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+#endif
+
+template <typename... KArgs, typename... Args>
+inline void launch_k(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                     Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = launch_overlap() ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);
+}
 
 // Element-level reference integrals in constant memory (per dimension).
 void upload_ref_tensors(const RefTensors& R2, const RefTensors& R3);
@@ -132,6 +166,20 @@ void launch_expand_monolithic(const DMesh& m, const int32_t* nat, const double* 
 void launch_dofs_perm(const DMesh& m, const int32_t* nat, const double* in, double* out,
                       int to_nat, cudaStream_t s);
 
+// ---- Taylor-Hood P3/P2 on triangles (fs_assembly.cu) ----------------------
+// m: a DMesh holding the P3 tables (c2d = the P3 map, 10 per cell; n2 = P3
+// nodes; nv = P2 pressure nodes; p2xyz = P3 node coordinates; patterns and
+// slot tables of P3Tables), c2p the P2 map (6 per cell), R the reference
+// integrals in device memory.  Blocks as launch_assemble_base /
+// launch_assemble_conv (FP64 atomics).
+void launch_p3_base(const DMesh& m, const int32_t* c2p, const RefP3* R, double mass_coef,
+                    double nu, double* base, double* Mv, double* B, double* BT, double* Kp,
+                    cudaStream_t s);
+void launch_p3_conv(const DMesh& m, const RefP3* R, const double* w, int64_t ldw,
+                    const double* wc, double* valA, cudaStream_t s);
+void launch_p3_exact_state(const DMesh& m, const DPhys& ph, double t, int zero_interior,
+                           const double* pxyz, double* x, cudaStream_t s);
+
 // ---- linear algebra (fs_linalg.cu) ---------------------------------------
 // Saddle-point operator in block form.
 template <typename T>
@@ -191,6 +239,9 @@ struct DHier {
   const int32_t* iperm = nullptr;
   // slots issued together per thread in the smoothing passes (4 or 6)
   int group = 4;
+  // Chebyshev degree of the pre- and post-smoothing below the finest level
+  // (3 or 2; the finest level always takes 3)
+  int coarse_deg = 2;
   // first level run by the fused cluster kernel (-1: none), its cluster size
   int tail = -1;
   int tail_cluster = 8;
@@ -281,6 +332,21 @@ void launch_cg_update(int64_t n, double* sc, const double* p, const double* q,
                       const double* dinv, double* x, double* r, double* z, double* part,
                       cudaStream_t s);
 void launch_cg_dir(int64_t n, const double* sc, const double* z, double* p, cudaStream_t s);
+// Flexible CG (preconditioner applied by the caller between the two):
+// t = r, x += alpha p, r -= alpha q (rr into sc[3]); then with z = M(r),
+// zeroed on the fixed rows, the dots r.z, t.z give beta (Polak-Ribiere) and
+// the new rz; first = 1 starts the iteration (p = z, rz = r.z).
+void launch_cg_update_flex(int64_t n, double* sc, const double* p, const double* q, double* x,
+                           double* r, double* t, double* part, cudaStream_t s);
+void launch_cg_dots_flex(int64_t n, const uint8_t* fixed, const double* r, const double* t,
+                         double* z, double* p, int first, double* part, double* sc,
+                         cudaStream_t s);
+
+// z = one V-cycle of the single-component hierarchy H on r (n level-0 rows
+// in the caller's order): the pressure Laplacian part of the block
+// preconditioner, reused to precondition the IPCS pressure increment.
+template <typename T>
+void launch_vcycle_scalar(const DHier<T>& H, const T* r, T* z, int64_t n, cudaStream_t s);
 
 // ---- segmented Krylov (fs_krylov.cu) -------------------------------------
 constexpr int kTileLen = 2048;  // vector entries per reduction tile

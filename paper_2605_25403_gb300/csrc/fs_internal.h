@@ -100,6 +100,37 @@ struct RefTensors {
 };
 void ref_tensors(int dim, RefTensors& R);
 
+// Taylor-Hood P3/P2 on a single 2D mesh (fs_p3.cpp): the P3 velocity map
+// c2u (ncell x 10) and P2 pressure map c2p (ncell x 6), node coordinates,
+// velocity Dirichlet flags, the block patterns A (P3-P3), B (P2-P3), BT
+// (P3-P2), Kp (P2-P2) and their slot tables (layouts as Mesh's).
+struct P3Tables {
+  int64_t n3 = 0, np = 0, ncell = 0;
+  std::vector<int32_t> c2u, c2p;
+  std::vector<double> xyz;      // n3 x 2 velocity node coordinates
+  std::vector<double> pxyz;     // np x 2 pressure node coordinates
+  std::vector<uint8_t> dir;     // n3
+  std::vector<int32_t> dlist;
+  HostCsr A, B, BT, Kp;
+  std::vector<uint8_t> posA, posB, posBT, posK;
+};
+int build_p3_tables(const Mesh& m, P3Tables& T);
+
+// Reference-triangle integrals of the P3/P2 basis (local orders of
+// fs_p3.cpp), by a Grundmann-Moeller rule of degree 9:
+//   mass[i][j] = int phi_i phi_j, stiff[i][j][r][t] = int d_r phi_i d_t phi_j,
+//   conv[i][k][j][r] = int phi_i phi_k d_r phi_j, div[q][j][r] = int psi_q
+//   d_r phi_j, pstiff[q][s][r][t] = int d_r psi_q d_t psi_s
+// (d_r = derivative in the barycentric coordinate lambda_r).
+struct RefP3 {
+  double mass[10][10];
+  double stiff[10][10][3][3];
+  double conv[10][10][10][3];
+  double div[6][10][3];
+  double pstiff[6][6][3][3];
+};
+void p3_ref_tensors(RefP3& R);
+
 // Multigrid hierarchy on the host (values FP64), built once per problem.
 struct HostLevel {
   HostCsr A;          // level operator

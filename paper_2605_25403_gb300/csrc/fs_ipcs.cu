@@ -309,6 +309,50 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_update(int64_t n, const doubl
   write_part(part, rz, rr);
 }
 
+// Flexible CG (variable preconditioner): t = r, x += alpha p, r -= alpha q;
+// partials (0, r.r)
+__global__ void __launch_bounds__(kCgThreads) k_cg_update_flex(
+    int64_t n, const double* __restrict__ sc, const double* __restrict__ p,
+    const double* __restrict__ q, double* __restrict__ x, double* __restrict__ r,
+    double* __restrict__ t, double* part) {
+  const double alpha = sc[1];
+  double rr = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] += alpha * p[i];
+    const double ro = r[i], ri = ro - alpha * q[i];
+    t[i] = ro;
+    r[i] = ri;
+    rr += ri * ri;
+  }
+  write_part(part, 0.0, rr);
+}
+
+// z = 0 on fixed rows (so that the search directions keep the fixed values),
+// then partials (r.z, t.z); with first, also p = z (the start of the
+// iteration)
+__global__ void __launch_bounds__(kCgThreads) k_cg_dots_flex(int64_t n,
+                                                             const uint8_t* __restrict__ fixed,
+                                                             const double* __restrict__ r,
+                                                             const double* __restrict__ t,
+                                                             double* __restrict__ z,
+                                                             double* __restrict__ p, int first,
+                                                             double* part) {
+  double rz = 0, tz = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double zi = z[i];
+    if (fixed && fixed[i]) {
+      zi = 0.0;
+      z[i] = 0.0;
+    }
+    rz += r[i] * zi;
+    tz += (first ? 0.0 : t[i] * zi);
+    if (first) p[i] = zi;
+  }
+  write_part(part, rz, tz);
+}
+
 // p = z + beta p
 __global__ void __launch_bounds__(kCgThreads) k_cg_dir(int64_t n, const double* __restrict__ sc,
                                                        const double* __restrict__ z,
@@ -323,6 +367,10 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_dir(int64_t n, const double* 
 //   mode 0 (after init):   rz = s0, rr = s1
 //   mode 1 (after apply):  alpha = rz / s0 (s0 = p . A p)
 //   mode 2 (after update): beta = s0 / rz, rz = s0, rr = s1
+//   mode 3 (after a flexible update): rr = s1
+//   mode 4 (after the flexible dots): beta = (s0 - s1) / rz, rz = s0
+//     (Polak-Ribiere: z_new . (r_new - r_old) / (z_old . r_old))
+//   mode 5 (first flexible dots): rz = s0
 __global__ void __launch_bounds__(kCgThreads) k_cg_scalars(const double* part, int nb, int mode,
                                                            double* sc) {
   double s0 = 0, s1 = 0;
@@ -337,10 +385,17 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_scalars(const double* part, i
       sc[3] = s1;
     } else if (mode == 1) {
       sc[1] = s0 != 0.0 ? sc[0] / s0 : 0.0;
-    } else {
+    } else if (mode == 2) {
       sc[2] = sc[0] != 0.0 ? s0 / sc[0] : 0.0;
       sc[0] = s0;
       sc[3] = s1;
+    } else if (mode == 3) {
+      sc[3] = s1;
+    } else if (mode == 4) {
+      sc[2] = sc[0] != 0.0 ? (s0 - s1) / sc[0] : 0.0;
+      sc[0] = s0;
+    } else {
+      sc[0] = s0;
     }
   }
 }
@@ -445,6 +500,21 @@ void launch_cg_update(int64_t n, double* sc, const double* p, const double* q,
                       cudaStream_t s) {
   k_cg_update<<<kFlatBlocks, kCgThreads, 0, s>>>(n, sc, p, q, dinv, x, r, z, part);
   k_cg_scalars<<<1, kCgThreads, 0, s>>>(part, kFlatBlocks, 2, sc);
+  count_launches(2);
+}
+
+void launch_cg_update_flex(int64_t n, double* sc, const double* p, const double* q, double* x,
+                           double* r, double* t, double* part, cudaStream_t s) {
+  k_cg_update_flex<<<kFlatBlocks, kCgThreads, 0, s>>>(n, sc, p, q, x, r, t, part);
+  k_cg_scalars<<<1, kCgThreads, 0, s>>>(part, kFlatBlocks, 3, sc);
+  count_launches(2);
+}
+
+void launch_cg_dots_flex(int64_t n, const uint8_t* fixed, const double* r, const double* t,
+                         double* z, double* p, int first, double* part, double* sc,
+                         cudaStream_t s) {
+  k_cg_dots_flex<<<kFlatBlocks, kCgThreads, 0, s>>>(n, fixed, r, t, z, p, first, part);
+  k_cg_scalars<<<1, kCgThreads, 0, s>>>(part, kFlatBlocks, first ? 5 : 4, sc);
   count_launches(2);
 }
 

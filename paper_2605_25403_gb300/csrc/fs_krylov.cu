@@ -97,6 +97,7 @@ template <typename V>
 __global__ void __launch_bounds__(kKB) k_seg_norm(const V* __restrict__ x, const Tile* tiles,
                                                   int ntiles, SegState* st, double* partial,
                                                   int field) {
+  pdl_wait();
   const Tile t = tiles[blockIdx.x];
   SegState& S = st[t.seg];
   double acc = 0;
@@ -123,6 +124,7 @@ __global__ void __launch_bounds__(kKB) k_seg_norm(const V* __restrict__ x, const
 // tol_abs = rtol * (relative_to_beta ? beta : bnorm).
 __global__ void k_seg_cycle_init(SegState* st, KCtl* ctl, int relative_to_beta,
                                  cudaGraphConditionalHandle cond) {
+  pdl_wait();
   __shared__ int ndone;
   if (threadIdx.x == 0) ndone = 0;
   __syncthreads();
@@ -153,6 +155,7 @@ __global__ void k_seg_cycle_init(SegState* st, KCtl* ctl, int relative_to_beta,
 template <typename V>
 __global__ void __launch_bounds__(kKB) k_seg_scale(JVec<V> xv, const Tile* tiles,
                                                    const SegState* st, int field) {
+  pdl_wait();
   const Tile t = tiles[blockIdx.x];
   const SegState& S = st[t.seg];
   if (S.done) return;
@@ -331,6 +334,7 @@ template <typename V>
 __global__ void __launch_bounds__(kKB, 2) k_seg_dot(const V* __restrict__ Vb, int64_t n,
                                                     const Tile* tiles, int ntiles, SegState* st,
                                                     const KCtl* ctl, double* partial) {
+  pdl_wait();
   constexpr int NB = Batch<V>::NB;
   const Tile t = tiles[blockIdx.x];
   SegState& S = st[t.seg];
@@ -365,6 +369,7 @@ __global__ void __launch_bounds__(kKB, 2) k_seg_upd(V* __restrict__ Vb, int64_t 
                                                     const Tile* tiles, int ntiles, SegState* st,
                                                     KCtl* ctl, double* partial,
                                                     cudaGraphConditionalHandle cond) {
+  pdl_wait();
   constexpr int NB = Batch<V>::NB;
   const Tile t = tiles[blockIdx.x];
   SegState& S = st[t.seg];
@@ -431,6 +436,7 @@ template <typename V>
 __global__ void __launch_bounds__(kKB, 2) k_seg_fin(V* __restrict__ Vb, int64_t n,
                                                     const Tile* tiles, SegState* st,
                                                     const KCtl* ctl, int jshift) {
+  pdl_wait();
   constexpr int NB = Batch<V>::NB;
   const Tile t = tiles[blockIdx.x];
   const SegState& S = st[t.seg];
@@ -463,6 +469,7 @@ __global__ void __launch_bounds__(kKB, 2) k_seg_fin(V* __restrict__ Vb, int64_t 
 // condition of the loop node (if any) becomes "a segment is still active and
 // j < m".
 __global__ void k_seg_givens(SegState* st, KCtl* ctl, cudaGraphConditionalHandle cond) {
+  pdl_wait();
   const int m = ctl->m;
   const int j = ctl->j;
   for (int s = threadIdx.x; s < ctl->nseg; s += blockDim.x) {
@@ -478,6 +485,7 @@ template <typename V, typename X>
 __global__ void __launch_bounds__(kKB) k_seg_update_x(const SegState* st, const KCtl* ctl,
                                                       const V* __restrict__ Z, int64_t n,
                                                       const Tile* tiles, X* __restrict__ x) {
+  pdl_wait();
   __shared__ double y[kMaxRestart];
   const Tile t = tiles[blockIdx.x];
   const SegState& S = st[t.seg];
@@ -511,6 +519,7 @@ template <typename A, typename B>
 __global__ void __launch_bounds__(kKB) k_seg_normalise(const A* __restrict__ in,
                                                        B* __restrict__ out, const Tile* tiles,
                                                        const SegState* st) {
+  pdl_wait();
   const Tile t = tiles[blockIdx.x];
   const SegState& S = st[t.seg];
   const double f = (S.retired || S.rnorm == 0.0) ? 0.0 : 1.0 / S.rnorm;
@@ -522,6 +531,7 @@ __global__ void __launch_bounds__(kKB) k_seg_normalise(const A* __restrict__ in,
 template <typename V, typename X>
 __global__ void __launch_bounds__(kKB) k_seg_axpy(X* __restrict__ x, const V* __restrict__ d,
                                                   const Tile* tiles, const SegState* st) {
+  pdl_wait();
   const Tile t = tiles[blockIdx.x];
   const SegState& S = st[t.seg];
   if (S.retired) return;
@@ -536,7 +546,7 @@ __global__ void __launch_bounds__(kKB) k_seg_axpy(X* __restrict__ x, const V* __
 template <typename V>
 void launch_seg_norm(const V* x, const TileList& tl, SegState* st, double* partial, int field,
                      cudaStream_t s) {
-  k_seg_norm<V><<<tl.ntiles, kKB, 0, s>>>(x, tl.tiles, tl.ntiles, st, partial, field);
+  launch_k(k_seg_norm<V>, tl.ntiles, kKB, 0, s, x, tl.tiles, tl.ntiles, st, partial, field);
   count_launches(1);
 }
 template void launch_seg_norm<double>(const double*, const TileList&, SegState*, double*, int,
@@ -546,14 +556,14 @@ template void launch_seg_norm<float>(const float*, const TileList&, SegState*, d
 
 void launch_seg_cycle_init(SegState* st, KCtl* ctl, int relative_to_beta,
                            cudaGraphConditionalHandle cond, cudaStream_t s) {
-  k_seg_cycle_init<<<1, 256, 0, s>>>(st, ctl, relative_to_beta, cond);
+  launch_k(k_seg_cycle_init, 1, 256, 0, s, st, ctl, relative_to_beta, cond);
   count_launches(1);
 }
 
 template <typename V>
 void launch_seg_scale(JVec<V> x, const TileList& tl, const SegState* st, int field,
                       cudaStream_t s) {
-  k_seg_scale<V><<<tl.ntiles, kKB, 0, s>>>(x, tl.tiles, st, field);
+  launch_k(k_seg_scale<V>, tl.ntiles, kKB, 0, s, x, tl.tiles, st, field);
   count_launches(1);
 }
 template void launch_seg_scale<double>(JVec<double>, const TileList&, const SegState*, int,
@@ -565,14 +575,14 @@ template <typename V>
 void launch_seg_cgs2(V* Vb, int64_t n, const TileList& tl, SegState* st, KCtl* ctl,
                      double* partial, bool with_givens, cudaGraphConditionalHandle cond,
                      cudaStream_t s) {
-  k_seg_dot<V><<<tl.ntiles, kKB, 0, s>>>(Vb, n, tl.tiles, tl.ntiles, st, ctl, partial);
+  launch_k(k_seg_dot<V>, tl.ntiles, kKB, 0, s, Vb, n, tl.tiles, tl.ntiles, st, ctl, partial);
   if (with_givens)
-    k_seg_upd<V, true><<<tl.ntiles, kKB, 0, s>>>(Vb, n, tl.tiles, tl.ntiles, st, ctl, partial,
+    launch_k(k_seg_upd<V, true>, tl.ntiles, kKB, 0, s, Vb, n, tl.tiles, tl.ntiles, st, ctl, partial,
                                                  cond);
   else
-    k_seg_upd<V, false><<<tl.ntiles, kKB, 0, s>>>(Vb, n, tl.tiles, tl.ntiles, st, ctl, partial,
+    launch_k(k_seg_upd<V, false>, tl.ntiles, kKB, 0, s, Vb, n, tl.tiles, tl.ntiles, st, ctl, partial,
                                                   0);
-  k_seg_fin<V><<<tl.ntiles, kKB, 0, s>>>(Vb, n, tl.tiles, st, ctl, with_givens ? 1 : 0);
+  launch_k(k_seg_fin<V>, tl.ntiles, kKB, 0, s, Vb, n, tl.tiles, st, ctl, with_givens ? 1 : 0);
   count_launches(3);
 }
 template void launch_seg_cgs2<double>(double*, int64_t, const TileList&, SegState*, KCtl*,
@@ -584,12 +594,12 @@ template <typename V>
 void launch_seg_cgs2_pass(V* Vb, int64_t n, const TileList& tl, SegState* st, KCtl* ctl,
                           double* partial, int pass, cudaStream_t s) {
   if (pass == 0)
-    k_seg_dot<V><<<tl.ntiles, kKB, 0, s>>>(Vb, n, tl.tiles, tl.ntiles, st, ctl, partial);
+    launch_k(k_seg_dot<V>, tl.ntiles, kKB, 0, s, Vb, n, tl.tiles, tl.ntiles, st, ctl, partial);
   else if (pass == 1)
-    k_seg_upd<V, false><<<tl.ntiles, kKB, 0, s>>>(Vb, n, tl.tiles, tl.ntiles, st, ctl, partial,
+    launch_k(k_seg_upd<V, false>, tl.ntiles, kKB, 0, s, Vb, n, tl.tiles, tl.ntiles, st, ctl, partial,
                                                   0);
   else
-    k_seg_fin<V><<<tl.ntiles, kKB, 0, s>>>(Vb, n, tl.tiles, st, ctl, 0);
+    launch_k(k_seg_fin<V>, tl.ntiles, kKB, 0, s, Vb, n, tl.tiles, st, ctl, 0);
   count_launches(1);
 }
 template void launch_seg_cgs2_pass<double>(double*, int64_t, const TileList&, SegState*, KCtl*,
@@ -600,14 +610,14 @@ template void launch_seg_cgs2_pass<float>(float*, int64_t, const TileList&, SegS
 void launch_seg_givens(SegState* st, KCtl* ctl, int nseg, cudaGraphConditionalHandle cond,
                        cudaStream_t s) {
   (void)nseg;
-  k_seg_givens<<<1, 256, 0, s>>>(st, ctl, cond);
+  launch_k(k_seg_givens, 1, 256, 0, s, st, ctl, cond);
   count_launches(1);
 }
 
 template <typename V, typename X>
 void launch_seg_update_x(const SegState* st, const KCtl* ctl, const V* Z, int64_t n,
                          const TileList& tl, X* x, cudaStream_t s) {
-  k_seg_update_x<V, X><<<tl.ntiles, kKB, 0, s>>>(st, ctl, Z, n, tl.tiles, x);
+  launch_k(k_seg_update_x<V, X>, tl.ntiles, kKB, 0, s, st, ctl, Z, n, tl.tiles, x);
   count_launches(1);
 }
 template void launch_seg_update_x<double, double>(const SegState*, const KCtl*, const double*,
@@ -619,7 +629,7 @@ template void launch_seg_update_x<float, float>(const SegState*, const KCtl*, co
 template <typename A, typename B>
 void launch_seg_normalise(const A* in, B* out, const TileList& tl, const SegState* st,
                           cudaStream_t s) {
-  k_seg_normalise<A, B><<<tl.ntiles, kKB, 0, s>>>(in, out, tl.tiles, st);
+  launch_k(k_seg_normalise<A, B>, tl.ntiles, kKB, 0, s, in, out, tl.tiles, st);
   count_launches(1);
 }
 template void launch_seg_normalise<double, float>(const double*, float*, const TileList&,
@@ -627,7 +637,7 @@ template void launch_seg_normalise<double, float>(const double*, float*, const T
 
 template <typename V, typename X>
 void launch_seg_axpy(X* x, const V* d, const TileList& tl, const SegState* st, cudaStream_t s) {
-  k_seg_axpy<V, X><<<tl.ntiles, kKB, 0, s>>>(x, d, tl.tiles, st);
+  launch_k(k_seg_axpy<V, X>, tl.ntiles, kKB, 0, s, x, d, tl.tiles, st);
   count_launches(1);
 }
 template void launch_seg_axpy<float, double>(double*, const float*, const TileList&,

@@ -60,6 +60,7 @@ template <typename T, typename V, int DIM, int kUS>
 __global__ void __launch_bounds__(256) k_spmv_full(DOp<T> op, JVec<const V> xv,
                                                    const V* __restrict__ b, JVec<V> yv,
                                                    int resid, const int* skip) {
+  pdl_wait();
   if (skip && *skip) return;
   const V* __restrict__ x = xv.get();
   V* __restrict__ y = yv.get();
@@ -455,6 +456,7 @@ __global__ void __launch_bounds__(256) k_mg(DSell<T> A, const T* __restrict__ di
                                             T alpha, T beta, T inv_theta, JVec<T> outv,
                                             int64_t out_ld, const int32_t* __restrict__ perm,
                                             int nc, const int* skip) {
+  pdl_wait();
   if (skip && *skip) return;
   const int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (row >= A.nrow) return;
@@ -468,6 +470,7 @@ __global__ void __launch_bounds__(256) k_mg_restrict(DCsr<T> R, const T* __restr
                                                      T* __restrict__ Dc,
                                                      const T* __restrict__ dinvc,
                                                      T inv_theta_c, const int* skip) {
+  pdl_wait();
   if (skip && *skip) return;
   const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t row = gt / L;
@@ -478,6 +481,7 @@ __global__ void __launch_bounds__(256) k_mg_restrict(DCsr<T> R, const T* __restr
 template <typename T, int NCP, int L>
 __global__ void __launch_bounds__(256) k_mg_prolong(DCsr<T> P, const T* __restrict__ Xc,
                                                     T* __restrict__ Gf, const int* skip) {
+  pdl_wait();
   if (skip && *skip) return;
   const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t row = gt / L;
@@ -490,6 +494,7 @@ template <typename T, int NCP>
 __global__ void k_mg_dense(DenseView<T> D, int64_t ncoarse, const T* __restrict__ b,
                            T* __restrict__ X, const int32_t* __restrict__ perm, JVec<T> outv,
                            int64_t out_ld, int nc, const int* skip) {
+  pdl_wait();
   if (skip && *skip) return;
   const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32;
   dense_row<T, NCP>(D, b, X, outv.get(), out_ld, perm, nc, row, threadIdx.x & 31,
@@ -524,24 +529,33 @@ __global__ void __launch_bounds__(NT, 1) k_mg_tail(const DHier<T>* __restrict__ 
     T *G0 = H.G0[l], *G1 = H.G1[l], *D0 = H.D0[l], *D1 = H.D1[l];
     const T* b = H.b[l];
     const T a1 = (T)L.a1, b1 = (T)L.b1, a2 = (T)L.a2, b2 = (T)L.b2, it = (T)L.inv_theta;
+    // degree 2 below the finest level: the phases of vcycle_level's light path
+    const bool light = l > 0 && H.coarse_deg == 2;
     for (int64_t r = tid; r < n; r += nth)
       mg_row<T, NC, NCP, MG_STEP>(L.A, L.dinv, b, G0, D0, G1, D1, a1, b1, it, nullptr, 0,
                                         nullptr, nc, r);
     cl.sync();
-    for (int64_t r = tid; r < n; r += nth)
-      mg_row<T, NC, NCP, MG_STEP>(L.A, L.dinv, b, G1, D1, G0, D0, a2, b2, it, nullptr, 0,
-                                        nullptr, nc, r);
-    cl.sync();
-    for (int64_t r = tid; r < n; r += nth)
-      mg_row<T, NC, NCP, MG_RESID>(L.A, L.dinv, b, G0, D0, G1, nullptr, T(0), T(0), it,
-                                         nullptr, 0, nullptr, nc, r);
+    if (light) {
+      for (int64_t r = tid; r < n; r += nth)
+        mg_row<T, NC, NCP, MG_RESID>(L.A, L.dinv, b, G1, D1, D0, nullptr, T(0), T(0), it,
+                                     nullptr, 0, nullptr, nc, r);
+    } else {
+      for (int64_t r = tid; r < n; r += nth)
+        mg_row<T, NC, NCP, MG_STEP>(L.A, L.dinv, b, G1, D1, G0, D0, a2, b2, it, nullptr, 0,
+                                    nullptr, nc, r);
+      cl.sync();
+      for (int64_t r = tid; r < n; r += nth)
+        mg_row<T, NC, NCP, MG_RESID>(L.A, L.dinv, b, G0, D0, G1, nullptr, T(0), T(0), it,
+                                     nullptr, 0, nullptr, nc, r);
+    }
     cl.sync();
     const DLevel<T>& C = H.lev[l + 1];
     const bool dense_next = l + 1 == last;
+    const T* resid = light ? D0 : G1;
     const int64_t nr = L.R.nrow, groups = nth / 4, sweeps = (nr + groups - 1) / groups;
     for (int64_t q = 0; q < sweeps; ++q) {
       const int64_t r = q * groups + tid / 4;
-      restrict_row<T, NCP, 4>(L.R, G1, H.b[l + 1], H.G0[l + 1], H.D0[l + 1],
+      restrict_row<T, NCP, 4>(L.R, resid, H.b[l + 1], H.G0[l + 1], H.D0[l + 1],
                                     dense_next ? nullptr : C.dinv, (T)C.inv_theta, r, lane4,
                                     r < nr);
     }
@@ -563,14 +577,27 @@ __global__ void __launch_bounds__(NT, 1) k_mg_tail(const DHier<T>* __restrict__ 
     T *G0 = H.G0[l], *G1 = H.G1[l], *D0 = H.D0[l], *D1 = H.D1[l];
     const T* b = H.b[l];
     const T a1 = (T)L.a1, b1 = (T)L.b1, a2 = (T)L.a2, b2 = (T)L.b2, it = (T)L.inv_theta;
+    const bool light = l > 0 && H.coarse_deg == 2;
     {
+      T* corrected = light ? G1 : G0;
       const int64_t nr = L.P.nrow, groups = nth / 4, sweeps = (nr + groups - 1) / groups;
       for (int64_t q = 0; q < sweeps; ++q) {
         const int64_t r = q * groups + tid / 4;
-        prolong_row<T, NCP, 4>(L.P, H.G1[l + 1], G0, r, lane4, r < nr);
+        prolong_row<T, NCP, 4>(L.P, H.G1[l + 1], corrected, r, lane4, r < nr);
       }
     }
     cl.sync();
+    if (light) {
+      for (int64_t r = tid; r < n; r += nth)
+        mg_row<T, NC, NCP, MG_START>(L.A, L.dinv, b, G1, nullptr, G0, D0, T(0), T(0), it,
+                                     nullptr, 0, nullptr, nc, r);
+      cl.sync();
+      for (int64_t r = tid; r < n; r += nth)
+        mg_row<T, NC, NCP, MG_LAST>(L.A, L.dinv, b, G0, D0, G1, nullptr, a1, b1, it, nullptr,
+                                    0, nullptr, nc, r);
+      if (l > l0) cl.sync();
+      continue;
+    }
     for (int64_t r = tid; r < n; r += nth)
       mg_row<T, NC, NCP, MG_START>(L.A, L.dinv, b, G0, nullptr, G1, D1, T(0), T(0), it,
                                          nullptr, 0, nullptr, nc, r);
@@ -596,7 +623,7 @@ void launch_mg(int mode, const DLevel<T>& L, const T* b, const T* Gin, const T* 
   const T it = (T)L.inv_theta;
   constexpr int NC = NCP == 4 ? 3 : NCP;  // real components (3D pads 3 to 4)
 #define FS_MG(M, G)                                                                        \
-  k_mg<T, NC, NCP, M, G><<<blocks_for(n), 256, 0, s>>>(L.A, L.dinv, b, Gin, Din, Gout, Dout, \
+  launch_k(k_mg<T, NC, NCP, M, G>, blocks_for(n), 256, 0, s, L.A, L.dinv, b, Gin, Din, Gout, Dout, \
                                                        alpha, beta, it, out, out_ld, perm, nc, skip)
   if (group == 6) {
     if (mode == MG_STEP) FS_MG(MG_STEP, 6);
@@ -650,7 +677,7 @@ void vcycle_level(const DHier<T>& H, int l, JVec<T> out, int64_t out_ld, int nc,
     return;
   }
   if (l == H.nlev - 1) {
-    k_mg_dense<T, NCP><<<blocks_for(H.ncoarse * 32), 256, 0, s>>>(
+    launch_k(k_mg_dense<T, NCP>, blocks_for(H.ncoarse * 32), 256, 0, s,
         dense_view(H), H.ncoarse, H.b[l], H.G1[l], top ? H.perm : nullptr,
         top ? out : JVec<T>(), out_ld, nc, skip);
     count_launches(1);
@@ -661,6 +688,30 @@ void vcycle_level(const DHier<T>& H, int l, JVec<T> out, int64_t out_ld, int nc,
   const T a1 = (T)L.a1, b1 = (T)L.b1, a2 = (T)L.a2, b2 = (T)L.b2;
   T *G0 = H.G0[l], *G1 = H.G1[l], *D0 = H.D0[l], *D1 = H.D1[l];
   const T* b = H.b[l];
+  const bool coarsest_next = l + 1 == H.nlev - 1;
+  if (!top && H.coarse_deg == 2) {
+    // degree 2 on a coarse level: one step after the restriction's first
+    // (x2 in G1), the residual into the free D0, the correction into G1,
+    // then the first post step and the last with the first step's
+    // coefficients (the result in G1, as the degree-3 cycle leaves it)
+    launch_mg<T, NCP>(MG_STEP, L, b, G0, D0, G1, D1, a1, b1, JVec<T>(), 0, nullptr, nc, skip,
+                      H.group, s);
+    launch_mg<T, NCP>(MG_RESID, L, b, G1, D1, D0, nullptr, T(0), T(0), JVec<T>(), 0, nullptr,
+                      nc, skip, H.group, s);
+    launch_k(k_mg_restrict<T, NCP, 4>, blocks_for(L.R.nrow * 4), 256, 0, s,
+        L.R, D0, H.b[l + 1], H.G0[l + 1], H.D0[l + 1], coarsest_next ? nullptr : C.dinv,
+        (T)C.inv_theta, skip);
+    count_launches(1);
+    vcycle_level<T, NCP>(H, l + 1, JVec<T>(), 0, nc, skip, s);
+    launch_k(k_mg_prolong<T, NCP, 4>, blocks_for(L.P.nrow * 4), 256, 0, s, L.P, H.G1[l + 1], G1,
+                                                                      skip);
+    count_launches(1);
+    launch_mg<T, NCP>(MG_START, L, b, G1, nullptr, G0, D0, T(0), T(0), JVec<T>(), 0, nullptr,
+                      nc, skip, H.group, s);
+    launch_mg<T, NCP>(MG_LAST, L, b, G0, D0, G1, nullptr, a1, b1, JVec<T>(), 0, nullptr, nc,
+                      skip, H.group, s);
+    return;
+  }
   launch_mg<T, NCP>(MG_STEP, L, b, G0, D0, G1, D1, a1, b1, JVec<T>(), 0, nullptr, nc, skip,
                     H.group, s);
   launch_mg<T, NCP>(MG_STEP, L, b, G1, D1, G0, D0, a2, b2, JVec<T>(), 0, nullptr, nc, skip,
@@ -668,13 +719,12 @@ void vcycle_level(const DHier<T>& H, int l, JVec<T> out, int64_t out_ld, int nc,
   // residual of x3 = G0 into G1; G0 keeps x3 for the correction
   launch_mg<T, NCP>(MG_RESID, L, b, G0, D0, G1, nullptr, T(0), T(0), JVec<T>(), 0, nullptr, nc,
                     skip, H.group, s);
-  const bool coarsest_next = l + 1 == H.nlev - 1;
-  k_mg_restrict<T, NCP, 4><<<blocks_for(L.R.nrow * 4), 256, 0, s>>>(
+  launch_k(k_mg_restrict<T, NCP, 4>, blocks_for(L.R.nrow * 4), 256, 0, s,
       L.R, G1, H.b[l + 1], H.G0[l + 1], H.D0[l + 1], coarsest_next ? nullptr : C.dinv,
       (T)C.inv_theta, skip);
   count_launches(1);
   vcycle_level<T, NCP>(H, l + 1, JVec<T>(), 0, nc, skip, s);
-  k_mg_prolong<T, NCP, 4><<<blocks_for(L.P.nrow * 4), 256, 0, s>>>(L.P, H.G1[l + 1], G0, skip);
+  launch_k(k_mg_prolong<T, NCP, 4>, blocks_for(L.P.nrow * 4), 256, 0, s, L.P, H.G1[l + 1], G0, skip);
   count_launches(1);
   launch_mg<T, NCP>(MG_START, L, b, G0, nullptr, G1, D1, T(0), T(0), JVec<T>(), 0, nullptr, nc,
                     skip, H.group, s);
@@ -721,6 +771,7 @@ __global__ void k_mg_load1(int64_t n, JVec<const T> rv,
                            const int32_t* __restrict__ iperm, const T* __restrict__ dinv0,
                            T inv_theta0, T* __restrict__ b0, T* __restrict__ G0,
                            T* __restrict__ D0, const int* skip) {
+  pdl_wait();
   if (skip && *skip) return;
   const T* __restrict__ r = rv.get();
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
@@ -739,6 +790,7 @@ template <typename T>
 __global__ void k_prec_p(int64_t nv, JVec<const T> rpv, const T* __restrict__ yk,
                          const T* __restrict__ mpl_inv_nu, T inv_dt, JVec<T> zpv,
                          const int* skip) {
+  pdl_wait();
   if (skip && *skip) return;
   const T* __restrict__ rp = rpv.get();
   T* __restrict__ zp = zpv.get();
@@ -749,6 +801,7 @@ __global__ void k_prec_p(int64_t nv, JVec<const T> rpv, const T* __restrict__ yk
 template <typename T>
 __global__ void k_pin_rows(const int32_t* __restrict__ pinned, int npinned, JVec<const T> rpv,
                            JVec<T> zpv, const int* skip) {
+  pdl_wait();
   if (skip && *skip) return;
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t < npinned) zpv.get()[pinned[t]] = rpv.get()[pinned[t]];
@@ -765,6 +818,7 @@ __global__ void __launch_bounds__(256) k_bt_add_mg(DSell<T> BT, int64_t n2, JVec
                                                    const T* __restrict__ dinv0, T inv_theta0,
                                                    T* __restrict__ b0, T* __restrict__ G0,
                                                    T* __restrict__ D0, const int* skip) {
+  pdl_wait();
   if (skip && *skip) return;
   const int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (row >= n2) return;
@@ -863,6 +917,7 @@ struct Extrap {
   double c[kExtrapMax + 1];
 };
 __global__ void k_extrapolate(double* x, Extrap e, int nprev, double* dst, int64_t n) {
+  pdl_wait();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const double a = x[i];
@@ -878,6 +933,7 @@ __global__ void k_extrapolate(double* x, Extrap e, int nprev, double* dst, int64
 template <typename A, typename B>
 __global__ void k_convert(const A* __restrict__ in, B* __restrict__ out, int64_t n,
                           const double* scale, int inv) {
+  pdl_wait();
   double s = scale ? *scale : 1.0;
   if (scale && inv) s = 1.0 / s;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -901,7 +957,7 @@ void launch_spmv_full(const DOp<T>& op, JVec<const V> x, const V* b, JVec<V> y, 
   // rows are partly bound by FP64 arithmetic and do best shallower)
   const int g = op.group ? op.group : (std::is_same<V, float>::value ? kUSpmv : kU);
 #define FS_SPMV(D, G) \
-  k_spmv_full<T, V, D, G><<<blocks_for(threads), 256, 0, s>>>(op, x, b, y, resid, skip)
+  launch_k(k_spmv_full<T, V, D, G>, blocks_for(threads), 256, 0, s, op, x, b, y, resid, skip)
   if (op.dim == 2) {
     if (g == 8) FS_SPMV(2, 8);
     else if (g == 6) FS_SPMV(2, 6);
@@ -965,17 +1021,17 @@ void launch_precond(const DOp<T>& op, const DHier<T>& HA, const DHier<T>& HK,
   // pressure: Cahouet-Chabard  z_p = nu Mp^-1 r_p + dt^-1 Kp^-1 r_p
   {
     const bool k1 = HK.nlev > 1;
-    k_mg_load1<T><<<grid_stride_blocks(nv), 256, 0, s>>>(
+    launch_k(k_mg_load1<T>, grid_stride_blocks(nv), 256, 0, s,
         nv, rp, HK.iperm, k1 ? HK.lev[0].dinv : nullptr, (T)HK.lev[0].inv_theta, HK.b[0], HK.G0[0],
         HK.D0[0], skip);
     count_launches(1);
     vcycle_level<T, 1>(HK, 0, JVec<T>(work_p), nv, 1, skip, s);
   }
-  k_prec_p<T><<<grid_stride_blocks(nv), 256, 0, s>>>(nv, rp, work_p, mpl_inv_nu, (T)inv_dt, zp,
+  launch_k(k_prec_p<T>, grid_stride_blocks(nv), 256, 0, s, nv, rp, work_p, mpl_inv_nu, (T)inv_dt, zp,
                                                      skip);
   count_launches(1);
   if (npinned > 0) {
-    k_pin_rows<T><<<blocks_for(npinned), 256, 0, s>>>(pinned, npinned, rp, zp, skip);
+    launch_k(k_pin_rows<T>, blocks_for(npinned), 256, 0, s, pinned, npinned, rp, zp, skip);
     count_launches(1);
   }
   // velocity: z_u = A^-1 (r_u + BT z_p) by one V-cycle on all components
@@ -983,12 +1039,12 @@ void launch_precond(const DOp<T>& op, const DHier<T>& HA, const DHier<T>& HK,
   const T* d0 = a1 ? HA.lev[0].dinv : nullptr;
   const T it0 = (T)HA.lev[0].inv_theta;
   if (dim == 2) {
-    k_bt_add_mg<T, 2, 2><<<blocks_for(n2), 256, 0, s>>>(op.BT, n2, r, zpc, HA.iperm, d0, it0,
+    launch_k(k_bt_add_mg<T, 2, 2>, blocks_for(n2), 256, 0, s, op.BT, n2, r, zpc, HA.iperm, d0, it0,
                                                         HA.b[0], HA.G0[0], HA.D0[0], skip);
     count_launches(1);
     vcycle_level<T, 2>(HA, 0, z, n2, 2, skip, s);
   } else {
-    k_bt_add_mg<T, 3, 4><<<blocks_for(n2), 256, 0, s>>>(op.BT, n2, r, zpc, HA.iperm, d0, it0,
+    launch_k(k_bt_add_mg<T, 3, 4>, blocks_for(n2), 256, 0, s, op.BT, n2, r, zpc, HA.iperm, d0, it0,
                                                         HA.b[0], HA.G0[0], HA.D0[0], skip);
     count_launches(1);
     vcycle_level<T, 4>(HA, 0, z, n2, 3, skip, s);
@@ -1002,6 +1058,20 @@ template void launch_precond<float>(const DOp<float>&, const DHier<float>&,
                                     const DHier<float>&, const float*, double,
                                     const int32_t*, int, JVec<const float>, JVec<float>, float*,
                                     float*, const int*, cudaStream_t);
+
+template <typename T>
+void launch_vcycle_scalar(const DHier<T>& H, const T* r, T* z, int64_t n, cudaStream_t s) {
+  const bool k1 = H.nlev > 1;
+  launch_k(k_mg_load1<T>, grid_stride_blocks(n), 256, 0, s,
+      n, JVec<const T>(r), H.iperm, k1 ? H.lev[0].dinv : nullptr, (T)H.lev[0].inv_theta, H.b[0],
+      H.G0[0], H.D0[0], nullptr);
+  count_launches(1);
+  vcycle_level<T, 1>(H, 0, JVec<T>(z), n, 1, nullptr, s);
+}
+template void launch_vcycle_scalar<double>(const DHier<double>&, const double*, double*, int64_t,
+                                           cudaStream_t);
+template void launch_vcycle_scalar<float>(const DHier<float>&, const float*, float*, int64_t,
+                                          cudaStream_t);
 
 void launch_gj_step(double* W, int64_t n, int64_t c, int64_t* piv, double* pval, int* bad,
                     cudaStream_t s) {
@@ -1114,14 +1184,14 @@ void launch_extrapolate(double* x, const double* const* prev, int nprev, double*
     e.c[j] = (j % 2 ? -1.0 : 1.0) * binom;
     if (j < nprev) e.p[j] = prev[j];
   }
-  k_extrapolate<<<grid_stride_blocks(n), 256, 0, s>>>(x, e, nprev, dst, n);
+  launch_k(k_extrapolate, grid_stride_blocks(n), 256, 0, s, x, e, nprev, dst, n);
   count_launches(1);
 }
 
 template <typename A, typename B>
 void launch_convert(const A* in, B* out, int64_t n, const double* scale, int inv,
                     cudaStream_t s) {
-  k_convert<A, B><<<grid_stride_blocks(n), 256, 0, s>>>(in, out, n, scale, inv);
+  launch_k(k_convert<A, B>, grid_stride_blocks(n), 256, 0, s, in, out, n, scale, inv);
   count_launches(1);
 }
 template void launch_convert<double, float>(const double*, float*, int64_t, const double*, int,

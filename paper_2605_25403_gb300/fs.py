@@ -33,7 +33,7 @@ STATUS = {0: "FS_OK", 1: "FS_ERR_INVALID_ARG", 2: "FS_ERR_INVALID_MESH", 3: "FS_
           7: "FS_ERR_TIMEOUT", 8: "FS_ERR_BUSY", 9: "FS_ERR_UNSUPPORTED"}
 FS_PREC_FP64, FS_PREC_FP32_REFINE = 0, 1
 FS_PROBLEM_UNSTEADY_BENCH, FS_PROBLEM_STEADY_POLY, FS_PROBLEM_CHANNEL, FS_PROBLEM_CUBE, \
-    FS_PROBLEM_POLY_OSEEN, FS_PROBLEM_POLY_OSEEN_T = range(6)
+    FS_PROBLEM_POLY_OSEEN, FS_PROBLEM_POLY_OSEEN_T, FS_PROBLEM_POLY3 = range(7)
 
 
 class FsError(RuntimeError):
@@ -104,6 +104,8 @@ _lib.fs_step.argtypes = [_vp, _int, _P(fs_solve_opts), _P(fs_solve_stats)]
 _lib.fs_step_picard.argtypes = [_vp, _int, _P(fs_solve_opts), _d, _int, _P(fs_picard_stats)]
 _lib.fs_solve_steady.argtypes = [_vp, _P(fs_solve_opts), _d, _int, _P(fs_picard_stats)]
 _lib.fs_step_ipcs.argtypes = [_vp, _int, _d, _int, _P(fs_ipcs_stats)]
+_lib.fs_problem_create_p3.argtypes = [_vp, _P(fs_problem_desc), _vp, _P(_vp)]
+_lib.fs_problem_sizes.argtypes = [_vp, _P(_i64)]
 _lib.fs_apply_operator.argtypes = [_vp, _vp, _vp]
 _lib.fs_get_state.argtypes = [_vp, _vp, _int, _P(_d)]
 _lib.fs_set_state.argtypes = [_vp, _vp, _int, _d]
@@ -127,7 +129,8 @@ class fs_server_desc(ctypes.Structure):
 
 class fs_schedule(ctypes.Structure):
     _fields_ = [("tail_rows_velocity", _i64), ("tail_rows_pressure", _i64),
-                ("spmv_group", _int), ("smooth_group", _int)]
+                ("spmv_group", _int), ("smooth_group", _int), ("coarse_degree", _int),
+                ("serial_launches", _int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -198,7 +201,8 @@ EXPORTED = ["fs_mesh_create", "fs_mesh_destroy", "fs_dof_map", "fs_problem_creat
             "fs_server_destroy", "fs_server_submit", "fs_server_progress",
             "fs_server_pop_completed", "fs_server_take_state", "fs_server_status",
             "fs_server_estimate_bytes", "fs_get_schedule", "fs_set_schedule", "fs_autotune",
-            "fs_step_picard", "fs_solve_steady", "fs_step_ipcs"]
+            "fs_step_picard", "fs_solve_steady", "fs_step_ipcs", "fs_problem_create_p3",
+            "fs_problem_sizes"]
 (FS_KERNEL_SPMV, FS_KERNEL_SPMV_FP64, FS_KERNEL_CHEB, FS_KERNEL_ASSEMBLE_CONV,
  FS_KERNEL_PRECOND, FS_KERNEL_CGS, FS_KERNEL_CGS_DOT, FS_KERNEL_CGS_UPD,
  FS_KERNEL_CGS_FIN) = range(9)
@@ -348,6 +352,26 @@ def fs_instance_stats(prob):
 _instance_counts = {}
 
 
+def fs_problem_sizes(prob):
+    """(velocity nodes per component, pressure nodes, n_dof)."""
+    out = (_i64 * 3)()
+    _check(_lib.fs_problem_sizes(prob, out), "fs_problem_sizes")
+    return tuple(int(v) for v in out)
+
+
+def fs_problem_create_p3(mesh, problem, nu, dt, t0=0.0, pin_pressure=1, init=0,
+                         wconst=(0.0, 0.0, 0.0), stream=None):
+    """A Taylor-Hood P3/P2 problem on a 2D mesh (stepped by fs_step_ipcs)."""
+    d = _problem_desc(problem, nu, dt, t0, FS_PREC_FP64, pin_pressure, init, wconst)
+    h = _vp()
+    s = None if stream is None else ctypes.c_void_p(int(stream))
+    _check(_lib.fs_problem_create_p3(mesh, ctypes.byref(d), s, ctypes.byref(h)),
+           "fs_problem_create_p3")
+    _state_sizes[h.value] = fs_problem_sizes(h)[2]
+    _instance_counts[h.value] = 1
+    return h
+
+
 def fs_problem_create(mesh, problem, nu, dt, t0=0.0, precision=FS_PREC_FP64, pin_pressure=1,
                       init=0, wconst=(0.0, 0.0, 0.0), stream=None, deterministic=0):
     d = _problem_desc(problem, nu, dt, t0, precision, pin_pressure, init, wconst, deterministic)
@@ -479,9 +503,10 @@ def fs_get_schedule(prob):
     return sc.as_dict()
 
 
-def fs_set_schedule(prob, tail_rows_velocity, tail_rows_pressure, spmv_group=0, smooth_group=0):
+def fs_set_schedule(prob, tail_rows_velocity, tail_rows_pressure, spmv_group=0, smooth_group=0,
+                    coarse_degree=0, serial_launches=0):
     sc = fs_schedule(int(tail_rows_velocity), int(tail_rows_pressure), int(spmv_group),
-                     int(smooth_group))
+                     int(smooth_group), int(coarse_degree), int(serial_launches))
     _check(_lib.fs_set_schedule(prob, ctypes.byref(sc)), "fs_set_schedule")
 
 
@@ -515,7 +540,8 @@ def fs_set_state(prob, x, t):
 # Convenience wrapper: one problem built from a workload description
 # ---------------------------------------------------------------------------
 _KIND = {0: FS_PROBLEM_UNSTEADY_BENCH, 1: FS_PROBLEM_STEADY_POLY, 2: FS_PROBLEM_CHANNEL,
-         3: FS_PROBLEM_CUBE, 4: FS_PROBLEM_POLY_OSEEN, 5: FS_PROBLEM_POLY_OSEEN_T}
+         3: FS_PROBLEM_CUBE, 4: FS_PROBLEM_POLY_OSEEN, 5: FS_PROBLEM_POLY_OSEEN_T,
+         6: FS_PROBLEM_POLY3}
 
 
 @dataclass
@@ -533,6 +559,17 @@ class Stepper:
                                  1 if wl.pin_p0 else 0, 1 if wl.init == "zero_interior" else 0,
                                  wl.wconst or (0.0, 0.0, 0.0), stream, deterministic)
         return cls(mesh, prob, info)
+
+    @classmethod
+    def from_workload_p3(cls, wl, stream=None):
+        """A Taylor-Hood P3/P2 problem on the workload's 2D mesh."""
+        mesh = fs_mesh_create(wl.dim, wl.n, wl.lo, wl.hi, wl.jitter, wl.seed, wl.side_mask)
+        prob = fs_problem_create_p3(mesh, _KIND[wl.problem], wl.nu, wl.dt, 0.0,
+                                    1 if wl.pin_p0 else 0,
+                                    1 if wl.init == "zero_interior" else 0,
+                                    wl.wconst or (0.0, 0.0, 0.0), stream)
+        n3, np_, ndof = fs_problem_sizes(prob)
+        return cls(mesh, prob, {"n_p3": n3, "n_p2_pressure": np_, "n_dof": ndof})
 
     @classmethod
     def from_workloads(cls, wls, precision=FS_PREC_FP64, stream=None):

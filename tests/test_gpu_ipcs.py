@@ -1,9 +1,10 @@
 """Incremental pressure-correction stepping on the GPU (paper Sec. 2.2.1,
 IPCS; the Sec. 4.1 table "IPCS convergence analysis") against the oracle's
-IPCS step, stage by stage solved exactly there and by Jacobi-preconditioned
-CG here: relative L2 <= 1e-9 at every step, free-running; exact discrete
-steady states are kept; boundary set-ups the scheme does not cover are
-refused."""
+IPCS step, stage by stage solved exactly there and by CG here (Jacobi for
+the velocity stages, one multigrid V-cycle per iteration for the pressure
+stage): relative L2 <= 1e-9 at every step, free-running; the pressure
+stage's iteration count stays flat under refinement; exact discrete steady
+states are kept; boundary set-ups the scheme does not cover are refused."""
 import numpy as np
 import pytest
 
@@ -46,6 +47,26 @@ def test_ipcs_steps_match_oracle(fs, wl):
             assert e <= 1e-9, (k, e)
     finally:
         S.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_refine"])
+def test_pressure_stage_iterations_flat_in_mesh_size(fs, prec):
+    # Jacobi CG needs O(n) iterations on the pressure Poisson problem (248 at
+    # 32 x 32 to 1e-13); the V-cycle preconditioner keeps the count bounded.
+    p = fs.FS_PREC_FP64 if prec == "fp64" else fs.FS_PREC_FP32_REFINE
+    its = {}
+    for n in (16, 64, 128):
+        wl = W.unit_square(n, nu=1.0 / 50, dt=5e-3, jitter=0.05, seed=4)
+        S = fs.Stepper.from_workload(wl, precision=p)
+        try:
+            st = fs.fs_step_ipcs(S.prob, 2)
+            assert all(s["status"] == 0 for s in st), st
+            its[n] = max(s["iters"][1] for s in st)
+        finally:
+            S.close()
+    print(prec, "pressure CG iterations by n:", its)
+    assert max(its.values()) <= 40, its
+    assert its[128] <= its[16] + 16, its
 
 
 @pytest.mark.parametrize("dim,n", [(2, (5, 4)), (3, (2, 3, 2))])

@@ -23,9 +23,12 @@ from tests.gpu_helpers import rel_l2
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-# (tail rows velocity, tail rows pressure, SpMV group, smoothing group)
-SCHEDULES = [(0, 0, 0, 0), (65536, 65536, 8, 6), (4096, 16384, 4, 4), (16384, 0, 6, 6)]
-KEYS = ("tail_rows_velocity", "tail_rows_pressure", "spmv_group", "smooth_group")
+# (tail rows velocity, tail rows pressure, SpMV group, smoothing group,
+#  coarse-level smoother degree, serialised launches)
+SCHEDULES = [(0, 0, 0, 0, 0, 0), (65536, 65536, 8, 6, 0, 0), (4096, 16384, 4, 4, 0, 1),
+             (16384, 0, 6, 6, 0, 0)]
+KEYS = ("tail_rows_velocity", "tail_rows_pressure", "spmv_group", "smooth_group",
+        "coarse_degree", "serial_launches")
 
 
 @pytest.fixture(scope="module")
@@ -38,14 +41,15 @@ def fs():
     return mod
 
 
-def _run(fs, make, sched, prec, nsteps=2):
+def _run(fs, make, sched, prec, nsteps=2, iters=False):
     S = make(prec)
     try:
         fs.fs_set_schedule(S.prob, *sched)
         assert fs.fs_get_schedule(S.prob) == dict(zip(KEYS, sched))
         st = fs.fs_step(S.prob, nsteps)
         assert all(s["status"] == 0 for s in st)
-        return S.state()[0]
+        x = S.state()[0]
+        return (x, [s["iters"] for s in st]) if iters else x
     finally:
         S.close()
 
@@ -70,6 +74,22 @@ def test_schedules_agree_batch(fs, prec):
     make = lambda q: fs.Stepper.from_workloads(wls, precision=q)
     xs = [_run(fs, make, sc, p) for sc in SCHEDULES[:2]]
     assert rel_l2(xs[1], xs[0]) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_refine"])
+def test_coarse_degree_two_reaches_the_same_solution(fs, prec):
+    """Degree-2 smoothing below the finest level (the default) is a
+    different preconditioner from degree 3: the iterates change, the solution
+    does not beyond the parity bar.  Both meshes have a smoothed level
+    between the finest and the dense coarsest one."""
+    p = fs.FS_PREC_FP64 if prec == "fp64" else fs.FS_PREC_FP32_REFINE
+    for wl in (W.channel(64, 16), W.cube(10, jitter=0.05)):
+        make = lambda q: fs.Stepper.from_workload(wl, precision=q)
+        x3, i3 = _run(fs, make, (0, 0, 0, 0, 3, 0), p, iters=True)
+        x2, i2 = _run(fs, make, (0, 0, 0, 0, 2, 0), p, iters=True)
+        print(wl.name, prec, "iterations per step, degree 3 / 2:", i3, i2)
+        assert not np.array_equal(x2, x3)  # the knob reaches the V-cycle
+        assert rel_l2(x2, x3) <= 1e-9
 
 
 def test_autotune_installs_a_candidate(fs):
@@ -98,5 +118,7 @@ def test_autotune_installs_a_candidate(fs):
             fs.fs_set_schedule(S.prob, 0, 0, spmv_group=5)
         with pytest.raises(fs.FsError):
             fs.fs_set_schedule(S.prob, 0, 0, smooth_group=8)
+        with pytest.raises(fs.FsError):
+            fs.fs_set_schedule(S.prob, 0, 0, serial_launches=2)
     finally:
         S.close()
