@@ -180,6 +180,10 @@ struct fs_problem {
   float *ip_rf = nullptr, *ip_zf = nullptr;
   int64_t* mrp = nullptr;  // paper-order monolithic row pointers (export)
   const int32_t* nat = nullptr;          // internal P2 node -> paper id
+  // batches: instance of every 32-row slice of the velocity rows (union
+  // node order) and of the pressure rows, -1 for slices of two instances
+  const int32_t* slice_seg_u = nullptr;
+  const int32_t* slice_seg_p = nullptr;
   double *natbuf = nullptr, *natbuf2 = nullptr;  // boundary conversions (lazy)
   // SELL-32 copies of the blocks for the iteration path (slice offsets and
   // columns shared by both precisions)
@@ -273,6 +277,8 @@ int upload_csr(fs_problem* P, const HostCsr& H, DCsr<T>& d) {
   std::vector<T> hv(H.val.begin(), H.val.end());
   FS_TRY(P->upload(&v, hv));
   d.nrow = (int32_t)H.nrow;
+  const double mean = H.nrow > 0 ? (double)H.col.size() / (double)H.nrow : 0.0;
+  d.lanes = mean <= 3.5 ? 1 : mean <= 16.0 ? 4 : 32;
   d.rp = rp;
   d.ci = ci;
   d.v = v;
@@ -461,6 +467,24 @@ int upload_hierarchy(fs_problem* P, const UnionHierarchy& U, int nc, DHier<T>& D
     dl.dinv = dinv;
     cheb_coeffs<T>(hl.lmax, dl);
     const int64_t rows = hl.A.nrow;
+    // batches: the segment (instance) of every 32-row slice of the level,
+    // -1 where a slice spans two instances
+    if (l < (int)U.inst_off.size() && U.inst_off[l].size() > 2) {
+      const std::vector<int64_t>& off = U.inst_off[l];
+      const int64_t nsl = (rows + 31) / 32;
+      std::vector<int32_t> ss(nsl);
+      for (int64_t q = 0; q < nsl; ++q) {
+        const int64_t r0 = 32 * q, r1 = std::min(rows, r0 + 32) - 1;
+        const auto seg = [&](int64_t r) {
+          return (int32_t)(std::upper_bound(off.begin(), off.end(), r) - off.begin() - 1);
+        };
+        const int32_t g0 = seg(r0);
+        ss[q] = g0 == seg(r1) ? g0 : -1;
+      }
+      int32_t* dss;
+      FS_TRY(P->upload(&dss, ss));
+      dl.skip.slice_seg = dss;
+    }
     // padded components stay zero
     for (T** v : {&D.b[l], &D.G0[l], &D.G1[l], &D.D0[l], &D.D1[l]}) {
       FS_TRY(P->alloc(v, (int64_t)D.ncp * rows));
@@ -678,6 +702,15 @@ int setup_precision(fs_problem* P, Precision<T>& pr, const UnionHierarchy& HA,
   std::vector<T> mi(mplinv_nu.begin(), mplinv_nu.end());
   FS_TRY(P->upload(&pr.mplinv_nu, mi));
   FS_TRY(alloc_krylov<T>(P, pr.kr, m, first, count));
+  // batches: the union kernels skip the rows of instances that have
+  // converged in the running cycle
+  if (P->nseg > 1) {
+    for (DHier<T>* H : {&pr.HA, &pr.HK})
+      for (int l = 0; l < H->nlev; ++l)
+        if (H->lev[l].skip.slice_seg) H->lev[l].skip.st = pr.kr.st;
+    pr.op.skip_u = {P->slice_seg_u, pr.kr.st};
+    pr.op.skip_p = {P->slice_seg_p, pr.kr.st};
+  }
   return FS_OK;
 }
 
@@ -727,7 +760,7 @@ int issue_iter(fs_problem* P, Precision<T>& pr, T* x, int relative_to_beta) {
     const JVec<T> w(K.Vb + n, jp, n);
     launch_precond<T>(pr.op, pr.HA, pr.HK, pr.mplinv_nu, 1.0 / P->desc.dt, P->pinned,
                       P->npinned, vj, zj, K.work_p, K.work_u, skip, q);
-    launch_spmv_full<T, T>(pr.op, zjc, nullptr, w, 0, skip, q);
+    launch_spmv_full<T, T>(pr.op, zjc, nullptr, w, 0, skip, q, /*seg=*/true);
     // one segment: the Givens step rides in the second CGS2 pass
     const bool fuse = P->nseg == 1;
     launch_seg_cgs2<T>(K.Vb, n, tl, K.st, K.ctl, K.partial, fuse, cond, q);
@@ -1133,9 +1166,10 @@ int time_precond(fs_problem* P, Precision<T>& pr, int reps, double* ms) {
   cudaGraph_t g;
   FS_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
   g_capturing = true;
+  const DHier<T> HA = without_skip(pr.HA), HK = without_skip(pr.HK);
   for (int i = 0; i < reps; ++i)
-    launch_precond<T>(pr.op, pr.HA, pr.HK, pr.mplinv_nu, 1.0 / P->desc.dt, P->pinned,
-                      P->npinned, K.Vb, K.Z, K.work_p, K.work_u, nullptr, s);
+    launch_precond<T>(pr.op, HA, HK, pr.mplinv_nu, 1.0 / P->desc.dt, P->pinned, P->npinned,
+                      K.Vb, K.Z, K.work_p, K.work_u, nullptr, s);
   g_capturing = false;
   FS_CUDA(cudaStreamEndCapture(s, &g));
   size_t nodes = 0;
@@ -1707,6 +1741,30 @@ int fs_problem_create_batch(fs_mesh* mesh, const fs_problem_desc* descs, int cou
     int32_t* nat;
     FS_TRY(P->upload(&nat, me.node_nat));
     P->nat = nat;
+  }
+  if (count > 1) {
+    std::vector<int32_t> own_u(me.n2), own_p(me.nv);
+    for (int i = 0; i < count; ++i) {
+      const Instance& I = me.inst[i];
+      for (int64_t q = 0; q < I.nv; ++q) own_u[I.voff + q] = own_p[I.voff + q] = i;
+      for (int64_t e = 0; e < I.ne; ++e) own_u[me.nv + I.eoff + e] = i;
+    }
+    const auto slices = [](const std::vector<int32_t>& own) {
+      const int64_t n = (int64_t)own.size(), ns = (n + 31) / 32;
+      std::vector<int32_t> ss(ns);
+      for (int64_t q = 0; q < ns; ++q) {
+        const int64_t r0 = 32 * q, r1 = std::min(n, r0 + 32);
+        ss[q] = own[r0];
+        for (int64_t r = r0 + 1; r < r1; ++r)
+          if (own[r] != own[r0]) ss[q] = -1;
+      }
+      return ss;
+    };
+    int32_t *su, *sp;
+    FS_TRY(P->upload(&su, slices(own_u)));
+    FS_TRY(P->upload(&sp, slices(own_p)));
+    P->slice_seg_u = su;
+    P->slice_seg_p = sp;
   }
   const int m = 30;
   if (d0.precision == FS_PREC_FP64)
@@ -2343,11 +2401,11 @@ int fs_profile_kernel(fs_problem* P, int kernel, int reps, double* avg_ms, doubl
       const int64_t n = P->n2;
       bytes = nnzA * (4 + s) + 4.0 * (n + 1) + n * s + 5.0 * d * n * s;
       if (f32) {
-        auto& H = P->p32.HA;
-        launch = [P, &H, d]() { launch_cheb_step<float>(H, d, P->stream); };
+        const DHier<float> H = without_skip(P->p32.HA);
+        launch = [P, H, d]() { launch_cheb_step<float>(H, d, P->stream); };
       } else {
-        auto& H = P->p64.HA;
-        launch = [P, &H, d]() { launch_cheb_step<double>(H, d, P->stream); };
+        const DHier<double> H = without_skip(P->p64.HA);
+        launch = [P, H, d]() { launch_cheb_step<double>(H, d, P->stream); };
       }
       break;
     }

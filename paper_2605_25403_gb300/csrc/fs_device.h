@@ -55,6 +55,11 @@ void upload_ref_tensors(const RefTensors& R2, const RefTensors& R3);
 template <typename T>
 struct DCsr {
   int32_t nrow = 0;
+  // threads that share a row in the transfer kernels (1, 4 or 32, from the
+  // mean row length: one thread per row for the 1-3 entries of a
+  // prolongation row, a warp for the ~50 of a restriction row onto a grid
+  // coarsened by 4)
+  int32_t lanes = 4;
   const int32_t* rp = nullptr;
   const int32_t* ci = nullptr;
   const T* v = nullptr;
@@ -182,6 +187,18 @@ void launch_p3_exact_state(const DMesh& m, const DPhys& ph, double t, int zero_i
 
 // ---- linear algebra (fs_linalg.cu) ---------------------------------------
 // Saddle-point operator in block form.
+struct SegState;
+
+// Rows of a batch whose segment (instance) has converged in the current
+// restart cycle: the union kernels skip them.  slice_seg[s] is the segment
+// of rows 32 s .. 32 s + 31 of a level (-1 where a slice holds rows of two
+// instances: never skipped); st is the Krylov segment state (null: nothing
+// is skipped, as for single problems and for timing runs).
+struct SegSkip {
+  const int32_t* slice_seg = nullptr;
+  const SegState* st = nullptr;
+};
+
 template <typename T>
 struct DOp {
   int dim = 0;
@@ -192,12 +209,17 @@ struct DOp {
   DSell<T> A, B, BT;
   const T* diagp = nullptr;
   int group = 0;  // slots issued together per thread (0: the default)
+  // batches: segments of the velocity rows (union node order) and of the
+  // pressure rows, for the Arnoldi steps' products
+  SegSkip skip_u, skip_p;
 };
 
 // y = K x (resid == 0) or y = b - K x (resid == 1); vectors of type V.
+// seg: skip the rows of converged segments (the Arnoldi step's product;
+// residuals and timing runs take every row).
 template <typename T, typename V>
 void launch_spmv_full(const DOp<T>& op, JVec<const V> x, const V* b, JVec<V> y,
-                      int resid, const int* skip, cudaStream_t s);
+                      int resid, const int* skip, cudaStream_t s, bool seg = false);
 
 // Scalar CSR values (row pointers rp) into a SELL-32 layout with slice
 // offsets off: out64 (and out32 when not null) receive the n-row matrix.
@@ -209,6 +231,7 @@ template <typename T>
 struct DLevel {
   DSell<T> A;           // level operator
   DCsr<T> P, R;         // P: prolongation from level+1, R = P^T
+  SegSkip skip;         // rows of this level by segment
   const T* dinv = nullptr;
   double inv_theta = 0, a1 = 0, b1 = 0, a2 = 0, b2 = 0;  // Chebyshev(3)
 };
@@ -248,6 +271,15 @@ struct DHier {
   // a copy of this struct in device memory (read by the coarse kernels)
   const DHier<T>* dev = nullptr;
 };
+
+// The hierarchy with segment skipping off (timing and profiling runs, whose
+// segment states are those of the last solve).
+template <typename T>
+inline DHier<T> without_skip(const DHier<T>& H) {
+  DHier<T> C = H;
+  for (int l = 0; l < 16; ++l) C.lev[l].skip.st = nullptr;
+  return C;
+}
 
 // Gauss-Jordan inversion with partial pivoting of a dense n x n FP64
 // matrix, held row-major as the augmented n x 2n array W = [A | I]; after
@@ -384,6 +416,14 @@ struct SegState {
   double cs[kMaxRestart], sn[kMaxRestart], g[kMaxRestart + 1];
   double h2[kMaxRestart + 1];
 };
+#ifdef __CUDACC__
+__device__ __forceinline__ bool seg_skipped(const SegSkip& k, int64_t row) {
+  if (!k.st) return false;
+  const int32_t g = k.slice_seg[row >> 5];
+  return g >= 0 && k.st[g].done;
+}
+#endif
+
 struct KCtl {
   int m;         // restart length
   int nseg;      // number of segments

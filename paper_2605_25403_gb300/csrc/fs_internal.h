@@ -178,6 +178,9 @@ struct UnionHierarchy {
                                      // on the device (one block above
                                      // kHostInverseMax rows)
   std::vector<int32_t> row_blk;      // coarsest row -> instance
+  // per level: first row of each instance (instance count + 1 entries;
+  // every level is block-diagonal in instance order)
+  std::vector<std::vector<int64_t>> inst_off;
   // level-0 rows are in instance-major (block) order, each instance's rows
   // in class order; perm[r] is the union row of block row r (empty when
   // the two orders agree)

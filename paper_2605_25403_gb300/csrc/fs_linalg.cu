@@ -59,7 +59,8 @@ constexpr int kUSpmv = 6;
 template <typename T, typename V, int DIM, int kUS>
 __global__ void __launch_bounds__(256) k_spmv_full(DOp<T> op, JVec<const V> xv,
                                                    const V* __restrict__ b, JVec<V> yv,
-                                                   int resid, const int* skip) {
+                                                   int resid, SegSkip sku, SegSkip skp,
+                                                   const int* skip) {
   pdl_wait();
   if (skip && *skip) return;
   const V* __restrict__ x = xv.get();
@@ -69,7 +70,7 @@ __global__ void __launch_bounds__(256) k_spmv_full(DOp<T> op, JVec<const V> xv,
   const V* __restrict__ xp = x + DIM * n2;
   if (t >= wp) {
     const int64_t row = t - wp;
-    if (row >= n2) return;
+    if (row >= n2 || seg_skipped(sku, row)) return;
     V acc[DIM];
 #pragma unroll
     for (int c = 0; c < DIM; ++c) acc[c] = V(0);
@@ -124,7 +125,7 @@ __global__ void __launch_bounds__(256) k_spmv_full(DOp<T> op, JVec<const V> xv,
     }
   } else {
     const int64_t q = t;
-    if (q >= nv) return;
+    if (q >= nv || seg_skipped(skp, q)) return;
     V acc = V(0);
     const int64_t t32 = q & 31, o1 = op.B.off[(q >> 5) + 1];
     for (int64_t o = op.B.off[q >> 5] + t32; o < o1; o += kUS * 32) {
@@ -455,11 +456,11 @@ __global__ void __launch_bounds__(256) k_mg(DSell<T> A, const T* __restrict__ di
                                             T* __restrict__ Gout, T* __restrict__ Dout,
                                             T alpha, T beta, T inv_theta, JVec<T> outv,
                                             int64_t out_ld, const int32_t* __restrict__ perm,
-                                            int nc, const int* skip) {
+                                            int nc, SegSkip sk, const int* skip) {
   pdl_wait();
   if (skip && *skip) return;
   const int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (row >= A.nrow) return;
+  if (row >= A.nrow || seg_skipped(sk, row)) return;
   mg_row<T, NC, NCP, MODE, G>(A, dinv, b, Gin, Din, Gout, Dout, alpha, beta, inv_theta,
                                   MODE == MG_LAST ? outv.get() : nullptr, out_ld, perm, nc, row);
 }
@@ -469,23 +470,26 @@ __global__ void __launch_bounds__(256) k_mg_restrict(DCsr<T> R, const T* __restr
                                                      T* __restrict__ bc, T* __restrict__ Gc,
                                                      T* __restrict__ Dc,
                                                      const T* __restrict__ dinvc,
-                                                     T inv_theta_c, const int* skip) {
+                                                     T inv_theta_c, SegSkip sk,
+                                                     const int* skip) {
   pdl_wait();
   if (skip && *skip) return;
   const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t row = gt / L;
+  // skipped rows stay in the lane groups' shuffles (inactive)
   restrict_row<T, NCP, L>(R, Rf, bc, Gc, Dc, dinvc, inv_theta_c, row, (int)(gt % L),
-                                 row < R.nrow);
+                          row < R.nrow && !seg_skipped(sk, row));
 }
 
 template <typename T, int NCP, int L>
 __global__ void __launch_bounds__(256) k_mg_prolong(DCsr<T> P, const T* __restrict__ Xc,
-                                                    T* __restrict__ Gf, const int* skip) {
+                                                    T* __restrict__ Gf, SegSkip sk,
+                                                    const int* skip) {
   pdl_wait();
   if (skip && *skip) return;
   const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t row = gt / L;
-  prolong_row<T, NCP, L>(P, Xc, Gf, row, (int)(gt % L), row < P.nrow);
+  prolong_row<T, NCP, L>(P, Xc, Gf, row, (int)(gt % L), row < P.nrow && !seg_skipped(sk, row));
 }
 
 // The coarsest level's solve; every pointer and size comes by value, so no
@@ -493,12 +497,12 @@ __global__ void __launch_bounds__(256) k_mg_prolong(DCsr<T> P, const T* __restri
 template <typename T, int NCP>
 __global__ void k_mg_dense(DenseView<T> D, int64_t ncoarse, const T* __restrict__ b,
                            T* __restrict__ X, const int32_t* __restrict__ perm, JVec<T> outv,
-                           int64_t out_ld, int nc, const int* skip) {
+                           int64_t out_ld, int nc, SegSkip sk, const int* skip) {
   pdl_wait();
   if (skip && *skip) return;
   const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32;
   dense_row<T, NCP>(D, b, X, outv.get(), out_ld, perm, nc, row, threadIdx.x & 31,
-                    row < ncoarse);
+                    row < ncoarse && !seg_skipped(sk, row));
 }
 
 // The V-cycle from level l0 (its right-hand side and first step in place)
@@ -510,6 +514,29 @@ __global__ void k_mg_dense(DenseView<T> D, int64_t ncoarse, const T* __restrict_
 // G1[l0], or in `out` when l0 = 0.  Vectors written in one phase and read in
 // the next go through plain loads: the barrier (barrier.cluster arrive with
 // release, wait with acquire semantics) orders them at cluster scope.
+// The transfer passes of the fused tail: every thread of the cluster takes
+// rows LN at a time (LN consecutive lanes of one warp per row).
+template <typename T, int NCP, int LN>
+__device__ __forceinline__ void tail_restrict(const DCsr<T>& R, const T* Rf, T* bc, T* Gc, T* Dc,
+                                              const T* dinvc, T inv_theta_c, int64_t tid,
+                                              int64_t nth) {
+  const int64_t nr = R.nrow, groups = nth / LN, sweeps = (nr + groups - 1) / groups;
+  for (int64_t q = 0; q < sweeps; ++q) {
+    const int64_t r = q * groups + tid / LN;
+    restrict_row<T, NCP, LN>(R, Rf, bc, Gc, Dc, dinvc, inv_theta_c, r, (int)(tid % LN), r < nr);
+  }
+}
+
+template <typename T, int NCP, int LN>
+__device__ __forceinline__ void tail_prolong(const DCsr<T>& P, const T* Xc, T* Gf, int64_t tid,
+                                             int64_t nth) {
+  const int64_t nr = P.nrow, groups = nth / LN, sweeps = (nr + groups - 1) / groups;
+  for (int64_t q = 0; q < sweeps; ++q) {
+    const int64_t r = q * groups + tid / LN;
+    prolong_row<T, NCP, LN>(P, Xc, Gf, r, (int)(tid % LN), r < nr);
+  }
+}
+
 template <typename T, int NCP, int NT>
 __global__ void __launch_bounds__(NT, 1) k_mg_tail(const DHier<T>* __restrict__ Hp, int l0,
                                                    JVec<T> outv, int64_t out_ld, int nc,
@@ -522,7 +549,7 @@ __global__ void __launch_bounds__(NT, 1) k_mg_tail(const DHier<T>* __restrict__ 
   const int64_t tid = (int64_t)blockIdx.x * NT + threadIdx.x;
   const int64_t nth = (int64_t)gridDim.x * NT;
   const int last = H.nlev - 1;
-  const int lane4 = threadIdx.x & 3, lane32 = threadIdx.x & 31;
+  const int lane32 = threadIdx.x & 31;
   for (int l = l0; l < last; ++l) {
     const DLevel<T>& L = H.lev[l];
     const int64_t n = L.A.nrow;
@@ -552,13 +579,16 @@ __global__ void __launch_bounds__(NT, 1) k_mg_tail(const DHier<T>* __restrict__ 
     const DLevel<T>& C = H.lev[l + 1];
     const bool dense_next = l + 1 == last;
     const T* resid = light ? D0 : G1;
-    const int64_t nr = L.R.nrow, groups = nth / 4, sweeps = (nr + groups - 1) / groups;
-    for (int64_t q = 0; q < sweeps; ++q) {
-      const int64_t r = q * groups + tid / 4;
-      restrict_row<T, NCP, 4>(L.R, resid, H.b[l + 1], H.G0[l + 1], H.D0[l + 1],
-                                    dense_next ? nullptr : C.dinv, (T)C.inv_theta, r, lane4,
-                                    r < nr);
-    }
+    const T* dinvc = dense_next ? nullptr : C.dinv;
+    if (L.R.lanes == 32)
+      tail_restrict<T, NCP, 32>(L.R, resid, H.b[l + 1], H.G0[l + 1], H.D0[l + 1], dinvc,
+                                (T)C.inv_theta, tid, nth);
+    else if (L.R.lanes == 1)
+      tail_restrict<T, NCP, 1>(L.R, resid, H.b[l + 1], H.G0[l + 1], H.D0[l + 1], dinvc,
+                               (T)C.inv_theta, tid, nth);
+    else
+      tail_restrict<T, NCP, 4>(L.R, resid, H.b[l + 1], H.G0[l + 1], H.D0[l + 1], dinvc,
+                               (T)C.inv_theta, tid, nth);
     cl.sync();
   }
   {
@@ -580,11 +610,12 @@ __global__ void __launch_bounds__(NT, 1) k_mg_tail(const DHier<T>* __restrict__ 
     const bool light = l > 0 && H.coarse_deg == 2;
     {
       T* corrected = light ? G1 : G0;
-      const int64_t nr = L.P.nrow, groups = nth / 4, sweeps = (nr + groups - 1) / groups;
-      for (int64_t q = 0; q < sweeps; ++q) {
-        const int64_t r = q * groups + tid / 4;
-        prolong_row<T, NCP, 4>(L.P, H.G1[l + 1], corrected, r, lane4, r < nr);
-      }
+      if (L.P.lanes == 32)
+        tail_prolong<T, NCP, 32>(L.P, H.G1[l + 1], corrected, tid, nth);
+      else if (L.P.lanes == 1)
+        tail_prolong<T, NCP, 1>(L.P, H.G1[l + 1], corrected, tid, nth);
+      else
+        tail_prolong<T, NCP, 4>(L.P, H.G1[l + 1], corrected, tid, nth);
     }
     cl.sync();
     if (light) {
@@ -615,6 +646,37 @@ __global__ void __launch_bounds__(NT, 1) k_mg_tail(const DHier<T>* __restrict__ 
   }
 }
 
+// Transfer passes with R.lanes / P.lanes threads per row.
+// sk: the segments of R's rows (the coarse level) / of P's rows (the fine one).
+template <typename T, int NCP>
+void launch_restrict(const DCsr<T>& R, const T* Rf, T* bc, T* Gc, T* Dc, const T* dinvc,
+                     T inv_theta_c, const SegSkip& sk, const int* skip, cudaStream_t s) {
+  const int64_t rows = R.nrow;
+  if (R.lanes == 32)
+    launch_k(k_mg_restrict<T, NCP, 32>, blocks_for(rows * 32), 256, 0, s, R, Rf, bc, Gc, Dc,
+             dinvc, inv_theta_c, sk, skip);
+  else if (R.lanes == 1)
+    launch_k(k_mg_restrict<T, NCP, 1>, blocks_for(rows), 256, 0, s, R, Rf, bc, Gc, Dc, dinvc,
+             inv_theta_c, sk, skip);
+  else
+    launch_k(k_mg_restrict<T, NCP, 4>, blocks_for(rows * 4), 256, 0, s, R, Rf, bc, Gc, Dc,
+             dinvc, inv_theta_c, sk, skip);
+  count_launches(1);
+}
+
+template <typename T, int NCP>
+void launch_prolong(const DCsr<T>& P, const T* Xc, T* Gf, const SegSkip& sk, const int* skip,
+                    cudaStream_t s) {
+  const int64_t rows = P.nrow;
+  if (P.lanes == 32)
+    launch_k(k_mg_prolong<T, NCP, 32>, blocks_for(rows * 32), 256, 0, s, P, Xc, Gf, sk, skip);
+  else if (P.lanes == 1)
+    launch_k(k_mg_prolong<T, NCP, 1>, blocks_for(rows), 256, 0, s, P, Xc, Gf, sk, skip);
+  else
+    launch_k(k_mg_prolong<T, NCP, 4>, blocks_for(rows * 4), 256, 0, s, P, Xc, Gf, sk, skip);
+  count_launches(1);
+}
+
 template <typename T, int NCP>
 void launch_mg(int mode, const DLevel<T>& L, const T* b, const T* Gin, const T* Din, T* Gout,
                T* Dout, T alpha, T beta, JVec<T> out, int64_t out_ld, const int32_t* perm, int nc,
@@ -623,8 +685,8 @@ void launch_mg(int mode, const DLevel<T>& L, const T* b, const T* Gin, const T* 
   const T it = (T)L.inv_theta;
   constexpr int NC = NCP == 4 ? 3 : NCP;  // real components (3D pads 3 to 4)
 #define FS_MG(M, G)                                                                        \
-  launch_k(k_mg<T, NC, NCP, M, G>, blocks_for(n), 256, 0, s, L.A, L.dinv, b, Gin, Din, Gout, Dout, \
-                                                       alpha, beta, it, out, out_ld, perm, nc, skip)
+  launch_k(k_mg<T, NC, NCP, M, G>, blocks_for(n), 256, 0, s, L.A, L.dinv, b, Gin, Din, Gout,    \
+           Dout, alpha, beta, it, out, out_ld, perm, nc, L.skip, skip)
   if (group == 6) {
     if (mode == MG_STEP) FS_MG(MG_STEP, 6);
     else if (mode == MG_RESID) FS_MG(MG_RESID, 6);
@@ -679,7 +741,7 @@ void vcycle_level(const DHier<T>& H, int l, JVec<T> out, int64_t out_ld, int nc,
   if (l == H.nlev - 1) {
     launch_k(k_mg_dense<T, NCP>, blocks_for(H.ncoarse * 32), 256, 0, s,
         dense_view(H), H.ncoarse, H.b[l], H.G1[l], top ? H.perm : nullptr,
-        top ? out : JVec<T>(), out_ld, nc, skip);
+        top ? out : JVec<T>(), out_ld, nc, H.lev[l].skip, skip);
     count_launches(1);
     return;
   }
@@ -698,14 +760,10 @@ void vcycle_level(const DHier<T>& H, int l, JVec<T> out, int64_t out_ld, int nc,
                       H.group, s);
     launch_mg<T, NCP>(MG_RESID, L, b, G1, D1, D0, nullptr, T(0), T(0), JVec<T>(), 0, nullptr,
                       nc, skip, H.group, s);
-    launch_k(k_mg_restrict<T, NCP, 4>, blocks_for(L.R.nrow * 4), 256, 0, s,
-        L.R, D0, H.b[l + 1], H.G0[l + 1], H.D0[l + 1], coarsest_next ? nullptr : C.dinv,
-        (T)C.inv_theta, skip);
-    count_launches(1);
+    launch_restrict<T, NCP>(L.R, D0, H.b[l + 1], H.G0[l + 1], H.D0[l + 1],
+                            coarsest_next ? nullptr : C.dinv, (T)C.inv_theta, C.skip, skip, s);
     vcycle_level<T, NCP>(H, l + 1, JVec<T>(), 0, nc, skip, s);
-    launch_k(k_mg_prolong<T, NCP, 4>, blocks_for(L.P.nrow * 4), 256, 0, s, L.P, H.G1[l + 1], G1,
-                                                                      skip);
-    count_launches(1);
+    launch_prolong<T, NCP>(L.P, H.G1[l + 1], G1, L.skip, skip, s);
     launch_mg<T, NCP>(MG_START, L, b, G1, nullptr, G0, D0, T(0), T(0), JVec<T>(), 0, nullptr,
                       nc, skip, H.group, s);
     launch_mg<T, NCP>(MG_LAST, L, b, G0, D0, G1, nullptr, a1, b1, JVec<T>(), 0, nullptr, nc,
@@ -719,13 +777,10 @@ void vcycle_level(const DHier<T>& H, int l, JVec<T> out, int64_t out_ld, int nc,
   // residual of x3 = G0 into G1; G0 keeps x3 for the correction
   launch_mg<T, NCP>(MG_RESID, L, b, G0, D0, G1, nullptr, T(0), T(0), JVec<T>(), 0, nullptr, nc,
                     skip, H.group, s);
-  launch_k(k_mg_restrict<T, NCP, 4>, blocks_for(L.R.nrow * 4), 256, 0, s,
-      L.R, G1, H.b[l + 1], H.G0[l + 1], H.D0[l + 1], coarsest_next ? nullptr : C.dinv,
-      (T)C.inv_theta, skip);
-  count_launches(1);
+  launch_restrict<T, NCP>(L.R, G1, H.b[l + 1], H.G0[l + 1], H.D0[l + 1],
+                          coarsest_next ? nullptr : C.dinv, (T)C.inv_theta, C.skip, skip, s);
   vcycle_level<T, NCP>(H, l + 1, JVec<T>(), 0, nc, skip, s);
-  launch_k(k_mg_prolong<T, NCP, 4>, blocks_for(L.P.nrow * 4), 256, 0, s, L.P, H.G1[l + 1], G0, skip);
-  count_launches(1);
+  launch_prolong<T, NCP>(L.P, H.G1[l + 1], G0, L.skip, skip, s);
   launch_mg<T, NCP>(MG_START, L, b, G0, nullptr, G1, D1, T(0), T(0), JVec<T>(), 0, nullptr, nc,
                     skip, H.group, s);
   launch_mg<T, NCP>(MG_STEP, L, b, G1, D1, G0, D0, a1, b1, JVec<T>(), 0, nullptr, nc, skip,
@@ -817,11 +872,14 @@ __global__ void __launch_bounds__(256) k_bt_add_mg(DSell<T> BT, int64_t n2, JVec
                                                    const int32_t* __restrict__ iperm,
                                                    const T* __restrict__ dinv0, T inv_theta0,
                                                    T* __restrict__ b0, T* __restrict__ G0,
-                                                   T* __restrict__ D0, const int* skip) {
+                                                   T* __restrict__ D0, SegSkip sk0,
+                                                   const int* skip) {
   pdl_wait();
   if (skip && *skip) return;
   const int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (row >= n2) return;
+  const int64_t dst = iperm ? iperm[row] : row;
+  if (seg_skipped(sk0, dst)) return;
   const T* __restrict__ r = rv.get();
   const T* __restrict__ zp = zpv.get();
   T acc[DIM];
@@ -834,7 +892,6 @@ __global__ void __launch_bounds__(256) k_bt_add_mg(DSell<T> BT, int64_t n2, JVec
 #pragma unroll
     for (int c = 0; c < DIM; ++c) acc[c] += BT.v[base + 32 * c] * p;
   }
-  const int64_t dst = iperm ? iperm[row] : row;
   T t[NCP], d0[NCP];
   const T s = dinv0 ? dinv0[dst] * inv_theta0 : T(0);
 #pragma unroll
@@ -951,13 +1008,15 @@ inline unsigned grid_stride_blocks(int64_t n) {
 
 template <typename T, typename V>
 void launch_spmv_full(const DOp<T>& op, JVec<const V> x, const V* b, JVec<V> y, int resid,
-                      const int* skip, cudaStream_t s) {
+                      const int* skip, cudaStream_t s, bool seg) {
   const int64_t threads = ((op.nv + 31) & ~(int64_t)31) + op.n2;
+  const SegSkip su = seg ? op.skip_u : SegSkip{}, sp = seg ? op.skip_p : SegSkip{};
   // slots per group: the schedule's, else 6 in FP32 and 4 in FP64 (FP64
   // rows are partly bound by FP64 arithmetic and do best shallower)
   const int g = op.group ? op.group : (std::is_same<V, float>::value ? kUSpmv : kU);
 #define FS_SPMV(D, G) \
-  launch_k(k_spmv_full<T, V, D, G>, blocks_for(threads), 256, 0, s, op, x, b, y, resid, skip)
+  launch_k(k_spmv_full<T, V, D, G>, blocks_for(threads), 256, 0, s, op, x, b, y, resid, su, sp, \
+           skip)
   if (op.dim == 2) {
     if (g == 8) FS_SPMV(2, 8);
     else if (g == 6) FS_SPMV(2, 6);
@@ -972,9 +1031,9 @@ void launch_spmv_full(const DOp<T>& op, JVec<const V> x, const V* b, JVec<V> y, 
 }
 template void launch_spmv_full<double, double>(const DOp<double>&, JVec<const double>,
                                                const double*, JVec<double>, int, const int*,
-                                               cudaStream_t);
+                                               cudaStream_t, bool);
 template void launch_spmv_full<float, float>(const DOp<float>&, JVec<const float>, const float*,
-                                             JVec<float>, int, const int*, cudaStream_t);
+                                             JVec<float>, int, const int*, cudaStream_t, bool);
 
 void launch_csr_to_sell(int64_t n, const int32_t* rp, const double* in, const int64_t* off,
                         double* out64, float* out32, cudaStream_t s) {
@@ -1039,13 +1098,13 @@ void launch_precond(const DOp<T>& op, const DHier<T>& HA, const DHier<T>& HK,
   const T* d0 = a1 ? HA.lev[0].dinv : nullptr;
   const T it0 = (T)HA.lev[0].inv_theta;
   if (dim == 2) {
-    launch_k(k_bt_add_mg<T, 2, 2>, blocks_for(n2), 256, 0, s, op.BT, n2, r, zpc, HA.iperm, d0, it0,
-                                                        HA.b[0], HA.G0[0], HA.D0[0], skip);
+    launch_k(k_bt_add_mg<T, 2, 2>, blocks_for(n2), 256, 0, s, op.BT, n2, r, zpc, HA.iperm, d0,
+             it0, HA.b[0], HA.G0[0], HA.D0[0], HA.lev[0].skip, skip);
     count_launches(1);
     vcycle_level<T, 2>(HA, 0, z, n2, 2, skip, s);
   } else {
-    launch_k(k_bt_add_mg<T, 3, 4>, blocks_for(n2), 256, 0, s, op.BT, n2, r, zpc, HA.iperm, d0, it0,
-                                                        HA.b[0], HA.G0[0], HA.D0[0], skip);
+    launch_k(k_bt_add_mg<T, 3, 4>, blocks_for(n2), 256, 0, s, op.BT, n2, r, zpc, HA.iperm, d0,
+             it0, HA.b[0], HA.G0[0], HA.D0[0], HA.lev[0].skip, skip);
     count_launches(1);
     vcycle_level<T, 4>(HA, 0, z, n2, 3, skip, s);
   }

@@ -514,6 +514,7 @@ void build_union_hierarchy(const Mesh& m, const std::vector<Mesh>& /*local*/,
   int depth = 0;
   for (int i = 0; i < K; ++i) depth = std::max(depth, (int)H[i].levels.size());
   U.H.levels.assign(depth, HostLevel());
+  U.inst_off.clear();
   for (int l = 0; l < depth; ++l) {
     std::vector<const HostCsr*> As, Ps, Rs;
     std::vector<HostCsr> ids;
@@ -538,6 +539,9 @@ void build_union_hierarchy(const Mesh& m, const std::vector<Mesh>& /*local*/,
       }
     }
     UL.A = block_diag(As);
+    std::vector<int64_t> off(1, 0);
+    for (const HostCsr* a : As) off.push_back(off.back() + a->nrow);
+    U.inst_off.push_back(off);
     if (l + 1 < depth) {
       UL.P = block_diag(Ps);
       UL.R = block_diag(Rs);
