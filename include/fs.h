@@ -447,7 +447,9 @@ int fs_csr_residual_norm_noalloc(int64_t n, const int64_t* rowptr,
  * `reps` applications, CUDA events) for every pair of candidate thresholds
  * {0, 4096, 16384, 65536} of the velocity and pressure hierarchies and both
  * smoothing group depths, and the saddle-point SpMV (`reps` launches) for
- * every SpMV group depth; it installs the fastest of each and reports them.  Leaves the state and assembled system
+ * every SpMV group depth, then the persistent form of the preconditioner
+ * (persistent_precond = 1) against the best of those; it installs the
+ * fastest of each and reports them.  Leaves the state and assembled system
  * unchanged.  Synchronises. */
 typedef struct {
   int64_t tail_rows_velocity;
@@ -468,6 +470,20 @@ typedef struct {
                             its first memory access); 1: plain serialised
                             launches.  Timing only: results are identical.
                             The autotuner keeps the value in place       */
+  int32_t persistent_precond; /* 1: each application of the block
+                            preconditioner is one persistent cooperative
+                            kernel over a device work-list of (phase,
+                            instance, row range) items, where an item waits
+                            only for the previous phase of its own instance
+                            (a batch's instances advance independently,
+                            and instances that have converged are skipped);
+                            0: one kernel per pass over all instances.  The
+                            per-row arithmetic is the same (results agree
+                            to rounding: the fused cluster tail and the
+                            slot-group depth are not used in this mode, it
+                            issues 4 slots at a time).  A wait that has not
+                            ended after one second makes the solve return
+                            FS_ERR_TIMEOUT.  fs_autotune times both forms */
 } fs_schedule;
 typedef struct {
   int candidates;        /* schedules timed                                  */
@@ -476,6 +492,9 @@ typedef struct {
   double spmv_default_ms;  /* one SpMV, schedule before                      */
   double spmv_best_ms;     /* ... with the installed schedule                */
   fs_schedule best;
+  double persistent_ms;    /* one preconditioner application in the persistent
+                              form, with the installed schedule's smoothing
+                              degree (0 when it could not be timed)        */
 } fs_tune_report;
 int fs_get_schedule(const fs_problem* prob, fs_schedule* out);
 int fs_set_schedule(fs_problem* prob, const fs_schedule* sched);

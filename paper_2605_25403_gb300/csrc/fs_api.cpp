@@ -108,6 +108,12 @@ struct Precision {
   DHier<T> HA, HK;
   T* mplinv_nu = nullptr;
   Krylov<T> kr;
+  // the persistent form of the preconditioner: first row of each instance
+  // per level of HA and HK, first caller pressure row of each instance, and
+  // the work-lists (one per coarse smoothing degree, built on first use)
+  std::vector<std::vector<int64_t>> offA, offK;
+  std::vector<int64_t> prow;
+  FlowDev flow[2];
 };
 
 // Resumable solve / step state.
@@ -206,7 +212,7 @@ struct fs_problem {
   std::vector<fs_solve_stats> last_stats;  // per instance, last solve
   double t = 0;
   bool assembled = false;
-  fs_schedule sched{0, 0, 0, 0};
+  fs_schedule sched{0, 0, 0, 0, 0, 0, 0};
 
   TileList tl() const { return TileList{tiles, ntiles}; }
 
@@ -557,6 +563,59 @@ int apply_tail(fs_problem* P, DHier<T>& D, int64_t tail_rows) {
   return FS_OK;
 }
 
+// The work-list of the persistent preconditioner for the hierarchies' current
+// coarse smoothing degree (built and uploaded on first use).
+template <typename T>
+int apply_flow(fs_problem* P, Precision<T>& pr) {
+  FlowDev& f = pr.flow[pr.HA.coarse_deg == 3 ? 1 : 0];
+  if (f.items) return FS_OK;
+  const int nb = flow_blocks<T>(pr.HA.ncp);
+  if (nb <= 0) {
+    set_error("persistent preconditioner: its kernel cannot be resident on this device");
+    return FS_ERR_UNSUPPORTED;
+  }
+  FlowHost h;
+  build_flow<T>(pr.HA, pr.HK, pr.offA, pr.offK, pr.prow, nb, h);
+  unsigned char* ph;
+  FlowItem* it;
+  int32_t* need;
+  unsigned *cnt, *ticket;
+  FS_TRY(P->upload(&ph, h.phases));
+  FS_TRY(P->upload(&it, h.items));
+  FS_TRY(P->upload(&need, h.need));
+  FS_TRY(P->alloc(&cnt, (int64_t)h.need.size()));
+  FS_TRY(P->alloc(&ticket, 1));
+  FS_CUDA(cudaMemsetAsync(cnt, 0, sizeof(unsigned) * h.need.size(), P->stream));
+  FS_CUDA(cudaMemsetAsync(ticket, 0, sizeof(unsigned), P->stream));
+  FS_CUDA(cudaStreamSynchronize(P->stream));  // host sources go out of scope
+  f.phases = ph;
+  f.items = it;
+  f.nitems = (int64_t)h.items.size();
+  f.cnt = cnt;
+  f.need = need;
+  f.ticket = ticket;
+  f.nphase = h.nphase;
+  f.nseg = P->nseg;
+  f.nblocks = nb;
+  return FS_OK;
+}
+
+// One application of the block preconditioner on r into z: the per-pass
+// launches, or the persistent kernel when the schedule asks for it (st: the
+// segment states whose done instances are skipped, or null).
+template <typename T>
+void issue_precond(fs_problem* P, Precision<T>& pr, const DHier<T>& HA, const DHier<T>& HK,
+                   JVec<const T> r, JVec<T> z, const SegState* st, const int* skip,
+                   cudaStream_t q) {
+  if (P->sched.persistent_precond)
+    launch_precond_flow<T>(pr.flow[HA.coarse_deg == 3 ? 1 : 0], pr.op, HA, pr.mplinv_nu,
+                           1.0 / P->desc.dt, P->pinned, P->npinned, r, z, pr.kr.work_p, st,
+                           pr.kr.st, skip, q);
+  else
+    launch_precond<T>(pr.op, HA, HK, pr.mplinv_nu, 1.0 / P->desc.dt, P->pinned, P->npinned, r,
+                      z, pr.kr.work_p, pr.kr.work_u, skip, q);
+}
+
 // Work-list over the n_dof entries: for every instance its vertex and edge
 // ranges in each component block and its pressure range, cut into tiles of
 // at most kTileLen entries; tiles of one instance are consecutive.
@@ -696,6 +755,9 @@ int setup_precision(fs_problem* P, Precision<T>& pr, const UnionHierarchy& HA,
                     const std::vector<int>& first, const std::vector<int>& count) {
   FS_TRY(upload_hierarchy<T>(P, HA, P->dim, pr.HA));
   FS_TRY(upload_hierarchy<T>(P, HK, 1, pr.HK));
+  pr.offA = HA.inst_off;
+  pr.offK = HK.inst_off;
+  pr.prow = HK.inst_off[0];  // vertices are numbered instance by instance
   FS_TRY(apply_tail<T>(P, pr.HA, P->sched.tail_rows_velocity));
   FS_TRY(apply_tail<T>(P, pr.HK, P->sched.tail_rows_pressure));
   apply_groups<T>(P, pr, P->sched);
@@ -758,8 +820,7 @@ int issue_iter(fs_problem* P, Precision<T>& pr, T* x, int relative_to_beta) {
     const JVec<T> zj(K.Z, jp, n);
     const JVec<const T> zjc(K.Z, jp, n);
     const JVec<T> w(K.Vb + n, jp, n);
-    launch_precond<T>(pr.op, pr.HA, pr.HK, pr.mplinv_nu, 1.0 / P->desc.dt, P->pinned,
-                      P->npinned, vj, zj, K.work_p, K.work_u, skip, q);
+    issue_precond<T>(P, pr, pr.HA, pr.HK, vj, zj, P->nseg > 1 ? K.st : nullptr, skip, q);
     launch_spmv_full<T, T>(pr.op, zjc, nullptr, w, 0, skip, q, /*seg=*/true);
     // one segment: the Givens step rides in the second CGS2 pass
     const bool fuse = P->nseg == 1;
@@ -1044,7 +1105,7 @@ int advance(fs_problem* P) {
         c.iters[q] += P->host_status[q].k;
         c.cycles[q] += 1;
         if (P->host_status[q].bad) {
-          c.status[q] = FS_ERR_NUMERIC;
+          c.status[q] = P->host_status[q].bad == 2 ? FS_ERR_TIMEOUT : FS_ERR_NUMERIC;
           c.retired[q] = 1;
         } else if (P->host_status[q].k == 0) {
           c.status[q] = FS_ERR_NOT_CONVERGED;
@@ -1107,7 +1168,7 @@ int advance(fs_problem* P) {
         c.iters[q] += P->host_status[q].k;
         c.cycles[q] += 1;
         if (P->host_status[q].bad) {
-          c.status[q] = FS_ERR_NUMERIC;
+          c.status[q] = P->host_status[q].bad == 2 ? FS_ERR_TIMEOUT : FS_ERR_NUMERIC;
           c.retired[q] = 1;
         }
       }
@@ -1143,6 +1204,7 @@ int install_schedule(fs_problem* P, Precision<T>& pr, const fs_schedule& sc) {
   apply_groups<T>(P, pr, sc);
   FS_TRY(apply_tail<T>(P, pr.HA, sc.tail_rows_velocity));
   FS_TRY(apply_tail<T>(P, pr.HK, sc.tail_rows_pressure));
+  if (sc.persistent_precond) FS_TRY(apply_flow<T>(P, pr));
   drop_graphs(pr.kr);
   return FS_OK;
 }
@@ -1159,7 +1221,7 @@ int install_schedule(fs_problem* P, const fs_schedule& sc) {
 // One application of the block preconditioner (mean over a CUDA graph of
 // `reps` applications on the Krylov scratch vectors, after one warm launch).
 template <typename T>
-int time_precond(fs_problem* P, Precision<T>& pr, int reps, double* ms) {
+int time_precond(fs_problem* P, Precision<T>& pr, int reps, int persistent, double* ms) {
   Krylov<T>& K = pr.kr;
   cudaStream_t s = P->stream;
   FS_CUDA(cudaMemsetAsync(K.Vb, 0, sizeof(T) * K.n, s));
@@ -1167,9 +1229,10 @@ int time_precond(fs_problem* P, Precision<T>& pr, int reps, double* ms) {
   FS_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
   g_capturing = true;
   const DHier<T> HA = without_skip(pr.HA), HK = without_skip(pr.HK);
-  for (int i = 0; i < reps; ++i)
-    launch_precond<T>(pr.op, HA, HK, pr.mplinv_nu, 1.0 / P->desc.dt, P->pinned, P->npinned,
-                      K.Vb, K.Z, K.work_p, K.work_u, nullptr, s);
+  const int saved = P->sched.persistent_precond;
+  P->sched.persistent_precond = persistent;
+  for (int i = 0; i < reps; ++i) issue_precond<T>(P, pr, HA, HK, K.Vb, K.Z, nullptr, nullptr, s);
+  P->sched.persistent_precond = saved;
   g_capturing = false;
   FS_CUDA(cudaStreamEndCapture(s, &g));
   size_t nodes = 0;
@@ -1200,9 +1263,10 @@ int time_precond(fs_problem* P, Precision<T>& pr, int reps, double* ms) {
   return FS_OK;
 }
 
-int time_precond(fs_problem* P, int reps, double* ms) {
-  if (P->desc.precision == FS_PREC_FP64) return time_precond<double>(P, P->p64, reps, ms);
-  return time_precond<float>(P, P->p32, reps, ms);
+int time_precond(fs_problem* P, int reps, int persistent, double* ms) {
+  if (P->desc.precision == FS_PREC_FP64)
+    return time_precond<double>(P, P->p64, reps, persistent, ms);
+  return time_precond<float>(P, P->p32, reps, persistent, ms);
 }
 
 // One saddle-point SpMV in the solver arithmetic (mean of `reps` launches
@@ -2419,7 +2483,7 @@ int fs_profile_kernel(fs_problem* P, int kernel, int reps, double* avg_ms, doubl
       break;
     }
     case FS_KERNEL_PRECOND: {
-      FS_TRY(time_precond(P, reps, avg_ms));
+      FS_TRY(time_precond(P, reps, P->sched.persistent_precond, avg_ms));
       *alg_bytes = 0;
       return FS_OK;
     }
@@ -2551,7 +2615,8 @@ int fs_set_schedule(fs_problem* P, const fs_schedule* sc) {
   };
   if (!P || !sc || sc->tail_rows_velocity < 0 || sc->tail_rows_pressure < 0 ||
       !in(sc->spmv_group, {0, 4, 6, 8}) || !in(sc->smooth_group, {0, 4, 6}) ||
-      !in(sc->coarse_degree, {0, 2, 3}) || !in(sc->serial_launches, {0, 1})) {
+      !in(sc->coarse_degree, {0, 2, 3}) || !in(sc->serial_launches, {0, 1}) ||
+      !in(sc->persistent_precond, {0, 1})) {
     set_error("fs_set_schedule: bad argument");
     return FS_ERR_INVALID_ARG;
   }
@@ -2581,7 +2646,7 @@ int fs_autotune(fs_problem* P, int reps, fs_tune_report* report) {
   const int sgroups[2] = {4, 6}, pgroups[3] = {4, 6, 8};
   fs_tune_report r{};
   r.best = P->sched;
-  FS_TRY(time_precond(P, reps, &r.default_ms));
+  FS_TRY(time_precond(P, reps, P->sched.persistent_precond, &r.default_ms));
   FS_TRY(time_spmv(P, reps, &r.spmv_default_ms));
   r.best_ms = r.default_ms;
   r.spmv_best_ms = r.spmv_default_ms;
@@ -2619,13 +2684,31 @@ int fs_autotune(fs_problem* P, int reps, fs_tune_report* report) {
         if (std::find(seen.begin(), seen.end(), k) != seen.end()) continue;
         seen.push_back(k);
         double ms = 0;
-        FS_TRY(time_precond(P, reps, &ms));
+        FS_TRY(time_precond(P, reps, 0, &ms));
         r.candidates += 1;
         if (ms < r.best_ms) {
           r.best_ms = ms;
           r.best = sc;
         }
       }
+  // the persistent preconditioner against the best per-pass schedule (its
+  // own time with that schedule's smoothing degree)
+  {
+    fs_schedule sc = r.best;
+    sc.persistent_precond = 0;
+    apply(sc);
+    double ms0 = 0, ms1 = 0;
+    FS_TRY(time_precond(P, reps, 0, &ms0));
+    int rc = P->desc.precision == FS_PREC_FP64 ? apply_flow<double>(P, P->p64)
+                                               : apply_flow<float>(P, P->p32);
+    if (rc == FS_OK) rc = time_precond(P, reps, 1, &ms1);
+    if (rc != FS_OK && rc != FS_ERR_UNSUPPORTED) return rc;
+    r.candidates += 1;
+    r.persistent_ms = rc == FS_OK ? ms1 : 0.0;
+    sc.persistent_precond = rc == FS_OK && ms1 < ms0 ? 1 : 0;
+    r.best = sc;
+    r.best_ms = sc.persistent_precond ? ms1 : std::min(r.best_ms, ms0);
+  }
   // the SpMV: group depths, with the preconditioner's choice in place
   for (int g : pgroups) {
     fs_schedule sc = r.best;

@@ -331,6 +331,63 @@ void launch_precond(const DOp<T>& op, const DHier<T>& HA, const DHier<T>& HK,
                     int npinned, JVec<const T> r, JVec<T> z, T* work_p, T* work_u,
                     const int* skip, cudaStream_t s);
 
+// ---- the block preconditioner as one persistent kernel (fs_linalg.cu) ----
+// The passes of launch_precond (pressure load, the pressure V-cycle, the
+// Cahouet-Chabard combination, the B^T coupling, the velocity V-cycle) become
+// phases of a work-list of items (phase, instance, row range).  One
+// cooperative launch (every block resident) walks it: block b takes items
+// b, b + grid, ... in list order; an item of phase p of instance i starts
+// once every item of phase p - 1 of instance i has finished (a counter per
+// (phase, instance), incremented after each item with release semantics,
+// polled with acquire loads by the block's first thread).  Instances are
+// independent (every operator of a batch is block-diagonal), so no phase
+// waits for the whole batch.  Items of instances that converged in the
+// running cycle are skipped.  The list is ordered by phase, so every item's
+// predecessors come before it and, all blocks being resident, every wait
+// ends; each wait still gives up after one second (the segment is then
+// marked with bad = 2 and the solve reports FS_ERR_TIMEOUT).  The last
+// block to leave zeroes the counters for the next launch.
+struct FlowItem {
+  int32_t phase, seg, row0, row1;
+};
+struct FlowHost {
+  std::vector<unsigned char> phases;  // nphase phase records (fs_linalg.cu)
+  std::vector<FlowItem> items;
+  std::vector<int32_t> need;          // items per (phase, instance): nphase x nseg
+  int nphase = 0;
+};
+struct FlowDev {
+  const void* phases = nullptr;
+  const FlowItem* items = nullptr;
+  int64_t nitems = 0;
+  unsigned* cnt = nullptr;             // nphase x nseg, zero between launches
+  const int32_t* need = nullptr;
+  unsigned* ticket = nullptr;          // exit ticket, zero between launches
+  int nphase = 0, nseg = 0, nblocks = 0;
+};
+// Resident blocks of the persistent kernel for this arithmetic and velocity
+// row width (ncp 2 or 4): blocks per SM x SMs of the current device.
+template <typename T>
+int flow_blocks(int ncp);
+// The work-list of one application.  offA / offK: per level of HA / HK the
+// first row of each instance (nseg + 1 entries, block order); prow: the
+// first caller pressure row of each instance (nseg + 1).  Items are
+// sized so that a phase over all instances has at least `nblocks` of them
+// when it has enough rows.
+template <typename T>
+void build_flow(const DHier<T>& HA, const DHier<T>& HK,
+                const std::vector<std::vector<int64_t>>& offA,
+                const std::vector<std::vector<int64_t>>& offK, const std::vector<int64_t>& prow,
+                int nblocks, FlowHost& out);
+// One application through the persistent kernel (same arguments as
+// launch_precond, plus the plan; st: skip instances with done set, or null;
+// flag: segment states that receive bad = 2 on a timed-out wait, or null).
+template <typename T>
+void launch_precond_flow(const FlowDev& f, const DOp<T>& op, const DHier<T>& HA,
+                         const T* mpl_inv_nu, double inv_dt, const int32_t* pinned,
+                         int npinned, JVec<const T> r, JVec<T> z, T* work_p,
+                         const SegState* st, SegState* flag, const int* skip, cudaStream_t s);
+
 // ---- incremental pressure correction (fs_ipcs.cu) -----------------------
 // Right-hand sides of the three stages (x = [u^n | p^n], b = the assembled
 // load with the Dirichlet and pinned values of t^{n+1}); see fs_ipcs.cu.

@@ -16,6 +16,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <type_traits>
 
 #include <cooperative_groups.h>
@@ -382,7 +383,7 @@ __host__ __device__ __forceinline__ DenseView<T> dense_view(const DHier<T>& H) {
 // boundary and a scalar tail), eight per lane in flight: a 3,500-row block
 // has only ~23 rows per SM, so the loads of one warp must cover the memory
 // latency.  b is re-read by every row from L1/L2.
-template <typename T, int NCP>
+template <typename T, int NCP, int U = 8>
 __device__ __forceinline__ void dense_row(const DenseView<T>& D, const T* __restrict__ b,
                                           T* __restrict__ X, T* __restrict__ out,
                                           int64_t out_ld, const int32_t* __restrict__ perm,
@@ -413,7 +414,6 @@ __device__ __forceinline__ void dense_row(const DenseView<T>& D, const T* __rest
     if (lane < h) add(Cr[lane], lane);
     const int64_t nvec = (nb - h) / E;
     const V* Cv = reinterpret_cast<const V*>(Cr + h);
-    constexpr int U = 8;  // 16-byte loads per lane issued together
     for (int64_t v0 = lane; v0 < nvec; v0 += 32 * U) {
       V q[U];
 #pragma unroll
@@ -1117,6 +1117,501 @@ template void launch_precond<float>(const DOp<float>&, const DHier<float>&,
                                     const DHier<float>&, const float*, double,
                                     const int32_t*, int, JVec<const float>, JVec<float>, float*,
                                     float*, const int*, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// The block preconditioner as one persistent kernel over a work-list
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kFlowThreads = 512;
+constexpr uint64_t kFlowWaitNs = 1000000000ull;  // one second per wait
+
+enum { FL_LOAD_P = 0, FL_MG, FL_RESTRICT, FL_PROLONG, FL_DENSE, FL_PREC_P, FL_BT_ADD };
+
+// One phase of the application: which pass, on which hierarchy (0 pressure,
+// 1 velocity), and every pointer and coefficient it takes.
+template <typename T>
+struct FlowPhase {
+  int32_t kind = 0, hier = 0, mode = 0, lanes = 1;
+  int32_t top = 0;  // writes the caller's vector (the last pass of level 0)
+  DSell<T> A;       // FL_MG: level operator
+  DCsr<T> X;        // FL_RESTRICT: R; FL_PROLONG: P
+  // FL_MG: the level's inverse diagonal; FL_RESTRICT: the coarse level's
+  // (null when the coarse level is solved densely); FL_LOAD_P, FL_BT_ADD:
+  // level 0's (null for a hierarchy of one level)
+  const T* dinv = nullptr;
+  const T* b = nullptr;    // FL_MG, FL_DENSE: the level's right-hand side
+  const T* in = nullptr;   // FL_MG: G in; FL_RESTRICT: fine residual; FL_PROLONG: coarse x
+  const T* din = nullptr;  // FL_MG: D in
+  T* out0 = nullptr;  // FL_MG: G out; FL_RESTRICT: coarse b; FL_PROLONG: fine G (in place);
+                      // FL_DENSE: x; FL_LOAD_P, FL_BT_ADD: level-0 b
+  T* out1 = nullptr;  // FL_MG: D out; FL_RESTRICT, FL_LOAD_P, FL_BT_ADD: G0
+  T* out2 = nullptr;  // FL_RESTRICT, FL_LOAD_P, FL_BT_ADD: D0
+  T alpha = 0, beta = 0, inv_theta = 0;
+  const int32_t* perm = nullptr;  // level-0 block row -> caller row (or null)
+  DenseView<T> dense{};           // FL_DENSE
+};
+
+template <typename T>
+struct FlowArgs {
+  FlowDev f;
+  DSell<T> BT;
+  JVec<const T> r;
+  JVec<T> z;
+  T* work_p;
+  const T* mpl;
+  T inv_dt;
+  const int32_t* pinned;
+  int npinned;
+  int64_t n2, nv;
+  int dim;
+  const SegState* st;
+  SegState* flag;
+  const int* skip;
+};
+
+__device__ __forceinline__ unsigned flow_ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint64_t flow_clock_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Chebyshev pass over rows [r0, r1) of one hierarchy (NC real components
+// padded to NCP), a thread per row; the phase's fields are read once.
+template <typename T, int NC, int NCP, int MODE>
+__device__ __forceinline__ void flow_mg_rows(const FlowPhase<T>& ph, int64_t r0, int64_t r1,
+                                             T* out, int64_t out_ld, int nc) {
+  const DSell<T> A = ph.A;
+  const T* dinv = ph.dinv;
+  const T *b = ph.b, *in = ph.in, *din = ph.din;
+  T *o0 = ph.out0, *o1 = ph.out1;
+  const T al = ph.alpha, be = ph.beta, it = ph.inv_theta;
+  const bool top = MODE == MG_LAST && ph.top;
+  T* dst = top ? out : nullptr;
+  const int32_t* perm = top ? ph.perm : nullptr;
+  for (int64_t r = r0 + threadIdx.x; r < r1; r += kFlowThreads)
+    mg_row<T, NC, NCP, MODE, kU>(A, dinv, b, in, din, o0, o1, al, be, it, dst, out_ld, perm, nc,
+                                 r);
+}
+template <typename T, int NC, int NCP>
+__device__ __forceinline__ void flow_mg(const FlowPhase<T>& ph, int64_t r0, int64_t r1, T* out,
+                                        int64_t out_ld, int nc) {
+  switch (ph.mode) {
+    case MG_STEP: flow_mg_rows<T, NC, NCP, MG_STEP>(ph, r0, r1, out, out_ld, nc); break;
+    case MG_RESID: flow_mg_rows<T, NC, NCP, MG_RESID>(ph, r0, r1, out, out_ld, nc); break;
+    case MG_START: flow_mg_rows<T, NC, NCP, MG_START>(ph, r0, r1, out, out_ld, nc); break;
+    default: flow_mg_rows<T, NC, NCP, MG_LAST>(ph, r0, r1, out, out_ld, nc);
+  }
+}
+
+// Transfer passes: L lanes per row, every thread of the block runs the same
+// number of sweeps (the lane groups' shuffles need all 32 lanes).
+template <typename T, int NCP, int L>
+__device__ __forceinline__ void flow_restrict(const FlowPhase<T>& ph, int64_t r0, int64_t r1) {
+  constexpr int rows = kFlowThreads / L;
+  for (int64_t base = r0; base < r1; base += rows) {
+    const int64_t r = base + threadIdx.x / L;
+    restrict_row<T, NCP, L>(ph.X, ph.in, ph.out0, ph.out1, ph.out2, ph.dinv, ph.inv_theta, r,
+                            (int)(threadIdx.x % L), r < r1);
+  }
+}
+template <typename T, int NCP, int L>
+__device__ __forceinline__ void flow_prolong(const FlowPhase<T>& ph, int64_t r0, int64_t r1) {
+  constexpr int rows = kFlowThreads / L;
+  for (int64_t base = r0; base < r1; base += rows) {
+    const int64_t r = base + threadIdx.x / L;
+    prolong_row<T, NCP, L>(ph.X, ph.in, ph.out0, r, (int)(threadIdx.x % L), r < r1);
+  }
+}
+template <typename T, int NCP>
+__device__ __forceinline__ void flow_transfer(const FlowPhase<T>& ph, int64_t r0, int64_t r1) {
+  if (ph.kind == FL_RESTRICT) {
+    if (ph.lanes == 32) flow_restrict<T, NCP, 32>(ph, r0, r1);
+    else if (ph.lanes == 1) flow_restrict<T, NCP, 1>(ph, r0, r1);
+    else flow_restrict<T, NCP, 4>(ph, r0, r1);
+  } else {
+    if (ph.lanes == 32) flow_prolong<T, NCP, 32>(ph, r0, r1);
+    else if (ph.lanes == 1) flow_prolong<T, NCP, 1>(ph, r0, r1);
+    else flow_prolong<T, NCP, 4>(ph, r0, r1);
+  }
+}
+template <typename T, int NCP>
+__device__ __forceinline__ void flow_dense(const FlowPhase<T>& ph, int64_t r0, int64_t r1,
+                                           T* out, int64_t out_ld, int nc) {
+  constexpr int rows = kFlowThreads / 32;
+  for (int64_t base = r0; base < r1; base += rows) {
+    const int64_t r = base + threadIdx.x / 32;
+    dense_row<T, NCP, 2>(ph.dense, ph.b, ph.out0, ph.top ? out : nullptr, out_ld,
+                      ph.top ? ph.perm : nullptr, nc, r, threadIdx.x & 31, r < r1);
+  }
+}
+
+template <typename T, int NCP>
+__device__ __forceinline__ void flow_item(const FlowArgs<T>& a, const FlowPhase<T>& ph,
+                                          int64_t r0, int64_t r1) {
+  constexpr int NC = NCP == 4 ? 3 : NCP;
+  const int64_t vel = (int64_t)a.dim * a.n2;
+  switch (ph.kind) {
+    case FL_MG:
+      if (ph.hier == 0) flow_mg<T, 1, 1>(ph, r0, r1, a.work_p, a.nv, 1);
+      else flow_mg<T, NC, NCP>(ph, r0, r1, a.z.get(), a.n2, a.dim);
+      break;
+    case FL_RESTRICT:
+    case FL_PROLONG:
+      if (ph.hier == 0) flow_transfer<T, 1>(ph, r0, r1);
+      else flow_transfer<T, NCP>(ph, r0, r1);
+      break;
+    case FL_DENSE:
+      if (ph.hier == 0) flow_dense<T, 1>(ph, r0, r1, a.work_p, a.nv, 1);
+      else flow_dense<T, NCP>(ph, r0, r1, a.z.get(), a.n2, a.dim);
+      break;
+    case FL_LOAD_P: {
+      // level-0 rows of the pressure hierarchy: b0 = r_p, G0 = D0 = D^-1 r_p / theta
+      const T* __restrict__ rp = a.r.get() + vel;
+      for (int64_t d = r0 + threadIdx.x; d < r1; d += kFlowThreads) {
+        const int64_t q = ph.perm ? ph.perm[d] : d;
+        const T v = rp[q];
+        const T d0 = ph.dinv ? ph.dinv[d] * v * ph.inv_theta : T(0);
+        ph.out0[d] = v;
+        ph.out1[d] = d0;
+        ph.out2[d] = d0;
+      }
+      break;
+    }
+    case FL_PREC_P: {
+      // caller pressure rows: z_p = nu Mp^-1 r_p + dt^-1 y_K, then z_p = r_p
+      // on the pinned rows of the range
+      const T* __restrict__ rp = a.r.get() + vel;
+      T* __restrict__ zp = a.z.get() + vel;
+      for (int64_t q = r0 + threadIdx.x; q < r1; q += kFlowThreads)
+        zp[q] = a.mpl[q] * rp[q] + a.inv_dt * a.work_p[q];
+      __syncthreads();
+      for (int i = threadIdx.x; i < a.npinned; i += kFlowThreads) {
+        const int64_t q = a.pinned[i];
+        if (q >= r0 && q < r1) zp[q] = rp[q];
+      }
+      break;
+    }
+    default: {  // FL_BT_ADD over level-0 rows of the velocity hierarchy
+      const T* __restrict__ r = a.r.get();
+      const T* __restrict__ zp = a.z.get() + vel;
+      constexpr int DIM = NC;
+      for (int64_t d = r0 + threadIdx.x; d < r1; d += kFlowThreads) {
+        const int64_t row = ph.perm ? ph.perm[d] : d;
+        T acc[DIM];
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) acc[c] = T(0);
+        const int64_t o1 = a.BT.off[(row >> 5) + 1];
+        for (int64_t o = a.BT.off[row >> 5] + (row & 31); o < o1; o += 32) {
+          const int64_t base = (o - (row & 31)) * DIM + (row & 31);
+          const T p = zp[a.BT.ci[o]];
+#pragma unroll
+          for (int c = 0; c < DIM; ++c) acc[c] += a.BT.v[base + 32 * c] * p;
+        }
+        T t[NCP], d0[NCP];
+        const T sc = ph.dinv ? ph.dinv[d] * ph.inv_theta : T(0);
+#pragma unroll
+        for (int c = 0; c < NCP; ++c) {
+          t[c] = c < DIM ? r[c * a.n2 + row] + acc[c] : T(0);
+          d0[c] = sc * t[c];
+        }
+        vstore<T, NCP>(ph.out0 + d * NCP, t);
+        vstore<T, NCP>(ph.out1 + d * NCP, d0);
+        vstore<T, NCP>(ph.out2 + d * NCP, d0);
+      }
+    }
+  }
+}
+
+template <typename T, int NCP>
+__global__ void __launch_bounds__(kFlowThreads, 2) k_prec_flow(FlowArgs<T> a) {
+  pdl_wait();
+  if (a.skip && *a.skip) return;  // the same for every block: no counter is touched
+  __shared__ int s_go[2];
+  __shared__ int s_last;
+  const FlowPhase<T>* __restrict__ phs = static_cast<const FlowPhase<T>*>(a.f.phases);
+  const int nseg = a.f.nseg;
+  int ok_p = -1, ok_s = -1;  // (phase, instance) whose predecessor was seen complete
+  int par = 0;
+  for (int64_t k = blockIdx.x; k < a.f.nitems; k += gridDim.x, par ^= 1) {
+    const FlowItem it = a.f.items[k];
+    if (threadIdx.x == 0) {
+      int go = 1;
+      if (a.st && a.st[it.seg].done) {
+        go = 0;
+      } else if (it.phase > 0 && !(it.phase == ok_p && it.seg == ok_s)) {
+        const int64_t q = (int64_t)(it.phase - 1) * nseg + it.seg;
+        const unsigned need = (unsigned)a.f.need[q];
+        if (flow_ld_acquire(a.f.cnt + q) < need) {
+          const uint64_t t0 = flow_clock_ns();
+          while (flow_ld_acquire(a.f.cnt + q) < need) {
+            if (flow_clock_ns() - t0 > kFlowWaitNs) {
+              // give up: the item runs on stale data and the solve reports it
+              if (a.flag) a.flag[it.seg].bad = 2;
+              break;
+            }
+          }
+        }
+        ok_p = it.phase;
+        ok_s = it.seg;
+      }
+      s_go[par] = go;
+    }
+    __syncthreads();
+    if (!s_go[par]) continue;
+    flow_item<T, NCP>(a, phs[it.phase], it.row0, it.row1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicAdd(a.f.cnt + (int64_t)it.phase * nseg + it.seg, 1u);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = atomicAdd(a.f.ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    const int64_t nc = (int64_t)a.f.nphase * nseg;
+    for (int64_t i = threadIdx.x; i < nc; i += kFlowThreads) a.f.cnt[i] = 0;
+    if (threadIdx.x == 0) *a.f.ticket = 0;
+  }
+}
+
+
+// Phases of one application, in the order launch_precond issues its passes.
+template <typename T>
+struct FlowGen {
+  std::vector<FlowPhase<T>> ph;
+  std::vector<std::vector<int64_t>> rows;  // per phase: first row of each instance
+  std::vector<int> sweep;                  // rows one block covers in one sweep
+
+  void add(const FlowPhase<T>& p, const std::vector<int64_t>& r, int sw) {
+    ph.push_back(p);
+    rows.push_back(r);
+    sweep.push_back(sw);
+  }
+  FlowPhase<T> mg(const DHier<T>& H, int hier, int l, int mode, const T* Gin, const T* Din,
+                  T* Gout, T* Dout, double alpha, double beta, bool top) {
+    FlowPhase<T> p;
+    const DLevel<T>& L = H.lev[l];
+    p.kind = FL_MG;
+    p.hier = hier;
+    p.mode = mode;
+    p.top = top;
+    p.A = L.A;
+    p.dinv = L.dinv;
+    p.b = H.b[l];
+    p.in = Gin;
+    p.din = Din;
+    p.out0 = Gout;
+    p.out1 = Dout;
+    p.alpha = (T)alpha;
+    p.beta = (T)beta;
+    p.inv_theta = (T)L.inv_theta;
+    p.perm = top ? H.perm : nullptr;
+    return p;
+  }
+  // mirrors vcycle_level (without the fused cluster tail)
+  void vcycle(const DHier<T>& H, int hier, const std::vector<std::vector<int64_t>>& off, int l) {
+    const bool top = l == 0;
+    const int kT = kFlowThreads;
+    if (l == H.nlev - 1) {
+      FlowPhase<T> p;
+      p.kind = FL_DENSE;
+      p.hier = hier;
+      p.top = top;
+      p.b = H.b[l];
+      p.out0 = H.G1[l];
+      p.perm = top ? H.perm : nullptr;
+      p.dense = dense_view(H);
+      add(p, off[l], kT / 32);
+      return;
+    }
+    const DLevel<T>& L = H.lev[l];
+    const DLevel<T>& C = H.lev[l + 1];
+    T *G0 = H.G0[l], *G1 = H.G1[l], *D0 = H.D0[l], *D1 = H.D1[l];
+    const bool coarsest_next = l + 1 == H.nlev - 1;
+    auto restrict_from = [&](const T* resid) {
+      FlowPhase<T> p;
+      p.kind = FL_RESTRICT;
+      p.hier = hier;
+      p.lanes = L.R.lanes;
+      p.X = L.R;
+      p.in = resid;
+      p.out0 = H.b[l + 1];
+      p.out1 = H.G0[l + 1];
+      p.out2 = H.D0[l + 1];
+      p.dinv = coarsest_next ? nullptr : C.dinv;
+      p.inv_theta = (T)C.inv_theta;
+      add(p, off[l + 1], kT / p.lanes);
+    };
+    auto prolong_into = [&](T* Gf) {
+      FlowPhase<T> p;
+      p.kind = FL_PROLONG;
+      p.hier = hier;
+      p.lanes = L.P.lanes;
+      p.X = L.P;
+      p.in = H.G1[l + 1];
+      p.out0 = Gf;
+      add(p, off[l], kT / p.lanes);
+    };
+    if (!top && H.coarse_deg == 2) {
+      add(mg(H, hier, l, MG_STEP, G0, D0, G1, D1, L.a1, L.b1, false), off[l], kT);
+      add(mg(H, hier, l, MG_RESID, G1, D1, D0, nullptr, 0, 0, false), off[l], kT);
+      restrict_from(D0);
+      vcycle(H, hier, off, l + 1);
+      prolong_into(G1);
+      add(mg(H, hier, l, MG_START, G1, nullptr, G0, D0, 0, 0, false), off[l], kT);
+      add(mg(H, hier, l, MG_LAST, G0, D0, G1, nullptr, L.a1, L.b1, false), off[l], kT);
+      return;
+    }
+    add(mg(H, hier, l, MG_STEP, G0, D0, G1, D1, L.a1, L.b1, false), off[l], kT);
+    add(mg(H, hier, l, MG_STEP, G1, D1, G0, D0, L.a2, L.b2, false), off[l], kT);
+    add(mg(H, hier, l, MG_RESID, G0, D0, G1, nullptr, 0, 0, false), off[l], kT);
+    restrict_from(G1);
+    vcycle(H, hier, off, l + 1);
+    prolong_into(G0);
+    add(mg(H, hier, l, MG_START, G0, nullptr, G1, D1, 0, 0, false), off[l], kT);
+    add(mg(H, hier, l, MG_STEP, G1, D1, G0, D0, L.a1, L.b1, false), off[l], kT);
+    add(mg(H, hier, l, MG_LAST, G0, D0, G1, nullptr, L.a2, L.b2, top), off[l], kT);
+  }
+};
+
+}  // namespace
+
+template <typename T>
+int flow_blocks(int ncp) {
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  auto k = ncp == 4 ? k_prec_flow<T, 4> : k_prec_flow<T, 2>;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, kFlowThreads, 0);
+  cudaGetLastError();
+  return std::max(0, per) * sms;
+}
+template int flow_blocks<double>(int);
+template int flow_blocks<float>(int);
+
+template <typename T>
+void build_flow(const DHier<T>& HA, const DHier<T>& HK,
+                const std::vector<std::vector<int64_t>>& offA,
+                const std::vector<std::vector<int64_t>>& offK, const std::vector<int64_t>& prow,
+                int nblocks, FlowHost& out) {
+  FlowGen<T> g;
+  const int kT = kFlowThreads;
+  {
+    FlowPhase<T> p;
+    p.kind = FL_LOAD_P;
+    p.hier = 0;
+    p.perm = HK.perm;
+    p.dinv = HK.nlev > 1 ? HK.lev[0].dinv : nullptr;
+    p.inv_theta = (T)HK.lev[0].inv_theta;
+    p.out0 = HK.b[0];
+    p.out1 = HK.G0[0];
+    p.out2 = HK.D0[0];
+    g.add(p, offK[0], kT);
+  }
+  g.vcycle(HK, 0, offK, 0);
+  {
+    FlowPhase<T> p;
+    p.kind = FL_PREC_P;
+    g.add(p, prow, kT);
+  }
+  {
+    FlowPhase<T> p;
+    p.kind = FL_BT_ADD;
+    p.hier = 1;
+    p.perm = HA.perm;
+    p.dinv = HA.nlev > 1 ? HA.lev[0].dinv : nullptr;
+    p.inv_theta = (T)HA.lev[0].inv_theta;
+    p.out0 = HA.b[0];
+    p.out1 = HA.G0[0];
+    p.out2 = HA.D0[0];
+    g.add(p, offA[0], kT);
+  }
+  g.vcycle(HA, 1, offA, 0);
+  const int nphase = (int)g.ph.size();
+  const int nseg = (int)prow.size() - 1;
+  out.nphase = nphase;
+  out.phases.resize(sizeof(FlowPhase<T>) * nphase);
+  std::memcpy(out.phases.data(), g.ph.data(), out.phases.size());
+  out.items.clear();
+  out.need.assign((size_t)nphase * nseg, 0);
+  const int64_t nb = std::max(1, nblocks);
+  for (int p = 0; p < nphase; ++p) {
+    const std::vector<int64_t>& r = g.rows[p];
+    const int64_t sw = g.sweep[p];
+    const int64_t total = r.back() - r.front();
+    // enough items to reach every block when the phase has the rows for it
+    const int64_t chunk = sw * std::max<int64_t>(1, total / (nb * sw));
+    for (int s = 0; s < nseg; ++s)
+      for (int64_t a = r[s]; a < r[s + 1]; a += chunk) {
+        out.items.push_back(
+            FlowItem{p, s, (int32_t)a, (int32_t)std::min(a + chunk, r[s + 1])});
+        out.need[(size_t)p * nseg + s] += 1;
+      }
+  }
+}
+template void build_flow<double>(const DHier<double>&, const DHier<double>&,
+                                 const std::vector<std::vector<int64_t>>&,
+                                 const std::vector<std::vector<int64_t>>&,
+                                 const std::vector<int64_t>&, int, FlowHost&);
+template void build_flow<float>(const DHier<float>&, const DHier<float>&,
+                                const std::vector<std::vector<int64_t>>&,
+                                const std::vector<std::vector<int64_t>>&,
+                                const std::vector<int64_t>&, int, FlowHost&);
+
+template <typename T>
+void launch_precond_flow(const FlowDev& f, const DOp<T>& op, const DHier<T>& HA,
+                         const T* mpl_inv_nu, double inv_dt, const int32_t* pinned,
+                         int npinned, JVec<const T> r, JVec<T> z, T* work_p,
+                         const SegState* st, SegState* flag, const int* skip, cudaStream_t s) {
+  FlowArgs<T> a;
+  a.f = f;
+  a.BT = op.BT;
+  a.r = r;
+  a.z = z;
+  a.work_p = work_p;
+  a.mpl = mpl_inv_nu;
+  a.inv_dt = (T)inv_dt;
+  a.pinned = pinned;
+  a.npinned = npinned;
+  a.n2 = op.n2;
+  a.nv = op.nv;
+  a.dim = op.dim;
+  a.st = st;
+  a.flag = flag;
+  a.skip = skip;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(f.nblocks);
+  cfg.blockDim = dim3(kFlowThreads);
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  auto k = HA.ncp == 4 ? k_prec_flow<T, 4> : k_prec_flow<T, 2>;
+  cudaLaunchKernelEx(&cfg, k, a);
+  count_launches(1);
+}
+template void launch_precond_flow<double>(const FlowDev&, const DOp<double>&,
+                                          const DHier<double>&, const double*, double,
+                                          const int32_t*, int, JVec<const double>,
+                                          JVec<double>, double*, const SegState*, SegState*,
+                                          const int*, cudaStream_t);
+template void launch_precond_flow<float>(const FlowDev&, const DOp<float>&, const DHier<float>&,
+                                         const float*, double, const int32_t*, int,
+                                         JVec<const float>, JVec<float>, float*,
+                                         const SegState*, SegState*, const int*, cudaStream_t);
 
 template <typename T>
 void launch_vcycle_scalar(const DHier<T>& H, const T* r, T* z, int64_t n, cudaStream_t s) {

@@ -130,7 +130,7 @@ class fs_server_desc(ctypes.Structure):
 class fs_schedule(ctypes.Structure):
     _fields_ = [("tail_rows_velocity", _i64), ("tail_rows_pressure", _i64),
                 ("spmv_group", _int), ("smooth_group", _int), ("coarse_degree", _int),
-                ("serial_launches", _int)]
+                ("serial_launches", _int), ("persistent_precond", _int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -138,12 +138,14 @@ class fs_schedule(ctypes.Structure):
 
 class fs_tune_report(ctypes.Structure):
     _fields_ = [("candidates", _int), ("default_ms", _d), ("best_ms", _d),
-                ("spmv_default_ms", _d), ("spmv_best_ms", _d), ("best", fs_schedule)]
+                ("spmv_default_ms", _d), ("spmv_best_ms", _d), ("best", fs_schedule),
+                ("persistent_ms", _d)]
 
     def as_dict(self):
         return {"candidates": self.candidates, "default_ms": self.default_ms,
                 "best_ms": self.best_ms, "spmv_default_ms": self.spmv_default_ms,
-                "spmv_best_ms": self.spmv_best_ms, "best": self.best.as_dict()}
+                "spmv_best_ms": self.spmv_best_ms, "best": self.best.as_dict(),
+                "persistent_ms": self.persistent_ms}
 
 
 class fs_request_result(ctypes.Structure):
@@ -504,9 +506,10 @@ def fs_get_schedule(prob):
 
 
 def fs_set_schedule(prob, tail_rows_velocity, tail_rows_pressure, spmv_group=0, smooth_group=0,
-                    coarse_degree=0, serial_launches=0):
+                    coarse_degree=0, serial_launches=0, persistent_precond=0):
     sc = fs_schedule(int(tail_rows_velocity), int(tail_rows_pressure), int(spmv_group),
-                     int(smooth_group), int(coarse_degree), int(serial_launches))
+                     int(smooth_group), int(coarse_degree), int(serial_launches),
+                     int(persistent_precond))
     _check(_lib.fs_set_schedule(prob, ctypes.byref(sc)), "fs_set_schedule")
 
 

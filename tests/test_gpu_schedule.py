@@ -24,11 +24,12 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 # (tail rows velocity, tail rows pressure, SpMV group, smoothing group,
-#  coarse-level smoother degree, serialised launches)
-SCHEDULES = [(0, 0, 0, 0, 0, 0), (65536, 65536, 8, 6, 0, 0), (4096, 16384, 4, 4, 0, 1),
-             (16384, 0, 6, 6, 0, 0)]
+#  coarse-level smoother degree, serialised launches, persistent preconditioner)
+SCHEDULES = [(0, 0, 0, 0, 0, 0, 0), (65536, 65536, 8, 6, 0, 0, 0), (4096, 16384, 4, 4, 0, 1, 0),
+             (16384, 0, 6, 6, 0, 0, 0), (0, 0, 0, 0, 0, 0, 1), (0, 0, 6, 0, 3, 1, 1)]
 KEYS = ("tail_rows_velocity", "tail_rows_pressure", "spmv_group", "smooth_group",
-        "coarse_degree", "serial_launches")
+        "coarse_degree", "serial_launches", "persistent_precond")
+PERSISTENT = (0, 0, 0, 0, 0, 0, 1)
 
 
 @pytest.fixture(scope="module")
@@ -72,8 +73,30 @@ def test_schedules_agree_batch(fs, prec):
     wls = [W.unit_square(12, jitter=0.1, seed=1), W.unit_square(20, jitter=0.1, seed=2),
            W.unit_square(9, jitter=0.1, seed=3)]
     make = lambda q: fs.Stepper.from_workloads(wls, precision=q)
-    xs = [_run(fs, make, sc, p) for sc in SCHEDULES[:2]]
-    assert rel_l2(xs[1], xs[0]) <= TOL[prec]
+    xs = [_run(fs, make, sc, p) for sc in SCHEDULES[:2] + [PERSISTENT]]
+    for x in xs[1:]:
+        assert rel_l2(x, xs[0]) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_refine"])
+def test_persistent_preconditioner_3d_and_batch_with_retirement(fs, prec):
+    """The persistent form on 3D rows (three components padded to four) and on
+    a batch whose instances converge at different iterations (a small
+    viscous square and a larger one at Re = 500): items of a converged
+    instance are skipped while the others continue."""
+    p = fs.FS_PREC_FP64 if prec == "fp64" else fs.FS_PREC_FP32_REFINE
+    wl = W.cube(6, jitter=0.05)
+    make = lambda q: fs.Stepper.from_workload(wl, precision=q)
+    x0 = _run(fs, make, SCHEDULES[0], p)
+    x1 = _run(fs, make, PERSISTENT, p)
+    assert rel_l2(x1, x0) <= TOL[prec]
+    wls = [W.unit_square(8, jitter=0.1, seed=4),
+           W.unit_square(48, nu=1.0 / 500.0), W.unit_square(16, jitter=0.1, seed=5)]
+    make = lambda q: fs.Stepper.from_workloads(wls, precision=q)
+    x0, i0 = _run(fs, make, SCHEDULES[0], p, nsteps=3, iters=True)
+    x1, i1 = _run(fs, make, PERSISTENT, p, nsteps=3, iters=True)
+    print(prec, "iterations per step, per pass / persistent:", i0, i1)
+    assert rel_l2(x1, x0) <= TOL[prec]
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32_refine"])
@@ -85,8 +108,8 @@ def test_coarse_degree_two_reaches_the_same_solution(fs, prec):
     p = fs.FS_PREC_FP64 if prec == "fp64" else fs.FS_PREC_FP32_REFINE
     for wl in (W.channel(64, 16), W.cube(10, jitter=0.05)):
         make = lambda q: fs.Stepper.from_workload(wl, precision=q)
-        x3, i3 = _run(fs, make, (0, 0, 0, 0, 3, 0), p, iters=True)
-        x2, i2 = _run(fs, make, (0, 0, 0, 0, 2, 0), p, iters=True)
+        x3, i3 = _run(fs, make, (0, 0, 0, 0, 3, 0, 0), p, iters=True)
+        x2, i2 = _run(fs, make, (0, 0, 0, 0, 2, 0, 0), p, iters=True)
         print(wl.name, prec, "iterations per step, degree 3 / 2:", i3, i2)
         assert not np.array_equal(x2, x3)  # the knob reaches the V-cycle
         assert rel_l2(x2, x3) <= 1e-9
@@ -98,6 +121,7 @@ def test_autotune_installs_a_candidate(fs):
         x0, t0 = S.state()
         rep = fs.fs_autotune(S.prob, reps=3)
         assert rep["candidates"] >= 2 and 0 < rep["best_ms"] <= rep["default_ms"]
+        assert rep["persistent_ms"] > 0  # the persistent form was timed too
         assert 0 < rep["spmv_best_ms"] <= rep["spmv_default_ms"]
         assert fs.fs_get_schedule(S.prob) == rep["best"]
         x1, t1 = S.state()
@@ -120,5 +144,7 @@ def test_autotune_installs_a_candidate(fs):
             fs.fs_set_schedule(S.prob, 0, 0, smooth_group=8)
         with pytest.raises(fs.FsError):
             fs.fs_set_schedule(S.prob, 0, 0, serial_launches=2)
+        with pytest.raises(fs.FsError):
+            fs.fs_set_schedule(S.prob, 0, 0, persistent_precond=2)
     finally:
         S.close()
