@@ -48,6 +48,9 @@ def parse(argv=None):
     p.add_argument("--coarse-degree", type=int, default=0, choices=[0, 2, 3],
                    help="Chebyshev degree of the smoothing below the finest multigrid level "
                         "(0: the library default, 2)")
+    p.add_argument("--fine-degree", type=int, default=0, choices=[0, 2, 3],
+                   help="Chebyshev degree on the finest multigrid level (0: the library "
+                        "default, 2)")
     p.add_argument("--serial-launches", type=int, default=0, choices=[0, 1],
                    help="1: plain serialised kernel launches instead of programmatic dependent "
                         "launches (the library default)")
@@ -497,7 +500,8 @@ def main():
     k64 = args.fp64_steps
     if prec != fs.FS_PREC_FP64 and k64 > 0:
         S64 = fs.Stepper.from_workload(wl, precision=fs.FS_PREC_FP64, stream=stream.cuda_stream)
-        fs.fs_set_schedule(S64.prob, 0, 0, 0, 0, args.coarse_degree, args.serial_launches)
+        fs.fs_set_schedule(S64.prob, 0, 0, 0, 0, args.coarse_degree, args.serial_launches,
+                           fine_degree=args.fine_degree)
         tune64 = fs.fs_autotune(S64.prob, reps=5)
         for _ in range(args.warmup):
             fs.fs_step(S64.prob, 1)
@@ -516,7 +520,8 @@ def main():
     S = fs.Stepper.from_workload(wl, precision=prec, stream=stream.cuda_stream)
     # set-up, untimed: pick the multigrid schedule by timing the candidates
     if args.schedule == "auto":
-        fs.fs_set_schedule(S.prob, 0, 0, 0, 0, args.coarse_degree, args.serial_launches)
+        fs.fs_set_schedule(S.prob, 0, 0, 0, 0, args.coarse_degree, args.serial_launches,
+                           fine_degree=args.fine_degree)
         tune = fs.fs_autotune(S.prob, reps=5)
     else:
         fs.fs_set_schedule(S.prob, *(int(q) for q in args.schedule.split(",")))
@@ -552,7 +557,8 @@ def main():
     SE = fs.Stepper.from_workload(wl, precision=prec, stream=stream.cuda_stream)
     fs.fs_set_schedule(SE.prob, sched["tail_rows_velocity"], sched["tail_rows_pressure"],
                        sched["spmv_group"], sched["smooth_group"], sched["coarse_degree"],
-                       sched["serial_launches"], sched["persistent_precond"])
+                       sched["serial_launches"], sched["persistent_precond"],
+                       sched["fine_degree"])
     for _ in range(max(0, args.warmup - 1)):
         fs.fs_step(SE.prob, 1)
     xh = torch.empty(ndof, dtype=torch.float64).pin_memory()

@@ -484,6 +484,12 @@ typedef struct {
                             issues 4 slots at a time).  A wait that has not
                             ended after one second makes the solve return
                             FS_ERR_TIMEOUT.  fs_autotune times both forms */
+  int32_t fine_degree;   /* degree of the Chebyshev smoother on the finest
+                            level of both hierarchies (pre and post): 3 or
+                            2; 0 = 2.  Like coarse_degree it changes the
+                            preconditioner (iteration counts, not the
+                            solution beyond rtol); the autotuner keeps the
+                            value in place                              */
 } fs_schedule;
 typedef struct {
   int candidates;        /* schedules timed                                  */

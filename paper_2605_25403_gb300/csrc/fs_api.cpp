@@ -110,11 +110,17 @@ struct Precision {
   Krylov<T> kr;
   // the persistent form of the preconditioner: first row of each instance
   // per level of HA and HK, first caller pressure row of each instance, and
-  // the work-lists (one per coarse smoothing degree, built on first use)
+  // the work-lists (one per set of smoothing degrees, built on first use)
   std::vector<std::vector<int64_t>> offA, offK;
   std::vector<int64_t> prow;
-  FlowDev flow[2];
+  FlowDev flow[8];
 };
+
+// The work-list built for the hierarchies' current smoothing degrees.
+template <typename T>
+int flow_index(const DHier<T>& HA, const DHier<T>& HK) {
+  return (HA.coarse_deg == 3) | (HA.fine_deg == 3) << 1 | (HK.fine_deg == 3) << 2;
+}
 
 // Resumable solve / step state.
 enum Phase { PH_IDLE, PH_CHECK, PH_ITER, PH_RES64, PH_INNER, PH_DONE };
@@ -212,7 +218,7 @@ struct fs_problem {
   std::vector<fs_solve_stats> last_stats;  // per instance, last solve
   double t = 0;
   bool assembled = false;
-  fs_schedule sched{0, 0, 0, 0, 0, 0, 0};
+  fs_schedule sched{0, 0, 0, 0, 0, 0, 0, 0};
 
   TileList tl() const { return TileList{tiles, ntiles}; }
 
@@ -542,6 +548,7 @@ void apply_groups(fs_problem* P, Precision<T>& pr, const fs_schedule& sc) {
   pr.op.group = sc.spmv_group;
   pr.HA.group = pr.HK.group = sc.smooth_group ? sc.smooth_group : 4;
   pr.HA.coarse_deg = pr.HK.coarse_deg = sc.coarse_degree == 3 ? 3 : 2;
+  pr.HA.fine_deg = pr.HK.fine_deg = sc.fine_degree == 3 ? 3 : 2;
 }
 
 // The fused cluster kernel takes the levels with at most tail_rows rows
@@ -567,7 +574,7 @@ int apply_tail(fs_problem* P, DHier<T>& D, int64_t tail_rows) {
 // coarse smoothing degree (built and uploaded on first use).
 template <typename T>
 int apply_flow(fs_problem* P, Precision<T>& pr) {
-  FlowDev& f = pr.flow[pr.HA.coarse_deg == 3 ? 1 : 0];
+  FlowDev& f = pr.flow[flow_index(pr.HA, pr.HK)];
   if (f.items) return FS_OK;
   const int nb = flow_blocks<T>(pr.HA.ncp);
   if (nb <= 0) {
@@ -608,7 +615,7 @@ void issue_precond(fs_problem* P, Precision<T>& pr, const DHier<T>& HA, const DH
                    JVec<const T> r, JVec<T> z, const SegState* st, const int* skip,
                    cudaStream_t q) {
   if (P->sched.persistent_precond)
-    launch_precond_flow<T>(pr.flow[HA.coarse_deg == 3 ? 1 : 0], pr.op, HA, pr.mplinv_nu,
+    launch_precond_flow<T>(pr.flow[flow_index(HA, HK)], pr.op, HA, pr.mplinv_nu,
                            1.0 / P->desc.dt, P->pinned, P->npinned, r, z, pr.kr.work_p, st,
                            pr.kr.st, skip, q);
   else
@@ -2616,7 +2623,7 @@ int fs_set_schedule(fs_problem* P, const fs_schedule* sc) {
   if (!P || !sc || sc->tail_rows_velocity < 0 || sc->tail_rows_pressure < 0 ||
       !in(sc->spmv_group, {0, 4, 6, 8}) || !in(sc->smooth_group, {0, 4, 6}) ||
       !in(sc->coarse_degree, {0, 2, 3}) || !in(sc->serial_launches, {0, 1}) ||
-      !in(sc->persistent_precond, {0, 1})) {
+      !in(sc->persistent_precond, {0, 1}) || !in(sc->fine_degree, {0, 2, 3})) {
     set_error("fs_set_schedule: bad argument");
     return FS_ERR_INVALID_ARG;
   }

@@ -263,8 +263,9 @@ struct DHier {
   // slots issued together per thread in the smoothing passes (4 or 6)
   int group = 4;
   // Chebyshev degree of the pre- and post-smoothing below the finest level
-  // (3 or 2; the finest level always takes 3)
+  // and on the finest level (3 or 2 each)
   int coarse_deg = 2;
+  int fine_deg = 3;
   // first level run by the fused cluster kernel (-1: none), its cluster size
   int tail = -1;
   int tail_cluster = 8;

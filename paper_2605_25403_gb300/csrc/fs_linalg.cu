@@ -557,7 +557,7 @@ __global__ void __launch_bounds__(NT, 1) k_mg_tail(const DHier<T>* __restrict__ 
     const T* b = H.b[l];
     const T a1 = (T)L.a1, b1 = (T)L.b1, a2 = (T)L.a2, b2 = (T)L.b2, it = (T)L.inv_theta;
     // degree 2 below the finest level: the phases of vcycle_level's light path
-    const bool light = l > 0 && H.coarse_deg == 2;
+    const bool light = (l > 0 ? H.coarse_deg : H.fine_deg) == 2;
     for (int64_t r = tid; r < n; r += nth)
       mg_row<T, NC, NCP, MG_STEP>(L.A, L.dinv, b, G0, D0, G1, D1, a1, b1, it, nullptr, 0,
                                         nullptr, nc, r);
@@ -607,7 +607,7 @@ __global__ void __launch_bounds__(NT, 1) k_mg_tail(const DHier<T>* __restrict__ 
     T *G0 = H.G0[l], *G1 = H.G1[l], *D0 = H.D0[l], *D1 = H.D1[l];
     const T* b = H.b[l];
     const T a1 = (T)L.a1, b1 = (T)L.b1, a2 = (T)L.a2, b2 = (T)L.b2, it = (T)L.inv_theta;
-    const bool light = l > 0 && H.coarse_deg == 2;
+    const bool light = (l > 0 ? H.coarse_deg : H.fine_deg) == 2;
     {
       T* corrected = light ? G1 : G0;
       if (L.P.lanes == 32)
@@ -623,9 +623,10 @@ __global__ void __launch_bounds__(NT, 1) k_mg_tail(const DHier<T>* __restrict__ 
         mg_row<T, NC, NCP, MG_START>(L.A, L.dinv, b, G1, nullptr, G0, D0, T(0), T(0), it,
                                      nullptr, 0, nullptr, nc, r);
       cl.sync();
+      const bool top = l == 0 && out;
       for (int64_t r = tid; r < n; r += nth)
-        mg_row<T, NC, NCP, MG_LAST>(L.A, L.dinv, b, G0, D0, G1, nullptr, a1, b1, it, nullptr,
-                                    0, nullptr, nc, r);
+        mg_row<T, NC, NCP, MG_LAST>(L.A, L.dinv, b, G0, D0, G1, nullptr, a1, b1, it,
+                                    top ? out : nullptr, out_ld, top ? H.perm : nullptr, nc, r);
       if (l > l0) cl.sync();
       continue;
     }
@@ -751,7 +752,7 @@ void vcycle_level(const DHier<T>& H, int l, JVec<T> out, int64_t out_ld, int nc,
   T *G0 = H.G0[l], *G1 = H.G1[l], *D0 = H.D0[l], *D1 = H.D1[l];
   const T* b = H.b[l];
   const bool coarsest_next = l + 1 == H.nlev - 1;
-  if (!top && H.coarse_deg == 2) {
+  if ((top ? H.fine_deg : H.coarse_deg) == 2) {
     // degree 2 on a coarse level: one step after the restriction's first
     // (x2 in G1), the residual into the free D0, the correction into G1,
     // then the first post step and the last with the first step's
@@ -766,8 +767,8 @@ void vcycle_level(const DHier<T>& H, int l, JVec<T> out, int64_t out_ld, int nc,
     launch_prolong<T, NCP>(L.P, H.G1[l + 1], G1, L.skip, skip, s);
     launch_mg<T, NCP>(MG_START, L, b, G1, nullptr, G0, D0, T(0), T(0), JVec<T>(), 0, nullptr,
                       nc, skip, H.group, s);
-    launch_mg<T, NCP>(MG_LAST, L, b, G0, D0, G1, nullptr, a1, b1, JVec<T>(), 0, nullptr, nc,
-                      skip, H.group, s);
+    launch_mg<T, NCP>(MG_LAST, L, b, G0, D0, G1, nullptr, a1, b1, top ? out : JVec<T>(),
+                      out_ld, top ? H.perm : nullptr, nc, skip, H.group, s);
     return;
   }
   launch_mg<T, NCP>(MG_STEP, L, b, G0, D0, G1, D1, a1, b1, JVec<T>(), 0, nullptr, nc, skip,
@@ -1463,14 +1464,14 @@ struct FlowGen {
       p.out0 = Gf;
       add(p, off[l], kT / p.lanes);
     };
-    if (!top && H.coarse_deg == 2) {
+    if ((top ? H.fine_deg : H.coarse_deg) == 2) {
       add(mg(H, hier, l, MG_STEP, G0, D0, G1, D1, L.a1, L.b1, false), off[l], kT);
       add(mg(H, hier, l, MG_RESID, G1, D1, D0, nullptr, 0, 0, false), off[l], kT);
       restrict_from(D0);
       vcycle(H, hier, off, l + 1);
       prolong_into(G1);
       add(mg(H, hier, l, MG_START, G1, nullptr, G0, D0, 0, 0, false), off[l], kT);
-      add(mg(H, hier, l, MG_LAST, G0, D0, G1, nullptr, L.a1, L.b1, false), off[l], kT);
+      add(mg(H, hier, l, MG_LAST, G0, D0, G1, nullptr, L.a1, L.b1, top), off[l], kT);
       return;
     }
     add(mg(H, hier, l, MG_STEP, G0, D0, G1, D1, L.a1, L.b1, false), off[l], kT);

@@ -24,12 +24,14 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 # (tail rows velocity, tail rows pressure, SpMV group, smoothing group,
-#  coarse-level smoother degree, serialised launches, persistent preconditioner)
-SCHEDULES = [(0, 0, 0, 0, 0, 0, 0), (65536, 65536, 8, 6, 0, 0, 0), (4096, 16384, 4, 4, 0, 1, 0),
-             (16384, 0, 6, 6, 0, 0, 0), (0, 0, 0, 0, 0, 0, 1), (0, 0, 6, 0, 3, 1, 1)]
+#  coarse-level smoother degree, serialised launches, persistent preconditioner,
+#  finest-level smoother degree)
+SCHEDULES = [(0, 0, 0, 0, 0, 0, 0, 0), (65536, 65536, 8, 6, 0, 0, 0, 0),
+             (4096, 16384, 4, 4, 0, 1, 0, 0), (16384, 0, 6, 6, 0, 0, 0, 0),
+             (0, 0, 0, 0, 0, 0, 1, 0), (0, 0, 6, 0, 0, 1, 1, 0)]
 KEYS = ("tail_rows_velocity", "tail_rows_pressure", "spmv_group", "smooth_group",
-        "coarse_degree", "serial_launches", "persistent_precond")
-PERSISTENT = (0, 0, 0, 0, 0, 0, 1)
+        "coarse_degree", "serial_launches", "persistent_precond", "fine_degree")
+PERSISTENT = (0, 0, 0, 0, 0, 0, 1, 0)
 
 
 @pytest.fixture(scope="module")
@@ -108,11 +110,30 @@ def test_coarse_degree_two_reaches_the_same_solution(fs, prec):
     p = fs.FS_PREC_FP64 if prec == "fp64" else fs.FS_PREC_FP32_REFINE
     for wl in (W.channel(64, 16), W.cube(10, jitter=0.05)):
         make = lambda q: fs.Stepper.from_workload(wl, precision=q)
-        x3, i3 = _run(fs, make, (0, 0, 0, 0, 3, 0, 0), p, iters=True)
-        x2, i2 = _run(fs, make, (0, 0, 0, 0, 2, 0, 0), p, iters=True)
+        x3, i3 = _run(fs, make, (0, 0, 0, 0, 3, 0, 0, 0), p, iters=True)
+        x2, i2 = _run(fs, make, (0, 0, 0, 0, 2, 0, 0, 0), p, iters=True)
         print(wl.name, prec, "iterations per step, degree 3 / 2:", i3, i2)
         assert not np.array_equal(x2, x3)  # the knob reaches the V-cycle
         assert rel_l2(x2, x3) <= 1e-9
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_refine"])
+def test_fine_degree_two_reaches_the_same_solution(fs, prec):
+    """Degree 2 on the finest level of both hierarchies (the default) against
+    degree 3, per-pass and in the persistent form and in the fused cluster
+    tail when that covers every level: the solution agrees within the parity
+    bar, and the persistent and tail forms agree with the per-pass one."""
+    p = fs.FS_PREC_FP64 if prec == "fp64" else fs.FS_PREC_FP32_REFINE
+    for wl in (W.channel(64, 16), W.cube(10, jitter=0.05)):
+        make = lambda q: fs.Stepper.from_workload(wl, precision=q)
+        x3, i3 = _run(fs, make, (0, 0, 0, 0, 0, 0, 0, 3), p, iters=True)
+        x2, i2 = _run(fs, make, (0, 0, 0, 0, 0, 0, 0, 2), p, iters=True)
+        xp = _run(fs, make, (0, 0, 0, 0, 0, 0, 1, 2), p)
+        xt = _run(fs, make, (1 << 30, 1 << 30, 0, 0, 0, 0, 0, 2), p)
+        print(wl.name, prec, "iterations per step, finest degree 3 / 2:", i3, i2)
+        assert not np.array_equal(x2, x3)
+        assert rel_l2(x2, x3) <= 1e-9
+        assert rel_l2(xp, x2) <= TOL[prec] and rel_l2(xt, x2) <= TOL[prec]
 
 
 def test_autotune_installs_a_candidate(fs):
@@ -146,5 +167,7 @@ def test_autotune_installs_a_candidate(fs):
             fs.fs_set_schedule(S.prob, 0, 0, serial_launches=2)
         with pytest.raises(fs.FsError):
             fs.fs_set_schedule(S.prob, 0, 0, persistent_precond=2)
+        with pytest.raises(fs.FsError):
+            fs.fs_set_schedule(S.prob, 0, 0, fine_degree=1)
     finally:
         S.close()
