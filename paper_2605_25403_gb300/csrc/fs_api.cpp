@@ -616,10 +616,10 @@ void issue_precond(fs_problem* P, Precision<T>& pr, const DHier<T>& HA, const DH
                    cudaStream_t q) {
   if (P->sched.persistent_precond)
     launch_precond_flow<T>(pr.flow[flow_index(HA, HK)], pr.op, HA, pr.mplinv_nu,
-                           1.0 / P->desc.dt, P->pinned, P->npinned, r, z, pr.kr.work_p, st,
+                           1.0 / P->desc.dt, r, z, pr.kr.work_p, st,
                            pr.kr.st, skip, q);
   else
-    launch_precond<T>(pr.op, HA, HK, pr.mplinv_nu, 1.0 / P->desc.dt, P->pinned, P->npinned, r,
+    launch_precond<T>(pr.op, HA, HK, pr.mplinv_nu, 1.0 / P->desc.dt, r,
                       z, pr.kr.work_p, pr.kr.work_u, skip, q);
 }
 
@@ -1753,8 +1753,11 @@ int fs_problem_create_batch(fs_mesh* mesh, const fs_problem_desc* descs, int cou
       for (int32_t k = Kp.rowptr[q]; k < Kp.rowptr[q + 1]; ++k)
         if (fixed[q] || fixed[Kp.col[k]]) Kp.val[k] = (Kp.col[k] == q) ? 1.0 : 0.0;
   }
+  // nu over the lumped pressure mass; a pinned vertex is marked by -1 (its
+  // row of the preconditioner passes r_p through)
   std::vector<double> mplinv_nu(P->nv);
   for (int64_t q = 0; q < P->nv; ++q) mplinv_nu[q] = nu_vert[q] / mplh[q];
+  for (int32_t q : P->pinned_host) mplinv_nu[q] = -1.0;
   UnionHierarchy HA, HK;
   // coarsest size.  Large single problems stop coarsening at 3500 rows: the
   // dense inverse (on the device, ~0.1 s of set-up) then replaces the one or

@@ -326,10 +326,13 @@ template <typename A, typename B>
 void launch_convert(const A* in, B* out, int64_t n, const double* scale,
                     int inv, cudaStream_t s);
 
+// z = P^-1 r, the block preconditioner.  mpl_inv_nu: nu over the lumped
+// pressure mass per vertex, negative on the pinned vertices (their rows pass
+// r_p through).
 template <typename T>
 void launch_precond(const DOp<T>& op, const DHier<T>& HA, const DHier<T>& HK,
-                    const T* mpl_inv_nu, double inv_dt, const int32_t* pinned,
-                    int npinned, JVec<const T> r, JVec<T> z, T* work_p, T* work_u,
+                    const T* mpl_inv_nu, double inv_dt, JVec<const T> r, JVec<T> z,
+                    T* work_p, T* work_u,
                     const int* skip, cudaStream_t s);
 
 // ---- the block preconditioner as one persistent kernel (fs_linalg.cu) ----
@@ -385,8 +388,8 @@ void build_flow(const DHier<T>& HA, const DHier<T>& HK,
 // flag: segment states that receive bad = 2 on a timed-out wait, or null).
 template <typename T>
 void launch_precond_flow(const FlowDev& f, const DOp<T>& op, const DHier<T>& HA,
-                         const T* mpl_inv_nu, double inv_dt, const int32_t* pinned,
-                         int npinned, JVec<const T> r, JVec<T> z, T* work_p,
+                         const T* mpl_inv_nu, double inv_dt, JVec<const T> r, JVec<T> z,
+                         T* work_p,
                          const SegState* st, SegState* flag, const int* skip, cudaStream_t s);
 
 // ---- incremental pressure correction (fs_ipcs.cu) -----------------------

@@ -733,7 +733,7 @@ void launch_tail(const DHier<T>& H, int l0, JVec<T> out, int64_t out_ld, int nc,
 // are in place; the level's result ends in G1[l], or in `out` for level 0.
 template <typename T, int NCP>
 void vcycle_level(const DHier<T>& H, int l, JVec<T> out, int64_t out_ld, int nc,
-                  const int* skip, cudaStream_t s) {
+                  const int* skip, cudaStream_t s, bool first_done = false) {
   const bool top = l == 0;
   if (H.tail >= 0 && l == H.tail) {
     launch_tail<T, NCP>(H, l, top ? out : JVec<T>(), out_ld, nc, skip, s);
@@ -756,9 +756,11 @@ void vcycle_level(const DHier<T>& H, int l, JVec<T> out, int64_t out_ld, int nc,
     // degree 2 on a coarse level: one step after the restriction's first
     // (x2 in G1), the residual into the free D0, the correction into G1,
     // then the first post step and the last with the first step's
-    // coefficients (the result in G1, as the degree-3 cycle leaves it)
-    launch_mg<T, NCP>(MG_STEP, L, b, G0, D0, G1, D1, a1, b1, JVec<T>(), 0, nullptr, nc, skip,
-                      H.group, s);
+    // coefficients (the result in G1, as the degree-3 cycle leaves it);
+    // first_done: the caller's load already took the first of these steps
+    if (!first_done)
+      launch_mg<T, NCP>(MG_STEP, L, b, G0, D0, G1, D1, a1, b1, JVec<T>(), 0, nullptr, nc, skip,
+                        H.group, s);
     launch_mg<T, NCP>(MG_RESID, L, b, G1, D1, D0, nullptr, T(0), T(0), JVec<T>(), 0, nullptr,
                       nc, skip, H.group, s);
     launch_restrict<T, NCP>(L.R, D0, H.b[l + 1], H.G0[l + 1], H.D0[l + 1],
@@ -771,8 +773,9 @@ void vcycle_level(const DHier<T>& H, int l, JVec<T> out, int64_t out_ld, int nc,
                       out_ld, top ? H.perm : nullptr, nc, skip, H.group, s);
     return;
   }
-  launch_mg<T, NCP>(MG_STEP, L, b, G0, D0, G1, D1, a1, b1, JVec<T>(), 0, nullptr, nc, skip,
-                    H.group, s);
+  if (!first_done)
+    launch_mg<T, NCP>(MG_STEP, L, b, G0, D0, G1, D1, a1, b1, JVec<T>(), 0, nullptr, nc, skip,
+                      H.group, s);
   launch_mg<T, NCP>(MG_STEP, L, b, G1, D1, G0, D0, a2, b2, JVec<T>(), 0, nullptr, nc, skip,
                     H.group, s);
   // residual of x3 = G0 into G1; G0 keeps x3 for the correction
@@ -841,66 +844,108 @@ __global__ void k_mg_load1(int64_t n, JVec<const T> rv,
   }
 }
 
-// z_p = nu Mp^-1 r_p + dt^-1 y_K ; then pinned rows: z_p = r_p
-template <typename T>
-__global__ void k_prec_p(int64_t nv, JVec<const T> rpv, const T* __restrict__ yk,
-                         const T* __restrict__ mpl_inv_nu, T inv_dt, JVec<T> zpv,
-                         const int* skip) {
+// The load of a single-component level 0 whose rows are in the caller's
+// order, fused with its first Chebyshev step: the load's first step from
+// x = 0 (G0 = D0 = D^-1 r / theta, b = r) is formed on the fly at every
+// neighbour instead of being stored and read back, so the pass reads r and
+// D^-1 at the neighbours and writes b, G1 and D1 (the same values, in the
+// same order of operations, as k_mg_load1 followed by the STEP pass).
+template <typename T, int G>
+__global__ void __launch_bounds__(256) k_mg_first1(DSell<T> A, const T* __restrict__ dinv,
+                                                   JVec<const T> rv, T inv_theta, T alpha,
+                                                   T beta, T* __restrict__ b,
+                                                   T* __restrict__ Gout, T* __restrict__ Dout,
+                                                   SegSkip sk, const int* skip) {
   pdl_wait();
   if (skip && *skip) return;
-  const T* __restrict__ rp = rpv.get();
-  T* __restrict__ zp = zpv.get();
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nv;
-       q += (int64_t)gridDim.x * blockDim.x)
-    zp[q] = mpl_inv_nu[q] * rp[q] + inv_dt * yk[q];
-}
-template <typename T>
-__global__ void k_pin_rows(const int32_t* __restrict__ pinned, int npinned, JVec<const T> rpv,
-                           JVec<T> zpv, const int* skip) {
-  pdl_wait();
-  if (skip && *skip) return;
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < npinned) zpv.get()[pinned[t]] = rpv.get()[pinned[t]];
+  const int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (row >= A.nrow || seg_skipped(sk, row)) return;
+  const T* __restrict__ r = rv.get();
+  const int64_t sl = row >> 5;
+  const int64_t o0 = (A.width ? sl * 32 * A.width : A.off[sl]) + (row & 31);
+  const int64_t o1 = A.width ? (sl + 1) * 32 * A.width : A.off[sl + 1];
+  T acc = T(0);
+  for (int64_t o = o0; o < o1; o += G * 32) {
+    T a[G];
+    int32_t j[G];
+#pragma unroll
+    for (int u = 0; u < G; ++u) {
+      const int64_t oo = o + u * 32;
+      const bool ok = oo < o1;
+      a[u] = ok ? A.v[oo] : T(0);
+      j[u] = ok ? A.ci[oo] : (int32_t)row;
+    }
+    T g[G];
+#pragma unroll
+    for (int u = 0; u < G; ++u) g[u] = dinv[j[u]] * r[j[u]] * inv_theta;
+#pragma unroll
+    for (int u = 0; u < G; ++u) acc += a[u] * g[u];
+  }
+  const T v = r[row], di = dinv[row];
+  const T g0 = di * v * inv_theta;
+  const T d = alpha * g0 + beta * di * (v - acc);
+  b[row] = v;
+  Gout[row] = g0 + d;
+  Dout[row] = d;
 }
 
-// Velocity right-hand side of the V-cycle, written straight into level 0:
-// t_c = r_c + BT_c z_p over the velocity rows (caller order), stored at the
-// level-0 (block-order) row iperm[i] as b0, with the first step from x = 0,
-// G0 = D0 = D^-1 t / theta.
+// The Cahouet-Chabard combination and the velocity right-hand side of the
+// V-cycle in one pass.  Threads [0, nvp) (nv rounded up to a warp) write the
+// pressure part of the result, z_p = nu Mp^-1 r_p + dt^-1 y_K (y_K the
+// pressure V-cycle's output), or z_p = r_p on a pinned row, which the
+// scaling vector marks with a negative entry.  The following threads take
+// the velocity rows (caller order): t_c = r_c + BT_c z_p, with z_p at each
+// BT column evaluated from the same formula instead of being read back, stored
+// at the level-0 (block-order) row iperm[i] as b0, with the first step from
+// x = 0, G0 = D0 = D^-1 t / theta.
+template <typename T>
+__device__ __forceinline__ T cc_combine(const T* __restrict__ mpl, const T* __restrict__ rp,
+                                        const T* __restrict__ yk, T inv_dt, int64_t q) {
+  const T m = mpl[q], p = rp[q];
+  return m < T(0) ? p : m * p + inv_dt * yk[q];
+}
+
 template <typename T, int DIM, int NCP>
-__global__ void __launch_bounds__(256) k_bt_add_mg(DSell<T> BT, int64_t n2, JVec<const T> rv,
-                                                   JVec<const T> zpv,
-                                                   const int32_t* __restrict__ iperm,
+__global__ void __launch_bounds__(256) k_bt_add_mg(DSell<T> BT, int64_t n2, int64_t nv,
+                                                   JVec<const T> rv, const T* __restrict__ yk,
+                                                   const T* __restrict__ mpl, T inv_dt,
+                                                   JVec<T> zv, const int32_t* __restrict__ iperm,
                                                    const T* __restrict__ dinv0, T inv_theta0,
                                                    T* __restrict__ b0, T* __restrict__ G0,
                                                    T* __restrict__ D0, SegSkip sk0,
                                                    const int* skip) {
   pdl_wait();
   if (skip && *skip) return;
-  const int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const T* __restrict__ r = rv.get();
+  const T* __restrict__ rp = r + DIM * n2;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t nvp = (nv + 31) & ~(int64_t)31;
+  if (t < nvp) {
+    if (t < nv) zv.get()[DIM * n2 + t] = cc_combine(mpl, rp, yk, inv_dt, t);
+    return;
+  }
+  const int64_t row = t - nvp;
   if (row >= n2) return;
   const int64_t dst = iperm ? iperm[row] : row;
   if (seg_skipped(sk0, dst)) return;
-  const T* __restrict__ r = rv.get();
-  const T* __restrict__ zp = zpv.get();
   T acc[DIM];
 #pragma unroll
   for (int c = 0; c < DIM; ++c) acc[c] = T(0);
   const int64_t o1 = BT.off[(row >> 5) + 1];
   for (int64_t o = BT.off[row >> 5] + (row & 31); o < o1; o += 32) {
     const int64_t base = (o - (row & 31)) * DIM + (row & 31);
-    const T p = zp[BT.ci[o]];
+    const T p = cc_combine(mpl, rp, yk, inv_dt, BT.ci[o]);
 #pragma unroll
     for (int c = 0; c < DIM; ++c) acc[c] += BT.v[base + 32 * c] * p;
   }
-  T t[NCP], d0[NCP];
-  const T s = dinv0 ? dinv0[dst] * inv_theta0 : T(0);
+  T tv[NCP], d0[NCP];
+  const T sc = dinv0 ? dinv0[dst] * inv_theta0 : T(0);
 #pragma unroll
   for (int c = 0; c < NCP; ++c) {
-    t[c] = c < DIM ? r[c * n2 + row] + acc[c] : T(0);
-    d0[c] = s * t[c];
+    tv[c] = c < DIM ? r[c * n2 + row] + acc[c] : T(0);
+    d0[c] = sc * tv[c];
   }
-  vstore<T, NCP>(b0 + dst * NCP, t);
+  vstore<T, NCP>(b0 + dst * NCP, tv);
   vstore<T, NCP>(G0 + dst * NCP, d0);
   vstore<T, NCP>(D0 + dst * NCP, d0);
 }
@@ -1069,54 +1114,63 @@ template void launch_cheb_step<float>(const DHier<float>&, int, cudaStream_t);
 
 template <typename T>
 void launch_precond(const DOp<T>& op, const DHier<T>& HA, const DHier<T>& HK,
-                    const T* mpl_inv_nu, double inv_dt, const int32_t* pinned,
-                    int npinned, JVec<const T> r, JVec<T> z, T* work_p, T* work_u,
+                    const T* mpl_inv_nu, double inv_dt, JVec<const T> r, JVec<T> z,
+                    T* work_p, T* work_u,
                     const int* skip, cudaStream_t s) {
   (void)work_u;
   const int64_t n2 = op.n2, nv = op.nv;
   const int dim = op.dim;
   const JVec<const T> rp = r.shifted(dim * n2);
-  const JVec<T> zp = z.shifted(dim * n2);
-  const JVec<const T> zpc(zp.base, zp.j, zp.stride);
-  // pressure: Cahouet-Chabard  z_p = nu Mp^-1 r_p + dt^-1 Kp^-1 r_p
+  // pressure: Cahouet-Chabard  z_p = nu Mp^-1 r_p + dt^-1 Kp^-1 r_p; the
+  // load and the first smoothing step in one pass when level 0 is smoothed
+  // by the per-pass kernels and its rows are in the caller's order
   {
     const bool k1 = HK.nlev > 1;
-    launch_k(k_mg_load1<T>, grid_stride_blocks(nv), 256, 0, s,
-        nv, rp, HK.iperm, k1 ? HK.lev[0].dinv : nullptr, (T)HK.lev[0].inv_theta, HK.b[0], HK.G0[0],
-        HK.D0[0], skip);
-    count_launches(1);
-    vcycle_level<T, 1>(HK, 0, JVec<T>(work_p), nv, 1, skip, s);
+    const DLevel<T>& L0 = HK.lev[0];
+    if (k1 && HK.tail != 0 && !HK.perm) {
+      if (HK.group == 6)
+        launch_k(k_mg_first1<T, 6>, blocks_for(nv), 256, 0, s, L0.A, L0.dinv, rp,
+                 (T)L0.inv_theta, (T)L0.a1, (T)L0.b1, HK.b[0], HK.G1[0], HK.D1[0], L0.skip, skip);
+      else
+        launch_k(k_mg_first1<T, 4>, blocks_for(nv), 256, 0, s, L0.A, L0.dinv, rp,
+                 (T)L0.inv_theta, (T)L0.a1, (T)L0.b1, HK.b[0], HK.G1[0], HK.D1[0], L0.skip, skip);
+      count_launches(1);
+      vcycle_level<T, 1>(HK, 0, JVec<T>(work_p), nv, 1, skip, s, /*first_done=*/true);
+    } else {
+      launch_k(k_mg_load1<T>, grid_stride_blocks(nv), 256, 0, s, nv, rp, HK.iperm,
+               k1 ? L0.dinv : nullptr, (T)L0.inv_theta, HK.b[0], HK.G0[0], HK.D0[0], skip);
+      count_launches(1);
+      vcycle_level<T, 1>(HK, 0, JVec<T>(work_p), nv, 1, skip, s);
+    }
   }
-  launch_k(k_prec_p<T>, grid_stride_blocks(nv), 256, 0, s, nv, rp, work_p, mpl_inv_nu, (T)inv_dt, zp,
-                                                     skip);
-  count_launches(1);
-  if (npinned > 0) {
-    launch_k(k_pin_rows<T>, blocks_for(npinned), 256, 0, s, pinned, npinned, rp, zp, skip);
-    count_launches(1);
-  }
-  // velocity: z_u = A^-1 (r_u + BT z_p) by one V-cycle on all components
+  // z_p and the velocity right-hand side in one pass (pinned rows are
+  // marked in mpl_inv_nu), then z_u = A^-1 (r_u + BT z_p) by one V-cycle
+  // on all components
   const bool a1 = HA.nlev > 1;
   const T* d0 = a1 ? HA.lev[0].dinv : nullptr;
   const T it0 = (T)HA.lev[0].inv_theta;
+  const unsigned nb = blocks_for(((nv + 31) & ~(int64_t)31) + n2);
   if (dim == 2) {
-    launch_k(k_bt_add_mg<T, 2, 2>, blocks_for(n2), 256, 0, s, op.BT, n2, r, zpc, HA.iperm, d0,
-             it0, HA.b[0], HA.G0[0], HA.D0[0], HA.lev[0].skip, skip);
+    launch_k(k_bt_add_mg<T, 2, 2>, nb, 256, 0, s, op.BT, n2, nv, r, (const T*)work_p,
+             mpl_inv_nu, (T)inv_dt, z, HA.iperm, d0, it0, HA.b[0], HA.G0[0], HA.D0[0],
+             HA.lev[0].skip, skip);
     count_launches(1);
     vcycle_level<T, 2>(HA, 0, z, n2, 2, skip, s);
   } else {
-    launch_k(k_bt_add_mg<T, 3, 4>, blocks_for(n2), 256, 0, s, op.BT, n2, r, zpc, HA.iperm, d0,
-             it0, HA.b[0], HA.G0[0], HA.D0[0], HA.lev[0].skip, skip);
+    launch_k(k_bt_add_mg<T, 3, 4>, nb, 256, 0, s, op.BT, n2, nv, r, (const T*)work_p,
+             mpl_inv_nu, (T)inv_dt, z, HA.iperm, d0, it0, HA.b[0], HA.G0[0], HA.D0[0],
+             HA.lev[0].skip, skip);
     count_launches(1);
     vcycle_level<T, 4>(HA, 0, z, n2, 3, skip, s);
   }
 }
 template void launch_precond<double>(const DOp<double>&, const DHier<double>&,
                                      const DHier<double>&, const double*, double,
-                                     const int32_t*, int, JVec<const double>, JVec<double>,
+                                     JVec<const double>, JVec<double>,
                                      double*, double*, const int*, cudaStream_t);
 template void launch_precond<float>(const DOp<float>&, const DHier<float>&,
                                     const DHier<float>&, const float*, double,
-                                    const int32_t*, int, JVec<const float>, JVec<float>, float*,
+                                    JVec<const float>, JVec<float>, float*,
                                     float*, const int*, cudaStream_t);
 
 // ---------------------------------------------------------------------------
@@ -1162,8 +1216,6 @@ struct FlowArgs {
   T* work_p;
   const T* mpl;
   T inv_dt;
-  const int32_t* pinned;
-  int npinned;
   int64_t n2, nv;
   int dim;
   const SegState* st;
@@ -1285,17 +1337,12 @@ __device__ __forceinline__ void flow_item(const FlowArgs<T>& a, const FlowPhase<
       break;
     }
     case FL_PREC_P: {
-      // caller pressure rows: z_p = nu Mp^-1 r_p + dt^-1 y_K, then z_p = r_p
-      // on the pinned rows of the range
+      // caller pressure rows: z_p = nu Mp^-1 r_p + dt^-1 y_K (r_p on the
+      // pinned rows, marked in the scaling vector)
       const T* __restrict__ rp = a.r.get() + vel;
       T* __restrict__ zp = a.z.get() + vel;
       for (int64_t q = r0 + threadIdx.x; q < r1; q += kFlowThreads)
-        zp[q] = a.mpl[q] * rp[q] + a.inv_dt * a.work_p[q];
-      __syncthreads();
-      for (int i = threadIdx.x; i < a.npinned; i += kFlowThreads) {
-        const int64_t q = a.pinned[i];
-        if (q >= r0 && q < r1) zp[q] = rp[q];
-      }
+        zp[q] = cc_combine(a.mpl, rp, a.work_p, a.inv_dt, q);
       break;
     }
     default: {  // FL_BT_ADD over level-0 rows of the velocity hierarchy
@@ -1572,8 +1619,8 @@ template void build_flow<float>(const DHier<float>&, const DHier<float>&,
 
 template <typename T>
 void launch_precond_flow(const FlowDev& f, const DOp<T>& op, const DHier<T>& HA,
-                         const T* mpl_inv_nu, double inv_dt, const int32_t* pinned,
-                         int npinned, JVec<const T> r, JVec<T> z, T* work_p,
+                         const T* mpl_inv_nu, double inv_dt, JVec<const T> r, JVec<T> z,
+                         T* work_p,
                          const SegState* st, SegState* flag, const int* skip, cudaStream_t s) {
   FlowArgs<T> a;
   a.f = f;
@@ -1583,8 +1630,6 @@ void launch_precond_flow(const FlowDev& f, const DOp<T>& op, const DHier<T>& HA,
   a.work_p = work_p;
   a.mpl = mpl_inv_nu;
   a.inv_dt = (T)inv_dt;
-  a.pinned = pinned;
-  a.npinned = npinned;
   a.n2 = op.n2;
   a.nv = op.nv;
   a.dim = op.dim;
@@ -1606,11 +1651,11 @@ void launch_precond_flow(const FlowDev& f, const DOp<T>& op, const DHier<T>& HA,
 }
 template void launch_precond_flow<double>(const FlowDev&, const DOp<double>&,
                                           const DHier<double>&, const double*, double,
-                                          const int32_t*, int, JVec<const double>,
+                                          JVec<const double>,
                                           JVec<double>, double*, const SegState*, SegState*,
                                           const int*, cudaStream_t);
 template void launch_precond_flow<float>(const FlowDev&, const DOp<float>&, const DHier<float>&,
-                                         const float*, double, const int32_t*, int,
+                                         const float*, double,
                                          JVec<const float>, JVec<float>, float*,
                                          const SegState*, SegState*, const int*, cudaStream_t);
 
