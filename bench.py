@@ -58,7 +58,9 @@ def parse(argv=None):
                    help="launch the solver's kernels one by one instead of replaying captured "
                         "CUDA graphs (for per-kernel profilers, which cannot see kernels inside "
                         "graphs with conditional nodes)")
-    p.add_argument("--roofline-kernel", default="cheb", choices=sorted(KERNELS))
+    p.add_argument("--roofline-kernel", default="cgs_upd", choices=sorted(KERNELS),
+                   help="kernel of the roofline line: the largest single kernel of the "
+                        "channel step's ncu launch list (the CGS2 update pass)")
     p.add_argument("--batch-steps", type=int, default=20,
                    help="timed steps of the 96-instance batched workload (0: skip)")
     p.add_argument("--cube-steps", type=int, default=10,
