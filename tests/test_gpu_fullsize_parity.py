@@ -99,3 +99,30 @@ def test_batch_hard_corner_vs_oracle(fs, prec):
                 assert e <= 1e-9, (i, k, e)
     finally:
         B.close()
+
+
+def test_batch_n256_re2000_vs_oracle(fs):
+    """The extreme corner of the batched workload, N = 256 (592,387 DOF) at
+    Re = 2000, inside a batch beside a small viscous instance: one step of
+    both precisions against the oracle's sparse direct solve of the same
+    step (about a minute on one core)."""
+    wls = [W.unit_square(256, nu=1 / 2000.0, dt=1e-3, jitter=0.0),
+           W.unit_square(16, nu=1.0, dt=1e-3, jitter=0.0)]
+    Bs = {p: fs.Stepper.from_workloads(wls, precision=p) for p in (1, 0)}
+    try:
+        Ps = [oracle_problem(w) for w in wls]
+        for P in Ps:
+            P.step(method="lu")
+        for p, B in Bs.items():
+            fs.fs_step(B.prob, 1)
+            stats = fs.fs_instance_stats(B.prob)
+            assert all(s["status"] == 0 and s["rel_res"] <= 1e-12 for s in stats), (p, stats)
+            xb, _ = B.state()
+            for i, P in enumerate(Ps):
+                e = rel_l2(B.instance_state(xb, i), P.x)
+                print(f"precision {p} instance {i} ({wls[i].name}): rel L2 {e:.2e}, "
+                      f"{stats[i]['iters']} iterations")
+                assert e <= 1e-9, (p, i, e)
+    finally:
+        for B in Bs.values():
+            B.close()
