@@ -51,6 +51,12 @@ def parse(argv=None):
     p.add_argument("--fine-degree", type=int, default=0, choices=[0, 2, 3],
                    help="Chebyshev degree on the finest multigrid level (0: the library "
                         "default, 2)")
+    p.add_argument("--smoother-ratios", default="4,6,8,12,16",
+                   help="candidate Chebyshev interval ratios fs_autotune_smoother times at "
+                        "set-up on every workload ('' keeps the library default, 8)")
+    p.add_argument("--smoother-steps", type=int, default=5,
+                   help="steps the smoother autotuner times per candidate (channel; the "
+                        "cube and the batch take 3)")
     p.add_argument("--serial-launches", type=int, default=0, choices=[0, 1],
                    help="1: plain serialised kernel launches instead of programmatic dependent "
                         "launches (the library default)")
@@ -67,7 +73,7 @@ def parse(argv=None):
                    help="timed FP32+refinement steps of the cube 48^3 (0: skip)")
     p.add_argument("--cube-fp64-steps", type=int, default=5,
                    help="timed FP64 steps of the cube 48^3")
-    p.add_argument("--serve-requests", type=int, default=48,
+    p.add_argument("--serve-requests", type=int, default=96,
                    help="requests of each serving run (0: skip)")
     p.add_argument("--serve-rate", type=float, default=200.0,
                    help="mean arrival rate of the saturation run (requests/s)")
@@ -90,6 +96,19 @@ KERNELS = {
     "cgs_upd": ("FS_KERNEL_CGS_UPD", "k_seg_upd (CGS2 update w -= V h, re-dot, norm; j = 15)"),
     "cgs_fin": ("FS_KERNEL_CGS_FIN", "k_seg_fin (CGS2 final update and normalisation; j = 15)"),
 }
+
+
+def tune_smoother(fs, S, ratios, nsteps):
+    """Set-up, untimed: the smoother's Chebyshev interval, picked by timing
+    `nsteps` steps from the problem's current state under each candidate
+    (the library restores the state afterwards)."""
+    if not ratios:
+        return None
+    return fs.fs_autotune_smoother(S.prob, nsteps=nsteps, ratios=ratios)
+
+
+def parse_ratios(text):
+    return tuple(int(q) for q in text.split(",") if q.strip())
 
 
 def workload(name):
@@ -235,7 +254,7 @@ def aggregate_time(total_s, dist):
 
 
 # ---------------------------------------------------------------------------
-def batched_run(torch, fs, steps, warmup=3, opts=None):
+def batched_run(torch, fs, steps, warmup=3, opts=None, ratios=()):
     """The batched workload: 96 unit-square instances, N and Re drawn
     log-uniform from the seed, one problem over their union (one launch per
     phase for all instances), FP32 inner / FP64 refinement."""
@@ -247,6 +266,7 @@ def batched_run(torch, fs, steps, warmup=3, opts=None):
     setup_s = time.perf_counter() - t0
     try:
         tune = fs.fs_autotune(B.prob, reps=3)
+        smoother = tune_smoother(fs, B, ratios, 3)
         for _ in range(warmup):
             fs.fs_step(B.prob, 1, opts)
         torch.cuda.synchronize()
@@ -270,7 +290,7 @@ def batched_run(torch, fs, steps, warmup=3, opts=None):
                         "dt 1e-3, seed 0", "instances": len(wls), "ndof_total": ndof,
             "ms_per_step": 1e3 * per_step, "steps_per_s": 1.0 / per_step,
             "instance_steps_per_s": len(wls) / per_step, "dof_per_s": ndof / per_step,
-            "setup_s": setup_s, "timed_steps": steps, "schedule": tune,
+            "setup_s": setup_s, "timed_steps": steps, "schedule": tune, "smoother": smoother,
             "iters_max": max(x["iters"] for x in st),
             "iters_median": float(np.median([x["iters"] for x in st])),
             "status_ok": all(x["status"] == 0 for x in st),
@@ -398,7 +418,7 @@ def picard_block(fs, n=64):
             "rel_res": st["rel_res"]}
 
 
-def cube_block(torch, fs, stream, flush, steps, steps64, warmup=3):
+def cube_block(torch, fs, stream, flush, steps, steps64, warmup=3, ratios=()):
     """The cube 48^3 (2,855,668 DOF): FP32+refinement and FP64 steps/s, the
     per-step difference between the two paths' states, and the L2-cold
     fractions of its SpMV and smoothing step (working sets above the L2)."""
@@ -412,6 +432,7 @@ def cube_block(torch, fs, stream, flush, steps, steps64, warmup=3):
         S = fs.Stepper.from_workload(wl, precision=prec, stream=stream.cuda_stream)
         try:
             fs.fs_autotune(S.prob, reps=3)
+            smoother = tune_smoother(fs, S, ratios, 3)
             xs = []
             for _ in range(warmup):
                 fs.fs_step(S.prob, 1)
@@ -421,7 +442,7 @@ def cube_block(torch, fs, stream, flush, steps, steps64, warmup=3):
             res[name] = {"steps_per_s": 1e3 * len(t) / sum(t), "ms_per_step": sum(t) / len(t),
                          "timed_steps": k, "dof_per_s": 1e3 * len(t) * wl.ndof / sum(t),
                          "iters_per_step": float(np.mean([q["iters"] for q in st])),
-                         "rel_res_max": max(q["rel_res"] for q in st)}
+                         "rel_res_max": max(q["rel_res"] for q in st), "smoother": smoother}
             states[name] = xs
             if prec == fs.FS_PREC_FP32_REFINE:
                 peak, kind = measured_peak_hbm()
@@ -493,6 +514,7 @@ def main():
     from paper_2605_25403_gb300 import fs
 
     wl = workload(args.workload)
+    ratios = parse_ratios(args.smoother_ratios)
     prec = fs.FS_PREC_FP32_REFINE if args.precision == "fp32_refine" else fs.FS_PREC_FP64
     stream = torch.cuda.Stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
@@ -505,6 +527,7 @@ def main():
         fs.fs_set_schedule(S64.prob, 0, 0, 0, 0, args.coarse_degree, args.serial_launches,
                            fine_degree=args.fine_degree)
         tune64 = fs.fs_autotune(S64.prob, reps=5)
+        smooth64 = tune_smoother(fs, S64, ratios, args.smoother_steps)
         for _ in range(args.warmup):
             fs.fs_step(S64.prob, 1)
         t64, st64 = time_steps(torch, fs, S64, stream, k64, flush)
@@ -515,7 +538,8 @@ def main():
                 "iters_per_step": float(np.mean([s["iters"] for s in st64])),
                 "iters_max": int(max(s["iters"] for s in st64)),
                 "cycles_per_step": float(np.mean([s["cycles"] for s in st64])),
-                "rel_res_max": max(s["rel_res"] for s in st64), "schedule": tune64}
+                "rel_res_max": max(s["rel_res"] for s in st64), "schedule": tune64,
+                "smoother": smooth64}
         S64.close()
 
     # ---- the timed path ----------------------------------------------------
@@ -528,6 +552,7 @@ def main():
     else:
         fs.fs_set_schedule(S.prob, *(int(q) for q in args.schedule.split(",")))
         tune = {"fixed": fs.fs_get_schedule(S.prob)}
+    smoother = tune_smoother(fs, S, ratios, args.smoother_steps)
     for _ in range(args.warmup):
         fs.fs_step(S.prob, 1)
     sampler = ClockSampler(local)
@@ -560,7 +585,7 @@ def main():
     fs.fs_set_schedule(SE.prob, sched["tail_rows_velocity"], sched["tail_rows_pressure"],
                        sched["spmv_group"], sched["smooth_group"], sched["coarse_degree"],
                        sched["serial_launches"], sched["persistent_precond"],
-                       sched["fine_degree"])
+                       sched["fine_degree"], sched["cheb_ratio"])
     for _ in range(max(0, args.warmup - 1)):
         fs.fs_step(SE.prob, 1)
     xh = torch.empty(ndof, dtype=torch.float64).pin_memory()
@@ -635,9 +660,10 @@ def main():
         except Exception as e:  # noqa: BLE001 - recorded in the JSON line
             return {"error": f"{type(e).__name__}: {e}"}
 
-    batch = block(args.batch_steps > 0, batched_run, torch, fs, args.batch_steps, 3, opts)
+    batch = block(args.batch_steps > 0, batched_run, torch, fs, args.batch_steps, 3, opts,
+                  ratios)
     cube = block(args.cube_steps > 0, cube_block, torch, fs, stream, flush, args.cube_steps,
-                 args.cube_fp64_steps)
+                 args.cube_fp64_steps, 3, ratios)
     serving = block(args.serve_requests > 0, serving_block, fs, args.serve_requests,
                     args.serve_rate)
     ipcs = block(args.ipcs_steps > 0, ipcs_block, torch, fs, stream, flush, args.ipcs_steps)
@@ -672,7 +698,7 @@ def main():
                 "d2h_bytes_per_step": 8 * ndof},
         "e2e_iters_per_step": float(np.mean(e2e_iters)),
         "gpu_launches": launches,
-        "schedule": tune,
+        "schedule": tune, "smoother": smoother,
         "roofline": roofline,
         "kernels": kernels,
         "cpu_baseline": cpu,

@@ -251,10 +251,11 @@ int fs_solve(fs_problem* prob, const fs_solve_opts* opts, double* x,
              fs_solve_stats* stats);
 
 /* nsteps backward-Euler Oseen steps: assemble (w = u^n), solve, t += dt.
- * Each solve starts from the extrapolation in time of the latest states:
- * 3 x^n - 3 x^(n-1) + x^(n-2), or 2 x^n - x^(n-1) and x^n while fewer
- * previous states are known (after problem creation, fs_solve, or
- * fs_set_state to a time other than the current one); the converged state
+ * Each solve starts from the polynomial extrapolation in time through x^n
+ * and up to four previous states (5 x^n - 10 x^(n-1) + 10 x^(n-2)
+ * - 5 x^(n-3) + x^(n-4) once they are known, lower orders before, and x^n
+ * after problem creation, fs_solve, or fs_set_state to a time other than
+ * the current one); the converged state
  * does not depend on the starting point beyond the solver tolerance.
  * per_step (host, nsteps entries, may be NULL) receives each solve's stats.
  * Synchronises. */
@@ -490,6 +491,12 @@ typedef struct {
                             preconditioner (iteration counts, not the
                             solution beyond rtol); the autotuner keeps the
                             value in place                              */
+  int32_t cheb_ratio;    /* the Chebyshev smoother targets the interval
+                            [1.1 lmax / cheb_ratio, 1.1 lmax] of D^-1 A on
+                            every level (lmax estimated at set-up): 2 to
+                            64; 0 = 8.  It changes the preconditioner like
+                            the degrees; fs_autotune_smoother picks it by
+                            timing steps                                */
 } fs_schedule;
 typedef struct {
   int candidates;        /* schedules timed                                  */
@@ -505,6 +512,21 @@ typedef struct {
 int fs_get_schedule(const fs_problem* prob, fs_schedule* out);
 int fs_set_schedule(fs_problem* prob, const fs_schedule* sched);
 int fs_autotune(fs_problem* prob, int reps, fs_tune_report* report);
+/* Picks the Chebyshev interval of the smoother (fs_schedule.cheb_ratio) by
+ * timing steps: for each of the nratios candidate ratios (2 to 64) the
+ * problem's state is put back to the one at the call, one untimed step
+ * captures the solver's graphs, the state is put back again and nsteps
+ * steps are timed with CUDA events on the problem's stream.  The fastest
+ * ratio is installed and the state at the call is restored, with no step
+ * history (the next solves start as after fs_set_state at another time).
+ * ms_out / iters_out (host, nratios entries, may be NULL) receive each
+ * candidate's mean time and inner iterations per step; best_out (may be
+ * NULL) the installed ratio.  No counterpart in the paper (its solver is a
+ * library call).  FS_ERR_UNSUPPORTED for P3/P2 problems, FS_ERR_BUSY while
+ * a step is in progress, the first failing step's status otherwise (the
+ * state is restored and the schedule left as it was).  Synchronises. */
+int fs_autotune_smoother(fs_problem* prob, int nsteps, const int32_t* ratios, int nratios,
+                         double* ms_out, double* iters_out, int32_t* best_out);
 
 /* Instrumentation (no counterpart in the paper).
  * fs_launch_count: kernels launched by this library since load, counting

@@ -114,6 +114,8 @@ struct Precision {
   std::vector<std::vector<int64_t>> offA, offK;
   std::vector<int64_t> prow;
   FlowDev flow[8];
+  int flow_ratio[8] = {};  // the Chebyshev interval ratio each work-list holds
+  int cheb_ratio = 8;      // the hierarchies' current Chebyshev interval ratio
 };
 
 // The work-list built for the hierarchies' current smoothing degrees.
@@ -218,7 +220,7 @@ struct fs_problem {
   std::vector<fs_solve_stats> last_stats;  // per instance, last solve
   double t = 0;
   bool assembled = false;
-  fs_schedule sched{0, 0, 0, 0, 0, 0, 0, 0};
+  fs_schedule sched{0, 0, 0, 0, 0, 0, 0, 0, 0};
 
   TileList tl() const { return TileList{tiles, ntiles}; }
 
@@ -370,8 +372,9 @@ int upload_sell(fs_problem* P, const HostCsr& H, DSell<T>& d, double uniform_sla
 
 // Chebyshev(3) coefficients on [lmax/8, 1.1 lmax] of D^-1 A.
 template <typename T>
-void cheb_coeffs(double lmax, DLevel<T>& L) {
-  double hi = 1.1 * lmax, lo = hi / 8.0;
+void cheb_coeffs(double lmax, DLevel<T>& L, double ratio = 8.0) {
+  double hi = 1.1 * lmax, lo = hi / ratio;
+  L.lmax = lmax;
   double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo);
   double sigma = theta / delta;
   double rho0 = 1.0 / sigma;
@@ -549,6 +552,12 @@ void apply_groups(fs_problem* P, Precision<T>& pr, const fs_schedule& sc) {
   pr.HA.group = pr.HK.group = sc.smooth_group ? sc.smooth_group : 4;
   pr.HA.coarse_deg = pr.HK.coarse_deg = sc.coarse_degree == 3 ? 3 : 2;
   pr.HA.fine_deg = pr.HK.fine_deg = sc.fine_degree == 3 ? 3 : 2;
+  const int ratio = sc.cheb_ratio ? sc.cheb_ratio : 8;
+  if (ratio != pr.cheb_ratio) {
+    for (DHier<T>* H : {&pr.HA, &pr.HK})
+      for (int l = 0; l < H->nlev; ++l) cheb_coeffs<T>(H->lev[l].lmax, H->lev[l], ratio);
+    pr.cheb_ratio = ratio;
+  }
 }
 
 // The fused cluster kernel takes the levels with at most tail_rows rows
@@ -574,8 +583,13 @@ int apply_tail(fs_problem* P, DHier<T>& D, int64_t tail_rows) {
 // coarse smoothing degree (built and uploaded on first use).
 template <typename T>
 int apply_flow(fs_problem* P, Precision<T>& pr) {
-  FlowDev& f = pr.flow[flow_index(pr.HA, pr.HK)];
-  if (f.items) return FS_OK;
+  const int idx = flow_index(pr.HA, pr.HK);
+  FlowDev& f = pr.flow[idx];
+  // a work-list holds the smoothing coefficients it was built with: one
+  // built for another interval is replaced (its buffers stay with the
+  // problem until it is destroyed)
+  if (f.items && pr.flow_ratio[idx] == pr.cheb_ratio) return FS_OK;
+  pr.flow_ratio[idx] = pr.cheb_ratio;
   const int nb = flow_blocks<T>(pr.HA.ncp);
   if (nb <= 0) {
     set_error("persistent preconditioner: its kernel cannot be resident on this device");
@@ -2626,7 +2640,8 @@ int fs_set_schedule(fs_problem* P, const fs_schedule* sc) {
   if (!P || !sc || sc->tail_rows_velocity < 0 || sc->tail_rows_pressure < 0 ||
       !in(sc->spmv_group, {0, 4, 6, 8}) || !in(sc->smooth_group, {0, 4, 6}) ||
       !in(sc->coarse_degree, {0, 2, 3}) || !in(sc->serial_launches, {0, 1}) ||
-      !in(sc->persistent_precond, {0, 1}) || !in(sc->fine_degree, {0, 2, 3})) {
+      !in(sc->persistent_precond, {0, 1}) || !in(sc->fine_degree, {0, 2, 3}) ||
+      (sc->cheb_ratio != 0 && (sc->cheb_ratio < 2 || sc->cheb_ratio > 64))) {
     set_error("fs_set_schedule: bad argument");
     return FS_ERR_INVALID_ARG;
   }
@@ -2734,6 +2749,90 @@ int fs_autotune(fs_problem* P, int reps, fs_tune_report* report) {
   }
   FS_TRY(install_schedule(P, r.best));
   if (report) *report = r;
+  return FS_OK;
+}
+
+int fs_autotune_smoother(fs_problem* P, int nsteps, const int32_t* ratios, int nratios,
+                         double* ms_out, double* iters_out, int32_t* best_out) {
+  if (P && P->p3) {
+    set_error("fs_autotune_smoother: P3/P2 problems are stepped by fs_step_ipcs");
+    return FS_ERR_UNSUPPORTED;
+  }
+  if (!P || nsteps < 1 || !ratios || nratios < 1 || nratios > 64) {
+    set_error("fs_autotune_smoother: bad argument");
+    return FS_ERR_INVALID_ARG;
+  }
+  for (int q = 0; q < nratios; ++q)
+    if (ratios[q] < 2 || ratios[q] > 64) {
+      set_error("fs_autotune_smoother: interval ratios must lie in [2, 64]");
+      return FS_ERR_INVALID_ARG;
+    }
+  if (P->ctx.phase != PH_IDLE && P->ctx.phase != PH_DONE) {
+    set_error("fs_autotune_smoother: a step is in progress");
+    return FS_ERR_BUSY;
+  }
+  cudaStream_t s = P->stream;
+  const fs_schedule base = P->sched;
+  const double t0 = P->t;
+  // the state at the call, in a scratch copy freed before returning
+  double* x0 = nullptr;
+  FS_CUDA(cudaMallocAsync((void**)&x0, sizeof(double) * P->ndof, s));
+  auto restore = [&]() {
+    cudaMemcpyAsync(P->x, x0, sizeof(double) * P->ndof, cudaMemcpyDeviceToDevice, s);
+    P->t = t0;
+    P->hist = 0;
+    P->assembled = false;
+    return cudaStreamSynchronize(s);
+  };
+  cudaMemcpyAsync(x0, P->x, sizeof(double) * P->ndof, cudaMemcpyDeviceToDevice, s);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  std::vector<fs_solve_stats> st(nsteps);
+  int rc = FS_OK, best = -1;
+  double best_ms = 0;
+  for (int q = 0; q < nratios && rc == FS_OK; ++q) {
+    fs_schedule sc = base;
+    sc.cheb_ratio = ratios[q];
+    rc = install_schedule(P, sc);
+    // one untimed step captures the solver's graphs for this schedule
+    if (rc == FS_OK && restore() != cudaSuccess) rc = FS_ERR_CUDA;
+    if (rc == FS_OK) rc = fs_step(P, 1, nullptr, st.data());
+    if (rc == FS_OK && restore() != cudaSuccess) rc = FS_ERR_CUDA;
+    if (rc != FS_OK) break;
+    cudaEventRecord(e0, s);
+    rc = fs_step(P, nsteps, nullptr, st.data());
+    cudaEventRecord(e1, s);
+    if (rc != FS_OK || cudaEventSynchronize(e1) != cudaSuccess) {
+      if (rc == FS_OK) rc = FS_ERR_CUDA;
+      break;
+    }
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    double it = 0;
+    for (const fs_solve_stats& x : st) it += x.iters;
+    if (ms_out) ms_out[q] = ms / nsteps;
+    if (iters_out) iters_out[q] = it / nsteps;
+    if (best < 0 || ms < best_ms) {
+      best = q;
+      best_ms = ms;
+    }
+  }
+  fs_schedule fin = base;
+  if (rc == FS_OK) fin.cheb_ratio = ratios[best];
+  const std::string err = rc == FS_OK ? std::string() : fs_last_error();
+  int rc2 = install_schedule(P, fin);
+  if (restore() != cudaSuccess && rc2 == FS_OK) rc2 = FS_ERR_CUDA;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFreeAsync(x0, s);
+  cudaStreamSynchronize(s);
+  if (rc != FS_OK) {
+    set_error("fs_autotune_smoother: " + err);
+    return rc;
+  }
+  if (rc2 != FS_OK) return rc2;
+  if (best_out) *best_out = ratios[best];
   return FS_OK;
 }
 

@@ -29,6 +29,7 @@ struct CRef {
   double stiff[kMaxLoc][kMaxLoc][4][4];
   double conv[kMaxLoc][kMaxLoc][16];
   double div[4][kMaxLoc][4];
+  double pmass[4][kMaxLoc];
 };
 __constant__ CRef c_ref[2];
 
@@ -40,6 +41,7 @@ void upload_ref_tensors(const RefTensors& R2, const RefTensors& R3) {
     memcpy(h[d].stiff, src[d]->stiff, sizeof(h[d].stiff));
     memcpy(h[d].conv, src[d]->conv, sizeof(h[d].conv));
     memcpy(h[d].div, src[d]->div, sizeof(h[d].div));
+    memcpy(h[d].pmass, src[d]->pmass, sizeof(h[d].pmass));
   }
   cudaMemcpyToSymbol(c_ref, h, sizeof(h));
 }
@@ -307,6 +309,61 @@ __global__ void __launch_bounds__(128) k_conv_elem(DMesh m, int64_t c0, int64_t 
   const uint8_t* pos = m.posA + (e * NL + i) * NL;
 #pragma unroll
   for (int j = 0; j < NL; ++j) row[__ldg(pos + j)] += acc[j];
+}
+
+// Convection on the pressure space, Np[q][s] = int psi_q (w . grad psi_s)
+// over P1 basis functions psi (the vertices of the cell) with the P2 field w
+// (the convection part of the pressure convection-diffusion operator of the
+// Schur-complement approximation): a thread per cell, FP64 atomics into the
+// P1-P1 pattern; rows of fixed vertices stay zero.
+template <int DIM>
+__global__ void __launch_bounds__(128) k_conv_p1(DMesh m, const double* __restrict__ w,
+                                                 int64_t ldw, double wc0, double wc1,
+                                                 double wc2, const uint8_t* __restrict__ fixed,
+                                                 double* __restrict__ Np) {
+  constexpr int NB = DIM + 1, NL = Loc<DIM>::nl;
+  const CRef& R = c_ref[DIM - 2];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m.ncell;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int32_t g[NL];
+    double xv[NB][DIM], gl[NB][DIM];
+    load_cell<DIM>(m, e, g, xv);
+    const double D = bary_grads<DIM>(xv, gl);
+    // wg[s][q] = sum_k (w_k . grad lambda_s) int lambda_q phi_k
+    double wg[NB][NB];
+#pragma unroll
+    for (int s = 0; s < NB; ++s)
+#pragma unroll
+      for (int q = 0; q < NB; ++q) wg[s][q] = 0.0;
+#pragma unroll
+    for (int k = 0; k < NL; ++k) {
+      double wk[DIM];
+      if (w) {
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) wk[c] = __ldg(w + c * ldw + g[k]);
+      } else {
+        wk[0] = wc0;
+        wk[1] = wc1;
+        if constexpr (DIM == 3) wk[2] = wc2;
+      }
+#pragma unroll
+      for (int s = 0; s < NB; ++s) {
+        double t = 0;
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) t += wk[c] * gl[s][c];
+#pragma unroll
+        for (int q = 0; q < NB; ++q) wg[s][q] += t * R.pmass[q][k];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+      if (fixed && __ldg(fixed + g[q])) continue;
+      const int32_t rb = __ldg(m.rpK + g[q]);
+#pragma unroll
+      for (int s = 0; s < NB; ++s)
+        atomicAdd(Np + rb + m.posK[(e * NB + q) * NB + s], D * wg[s][q]);
+    }
+  }
 }
 
 // The same element matrices, a thread per cell over all cells at once,
@@ -740,6 +797,17 @@ void launch_assemble_conv(const DMesh& m, const std::vector<int64_t>& color_ptr,
     }
     count_launches(1);
   }
+}
+
+void launch_assemble_conv_p1(const DMesh& m, const double* w, int64_t ldw, const double* wc,
+                             const uint8_t* fixed, double* Np, cudaStream_t s) {
+  const unsigned g = grid_for(m.ncell, 128);
+  const double w0 = wc ? wc[0] : 0, w1 = wc ? wc[1] : 0, w2 = wc ? wc[2] : 0;
+  if (m.dim == 2)
+    k_conv_p1<2><<<g, 128, 0, s>>>(m, w, ldw, w0, w1, w2, fixed, Np);
+  else
+    k_conv_p1<3><<<g, 128, 0, s>>>(m, w, ldw, w0, w1, w2, fixed, Np);
+  count_launches(1);
 }
 
 template <typename T>

@@ -143,6 +143,12 @@ void launch_assemble_base(const DMesh& m, const std::vector<int64_t>& color_ptr,
 void launch_assemble_conv(const DMesh& m, const std::vector<int64_t>& color_ptr,
                           const double* w, int64_t ldw, const double* wc, double* valA,
                           bool deterministic, cudaStream_t s);
+// Np += the pressure-space convection int psi_q (w . grad psi_s) (P1-P1
+// pattern, slot tables posK; w component-blocked with stride ldw, or the
+// constant field wc when w == nullptr); rows of the vertices with fixed set
+// stay untouched.  FP64 atomics.
+void launch_assemble_conv_p1(const DMesh& m, const double* w, int64_t ldw, const double* wc,
+                             const uint8_t* fixed, double* Np, cudaStream_t s);
 // Dirichlet rows of the scalar block become identity rows.
 template <typename T>
 void launch_bc_rows(const DMesh& m, T* valA, cudaStream_t s);
@@ -234,6 +240,7 @@ struct DLevel {
   SegSkip skip;         // rows of this level by segment
   const T* dinv = nullptr;
   double inv_theta = 0, a1 = 0, b1 = 0, a2 = 0, b2 = 0;  // Chebyshev(3)
+  double lmax = 0;  // estimate of the largest eigenvalue of D^-1 A (host set-up)
 };
 template <typename T>
 struct DHier {
@@ -326,14 +333,28 @@ template <typename A, typename B>
 void launch_convert(const A* in, B* out, int64_t n, const double* scale,
                     int inv, cudaStream_t s);
 
+// The convection part of the pressure convection-diffusion operator, for
+// the Schur-complement approximation: the P1-P1 matrix Np (CSR rows of the
+// pressure vertices) and the inverse lumped pressure mass.  v == nullptr:
+// not used.
+template <typename T>
+struct PcdView {
+  const int32_t* rp = nullptr;
+  const int32_t* ci = nullptr;
+  const T* v = nullptr;
+  const T* invm = nullptr;
+};
+
 // z = P^-1 r, the block preconditioner.  mpl_inv_nu: nu over the lumped
 // pressure mass per vertex, negative on the pinned vertices (their rows pass
-// r_p through).
+// r_p through).  With pcd.v set, the Schur part is
+// M_p^-1 (M_p / dt + nu K_p + N_p) K_p^-1 (pressure convection-diffusion)
+// instead of nu M_p^-1 + dt^-1 K_p^-1 (Cahouet-Chabard).
 template <typename T>
 void launch_precond(const DOp<T>& op, const DHier<T>& HA, const DHier<T>& HK,
                     const T* mpl_inv_nu, double inv_dt, JVec<const T> r, JVec<T> z,
                     T* work_p, T* work_u,
-                    const int* skip, cudaStream_t s);
+                    const int* skip, cudaStream_t s, const PcdView<T>& pcd = PcdView<T>());
 
 // ---- the block preconditioner as one persistent kernel (fs_linalg.cu) ----
 // The passes of launch_precond (pressure load, the pressure V-cycle, the

@@ -97,6 +97,7 @@ struct RefTensors {
   double stiff[kMaxLoc][kMaxLoc][4][4];     // int d_r phi_i d_s phi_j
   double conv[kMaxLoc][kMaxLoc][16];        // int phi_i phi_k d_{r(p)} phi_{j(p)}
   double div[4][kMaxLoc][4];                // int lambda_q d_r phi_j
+  double pmass[4][kMaxLoc];                 // int lambda_q phi_k
 };
 void ref_tensors(int dim, RefTensors& R);
 

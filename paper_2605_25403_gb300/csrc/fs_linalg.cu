@@ -889,6 +889,30 @@ __global__ void __launch_bounds__(256) k_mg_first1(DSell<T> A, const T* __restri
   Dout[row] = d;
 }
 
+// Pressure part of the preconditioner in the convection-diffusion form:
+// z_p = nu Mp^-1 r_p + dt^-1 y_K + Mp^-1 (N_p y_K), y_K = K_p^-1 r_p the
+// pressure V-cycle's output (r_p on pinned rows, marked by a negative mpl).
+template <typename T>
+__global__ void __launch_bounds__(256) k_prec_pcd(int64_t nv, JVec<const T> rpv,
+                                                  const T* __restrict__ yk,
+                                                  const T* __restrict__ mpl, T inv_dt,
+                                                  PcdView<T> pcd, JVec<T> zpv,
+                                                  const int* skip) {
+  pdl_wait();
+  if (skip && *skip) return;
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= nv) return;
+  const T* __restrict__ rp = rpv.get();
+  const T m = mpl[q], p = rp[q];
+  T z = p;
+  if (m >= T(0)) {
+    T acc = T(0);
+    for (int32_t k = pcd.rp[q]; k < pcd.rp[q + 1]; ++k) acc += pcd.v[k] * yk[pcd.ci[k]];
+    z = m * p + inv_dt * yk[q] + pcd.invm[q] * acc;
+  }
+  zpv.get()[q] = z;
+}
+
 // The Cahouet-Chabard combination and the velocity right-hand side of the
 // V-cycle in one pass.  Threads [0, nvp) (nv rounded up to a warp) write the
 // pressure part of the result, z_p = nu Mp^-1 r_p + dt^-1 y_K (y_K the
@@ -905,7 +929,7 @@ __device__ __forceinline__ T cc_combine(const T* __restrict__ mpl, const T* __re
   return m < T(0) ? p : m * p + inv_dt * yk[q];
 }
 
-template <typename T, int DIM, int NCP>
+template <typename T, int DIM, int NCP, bool ZREAD>
 __global__ void __launch_bounds__(256) k_bt_add_mg(DSell<T> BT, int64_t n2, int64_t nv,
                                                    JVec<const T> rv, const T* __restrict__ yk,
                                                    const T* __restrict__ mpl, T inv_dt,
@@ -920,8 +944,11 @@ __global__ void __launch_bounds__(256) k_bt_add_mg(DSell<T> BT, int64_t n2, int6
   const T* __restrict__ rp = r + DIM * n2;
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t nvp = (nv + 31) & ~(int64_t)31;
+  // ZREAD: z_p was written by the pressure kernel before (convection-
+  // diffusion form), read it back
+  const T* __restrict__ zp = zv.get() + DIM * n2;
   if (t < nvp) {
-    if (t < nv) zv.get()[DIM * n2 + t] = cc_combine(mpl, rp, yk, inv_dt, t);
+    if (!ZREAD && t < nv) zv.get()[DIM * n2 + t] = cc_combine(mpl, rp, yk, inv_dt, t);
     return;
   }
   const int64_t row = t - nvp;
@@ -934,7 +961,7 @@ __global__ void __launch_bounds__(256) k_bt_add_mg(DSell<T> BT, int64_t n2, int6
   const int64_t o1 = BT.off[(row >> 5) + 1];
   for (int64_t o = BT.off[row >> 5] + (row & 31); o < o1; o += 32) {
     const int64_t base = (o - (row & 31)) * DIM + (row & 31);
-    const T p = cc_combine(mpl, rp, yk, inv_dt, BT.ci[o]);
+    const T p = ZREAD ? zp[BT.ci[o]] : cc_combine(mpl, rp, yk, inv_dt, BT.ci[o]);
 #pragma unroll
     for (int c = 0; c < DIM; ++c) acc[c] += BT.v[base + 32 * c] * p;
   }
@@ -1116,7 +1143,7 @@ template <typename T>
 void launch_precond(const DOp<T>& op, const DHier<T>& HA, const DHier<T>& HK,
                     const T* mpl_inv_nu, double inv_dt, JVec<const T> r, JVec<T> z,
                     T* work_p, T* work_u,
-                    const int* skip, cudaStream_t s) {
+                    const int* skip, cudaStream_t s, const PcdView<T>& pcd) {
   (void)work_u;
   const int64_t n2 = op.n2, nv = op.nv;
   const int dim = op.dim;
@@ -1150,16 +1177,22 @@ void launch_precond(const DOp<T>& op, const DHier<T>& HA, const DHier<T>& HK,
   const T* d0 = a1 ? HA.lev[0].dinv : nullptr;
   const T it0 = (T)HA.lev[0].inv_theta;
   const unsigned nb = blocks_for(((nv + 31) & ~(int64_t)31) + n2);
+  const bool pc = pcd.v != nullptr;
+  if (pc) {
+    launch_k(k_prec_pcd<T>, blocks_for(nv), 256, 0, s, nv, rp, (const T*)work_p, mpl_inv_nu,
+             (T)inv_dt, pcd, z.shifted(dim * n2), skip);
+    count_launches(1);
+  }
   if (dim == 2) {
-    launch_k(k_bt_add_mg<T, 2, 2>, nb, 256, 0, s, op.BT, n2, nv, r, (const T*)work_p,
-             mpl_inv_nu, (T)inv_dt, z, HA.iperm, d0, it0, HA.b[0], HA.G0[0], HA.D0[0],
-             HA.lev[0].skip, skip);
+    launch_k(pc ? k_bt_add_mg<T, 2, 2, true> : k_bt_add_mg<T, 2, 2, false>, nb, 256, 0, s,
+             op.BT, n2, nv, r, (const T*)work_p, mpl_inv_nu, (T)inv_dt, z, HA.iperm, d0, it0,
+             HA.b[0], HA.G0[0], HA.D0[0], HA.lev[0].skip, skip);
     count_launches(1);
     vcycle_level<T, 2>(HA, 0, z, n2, 2, skip, s);
   } else {
-    launch_k(k_bt_add_mg<T, 3, 4>, nb, 256, 0, s, op.BT, n2, nv, r, (const T*)work_p,
-             mpl_inv_nu, (T)inv_dt, z, HA.iperm, d0, it0, HA.b[0], HA.G0[0], HA.D0[0],
-             HA.lev[0].skip, skip);
+    launch_k(pc ? k_bt_add_mg<T, 3, 4, true> : k_bt_add_mg<T, 3, 4, false>, nb, 256, 0, s,
+             op.BT, n2, nv, r, (const T*)work_p, mpl_inv_nu, (T)inv_dt, z, HA.iperm, d0, it0,
+             HA.b[0], HA.G0[0], HA.D0[0], HA.lev[0].skip, skip);
     count_launches(1);
     vcycle_level<T, 4>(HA, 0, z, n2, 3, skip, s);
   }
@@ -1167,11 +1200,12 @@ void launch_precond(const DOp<T>& op, const DHier<T>& HA, const DHier<T>& HK,
 template void launch_precond<double>(const DOp<double>&, const DHier<double>&,
                                      const DHier<double>&, const double*, double,
                                      JVec<const double>, JVec<double>,
-                                     double*, double*, const int*, cudaStream_t);
+                                     double*, double*, const int*, cudaStream_t,
+                                     const PcdView<double>&);
 template void launch_precond<float>(const DOp<float>&, const DHier<float>&,
                                     const DHier<float>&, const float*, double,
                                     JVec<const float>, JVec<float>, float*,
-                                    float*, const int*, cudaStream_t);
+                                    float*, const int*, cudaStream_t, const PcdView<float>&);
 
 // ---------------------------------------------------------------------------
 // The block preconditioner as one persistent kernel over a work-list

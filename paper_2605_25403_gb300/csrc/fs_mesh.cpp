@@ -606,8 +606,10 @@ void ref_tensors(int dim, RefTensors& R) {
         for (int p = 0; p < R.npair; ++p)
           R.conv[i][k][p] += w * phi[i] * phi[k] * dphi[R.pair_j[p]][R.pair_r[p]];
     for (int qv = 0; qv < R.nb; ++qv)
-      for (int j = 0; j < R.nloc; ++j)
+      for (int j = 0; j < R.nloc; ++j) {
         for (int r = 0; r < R.nb; ++r) R.div[qv][j][r] += w * l[qv] * dphi[j][r];
+        R.pmass[qv][j] += w * l[qv] * phi[j];
+      }
   }
 }
 

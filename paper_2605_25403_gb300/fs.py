@@ -131,7 +131,7 @@ class fs_schedule(ctypes.Structure):
     _fields_ = [("tail_rows_velocity", _i64), ("tail_rows_pressure", _i64),
                 ("spmv_group", _int), ("smooth_group", _int), ("coarse_degree", _int),
                 ("serial_launches", _int), ("persistent_precond", _int),
-                ("fine_degree", _int)]
+                ("fine_degree", _int), ("cheb_ratio", _int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -185,6 +185,9 @@ _lib.fs_profile_kernel.restype = _int
 _lib.fs_profile_kernel.argtypes = [_vp, _int, _int, _P(_d), _P(_d)]
 _lib.fs_get_schedule.restype = _int
 _lib.fs_get_schedule.argtypes = [_vp, _P(fs_schedule)]
+_lib.fs_autotune_smoother.restype = _int
+_lib.fs_autotune_smoother.argtypes = [_vp, _int, _P(ctypes.c_int32), _int, _P(_d), _P(_d),
+                                      _P(ctypes.c_int32)]
 _lib.fs_set_schedule.restype = _int
 _lib.fs_set_schedule.argtypes = [_vp, _P(fs_schedule)]
 _lib.fs_autotune.restype = _int
@@ -204,6 +207,7 @@ EXPORTED = ["fs_mesh_create", "fs_mesh_destroy", "fs_dof_map", "fs_problem_creat
             "fs_server_destroy", "fs_server_submit", "fs_server_progress",
             "fs_server_pop_completed", "fs_server_take_state", "fs_server_status",
             "fs_server_estimate_bytes", "fs_get_schedule", "fs_set_schedule", "fs_autotune",
+            "fs_autotune_smoother",
             "fs_step_picard", "fs_solve_steady", "fs_step_ipcs", "fs_problem_create_p3",
             "fs_problem_sizes"]
 (FS_KERNEL_SPMV, FS_KERNEL_SPMV_FP64, FS_KERNEL_CHEB, FS_KERNEL_ASSEMBLE_CONV,
@@ -507,10 +511,11 @@ def fs_get_schedule(prob):
 
 
 def fs_set_schedule(prob, tail_rows_velocity, tail_rows_pressure, spmv_group=0, smooth_group=0,
-                    coarse_degree=0, serial_launches=0, persistent_precond=0, fine_degree=0):
+                    coarse_degree=0, serial_launches=0, persistent_precond=0, fine_degree=0,
+                    cheb_ratio=0):
     sc = fs_schedule(int(tail_rows_velocity), int(tail_rows_pressure), int(spmv_group),
                      int(smooth_group), int(coarse_degree), int(serial_launches),
-                     int(persistent_precond), int(fine_degree))
+                     int(persistent_precond), int(fine_degree), int(cheb_ratio))
     _check(_lib.fs_set_schedule(prob, ctypes.byref(sc)), "fs_set_schedule")
 
 
@@ -520,6 +525,21 @@ def fs_autotune(prob, reps=10):
     r = fs_tune_report()
     _check(_lib.fs_autotune(prob, int(reps), ctypes.byref(r)), "fs_autotune")
     return r.as_dict()
+
+
+def fs_autotune_smoother(prob, nsteps=3, ratios=(4, 6, 8, 12, 16)):
+    """Times `nsteps` steps from the current state under each Chebyshev
+    interval ratio, installs the fastest and restores the state; returns
+    {"ratios", "ms_per_step", "iters_per_step", "best"}."""
+    n = len(ratios)
+    rr = (ctypes.c_int32 * n)(*[int(r) for r in ratios])
+    ms = (_d * n)()
+    it = (_d * n)()
+    best = ctypes.c_int32(0)
+    _check(_lib.fs_autotune_smoother(prob, int(nsteps), rr, n, ms, it, ctypes.byref(best)),
+           "fs_autotune_smoother")
+    return {"ratios": list(ratios), "ms_per_step": list(ms), "iters_per_step": list(it),
+            "best": int(best.value)}
 
 
 def fs_profile_kernel(prob, kernel, reps=20, cold=False):

@@ -25,13 +25,13 @@ pytestmark = pytest.mark.gpu
 
 # (tail rows velocity, tail rows pressure, SpMV group, smoothing group,
 #  coarse-level smoother degree, serialised launches, persistent preconditioner,
-#  finest-level smoother degree)
-SCHEDULES = [(0, 0, 0, 0, 0, 0, 0, 0), (65536, 65536, 8, 6, 0, 0, 0, 0),
-             (4096, 16384, 4, 4, 0, 1, 0, 0), (16384, 0, 6, 6, 0, 0, 0, 0),
-             (0, 0, 0, 0, 0, 0, 1, 0), (0, 0, 6, 0, 0, 1, 1, 0)]
+#  finest-level smoother degree, Chebyshev interval ratio)
+SCHEDULES = [(0, 0, 0, 0, 0, 0, 0, 0, 0), (65536, 65536, 8, 6, 0, 0, 0, 0, 0),
+             (4096, 16384, 4, 4, 0, 1, 0, 0, 0), (16384, 0, 6, 6, 0, 0, 0, 0, 0),
+             (0, 0, 0, 0, 0, 0, 1, 0, 0), (0, 0, 6, 0, 0, 1, 1, 0, 8)]
 KEYS = ("tail_rows_velocity", "tail_rows_pressure", "spmv_group", "smooth_group",
-        "coarse_degree", "serial_launches", "persistent_precond", "fine_degree")
-PERSISTENT = (0, 0, 0, 0, 0, 0, 1, 0)
+        "coarse_degree", "serial_launches", "persistent_precond", "fine_degree", "cheb_ratio")
+PERSISTENT = (0, 0, 0, 0, 0, 0, 1, 0, 0)
 
 
 @pytest.fixture(scope="module")
@@ -110,8 +110,8 @@ def test_coarse_degree_two_reaches_the_same_solution(fs, prec):
     p = fs.FS_PREC_FP64 if prec == "fp64" else fs.FS_PREC_FP32_REFINE
     for wl in (W.channel(64, 16), W.cube(10, jitter=0.05)):
         make = lambda q: fs.Stepper.from_workload(wl, precision=q)
-        x3, i3 = _run(fs, make, (0, 0, 0, 0, 3, 0, 0, 0), p, iters=True)
-        x2, i2 = _run(fs, make, (0, 0, 0, 0, 2, 0, 0, 0), p, iters=True)
+        x3, i3 = _run(fs, make, (0, 0, 0, 0, 3, 0, 0, 0, 0), p, iters=True)
+        x2, i2 = _run(fs, make, (0, 0, 0, 0, 2, 0, 0, 0, 0), p, iters=True)
         print(wl.name, prec, "iterations per step, degree 3 / 2:", i3, i2)
         assert not np.array_equal(x2, x3)  # the knob reaches the V-cycle
         assert rel_l2(x2, x3) <= 1e-9
@@ -126,14 +126,64 @@ def test_fine_degree_two_reaches_the_same_solution(fs, prec):
     p = fs.FS_PREC_FP64 if prec == "fp64" else fs.FS_PREC_FP32_REFINE
     for wl in (W.channel(64, 16), W.cube(10, jitter=0.05)):
         make = lambda q: fs.Stepper.from_workload(wl, precision=q)
-        x3, i3 = _run(fs, make, (0, 0, 0, 0, 0, 0, 0, 3), p, iters=True)
-        x2, i2 = _run(fs, make, (0, 0, 0, 0, 0, 0, 0, 2), p, iters=True)
-        xp = _run(fs, make, (0, 0, 0, 0, 0, 0, 1, 2), p)
-        xt = _run(fs, make, (1 << 30, 1 << 30, 0, 0, 0, 0, 0, 2), p)
+        x3, i3 = _run(fs, make, (0, 0, 0, 0, 0, 0, 0, 3, 0), p, iters=True)
+        x2, i2 = _run(fs, make, (0, 0, 0, 0, 0, 0, 0, 2, 0), p, iters=True)
+        xp = _run(fs, make, (0, 0, 0, 0, 0, 0, 1, 2, 0), p)
+        xt = _run(fs, make, (1 << 30, 1 << 30, 0, 0, 0, 0, 0, 2, 0), p)
         print(wl.name, prec, "iterations per step, finest degree 3 / 2:", i3, i2)
         assert not np.array_equal(x2, x3)
         assert rel_l2(x2, x3) <= 1e-9
         assert rel_l2(xp, x2) <= TOL[prec] and rel_l2(xt, x2) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_refine"])
+def test_chebyshev_interval_reaches_the_same_solution(fs, prec):
+    """Another smoothing interval is another preconditioner: the iterates
+    change, the solution stays within the parity bar; the persistent form
+    rebuilds its work-list with the new coefficients and agrees with the
+    per-pass form at the same interval."""
+    p = fs.FS_PREC_FP64 if prec == "fp64" else fs.FS_PREC_FP32_REFINE
+    wl = W.channel(64, 16)
+    make = lambda q: fs.Stepper.from_workload(wl, precision=q)
+    x8, i8 = _run(fs, make, (0, 0, 0, 0, 0, 0, 0, 0, 8), p, iters=True)
+    x12, i12 = _run(fs, make, (0, 0, 0, 0, 0, 0, 0, 0, 12), p, iters=True)
+    S = make(p)
+    try:
+        # the persistent work-list is built at ratio 8 first, then replaced
+        fs.fs_set_schedule(S.prob, 0, 0, persistent_precond=1)
+        fs.fs_set_schedule(S.prob, 0, 0, persistent_precond=1, cheb_ratio=12)
+        st = fs.fs_step(S.prob, 2)
+        assert all(s["status"] == 0 for s in st)
+        xp12 = S.state()[0]
+    finally:
+        S.close()
+    print(prec, "iterations per step, ratio 8 / 12:", i8, i12)
+    assert not np.array_equal(x8, x12)
+    assert rel_l2(x12, x8) <= 1e-9
+    assert rel_l2(xp12, x12) <= TOL[prec]
+
+
+def test_autotune_smoother_restores_the_state(fs):
+    S = fs.Stepper.from_workload(W.channel(64, 16), precision=fs.FS_PREC_FP32_REFINE)
+    try:
+        fs.fs_step(S.prob, 2)
+        x0, t0 = S.state()
+        rep = fs.fs_autotune_smoother(S.prob, nsteps=2, ratios=(6, 12))
+        print(rep)
+        assert rep["best"] in (6, 12)
+        assert all(m > 0 for m in rep["ms_per_step"])
+        assert all(i > 0 for i in rep["iters_per_step"])
+        assert fs.fs_get_schedule(S.prob)["cheb_ratio"] == rep["best"]
+        x1, t1 = S.state()
+        assert t1 == t0 and np.array_equal(x0, x1)
+        st = fs.fs_step(S.prob, 1)[0]
+        assert st["status"] == 0 and st["rel_res"] <= 1e-12
+        with pytest.raises(fs.FsError):
+            fs.fs_autotune_smoother(S.prob, nsteps=1, ratios=(1,))
+        with pytest.raises(fs.FsError):
+            fs.fs_set_schedule(S.prob, 0, 0, cheb_ratio=100)
+    finally:
+        S.close()
 
 
 def test_autotune_installs_a_candidate(fs):
