@@ -585,7 +585,7 @@ def main():
     fs.fs_set_schedule(SE.prob, sched["tail_rows_velocity"], sched["tail_rows_pressure"],
                        sched["spmv_group"], sched["smooth_group"], sched["coarse_degree"],
                        sched["serial_launches"], sched["persistent_precond"],
-                       sched["fine_degree"], sched["cheb_ratio"])
+                       sched["fine_degree"], sched["cheb_ratio"], sched["schur"])
     for _ in range(max(0, args.warmup - 1)):
         fs.fs_step(SE.prob, 1)
     xh = torch.empty(ndof, dtype=torch.float64).pin_memory()

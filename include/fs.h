@@ -497,6 +497,14 @@ typedef struct {
                             64; 0 = 8.  It changes the preconditioner like
                             the degrees; fs_autotune_smoother picks it by
                             timing steps                                */
+  int32_t schur;         /* approximation of the pressure Schur complement:
+                            0 Cahouet-Chabard, S^-1 = nu Mp^-1 + dt^-1 Kp^-1;
+                            1 pressure convection-diffusion,
+                            S^-1 = Mp^-1 (Mp/dt + nu Kp + Np(w)) Kp^-1 with
+                            Np(w) the convection by the step's w on the
+                            pressure space (assembled with the system).
+                            Changes the preconditioner like the degrees.
+                            Not with persistent_precond (FS_ERR_UNSUPPORTED) */
 } fs_schedule;
 typedef struct {
   int candidates;        /* schedules timed                                  */

@@ -116,6 +116,10 @@ struct Precision {
   FlowDev flow[8];
   int flow_ratio[8] = {};  // the Chebyshev interval ratio each work-list holds
   int cheb_ratio = 8;      // the hierarchies' current Chebyshev interval ratio
+  // pressure convection-diffusion form of the Schur part: inverse lumped
+  // pressure mass, the pressure convection matrix in this precision
+  T* invm = nullptr;
+  T* Np = nullptr;
 };
 
 // The work-list built for the hierarchies' current smoothing degrees.
@@ -168,6 +172,11 @@ struct fs_problem {
   int hist = 0, hist_head = 0;
   int32_t* pinned = nullptr;
   int npinned = 0;
+  // vertices whose rows of the preconditioner's pressure Poisson are fixed,
+  // and the pressure convection matrix (P1-P1 pattern, FP64; allocated when
+  // a schedule asks for the convection-diffusion Schur part)
+  uint8_t* pfix = nullptr;
+  double* Np64 = nullptr;
   std::vector<int32_t> pinned_host;  // the same vertices, on the host
   // Taylor-Hood P3/P2 problems (fs_problem_create_p3): the P2 pressure map,
   // pressure node coordinates, reference integrals; stepped by IPCS only
@@ -220,7 +229,7 @@ struct fs_problem {
   std::vector<fs_solve_stats> last_stats;  // per instance, last solve
   double t = 0;
   bool assembled = false;
-  fs_schedule sched{0, 0, 0, 0, 0, 0, 0, 0, 0};
+  fs_schedule sched{0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
 
   TileList tl() const { return TileList{tiles, ntiles}; }
 
@@ -632,9 +641,12 @@ void issue_precond(fs_problem* P, Precision<T>& pr, const DHier<T>& HA, const DH
     launch_precond_flow<T>(pr.flow[flow_index(HA, HK)], pr.op, HA, pr.mplinv_nu,
                            1.0 / P->desc.dt, r, z, pr.kr.work_p, st,
                            pr.kr.st, skip, q);
-  else
+  else {
+    PcdView<T> pcd;
+    if (P->sched.schur) pcd = PcdView<T>{P->dm.rpK, P->dm.ciK, pr.Np, pr.invm};
     launch_precond<T>(pr.op, HA, HK, pr.mplinv_nu, 1.0 / P->desc.dt, r,
-                      z, pr.kr.work_p, pr.kr.work_u, skip, q);
+                      z, pr.kr.work_p, pr.kr.work_u, skip, q, pcd);
+  }
 }
 
 // Work-list over the n_dof entries: for every instance its vertex and edge
@@ -952,6 +964,24 @@ int push_rtol(fs_problem* P, Krylov<T>& K, const std::vector<double>& rtol) {
 // The Oseen system of the step to t_next: convecting field w (the state
 // when null; a Picard iterate otherwise) and the previous time level u_old in
 // the load (the state when null).
+// Problems whose convecting field is a given constant (the polynomial
+// exactness problems), not the state.
+bool const_w(const fs_problem* P) {
+  return P->desc.problem == FS_PROBLEM_POLY_OSEEN || P->desc.problem == FS_PROBLEM_POLY_OSEEN_T ||
+         P->desc.problem == FS_PROBLEM_POLY3;
+}
+
+// The pressure convection matrix of the convection-diffusion Schur part,
+// for the convecting field w (or the constant wc), in FP64 and, for the
+// FP32 inner solves, converted to FP32.
+void assemble_np(fs_problem* P, const double* w, const double* wc) {
+  cudaStream_t s = P->stream;
+  const int64_t nnz = P->mesh->m.Kp.nnz();
+  cudaMemsetAsync(P->Np64, 0, sizeof(double) * nnz, s);
+  launch_assemble_conv_p1(P->dm, w, P->n2, wc, P->pfix, P->Np64, s);
+  if (P->has32) launch_convert<double, float>(P->Np64, P->p32.Np, nnz, nullptr, 0, s);
+}
+
 int assemble_impl(fs_problem* P, double t_next, const double* w = nullptr,
                   const double* u_old = nullptr) {
   cudaStream_t s = P->stream;
@@ -959,9 +989,7 @@ int assemble_impl(fs_problem* P, double t_next, const double* w = nullptr,
   const int64_t nnzA = me.A.nnz();
   if (!w) w = P->x;
   if (!u_old) u_old = P->x;
-  const bool constw = P->desc.problem == FS_PROBLEM_POLY_OSEEN ||
-                      P->desc.problem == FS_PROBLEM_POLY_OSEEN_T ||
-                      P->desc.problem == FS_PROBLEM_POLY3;
+  const bool constw = const_w(P);
   if (P->p3) {
     const int64_t nnz3 = P->p3nnzA;
     FS_CUDA(cudaMemcpyAsync(P->valA, P->baseA, sizeof(double) * nnz3, cudaMemcpyDeviceToDevice,
@@ -983,6 +1011,7 @@ int assemble_impl(fs_problem* P, double t_next, const double* w = nullptr,
   launch_rhs(P->dm, P->ph, t_next, P->Mv, P->F, P->pinned, P->npinned, P->b, s);
   launch_csr_to_sell(P->n2, P->dm.rpA, P->valA, P->offA, P->sA64, P->has32 ? P->sA32 : nullptr,
                      s);
+  if (P->sched.schur) assemble_np(P, constw ? nullptr : w, constw ? P->desc.wconst : nullptr);
   FS_TRY(check_launch("assembly"));
   P->assembled = true;
   return FS_OK;
@@ -1231,11 +1260,23 @@ int install_schedule(fs_problem* P, Precision<T>& pr, const fs_schedule& sc) {
 }
 
 int install_schedule(fs_problem* P, const fs_schedule& sc) {
+  if (sc.schur && !P->Np64) {
+    const int64_t nnz = P->mesh->m.Kp.nnz();
+    FS_TRY(P->alloc(&P->Np64, nnz));
+    P->p64.Np = P->Np64;
+    if (P->has32) FS_TRY(P->alloc(&P->p32.Np, nnz));
+  }
+  const bool fresh_np = sc.schur && !P->sched.schur;
   if (P->desc.precision == FS_PREC_FP64)
     FS_TRY(install_schedule<double>(P, P->p64, sc));
   else
     FS_TRY(install_schedule<float>(P, P->p32, sc));
   P->sched = sc;
+  // a system assembled before gets its pressure convection from the state
+  if (fresh_np && P->assembled) {
+    assemble_np(P, const_w(P) ? nullptr : P->x, const_w(P) ? P->desc.wconst : nullptr);
+    FS_TRY(check_launch("pressure convection"));
+  }
   return FS_OK;
 }
 
@@ -1760,12 +1801,15 @@ int fs_problem_create_batch(fs_mesh* mesh, const fs_problem_desc* descs, int cou
                           s));
   FS_CUDA(cudaMemcpyAsync(P->diagp, dp.data(), sizeof(double) * P->nv, cudaMemcpyHostToDevice, s));
   // pressure Poisson of the preconditioner with its fixed rows
+  std::vector<double> invm(P->nv);
   {
     std::vector<uint8_t> fixed(P->nv, 0);
     for (int32_t q : kfix) fixed[q] = 1;
     for (int64_t q = 0; q < P->nv; ++q)
       for (int32_t k = Kp.rowptr[q]; k < Kp.rowptr[q + 1]; ++k)
         if (fixed[q] || fixed[Kp.col[k]]) Kp.val[k] = (Kp.col[k] == q) ? 1.0 : 0.0;
+    FS_TRY(P->upload(&P->pfix, fixed));
+    for (int64_t q = 0; q < P->nv; ++q) invm[q] = 1.0 / mplh[q];
   }
   // nu over the lumped pressure mass; a pinned vertex is marked by -1 (its
   // row of the preconditioner passes r_p through)
@@ -1855,10 +1899,14 @@ int fs_problem_create_batch(fs_mesh* mesh, const fs_problem_desc* descs, int cou
     P->slice_seg_p = sp;
   }
   const int m = 30;
-  if (d0.precision == FS_PREC_FP64)
+  if (d0.precision == FS_PREC_FP64) {
     FS_TRY(setup_precision<double>(P.get(), P->p64, HA, HK, mplinv_nu, m, first, tcount));
-  else
+    FS_TRY(P->upload(&P->p64.invm, invm));
+  } else {
     FS_TRY(setup_precision<float>(P.get(), P->p32, HA, HK, mplinv_nu, m, first, tcount));
+    std::vector<float> im(invm.begin(), invm.end());
+    FS_TRY(P->upload(&P->p32.invm, im));
+  }
   launch_exact_state(dm, P->ph, d0.t0, d0.init == 1, P->x, s);
   FS_TRY(check_launch("initial state"));
   FS_CUDA(cudaStreamSynchronize(s));
@@ -2641,9 +2689,15 @@ int fs_set_schedule(fs_problem* P, const fs_schedule* sc) {
       !in(sc->spmv_group, {0, 4, 6, 8}) || !in(sc->smooth_group, {0, 4, 6}) ||
       !in(sc->coarse_degree, {0, 2, 3}) || !in(sc->serial_launches, {0, 1}) ||
       !in(sc->persistent_precond, {0, 1}) || !in(sc->fine_degree, {0, 2, 3}) ||
-      (sc->cheb_ratio != 0 && (sc->cheb_ratio < 2 || sc->cheb_ratio > 64))) {
+      (sc->cheb_ratio != 0 && (sc->cheb_ratio < 2 || sc->cheb_ratio > 64)) ||
+      !in(sc->schur, {0, 1})) {
     set_error("fs_set_schedule: bad argument");
     return FS_ERR_INVALID_ARG;
+  }
+  if (sc->schur && sc->persistent_precond) {
+    set_error("fs_set_schedule: the persistent preconditioner takes the Cahouet-Chabard "
+              "Schur part only");
+    return FS_ERR_UNSUPPORTED;
   }
   if (P->ctx.phase != PH_IDLE && P->ctx.phase != PH_DONE) {
     set_error("fs_set_schedule: a step is in progress");
@@ -2724,8 +2778,10 @@ int fs_autotune(fs_problem* P, int reps, fs_tune_report* report) {
     apply(sc);
     double ms0 = 0, ms1 = 0;
     FS_TRY(time_precond(P, reps, 0, &ms0));
-    int rc = P->desc.precision == FS_PREC_FP64 ? apply_flow<double>(P, P->p64)
-                                               : apply_flow<float>(P, P->p32);
+    int rc = FS_ERR_UNSUPPORTED;
+    if (!base.schur)
+      rc = P->desc.precision == FS_PREC_FP64 ? apply_flow<double>(P, P->p64)
+                                             : apply_flow<float>(P, P->p32);
     if (rc == FS_OK) rc = time_precond(P, reps, 1, &ms1);
     if (rc != FS_OK && rc != FS_ERR_UNSUPPORTED) return rc;
     r.candidates += 1;

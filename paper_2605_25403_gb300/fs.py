@@ -131,7 +131,7 @@ class fs_schedule(ctypes.Structure):
     _fields_ = [("tail_rows_velocity", _i64), ("tail_rows_pressure", _i64),
                 ("spmv_group", _int), ("smooth_group", _int), ("coarse_degree", _int),
                 ("serial_launches", _int), ("persistent_precond", _int),
-                ("fine_degree", _int), ("cheb_ratio", _int)]
+                ("fine_degree", _int), ("cheb_ratio", _int), ("schur", _int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -512,10 +512,10 @@ def fs_get_schedule(prob):
 
 def fs_set_schedule(prob, tail_rows_velocity, tail_rows_pressure, spmv_group=0, smooth_group=0,
                     coarse_degree=0, serial_launches=0, persistent_precond=0, fine_degree=0,
-                    cheb_ratio=0):
+                    cheb_ratio=0, schur=0):
     sc = fs_schedule(int(tail_rows_velocity), int(tail_rows_pressure), int(spmv_group),
                      int(smooth_group), int(coarse_degree), int(serial_launches),
-                     int(persistent_precond), int(fine_degree), int(cheb_ratio))
+                     int(persistent_precond), int(fine_degree), int(cheb_ratio), int(schur))
     _check(_lib.fs_set_schedule(prob, ctypes.byref(sc)), "fs_set_schedule")
 
 

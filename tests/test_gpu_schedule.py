@@ -25,13 +25,14 @@ pytestmark = pytest.mark.gpu
 
 # (tail rows velocity, tail rows pressure, SpMV group, smoothing group,
 #  coarse-level smoother degree, serialised launches, persistent preconditioner,
-#  finest-level smoother degree, Chebyshev interval ratio)
-SCHEDULES = [(0, 0, 0, 0, 0, 0, 0, 0, 0), (65536, 65536, 8, 6, 0, 0, 0, 0, 0),
-             (4096, 16384, 4, 4, 0, 1, 0, 0, 0), (16384, 0, 6, 6, 0, 0, 0, 0, 0),
-             (0, 0, 0, 0, 0, 0, 1, 0, 0), (0, 0, 6, 0, 0, 1, 1, 0, 8)]
+#  finest-level smoother degree, Chebyshev interval ratio, Schur-complement form)
+SCHEDULES = [(0, 0, 0, 0, 0, 0, 0, 0, 0, 0), (65536, 65536, 8, 6, 0, 0, 0, 0, 0, 0),
+             (4096, 16384, 4, 4, 0, 1, 0, 0, 0, 0), (16384, 0, 6, 6, 0, 0, 0, 0, 0, 0),
+             (0, 0, 0, 0, 0, 0, 1, 0, 0, 0), (0, 0, 6, 0, 0, 1, 1, 0, 8, 0)]
 KEYS = ("tail_rows_velocity", "tail_rows_pressure", "spmv_group", "smooth_group",
-        "coarse_degree", "serial_launches", "persistent_precond", "fine_degree", "cheb_ratio")
-PERSISTENT = (0, 0, 0, 0, 0, 0, 1, 0, 0)
+        "coarse_degree", "serial_launches", "persistent_precond", "fine_degree", "cheb_ratio",
+        "schur")
+PERSISTENT = (0, 0, 0, 0, 0, 0, 1, 0, 0, 0)
 
 
 @pytest.fixture(scope="module")
@@ -110,8 +111,8 @@ def test_coarse_degree_two_reaches_the_same_solution(fs, prec):
     p = fs.FS_PREC_FP64 if prec == "fp64" else fs.FS_PREC_FP32_REFINE
     for wl in (W.channel(64, 16), W.cube(10, jitter=0.05)):
         make = lambda q: fs.Stepper.from_workload(wl, precision=q)
-        x3, i3 = _run(fs, make, (0, 0, 0, 0, 3, 0, 0, 0, 0), p, iters=True)
-        x2, i2 = _run(fs, make, (0, 0, 0, 0, 2, 0, 0, 0, 0), p, iters=True)
+        x3, i3 = _run(fs, make, (0, 0, 0, 0, 3, 0, 0, 0, 0, 0), p, iters=True)
+        x2, i2 = _run(fs, make, (0, 0, 0, 0, 2, 0, 0, 0, 0, 0), p, iters=True)
         print(wl.name, prec, "iterations per step, degree 3 / 2:", i3, i2)
         assert not np.array_equal(x2, x3)  # the knob reaches the V-cycle
         assert rel_l2(x2, x3) <= 1e-9
@@ -126,10 +127,10 @@ def test_fine_degree_two_reaches_the_same_solution(fs, prec):
     p = fs.FS_PREC_FP64 if prec == "fp64" else fs.FS_PREC_FP32_REFINE
     for wl in (W.channel(64, 16), W.cube(10, jitter=0.05)):
         make = lambda q: fs.Stepper.from_workload(wl, precision=q)
-        x3, i3 = _run(fs, make, (0, 0, 0, 0, 0, 0, 0, 3, 0), p, iters=True)
-        x2, i2 = _run(fs, make, (0, 0, 0, 0, 0, 0, 0, 2, 0), p, iters=True)
-        xp = _run(fs, make, (0, 0, 0, 0, 0, 0, 1, 2, 0), p)
-        xt = _run(fs, make, (1 << 30, 1 << 30, 0, 0, 0, 0, 0, 2, 0), p)
+        x3, i3 = _run(fs, make, (0, 0, 0, 0, 0, 0, 0, 3, 0, 0), p, iters=True)
+        x2, i2 = _run(fs, make, (0, 0, 0, 0, 0, 0, 0, 2, 0, 0), p, iters=True)
+        xp = _run(fs, make, (0, 0, 0, 0, 0, 0, 1, 2, 0, 0), p)
+        xt = _run(fs, make, (1 << 30, 1 << 30, 0, 0, 0, 0, 0, 2, 0, 0), p)
         print(wl.name, prec, "iterations per step, finest degree 3 / 2:", i3, i2)
         assert not np.array_equal(x2, x3)
         assert rel_l2(x2, x3) <= 1e-9
@@ -145,8 +146,8 @@ def test_chebyshev_interval_reaches_the_same_solution(fs, prec):
     p = fs.FS_PREC_FP64 if prec == "fp64" else fs.FS_PREC_FP32_REFINE
     wl = W.channel(64, 16)
     make = lambda q: fs.Stepper.from_workload(wl, precision=q)
-    x8, i8 = _run(fs, make, (0, 0, 0, 0, 0, 0, 0, 0, 8), p, iters=True)
-    x12, i12 = _run(fs, make, (0, 0, 0, 0, 0, 0, 0, 0, 12), p, iters=True)
+    x8, i8 = _run(fs, make, (0, 0, 0, 0, 0, 0, 0, 0, 8, 0), p, iters=True)
+    x12, i12 = _run(fs, make, (0, 0, 0, 0, 0, 0, 0, 0, 12, 0), p, iters=True)
     S = make(p)
     try:
         # the persistent work-list is built at ratio 8 first, then replaced
@@ -161,6 +162,40 @@ def test_chebyshev_interval_reaches_the_same_solution(fs, prec):
     assert not np.array_equal(x8, x12)
     assert rel_l2(x12, x8) <= 1e-9
     assert rel_l2(xp12, x12) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_refine"])
+def test_convection_diffusion_schur_reaches_the_same_solution(fs, prec):
+    """The pressure convection-diffusion Schur part is another preconditioner:
+    the solution agrees with the Cahouet-Chabard one within the parity bar,
+    on the channel (do-nothing outflow, fixed outflow rows), a jittered cube,
+    and a batch (per-instance viscosity and a pinned vertex per instance)."""
+    p = fs.FS_PREC_FP64 if prec == "fp64" else fs.FS_PREC_FP32_REFINE
+    cases = [(W.channel(64, 16), lambda w, q: fs.Stepper.from_workload(w, precision=q)),
+             (W.cube(8, jitter=0.05), lambda w, q: fs.Stepper.from_workload(w, precision=q)),
+             ([W.unit_square(12, nu=1 / 500.0, dt=1e-3), W.unit_square(20, nu=0.1, dt=1e-3)],
+              lambda w, q: fs.Stepper.from_workloads(w, precision=q))]
+    for wl, mk in cases:
+        make = lambda q: mk(wl, q)
+        xc, ic = _run(fs, make, (0, 0, 0, 0, 0, 0, 0, 0, 0, 0), p, nsteps=3, iters=True)
+        xp, ip = _run(fs, make, (0, 0, 0, 0, 0, 0, 0, 0, 0, 1), p, nsteps=3, iters=True)
+        print(prec, "iterations per step, Cahouet-Chabard / convection-diffusion:", ic, ip)
+        assert not np.array_equal(xc, xp)
+        assert rel_l2(xp, xc) <= 1e-9
+    S = fs.Stepper.from_workload(W.channel(64, 16), precision=p)
+    try:
+        with pytest.raises(fs.FsError):
+            fs.fs_set_schedule(S.prob, 0, 0, persistent_precond=1, schur=1)
+        with pytest.raises(fs.FsError):
+            fs.fs_set_schedule(S.prob, 0, 0, schur=2)
+        # switched on after the first step: the assembled system's pressure
+        # convection is built from the state at once
+        fs.fs_step(S.prob, 1)
+        fs.fs_set_schedule(S.prob, 0, 0, schur=1)
+        st = fs.fs_step(S.prob, 2)
+        assert all(s["status"] == 0 for s in st)
+    finally:
+        S.close()
 
 
 def test_autotune_smoother_restores_the_state(fs):
