@@ -52,8 +52,9 @@ def parse(argv=None):
                    help="Chebyshev degree on the finest multigrid level (0: the library "
                         "default, 2)")
     p.add_argument("--smoother-ratios", default="4,6,8,12,16",
-                   help="candidate Chebyshev interval ratios fs_autotune_smoother times at "
-                        "set-up on every workload ('' keeps the library default, 8)")
+                   help="candidate Chebyshev interval ratios the smoother tuner times at "
+                        "set-up on every workload, after the degree pairs (2,2), (1,2), (2,1), "
+                        "(1,1) ('' keeps the library defaults: ratio 8, degree 2)")
     p.add_argument("--smoother-steps", type=int, default=5,
                    help="steps the smoother autotuner times per candidate (channel; the "
                         "cube and the batch take 3)")
@@ -98,13 +99,17 @@ KERNELS = {
 }
 
 
+SMOOTHER_DEGREES = ((2, 2), (1, 2), (2, 1), (1, 1))
+
+
 def tune_smoother(fs, S, ratios, nsteps):
-    """Set-up, untimed: the smoother's Chebyshev interval, picked by timing
-    `nsteps` steps from the problem's current state under each candidate
-    (the library restores the state afterwards)."""
+    """Set-up, untimed: the smoother's degrees (coarse levels, finest level)
+    and then its Chebyshev interval, each picked by timing `nsteps` steps
+    from the problem's current state under every candidate (the library
+    restores the state afterwards)."""
     if not ratios:
         return None
-    return fs.fs_autotune_smoother(S.prob, nsteps=nsteps, ratios=ratios)
+    return fs.fs_tune_smoother(S.prob, nsteps=nsteps, degrees=SMOOTHER_DEGREES, ratios=ratios)
 
 
 def parse_ratios(text):

@@ -459,8 +459,13 @@ typedef struct {
                             4, 6 or 8; 0 = 6 in FP32, 4 in FP64 */
   int32_t smooth_group;  /* ... in the smoothing passes: 4 or 6; 0 = 4    */
   int32_t coarse_degree; /* degree of the Chebyshev smoother on the levels
-                            below the finest (pre and post): 3 or 2; 0 = 2.
-                            Unlike the other fields it changes the
+                            below the finest (pre and post): 3, 2 or 1;
+                            0 = 2 (1: the first step of the restriction is
+                            the pre-smoothing, one step after the
+                            correction the post-smoothing; not with the
+                            fused tail, which then stays off, nor with the
+                            persistent form).  Unlike the other fields it
+                            changes the
                             preconditioner, so iteration counts (not the
                             solution beyond rtol) depend on it; the
                             autotuner keeps the value in place          */
@@ -486,8 +491,8 @@ typedef struct {
                             ended after one second makes the solve return
                             FS_ERR_TIMEOUT.  fs_autotune times both forms */
   int32_t fine_degree;   /* degree of the Chebyshev smoother on the finest
-                            level of both hierarchies (pre and post): 3 or
-                            2; 0 = 2.  Like coarse_degree it changes the
+                            level of both hierarchies (pre and post): 3, 2
+                            or 1; 0 = 2.  Like coarse_degree it changes the
                             preconditioner (iteration counts, not the
                             solution beyond rtol); the autotuner keeps the
                             value in place                              */
@@ -495,8 +500,8 @@ typedef struct {
                             [1.1 lmax / cheb_ratio, 1.1 lmax] of D^-1 A on
                             every level (lmax estimated at set-up): 2 to
                             64; 0 = 8.  It changes the preconditioner like
-                            the degrees; fs_autotune_smoother picks it by
-                            timing steps                                */
+                            the degrees; fs_autotune_smoother picks it (and
+                            the degrees) by timing steps                */
   int32_t schur;         /* approximation of the pressure Schur complement:
                             0 Cahouet-Chabard, S^-1 = nu Mp^-1 + dt^-1 Kp^-1;
                             1 pressure convection-diffusion,
@@ -520,21 +525,25 @@ typedef struct {
 int fs_get_schedule(const fs_problem* prob, fs_schedule* out);
 int fs_set_schedule(fs_problem* prob, const fs_schedule* sched);
 int fs_autotune(fs_problem* prob, int reps, fs_tune_report* report);
-/* Picks the Chebyshev interval of the smoother (fs_schedule.cheb_ratio) by
- * timing steps: for each of the nratios candidate ratios (2 to 64) the
- * problem's state is put back to the one at the call, one untimed step
- * captures the solver's graphs, the state is put back again and nsteps
- * steps are timed with CUDA events on the problem's stream.  The fastest
- * ratio is installed and the state at the call is restored, with no step
- * history (the next solves start as after fs_set_state at another time).
- * ms_out / iters_out (host, nratios entries, may be NULL) receive each
- * candidate's mean time and inner iterations per step; best_out (may be
- * NULL) the installed ratio.  No counterpart in the paper (its solver is a
- * library call).  FS_ERR_UNSUPPORTED for P3/P2 problems, FS_ERR_BUSY while
- * a step is in progress, the first failing step's status otherwise (the
- * state is restored and the schedule left as it was).  Synchronises. */
-int fs_autotune_smoother(fs_problem* prob, int nsteps, const int32_t* ratios, int nratios,
-                         double* ms_out, double* iters_out, int32_t* best_out);
+/* Picks the smoother (fs_schedule.cheb_ratio, coarse_degree, fine_degree)
+ * by timing steps.  cand holds ncand triples (cheb_ratio, coarse_degree,
+ * fine_degree); a 0 keeps that field of the installed schedule.  For each
+ * candidate the problem's state is put back to the one at the call, one
+ * untimed step captures the solver's graphs, the state is put back again
+ * and nsteps steps are timed with CUDA events on the problem's stream.  The
+ * fastest candidate is installed and the state at the call is restored,
+ * with no step history (the next solves start as after fs_set_state at
+ * another time).  ms_out / iters_out (host, ncand entries, may be NULL)
+ * receive each candidate's mean time and inner iterations per step;
+ * best_out (may be NULL) the installed schedule.  Callers can search the
+ * fields one after the other (degrees, then the interval).  No counterpart
+ * in the paper (its solver is a library call).  FS_ERR_INVALID_ARG for a
+ * field out of its range (fs_set_schedule's), FS_ERR_UNSUPPORTED for P3/P2
+ * problems or a degree of 1 with the persistent form, FS_ERR_BUSY while a
+ * step is in progress, the first failing step's status otherwise (the state
+ * is restored and the schedule left as it was).  Synchronises. */
+int fs_autotune_smoother(fs_problem* prob, int nsteps, const int32_t* cand, int ncand,
+                         double* ms_out, double* iters_out, fs_schedule* best_out);
 
 /* Instrumentation (no counterpart in the paper).
  * fs_launch_count: kernels launched by this library since load, counting

@@ -559,8 +559,8 @@ void apply_groups(fs_problem* P, Precision<T>& pr, const fs_schedule& sc) {
   (void)P;
   pr.op.group = sc.spmv_group;
   pr.HA.group = pr.HK.group = sc.smooth_group ? sc.smooth_group : 4;
-  pr.HA.coarse_deg = pr.HK.coarse_deg = sc.coarse_degree == 3 ? 3 : 2;
-  pr.HA.fine_deg = pr.HK.fine_deg = sc.fine_degree == 3 ? 3 : 2;
+  pr.HA.coarse_deg = pr.HK.coarse_deg = sc.coarse_degree ? sc.coarse_degree : 2;
+  pr.HA.fine_deg = pr.HK.fine_deg = sc.fine_degree ? sc.fine_degree : 2;
   const int ratio = sc.cheb_ratio ? sc.cheb_ratio : 8;
   if (ratio != pr.cheb_ratio) {
     for (DHier<T>* H : {&pr.HA, &pr.HK})
@@ -575,7 +575,8 @@ void apply_groups(fs_problem* P, Precision<T>& pr, const fs_schedule& sc) {
 template <typename T>
 int apply_tail(fs_problem* P, DHier<T>& D, int64_t tail_rows) {
   D.tail = -1;
-  if (tail_rows > 0)
+  // (the fused cluster tail smooths with degree 2 or 3)
+  if (tail_rows > 0 && D.coarse_deg != 1 && D.fine_deg != 1)
     for (int l = 0; l + 1 < D.nlev; ++l)
       if (D.lev[l].A.nrow <= tail_rows) {
         D.tail = l;
@@ -2687,16 +2688,16 @@ int fs_set_schedule(fs_problem* P, const fs_schedule* sc) {
   };
   if (!P || !sc || sc->tail_rows_velocity < 0 || sc->tail_rows_pressure < 0 ||
       !in(sc->spmv_group, {0, 4, 6, 8}) || !in(sc->smooth_group, {0, 4, 6}) ||
-      !in(sc->coarse_degree, {0, 2, 3}) || !in(sc->serial_launches, {0, 1}) ||
-      !in(sc->persistent_precond, {0, 1}) || !in(sc->fine_degree, {0, 2, 3}) ||
+      !in(sc->coarse_degree, {0, 1, 2, 3}) || !in(sc->serial_launches, {0, 1}) ||
+      !in(sc->persistent_precond, {0, 1}) || !in(sc->fine_degree, {0, 1, 2, 3}) ||
       (sc->cheb_ratio != 0 && (sc->cheb_ratio < 2 || sc->cheb_ratio > 64)) ||
       !in(sc->schur, {0, 1})) {
     set_error("fs_set_schedule: bad argument");
     return FS_ERR_INVALID_ARG;
   }
-  if (sc->schur && sc->persistent_precond) {
+  if (sc->persistent_precond && (sc->schur || sc->coarse_degree == 1 || sc->fine_degree == 1)) {
     set_error("fs_set_schedule: the persistent preconditioner takes the Cahouet-Chabard "
-              "Schur part only");
+              "Schur part and smoothing degrees 2 and 3 only");
     return FS_ERR_UNSUPPORTED;
   }
   if (P->ctx.phase != PH_IDLE && P->ctx.phase != PH_DONE) {
@@ -2779,7 +2780,7 @@ int fs_autotune(fs_problem* P, int reps, fs_tune_report* report) {
     double ms0 = 0, ms1 = 0;
     FS_TRY(time_precond(P, reps, 0, &ms0));
     int rc = FS_ERR_UNSUPPORTED;
-    if (!base.schur)
+    if (!base.schur && base.coarse_degree != 1 && base.fine_degree != 1)
       rc = P->desc.precision == FS_PREC_FP64 ? apply_flow<double>(P, P->p64)
                                              : apply_flow<float>(P, P->p32);
     if (rc == FS_OK) rc = time_precond(P, reps, 1, &ms1);
@@ -2808,27 +2809,40 @@ int fs_autotune(fs_problem* P, int reps, fs_tune_report* report) {
   return FS_OK;
 }
 
-int fs_autotune_smoother(fs_problem* P, int nsteps, const int32_t* ratios, int nratios,
-                         double* ms_out, double* iters_out, int32_t* best_out) {
+int fs_autotune_smoother(fs_problem* P, int nsteps, const int32_t* cand, int ncand,
+                         double* ms_out, double* iters_out, fs_schedule* best_out) {
   if (P && P->p3) {
     set_error("fs_autotune_smoother: P3/P2 problems are stepped by fs_step_ipcs");
     return FS_ERR_UNSUPPORTED;
   }
-  if (!P || nsteps < 1 || !ratios || nratios < 1 || nratios > 64) {
+  if (!P || nsteps < 1 || !cand || ncand < 1 || ncand > 64) {
     set_error("fs_autotune_smoother: bad argument");
     return FS_ERR_INVALID_ARG;
   }
-  for (int q = 0; q < nratios; ++q)
-    if (ratios[q] < 2 || ratios[q] > 64) {
-      set_error("fs_autotune_smoother: interval ratios must lie in [2, 64]");
-      return FS_ERR_INVALID_ARG;
-    }
   if (P->ctx.phase != PH_IDLE && P->ctx.phase != PH_DONE) {
     set_error("fs_autotune_smoother: a step is in progress");
     return FS_ERR_BUSY;
   }
-  cudaStream_t s = P->stream;
   const fs_schedule base = P->sched;
+  std::vector<fs_schedule> scs(ncand, base);
+  for (int q = 0; q < ncand; ++q) {
+    const int32_t* c = cand + 3 * q;
+    if (c[0]) scs[q].cheb_ratio = c[0];
+    if (c[1]) scs[q].coarse_degree = c[1];
+    if (c[2]) scs[q].fine_degree = c[2];
+    const fs_schedule& sc = scs[q];
+    if ((sc.cheb_ratio != 0 && (sc.cheb_ratio < 2 || sc.cheb_ratio > 64)) ||
+        sc.coarse_degree < 0 || sc.coarse_degree > 3 || sc.fine_degree < 0 ||
+        sc.fine_degree > 3) {
+      set_error("fs_autotune_smoother: a candidate field is out of range");
+      return FS_ERR_INVALID_ARG;
+    }
+    if (sc.persistent_precond && (sc.coarse_degree == 1 || sc.fine_degree == 1)) {
+      set_error("fs_autotune_smoother: degree 1 with the persistent preconditioner");
+      return FS_ERR_UNSUPPORTED;
+    }
+  }
+  cudaStream_t s = P->stream;
   const double t0 = P->t;
   // the state at the call, in a scratch copy freed before returning
   double* x0 = nullptr;
@@ -2847,10 +2861,8 @@ int fs_autotune_smoother(fs_problem* P, int nsteps, const int32_t* ratios, int n
   std::vector<fs_solve_stats> st(nsteps);
   int rc = FS_OK, best = -1;
   double best_ms = 0;
-  for (int q = 0; q < nratios && rc == FS_OK; ++q) {
-    fs_schedule sc = base;
-    sc.cheb_ratio = ratios[q];
-    rc = install_schedule(P, sc);
+  for (int q = 0; q < ncand && rc == FS_OK; ++q) {
+    rc = install_schedule(P, scs[q]);
     // one untimed step captures the solver's graphs for this schedule
     if (rc == FS_OK && restore() != cudaSuccess) rc = FS_ERR_CUDA;
     if (rc == FS_OK) rc = fs_step(P, 1, nullptr, st.data());
@@ -2874,8 +2886,7 @@ int fs_autotune_smoother(fs_problem* P, int nsteps, const int32_t* ratios, int n
       best_ms = ms;
     }
   }
-  fs_schedule fin = base;
-  if (rc == FS_OK) fin.cheb_ratio = ratios[best];
+  const fs_schedule fin = rc == FS_OK ? scs[best] : base;
   const std::string err = rc == FS_OK ? std::string() : fs_last_error();
   int rc2 = install_schedule(P, fin);
   if (restore() != cudaSuccess && rc2 == FS_OK) rc2 = FS_ERR_CUDA;
@@ -2888,7 +2899,7 @@ int fs_autotune_smoother(fs_problem* P, int nsteps, const int32_t* ratios, int n
     return rc;
   }
   if (rc2 != FS_OK) return rc2;
-  if (best_out) *best_out = ratios[best];
+  if (best_out) *best_out = P->sched;
   return FS_OK;
 }
 

@@ -752,6 +752,21 @@ void vcycle_level(const DHier<T>& H, int l, JVec<T> out, int64_t out_ld, int nc,
   T *G0 = H.G0[l], *G1 = H.G1[l], *D0 = H.D0[l], *D1 = H.D1[l];
   const T* b = H.b[l];
   const bool coarsest_next = l + 1 == H.nlev - 1;
+  if ((top ? H.fine_deg : H.coarse_deg) == 1) {
+    // degree 1: the first step of the load or restriction (x1 in G0, D0) is
+    // the whole pre-smoothing; the residual into the free G1, the correction
+    // into G0, and one step from there (the first step's formula, alpha = 0)
+    // gives the level's result in G1
+    launch_mg<T, NCP>(MG_RESID, L, b, G0, D0, G1, nullptr, T(0), T(0), JVec<T>(), 0, nullptr,
+                      nc, skip, H.group, s);
+    launch_restrict<T, NCP>(L.R, G1, H.b[l + 1], H.G0[l + 1], H.D0[l + 1],
+                            coarsest_next ? nullptr : C.dinv, (T)C.inv_theta, C.skip, skip, s);
+    vcycle_level<T, NCP>(H, l + 1, JVec<T>(), 0, nc, skip, s);
+    launch_prolong<T, NCP>(L.P, H.G1[l + 1], G0, L.skip, skip, s);
+    launch_mg<T, NCP>(MG_LAST, L, b, G0, D0, G1, nullptr, T(0), (T)L.inv_theta,
+                      top ? out : JVec<T>(), out_ld, top ? H.perm : nullptr, nc, skip, H.group, s);
+    return;
+  }
   if ((top ? H.fine_deg : H.coarse_deg) == 2) {
     // degree 2 on a coarse level: one step after the restriction's first
     // (x2 in G1), the residual into the free D0, the correction into G1,
@@ -1154,7 +1169,7 @@ void launch_precond(const DOp<T>& op, const DHier<T>& HA, const DHier<T>& HK,
   {
     const bool k1 = HK.nlev > 1;
     const DLevel<T>& L0 = HK.lev[0];
-    if (k1 && HK.tail != 0 && !HK.perm) {
+    if (k1 && HK.tail != 0 && !HK.perm && HK.fine_deg != 1) {
       if (HK.group == 6)
         launch_k(k_mg_first1<T, 6>, blocks_for(nv), 256, 0, s, L0.A, L0.dinv, rp,
                  (T)L0.inv_theta, (T)L0.a1, (T)L0.b1, HK.b[0], HK.G1[0], HK.D1[0], L0.skip, skip);

@@ -187,7 +187,7 @@ _lib.fs_get_schedule.restype = _int
 _lib.fs_get_schedule.argtypes = [_vp, _P(fs_schedule)]
 _lib.fs_autotune_smoother.restype = _int
 _lib.fs_autotune_smoother.argtypes = [_vp, _int, _P(ctypes.c_int32), _int, _P(_d), _P(_d),
-                                      _P(ctypes.c_int32)]
+                                      _P(fs_schedule)]
 _lib.fs_set_schedule.restype = _int
 _lib.fs_set_schedule.argtypes = [_vp, _P(fs_schedule)]
 _lib.fs_autotune.restype = _int
@@ -527,19 +527,32 @@ def fs_autotune(prob, reps=10):
     return r.as_dict()
 
 
-def fs_autotune_smoother(prob, nsteps=3, ratios=(4, 6, 8, 12, 16)):
-    """Times `nsteps` steps from the current state under each Chebyshev
-    interval ratio, installs the fastest and restores the state; returns
-    {"ratios", "ms_per_step", "iters_per_step", "best"}."""
-    n = len(ratios)
-    rr = (ctypes.c_int32 * n)(*[int(r) for r in ratios])
+def fs_autotune_smoother(prob, candidates, nsteps=3):
+    """Times `nsteps` steps from the current state under each candidate
+    (cheb_ratio, coarse_degree, fine_degree) (0 keeps the installed value),
+    installs the fastest and restores the state; returns the trials and the
+    installed schedule."""
+    n = len(candidates)
+    flat = [int(v) for c in candidates for v in c]
+    cc = (ctypes.c_int32 * (3 * n))(*flat)
     ms = (_d * n)()
     it = (_d * n)()
-    best = ctypes.c_int32(0)
-    _check(_lib.fs_autotune_smoother(prob, int(nsteps), rr, n, ms, it, ctypes.byref(best)),
+    best = fs_schedule()
+    _check(_lib.fs_autotune_smoother(prob, int(nsteps), cc, n, ms, it, ctypes.byref(best)),
            "fs_autotune_smoother")
-    return {"ratios": list(ratios), "ms_per_step": list(ms), "iters_per_step": list(it),
-            "best": int(best.value)}
+    return {"candidates": [list(c) for c in candidates], "ms_per_step": list(ms),
+            "iters_per_step": list(it), "best": best.as_dict()}
+
+
+def fs_tune_smoother(prob, nsteps=3, degrees=((2, 2), (1, 2), (2, 1), (1, 1)),
+                     ratios=(4, 6, 8, 12, 16)):
+    """The smoother picked field by field: the degree pairs (coarse, finest)
+    at the installed interval, then the interval at the chosen degrees."""
+    d = fs_autotune_smoother(prob, [(0, c, f) for c, f in degrees], nsteps) if degrees else None
+    r = fs_autotune_smoother(prob, [(q, 0, 0) for q in ratios], nsteps) if ratios else None
+    sc = fs_get_schedule(prob)
+    return {"degrees": d, "ratios": r, "cheb_ratio": sc["cheb_ratio"],
+            "coarse_degree": sc["coarse_degree"], "fine_degree": sc["fine_degree"]}
 
 
 def fs_profile_kernel(prob, kernel, reps=20, cold=False):

@@ -148,6 +148,10 @@ def test_chebyshev_interval_reaches_the_same_solution(fs, prec):
     make = lambda q: fs.Stepper.from_workload(wl, precision=q)
     x8, i8 = _run(fs, make, (0, 0, 0, 0, 0, 0, 0, 0, 8, 0), p, iters=True)
     x12, i12 = _run(fs, make, (0, 0, 0, 0, 0, 0, 0, 0, 12, 0), p, iters=True)
+    # degree 1 on every level (the restriction's or load's first step alone)
+    x1, i1 = _run(fs, make, (0, 0, 0, 0, 1, 0, 0, 1, 8, 0), p, iters=True)
+    print(prec, "iterations per step, degree 1:", i1)
+    assert rel_l2(x1, x8) <= 1e-9
     S = make(p)
     try:
         # the persistent work-list is built at ratio 8 first, then replaced
@@ -203,18 +207,22 @@ def test_autotune_smoother_restores_the_state(fs):
     try:
         fs.fs_step(S.prob, 2)
         x0, t0 = S.state()
-        rep = fs.fs_autotune_smoother(S.prob, nsteps=2, ratios=(6, 12))
+        rep = fs.fs_tune_smoother(S.prob, nsteps=2, degrees=((2, 2), (1, 1)), ratios=(6, 12))
         print(rep)
-        assert rep["best"] in (6, 12)
-        assert all(m > 0 for m in rep["ms_per_step"])
-        assert all(i > 0 for i in rep["iters_per_step"])
-        assert fs.fs_get_schedule(S.prob)["cheb_ratio"] == rep["best"]
+        assert rep["cheb_ratio"] in (6, 12)
+        assert (rep["coarse_degree"], rep["fine_degree"]) in ((2, 2), (1, 1))
+        for part in ("degrees", "ratios"):
+            assert all(m > 0 for m in rep[part]["ms_per_step"])
+            assert all(i > 0 for i in rep[part]["iters_per_step"])
+        assert fs.fs_get_schedule(S.prob) == rep["ratios"]["best"]
         x1, t1 = S.state()
         assert t1 == t0 and np.array_equal(x0, x1)
         st = fs.fs_step(S.prob, 1)[0]
         assert st["status"] == 0 and st["rel_res"] <= 1e-12
         with pytest.raises(fs.FsError):
-            fs.fs_autotune_smoother(S.prob, nsteps=1, ratios=(1,))
+            fs.fs_autotune_smoother(S.prob, [(1, 0, 0)], nsteps=1)
+        with pytest.raises(fs.FsError):
+            fs.fs_autotune_smoother(S.prob, [(0, 4, 0)], nsteps=1)
         with pytest.raises(fs.FsError):
             fs.fs_set_schedule(S.prob, 0, 0, cheb_ratio=100)
     finally:
@@ -253,6 +261,6 @@ def test_autotune_installs_a_candidate(fs):
         with pytest.raises(fs.FsError):
             fs.fs_set_schedule(S.prob, 0, 0, persistent_precond=2)
         with pytest.raises(fs.FsError):
-            fs.fs_set_schedule(S.prob, 0, 0, fine_degree=1)
+            fs.fs_set_schedule(S.prob, 0, 0, fine_degree=4)
     finally:
         S.close()
