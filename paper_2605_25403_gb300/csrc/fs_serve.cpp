@@ -103,11 +103,12 @@ int64_t estimate_bytes(const fs_mesh_desc& md, int precision) {
   if (precision == FS_PREC_FP32_REFINE) b += 4 * (nnzA + 2 * dim * nnzB);
   b += s * (61.0 * ndof + dim * n2 + nv);                            // V, Z, work
   b += 1.6 * (s * nnzA + 4 * nnzA + 5 * s * dim * n2);              // hierarchies
-  // dense coarsest inverses: large problems keep up to 3500 rows per
+  // dense coarsest inverses: large 3D problems keep up to 3500 rows per
   // hierarchy, inverted on the device through a 3500 x 7000 FP64 workspace
-  // (one at a time, freed after set-up); smaller ones at most 800 rows
-  const double nc = n2 >= 100000 ? 3500.0 : 800.0;
-  b += 2 * s * nc * nc + (n2 >= 100000 ? 16.0 * nc * nc : 0.0);
+  // (one at a time, freed after set-up); the others at most 800 rows
+  const bool big = n2 >= 100000 && dim == 3;
+  const double nc = big ? 3500.0 : 800.0;
+  b += 2 * s * nc * nc + (big ? 16.0 * nc * nc : 0.0);
   // partial sums: tiles of up to 2048 entries, or up to four per SM when
   // the problem is small (counted for up to 256 SMs)
   b += 8.0 * 33 * std::max(ndof / 2048.0 + 2 * dim + 1, 1024.0);
