@@ -1818,14 +1818,15 @@ int fs_problem_create_batch(fs_mesh* mesh, const fs_problem_desc* descs, int cou
   for (int64_t q = 0; q < P->nv; ++q) mplinv_nu[q] = nu_vert[q] / mplh[q];
   for (int32_t q : P->pinned_host) mplinv_nu[q] = -1.0;
   UnionHierarchy HA, HK;
-  // coarsest size.  Large 3D problems stop coarsening at 3500 rows: the
-  // dense inverse (on the device, ~0.1 s of set-up) then replaces the one or
-  // two latency-bound coarsest levels of each V-cycle with one dense matvec.
-  // In 2D a grid coarsened by 4 more is cheaper than that matvec (a 3,225
-  // x 3,225 inverse is 41.6 MB in FP32), and small problems would pay the
-  // device inversion in their set-up latency (the serving loop creates
-  // many), so they keep 800 rows; batches keep small per-instance blocks.
-  const int64_t cmax = count > 1 ? 400 : (me.n2 >= 100000 && me.dim == 3) ? 3500 : 800;
+  // coarsest size.  Large problems stop coarsening at 3500 rows in 3D and
+  // 2000 in 2D: the dense inverse (on the device, ~0.1 s of set-up) then
+  // replaces the one or two latency-bound coarsest levels of each V-cycle
+  // with one dense matvec.  In 2D a grid of 2000 to 3500 rows coarsened by
+  // 4 once more is cheaper than that matvec (a 3,225 x 3,225 inverse is
+  // 41.6 MB in FP32).  Small problems would pay the device inversion in
+  // their set-up latency (the serving loop creates many), so they keep 800
+  // rows; batches keep small per-instance blocks.
+  const int64_t cmax = count > 1 ? 400 : me.n2 >= 100000 ? (me.dim == 3 ? 3500 : 2000) : 800;
   build_union_hierarchy(me, {}, A0, true, me.dlist, cmax, HA);
   build_union_hierarchy(me, {}, Kp, false, kfix, cmax, HK);
 

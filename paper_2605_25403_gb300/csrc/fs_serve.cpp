@@ -103,11 +103,11 @@ int64_t estimate_bytes(const fs_mesh_desc& md, int precision) {
   if (precision == FS_PREC_FP32_REFINE) b += 4 * (nnzA + 2 * dim * nnzB);
   b += s * (61.0 * ndof + dim * n2 + nv);                            // V, Z, work
   b += 1.6 * (s * nnzA + 4 * nnzA + 5 * s * dim * n2);              // hierarchies
-  // dense coarsest inverses: large 3D problems keep up to 3500 rows per
-  // hierarchy, inverted on the device through a 3500 x 7000 FP64 workspace
-  // (one at a time, freed after set-up); the others at most 800 rows
-  const bool big = n2 >= 100000 && dim == 3;
-  const double nc = big ? 3500.0 : 800.0;
+  // dense coarsest inverses: large problems keep up to 3500 (3D) or 2000
+  // (2D) rows per hierarchy, inverted on the device through an n x 2n FP64
+  // workspace (one at a time, freed after set-up); smaller ones at most 800
+  const bool big = n2 >= 100000;
+  const double nc = big ? (dim == 3 ? 3500.0 : 2000.0) : 800.0;
   b += 2 * s * nc * nc + (big ? 16.0 * nc * nc : 0.0);
   // partial sums: tiles of up to 2048 entries, or up to four per SM when
   // the problem is small (counted for up to 256 SMs)

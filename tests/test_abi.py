@@ -118,13 +118,14 @@ def test_server_estimate_and_rejection(fs):
 
 
 def test_server_estimate_covers_history_and_dense_coarsest(fs):
-    """A 3D request of at least 100,000 P2 nodes keeps coarsest levels of up
-    to 3,500 rows (dense FP32 inverses, made through an FP64 workspace at
-    set-up) and four previous states for the steps' starting guesses: the
-    admission estimate counts them with the Krylov basis."""
-    wl = W.C3
-    est = fs.fs_server_estimate_bytes(wl)
-    krylov = 4 * 61 * wl.ndof          # V (31 vectors) and Z (30), FP32
-    history = 8 * 4 * wl.ndof          # previous states, FP64
-    dense = (2 * 4 + 16) * 3500 ** 2   # two FP32 inverses + the set-up workspace
-    assert est >= krylov + history + dense
+    """A request of at least 100,000 P2 nodes keeps coarsest levels of up to
+    3,500 rows in 3D and 2,000 in 2D (dense FP32 inverses, made through an
+    FP64 workspace at set-up) and four previous states for the steps'
+    starting guesses: the admission estimate counts them with the Krylov
+    basis."""
+    for wl, nc in ((W.C3, 3500), (W.C2, 2000)):
+        est = fs.fs_server_estimate_bytes(wl)
+        krylov = 4 * 61 * wl.ndof          # V (31 vectors) and Z (30), FP32
+        history = 8 * 4 * wl.ndof          # previous states, FP64
+        dense = (2 * 4 + 16) * nc ** 2     # two FP32 inverses + the set-up workspace
+        assert est >= krylov + history + dense
