@@ -55,6 +55,10 @@ def parse(argv=None):
                    help="candidate Chebyshev interval ratios the smoother tuner times at "
                         "set-up on every workload, after the degree pairs (2,2), (1,2), (2,1), "
                         "(1,1) ('' keeps the library defaults: ratio 8, degree 2)")
+    p.add_argument("--smoother", default="",
+                   help="fixed smoother 'COARSE,FINEST,RATIO' (degrees and Chebyshev interval "
+                        "ratio) instead of the set-up tuner, for profiler runs, under which the "
+                        "tuner's step timings are distorted")
     p.add_argument("--smoother-steps", type=int, default=5,
                    help="steps the smoother autotuner times per candidate (channel; the "
                         "cube and the batch take 3)")
@@ -102,11 +106,17 @@ KERNELS = {
 SMOOTHER_DEGREES = ((2, 2), (1, 2), (2, 1), (1, 1))
 
 
+FIXED_SMOOTHER = None  # (coarse degree, finest degree, ratio) from --smoother
+
+
 def tune_smoother(fs, S, ratios, nsteps):
     """Set-up, untimed: the smoother's degrees (coarse levels, finest level)
     and then its Chebyshev interval, each picked by timing `nsteps` steps
     from the problem's current state under every candidate (the library
-    restores the state afterwards)."""
+    restores the state afterwards); or the fixed smoother of --smoother."""
+    if FIXED_SMOOTHER:
+        c, f, r = FIXED_SMOOTHER
+        return fs.fs_autotune_smoother(S.prob, [(r, c, f)], nsteps=1)["best"]
     if not ratios:
         return None
     return fs.fs_tune_smoother(S.prob, nsteps=nsteps, degrees=SMOOTHER_DEGREES, ratios=ratios)
@@ -520,6 +530,9 @@ def main():
 
     wl = workload(args.workload)
     ratios = parse_ratios(args.smoother_ratios)
+    global FIXED_SMOOTHER
+    if args.smoother:
+        FIXED_SMOOTHER = tuple(int(q) for q in args.smoother.split(","))
     prec = fs.FS_PREC_FP32_REFINE if args.precision == "fp32_refine" else fs.FS_PREC_FP64
     stream = torch.cuda.Stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
